@@ -1,0 +1,194 @@
+"""CPU FP64 oracle for QR factorization in an oblique inner product.
+
+TEST INFRASTRUCTURE ONLY: the slow, plain reference that the CUDA path is
+checked against (arXiv:1401.5171).  Only the tests, the smoke check and the
+benchmark's CPU-baseline arm may import this package; the CUDA library never
+does.  The arithmetic lives in ``oqr_oracle.c`` (plain C, FP64, no blocking);
+this module only builds it with gcc and marshals numpy arrays.
+
+Every matrix argument is a 2-D float64 numpy array; it is passed column-major
+(Fortran order, leading dimension = number of rows), copied if needed.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oqr_oracle.c")
+_LIB = os.path.join(_HERE, "liboqr_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (OpenMP, IEEE semantics, no FMA contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        cmd = ["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+               "-fno-fast-math", "-std=c99", _SRC, "-o", _LIB + ".tmp", "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(_LIB + ".tmp", _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = os.environ.get("OQR_ORACLE_LIB")   # a planted-mistake build (mutation test)
+            if not path:
+                path = build()
+            lib = ctypes.CDLL(path)
+            dp = ctypes.POINTER(ctypes.c_double)
+            i, l = ctypes.c_int, ctypes.c_long
+            lib.orc_chol_upper.argtypes = [i, dp, l, dp, l]
+            lib.orc_chol_upper.restype = i
+            lib.orc_symm_times.argtypes = [i, i, dp, l, dp, l, dp, l]
+            lib.orc_gram.argtypes = [i, i, dp, l, dp, l, dp, l]
+            lib.orc_trsm_right_upper.argtypes = [i, i, dp, l, dp, l, dp, l]
+            lib.orc_upper_times_upper.argtypes = [i, dp, l, dp, l, dp, l]
+            lib.orc_cholqr.argtypes = [i, i, dp, l, dp, l, dp, l, dp, l]
+            lib.orc_cholqr.restype = i
+            lib.orc_householder_qr.argtypes = [i, i, dp, l, dp, l, dp, l]
+            lib.orc_oblique_qr.argtypes = [i, i, dp, l, dp, l, dp, l, dp, l]
+            lib.orc_oblique_qr.restype = i
+            lib.orc_orth_defect.argtypes = [i, i, dp, l, dp, l, dp, l]
+            lib.orc_repres_residual.argtypes = [i, i, dp, l, dp, l, dp, l, dp, l]
+            _lib = lib
+    return _lib
+
+
+def _f(x):
+    x = np.asarray(x, dtype=np.float64)
+    if x.ndim == 1:
+        x = x.reshape(-1, 1)
+    return np.asfortranarray(x)
+
+
+def _p(x):
+    return x.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _ld(x):
+    return max(1, x.shape[0])
+
+
+class OracleBreakdown(RuntimeError):
+    """Cholesky breakdown: the 1-based column is in ``.column``."""
+
+    def __init__(self, what, column):
+        super().__init__(f"{what}: Cholesky breakdown at column {column}")
+        self.column = column
+
+
+def chol_upper(A):
+    """C upper with A = C^T C (lower triangle of A read)."""
+    A = _f(A)
+    n = A.shape[0]
+    C = np.zeros((n, n), order="F")
+    info = _load().orc_chol_upper(n, _p(A), _ld(A), _p(C), _ld(C))
+    if info:
+        raise OracleBreakdown("chol_upper", info)
+    return C
+
+
+def symm_times(A, Z):
+    A, Z = _f(A), _f(Z)
+    m, n = Z.shape
+    B = np.zeros((m, n), order="F")
+    _load().orc_symm_times(m, n, _p(A), _ld(A), _p(Z), _ld(Z), _p(B), _ld(B))
+    return B
+
+
+def gram(A, Z):
+    """G = Z^T A Z (Algorithm 1, lines 1-2)."""
+    A, Z = _f(A), _f(Z)
+    m, n = Z.shape
+    G = np.zeros((n, n), order="F")
+    _load().orc_gram(m, n, _p(A), _ld(A), _p(Z), _ld(Z), _p(G), _ld(G))
+    return G
+
+
+def trsm_right_upper(Z, R):
+    """Q = Z R^{-1}, row by row (Algorithm 1, line 4)."""
+    Z, R = _f(Z), _f(R)
+    m, n = Z.shape
+    Q = np.zeros((m, n), order="F")
+    _load().orc_trsm_right_upper(m, n, _p(Z), _ld(Z), _p(R), _ld(R), _p(Q), _ld(Q))
+    return Q
+
+
+def upper_times_upper(U, S):
+    U, S = _f(U), _f(S)
+    n = U.shape[0]
+    R = np.zeros((n, n), order="F")
+    _load().orc_upper_times_upper(n, _p(U), _ld(U), _p(S), _ld(S), _p(R), _ld(R))
+    return R
+
+
+def cholqr(A, Z):
+    """CHOLQR (Algorithm 1) restated on the CPU; returns (Q, R)."""
+    A, Z = _f(A), _f(Z)
+    m, n = Z.shape
+    Q = np.zeros((m, n), order="F")
+    R = np.zeros((n, n), order="F")
+    info = _load().orc_cholqr(m, n, _p(A), _ld(A), _p(Z), _ld(Z), _p(Q), _ld(Q), _p(R), _ld(R))
+    if info:
+        raise OracleBreakdown("cholqr", info)
+    return Q, R
+
+
+def householder_qr(W):
+    """Euclidean Householder QR, thin Y and R_h (signs as produced)."""
+    W = _f(W).copy(order="F")
+    m, n = W.shape
+    Y = np.zeros((m, n), order="F")
+    Rh = np.zeros((n, n), order="F")
+    _load().orc_householder_qr(m, n, _p(W), _ld(W), _p(Y), _ld(Y), _p(Rh), _ld(Rh))
+    return Y, Rh
+
+
+def oblique_qr(A, Z):
+    """The oracle: (Q, R) of Z = QR with Q^T A Q = I by CHOL-EQR (Algorithm 3)."""
+    A, Z = _f(A), _f(Z)
+    m, n = Z.shape
+    Q = np.zeros((m, n), order="F")
+    R = np.zeros((n, n), order="F")
+    info = _load().orc_oblique_qr(m, n, _p(A), _ld(A), _p(Z), _ld(Z), _p(Q), _ld(Q), _p(R), _ld(R))
+    if info:
+        raise OracleBreakdown("oblique_qr", info)
+    return Q, R
+
+
+def orth_defect(A, Q):
+    """E = Q^T A Q - I, summed in long double."""
+    A, Q = _f(A), _f(Q)
+    m, n = Q.shape
+    E = np.zeros((n, n), order="F")
+    _load().orc_orth_defect(m, n, _p(A), _ld(A), _p(Q), _ld(Q), _p(E), _ld(E))
+    return E
+
+
+def repres_residual(Z, Q, R):
+    """D = Z - Q R, summed in long double."""
+    Z, Q, R = _f(Z), _f(Q), _f(R)
+    m, n = Z.shape
+    D = np.zeros((m, n), order="F")
+    _load().orc_repres_residual(m, n, _p(Z), _ld(Z), _p(Q), _ld(Q), _p(R), _ld(R), _p(D), _ld(D))
+    return D
+
+
+def orth_error(A, Q):
+    """||Q^T A Q - I||_2 (Sec. 7's orthogonality measure)."""
+    E = orth_defect(A, Q)
+    return float(np.max(np.abs(np.linalg.eigvalsh(0.5 * (E + E.T))))) if E.size else 0.0
+
+
+def repres_error(Z, Q, R):
+    """||Z - Q R||_2 / ||Z||_2 (Sec. 7's representativity measure)."""
+    D = repres_residual(Z, Q, R)
+    return float(np.linalg.norm(D, 2) / np.linalg.norm(np.asarray(Z), 2))
