@@ -1,0 +1,367 @@
+#!/usr/bin/env python
+"""Benchmark of the oblique-QR hot path on GB300.
+
+One step = one oblique QR factorization (Z = Q R, Q^T A Q = I) of the
+single large instance m=32768, n=256 with kappa(A)=1e6 and kappa(Z)=1e2
+(dense SPD A, lower triangle read), through the library's C ABI.  The
+default path is A-CholQR2 in FP64.  Inputs are synthetic (the Sec. 7
+recipe; A is 8.6 GB, larger than L2, so no flush is needed between steps).
+
+Prints one JSON line (rank 0).  Under torchrun every rank factors its own
+instance (replicas, weak scaling; the instances are independent).
+`--impl reference` times the CPU oracle (CHOL-EQR, plain C) on the host cores
+on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "oblique QRs/sec and TFLOP/s at ||Q^T A Q - I|| <= 1e-12, mixed vs FP64 on one GB300"
+SMS, FP64_FLOPS_PER_CLK_SM = 152, 4      # GB300: 2 FP64 FMAs per clock per SM
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--m", type=int, default=32768)
+    p.add_argument("--n", type=int, default=256)
+    p.add_argument("--kappa-a", type=float, default=1e6)
+    p.add_argument("--kappa-z", type=float, default=1e2)
+    p.add_argument("--algo", default="cholqr2", choices=["cholqr", "cholqr2", "scholqr3", "cgs2"])
+    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def normalised_flops(m, n, passes):
+    """The paper's count for CHOLQR, 2 m^2 n + 2 m n^2 per pass (Sec. 8)."""
+    return passes * (2.0 * m * m * n + 2.0 * m * n * n)
+
+
+def gram_algorithmic_flops(m, n):
+    """Flops of one fused symmetric Gram launch: the lower-triangle product
+    M Z (m(m+1)/2 x n multiply-adds) plus Z^T (M Z) (m n^2 multiply-adds)."""
+    return 2.0 * (m * (m + 1) / 2.0) * n + 2.0 * m * n * n
+
+
+def oracle_cost(m, n):
+    """Flop model of the oracle (CHOL-EQR): chol(A), C Z, Householder, C^{-1} Y."""
+    return m ** 3 / 3.0 + m * m * n + 2.0 * m * n * n + m * m * n
+
+
+class Clocks:
+    """Samples nvidia-smi clocks during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        try:
+            import torch
+            self.ident = f"GPU-{torch.cuda.get_device_properties(index).uuid}"
+        except Exception:
+            self.ident = str(index)
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.ident}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def ncu_traffic(kernel_tag, source_files):
+    """Per-launch DRAM bytes recorded by the committed ncu summary, if the
+    kernel sources are unchanged since the capture (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"{kernel_tag}.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    h = hashlib.sha256()
+    for f in source_files:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    mh = re.search(r"source_sha256:\s*([0-9a-f]+)", txt)
+    mt = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    if not mh or not mt or mh.group(1) != h.hexdigest()[:16]:
+        return None
+    return float(mt.group(1))
+
+
+def cpu_baseline_sample(n, target_s=12.0):
+    """Times the oracle on a bounded sample: one instance of the same recipe at a
+    smaller m sized for ~target_s seconds; returns (seconds, m_sample, n_sample)."""
+    import numpy as np
+
+    import oracle
+    from paper_1401_5171_gb300 import inputs
+    oracle.build()
+    m0 = 768
+    A, _ = inputs.dense_spd(m0, 1e6, seed=5)
+    Z = inputs.tall_z(m0, min(n, m0), 1e2, seed=6)
+    t = time.perf_counter()
+    oracle.oblique_qr(A.numpy(), Z.numpy())
+    t0 = time.perf_counter() - t
+    ms = m0
+    while ms < 32768 and t0 * oracle_cost(2 * ms, n) / oracle_cost(m0, n) < target_s:
+        ms *= 2
+    ns = min(n, ms)
+    A, _ = inputs.dense_spd(ms, 1e6, seed=5)
+    Z = inputs.tall_z(ms, ns, 1e2, seed=6)
+    A, Z = np.asfortranarray(A.numpy()), np.asfortranarray(Z.numpy())
+    t = time.perf_counter()
+    oracle.oblique_qr(A, Z)
+    return time.perf_counter() - t, ms, ns
+
+
+def run_reference(args, rank, world):
+    """The oracle as it stands, on the host cores, on bounded samples."""
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    from paper_1401_5171_gb300 import inputs
+    oracle.build()
+    # sample size: ~4 s per step so that warmup + steps stays within minutes
+    m0 = 768
+    A, _ = inputs.dense_spd(m0, args.kappa_a, seed=5)
+    Z = inputs.tall_z(m0, min(args.n, m0), args.kappa_z, seed=6)
+    t = time.perf_counter()
+    oracle.oblique_qr(A.numpy(), Z.numpy())
+    t0 = time.perf_counter() - t
+    ms = m0
+    while ms < args.m and t0 * oracle_cost(2 * ms, args.n) / oracle_cost(m0, args.n) < 4.0:
+        ms *= 2
+    ns = min(args.n, ms)
+    A, _ = inputs.dense_spd(ms, args.kappa_a, seed=5)
+    Z = inputs.tall_z(ms, ns, args.kappa_z, seed=6)
+    A, Z = np.asfortranarray(A.numpy()), np.asfortranarray(Z.numpy())
+    for _ in range(args.warmup):
+        oracle.oblique_qr(A, Z)
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        oracle.oblique_qr(A, Z)
+        times.append(time.perf_counter() - t)
+    scale = oracle_cost(args.m, args.n) / oracle_cost(ms, ns)
+    per_full = sum(times) / len(times) * scale
+    value = 1.0 / per_full
+    cores = os.cpu_count()
+    sample = (f"oracle CHOL-EQR on m={ms}, n={ns} (same recipe), {args.steps} runs; QRs/s scaled to "
+              f"m={args.m}, n={args.n} by the oracle's flop model m^3/3 + 2 m^2 n + 2 m n^2")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "QR/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_full * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(args),
+            "cpu_baseline": {"value": value, "unit": "QR/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "QR/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_of(args):
+    return {"workload": f"single dense oblique QR m={args.m} n={args.n} kappa(A)={args.kappa_a:g} "
+                        f"kappa(Z)={args.kappa_z:g}, random U (Sec. 7 case 4 recipe)",
+            "m": args.m, "n": args.n, "kappa_A": args.kappa_a, "kappa_Z": args.kappa_z, "algo": args.algo,
+            "precision": "fp64", "l2": "inputs larger than L2 (A alone is 8.6 GB), no flush"}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import torch
+    import torch.distributed as dist
+
+    from paper_1401_5171_gb300 import build as _build
+    from paper_1401_5171_gb300 import inputs, oqr
+    _build.build()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    m, n = args.m, args.n
+    # inputs resident in HBM before the timed region
+    Af, _ = inputs.dense_spd(m, args.kappa_a, seed=1000 + rank, device=dev)
+    A = oqr.colmajor(Af)
+    del Af
+    Z = oqr.colmajor(inputs.tall_z(m, n, args.kappa_z, seed=2000 + rank, device=dev))
+    Q = oqr.empty_colmajor(m, n, dev)
+    R = oqr.empty_colmajor(n, n, dev)
+    ctx = oqr.Oqr(local)
+    algo = {"cholqr": ("oqr_cholqr", {}, 1), "cholqr2": ("oqr_cholqr2", {}, 2),
+            "scholqr3": ("oqr_cholqr2", {"shifted": 1}, 3), "cgs2": ("oqr_cgs2", {}, 2)}[args.algo]
+    name, kw, passes = algo
+    opts = oqr.make_opts(**kw)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(sync=False):
+        ctx._qr(name, A, Z, Q=Q, R=R, opts=opts, stream=stream, sync=sync)
+
+    # correctness of what is timed: orthogonality measured once, outside the timing
+    Qc, Rc, (st, info) = ctx._qr(name, A, Z, Q=Q, R=R, opts=oqr.make_opts(check=1, **kw), stream=stream)
+    orth = info.orth_err
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = t.item()
+        dist.barrier()
+    ms_per_step = ms / args.steps
+    value = world * args.steps / (ms / 1e3)
+    tflops = world * normalised_flops(m, n, passes) * args.steps / (ms / 1e3) / 1e12
+
+    # dominant kernel: the fused Gram, timed alone on the same stream
+    G = oqr.empty_colmajor(n, n, dev)
+    for _ in range(2):
+        ctx.oqr_gram(A, Z, G=G, stream=stream)
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = max(2, min(args.steps, 5))
+    g0.record(stream)
+    for _ in range(reps):
+        ctx.oqr_gram(A, Z, G=G, stream=stream)
+    g1.record(stream)
+    torch.cuda.synchronize()
+    gram_s = g0.elapsed_time(g1) / reps / 1e3
+    clocks = clk.summary()
+    peak = SMS * FP64_FLOPS_PER_CLK_SM * ((clocks or {}).get("sm_max_mhz") or 2070.0) * 1e6 / 1e12
+    achieved = gram_algorithmic_flops(m, n) / gram_s / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": ncu_traffic("gram_f64_m32768_n256",
+                                       ["paper_1401_5171_gb300/csrc/k_gram_f64.cu"]) if (m, n) == (32768, 256) else None,
+                "kernel": "gram_f64_kernel (fused symmetric Z^T A Z, FP64 DFMA)",
+                "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x max SM clock (DFMA unit count)"}
+
+    # end to end: host buffers in pinned memory, copies inside the timed region
+    e2e = None
+    if args.e2e_steps > 0:
+        Ah = torch.empty((m, m), dtype=torch.float64, pin_memory=True).t()
+        Ah.copy_(A)
+        Zh = torch.empty((n, m), dtype=torch.float64, pin_memory=True).t()
+        Zh.copy_(Z)
+        Qh = torch.empty((n, m), dtype=torch.float64, pin_memory=True).t()
+        Rh = torch.empty((n, n), dtype=torch.float64, pin_memory=True).t()
+        Ad2 = oqr.empty_colmajor(m, m, dev)
+        Zd2 = oqr.empty_colmajor(m, n, dev)
+
+        def e2e_step():
+            Ad2.copy_(Ah, non_blocking=True)
+            Zd2.copy_(Zh, non_blocking=True)
+            ctx._qr(name, Ad2, Zd2, Q=Q, R=R, opts=opts, stream=stream, sync=False)
+            Qh.copy_(Q, non_blocking=True)
+            Rh.copy_(R, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        x0, x1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        x0.record(stream)
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        x1.record(stream)
+        torch.cuda.synchronize()
+        ems = x0.elapsed_time(x1)
+        if world > 1:
+            t = torch.tensor([ems], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = t.item()
+        e2e = {"value": world * args.e2e_steps / (ems / 1e3), "unit": "QR/s",
+               "h2d_bytes_per_step": 8 * (m * m + m * n), "d2h_bytes_per_step": 8 * (m * n + n * n)}
+        del Ah, Ad2
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        secs, msamp, nsamp = cpu_baseline_sample(n)
+        cpu = {"value": 1.0 / (secs * oracle_cost(m, n) / oracle_cost(msamp, nsamp)), "unit": "QR/s",
+               "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"oracle CHOL-EQR once on m={msamp}, n={nsamp} (same recipe, {secs:.1f} s); QRs/s "
+                         f"scaled to m={m}, n={n} by its flop model m^3/3 + 2 m^2 n + 2 m n^2"}
+
+    # per pass: gram, gram-reduce, potrf, trsm; plus one R copy and (passes-1) R products,
+    # plus the two norm/shift kernels of the shifted pass
+    launches = args.steps * (passes * 4 + (passes if passes > 1 else 0) + (2 if args.algo == "scholqr3" else 0))
+    if args.algo == "cgs2":
+        launches = None
+    line = {"metric": METRIC, "value": value, "unit": "QR/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_of(args),
+            "tflops_normalised": tflops, "orth_err": orth, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches, "clocks": clocks}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,180 @@
+/*
+ * liboqr: QR factorization in an oblique inner product on one GB300 GPU.
+ *
+ * Problem (Lowery & Langou, arXiv:1401.5171, Sec. 1): given A (m x m,
+ * symmetric positive definite) and Z (m x n, full rank, m >= n >= 1), find
+ * Q (m x n) with Q^T A Q = I and R (n x n, upper triangular) with Z = Q R.
+ * R has a positive diagonal, which makes (Q, R) unique: R is the Cholesky
+ * factor of the normal-equation matrix Z^T A Z (Sec. 2).
+ *
+ * Conventions for every entry point below:
+ *   - Matrices are FP64, column-major: element (i, j) of X is X[i + j*ldx],
+ *     ldx >= number of rows.  All matrix pointers are DEVICE pointers owned by
+ *     the caller.
+ *   - A is read from its lower triangle only; the strict upper triangle is
+ *     never read and may hold anything.
+ *   - R is written in full: positive diagonal, zeros below it.
+ *   - Q may alias Z exactly (in-place factorization).  Any other overlap of an
+ *     output with an input is not allowed and is not detected.
+ *   - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ *     stream) and runs asynchronously.  If `info` is non-NULL the call
+ *     synchronizes the stream and reports device-side outcomes (Cholesky
+ *     breakdown, timeouts) in the return value and in *info.  If `info` is
+ *     NULL the call returns after enqueueing; device-side outcomes are then
+ *     read with oqr_get_status.
+ *   - The context's device must be the current device of the calling thread.
+ *   - Scratch memory comes from the context's workspace: a buffer that the
+ *     context allocates on first need and keeps (grown when a larger problem
+ *     arrives), or one the caller hands over with oqr_set_workspace.
+ *   - Errors never abort, trap or hang: every device-side wait has a time
+ *     limit (oqr_opts.spin_limit) after which the kernel records
+ *     OQR_ERR_TIMEOUT and returns.
+ */
+#ifndef OQR_H
+#define OQR_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    OQR_OK = 0,
+    OQR_ERR_INVALID_ARG = 1,   /* bad size, leading dimension, pointer or option */
+    OQR_ERR_NOT_SPD = 2,       /* Cholesky breakdown; info = 1-based column */
+    OQR_ERR_CHECK_FAILED = 3,  /* the requested orthogonality check exceeded its tolerance */
+    OQR_ERR_CUDA = 4,          /* a CUDA runtime call failed */
+    OQR_ERR_NO_MEMORY = 5,     /* workspace could not be allocated or is too small */
+    OQR_ERR_TIMEOUT = 6,       /* a device-side wait ran past spin_limit */
+    OQR_ERR_UNSUPPORTED = 7    /* size or option outside what this build supports */
+} oqr_status;
+
+typedef enum {
+    OQR_FP64 = 0,     /* every product in FP64 */
+    OQR_BF16X3 = 1,   /* preconditioning passes: hi/lo BF16 split, 3 products, FP32 accumulation */
+    OQR_FP8 = 2       /* preconditioning passes: E4M3 with power-of-two block scales */
+} oqr_precision;
+
+typedef enum { OQR_ALGO_CHOLQR = 0, OQR_ALGO_CHOLQR2 = 1, OQR_ALGO_SCHOLQR3 = 2, OQR_ALGO_CGS2 = 3 } oqr_algo;
+
+/* Options; a NULL pointer means all defaults (the values in brackets). */
+typedef struct {
+    int passes;       /* oqr_cholqr2: passes of the normal-equation method [2]; 3 when shifted */
+    int shifted;      /* oqr_cholqr2: 1 = shifted A-CholQR3, a shifted first pass then two plain ones [0] */
+    int prec;         /* oqr_precision of the preconditioning passes [OQR_FP64] */
+    double shift_c;   /* constant c of the shift s = c u (m n + n (n+1)) ||A||_F ||Z||_F^2 [11] */
+    int block;        /* oqr_cgs2: column block size b [64] */
+    int check;        /* 1 = measure ||Q^T A Q - I||_2 after the factorization into info->orth_err [0] */
+    long spin_limit;  /* time limit of any device-side wait, in nanoseconds [4e9] */
+} oqr_opts;
+
+/* Optional per-call report (filled only when passed non-NULL). */
+typedef struct {
+    int info;          /* 1-based breakdown column for OQR_ERR_NOT_SPD, else 0 */
+    int passes_run;    /* normal-equation passes (or CGS2 sweeps per block) executed */
+    double orth_err;   /* ||Q^T A Q - I||_2 estimate when opts->check, else -1 */
+    double shift;      /* shift s used by the first pass of shifted A-CholQR3, else 0 */
+} oqr_info;
+
+typedef struct oqr_ctx oqr_ctx;
+
+/* Fills *opts with the defaults. */
+void oqr_default_opts(oqr_opts* opts);
+
+/* Human-readable name of a status code (static string). */
+const char* oqr_status_string(oqr_status s);
+
+/* Creates a context bound to CUDA device `device` (made current by the call).
+ * No workspace is allocated yet. */
+oqr_status oqr_create(oqr_ctx** ctx, int device);
+
+/* Releases the context and the workspace it allocated (not one handed over
+ * with oqr_set_workspace).  NULL is accepted. */
+oqr_status oqr_destroy(oqr_ctx* ctx);
+
+/* Bytes of workspace that `algo` (oqr_algo) needs for an m x n problem. */
+oqr_status oqr_workspace_size(oqr_ctx* ctx, int algo, int m, int n, const oqr_opts* opts, size_t* bytes);
+
+/* Hands the context a caller-owned device buffer of `bytes` bytes (256-byte
+ * aligned) to use as workspace; the context then never allocates.  A call
+ * that needs more returns OQR_ERR_NO_MEMORY.  ptr = NULL returns to
+ * context-owned workspace. */
+oqr_status oqr_set_workspace(oqr_ctx* ctx, void* ptr, size_t bytes);
+
+/* Device-side outcome of the last call on this context: synchronizes
+ * `stream`, returns the status code and writes the breakdown column to
+ * *info (may be NULL). */
+oqr_status oqr_get_status(oqr_ctx* ctx, void* stream, int* info);
+
+/*
+ * A-CholQR: one pass of Algorithm 1 (CHOLQR, Sec. 2):
+ *   B = A Z;  C = Z^T B;  R = chol(C);  Q = Z / R.
+ * B is never stored: C is formed by one fused kernel as P + P^T with
+ * P = Z^T (M Z), M = tril(A, -1) + diag(A)/2, reading A's lower triangle
+ * once.  Q = Z / R is the row-wise triangular solve of Sec. 2.
+ * Accuracy (Thm 2.1): ||Q^T A Q - I|| grows like u kappa(A^{1/2} Z)^2.
+ */
+oqr_status oqr_cholqr(oqr_ctx* ctx, int m, int n, const double* A, long lda, const double* Z, long ldz,
+                      double* Q, long ldq, double* R, long ldr, const oqr_opts* opts, oqr_info* info,
+                      void* stream);
+
+/*
+ * A-CholQR2 (default) and shifted A-CholQR3 (opts->shifted = 1): Algorithm 1
+ * repeated on its own output, Q_1 = Z R_1^{-1}, Q = Q_1 R_2^{-1},
+ * R = R_2 R_1 (the product form of "R = U S", Algorithm 2).  The shifted form
+ * adds s I to the first pass's normal-equation matrix so that its Cholesky
+ * completes for ill-conditioned Z, then runs two plain passes,
+ * R = R_3 R_2 R_1.  Neither repetition is in the paper; they follow the
+ * Euclidean CholeskyQR2 and shifted CholeskyQR3 with Z^T Z replaced by
+ * Z^T A Z.  With opts->prec = OQR_BF16X3 or OQR_FP8 every pass but the last
+ * forms its normal-equation matrix in that precision; the last pass is FP64.
+ */
+oqr_status oqr_cholqr2(oqr_ctx* ctx, int m, int n, const double* A, long lda, const double* Z, long ldz,
+                       double* Q, long ldq, double* R, long ldr, const oqr_opts* opts, oqr_info* info,
+                       void* stream);
+
+/*
+ * A-CGS2: classical Gram-Schmidt with reorthogonalisation in the A inner
+ * product (Sec. 6, Thm 6.4), in block form with column blocks of
+ * opts->block columns.  For each block Z_j: S_j = A Z_j; twice
+ * { r = (A Q)^T Z_j; Z_j -= Q r; S_j -= (A Q) r; R(<j, j) += r };
+ * then A-CholQR2 of the block against S_j; A Q is kept so that each block
+ * costs one product with A.  Needs an extra m x n of workspace for A Q.
+ */
+oqr_status oqr_cgs2(oqr_ctx* ctx, int m, int n, const double* A, long lda, const double* Z, long ldz,
+                    double* Q, long ldq, double* R, long ldr, const oqr_opts* opts, oqr_info* info,
+                    void* stream);
+
+/*
+ * Step kernels of Algorithm 1, exposed for testing and composition.
+ *
+ * oqr_gram: G = Z^T A Z (lines 1-2 of Algorithm 1), n x n, written in full
+ *   and exactly symmetric.  prec selects the arithmetic of the products
+ *   (OQR_FP64 only in this build of the step entry point).
+ * oqr_potrf: R = chol(G + shift I) (line 3), G read from its lower triangle,
+ *   R upper with positive diagonal, zeros below.  Breakdown is reported as
+ *   OQR_ERR_NOT_SPD with the 1-based column (synchronizes the stream when
+ *   info != NULL).
+ * oqr_trsm: Q = Z / R (line 4), row-wise substitution; Q may alias Z.
+ * oqr_rprod: R = U S for upper triangular U, S (R must not alias U or S).
+ * oqr_check: E = Q^T A Q - I (n x n, written in full when E != NULL), and
+ *   the estimate of ||E||_2 (Sec. 7's orthogonality measure) in *orth2 and
+ *   ||E||_F in *orthF (host pointers, may be NULL; non-NULL synchronizes).
+ */
+oqr_status oqr_gram(oqr_ctx* ctx, int m, int n, const double* A, long lda, const double* Z, long ldz,
+                    double* G, long ldg, int prec, void* stream);
+oqr_status oqr_potrf(oqr_ctx* ctx, int n, const double* G, long ldg, double shift, double* R, long ldr,
+                     int* info, void* stream);
+oqr_status oqr_trsm(oqr_ctx* ctx, int m, int n, const double* Z, long ldz, const double* R, long ldr,
+                    double* Q, long ldq, void* stream);
+oqr_status oqr_rprod(oqr_ctx* ctx, int n, const double* U, long ldu, const double* S, long lds, double* R,
+                     long ldr, void* stream);
+oqr_status oqr_check(oqr_ctx* ctx, int m, int n, const double* A, long lda, const double* Q, long ldq,
+                     double* E, long lde, double* orth2, double* orthF, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OQR_H */

@@ -1,0 +1,488 @@
+// Small dense FP64 kernels of the normal-equation path (Algorithm 1, lines
+// 3-4, and the pass composition), the norms behind the shift, the
+// orthogonality check, and the generic FP64 GEMM used by block A-CGS2.
+// FP64 on GB300 issues about 2 FMAs per clock per SM; these kernels are
+// sized so that their cost stays O(m n^2 + n^3) next to the m^2 n Gram.
+#include <math.h>
+
+#include "oqr_internal.cuh"
+
+namespace oqr {
+namespace {
+
+// ------------------------------------------------------------- Cholesky ----
+// R = chol(G + shift I), upper, G read from its lower triangle
+// (Algorithm 1, line 3).  One CTA, right-looking, 32-column panels: the
+// panel's diagonal block is factored by one warp in shared memory, the panel
+// row is solved against it, and the trailing upper triangle is updated by
+// all threads.  A pivot that is not positive (or NaN) stops the
+// factorization and records OQR_ERR_NOT_SPD with the 1-based column.
+constexpr int POTRF_THREADS = 512;
+constexpr int PNB = 32;
+
+__global__ void __launch_bounds__(POTRF_THREADS) potrf_kernel(int n, const double* __restrict__ G, long ldg, double* R,
+                                                              long ldr, const double* shift_ptr, DevStatus* st)
+{
+    __shared__ double D[PNB][PNB + 1];
+    __shared__ int broke;
+    if (*(volatile int*)&st->code != 0) return;
+    const int tid = threadIdx.x;
+    const double shift = shift_ptr ? *shift_ptr : 0.0;
+    for (long e = tid; e < (long)n * n; e += POTRF_THREADS) {
+        const long i = e % n, j = e / n;
+        double v = 0.0;
+        if (i <= j) {
+            v = G[j + i * ldg];
+            if (i == j) v += shift;
+        }
+        R[i + j * ldr] = v;
+    }
+    if (tid == 0) broke = 0;
+    __syncthreads();
+    for (int jb = 0; jb < n; jb += PNB) {
+        const int nb = min(PNB, n - jb);
+        for (int e = tid; e < nb * nb; e += POTRF_THREADS) {
+            const int i = e % nb, j = e / nb;
+            D[i][j] = (i <= j) ? R[(jb + i) + (long)(jb + j) * ldr] : 0.0;
+        }
+        __syncthreads();
+        if (tid < 32) {
+            const int lane = tid;
+            for (int j = 0; j < nb; ++j) {
+                const double piv = D[j][j];
+                if (!(piv > 0.0)) {
+                    if (lane == 0) broke = jb + j + 1;
+                    break;
+                }
+                const double d = sqrt(piv);
+                __syncwarp();
+                if (lane == 0) D[j][j] = d;
+                for (int c = j + 1 + lane; c < nb; c += 32) D[j][c] /= d;
+                __syncwarp();
+                for (int c = j + 1 + lane; c < nb; c += 32) {
+                    const double djc = D[j][c];
+                    for (int r = j + 1; r <= c; ++r) D[r][c] -= D[j][r] * djc;
+                }
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        if (broke) {
+            if (tid == 0) raise_status(st, OQR_ERR_NOT_SPD, broke, TAG_POTRF);
+            return;
+        }
+        for (int e = tid; e < nb * nb; e += POTRF_THREADS) {
+            const int i = e % nb, j = e / nb;
+            if (i <= j) R[(jb + i) + (long)(jb + j) * ldr] = D[i][j];
+        }
+        // panel row: R(jb:jb+nb, c) <- D^{-T} R(jb:jb+nb, c), forward substitution
+        for (int c = jb + nb + tid; c < n; c += POTRF_THREADS) {
+            double x[PNB];
+            for (int i = 0; i < nb; ++i) {
+                double t = R[(jb + i) + (long)c * ldr];
+                for (int k = 0; k < i; ++k) t -= D[k][i] * x[k];
+                x[i] = t / D[i][i];
+                R[(jb + i) + (long)c * ldr] = x[i];
+            }
+        }
+        __syncthreads();
+        // trailing update of the upper triangle: R(r, c) -= sum_k R(jb+k, r) R(jb+k, c)
+        const int t0 = jb + nb, nt = n - t0;
+        for (long e = tid; e < (long)nt * nt; e += POTRF_THREADS) {
+            const int r = t0 + (int)(e % nt), c = t0 + (int)(e / nt);
+            if (r > c) continue;
+            double s = R[r + (long)c * ldr];
+            for (int k = 0; k < nb; ++k) s -= R[(jb + k) + (long)r * ldr] * R[(jb + k) + (long)c * ldr];
+            R[r + (long)c * ldr] = s;
+        }
+        __syncthreads();
+    }
+}
+
+// ----------------------------------------------------------------- TRSM ----
+// Q = Z / R (Algorithm 1, line 4): every row of Q solves q (R) = z.  A CTA
+// holds ROWS rows of Z in shared memory and walks 32-column blocks: a GEMM
+// update from the already solved columns, then substitution within the block
+// against R's diagonal block.  In place when Q aliases Z.
+constexpr int TRSM_THREADS = 256;
+constexpr int TNB = 32;
+
+__global__ void __launch_bounds__(TRSM_THREADS) trsm_kernel(int m, int n, int rows, const double* Z, long ldz,
+                                                            const double* __restrict__ R, long ldr, double* Q,
+                                                            long ldq, const DevStatus* st)
+{
+    extern __shared__ double ts[];
+    if (*(volatile const int*)&st->code != 0) return;
+    const int ldsm = n + 1;                         // padded row stride
+    double* Zs = ts;                                // [rows][n+1]
+    double* Rd = ts + (size_t)rows * ldsm;          // [TNB][TNB+1] diagonal block
+    double* Rt = Rd + TNB * (TNB + 1);              // [TNB][TNB+1] off-diagonal tile
+    const int tid = threadIdx.x;
+    const long row0 = (long)blockIdx.x * rows;
+    for (long e = tid; e < (long)rows * n; e += TRSM_THREADS) {
+        const int r = (int)(e % rows), c = (int)(e / rows);
+        const long gr = row0 + r;
+        Zs[r * ldsm + c] = gr < m ? Z[gr + c * ldz] : 0.0;
+    }
+    const int j = tid & 31, rg = tid >> 5;  // update phase: column j of the block, rows rg + 8 t
+    constexpr int RPT = 8;                  // rows per thread per pass (rows <= 64)
+    for (int jb = 0; jb < n; jb += TNB) {
+        const int nb = min(TNB, n - jb);
+        double acc[RPT];
+#pragma unroll
+        for (int t = 0; t < RPT; ++t) acc[t] = 0.0;
+        for (int k0 = 0; k0 < jb; k0 += TNB) {   // S(:, block) -= Q(:, k0:k0+32) R(k0:k0+32, block)
+            __syncthreads();
+            for (int e = tid; e < TNB * TNB; e += TRSM_THREADS) {
+                const int k = e % TNB, c = e / TNB;
+                Rt[k * (TNB + 1) + c] = (c < nb) ? R[(k0 + k) + (long)(jb + c) * ldr] : 0.0;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int t = 0; t < RPT; ++t) {
+                const int r = rg + 8 * t;
+                if (r < rows) {
+                    double s = 0.0;
+                    const double* zr = Zs + r * ldsm + k0;
+#pragma unroll 8
+                    for (int k = 0; k < TNB; ++k) s = fma(zr[k], Rt[k * (TNB + 1) + j], s);
+                    acc[t] += s;
+                }
+            }
+        }
+        __syncthreads();
+        for (int e = tid; e < TNB * TNB; e += TRSM_THREADS) {
+            const int i = e % TNB, c = e / TNB;
+            Rd[i * (TNB + 1) + c] = (i < nb && c < nb) ? R[(jb + i) + (long)(jb + c) * ldr] : 0.0;
+        }
+        if (j < nb) {
+#pragma unroll
+            for (int t = 0; t < RPT; ++t) {
+                const int r = rg + 8 * t;
+                if (r < rows) Zs[r * ldsm + jb + j] -= acc[t];
+            }
+        }
+        __syncthreads();
+        for (int r = tid; r < rows; r += TRSM_THREADS) {
+            double* zr = Zs + r * ldsm + jb;
+            for (int c = 0; c < nb; ++c) {
+                double t = zr[c];
+                for (int k = 0; k < c; ++k) t -= zr[k] * Rd[k * (TNB + 1) + c];
+                zr[c] = t / Rd[c * (TNB + 1) + c];
+            }
+        }
+    }
+    __syncthreads();
+    for (long e = tid; e < (long)rows * n; e += TRSM_THREADS) {
+        const int r = (int)(e % rows), c = (int)(e / rows);
+        const long gr = row0 + r;
+        if (gr < m) Q[gr + c * ldq] = Zs[r * ldsm + c];
+    }
+}
+
+// ------------------------------------------------------------ R = U S ------
+__global__ void rprod_kernel(int n, const double* __restrict__ U, long ldu, const double* __restrict__ S, long lds,
+                             double* R, long ldr)
+{
+    const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long)n * n) return;
+    const int i = (int)(e % n), j = (int)(e / n);
+    double s = 0.0;
+    if (i <= j)
+        for (int k = i; k <= j; ++k) s += U[i + (long)k * ldu] * S[k + (long)j * lds];
+    R[i + (long)j * ldr] = s;
+}
+
+__global__ void copy_upper_kernel(int n, const double* __restrict__ S, long lds, double* D, long ldd)
+{
+    const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long)n * n) return;
+    const int i = (int)(e % n), j = (int)(e / n);
+    D[i + (long)j * ldd] = i <= j ? S[i + (long)j * lds] : 0.0;
+}
+
+// ------------------------------------------------------- norms and shift ---
+// Partial sums of ||A||_F^2 over the lower triangle (off-diagonal twice) and
+// of ||Z||_F^2; block b handles columns b, b + gridDim.x, ...
+constexpr int NORM_THREADS = 256;
+
+__device__ inline double block_sum(double v, double* red)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+    return s;
+}
+
+__global__ void norms_partial_kernel(int m, int n, const double* __restrict__ A, long lda,
+                                     const double* __restrict__ Z, long ldz, double* scratch)
+{
+    __shared__ double red[32];
+    double sa = 0.0, sz = 0.0;
+    for (long j = blockIdx.x; j < m; j += gridDim.x) {
+        for (long i = j + threadIdx.x; i < m; i += NORM_THREADS) {
+            const double v = A[i + j * lda];
+            sa += (i == j ? 1.0 : 2.0) * v * v;
+        }
+        if (j < n)
+            for (long i = threadIdx.x; i < m; i += NORM_THREADS) {
+                const double v = Z[i + j * ldz];
+                sz += v * v;
+            }
+    }
+    const double ta = block_sum(sa, red);
+    const double tz = block_sum(sz, red);
+    if (threadIdx.x == 0) {
+        scratch[2 * blockIdx.x] = ta;
+        scratch[2 * blockIdx.x + 1] = tz;
+    }
+}
+
+__global__ void shift_finish_kernel(int m, int n, int parts, const double* scratch, double c, double u,
+                                    DevStatus* st)
+{
+    if (threadIdx.x != 0) return;
+    double sa = 0.0, sz = 0.0;
+    for (int p = 0; p < parts; ++p) {
+        sa += scratch[2 * p];
+        sz += scratch[2 * p + 1];
+    }
+    const double nA = sqrt(sa);
+    st->normA_fro = nA;
+    st->normZ_fro2 = sz;
+    st->shift = c * u * ((double)m * n + (double)n * (n + 1)) * nA * sz;
+}
+
+// ------------------------------------------------------ orthogonality ------
+// E = G - I, ||E||_F, and a power-iteration estimate of ||E||_2 (E is
+// symmetric; the estimate max ||E x|| / ||x|| is a lower bound that
+// converges to ||E||_2).
+constexpr int CHECK_THREADS = 512;
+
+__global__ void __launch_bounds__(CHECK_THREADS) check_finish_kernel(int n, const double* __restrict__ G, long ldg,
+                                                                      double* E, long lde, double* work,
+                                                                      DevStatus* st)
+{
+    __shared__ double red[32];
+    __shared__ double bc;
+    double sf = 0.0;
+    for (long e = threadIdx.x; e < (long)n * n; e += CHECK_THREADS) {
+        const long i = e % n, j = e / n;
+        const double v = G[i + j * ldg] - (i == j ? 1.0 : 0.0);
+        if (E) E[i + j * lde] = v;
+        work[e] = v;
+        sf += v * v;
+    }
+    const double tf = block_sum(sf, red);
+    if (threadIdx.x == 0) st->orthF = sqrt(tf);
+    double* x = work + (size_t)n * n;
+    double* y = x + n;
+    for (int i = threadIdx.x; i < n; i += CHECK_THREADS) x[i] = 1.0 + 0.25 * sin(1.0 + i);
+    __syncthreads();
+    double best = 0.0;
+    for (int it = 0; it < 64; ++it) {
+        double sx = 0.0;
+        for (int i = threadIdx.x; i < n; i += CHECK_THREADS) sx += x[i] * x[i];
+        const double nx = block_sum(sx, red);
+        if (threadIdx.x == 0) bc = sqrt(nx);
+        __syncthreads();
+        const double nrm = bc;
+        if (!(nrm > 0.0)) break;
+        for (int i = threadIdx.x; i < n; i += CHECK_THREADS) {
+            double s = 0.0;
+            for (int k = 0; k < n; ++k) s += work[i + (size_t)k * n] * x[k];
+            y[i] = s / nrm;
+        }
+        __syncthreads();
+        double sy = 0.0;
+        for (int i = threadIdx.x; i < n; i += CHECK_THREADS) sy += y[i] * y[i];
+        const double ny = block_sum(sy, red);
+        if (threadIdx.x == 0) bc = sqrt(ny);
+        __syncthreads();
+        best = fmax(best, bc);
+        for (int i = threadIdx.x; i < n; i += CHECK_THREADS) x[i] = y[i];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) st->orth2 = best;
+}
+
+// ---------------------------------------------------------- FP64 GEMM ------
+// C = beta C + alpha op(A) B, 64 x 64 tiles, 16-deep k-steps, 4 x 4 per
+// thread; gridDim.z > 1 splits K and writes partials that a second kernel
+// sums in a fixed order.
+constexpr int GT = 64, GK = 16, GTHREADS = 256;
+
+__device__ inline double opa(GemmOp op, const double* A, long lda, long i, long k)
+{
+    if (op == GEMM_N) return A[i + k * lda];
+    if (op == GEMM_T) return A[k + i * lda];
+    return i >= k ? A[i + k * lda] : A[k + i * lda];
+}
+
+__global__ void __launch_bounds__(GTHREADS) gemm_f64_kernel(GemmOp op, int M, int N, int K, double alpha,
+                                                            const double* __restrict__ A, long lda,
+                                                            const double* __restrict__ B, long ldb, double beta,
+                                                            double* C, long ldc, double* ws)
+{
+    __shared__ double As[GK][GT + 1];
+    __shared__ double Bs[GK][GT + 1];
+    const int tid = threadIdx.x, ty = tid & 15, tx = tid >> 4;
+    const long i0 = (long)blockIdx.x * GT, j0 = (long)blockIdx.y * GT;
+    const int splits = gridDim.z;
+    const long kper = ((K + splits - 1) / splits + GK - 1) / GK * GK;
+    const long k0 = (long)blockIdx.z * kper, k1 = min((long)K, k0 + kper);
+    double acc[4][4] = {};
+    for (long kk = k0; kk < k1; kk += GK) {
+        for (int e = tid; e < GT * GK; e += GTHREADS) {
+            int r, k;
+            if (op == GEMM_T) { k = e % GK; r = e / GK; } else { r = e % GT; k = e / GT; }
+            const long gi = i0 + r, gk = kk + k;
+            As[k][r] = (gi < M && gk < k1) ? opa(op, A, lda, gi, gk) : 0.0;
+        }
+        for (int e = tid; e < GT * GK; e += GTHREADS) {
+            const int k = e % GK, c = e / GK;
+            const long gk = kk + k, gj = j0 + c;
+            Bs[k][c] = (gk < k1 && gj < N) ? B[gk + gj * ldb] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < GK; ++k) {
+            double av[4], bv[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) av[i] = As[k][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) bv[j] = Bs[k][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const long gi = i0 + ty + 16 * i, gj = j0 + tx + 16 * j;
+            if (gi >= M || gj >= N) continue;
+            if (splits == 1) {
+                const double c0 = beta == 0.0 ? 0.0 : beta * C[gi + gj * ldc];
+                C[gi + gj * ldc] = c0 + alpha * acc[i][j];
+            } else {
+                ws[(size_t)blockIdx.z * M * N + gi + gj * (size_t)M] = acc[i][j];
+            }
+        }
+}
+
+__global__ void gemm_splitk_reduce_kernel(int M, int N, int splits, double alpha, const double* ws, double beta,
+                                          double* C, long ldc)
+{
+    const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long)M * N) return;
+    const long i = e % M, j = e / M;
+    double s = 0.0;
+    for (int z = 0; z < splits; ++z) s += ws[(size_t)z * M * N + e];
+    const double c0 = beta == 0.0 ? 0.0 : beta * C[i + j * ldc];
+    C[i + j * ldc] = c0 + alpha * s;
+}
+
+__global__ void axpby_kernel(int M, int N, double alpha, const double* X, long ldx, double beta, double* Y, long ldy)
+{
+    const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long)M * N) return;
+    const long i = e % M, j = e / M;
+    const double y0 = beta == 0.0 ? 0.0 : beta * Y[i + j * ldy];
+    Y[i + j * ldy] = y0 + alpha * X[i + j * ldx];
+}
+
+}  // namespace
+
+cudaError_t launch_axpby(int M, int N, double alpha, const double* X, long ldx, double beta, double* Y, long ldy,
+                         cudaStream_t s)
+{
+    const long total = (long)M * N;
+    if (total <= 0) return cudaSuccess;
+    axpby_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(M, N, alpha, X, ldx, beta, Y, ldy);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_potrf(int n, const double* G, long ldg, double* R, long ldr, const double* shift_ptr,
+                         DevStatus* st, cudaStream_t s)
+{
+    potrf_kernel<<<1, POTRF_THREADS, 0, s>>>(n, G, ldg, R, ldr, shift_ptr, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_trsm(int m, int n, const double* Z, long ldz, const double* R, long ldr, double* Q, long ldq,
+                        DevStatus* st, cudaStream_t s)
+{
+    int rows = 64;
+    while (rows > 8 && (size_t)rows * (n + 1) * sizeof(double) > 160 * 1024) rows /= 2;
+    const size_t smem = ((size_t)rows * (n + 1) + 2 * TNB * (TNB + 1)) * sizeof(double);
+    if (smem > 220 * 1024) return cudaErrorInvalidValue;
+    cudaFuncSetAttribute(trsm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const unsigned blocks = (unsigned)((m + rows - 1) / rows);
+    trsm_kernel<<<blocks, TRSM_THREADS, smem, s>>>(m, n, rows, Z, ldz, R, ldr, Q, ldq, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rprod(int n, const double* U, long ldu, const double* S, long lds, double* R, long ldr,
+                         cudaStream_t s)
+{
+    const long total = (long)n * n;
+    rprod_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(n, U, ldu, S, lds, R, ldr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy_upper(int n, const double* S, long lds, double* D, long ldd, cudaStream_t s)
+{
+    const long total = (long)n * n;
+    copy_upper_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(n, S, lds, D, ldd);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_norms_and_shift(int m, int n, const double* A, long lda, const double* Z, long ldz, double c,
+                                   double u, double* scratch, int scratch_len, DevStatus* st, cudaStream_t s)
+{
+    int parts = scratch_len / 2;
+    if (parts > m) parts = m;
+    if (parts < 1) return cudaErrorInvalidValue;
+    norms_partial_kernel<<<parts, NORM_THREADS, 0, s>>>(m, n, A, lda, Z, ldz, scratch);
+    shift_finish_kernel<<<1, 32, 0, s>>>(m, n, parts, scratch, c, u, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_finish(int n, const double* G, long ldg, double* E, long lde, double* work,
+                                DevStatus* st, cudaStream_t s)
+{
+    check_finish_kernel<<<1, CHECK_THREADS, 0, s>>>(n, G, ldg, E, lde, work, st);
+    return cudaGetLastError();
+}
+
+size_t gemm_splitk_bytes(int M, int N, int splits)
+{
+    return splits > 1 ? (size_t)splits * M * N * sizeof(double) : 0;
+}
+
+cudaError_t launch_gemm_f64(GemmOp op, int M, int N, int K, double alpha, const double* A, long lda,
+                            const double* B, long ldb, double beta, double* C, long ldc, double* splitk_ws,
+                            int splits, cudaStream_t s)
+{
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    if (splits < 1) splits = 1;
+    dim3 grid((M + GT - 1) / GT, (N + GT - 1) / GT, splits);
+    gemm_f64_kernel<<<grid, GTHREADS, 0, s>>>(op, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, splitk_ws);
+    if (splits > 1) {
+        const long total = (long)M * N;
+        gemm_splitk_reduce_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(M, N, splits, alpha, splitk_ws,
+                                                                                 beta, C, ldc);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace oqr

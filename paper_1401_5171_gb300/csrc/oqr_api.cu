@@ -1,0 +1,569 @@
+// C-ABI layer of liboqr: argument checking, workspace, and the composition of
+// the step kernels into A-CholQR, A-CholQR2, shifted A-CholQR3 and A-CGS2.
+// Every arithmetic step runs in this library's CUDA kernels; the host only
+// validates, carves workspace and enqueues.
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+
+#include "oqr_internal.cuh"
+
+using namespace oqr;
+
+struct oqr_ctx {
+    int device = 0;
+    int sm_count = 0;
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    bool ws_owned = true;
+    DevStatus* st = nullptr;  // device status block (owned, allocated at create)
+};
+
+namespace {
+
+constexpr double U64 = 1.1102230246251565e-16;  // 2^-53
+constexpr int SHIFT_PARTS = 1024;
+constexpr int CGS_MAX_SPLITS = 64;
+
+void fill_defaults(oqr_opts* o)
+{
+    o->passes = 2;
+    o->shifted = 0;
+    o->prec = OQR_FP64;
+    o->shift_c = 11.0;
+    o->block = 64;
+    o->check = 0;
+    o->spin_limit = 4000000000L;
+}
+
+oqr_opts resolve(const oqr_opts* o)
+{
+    oqr_opts r;
+    fill_defaults(&r);
+    if (o) r = *o;
+    if (r.passes <= 0) r.passes = 2;
+    if (r.shift_c <= 0) r.shift_c = 11.0;
+    if (r.block <= 0) r.block = 64;
+    if (r.spin_limit <= 0) r.spin_limit = 4000000000L;
+    return r;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+// Bump allocator over the workspace.
+struct Carve {
+    char* base;
+    size_t off = 0;
+    explicit Carve(void* b) : base(static_cast<char*>(b)) {}
+    template <class T>
+    T* take(size_t count)
+    {
+        T* p = reinterpret_cast<T*>(base ? base + off : nullptr);
+        off += align256(count * sizeof(T));
+        return p;
+    }
+};
+
+// Workspace of the normal-equation family: Gram partials, G (+ check work),
+// three n x n triangles, shift scratch.
+template <class C>
+void layout_cholqr(C& c, const GramPlan& p, double** partials, double** G, double** work, double** R1,
+                   double** R2, double** R3, double** scratch)
+{
+    const size_t n = p.n;
+    *partials = c.template take<double>(gram_partials_bytes(p) / sizeof(double));
+    *G = c.template take<double>(n * n);
+    *work = c.template take<double>(n * n + 2 * n);
+    *R1 = c.template take<double>(n * n);
+    *R2 = c.template take<double>(n * n);
+    *R3 = c.template take<double>(n * n);
+    *scratch = c.template take<double>(2 * SHIFT_PARTS);
+}
+
+struct CgsLayout {
+    GramPlan gp;
+    int b, splits;
+    double *AQ, *S, *r, *sk, *Gb, *R1, *R2, *Rt, *work, *Rj;
+};
+
+template <class C>
+void layout_cgs2(C& c, CgsLayout& L, int m, int n)
+{
+    const int b = L.b;
+    L.AQ = c.template take<double>((size_t)m * n);
+    L.S = c.template take<double>((size_t)m * b);
+    L.r = c.template take<double>((size_t)n * b);
+    L.sk = c.template take<double>((size_t)L.splits * std::max(n, b) * b);
+    L.Gb = c.template take<double>((size_t)b * b);
+    L.R1 = c.template take<double>((size_t)b * b);
+    L.R2 = c.template take<double>((size_t)b * b);
+    L.Rt = c.template take<double>((size_t)b * b);
+    L.Rj = c.template take<double>((size_t)b * b);
+    L.work = c.template take<double>((size_t)b * b + 2 * b);
+}
+
+oqr_status cuda_status(cudaError_t e) { return e == cudaSuccess ? OQR_OK : OQR_ERR_CUDA; }
+
+oqr_status ensure_ws(oqr_ctx* ctx, size_t need)
+{
+    if (need <= ctx->ws_bytes) return OQR_OK;
+    if (!ctx->ws_owned) return OQR_ERR_NO_MEMORY;
+    if (ctx->ws) {
+        cudaDeviceSynchronize();
+        cudaFree(ctx->ws);
+        ctx->ws = nullptr;
+        ctx->ws_bytes = 0;
+    }
+    size_t want = need + need / 8;
+    if (cudaMalloc(&ctx->ws, want) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->ws = nullptr;
+        return OQR_ERR_NO_MEMORY;
+    }
+    ctx->ws_bytes = want;
+    return OQR_OK;
+}
+
+bool bad_matrix(const void* p, long ld, long rows, long cols)
+{
+    if (rows > 0 && cols > 0 && p == nullptr) return true;
+    return ld < std::max(1L, rows);
+}
+
+oqr_status check_common(oqr_ctx* ctx, int m, int n, const double* A, long lda, const double* Z, long ldz,
+                        const double* Q, long ldq, const double* R, long ldr)
+{
+    if (!ctx) return OQR_ERR_INVALID_ARG;
+    if (m < 1 || n < 1 || n > m) return OQR_ERR_INVALID_ARG;
+    if (bad_matrix(A, lda, m, m) || bad_matrix(Z, ldz, m, n) || bad_matrix(Q, ldq, m, n) ||
+        bad_matrix(R, ldr, n, n))
+        return OQR_ERR_INVALID_ARG;
+    if (n > 1024) return OQR_ERR_UNSUPPORTED;
+    // Q may alias Z exactly; any other overlap between Q and Z is refused.
+    if (Q != Z) {
+        const char* q0 = reinterpret_cast<const char*>(Q);
+        const char* q1 = reinterpret_cast<const char*>(Q + (size_t)ldq * (n - 1) + m);
+        const char* z0 = reinterpret_cast<const char*>(Z);
+        const char* z1 = reinterpret_cast<const char*>(Z + (size_t)ldz * (n - 1) + m);
+        if (q0 < z1 && z0 < q1) return OQR_ERR_INVALID_ARG;
+    }
+    return OQR_OK;
+}
+
+// Reads the device status block after the stream has drained.
+oqr_status finish(oqr_ctx* ctx, cudaStream_t s, oqr_info* info, int passes_run, bool checked)
+{
+    if (!info) return cuda_status(cudaGetLastError());
+    if (cudaStreamSynchronize(s) != cudaSuccess) return OQR_ERR_CUDA;
+    DevStatus h;
+    if (cudaMemcpy(&h, ctx->st, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return OQR_ERR_CUDA;
+    info->info = h.code == OQR_ERR_NOT_SPD ? h.info : 0;
+    info->passes_run = passes_run;
+    info->orth_err = checked ? h.orth2 : -1.0;
+    info->shift = h.shift;
+    return static_cast<oqr_status>(h.code);
+}
+
+#define OQR_TRY(x)                                  \
+    do {                                            \
+        cudaError_t e_ = (x);                       \
+        if (e_ != cudaSuccess) return OQR_ERR_CUDA; \
+    } while (0)
+
+oqr_status reset_status(oqr_ctx* ctx, cudaStream_t s)
+{
+    return cuda_status(cudaMemsetAsync(ctx->st, 0, sizeof(DevStatus), s));
+}
+
+// One normal-equation pass: G = X^T A X (+ shift), Rp = chol(G), Q = X / Rp.
+cudaError_t run_pass(oqr_ctx* ctx, const GramPlan& gp, const double* A, long lda, const double* X, long ldx,
+                     double* Q, long ldq, double* Rp, long ldrp, double* partials, double* G,
+                     const double* shift_ptr, uint64_t limit, cudaStream_t s)
+{
+    cudaError_t e = launch_gram_f64(gp, A, lda, X, ldx, partials, ctx->st, limit, s);
+    if (e != cudaSuccess) return e;
+    e = launch_gram_reduce(gp, partials, G, gp.n, shift_ptr, ctx->st, s);
+    if (e != cudaSuccess) return e;
+    e = launch_potrf(gp.n, G, gp.n, Rp, ldrp, nullptr, ctx->st, s);
+    if (e != cudaSuccess) return e;
+    return launch_trsm(gp.m, gp.n, X, ldx, Rp, ldrp, Q, ldq, ctx->st, s);
+}
+
+oqr_status run_check(oqr_ctx* ctx, const GramPlan& gp, const double* A, long lda, const double* Q, long ldq,
+                     double* partials, double* G, double* work, double* E, long lde, uint64_t limit, cudaStream_t s)
+{
+    OQR_TRY(launch_gram_f64(gp, A, lda, Q, ldq, partials, ctx->st, limit, s));
+    OQR_TRY(launch_gram_reduce(gp, partials, G, gp.n, nullptr, ctx->st, s));
+    OQR_TRY(launch_check_finish(gp.n, G, gp.n, E, lde, work, ctx->st, s));
+    return OQR_OK;
+}
+
+oqr_status normal_equation(oqr_ctx* ctx, int m, int n, const double* A, long lda, const double* Z, long ldz,
+                           double* Q, long ldq, double* R, long ldr, const oqr_opts* opts_in, oqr_info* info,
+                           void* stream, int forced_passes)
+{
+    oqr_status v = check_common(ctx, m, n, A, lda, Z, ldz, Q, ldq, R, ldr);
+    if (v != OQR_OK) return v;
+    const oqr_opts o = resolve(opts_in);
+    if (o.prec != OQR_FP64) return OQR_ERR_UNSUPPORTED;
+    int passes = forced_passes > 0 ? forced_passes : (o.shifted ? 3 : o.passes);
+    if (passes > 8) return OQR_ERR_INVALID_ARG;
+    const bool shifted = forced_passes == 0 && o.shifted;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const uint64_t limit = (uint64_t)o.spin_limit;
+    const GramPlan gp = gram_plan(m, n, ctx->sm_count);
+    Carve probe(nullptr);
+    double *partials, *G, *work, *R1, *R2, *R3, *scratch;
+    layout_cholqr(probe, gp, &partials, &G, &work, &R1, &R2, &R3, &scratch);
+    if ((v = ensure_ws(ctx, probe.off)) != OQR_OK) return v;
+    Carve c(ctx->ws);
+    layout_cholqr(c, gp, &partials, &G, &work, &R1, &R2, &R3, &scratch);
+    if ((v = reset_status(ctx, s)) != OQR_OK) return v;
+
+    const double* shift_ptr = nullptr;
+    if (shifted) {
+        OQR_TRY(launch_norms_and_shift(m, n, A, lda, Z, ldz, o.shift_c, U64, scratch, 2 * SHIFT_PARTS, ctx->st, s));
+        shift_ptr = &ctx->st->shift;
+    }
+    // R accumulates as R_p ... R_1; Racc alternates between R2 and R3.
+    const double* X = Z;
+    long ldx = ldz;
+    double* Racc = nullptr;
+    for (int p = 0; p < passes; ++p) {
+        double* Rp = (passes == 1) ? R : R1;
+        const long ldrp = (passes == 1) ? ldr : n;
+        OQR_TRY(run_pass(ctx, gp, A, lda, X, ldx, Q, ldq, Rp, ldrp, partials, G, p == 0 ? shift_ptr : nullptr,
+                         limit, s));
+        if (passes > 1) {
+            if (p == 0) {
+                OQR_TRY(launch_copy_upper(n, R1, n, R2, n, s));
+                Racc = R2;
+            } else if (p == passes - 1) {
+                OQR_TRY(launch_rprod(n, R1, n, Racc, n, R, ldr, s));
+            } else {
+                double* Rn = (Racc == R2) ? R3 : R2;
+                OQR_TRY(launch_rprod(n, R1, n, Racc, n, Rn, n, s));
+                Racc = Rn;
+            }
+        }
+        X = Q;
+        ldx = ldq;
+    }
+    if (o.check) {
+        if ((v = run_check(ctx, gp, A, lda, Q, ldq, partials, G, work, nullptr, 0, limit, s)) != OQR_OK) return v;
+    }
+    return finish(ctx, s, info, passes, o.check != 0);
+}
+
+oqr_status cgs2_impl(oqr_ctx* ctx, int m, int n, const double* A, long lda, const double* Z, long ldz, double* Q,
+                     long ldq, double* R, long ldr, const oqr_opts* opts_in, oqr_info* info, void* stream)
+{
+    oqr_status v = check_common(ctx, m, n, A, lda, Z, ldz, Q, ldq, R, ldr);
+    if (v != OQR_OK) return v;
+    const oqr_opts o = resolve(opts_in);
+    if (o.prec != OQR_FP64) return OQR_ERR_UNSUPPORTED;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const uint64_t limit = (uint64_t)o.spin_limit;
+    const GramPlan gp = gram_plan(m, n, ctx->sm_count);
+    CgsLayout L;
+    L.b = std::min(o.block, n);
+    L.gp = gram_plan(m, L.b, ctx->sm_count);
+    L.splits = CGS_MAX_SPLITS;
+    double *partials, *G, *work, *R1, *R2, *R3, *scratch;
+    Carve probe(nullptr);
+    layout_cholqr(probe, gp, &partials, &G, &work, &R1, &R2, &R3, &scratch);
+    layout_cgs2(probe, L, m, n);
+    if ((v = ensure_ws(ctx, probe.off)) != OQR_OK) return v;
+    Carve c(ctx->ws);
+    layout_cholqr(c, gp, &partials, &G, &work, &R1, &R2, &R3, &scratch);
+    layout_cgs2(c, L, m, n);
+    if ((v = reset_status(ctx, s)) != OQR_OK) return v;
+    OQR_TRY(cudaMemset2DAsync(R, ldr * sizeof(double), 0, n * sizeof(double), n, s));
+    if (Q != Z)
+        OQR_TRY(cudaMemcpy2DAsync(Q, ldq * sizeof(double), Z, ldz * sizeof(double), m * sizeof(double), n,
+                                  cudaMemcpyDeviceToDevice, s));
+    const int b = L.b;
+    auto splits_for = [&](int M, int N) {
+        const int tiles = ((M + 63) / 64) * ((N + 63) / 64);
+        return std::max(1, std::min(CGS_MAX_SPLITS, 2 * ctx->sm_count / tiles));
+    };
+    for (int j0 = 0; j0 < n; j0 += b) {
+        const int bj = std::min(b, n - j0);
+        double* Zj = Q + (size_t)j0 * ldq;
+        // S = A Z_j (symmetric A from its lower triangle)
+        OQR_TRY(launch_gemm_f64(GEMM_SYML, m, bj, m, 1.0, A, lda, Zj, ldq, 0.0, L.S, m, nullptr, 1, s));
+        for (int sweep = 0; sweep < 2 && j0 > 0; ++sweep) {
+            const int sp = splits_for(j0, bj);
+            // r = (A Q)^T Z_j ; Z_j -= Q r ; S -= (A Q) r ; R(:j0, block) += r
+            OQR_TRY(launch_gemm_f64(GEMM_T, j0, bj, m, 1.0, L.AQ, m, Zj, ldq, 0.0, L.r, n, L.sk, sp, s));
+            OQR_TRY(launch_gemm_f64(GEMM_N, m, bj, j0, -1.0, Q, ldq, L.r, n, 1.0, Zj, ldq, nullptr, 1, s));
+            OQR_TRY(launch_gemm_f64(GEMM_N, m, bj, j0, -1.0, L.AQ, m, L.r, n, 1.0, L.S, m, nullptr, 1, s));
+            OQR_TRY(launch_axpby(j0, bj, 1.0, L.r, n, 1.0, R + (size_t)j0 * ldr, ldr, s));
+        }
+        // A-CholQR2 of the block against S = A Z_j
+        const int sp = splits_for(bj, bj);
+        for (int pass = 0; pass < 2; ++pass) {
+            double* Rp = pass == 0 ? L.R1 : L.R2;
+            OQR_TRY(launch_gemm_f64(GEMM_T, bj, bj, m, 1.0, Zj, ldq, L.S, m, 0.0, L.Gb, b, L.sk, sp, s));
+            OQR_TRY(launch_potrf(bj, L.Gb, b, Rp, b, nullptr, ctx->st, s));
+            OQR_TRY(launch_trsm(m, bj, Zj, ldq, Rp, b, Zj, ldq, ctx->st, s));
+            OQR_TRY(launch_trsm(m, bj, L.S, m, Rp, b, L.S, m, ctx->st, s));
+        }
+        OQR_TRY(launch_rprod(bj, L.R2, b, L.R1, b, R + (size_t)j0 + (size_t)j0 * ldr, ldr, s));
+        OQR_TRY(cudaMemcpy2DAsync(L.AQ + (size_t)j0 * m, m * sizeof(double), L.S, m * sizeof(double),
+                                  m * sizeof(double), bj, cudaMemcpyDeviceToDevice, s));
+    }
+    if (o.check) {
+        if ((v = run_check(ctx, gp, A, lda, Q, ldq, partials, G, work, nullptr, 0, limit, s)) != OQR_OK) return v;
+    }
+    return finish(ctx, s, info, 2, o.check != 0);
+}
+
+}  // namespace
+
+extern "C" {
+
+void oqr_default_opts(oqr_opts* opts)
+{
+    if (opts) fill_defaults(opts);
+}
+
+const char* oqr_status_string(oqr_status s)
+{
+    switch (s) {
+        case OQR_OK: return "OQR_OK";
+        case OQR_ERR_INVALID_ARG: return "OQR_ERR_INVALID_ARG: invalid argument";
+        case OQR_ERR_NOT_SPD: return "OQR_ERR_NOT_SPD: Cholesky breakdown (matrix not numerically SPD)";
+        case OQR_ERR_CHECK_FAILED: return "OQR_ERR_CHECK_FAILED: orthogonality check failed";
+        case OQR_ERR_CUDA: return "OQR_ERR_CUDA: CUDA runtime error";
+        case OQR_ERR_NO_MEMORY: return "OQR_ERR_NO_MEMORY: workspace unavailable";
+        case OQR_ERR_TIMEOUT: return "OQR_ERR_TIMEOUT: device-side wait timed out";
+        case OQR_ERR_UNSUPPORTED: return "OQR_ERR_UNSUPPORTED: not supported by this build";
+    }
+    return "unknown oqr_status";
+}
+
+oqr_status oqr_create(oqr_ctx** out, int device)
+{
+    if (!out) return OQR_ERR_INVALID_ARG;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+        cudaGetLastError();
+        return OQR_ERR_INVALID_ARG;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) return OQR_ERR_CUDA;
+    oqr_ctx* ctx = new (std::nothrow) oqr_ctx;
+    if (!ctx) return OQR_ERR_NO_MEMORY;
+    ctx->device = device;
+    cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (cudaMalloc(&ctx->st, sizeof(DevStatus)) != cudaSuccess) {
+        delete ctx;
+        return OQR_ERR_NO_MEMORY;
+    }
+    cudaMemset(ctx->st, 0, sizeof(DevStatus));
+    *out = ctx;
+    return OQR_OK;
+}
+
+oqr_status oqr_destroy(oqr_ctx* ctx)
+{
+    if (!ctx) return OQR_OK;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    if (ctx->ws && ctx->ws_owned) cudaFree(ctx->ws);
+    if (ctx->st) cudaFree(ctx->st);
+    delete ctx;
+    return OQR_OK;
+}
+
+oqr_status oqr_workspace_size(oqr_ctx* ctx, int algo, int m, int n, const oqr_opts* opts, size_t* bytes)
+{
+    if (!ctx || !bytes || m < 1 || n < 1 || n > m) return OQR_ERR_INVALID_ARG;
+    const oqr_opts o = resolve(opts);
+    const GramPlan gp = gram_plan(m, n, ctx->sm_count);
+    Carve c(nullptr);
+    double *partials, *G, *work, *R1, *R2, *R3, *scratch;
+    layout_cholqr(c, gp, &partials, &G, &work, &R1, &R2, &R3, &scratch);
+    if (algo == OQR_ALGO_CGS2) {
+        CgsLayout L;
+        L.b = std::min(o.block, n);
+        L.gp = gram_plan(m, L.b, ctx->sm_count);
+        L.splits = CGS_MAX_SPLITS;
+        layout_cgs2(c, L, m, n);
+    } else if (algo < 0 || algo > OQR_ALGO_CGS2) {
+        return OQR_ERR_INVALID_ARG;
+    }
+    *bytes = c.off;
+    return OQR_OK;
+}
+
+oqr_status oqr_set_workspace(oqr_ctx* ctx, void* ptr, size_t bytes)
+{
+    if (!ctx) return OQR_ERR_INVALID_ARG;
+    if (ptr && (reinterpret_cast<uintptr_t>(ptr) % 256 != 0)) return OQR_ERR_INVALID_ARG;
+    if (ctx->ws && ctx->ws_owned) {
+        cudaDeviceSynchronize();
+        cudaFree(ctx->ws);
+    }
+    ctx->ws = ptr;
+    ctx->ws_bytes = ptr ? bytes : 0;
+    ctx->ws_owned = ptr == nullptr;
+    return OQR_OK;
+}
+
+oqr_status oqr_get_status(oqr_ctx* ctx, void* stream, int* info)
+{
+    if (!ctx) return OQR_ERR_INVALID_ARG;
+    if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return OQR_ERR_CUDA;
+    DevStatus h;
+    if (cudaMemcpy(&h, ctx->st, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return OQR_ERR_CUDA;
+    if (info) *info = h.info;
+    return static_cast<oqr_status>(h.code);
+}
+
+oqr_status oqr_cholqr(oqr_ctx* ctx, int m, int n, const double* A, long lda, const double* Z, long ldz, double* Q,
+                      long ldq, double* R, long ldr, const oqr_opts* opts, oqr_info* info, void* stream)
+{
+    return normal_equation(ctx, m, n, A, lda, Z, ldz, Q, ldq, R, ldr, opts, info, stream, 1);
+}
+
+oqr_status oqr_cholqr2(oqr_ctx* ctx, int m, int n, const double* A, long lda, const double* Z, long ldz,
+                       double* Q, long ldq, double* R, long ldr, const oqr_opts* opts, oqr_info* info, void* stream)
+{
+    return normal_equation(ctx, m, n, A, lda, Z, ldz, Q, ldq, R, ldr, opts, info, stream, 0);
+}
+
+oqr_status oqr_cgs2(oqr_ctx* ctx, int m, int n, const double* A, long lda, const double* Z, long ldz, double* Q,
+                    long ldq, double* R, long ldr, const oqr_opts* opts, oqr_info* info, void* stream)
+{
+    return cgs2_impl(ctx, m, n, A, lda, Z, ldz, Q, ldq, R, ldr, opts, info, stream);
+}
+
+oqr_status oqr_gram(oqr_ctx* ctx, int m, int n, const double* A, long lda, const double* Z, long ldz, double* G,
+                    long ldg, int prec, void* stream)
+{
+    if (!ctx || m < 1 || n < 1 || n > m || bad_matrix(A, lda, m, m) || bad_matrix(Z, ldz, m, n) ||
+        bad_matrix(G, ldg, n, n))
+        return OQR_ERR_INVALID_ARG;
+    if (prec != OQR_FP64) return OQR_ERR_UNSUPPORTED;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const GramPlan gp = gram_plan(m, n, ctx->sm_count);
+    oqr_status v = ensure_ws(ctx, align256(gram_partials_bytes(gp)));
+    if (v != OQR_OK) return v;
+    if ((v = reset_status(ctx, s)) != OQR_OK) return v;
+    OQR_TRY(launch_gram_f64(gp, A, lda, Z, ldz, static_cast<double*>(ctx->ws), ctx->st, 4000000000ull, s));
+    OQR_TRY(launch_gram_reduce(gp, static_cast<double*>(ctx->ws), G, ldg, nullptr, ctx->st, s));
+    return OQR_OK;
+}
+
+oqr_status oqr_potrf(oqr_ctx* ctx, int n, const double* G, long ldg, double shift, double* R, long ldr, int* info,
+                     void* stream)
+{
+    if (!ctx || n < 1 || bad_matrix(G, ldg, n, n) || bad_matrix(R, ldr, n, n) || G == R) return OQR_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    oqr_status v = reset_status(ctx, s);
+    if (v != OQR_OK) return v;
+    OQR_TRY(cudaMemcpyAsync(&ctx->st->shift, &shift, sizeof(double), cudaMemcpyHostToDevice, s));
+    OQR_TRY(launch_potrf(n, G, ldg, R, ldr, &ctx->st->shift, ctx->st, s));
+    if (!info) return OQR_OK;
+    int col = 0;
+    v = oqr_get_status(ctx, stream, &col);
+    *info = v == OQR_ERR_NOT_SPD ? col : 0;
+    return v;
+}
+
+oqr_status oqr_trsm(oqr_ctx* ctx, int m, int n, const double* Z, long ldz, const double* R, long ldr, double* Q,
+                    long ldq, void* stream)
+{
+    if (!ctx || m < 1 || n < 1 || bad_matrix(Z, ldz, m, n) || bad_matrix(R, ldr, n, n) || bad_matrix(Q, ldq, m, n))
+        return OQR_ERR_INVALID_ARG;
+    if (n > 1024) return OQR_ERR_UNSUPPORTED;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    oqr_status v = reset_status(ctx, s);
+    if (v != OQR_OK) return v;
+    OQR_TRY(launch_trsm(m, n, Z, ldz, R, ldr, Q, ldq, ctx->st, s));
+    return OQR_OK;
+}
+
+oqr_status oqr_rprod(oqr_ctx* ctx, int n, const double* U, long ldu, const double* S, long lds, double* R, long ldr,
+                     void* stream)
+{
+    if (!ctx || n < 1 || bad_matrix(U, ldu, n, n) || bad_matrix(S, lds, n, n) || bad_matrix(R, ldr, n, n) ||
+        R == U || R == S)
+        return OQR_ERR_INVALID_ARG;
+    OQR_TRY(launch_rprod(n, U, ldu, S, lds, R, ldr, static_cast<cudaStream_t>(stream)));
+    return OQR_OK;
+}
+
+oqr_status oqr_check(oqr_ctx* ctx, int m, int n, const double* A, long lda, const double* Q, long ldq, double* E,
+                     long lde, double* orth2, double* orthF, void* stream)
+{
+    if (!ctx || m < 1 || n < 1 || n > m || bad_matrix(A, lda, m, m) || bad_matrix(Q, ldq, m, n) ||
+        (E && lde < n))
+        return OQR_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const GramPlan gp = gram_plan(m, n, ctx->sm_count);
+    Carve probe(nullptr);
+    double *partials, *G, *work, *R1, *R2, *R3, *scratch;
+    layout_cholqr(probe, gp, &partials, &G, &work, &R1, &R2, &R3, &scratch);
+    oqr_status v = ensure_ws(ctx, probe.off);
+    if (v != OQR_OK) return v;
+    Carve c(ctx->ws);
+    layout_cholqr(c, gp, &partials, &G, &work, &R1, &R2, &R3, &scratch);
+    if ((v = reset_status(ctx, s)) != OQR_OK) return v;
+    if ((v = run_check(ctx, gp, A, lda, Q, ldq, partials, G, work, E, lde, 4000000000ull, s)) != OQR_OK) return v;
+    if (orth2 || orthF) {
+        if (cudaStreamSynchronize(s) != cudaSuccess) return OQR_ERR_CUDA;
+        DevStatus h;
+        if (cudaMemcpy(&h, ctx->st, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return OQR_ERR_CUDA;
+        if (orth2) *orth2 = h.orth2;
+        if (orthF) *orthF = h.orthF;
+        return static_cast<oqr_status>(h.code);
+    }
+    return OQR_OK;
+}
+
+}  // extern "C"
+
+// --------------------------------------------------------- tensor maps ------
+namespace oqr {
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+        cudaGetLastError();
+    }
+    return fn;
+}
+
+bool make_tensor_map_2d(CUtensorMap* map, CUtensorMapDataType dtype, int elem_bytes, const void* base, long rows,
+                        long cols, long ld, int box_rows, int box_cols)
+{
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)rows, (cuuint64_t)cols};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * (cuuint64_t)elem_bytes};
+    cuuint32_t box[2] = {(cuuint32_t)box_rows, (cuuint32_t)box_cols};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(map, dtype, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+}  // namespace oqr

@@ -1,0 +1,182 @@
+// Internal declarations of the oblique-QR CUDA library (sm_103a).
+// Shared by the kernel translation units and the C-ABI layer; never exported.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/oqr.h"
+
+namespace oqr {
+
+// ------------------------------------------------------------------ status --
+// Device status block, one per context (in its workspace):
+//   code  : first error raised by a kernel (oqr_status), 0 = none
+//   info  : 1-based Cholesky breakdown column, or a kernel-specific detail
+//   where : which kernel timed out or broke down (small integer tag)
+struct DevStatus {
+    int code;
+    int info;
+    int where;
+    int pad;
+    double shift;       // shift applied by the last shifted pass
+    double normA_fro;   // ||A||_F of the last shifted pass
+    double normZ_fro2;  // ||Z||_F^2 of the last shifted pass
+    double orth2;       // ||Q^T A Q - I||_2 estimate from the last check
+    double orthF;       // ||Q^T A Q - I||_F from the last check
+    double pad2[5];
+};
+static_assert(sizeof(DevStatus) == 96, "status layout");
+
+enum KernelTag { TAG_GRAM = 1, TAG_POTRF = 2, TAG_TRSM = 3, TAG_GEMM = 4, TAG_CHECK = 5, TAG_MIXED = 6,
+                 TAG_BATCH = 7 };
+
+__device__ inline void raise_status(DevStatus* st, int code, int info, int where)
+{
+    if (atomicCAS(&st->code, 0, code) == 0) {
+        st->info = info;
+        st->where = where;
+    }
+}
+
+__device__ inline uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ inline uint32_t smem_u32(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// ---------------------------------------------------------------- mbarrier --
+__device__ inline void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ inline void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ inline void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ inline bool mbar_test(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Waits for the phase with the given parity to complete, for at most
+// limit_ns nanoseconds of wall time.  Returns false on timeout.
+__device__ inline bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns)
+{
+    if (mbar_test(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (!mbar_test(bar, parity)) {
+        if (global_ns() - t0 > limit_ns) return false;
+    }
+    return true;
+}
+
+__device__ inline void fence_barrier_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ inline void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// -------------------------------------------------------------------- TMA --
+// 2-D tiled bulk tensor load into shared memory, completion signalled on bar.
+__device__ inline void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cta.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ inline void tma_prefetch_desc(const CUtensorMap* map)
+{
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
+// ---------------------------------------------------------- host helpers --
+// Builds a 2-D tensor map over a column-major matrix (rows contiguous).
+// Returns false when the driver refuses it (alignment, stride) or is absent.
+bool make_tensor_map_2d(CUtensorMap* map, CUtensorMapDataType dtype, int elem_bytes, const void* base,
+                        long rows, long cols, long ld, int box_rows, int box_cols);
+
+// True when a column-major matrix can be read by TMA: 16-byte aligned base and
+// a leading dimension whose byte stride is a multiple of 16.
+inline bool tma_ok(const void* p, long ld, int elem_bytes)
+{
+    return (reinterpret_cast<uintptr_t>(p) % 16 == 0) && ((ld * elem_bytes) % 16 == 0);
+}
+
+// ---------------------------------------------------- kernel entry points --
+// Fused symmetric Gram, FP64: P_s = Z^T (M Z) restricted to split s, with
+// M = tril(A,-1) + diag(A)/2; see k_gram_f64.cu.
+struct GramPlan {
+    int m, n;
+    int bn;        // column chunk width
+    int chunks;    // ceil(n / bn)
+    int splits;    // work splits of the lower triangle
+    long steps;    // total k-steps over the lower triangle (per chunk)
+};
+GramPlan gram_plan(int m, int n, int sm_count);
+size_t gram_partials_bytes(const GramPlan& p);
+cudaError_t launch_gram_f64(const GramPlan& p, const double* A, long lda, const double* Z, long ldz,
+                            double* partials, DevStatus* st, uint64_t limit_ns, cudaStream_t s);
+// G = sum_s (P_s + P_s^T) (+ shift*I if shift_ptr), G dense n x n with ldg.
+cudaError_t launch_gram_reduce(const GramPlan& p, const double* partials, double* G, long ldg,
+                               const double* shift_ptr, DevStatus* st, cudaStream_t s);
+
+// Dense small kernels (k_dense.cu).
+cudaError_t launch_potrf(int n, const double* G, long ldg, double* R, long ldr, const double* shift_ptr,
+                         DevStatus* st, cudaStream_t s);
+cudaError_t launch_trsm(int m, int n, const double* Z, long ldz, const double* R, long ldr, double* Q, long ldq,
+                        DevStatus* st, cudaStream_t s);
+cudaError_t launch_rprod(int n, const double* U, long ldu, const double* S, long lds, double* R, long ldr,
+                         cudaStream_t s);
+cudaError_t launch_copy_upper(int n, const double* S, long lds, double* D, long ldd, cudaStream_t s);
+// Shift for the shifted pass: s = c * u * (m n + n (n+1)) * ||A||_F * ||Z||_F^2.
+cudaError_t launch_norms_and_shift(int m, int n, const double* A, long lda, const double* Z, long ldz,
+                                   double c, double u, double* scratch, int scratch_len, DevStatus* st,
+                                   cudaStream_t s);
+// Orthogonality check: E = G - I given G (n x n); writes E (if non-NULL),
+// orth2 (power-iteration estimate of ||E||_2) and orthF into st.  work holds
+// n*n + 2n doubles.
+cudaError_t launch_check_finish(int n, const double* G, long ldg, double* E, long lde, double* work,
+                                DevStatus* st, cudaStream_t s);
+
+// Generic FP64 GEMM used by CGS2: C = beta*C + alpha * op(A) * B with
+// op(A) = A (m x k), A^T (A stored k x m), or the symmetric matrix stored in
+// the lower triangle of A (m x m).
+enum GemmOp { GEMM_N = 0, GEMM_T = 1, GEMM_SYML = 2 };
+size_t gemm_splitk_bytes(int M, int N, int splits);
+cudaError_t launch_gemm_f64(GemmOp op, int M, int N, int K, double alpha, const double* A, long lda,
+                            const double* B, long ldb, double beta, double* C, long ldc, double* splitk_ws,
+                            int splits, cudaStream_t s);
+
+// Y = alpha X + beta Y (M x N, column-major).
+cudaError_t launch_axpby(int M, int N, double alpha, const double* X, long ldx, double beta, double* Y, long ldy,
+                         cudaStream_t s);
+
+}  // namespace oqr

@@ -1,0 +1,255 @@
+"""Python binding of liboqr (include/oqr.h): argument marshalling only.
+
+The C entry points are exposed under their own names (``oqr_cholqr``,
+``oqr_cholqr2``, ``oqr_cgs2``, ...) and take raw device pointers and leading
+dimensions, exactly as declared in the header.  ``Oqr`` wraps a context and
+accepts torch tensors: a matrix argument is a 2-D float64 CUDA tensor stored
+column-major (``x.stride(0) == 1``; leading dimension ``x.stride(1)``), which
+``colmajor`` produces from any tensor.  Every computation runs in the CUDA
+library; if it cannot be loaded this module raises, it never falls back.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liboqr.so")
+HEADERS = [os.path.join(os.path.dirname(HERE), "include", "oqr.h")]
+
+OQR_OK, OQR_ERR_INVALID_ARG, OQR_ERR_NOT_SPD, OQR_ERR_CHECK_FAILED = 0, 1, 2, 3
+OQR_ERR_CUDA, OQR_ERR_NO_MEMORY, OQR_ERR_TIMEOUT, OQR_ERR_UNSUPPORTED = 4, 5, 6, 7
+OQR_FP64, OQR_BF16X3, OQR_FP8 = 0, 1, 2
+OQR_ALGO_CHOLQR, OQR_ALGO_CHOLQR2, OQR_ALGO_SCHOLQR3, OQR_ALGO_CGS2 = 0, 1, 2, 3
+
+
+class oqr_opts(ctypes.Structure):
+    _fields_ = [("passes", ctypes.c_int), ("shifted", ctypes.c_int), ("prec", ctypes.c_int),
+                ("shift_c", ctypes.c_double), ("block", ctypes.c_int), ("check", ctypes.c_int),
+                ("spin_limit", ctypes.c_long)]
+
+
+class oqr_info(ctypes.Structure):
+    _fields_ = [("info", ctypes.c_int), ("passes_run", ctypes.c_int), ("orth_err", ctypes.c_double),
+                ("shift", ctypes.c_double)]
+
+
+class OqrError(RuntimeError):
+    def __init__(self, status, what, info=0):
+        self.status = status
+        self.info = info
+        super().__init__(f"{what}: {status_string(status)} (info={info})")
+
+
+_lib = None
+
+
+def declared_functions(headers=None):
+    """Names of the functions declared in include/*.h (used by the export test)."""
+    names = []
+    for h in headers or HEADERS:
+        txt = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*(oqr_[a-z0-9_]+)\s*\(", txt, flags=re.M)
+    return sorted(set(names))
+
+
+def load(path: str | None = None):
+    """Loads liboqr.so (building it first if it is missing and nvcc is present)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        from . import build as _build
+        _build.build()
+    if not os.path.exists(p):
+        raise RuntimeError(f"liboqr.so not found at {p}: build it with paper_1401_5171_gb300/build.py")
+    lib = ctypes.CDLL(p)
+    vp, i, l, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_long, ctypes.c_double
+    S = ctypes.c_int
+    po, pi = ctypes.POINTER(oqr_opts), ctypes.POINTER(oqr_info)
+    lib.oqr_default_opts.argtypes = [po]
+    lib.oqr_default_opts.restype = None
+    lib.oqr_status_string.argtypes = [S]
+    lib.oqr_status_string.restype = ctypes.c_char_p
+    lib.oqr_create.argtypes = [ctypes.POINTER(vp), i]
+    lib.oqr_destroy.argtypes = [vp]
+    lib.oqr_workspace_size.argtypes = [vp, i, i, i, po, ctypes.POINTER(ctypes.c_size_t)]
+    lib.oqr_set_workspace.argtypes = [vp, vp, ctypes.c_size_t]
+    lib.oqr_get_status.argtypes = [vp, vp, ctypes.POINTER(i)]
+    qr = [vp, i, i, vp, l, vp, l, vp, l, vp, l, po, pi, vp]
+    for name in ("oqr_cholqr", "oqr_cholqr2", "oqr_cgs2"):
+        getattr(lib, name).argtypes = qr
+    lib.oqr_gram.argtypes = [vp, i, i, vp, l, vp, l, vp, l, i, vp]
+    lib.oqr_potrf.argtypes = [vp, i, vp, l, d, vp, l, ctypes.POINTER(i), vp]
+    lib.oqr_trsm.argtypes = [vp, i, i, vp, l, vp, l, vp, l, vp]
+    lib.oqr_rprod.argtypes = [vp, i, vp, l, vp, l, vp, l, vp]
+    lib.oqr_check.argtypes = [vp, i, i, vp, l, vp, l, vp, l, ctypes.POINTER(d), ctypes.POINTER(d), vp]
+    for name in declared_functions():
+        f = getattr(lib, name)
+        if f.restype is ctypes.c_int or name not in ("oqr_default_opts", "oqr_status_string"):
+            if name not in ("oqr_default_opts", "oqr_status_string"):
+                f.restype = S
+    _lib = lib
+    return lib
+
+
+def status_string(s: int) -> str:
+    return load().oqr_status_string(int(s)).decode()
+
+
+# ---- raw entry points, same names as the C ABI ------------------------------
+def _raw(name):
+    def f(*args):
+        return getattr(load(), name)(*args)
+    f.__name__ = name
+    return f
+
+
+for _n in ("oqr_default_opts", "oqr_create", "oqr_destroy", "oqr_workspace_size", "oqr_set_workspace",
+           "oqr_get_status", "oqr_cholqr", "oqr_cholqr2", "oqr_cgs2", "oqr_gram", "oqr_potrf", "oqr_trsm",
+           "oqr_rprod", "oqr_check"):
+    globals()[_n] = _raw(_n)
+
+
+# ---- tensor-level convenience -------------------------------------------------
+def colmajor(x):
+    """Column-major copy (or view) of a 2-D tensor: stride(0) == 1."""
+    if x.dim() == 1:
+        x = x.reshape(-1, 1)
+    if x.stride(0) == 1 and x.stride(1) >= max(1, x.shape[0]):
+        return x
+    return x.t().contiguous().t()
+
+
+def _m(x):
+    if x.dtype.is_floating_point is False or x.element_size() != 8:
+        raise TypeError("liboqr matrices are float64")
+    if not x.is_cuda:
+        raise TypeError("liboqr matrices live in device memory")
+    if x.dim() != 2 or x.stride(0) != 1:
+        raise ValueError("matrix must be 2-D column-major (stride(0) == 1); use colmajor()")
+    return ctypes.c_void_p(x.data_ptr()), ctypes.c_long(max(1, x.stride(1)))
+
+
+def empty_colmajor(rows, cols, device, dtype=None):
+    import torch
+    return torch.empty((cols, rows), dtype=dtype or torch.float64, device=device).t()
+
+
+def make_opts(**kw) -> oqr_opts:
+    o = oqr_opts()
+    load().oqr_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class Oqr:
+    """A liboqr context on one device; methods take column-major float64 CUDA tensors."""
+
+    def __init__(self, device: int = 0):
+        self.lib = load()
+        self.device = device
+        self.ctx = ctypes.c_void_p()
+        st = self.lib.oqr_create(ctypes.byref(self.ctx), int(device))
+        if st != OQR_OK:
+            raise OqrError(st, "oqr_create")
+
+    def close(self):
+        if self.ctx:
+            self.lib.oqr_destroy(self.ctx)
+            self.ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _stream(stream):
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream()
+        return ctypes.c_void_p(s.cuda_stream)
+
+    def _qr(self, name, A, Z, Q=None, R=None, opts=None, stream=None, sync=True, raise_on_error=True, **kw):
+        m, n = Z.shape
+        Q = Q if Q is not None else empty_colmajor(m, n, Z.device)
+        R = R if R is not None else empty_colmajor(n, n, Z.device)
+        o = opts if opts is not None else make_opts(**kw)
+        info = oqr_info()
+        a, lda = _m(A)
+        z, ldz = _m(Z)
+        q, ldq = _m(Q)
+        r, ldr = _m(R)
+        st = getattr(self.lib, name)(self.ctx, m, n, a, lda, z, ldz, q, ldq, r, ldr, ctypes.byref(o),
+                                     ctypes.byref(info) if sync else None, self._stream(stream))
+        if st != OQR_OK and raise_on_error:
+            raise OqrError(st, name, info.info)
+        return Q, R, (st, info)
+
+    def oqr_cholqr(self, A, Z, **kw):
+        return self._qr("oqr_cholqr", A, Z, **kw)
+
+    def oqr_cholqr2(self, A, Z, **kw):
+        return self._qr("oqr_cholqr2", A, Z, **kw)
+
+    def oqr_cgs2(self, A, Z, **kw):
+        return self._qr("oqr_cgs2", A, Z, **kw)
+
+    def oqr_gram(self, A, Z, G=None, prec=OQR_FP64, stream=None):
+        n = Z.shape[1]
+        G = G if G is not None else empty_colmajor(n, n, Z.device)
+        a, lda = _m(A)
+        z, ldz = _m(Z)
+        g, ldg = _m(G)
+        st = self.lib.oqr_gram(self.ctx, Z.shape[0], n, a, lda, z, ldz, g, ldg, prec, self._stream(stream))
+        if st != OQR_OK:
+            raise OqrError(st, "oqr_gram")
+        return G
+
+    def oqr_potrf(self, G, shift=0.0, R=None, stream=None):
+        n = G.shape[0]
+        R = R if R is not None else empty_colmajor(n, n, G.device)
+        g, ldg = _m(G)
+        r, ldr = _m(R)
+        info = ctypes.c_int(0)
+        st = self.lib.oqr_potrf(self.ctx, n, g, ldg, float(shift), r, ldr, ctypes.byref(info), self._stream(stream))
+        return R, st, info.value
+
+    def oqr_trsm(self, Z, R, Q=None, stream=None):
+        m, n = Z.shape
+        Q = Q if Q is not None else empty_colmajor(m, n, Z.device)
+        z, ldz = _m(Z)
+        r, ldr = _m(R)
+        q, ldq = _m(Q)
+        st = self.lib.oqr_trsm(self.ctx, m, n, z, ldz, r, ldr, q, ldq, self._stream(stream))
+        if st != OQR_OK:
+            raise OqrError(st, "oqr_trsm")
+        return Q
+
+    def oqr_rprod(self, U, S, R=None, stream=None):
+        n = U.shape[0]
+        R = R if R is not None else empty_colmajor(n, n, U.device)
+        u, ldu = _m(U)
+        s_, lds = _m(S)
+        r, ldr = _m(R)
+        st = self.lib.oqr_rprod(self.ctx, n, u, ldu, s_, lds, r, ldr, self._stream(stream))
+        if st != OQR_OK:
+            raise OqrError(st, "oqr_rprod")
+        return R
+
+    def oqr_check(self, A, Q, want_E=False, stream=None):
+        m, n = Q.shape
+        E = empty_colmajor(n, n, Q.device) if want_E else None
+        a, lda = _m(A)
+        q, ldq = _m(Q)
+        e, lde = _m(E) if E is not None else (None, ctypes.c_long(n))
+        o2, of = ctypes.c_double(), ctypes.c_double()
+        st = self.lib.oqr_check(self.ctx, m, n, a, lda, q, ldq, e, lde, ctypes.byref(o2), ctypes.byref(of),
+                                self._stream(stream))
+        if st != OQR_OK:
+            raise OqrError(st, "oqr_check")
+        return o2.value, of.value, E

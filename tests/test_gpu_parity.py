@@ -1,0 +1,281 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+The oracle is CHOL-EQR (Algorithm 3) in plain C; the unique oblique QR it
+returns is what every normal-equation variant must reach.  Tolerances
+(FP64 path, kappa(A^{1/2} Z) <= 1e3): ||R - R_ref|| / ||R|| <= 1e-12 and
+||Q^T A Q - I||_2 <= max(1e-12, 10 x the oracle's own), with the
+orthogonality of the GPU's Q measured on the CPU in long double.  One-pass
+A-CholQR is held to 100 x the error of the same algorithm restated on the
+CPU (Thm 2.1: its error grows like kappa^2).  Step kernels are compared
+element by element with the oracle's definitions.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1401_5171_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+U = 2.0 ** -53
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1401_5171_gb300 import oqr
+    return torch, oqr, oqr.Oqr(0)
+
+
+def dev(torch, x, oqr):
+    return oqr.colmajor(torch.as_tensor(np.asarray(x), dtype=torch.float64).cuda())
+
+
+def host(x):
+    return np.asfortranarray(x.cpu().numpy())
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+# --------------------------------------------------------------- step kernels --
+@pytest.mark.parametrize("m,n", [(1, 1), (7, 3), (128, 64), (300, 37), (1000, 130), (2000, 20), (513, 257)])
+def test_gram_matches_oracle(env, m, n):
+    torch, oqr, ctx = env
+    rng = np.random.default_rng(m * 7 + n)
+    B = rng.standard_normal((m, m))
+    A = B + B.T + 2 * m * np.eye(m)
+    Z = rng.standard_normal((m, n))
+    P = A.copy()
+    P[np.triu_indices(m, 1)] = np.nan          # the upper triangle is never used
+    G = host(ctx.oqr_gram(dev(torch, P, oqr), dev(torch, Z, oqr)))
+    Gr = oracle.gram(A, Z)
+    assert np.array_equal(G, G.T)              # exactly symmetric by construction
+    scale = np.abs(Z).T @ np.abs(A) @ np.abs(Z)
+    assert np.all(np.abs(G - Gr) <= 4 * m * U * scale + 1e-300)
+
+
+def test_gram_odd_leading_dimension_plain_path(env):
+    torch, oqr, ctx = env
+    m, n = 301, 45
+    rng = np.random.default_rng(5)
+    B = rng.standard_normal((m, m))
+    A = B @ B.T
+    Z = rng.standard_normal((m, n))
+    # lda = m + 2 = 303: its byte stride is not a multiple of 16, so TMA cannot address A
+    Ab = torch.zeros((m, m + 2), dtype=torch.float64, device="cuda")
+    Ab[:, :m] = torch.as_tensor(A.T)
+    Am = Ab.t()[:m]
+    assert Am.stride(0) == 1 and Am.stride(1) == m + 2
+    Zm = dev(torch, Z, oqr)
+    G = host(ctx.oqr_gram(Am, Zm))
+    scale = np.abs(Z).T @ np.abs(A) @ np.abs(Z)
+    assert np.all(np.abs(G - oracle.gram(A, Z)) <= 4 * m * U * scale)
+
+
+@pytest.mark.parametrize("n", [1, 5, 32, 33, 100, 257, 512])
+def test_potrf_matches_oracle(env, n):
+    torch, oqr, ctx = env
+    rng = np.random.default_rng(n)
+    B = rng.standard_normal((n, n))
+    G = B @ B.T + n * np.eye(n)
+    P = G.copy()
+    P[np.triu_indices(n, 1)] = np.nan
+    R, st, info = ctx.oqr_potrf(dev(torch, P, oqr))
+    assert st == oqr.OQR_OK and info == 0
+    R = host(R)
+    Rr = oracle.chol_upper(G)
+    assert np.all(np.tril(R, -1) == 0)
+    assert rel(R, Rr) < 1e-13
+
+
+def test_potrf_pascal_exact(env):
+    torch, oqr, ctx = env
+    n = 12
+    P = np.array([[math.comb(i + j, i) for j in range(n)] for i in range(n)], dtype=np.float64)
+    R, st, _ = ctx.oqr_potrf(dev(torch, P, oqr))
+    assert st == oqr.OQR_OK
+    assert np.array_equal(host(R), oracle.chol_upper(P))
+
+
+@pytest.mark.parametrize("n,col", [(4, 3), (40, 35), (70, 1)])
+def test_potrf_breakdown_column(env, n, col):
+    torch, oqr, ctx = env
+    d = np.ones(n)
+    d[col - 1] = -1.0
+    G = np.diag(d)
+    with pytest.raises(oracle.OracleBreakdown) as e:
+        oracle.chol_upper(G)
+    R, st, info = ctx.oqr_potrf(dev(torch, G, oqr))
+    assert st == oqr.OQR_ERR_NOT_SPD and info == e.value.column == col
+
+
+def test_potrf_shift(env):
+    torch, oqr, ctx = env
+    n = 50
+    rng = np.random.default_rng(3)
+    B = rng.standard_normal((n, n))
+    G = B @ B.T + np.eye(n)
+    R, st, _ = ctx.oqr_potrf(dev(torch, G, oqr), shift=2.5)
+    assert rel(host(R), oracle.chol_upper(G + 2.5 * np.eye(n))) < 1e-13
+
+
+@pytest.mark.parametrize("m,n", [(1, 1), (63, 20), (1000, 33), (2000, 20), (4097, 300), (640, 512)])
+def test_trsm_matches_oracle(env, m, n):
+    torch, oqr, ctx = env
+    rng = np.random.default_rng(m + n)
+    R = np.triu(rng.standard_normal((n, n))) + 3 * np.eye(n)
+    Z = rng.standard_normal((m, n))
+    Q = host(ctx.oqr_trsm(dev(torch, Z, oqr), dev(torch, R, oqr)))
+    Qr = oracle.trsm_right_upper(Z, R)
+    assert rel(Q, Qr) < 1e-13
+    # in place
+    Zd = dev(torch, Z, oqr)
+    ctx.oqr_trsm(Zd, dev(torch, R, oqr), Q=Zd)
+    assert rel(host(Zd), Qr) < 1e-13
+
+
+def test_trsm_exact_integers(env):
+    torch, oqr, ctx = env
+    rng = np.random.default_rng(4)
+    m, n = 200, 70
+    R = np.triu(rng.integers(-3, 4, size=(n, n))).astype(np.float64)
+    np.fill_diagonal(R, 2.0 ** rng.integers(0, 3, size=n))
+    Q0 = rng.integers(-2, 3, size=(m, n)).astype(np.float64)
+    Z = Q0 @ R
+    assert np.abs(Z).max() < 2 ** 40
+    assert np.array_equal(host(ctx.oqr_trsm(dev(torch, Z, oqr), dev(torch, R, oqr))), Q0)
+
+
+@pytest.mark.parametrize("n", [1, 9, 64, 200])
+def test_rprod_exact(env, n):
+    torch, oqr, ctx = env
+    rng = np.random.default_rng(n)
+    Uu = np.triu(rng.integers(-5, 6, size=(n, n))).astype(np.float64)
+    S = np.triu(rng.integers(-5, 6, size=(n, n))).astype(np.float64)
+    assert np.array_equal(host(ctx.oqr_rprod(dev(torch, Uu, oqr), dev(torch, S, oqr))), oracle.upper_times_upper(Uu, S))
+
+
+# --------------------------------------------------------------- whole path --
+def factor(ctx, name, torch, oqr, A, Z, **kw):
+    Q, R, (st, info) = getattr(ctx, name)(dev(torch, A, oqr), dev(torch, Z, oqr), **kw)
+    return host(Q), host(R), info
+
+
+@pytest.mark.parametrize("name,kw", [("oqr_cholqr2", {}), ("oqr_cholqr2", {"shifted": 1}),
+                                     ("oqr_cgs2", {}), ("oqr_cgs2", {"block": 7})])
+def test_config0_parity(env, name, kw):
+    torch, oqr, ctx = env
+    A, Z = inputs.config0(seed=0)
+    Qr, Rr = oracle.oblique_qr(A, Z)
+    orth_ref = oracle.orth_error(A, Qr)
+    Q, R, info = factor(ctx, name, torch, oqr, A, Z, **kw)
+    assert np.all(np.tril(R, -1) == 0) and np.all(np.diag(R) > 0)
+    assert rel(R, Rr) <= 1e-12
+    assert oracle.orth_error(A, Q) <= max(1e-12, 10 * orth_ref)
+    assert rel(Q, Qr) <= 1e-10
+    assert oracle.repres_error(Z, Q, R) <= 1e-13
+
+
+def test_config0_one_pass_cholqr(env):
+    torch, oqr, ctx = env
+    A, Z = inputs.config0(seed=0)
+    Qr, Rr = oracle.oblique_qr(A, Z)
+    Qc, Rc = oracle.cholqr(A, Z)                       # the same algorithm on the CPU
+    Q, R, _ = factor(ctx, "oqr_cholqr", torch, oqr, A, Z)
+    assert rel(R, Rr) <= max(100 * rel(Rc, Rr), 1e-12)
+    assert oracle.orth_error(A, Q) <= max(100 * oracle.orth_error(A, Qc), 1e-12)
+    assert oracle.repres_error(Z, Q, R) <= 1e-13
+
+
+@pytest.mark.parametrize("case", [1, 2, 3, 4, 5])
+def test_paper_cases_cholqr2(env, case):
+    # Sec. 7 cases at m=80, n=10, kappa(A)=1e6, kappa(Z)=1e3
+    torch, oqr, ctx = env
+    A, Z = inputs.paper_case(case, 80, 10, 1e6, 1e3 if case != 5 else None, seed=40 + case)
+    Qr, Rr = oracle.oblique_qr(A, Z)
+    kap = np.linalg.cond(Rr)
+    Q, R, _ = factor(ctx, "oqr_cholqr2", torch, oqr, A, Z)
+    assert rel(R, Rr) <= max(1e-12, 100 * kap * U)
+    assert oracle.orth_error(A, Q) <= max(1e-12, 10 * oracle.orth_error(A, Qr))
+
+
+@pytest.mark.parametrize("m,n", [(1, 1), (2, 2), (5, 1), (64, 64), (129, 65), (1000, 130), (777, 100)])
+def test_ragged_and_edge_shapes(env, m, n):
+    torch, oqr, ctx = env
+    A, Z = inputs.paper_case(4, m, n, 1e3, 1e1, seed=m + n)
+    Qr, Rr = oracle.oblique_qr(A, Z)
+    Q, R, _ = factor(ctx, "oqr_cholqr2", torch, oqr, A, Z)
+    assert rel(R, Rr) <= 1e-12
+    assert oracle.orth_error(A, Q) <= 1e-12
+
+
+def test_in_place_and_upper_triangle_garbage(env):
+    torch, oqr, ctx = env
+    A, Z = inputs.paper_case(4, 500, 40, 1e4, 1e2, seed=9)
+    Qr, Rr = oracle.oblique_qr(A, Z)
+    P = A.copy()
+    P[np.triu_indices(500, 1)] = np.nan
+    Ad, Zd = dev(torch, P, oqr), dev(torch, Z, oqr)
+    Q, R, _ = ctx.oqr_cholqr2(Ad, Zd, Q=Zd)
+    assert Q.data_ptr() == Zd.data_ptr()
+    assert rel(host(R), Rr) <= 1e-12 and oracle.orth_error(A, host(Q)) <= 1e-12
+
+
+def test_not_spd_reports_breakdown(env):
+    torch, oqr, ctx = env
+    m, n = 200, 10
+    A = np.eye(m)
+    A[3, 3] = -1.0                                 # indefinite A
+    Z = np.zeros((m, n))
+    Z[:n, :n] = np.eye(n)
+    Q, R, (st, info) = ctx.oqr_cholqr(dev(torch, A, oqr), dev(torch, Z, oqr), raise_on_error=False)
+    assert st == oqr.OQR_ERR_NOT_SPD and info.info == 4
+
+
+def test_check_matches_oracle(env):
+    torch, oqr, ctx = env
+    A, Z = inputs.config0(seed=1)
+    Q, R, _ = factor(ctx, "oqr_cholqr", torch, oqr, A, Z)   # one pass: visible loss of orthogonality
+    o2, oF, E = ctx.oqr_check(dev(torch, A, oqr), dev(torch, Q, oqr), want_E=True)
+    Er = oracle.orth_defect(A, Q)
+    ref2 = float(np.max(np.abs(np.linalg.eigvalsh(0.5 * (Er + Er.T)))))
+    assert abs(o2 - ref2) <= 0.05 * ref2 + 1e-14
+    assert abs(oF - np.linalg.norm(Er)) <= 0.01 * np.linalg.norm(Er) + 1e-14
+    _, _, (st, info) = ctx.oqr_cholqr2(dev(torch, A, oqr), dev(torch, Z, oqr), check=1)
+    assert 0 <= info.orth_err < 1e-12
+
+
+# ---------------------------------------------------- full size, properties --
+@pytest.mark.parametrize("shifted", [0, 1])
+def test_config1_full_size_properties(env, shifted):
+    """m=32768, n=256, kappa(A)=1e6, kappa(Z)=1e2: the benchmark's launch configuration.
+
+    No oracle at this size: Q^T A Q = I, Z = Q R, R upper with positive
+    diagonal, and sigma(R)^2 = eig(Z^T A Z) (Thm 1.1) together fix (Q, R);
+    each is measured with torch's own FP64 GEMM/eigensolver on the GPU.
+    """
+    torch, oqr, ctx = env
+    m, n = 32768, 256
+    Af, _ = inputs.dense_spd(m, 1e6, seed=101, device="cuda")
+    Z = inputs.tall_z(m, n, 1e2, seed=102, device="cuda")
+    A = oqr.colmajor(Af)
+    Zc = oqr.colmajor(Z.clone())
+    Q, R, (st, info) = ctx.oqr_cholqr2(A, Zc, shifted=shifted)
+    assert st == 0
+    AQ = Af @ Q
+    E = Q.T @ AQ - torch.eye(n, dtype=torch.float64, device="cuda")
+    orth = torch.linalg.eigvalsh(0.5 * (E + E.T)).abs().max().item()
+    rep = (torch.linalg.matrix_norm(Z - Q @ R, 2) / torch.linalg.matrix_norm(Z, 2)).item()
+    assert torch.all(torch.tril(R, -1) == 0) and torch.all(torch.diagonal(R) > 0)
+    sv = torch.linalg.svdvals(R).sort().values
+    G = Z.T @ (Af @ Z)
+    ev = torch.linalg.eigvalsh(0.5 * (G + G.T)).clamp_min(0).sqrt().sort().values
+    assert torch.max((sv - ev).abs() / ev.max()).item() < 1e-10
+    assert orth < 1e-11 and rep < 1e-13
+    del Af, A, AQ, G
+    torch.cuda.empty_cache()
