@@ -142,6 +142,26 @@ def ncu_traffic(kernel_tag, source_files):
     return float(mt.group(1))
 
 
+def size_oracle_sample(n, kappa_a, kappa_z, target_s, m_max):
+    """Largest m (multiple of 256, <= m_max) whose oracle run is predicted to
+    take about target_s seconds, from a warm timing at m=1024."""
+    import oracle
+    from paper_1401_5171_gb300 import inputs
+    oracle.build()
+    m0 = 1024
+    A, _ = inputs.dense_spd(m0, kappa_a, seed=5)
+    Z = inputs.tall_z(m0, min(n, m0), kappa_z, seed=6)
+    A, Z = A.numpy(), Z.numpy()
+    oracle.oblique_qr(A, Z)                    # warm up threads and caches
+    t = time.perf_counter()
+    oracle.oblique_qr(A, Z)
+    t0 = time.perf_counter() - t
+    ms = m0
+    while ms + 256 <= m_max and t0 * oracle_cost(ms + 256, n) / oracle_cost(m0, min(n, m0)) < target_s:
+        ms += 256
+    return ms, min(n, ms)
+
+
 def cpu_baseline_sample(n, target_s=12.0):
     """Times the oracle on a bounded sample: one instance of the same recipe at a
     smaller m sized for ~target_s seconds; returns (seconds, m_sample, n_sample)."""
@@ -149,17 +169,7 @@ def cpu_baseline_sample(n, target_s=12.0):
 
     import oracle
     from paper_1401_5171_gb300 import inputs
-    oracle.build()
-    m0 = 768
-    A, _ = inputs.dense_spd(m0, 1e6, seed=5)
-    Z = inputs.tall_z(m0, min(n, m0), 1e2, seed=6)
-    t = time.perf_counter()
-    oracle.oblique_qr(A.numpy(), Z.numpy())
-    t0 = time.perf_counter() - t
-    ms = m0
-    while ms < 32768 and t0 * oracle_cost(2 * ms, n) / oracle_cost(m0, n) < target_s:
-        ms *= 2
-    ns = min(n, ms)
+    ms, ns = size_oracle_sample(n, 1e6, 1e2, target_s, 32768)
     A, _ = inputs.dense_spd(ms, 1e6, seed=5)
     Z = inputs.tall_z(ms, ns, 1e2, seed=6)
     A, Z = np.asfortranarray(A.numpy()), np.asfortranarray(Z.numpy())
@@ -177,17 +187,9 @@ def run_reference(args, rank, world):
     import oracle
     from paper_1401_5171_gb300 import inputs
     oracle.build()
-    # sample size: ~4 s per step so that warmup + steps stays within minutes
-    m0 = 768
-    A, _ = inputs.dense_spd(m0, args.kappa_a, seed=5)
-    Z = inputs.tall_z(m0, min(args.n, m0), args.kappa_z, seed=6)
-    t = time.perf_counter()
-    oracle.oblique_qr(A.numpy(), Z.numpy())
-    t0 = time.perf_counter() - t
-    ms = m0
-    while ms < args.m and t0 * oracle_cost(2 * ms, args.n) / oracle_cost(m0, args.n) < 4.0:
-        ms *= 2
-    ns = min(args.n, ms)
+    # sample size: a few seconds per step so that warmup + steps stays within minutes
+    per_step = min(8.0, 150.0 / max(1, args.warmup + args.steps))
+    ms, ns = size_oracle_sample(args.n, args.kappa_a, args.kappa_z, per_step, args.m)
     A, _ = inputs.dense_spd(ms, args.kappa_a, seed=5)
     Z = inputs.tall_z(ms, ns, args.kappa_z, seed=6)
     A, Z = np.asfortranarray(A.numpy()), np.asfortranarray(Z.numpy())
