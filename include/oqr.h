@@ -173,6 +173,26 @@ oqr_status oqr_rprod(oqr_ctx* ctx, int n, const double* U, long ldu, const doubl
 oqr_status oqr_check(oqr_ctx* ctx, int m, int n, const double* A, long lda, const double* Q, long ldq,
                      double* E, long lde, double* orth2, double* orthF, void* stream);
 
+/*
+ * oqr_gram_noalloc: the same G = Z^T A Z as oqr_gram (FP64), for callers that
+ *   cannot allocate device memory (a plug-in under another framework's caching
+ *   allocator that owns the memory; real-time or embedded hosts that fix their
+ *   memory at start-up).  The paper has no counterpart: this is a
+ *   deployment variant of the step kernel.  It takes no context and allocates
+ *   nothing: its scratch (split-K partials and a status word) is one
+ *   file-scope device array of 8 MiB + 256 B that every GPU loading the
+ *   library holds until the process exits.  A, Z, G are caller-owned device
+ *   memory on the current device; A is read from its lower triangle.
+ *   Limits: n <= 1024 (n above that returns OQR_ERR_UNSUPPORTED); the
+ *   partial count is capped at floor(8 MiB / (8 n^2)), so large n runs on
+ *   fewer CTAs than oqr_gram.  The first call on a device looks up the
+ *   array's device address and should come before any stream capture on that
+ *   device.  All calls share the array: calls that overlap on the GPU race.
+ *   Device-side timeouts are not reported (there is no context to hold them).
+ */
+oqr_status oqr_gram_noalloc(int m, int n, const double* A, long lda, const double* Z, long ldz, double* G,
+                            long ldg, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -82,6 +82,7 @@ def load(path: str | None = None):
     for name in ("oqr_cholqr", "oqr_cholqr2", "oqr_cgs2"):
         getattr(lib, name).argtypes = qr
     lib.oqr_gram.argtypes = [vp, i, i, vp, l, vp, l, vp, l, i, vp]
+    lib.oqr_gram_noalloc.argtypes = [i, i, vp, l, vp, l, vp, l, vp]
     lib.oqr_potrf.argtypes = [vp, i, vp, l, d, vp, l, ctypes.POINTER(i), vp]
     lib.oqr_trsm.argtypes = [vp, i, i, vp, l, vp, l, vp, l, vp]
     lib.oqr_rprod.argtypes = [vp, i, vp, l, vp, l, vp, l, vp]
@@ -108,7 +109,7 @@ def _raw(name):
 
 
 for _n in ("oqr_default_opts", "oqr_create", "oqr_destroy", "oqr_workspace_size", "oqr_set_workspace",
-           "oqr_get_status", "oqr_cholqr", "oqr_cholqr2", "oqr_cgs2", "oqr_gram", "oqr_potrf", "oqr_trsm",
+           "oqr_get_status", "oqr_cholqr", "oqr_cholqr2", "oqr_cgs2", "oqr_gram", "oqr_gram_noalloc", "oqr_potrf", "oqr_trsm",
            "oqr_rprod", "oqr_check"):
     globals()[_n] = _raw(_n)
 
