@@ -187,13 +187,8 @@ def tall_z(m: int, n: int, kappa_z: float, seed: int, device="cpu", U=None):
 
     rng = np.random.default_rng(seed)
     if U is None:
-        g = torch.tensor(rng.standard_normal((m, n)), dtype=torch.float64, device=device)
-        q, r = torch.linalg.qr(g)
-        s = torch.sign(torch.diagonal(r))
-        s[s == 0] = 1.0
-        U = q * s
-    else:
-        U = torch.as_tensor(np.asarray(U), dtype=torch.float64, device=device)
+        U = haar(rng, m, n)          # on the host: one m x n QR
+    U = torch.as_tensor(np.asarray(U), dtype=torch.float64, device=device)
     W = torch.tensor(haar(rng, n), dtype=torch.float64, device=device)
     sig = torch.tensor(singular_values(n, kappa_z), dtype=torch.float64, device=device)
     return (U * sig) @ W.T

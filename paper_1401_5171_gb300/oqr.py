@@ -115,11 +115,25 @@ for _n in ("oqr_default_opts", "oqr_create", "oqr_destroy", "oqr_workspace_size"
 
 
 # ---- tensor-level convenience -------------------------------------------------
+def _leading_dim(x):
+    """Leading dimension of a column-major 2-D tensor, or None if it is not column-major.
+
+    Strides of size-1 dimensions carry no information (torch normalises them),
+    so a single column has leading dimension = its row count and a single row
+    needs no unit row stride.
+    """
+    rows, cols = x.shape
+    if rows > 1 and x.stride(0) != 1:
+        return None
+    ld = x.stride(1) if cols > 1 else rows
+    return ld if ld >= max(1, rows) else None
+
+
 def colmajor(x):
-    """Column-major copy (or view) of a 2-D tensor: stride(0) == 1."""
+    """Column-major copy (or view) of a 2-D tensor: element (i, j) at i + j * ld."""
     if x.dim() == 1:
         x = x.reshape(-1, 1)
-    if x.stride(0) == 1 and x.stride(1) >= max(1, x.shape[0]):
+    if _leading_dim(x) is not None:
         return x
     return x.t().contiguous().t()
 
@@ -129,9 +143,10 @@ def _m(x):
         raise TypeError("liboqr matrices are float64")
     if not x.is_cuda:
         raise TypeError("liboqr matrices live in device memory")
-    if x.dim() != 2 or x.stride(0) != 1:
+    ld = _leading_dim(x) if x.dim() == 2 else None
+    if ld is None:
         raise ValueError("matrix must be 2-D column-major (stride(0) == 1); use colmajor()")
-    return ctypes.c_void_p(x.data_ptr()), ctypes.c_long(max(1, x.stride(1)))
+    return ctypes.c_void_p(x.data_ptr()), ctypes.c_long(max(1, ld))
 
 
 def empty_colmajor(rows, cols, device, dtype=None):
