@@ -51,9 +51,11 @@ typedef enum {
 } oqr_status;
 
 typedef enum {
-    OQR_FP64 = 0,     /* every product in FP64 */
-    OQR_BF16X3 = 1,   /* preconditioning passes: hi/lo BF16 split, 3 products, FP32 accumulation */
-    OQR_FP8 = 2       /* preconditioning passes: E4M3 with power-of-two block scales */
+    OQR_FP64 = 0,     /* every product in FP64 (DFMA) */
+    OQR_BF16X3 = 1,   /* hi/lo BF16 split, 3 products, FP32 accumulation (tensor cores) */
+    OQR_FP8 = 2,      /* E4M3 with power-of-two block scales (not in this build: OQR_ERR_UNSUPPORTED) */
+    OQR_FP64_TC = 3   /* FP64-accurate products from 7 exact BF16 slices per operand, exact FP32
+                         accumulation per 128-long chunk, double-float sum (tensor cores) */
 } oqr_precision;
 
 typedef enum { OQR_ALGO_CHOLQR = 0, OQR_ALGO_CHOLQR2 = 1, OQR_ALGO_SCHOLQR3 = 2, OQR_ALGO_CGS2 = 3 } oqr_algo;
@@ -67,6 +69,7 @@ typedef struct {
     int block;        /* oqr_cgs2: column block size b [64] */
     int check;        /* 1 = measure ||Q^T A Q - I||_2 after the factorization into info->orth_err [0] */
     long spin_limit;  /* time limit of any device-side wait, in nanoseconds [4e9] */
+    int final_prec;   /* oqr_cholqr2: oqr_precision of the last pass [OQR_FP64]; OQR_FP64 or OQR_FP64_TC */
 } oqr_opts;
 
 /* Optional per-call report (filled only when passed non-NULL). */
@@ -127,8 +130,12 @@ oqr_status oqr_cholqr(oqr_ctx* ctx, int m, int n, const double* A, long lda, con
  * completes for ill-conditioned Z, then runs two plain passes,
  * R = R_3 R_2 R_1.  Neither repetition is in the paper; they follow the
  * Euclidean CholeskyQR2 and shifted CholeskyQR3 with Z^T Z replaced by
- * Z^T A Z.  With opts->prec = OQR_BF16X3 or OQR_FP8 every pass but the last
- * forms its normal-equation matrix in that precision; the last pass is FP64.
+ * Z^T A Z.  Every pass but the last forms its normal-equation matrix in
+ * opts->prec and the last in opts->final_prec; the Cholesky factorizations,
+ * the shift, the triangular solves and R = R_2 R_1 are always FP64.  The
+ * mixed form (prec = OQR_BF16X3, final_prec = OQR_FP64_TC) runs all products
+ * on the tensor cores; its accuracy comes from the last pass, whose
+ * normal-equation matrix is FP64-accurate.
  */
 oqr_status oqr_cholqr2(oqr_ctx* ctx, int m, int n, const double* A, long lda, const double* Z, long ldz,
                        double* Q, long ldq, double* R, long ldr, const oqr_opts* opts, oqr_info* info,
@@ -150,8 +157,8 @@ oqr_status oqr_cgs2(oqr_ctx* ctx, int m, int n, const double* A, long lda, const
  * Step kernels of Algorithm 1, exposed for testing and composition.
  *
  * oqr_gram: G = Z^T A Z (lines 1-2 of Algorithm 1), n x n, written in full
- *   and exactly symmetric.  prec selects the arithmetic of the products
- *   (OQR_FP64 only in this build of the step entry point).
+ *   and exactly symmetric.  prec selects the arithmetic of the products:
+ *   OQR_FP64 (DFMA), OQR_BF16X3 or OQR_FP64_TC (tensor cores).
  * oqr_potrf: R = chol(G + shift I) (line 3), G read from its lower triangle,
  *   R upper with positive diagonal, zeros below.  Breakdown is reported as
  *   OQR_ERR_NOT_SPD with the 1-based column (synchronizes the stream when

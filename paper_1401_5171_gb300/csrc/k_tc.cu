@@ -1,0 +1,943 @@
+// Tensor-core (tcgen05, BF16 -> FP32 in TMEM) products for the
+// normal-equation matrix of Algorithm 1 (lines 1-2: B = A Z, C = Z^T B).
+//
+// The paper forms both products in FP64 (MKL).  On GB300 FP64 runs at about
+// 1/1600 of the BF16 tensor rate, so this file computes them from BF16 slices
+// of the FP64 operands on the 5th-generation tensor cores, in one of two modes:
+//
+//  * BF16X3 (preconditioning passes): x = hi + lo with hi = bf16(x),
+//    lo = bf16(x - hi); the product sums hi*hi + hi*lo + lo*hi in one FP32
+//    TMEM accumulator.  Relative accuracy about 2^-16 per product plus FP32
+//    accumulation.
+//
+//  * EMU64 (FP64-accurate final pass; error-free slicing in the manner of
+//    Ozaki, Ogita, Oishi and Rump 2012): for every row of the left operand and
+//    every 128-long chunk of the contraction index k, a power-of-two exponent e
+//    is taken from the chunk's largest magnitude, and x 2^-e is written as
+//    sum_s x_s 2^(-7-8(s-1)) with integer x_s in [-128, 128] (exact in BF16),
+//    rounded to nearest at 2^(-7-48).
+//    The right operand is sliced the same way per column.  A product x_s y_t
+//    is an integer below 2^14; over one 128-long chunk the S-1 or fewer
+//    products of one level L = s + t sum to below 2^24 and are therefore exact
+//    in the FP32 accumulator.  Levels 2..S+1 (S(S+1)/2 products) each own a
+//    TMEM accumulator; after every chunk the drain warps scale each level by
+//    its power of two and add it into a double-float (hi, lo) register sum.
+//    With S = 7 the truncation error is about 2^-55 relative to the chunk's
+//    largest term.
+//
+// Kernel structure (one CTA per SM, persistent over work items):
+//   warp 0      TMA producer: all S slice tiles of A and of B per k-step
+//   warp 1      TMEM allocation and the single MMA-issuing thread
+//   warps 2..9  drain: tcgen05.ld of the accumulators (TMEM lane = row);
+//               two warps per TMEM lane quarter, each owning half the columns
+// An item is (128-row tile I of the left operand, a piece of its k range,
+// an N-column chunk of the right operand); its result goes to its own FP64
+// slot, and a reduce kernel sums the slots of each tile in a fixed order.
+// In triangular mode the left operand is M = tril(A,-1) + diag(A)/2 (rows i,
+// columns k <= i), so row tile I stops at k = 128 (I + 1).
+//
+// Every mbarrier wait is bounded by %globaltimer; on timeout the CTA records
+// OQR_ERR_TIMEOUT, stops issuing, drains in-flight copies with a bounded wait,
+// frees its TMEM and returns.
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include "oqr_internal.cuh"
+
+namespace oqr {
+namespace {
+
+constexpr int TM = 128;            // UMMA M (rows of the left operand per tile)
+constexpr int KCH = 128;           // exact chunk (EMU64) and exponent chunk
+constexpr int EXP_NONE = -100000;  // exponent of an all-zero chunk
+constexpr int TC_THREADS = 320;   // producer warp, MMA warp, 8 drain warps
+
+// ------------------------------------------------------------ splitting ----
+// GB300 issues about two FP64 instructions per clock per SM, so an FP64
+// operation per element of A costs about a millisecond at m = 32768.  The
+// splits therefore work on the FP64 bit pattern with integer instructions:
+// x = (-1)^s M 2^E with M the 53-bit integer significand.
+
+struct Bits {
+    unsigned long long M;  // integer significand (implicit bit included for normal numbers)
+    int Eb;                // biased exponent, 1 for zero and subnormals
+    bool neg;
+};
+
+__device__ inline Bits bits_of(double x)
+{
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const int b = (int)((u >> 52) & 0x7FF);
+    const unsigned long long f = u & 0xFFFFFFFFFFFFFull;
+    Bits r;
+    r.M = b ? (f | (1ull << 52)) : f;
+    r.Eb = b ? b : 1;
+    r.neg = (u >> 63) != 0;
+    return r;
+}
+
+// |x| as an integer key that orders like the magnitude (finite x).
+__device__ inline unsigned long long mag_key(double x)
+{
+    return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+
+// Chunk exponent e from the largest magnitude key: amax = f 2^e, f in [0.5, 1).
+__device__ inline int chunk_exponent_key(unsigned long long key)
+{
+    if (key == 0) return EXP_NONE;
+    const int b = (int)(key >> 52);
+    return b ? b - 1022 : -1021;
+}
+
+// Round-to-nearest-even right shift of a non-negative integer.
+__device__ inline unsigned long long rne_shift(unsigned long long v, int sh)
+{
+    if (sh <= 0) return v;
+    if (sh >= 64) return 0;
+    const unsigned long long q = v >> sh, rem = v & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+    return q + ((rem > half || (rem == half && (q & 1))) ? 1 : 0);
+}
+
+// EMU64 slices of x for chunk exponent e (|x| < 2^e): with y = x 2^(7-e),
+// Y = RNE(y 2^48) is an integer below 2^55, written in balanced base 256,
+// Y = sum_s d_s 2^(8(6-s)), d_s integers in [-128, 128]: out[s] = d_s, s = 0..6.
+__device__ inline void emu_slices7(double x, int e, float* out)
+{
+    const Bits b = bits_of(x);
+    const int k = b.Eb - e - 1020;  // y 2^48 = M 2^k, k <= 2 because |x| < 2^e
+    long long Y = 0;
+    if (b.M != 0) {
+        const unsigned long long mag = k >= 0 ? (b.M << k) : rne_shift(b.M, -k);
+        Y = b.neg ? -(long long)mag : (long long)mag;
+    }
+#pragma unroll
+    for (int s = 6; s >= 1; --s) {
+        int d = (int)(Y & 255);
+        if (d > 127) d -= 256;
+        out[s] = (float)d;
+        Y = (Y - d) >> 8;  // exact: Y - d is a multiple of 256
+    }
+    out[0] = (float)Y;
+}
+
+// hi = bf16(x), lo = bf16(x - hi), both round-to-nearest-even (8 significant bits).
+// Valid for |x| within the normal FP32 range, as BF16 itself.
+__device__ inline void bf16x2_split(double x, __nv_bfloat16& hi, __nv_bfloat16& lo)
+{
+    const Bits b = bits_of(x);
+    if (b.M == 0) {
+        hi = lo = __float2bfloat16_rn(0.0f);
+        return;
+    }
+    const int E = b.Eb - 1075;  // x = +-M 2^E
+    const int msb = 63 - __clzll((long long)b.M);
+    const int sh = msb - 7;
+    float hf, lf = 0.0f;
+    if (sh <= 0) {
+        hf = ldexpf((float)b.M, E);
+    } else {
+        const unsigned long long q = rne_shift(b.M, sh);  // <= 256
+        hf = ldexpf((float)q, E + sh);
+        const long long r = (long long)b.M - (long long)(q << sh);
+        if (r != 0) {
+            const unsigned long long ar = (unsigned long long)(r < 0 ? -r : r);
+            const int msb2 = 63 - __clzll((long long)ar);
+            const int sh2 = msb2 - 7 > 0 ? msb2 - 7 : 0;
+            const unsigned long long q2 = rne_shift(ar, sh2);
+            lf = ldexpf((float)q2, E + sh2);
+            if (r < 0) lf = -lf;
+        }
+    }
+    if (b.neg) {
+        hf = -hf;
+        lf = -lf;
+    }
+    hi = __float2bfloat16_rn(hf);  // exact: at most 8 significant bits
+    lo = __float2bfloat16_rn(lf);
+}
+
+__device__ inline unsigned long long warp_max_u64(unsigned long long v)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w > v ? w : v;
+    }
+    return v;
+}
+
+// A (m x m, column-major, lower triangle) -> slices of M = tril(A,-1) + diag(A)/2,
+// written row-major (row i, k contiguous): planes + s*plane + i*ldp + k.
+// One CTA: 32 rows x one 128-column chunk; 8 warps.
+template <bool EMU>
+__global__ void __launch_bounds__(256) split_lower_kernel(int m, const double* __restrict__ A, long lda, int S,
+                                                          __nv_bfloat16* planes, long ldp, size_t plane,
+                                                          int* eA, int* emax)
+{
+    __shared__ double T[32][KCH + 1];
+    const int kc = blockIdx.x, ib = blockIdx.y;
+    const long row0 = (long)ib * 32, col0 = (long)kc * KCH;
+    if (row0 >= m || col0 > row0 + 31) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int k = w; k < KCH; k += 8) {
+        const long i = row0 + lane, kk = col0 + k;
+        double v = 0.0;
+        if (i < m && kk < m && kk <= i) {
+            v = A[i + kk * lda];
+            if (kk == i) v *= 0.5;  // one FP64 multiply per diagonal element
+        }
+        T[lane][k] = v;
+    }
+    __syncthreads();
+    for (int r = w * 4; r < w * 4 + 4; ++r) {
+        const long i = row0 + r;
+        if (i >= m) break;
+        double v[4];
+        unsigned long long key = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            v[j] = T[r][lane + 32 * j];
+            const unsigned long long kj = mag_key(v[j]);
+            key = kj > key ? kj : key;
+        }
+        key = warp_max_u64(key);
+        const int e = EMU ? chunk_exponent_key(key) : 0;
+        if (EMU && lane == 0) {
+            eA[(size_t)kc * m + i] = e;
+            if (e != EXP_NONE) atomicMax(&emax[i], e);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const long k = col0 + lane + 32 * j;
+            if (k >= m) continue;
+            __nv_bfloat16* dst = planes + i * ldp + k;
+            if (EMU) {
+                float sl[7];
+                if (e == EXP_NONE) {
+#pragma unroll
+                    for (int s = 0; s < 7; ++s) sl[s] = 0.f;
+                } else {
+                    emu_slices7(v[j], e, sl);
+                }
+#pragma unroll
+                for (int s = 0; s < 7; ++s) dst[s * plane] = __float2bfloat16_rn(sl[s]);
+            } else {
+                __nv_bfloat16 hi, lo;
+                bf16x2_split(v[j], hi, lo);
+                dst[0] = hi;
+                dst[plane] = lo;
+            }
+        }
+    }
+}
+
+// X (K x C, column-major) -> slices written column-major (column c, k
+// contiguous): planes + s*plane + c*ldp + k.  One warp per (chunk, column).
+template <bool EMU>
+__global__ void __launch_bounds__(256) split_tall_kernel(int K, int C, const double* __restrict__ X, long ldx, int S,
+                                                         __nv_bfloat16* planes, long ldp, size_t plane, int* eX,
+                                                         int* xmax)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int kc = blockIdx.x;
+    const long c = (long)blockIdx.y * 8 + w;
+    if (c >= C) return;
+    const long k0 = (long)kc * KCH;
+    double v[4];
+    unsigned long long key = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const long k = k0 + lane + 32 * j;
+        v[j] = k < K ? X[k + c * ldx] : 0.0;
+        const unsigned long long kj = mag_key(v[j]);
+        key = kj > key ? kj : key;
+    }
+    key = warp_max_u64(key);
+    const int e = EMU ? chunk_exponent_key(key) : 0;
+    if (EMU && lane == 0) {
+        eX[(size_t)kc * C + c] = e;
+        if (e != EXP_NONE) atomicMax(&xmax[c], e);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const long k = k0 + lane + 32 * j;
+        if (k >= K) continue;
+        __nv_bfloat16* dst = planes + c * ldp + k;
+        if (EMU) {
+            float sl[7];
+            if (e == EXP_NONE) {
+#pragma unroll
+                for (int s = 0; s < 7; ++s) sl[s] = 0.f;
+            } else {
+                emu_slices7(v[j], e, sl);
+            }
+#pragma unroll
+            for (int s = 0; s < 7; ++s) dst[s * plane] = __float2bfloat16_rn(sl[s]);
+        } else {
+            __nv_bfloat16 hi, lo;
+            bf16x2_split(v[j], hi, lo);
+            dst[0] = hi;
+            dst[plane] = lo;
+        }
+    }
+}
+
+__global__ void fill_int_kernel(int* p, long n, int v)
+{
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
+}
+
+// ---------------------------------------------------------- work items ----
+struct TcArgs {
+    int rowsA, colsB, K;  // left operand rows, right operand columns, contraction length
+    int tri;              // 1: row tile I stops at k = 128 (I + 1)
+    int ks;               // k-step (elements)
+    int piece;            // k-steps per item
+    int cc;               // column chunks
+    int rt;               // row tiles
+    int nitems;
+    const int* cum;       // rt + 1 item offsets
+    double* slots;        // nitems x 128 x N, row-major per slot
+    const int* eA;        // [K/128][rowsA]
+    const int* eB;        // [K/128][colsB]
+    const int* emaxA;     // [rowsA]
+    const int* emaxB;     // [colsB]
+    DevStatus* st;
+    uint64_t limit_ns;
+};
+
+__device__ __host__ inline int kend_of(const TcArgs& a, int I)
+{
+    if (!a.tri) return a.K;
+    const long e = (long)(I + 1) * TM;
+    return e < a.K ? (int)e : a.K;
+}
+
+__device__ __host__ inline int nks_of(const TcArgs& a, int I) { return (kend_of(a, I) + a.ks - 1) / a.ks; }
+
+__device__ __host__ inline int pieces_of(const TcArgs& a, int I) { return (nks_of(a, I) + a.piece - 1) / a.piece; }
+
+__global__ void item_prefix_kernel(TcArgs a, int* cum)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int s = 0;
+    for (int I = 0; I < a.rt; ++I) {
+        cum[I] = s;
+        s += pieces_of(a, I) * a.cc;
+    }
+    cum[a.rt] = s;
+}
+
+struct Item {
+    int I, ks0, ks1, c;
+};
+
+__device__ inline Item item_of(const TcArgs& a, int j)
+{
+    int lo = 0, hi = a.rt - 1;
+    while (lo < hi) {  // last I with cum[I] <= j
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.cum[mid] <= j) lo = mid;
+        else hi = mid - 1;
+    }
+    Item it;
+    it.I = lo;
+    const int rem = j - a.cum[lo];
+    const int p = rem / a.cc;
+    it.c = rem % a.cc;
+    it.ks0 = p * a.piece;
+    const int n = nks_of(a, lo);
+    it.ks1 = min(n, it.ks0 + a.piece);
+    return it;
+}
+
+// ------------------------------------------------------ tcgen05 helpers ----
+__device__ inline uint64_t smem_desc(uint32_t addr, int swizzle_bytes)
+{
+    const uint64_t sbo = (uint64_t)(8 * swizzle_bytes) >> 4;  // 8 rows x swizzle width
+    const uint64_t layout = swizzle_bytes == 128 ? 2ull : 4ull;  // SWIZZLE_128B : SWIZZLE_64B
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | (1ull << 16) | (sbo << 32) | (1ull << 46) | (layout << 61);
+}
+
+// kind::f16 instruction descriptor: D = F32, A = B = BF16, both K-major, M = 128.
+__host__ __device__ constexpr uint32_t idesc_bf16(int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+}
+
+__device__ inline void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ inline void umma_commit(uint64_t* bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ inline void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ inline void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ inline void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cta.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// 32 consecutive accumulator columns of this thread's TMEM lane.
+__device__ inline void tmem_ld32(uint32_t taddr, float* v)
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ inline float pow2f(int d)
+{
+    if (d < -126) return 0.0f;  // below 2^-126 of the row/column scale: negligible
+    if (d > 127) d = 127;
+    return __int_as_float((d + 127) << 23);
+}
+
+// ---------------------------------------------------------- the kernel ----
+template <int KS, int N, int S, bool EMU>
+struct TcCfg {
+    static constexpr int SW = KS * 2;                  // swizzle width in bytes (row of KS BF16)
+    static constexpr int A_TILE = TM * KS * 2;         // bytes
+    static constexpr int B_TILE = N * KS * 2;
+    static constexpr int STAGE = S * A_TILE + S * B_TILE;
+    static constexpr int STAGES = 2;
+    static constexpr int LEVELS = EMU ? S : 1;
+    static constexpr int TMEM_COLS_USED = LEVELS * N;
+    static constexpr int TMEM_COLS = TMEM_COLS_USED <= 32 ? 32 : TMEM_COLS_USED <= 64 ? 64
+                                   : TMEM_COLS_USED <= 128 ? 128 : TMEM_COLS_USED <= 256 ? 256 : 512;
+    static constexpr int CH_STEPS = EMU ? KCH / KS : 1 << 30;  // k-steps per drained chunk
+    static constexpr size_t SMEM = 1024 + STAGES * (size_t)STAGE + 2048;  // align slack + barriers, exponents
+    static_assert(SW == 64 || SW == 128, "swizzle");
+    static_assert(TMEM_COLS_USED <= 512, "TMEM");
+    static_assert(N % 64 == 0 && N >= 64 && N <= 256, "N");
+    static_assert(A_TILE % 1024 == 0 && B_TILE % 1024 == 0, "tile alignment");
+};
+
+template <int KS, int N, int S, bool EMU>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, TcArgs a)
+{
+    using C = TcCfg<KS, N, S, EMU>;
+    extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
+    unsigned char* smem =
+        reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE);
+    uint64_t* empty = full + C::STAGES;
+    uint64_t* accf = empty + C::STAGES;
+    uint64_t* acce = accf + 1;
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(acce + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);  // colexp follows at +32 ints
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (*(volatile int*)&a.st->code != 0) return;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < C::STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(accf, 1);
+        mbar_init(acce, 1);
+        *abort_flag = 0;
+        fence_barrier_init();
+        tma_prefetch_desc(&mapA);
+        tma_prefetch_desc(&mapB);
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
+                     "r"(C::TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_holder;
+
+    auto fail = [&](int where_info) {
+        if (*abort_flag == 0) {
+            *abort_flag = 1;
+            raise_status(a.st, OQR_ERR_TIMEOUT, where_info, TAG_MIXED);
+        }
+    };
+
+    if (warp == 0) {
+        // ------------------------------------------------ TMA producer
+        if (lane == 0) {
+            long it = 0;
+            for (int j = blockIdx.x; j < a.nitems && !*abort_flag; j += gridDim.x) {
+                const Item item = item_of(a, j);
+                for (int ks = item.ks0; ks < item.ks1 && !*abort_flag; ++ks, ++it) {
+                    const int stg = (int)(it % C::STAGES);
+                    const uint32_t ph = (uint32_t)((it / C::STAGES) & 1);
+                    if (!mbar_wait(&empty[stg], ph ^ 1u, a.limit_ns)) {
+                        fail(1);
+                        break;
+                    }
+                    unsigned char* base = smem + stg * C::STAGE;
+                    mbar_expect_tx(&full[stg], C::STAGE);
+                    for (int s = 0; s < S; ++s)
+                        tma_load_3d(base + s * C::A_TILE, &mapA, &full[stg], ks * KS, item.I * TM, s);
+                    for (int t = 0; t < S; ++t)
+                        tma_load_3d(base + S * C::A_TILE + t * C::B_TILE, &mapB, &full[stg], ks * KS, item.c * N, t);
+                }
+            }
+            // copies still in flight must land before the CTA may exit
+            const long issued = it;
+            for (long q = issued - C::STAGES; q < issued; ++q)
+                if (q >= 0) mbar_wait(&full[q % C::STAGES], (uint32_t)((q / C::STAGES) & 1), a.limit_ns);
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_bf16(N);
+            long it = 0, chunk = 0;
+            for (int j = blockIdx.x; j < a.nitems && !*abort_flag; j += gridDim.x) {
+                const Item item = item_of(a, j);
+                for (int ks = item.ks0; ks < item.ks1 && !*abort_flag; ++ks, ++it) {
+                    const bool chunk_start = EMU ? ((ks - item.ks0) % C::CH_STEPS == 0) : (ks == item.ks0);
+                    const bool chunk_end = EMU ? ((ks - item.ks0 + 1) % C::CH_STEPS == 0 || ks + 1 == item.ks1)
+                                               : (ks + 1 == item.ks1);
+                    if (chunk_start && chunk > 0) {  // the drain must have emptied the accumulators
+                        if (!mbar_wait(acce, (uint32_t)((chunk - 1) & 1), a.limit_ns)) {
+                            fail(2);
+                            break;
+                        }
+                        tc_fence_after();
+                    }
+                    const int stg = (int)(it % C::STAGES);
+                    if (!mbar_wait(&full[stg], (uint32_t)((it / C::STAGES) & 1), a.limit_ns)) {
+                        fail(3);
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t base = smem_u32(smem + stg * C::STAGE);
+                    if (EMU) {
+#pragma unroll 1
+                        for (int s = 0; s < S; ++s)
+#pragma unroll 1
+                            for (int t = 0; s + t < S; ++t) {  // level L = s + t + 2 <= S + 1
+                                const uint32_t d = tmem + (uint32_t)((s + t) * N);
+                                const bool first_of_level = chunk_start && (s == 0);
+#pragma unroll
+                                for (int kk = 0; kk < KS / 16; ++kk) {
+                                    const uint64_t ad = smem_desc(base + s * C::A_TILE + kk * 32, C::SW);
+                                    const uint64_t bd = smem_desc(base + S * C::A_TILE + t * C::B_TILE + kk * 32, C::SW);
+                                    umma_bf16(d, ad, bd, idesc, (first_of_level && kk == 0) ? 0u : 1u);
+                                }
+                            }
+                    } else {
+                        // hi*hi, hi*lo, lo*hi into one accumulator
+                        const int sa[3] = {0, 0, 1}, tb[3] = {0, 1, 0};
+#pragma unroll
+                        for (int p = 0; p < 3; ++p)
+#pragma unroll
+                            for (int kk = 0; kk < KS / 16; ++kk) {
+                                const uint64_t ad = smem_desc(base + sa[p] * C::A_TILE + kk * 32, C::SW);
+                                const uint64_t bd =
+                                    smem_desc(base + S * C::A_TILE + tb[p] * C::B_TILE + kk * 32, C::SW);
+                                umma_bf16(tmem, ad, bd, idesc, (chunk_start && p == 0 && kk == 0) ? 0u : 1u);
+                            }
+                    }
+                    umma_commit(&empty[stg]);
+                    if (chunk_end) {
+                        umma_commit(accf);
+                        ++chunk;
+                    }
+                }
+            }
+            // wait for the last MMAs before TMEM is released
+            if (chunk > 0) mbar_wait(acce, (uint32_t)((chunk - 1) & 1), a.limit_ns);
+        }
+    } else {
+        // ------------------------------------------------ drain (warps 2..9)
+        // One drain thread waits on the accumulator barrier (time-limited) and
+        // publishes the outcome; the 256 drain threads then pass a named
+        // barrier together, so every exit below is taken by all of them.
+        constexpr int NH = N / 2;             // columns owned by this thread
+        const int dt = threadIdx.x - 64;      // 0..255 within the drain group
+        const int q = warp & 3;               // TMEM lane quarter this warp may access
+        const int half = (warp - 2) >> 2;     // which half of the N columns
+        const int r = q * 32 + lane;          // row within the tile = TMEM lane
+        const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(half * NH);
+        int* colexp = const_cast<int*>(abort_flag) + 32;  // N column scale exponents of the current chunk
+        volatile int* go = colexp + 256;                  // outcome of the wait, published by dt == 0
+        long chunk = 0;
+        bool stop = false;
+        for (int j = blockIdx.x; j < a.nitems && !stop; j += gridDim.x) {
+            const Item item = item_of(a, j);
+            const long gi = (long)item.I * TM + r;
+            const bool row_ok = gi < a.rowsA;
+            double* slot = a.slots + (size_t)j * TM * N + (size_t)r * N + half * NH;
+            float H[EMU ? NH : 1], L[EMU ? NH : 1];
+#pragma unroll
+            for (int c = 0; c < (EMU ? NH : 1); ++c) H[c] = L[c] = 0.f;
+            const int emax_r = (EMU && row_ok) ? a.emaxA[gi] : 0;
+            const int nsteps = item.ks1 - item.ks0;
+            const int nch = EMU ? (nsteps + C::CH_STEPS - 1) / C::CH_STEPS : 1;
+            for (int ch = 0; ch < nch; ++ch, ++chunk) {
+                const int kcg = (item.ks0 * KS) / KCH + ch;  // global 128-chunk index
+                if (dt == 0) {
+                    const bool ok = mbar_wait(accf, (uint32_t)(chunk & 1), a.limit_ns);
+                    if (!ok) fail(4);
+                    *go = (ok && !*abort_flag) ? 1 : 0;
+                }
+                if (EMU && dt < N) {
+                    const int col = item.c * N + dt;
+                    int v = EXP_NONE;
+                    if (col < a.colsB) {
+                        const int eb = a.eB[(size_t)kcg * a.colsB + col];
+                        v = eb == EXP_NONE ? EXP_NONE : eb - a.emaxB[col];
+                    }
+                    colexp[dt] = v;
+                }
+                asm volatile("bar.sync 1, 256;" ::: "memory");
+                if (*go == 0) {
+                    stop = true;
+                    break;
+                }
+                tc_fence_after();
+                if (EMU) {
+                    const int e_r = row_ok ? a.eA[(size_t)kcg * a.rowsA + gi] : EXP_NONE;
+                    const int drow = e_r == EXP_NONE ? EXP_NONE : e_r - emax_r;
+#pragma unroll 1
+                    for (int lv = 0; lv < S; ++lv) {
+#pragma unroll
+                        for (int h = 0; h < NH / 32; ++h) {
+                            float v[32];
+                            tmem_ld32(lane_addr + (uint32_t)(lv * N + h * 32), v);
+#pragma unroll
+                            for (int c = 0; c < 32; ++c) {
+                                const int cc = h * 32 + c;
+                                const int dc = colexp[half * NH + cc];
+                                const int d = (drow == EXP_NONE || dc == EXP_NONE) ? -1000 : drow + dc - 14 - 8 * lv;
+                                const float t = __fmul_rn(v[c], pow2f(d));
+                                const float sm = __fadd_rn(H[cc], t);
+                                const float bp = __fsub_rn(sm, H[cc]);
+                                const float err = __fadd_rn(__fsub_rn(H[cc], __fsub_rn(sm, bp)), __fsub_rn(t, bp));
+                                H[cc] = sm;
+                                L[cc] = __fadd_rn(L[cc], err);
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int c = 0; c < NH; ++c) {  // renormalise (Fast2Sum)
+                        const float sm = __fadd_rn(H[c], L[c]);
+                        L[c] = __fsub_rn(L[c], __fsub_rn(sm, H[c]));
+                        H[c] = sm;
+                    }
+                } else {
+#pragma unroll 1
+                    for (int h = 0; h < NH / 32; ++h) {
+                        float v[32];
+                        tmem_ld32(lane_addr + (uint32_t)(h * 32), v);
+#pragma unroll
+                        for (int c = 0; c < 32; ++c) slot[h * 32 + c] = (double)v[c];
+                    }
+                }
+                tc_fence_before();
+                asm volatile("bar.sync 1, 256;" ::: "memory");  // TMEM and colexp fully read
+                if (dt == 0) mbar_arrive(acce);
+            }
+            if (stop) break;
+            if (EMU) {
+#pragma unroll
+                for (int c = 0; c < NH; ++c) {
+                    const int col = item.c * N + half * NH + c;
+                    const int bmax = col < a.colsB ? __ldg(a.emaxB + col) : 0;
+                    slot[c] = ldexp((double)H[c] + (double)L[c], emax_r + bmax);
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TMEM_COLS)
+                     : "memory");
+    }
+}
+
+// out (rowsA x colsB, column-major, ldo) = sum over the pieces of each tile.
+template <int N>
+__global__ void slot_reduce_kernel(TcArgs a, double* out, long ldo, const DevStatus* st)
+{
+    if (*(volatile const int*)&st->code != 0) return;
+    const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long)a.rowsA * a.colsB) return;
+    const int col = (int)(e / a.rowsA), row = (int)(e % a.rowsA);
+    const int I = row / TM, c = col / N;
+    const int np = pieces_of(a, I);
+    double s = 0.0;
+    for (int p = 0; p < np; ++p) {
+        const int j = a.cum[I] + p * a.cc + c;
+        s += a.slots[(size_t)j * TM * N + (size_t)(row % TM) * N + (col % N)];
+    }
+    out[row + (long)col * ldo] = s;
+}
+
+// G = C + C^T (+ shift I), exactly symmetric.
+__global__ void symmetrize_kernel(int n, const double* __restrict__ Cm, long ldc, double* G, long ldg,
+                                  const double* shift_ptr, const DevStatus* st)
+{
+    if (*(volatile const int*)&st->code != 0) return;
+    const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long)n * n) return;
+    const long r = e % n, c = e / n;
+    double v = Cm[r + c * ldc] + Cm[c + r * ldc];
+    if (r == c && shift_ptr) v += *shift_ptr;
+    G[r + c * ldg] = v;
+}
+
+// ------------------------------------------------------------ host side ----
+bool make_map_3d(CUtensorMap* map, const void* base, long kext, long rows, long ldp, size_t plane_bytes, int S,
+                 int box_k, int box_rows);
+
+template <int KS, int N, int S, bool EMU>
+cudaError_t launch_tc(const TcArgs& a0, const void* planesA, long ldpA, size_t planeA, const void* planesB, long ldpB,
+                      size_t planeB, int sms, cudaStream_t s)
+{
+    using C = TcCfg<KS, N, S, EMU>;
+    TcArgs a = a0;
+    CUtensorMap mA{}, mB{};
+    const long krows_a = a.tri ? a.K : a.K;
+    if (!make_map_3d(&mA, planesA, krows_a, a.rowsA, ldpA, planeA * 2, S, KS, TM)) return cudaErrorInvalidValue;
+    if (!make_map_3d(&mB, planesB, a.K, a.colsB, ldpB, planeB * 2, S, KS, N)) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(tc_kernel<KS, N, S, EMU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)C::SMEM);
+    if (e != cudaSuccess) return e;
+    const int grid = a.nitems < sms ? a.nitems : sms;
+    if (grid > 0) tc_kernel<KS, N, S, EMU><<<grid, TC_THREADS, C::SMEM, s>>>(mA, mB, a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// -------------------------------------------------------- public (internal) API
+size_t tc_plan_bytes(const TcPlan& p)
+{
+    return (size_t)p.nitems_max * TM * p.N * sizeof(double);
+}
+
+static TcArgs make_args(const TcPlan& p, int rowsA, int colsB, int K, int tri, int N)
+{
+    TcArgs a{};
+    a.rowsA = rowsA;
+    a.colsB = colsB;
+    a.K = K;
+    a.tri = tri;
+    a.ks = p.emu ? 32 : 64;
+    a.piece = p.emu ? 64 : 32;
+    a.cc = (colsB + N - 1) / N;
+    a.rt = (rowsA + TM - 1) / TM;
+    int s = 0;
+    for (int I = 0; I < a.rt; ++I) s += pieces_of(a, I) * a.cc;
+    a.nitems = s;
+    return a;
+}
+
+TcPlan tc_plan(int m, int n, bool emu)
+{
+    TcPlan p{};
+    p.m = m;
+    p.n = n;
+    p.emu = emu;
+    p.S = emu ? 7 : 2;
+    p.N = emu ? 64 : (n <= 64 ? 64 : n <= 128 ? 128 : 256);
+    p.ldp = ((long)m + 63) / 64 * 64;
+    p.kch = (m + KCH - 1) / KCH;
+    const TcArgs u = make_args(p, m, n, m, 1, p.N);
+    const TcArgs c = make_args(p, n, n, m, 0, p.N);
+    p.nitems_max = u.nitems > c.nitems ? u.nitems : c.nitems;
+    return p;
+}
+
+size_t tc_workspace_bytes(const TcPlan& p)
+{
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    size_t b = 0;
+    b += al((size_t)p.S * p.m * p.ldp * 2);      // A planes (row-major, full m x ldp)
+    b += al((size_t)p.S * p.n * p.ldp * 2);      // Z planes
+    b += al((size_t)p.S * p.n * p.ldp * 2);      // U planes
+    b += al((size_t)p.kch * p.m * 4);            // eA
+    b += al((size_t)p.kch * p.n * 4) * 2;        // eZ, eU
+    b += al((size_t)p.m * 4) + al((size_t)p.n * 4) * 2;  // emaxA, emaxZ, emaxU
+    b += al((size_t)((p.m + TM - 1) / TM + 2) * 4) * 2;  // item prefixes
+    b += al(tc_plan_bytes(p));                   // slots
+    b += al((size_t)p.m * p.n * 8);              // U
+    b += al((size_t)p.n * p.n * 8);              // C
+    return b;
+}
+
+// G = Z^T A Z (+ shift) from A's lower triangle on the tensor cores; see the
+// file comment.  ws holds tc_workspace_bytes(p).
+cudaError_t launch_tc_gram(const TcPlan& p, const double* A, long lda, const double* Z, long ldz, double* G, long ldg,
+                           const double* shift_ptr, void* ws, DevStatus* st, uint64_t limit_ns, int sms,
+                           cudaStream_t s)
+{
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    char* w = static_cast<char*>(ws);
+    const size_t planeA = (size_t)p.m * p.ldp, planeZ = (size_t)p.n * p.ldp;
+    __nv_bfloat16* Ap = reinterpret_cast<__nv_bfloat16*>(w);
+    w += al((size_t)p.S * planeA * 2);
+    __nv_bfloat16* Zp = reinterpret_cast<__nv_bfloat16*>(w);
+    w += al((size_t)p.S * planeZ * 2);
+    __nv_bfloat16* Up = reinterpret_cast<__nv_bfloat16*>(w);
+    w += al((size_t)p.S * planeZ * 2);
+    int* eA = reinterpret_cast<int*>(w);
+    w += al((size_t)p.kch * p.m * 4);
+    int* eZ = reinterpret_cast<int*>(w);
+    w += al((size_t)p.kch * p.n * 4);
+    int* eU = reinterpret_cast<int*>(w);
+    w += al((size_t)p.kch * p.n * 4);
+    int* mA = reinterpret_cast<int*>(w);
+    w += al((size_t)p.m * 4);
+    int* mZ = reinterpret_cast<int*>(w);
+    w += al((size_t)p.n * 4);
+    int* mU = reinterpret_cast<int*>(w);
+    w += al((size_t)p.n * 4);
+    int* cum1 = reinterpret_cast<int*>(w);
+    w += al((size_t)((p.m + TM - 1) / TM + 2) * 4);
+    int* cum2 = reinterpret_cast<int*>(w);
+    w += al((size_t)((p.m + TM - 1) / TM + 2) * 4);
+    double* slots = reinterpret_cast<double*>(w);
+    w += al(tc_plan_bytes(p));
+    double* U = reinterpret_cast<double*>(w);
+    w += al((size_t)p.m * p.n * 8);
+    double* Cm = reinterpret_cast<double*>(w);
+
+    const int S = p.S;
+    const int mm = p.m, nn = p.n;
+    cudaError_t e;
+    if (p.emu) {
+        fill_int_kernel<<<(mm + 255) / 256, 256, 0, s>>>(mA, mm, EXP_NONE);
+        fill_int_kernel<<<(nn + 255) / 256, 256, 0, s>>>(mZ, nn, EXP_NONE);
+        fill_int_kernel<<<(nn + 255) / 256, 256, 0, s>>>(mU, nn, EXP_NONE);
+    }
+    {
+        dim3 g(p.kch, (mm + 31) / 32);
+        if (p.emu) split_lower_kernel<true><<<g, 256, 0, s>>>(mm, A, lda, S, Ap, p.ldp, planeA, eA, mA);
+        else split_lower_kernel<false><<<g, 256, 0, s>>>(mm, A, lda, S, Ap, p.ldp, planeA, eA, mA);
+        dim3 gz(p.kch, (nn + 7) / 8);
+        if (p.emu) split_tall_kernel<true><<<gz, 256, 0, s>>>(mm, nn, Z, ldz, S, Zp, p.ldp, planeZ, eZ, mZ);
+        else split_tall_kernel<false><<<gz, 256, 0, s>>>(mm, nn, Z, ldz, S, Zp, p.ldp, planeZ, eZ, mZ);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // U = M Z (triangular)
+    TcArgs a1 = make_args(p, mm, nn, mm, 1, p.N);
+    a1.cum = cum1;
+    a1.slots = slots;
+    a1.eA = eA;
+    a1.eB = eZ;
+    a1.emaxA = mA;
+    a1.emaxB = mZ;
+    a1.st = st;
+    a1.limit_ns = limit_ns;
+    item_prefix_kernel<<<1, 32, 0, s>>>(a1, cum1);
+    if (p.emu) e = launch_tc<32, 64, 7, true>(a1, Ap, p.ldp, planeA, Zp, p.ldp, planeZ, sms, s);
+    else if (p.N == 64) e = launch_tc<64, 64, 2, false>(a1, Ap, p.ldp, planeA, Zp, p.ldp, planeZ, sms, s);
+    else if (p.N == 128) e = launch_tc<64, 128, 2, false>(a1, Ap, p.ldp, planeA, Zp, p.ldp, planeZ, sms, s);
+    else e = launch_tc<64, 256, 2, false>(a1, Ap, p.ldp, planeA, Zp, p.ldp, planeZ, sms, s);
+    if (e != cudaSuccess) return e;
+    {
+        const long tot = (long)mm * nn;
+        if (p.N == 64) slot_reduce_kernel<64><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(a1, U, mm, st);
+        else if (p.N == 128) slot_reduce_kernel<128><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(a1, U, mm, st);
+        else slot_reduce_kernel<256><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(a1, U, mm, st);
+    }
+    // C = Z^T U (left operand: Z's columns as rows, K-major), then G = C + C^T
+    {
+        dim3 gu(p.kch, (nn + 7) / 8);
+        if (p.emu) split_tall_kernel<true><<<gu, 256, 0, s>>>(mm, nn, U, mm, S, Up, p.ldp, planeZ, eU, mU);
+        else split_tall_kernel<false><<<gu, 256, 0, s>>>(mm, nn, U, mm, S, Up, p.ldp, planeZ, eU, mU);
+    }
+    TcArgs a2 = make_args(p, nn, nn, mm, 0, p.N);
+    a2.cum = cum2;
+    a2.slots = slots;
+    a2.eA = eZ;
+    a2.eB = eU;
+    a2.emaxA = mZ;
+    a2.emaxB = mU;
+    a2.st = st;
+    a2.limit_ns = limit_ns;
+    item_prefix_kernel<<<1, 32, 0, s>>>(a2, cum2);
+    if (p.emu) e = launch_tc<32, 64, 7, true>(a2, Zp, p.ldp, planeZ, Up, p.ldp, planeZ, sms, s);
+    else if (p.N == 64) e = launch_tc<64, 64, 2, false>(a2, Zp, p.ldp, planeZ, Up, p.ldp, planeZ, sms, s);
+    else if (p.N == 128) e = launch_tc<64, 128, 2, false>(a2, Zp, p.ldp, planeZ, Up, p.ldp, planeZ, sms, s);
+    else e = launch_tc<64, 256, 2, false>(a2, Zp, p.ldp, planeZ, Up, p.ldp, planeZ, sms, s);
+    if (e != cudaSuccess) return e;
+    {
+        const long tot = (long)nn * nn;
+        if (p.N == 64) slot_reduce_kernel<64><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(a2, Cm, nn, st);
+        else if (p.N == 128) slot_reduce_kernel<128><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(a2, Cm, nn, st);
+        else slot_reduce_kernel<256><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(a2, Cm, nn, st);
+        symmetrize_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(nn, Cm, nn, G, ldg, shift_ptr, st);
+    }
+    return cudaGetLastError();
+}
+
+namespace {
+typedef CUresult (*EncodeTiledFn3)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn3 encode3()
+{
+    static EncodeTiledFn3 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn3>(p);
+        cudaGetLastError();
+    }
+    return fn;
+}
+
+// Slice planes: dims {K (contiguous), rows, S}; box {box_k, box_rows, 1};
+// swizzle = box_k * 2 bytes (64 or 128), matching the UMMA K-major layout.
+bool make_map_3d(CUtensorMap* map, const void* base, long kext, long rows, long ldp, size_t plane_bytes, int S,
+                 int box_k, int box_rows)
+{
+    EncodeTiledFn3 fn = encode3();
+    if (!fn) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)kext, (cuuint64_t)rows, (cuuint64_t)S};
+    cuuint64_t strides[2] = {(cuuint64_t)ldp * 2, (cuuint64_t)plane_bytes};
+    cuuint32_t box[3] = {(cuuint32_t)box_k, (cuuint32_t)box_rows, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    const CUtensorMapSwizzle sw = box_k * 2 == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+}  // namespace
+
+}  // namespace oqr

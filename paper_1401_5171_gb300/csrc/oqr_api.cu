@@ -35,6 +35,7 @@ void fill_defaults(oqr_opts* o)
     o->block = 64;
     o->check = 0;
     o->spin_limit = 4000000000L;
+    o->final_prec = OQR_FP64;
 }
 
 oqr_opts resolve(const oqr_opts* o)
@@ -176,20 +177,6 @@ oqr_status reset_status(oqr_ctx* ctx, cudaStream_t s)
     return cuda_status(cudaMemsetAsync(ctx->st, 0, sizeof(DevStatus), s));
 }
 
-// One normal-equation pass: G = X^T A X (+ shift), Rp = chol(G), Q = X / Rp.
-cudaError_t run_pass(oqr_ctx* ctx, const GramPlan& gp, const double* A, long lda, const double* X, long ldx,
-                     double* Q, long ldq, double* Rp, long ldrp, double* partials, double* G,
-                     const double* shift_ptr, uint64_t limit, cudaStream_t s)
-{
-    cudaError_t e = launch_gram_f64(gp, A, lda, X, ldx, partials, ctx->st, limit, s);
-    if (e != cudaSuccess) return e;
-    e = launch_gram_reduce(gp, partials, G, gp.n, shift_ptr, ctx->st, s);
-    if (e != cudaSuccess) return e;
-    e = launch_potrf(gp.n, G, gp.n, Rp, ldrp, nullptr, ctx->st, s);
-    if (e != cudaSuccess) return e;
-    return launch_trsm(gp.m, gp.n, X, ldx, Rp, ldrp, Q, ldq, ctx->st, s);
-}
-
 oqr_status run_check(oqr_ctx* ctx, const GramPlan& gp, const double* A, long lda, const double* Q, long ldq,
                      double* partials, double* G, double* work, double* E, long lde, uint64_t limit, cudaStream_t s)
 {
@@ -199,6 +186,30 @@ oqr_status run_check(oqr_ctx* ctx, const GramPlan& gp, const double* A, long lda
     return OQR_OK;
 }
 
+bool prec_ok(int p) { return p == OQR_FP64 || p == OQR_BF16X3 || p == OQR_FP64_TC; }
+
+// G = X^T A X (+ shift) in the requested arithmetic.
+cudaError_t form_gram(oqr_ctx* ctx, int prec, const GramPlan& gp, const double* A, long lda, const double* X,
+                      long ldx, double* partials, double* G, const double* shift_ptr, void* tcws, uint64_t limit,
+                      cudaStream_t s)
+{
+    if (prec == OQR_FP64) {
+        cudaError_t e = launch_gram_f64(gp, A, lda, X, ldx, partials, ctx->st, limit, s);
+        if (e != cudaSuccess) return e;
+        return launch_gram_reduce(gp, partials, G, gp.n, shift_ptr, ctx->st, s);
+    }
+    const TcPlan tp = tc_plan(gp.m, gp.n, prec == OQR_FP64_TC);
+    return launch_tc_gram(tp, A, lda, X, ldx, G, gp.n, shift_ptr, tcws, ctx->st, limit, ctx->sm_count, s);
+}
+
+size_t tc_bytes_for(int m, int n, int prec_a, int prec_b)
+{
+    size_t b = 0;
+    if (prec_a == OQR_BF16X3 || prec_b == OQR_BF16X3) b = std::max(b, tc_workspace_bytes(tc_plan(m, n, false)));
+    if (prec_a == OQR_FP64_TC || prec_b == OQR_FP64_TC) b = std::max(b, tc_workspace_bytes(tc_plan(m, n, true)));
+    return b;
+}
+
 oqr_status normal_equation(oqr_ctx* ctx, int m, int n, const double* A, long lda, const double* Z, long ldz,
                            double* Q, long ldq, double* R, long ldr, const oqr_opts* opts_in, oqr_info* info,
                            void* stream, int forced_passes)
@@ -206,24 +217,32 @@ oqr_status normal_equation(oqr_ctx* ctx, int m, int n, const double* A, long lda
     oqr_status v = check_common(ctx, m, n, A, lda, Z, ldz, Q, ldq, R, ldr);
     if (v != OQR_OK) return v;
     const oqr_opts o = resolve(opts_in);
-    if (o.prec != OQR_FP64) return OQR_ERR_UNSUPPORTED;
+    if (o.prec == OQR_FP8 || o.final_prec == OQR_FP8) return OQR_ERR_UNSUPPORTED;
+    if (!prec_ok(o.prec) || !prec_ok(o.final_prec)) return OQR_ERR_INVALID_ARG;
     int passes = forced_passes > 0 ? forced_passes : (o.shifted ? 3 : o.passes);
     if (passes > 8) return OQR_ERR_INVALID_ARG;
     const bool shifted = forced_passes == 0 && o.shifted;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const uint64_t limit = (uint64_t)o.spin_limit;
     const GramPlan gp = gram_plan(m, n, ctx->sm_count);
+    const int prec_first = passes > 1 ? o.prec : o.final_prec;
     Carve probe(nullptr);
     double *partials, *G, *work, *R1, *R2, *R3, *scratch;
     layout_cholqr(probe, gp, &partials, &G, &work, &R1, &R2, &R3, &scratch);
+    const size_t tcb = tc_bytes_for(m, n, prec_first, o.final_prec);
+    char* tcws_probe = probe.take<char>(tcb);
+    (void)tcws_probe;
     if ((v = ensure_ws(ctx, probe.off)) != OQR_OK) return v;
     Carve c(ctx->ws);
     layout_cholqr(c, gp, &partials, &G, &work, &R1, &R2, &R3, &scratch);
+    void* tcws = c.take<char>(tcb);
     if ((v = reset_status(ctx, s)) != OQR_OK) return v;
 
     const double* shift_ptr = nullptr;
     if (shifted) {
-        OQR_TRY(launch_norms_and_shift(m, n, A, lda, Z, ldz, o.shift_c, U64, scratch, 2 * SHIFT_PARTS, ctx->st, s));
+        // the shift follows the unit roundoff of the first pass's arithmetic
+        const double u = o.prec == OQR_BF16X3 ? 3.0517578125e-05 /* 2^-15 */ : U64;
+        OQR_TRY(launch_norms_and_shift(m, n, A, lda, Z, ldz, o.shift_c, u, scratch, 2 * SHIFT_PARTS, ctx->st, s));
         shift_ptr = &ctx->st->shift;
     }
     // R accumulates as R_p ... R_1; Racc alternates between R2 and R3.
@@ -233,8 +252,10 @@ oqr_status normal_equation(oqr_ctx* ctx, int m, int n, const double* A, long lda
     for (int p = 0; p < passes; ++p) {
         double* Rp = (passes == 1) ? R : R1;
         const long ldrp = (passes == 1) ? ldr : n;
-        OQR_TRY(run_pass(ctx, gp, A, lda, X, ldx, Q, ldq, Rp, ldrp, partials, G, p == 0 ? shift_ptr : nullptr,
-                         limit, s));
+        const int prec = (p == passes - 1) ? o.final_prec : o.prec;
+        OQR_TRY(form_gram(ctx, prec, gp, A, lda, X, ldx, partials, G, p == 0 ? shift_ptr : nullptr, tcws, limit, s));
+        OQR_TRY(launch_potrf(n, G, n, Rp, ldrp, nullptr, ctx->st, s));
+        OQR_TRY(launch_trsm(m, n, X, ldx, Rp, ldrp, Q, ldq, ctx->st, s));
         if (passes > 1) {
             if (p == 0) {
                 OQR_TRY(launch_copy_upper(n, R1, n, R2, n, s));
@@ -447,14 +468,28 @@ oqr_status oqr_gram(oqr_ctx* ctx, int m, int n, const double* A, long lda, const
     if (!ctx || m < 1 || n < 1 || n > m || bad_matrix(A, lda, m, m) || bad_matrix(Z, ldz, m, n) ||
         bad_matrix(G, ldg, n, n))
         return OQR_ERR_INVALID_ARG;
-    if (prec != OQR_FP64) return OQR_ERR_UNSUPPORTED;
+    if (prec == OQR_FP8) return OQR_ERR_UNSUPPORTED;
+    if (!prec_ok(prec)) return OQR_ERR_INVALID_ARG;
+    if (n > 1024) return OQR_ERR_UNSUPPORTED;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const GramPlan gp = gram_plan(m, n, ctx->sm_count);
-    oqr_status v = ensure_ws(ctx, align256(gram_partials_bytes(gp)));
+    if (prec == OQR_FP64) {
+        oqr_status v = ensure_ws(ctx, align256(gram_partials_bytes(gp)));
+        if (v != OQR_OK) return v;
+        if ((v = reset_status(ctx, s)) != OQR_OK) return v;
+        OQR_TRY(launch_gram_f64(gp, A, lda, Z, ldz, static_cast<double*>(ctx->ws), ctx->st, 4000000000ull, s));
+        OQR_TRY(launch_gram_reduce(gp, static_cast<double*>(ctx->ws), G, ldg, nullptr, ctx->st, s));
+        return OQR_OK;
+    }
+    const TcPlan tp = tc_plan(m, n, prec == OQR_FP64_TC);
+    oqr_status v = ensure_ws(ctx, align256(tc_workspace_bytes(tp)) + align256((size_t)n * n * 8));
     if (v != OQR_OK) return v;
     if ((v = reset_status(ctx, s)) != OQR_OK) return v;
-    OQR_TRY(launch_gram_f64(gp, A, lda, Z, ldz, static_cast<double*>(ctx->ws), ctx->st, 4000000000ull, s));
-    OQR_TRY(launch_gram_reduce(gp, static_cast<double*>(ctx->ws), G, ldg, nullptr, ctx->st, s));
+    // the tensor-core path writes G with leading dimension n into the workspace tail, then copies out
+    double* Gt = reinterpret_cast<double*>(static_cast<char*>(ctx->ws) + align256(tc_workspace_bytes(tp)));
+    OQR_TRY(launch_tc_gram(tp, A, lda, Z, ldz, Gt, n, nullptr, ctx->ws, ctx->st, 4000000000ull, ctx->sm_count, s));
+    OQR_TRY(cudaMemcpy2DAsync(G, ldg * sizeof(double), Gt, n * sizeof(double), n * sizeof(double), n,
+                              cudaMemcpyDeviceToDevice, s));
     return OQR_OK;
 }
 

@@ -175,6 +175,25 @@ cudaError_t launch_gemm_f64(GemmOp op, int M, int N, int K, double alpha, const 
                             const double* B, long ldb, double beta, double* C, long ldc, double* splitk_ws,
                             int splits, cudaStream_t s);
 
+// Tensor-core normal-equation matrix (k_tc.cu): G = Z^T A Z from BF16 slices.
+// emu = false: BF16X3 (hi/lo, 3 products, FP32 accumulation);
+// emu = true : FP64-accurate (7 exact slices per operand, 28 products).
+struct TcPlan {
+    int m, n;
+    bool emu;
+    int S;          // slices per operand
+    int N;          // UMMA N (column chunk)
+    long ldp;       // leading dimension of the slice planes
+    int kch;        // 128-long chunks of the contraction
+    int nitems_max; // work items of the larger of the two products
+};
+TcPlan tc_plan(int m, int n, bool emu);
+size_t tc_plan_bytes(const TcPlan& p);
+size_t tc_workspace_bytes(const TcPlan& p);
+cudaError_t launch_tc_gram(const TcPlan& p, const double* A, long lda, const double* Z, long ldz, double* G, long ldg,
+                           const double* shift_ptr, void* ws, DevStatus* st, uint64_t limit_ns, int sms,
+                           cudaStream_t s);
+
 // Y = alpha X + beta Y (M x N, column-major).
 cudaError_t launch_axpby(int M, int N, double alpha, const double* X, long ldx, double beta, double* Y, long ldy,
                          cudaStream_t s);

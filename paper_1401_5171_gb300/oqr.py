@@ -20,14 +20,14 @@ HEADERS = [os.path.join(os.path.dirname(HERE), "include", "oqr.h")]
 
 OQR_OK, OQR_ERR_INVALID_ARG, OQR_ERR_NOT_SPD, OQR_ERR_CHECK_FAILED = 0, 1, 2, 3
 OQR_ERR_CUDA, OQR_ERR_NO_MEMORY, OQR_ERR_TIMEOUT, OQR_ERR_UNSUPPORTED = 4, 5, 6, 7
-OQR_FP64, OQR_BF16X3, OQR_FP8 = 0, 1, 2
+OQR_FP64, OQR_BF16X3, OQR_FP8, OQR_FP64_TC = 0, 1, 2, 3
 OQR_ALGO_CHOLQR, OQR_ALGO_CHOLQR2, OQR_ALGO_SCHOLQR3, OQR_ALGO_CGS2 = 0, 1, 2, 3
 
 
 class oqr_opts(ctypes.Structure):
     _fields_ = [("passes", ctypes.c_int), ("shifted", ctypes.c_int), ("prec", ctypes.c_int),
                 ("shift_c", ctypes.c_double), ("block", ctypes.c_int), ("check", ctypes.c_int),
-                ("spin_limit", ctypes.c_long)]
+                ("spin_limit", ctypes.c_long), ("final_prec", ctypes.c_int)]
 
 
 class oqr_info(ctypes.Structure):
