@@ -4,7 +4,10 @@
 One step = one oblique QR factorization (Z = Q R, Q^T A Q = I) of the
 single large instance m=32768, n=256 with kappa(A)=1e6 and kappa(Z)=1e2
 (dense SPD A, lower triangle read), through the library's C ABI.  The
-default path is A-CholQR2 in FP64.  Inputs are synthetic (the Sec. 7
+headline path is the mixed A-CholQR2 (a BF16X3 pass, then an FP64-accurate
+pass, both on the tensor cores); the FP64 (DFMA) and the all-FP64-accurate
+tensor-core paths are timed beside it.  Each path's ||Q^T A Q - I||_2 is
+measured on the timed configuration.  Inputs are synthetic (the Sec. 7
 recipe; A is 8.6 GB, larger than L2, so no flush is needed between steps).
 
 Prints one JSON line (rank 0).  Under torchrun every rank factors its own
@@ -41,7 +44,8 @@ def parse():
     p.add_argument("--n", type=int, default=256)
     p.add_argument("--kappa-a", type=float, default=1e6)
     p.add_argument("--kappa-z", type=float, default=1e2)
-    p.add_argument("--algo", default="cholqr2", choices=["cholqr", "cholqr2", "scholqr3", "cgs2"])
+    p.add_argument("--path", default="mixed", choices=["mixed", "fp64tc", "fp64", "scholqr3", "cgs2"])
+    p.add_argument("--no-side-paths", action="store_true", help="time only the headline path")
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
@@ -215,11 +219,50 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+PATHS = {
+    # name: (entry point, options, normal-equation passes, description)
+    "mixed": ("oqr_cholqr2", {"prec": 1, "final_prec": 3}, 2,
+              "A-CholQR2: BF16X3 pass, then FP64-accurate pass, both on tcgen05 tensor cores"),
+    "fp64tc": ("oqr_cholqr2", {"prec": 3, "final_prec": 3}, 2,
+               "A-CholQR2: two FP64-accurate tensor-core passes"),
+    "fp64": ("oqr_cholqr2", {}, 2, "A-CholQR2: two FP64 DFMA passes"),
+    "scholqr3": ("oqr_cholqr2", {"shifted": 1}, 3, "shifted A-CholQR3, FP64 DFMA"),
+    "cgs2": ("oqr_cgs2", {}, 2, "block A-CGS2, FP64 DFMA"),
+}
+
+
+def launches_per_step(path):
+    """Kernels the library launches for one factorization (counted from oqr_api.cu / k_tc.cu)."""
+    name, kw, passes, _ = PATHS[path]
+    if name == "oqr_cgs2":
+        return None
+    per_pass = []
+    for p in range(passes):
+        prec = kw.get("final_prec", 0) if p == passes - 1 else kw.get("prec", 0)
+        gram = 2 if prec == 0 else (9 + (3 if prec == 3 else 0))
+        per_pass.append(gram + 2)  # + potrf + trsm
+    extra = passes if passes > 1 else 0          # R copy + (passes - 1) products
+    if kw.get("shifted"):
+        extra += 2                               # norms + shift
+    return sum(per_pass) + extra
+
+
+def tc_u_flops(m, n):
+    """Tensor-core flops of the FP64-accurate U = M Z product as executed: 28 slice
+    products (levels 2..8 of 7 slices) over the 128-row tiles of the lower triangle,
+    each row tile I contracting over k < 128 (I + 1), n padded to the 64-column chunks."""
+    npad = -(-n // 64) * 64
+    rt = -(-m // 128)
+    ksum = sum(min(128 * (i + 1), m) for i in range(rt))
+    return 2.0 * 28 * 128 * npad * ksum
+
+
 def config_of(args):
     return {"workload": f"single dense oblique QR m={args.m} n={args.n} kappa(A)={args.kappa_a:g} "
                         f"kappa(Z)={args.kappa_z:g}, random U (Sec. 7 case 4 recipe)",
-            "m": args.m, "n": args.n, "kappa_A": args.kappa_a, "kappa_Z": args.kappa_z, "algo": args.algo,
-            "precision": "fp64", "l2": "inputs larger than L2 (A alone is 8.6 GB), no flush"}
+            "m": args.m, "n": args.n, "kappa_A": args.kappa_a, "kappa_Z": args.kappa_z, "path": args.path,
+            "path_desc": PATHS[args.path][3],
+            "l2": "inputs larger than L2 (A alone is 8.6 GB), no flush"}
 
 
 def main():
@@ -249,80 +292,108 @@ def main():
     Q = oqr.empty_colmajor(m, n, dev)
     R = oqr.empty_colmajor(n, n, dev)
     ctx = oqr.Oqr(local)
-    algo = {"cholqr": ("oqr_cholqr", {}, 1), "cholqr2": ("oqr_cholqr2", {}, 2),
-            "scholqr3": ("oqr_cholqr2", {"shifted": 1}, 3), "cgs2": ("oqr_cgs2", {}, 2)}[args.algo]
-    name, kw, passes = algo
-    opts = oqr.make_opts(**kw)
     stream = torch.cuda.current_stream(dev)
 
-    def step(sync=False):
-        ctx._qr(name, A, Z, Q=Q, R=R, opts=opts, stream=stream, sync=sync)
-
-    # correctness of what is timed: orthogonality measured once, outside the timing
-    Qc, Rc, (st, info) = ctx._qr(name, A, Z, Q=Q, R=R, opts=oqr.make_opts(check=1, **kw), stream=stream)
-    orth = info.orth_err
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with Clocks(local) as clk:
+    def run(path, steps, warmup):
+        name, kw, passes, _ = PATHS[path]
+        opts = oqr.make_opts(**kw)
+        # orthogonality of exactly what is timed, measured once outside the timing
+        _, _, (st, info) = ctx._qr(name, A, Z, Q=Q, R=R, opts=oqr.make_opts(check=1, **kw), stream=stream)
+        for _ in range(warmup):
+            ctx._qr(name, A, Z, Q=Q, R=R, opts=opts, stream=stream, sync=False)
         torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(args.steps):
-            step()
+        for _ in range(steps):
+            ctx._qr(name, A, Z, Q=Q, R=R, opts=opts, stream=stream, sync=False)
         e1.record(stream)
         torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = t.item()
-        dist.barrier()
-    ms_per_step = ms / args.steps
-    value = world * args.steps / (ms / 1e3)
-    tflops = world * normalised_flops(m, n, passes) * args.steps / (ms / 1e3) / 1e12
+        ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = t.item()
+            dist.barrier()
+        return {"qr_per_s": world * steps / (ms / 1e3), "ms_per_qr": ms / steps,
+                "tflops_normalised": world * normalised_flops(m, n, passes) * steps / (ms / 1e3) / 1e12,
+                "orth_err": info.orth_err, "status": st, "steps": steps}
 
-    # dominant kernel: the fused Gram, timed alone on the same stream
-    G = oqr.empty_colmajor(n, n, dev)
-    for _ in range(2):
-        ctx.oqr_gram(A, Z, G=G, stream=stream)
-    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    reps = max(2, min(args.steps, 5))
-    g0.record(stream)
-    for _ in range(reps):
-        ctx.oqr_gram(A, Z, G=G, stream=stream)
-    g1.record(stream)
-    torch.cuda.synchronize()
-    gram_s = g0.elapsed_time(g1) / reps / 1e3
+    with Clocks(local) as clk:
+        head = run(args.path, args.steps, args.warmup)
     clocks = clk.summary()
-    peak = SMS * FP64_FLOPS_PER_CLK_SM * ((clocks or {}).get("sm_max_mhz") or 2070.0) * 1e6 / 1e12
-    achieved = gram_algorithmic_flops(m, n) / gram_s / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": ncu_traffic("gram_f64_m32768_n256",
-                                       ["paper_1401_5171_gb300/csrc/k_gram_f64.cu"]) if (m, n) == (32768, 256) else None,
-                "kernel": "gram_f64_kernel (fused symmetric Z^T A Z, FP64 DFMA)",
-                "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x max SM clock (DFMA unit count)"}
+    others = {}
+    if not args.no_side_paths:
+        for p in ("fp64", "fp64tc", "mixed"):
+            if p != args.path:
+                others[p] = run(p, 2, 1)
 
-    # end to end: host buffers in pinned memory, copies inside the timed region
+    # dominant kernel of the headline path, timed alone with CUDA events on the same stream
+    G = oqr.empty_colmajor(n, n, dev)
+    roofline = None
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    if args.path in ("mixed", "fp64tc"):
+        reps = 3
+        ctx.oqr_gram_phases(A, Z, 3, G=G, stream=stream)
+        u_ms = []
+        for _ in range(reps):
+            ph, _ = ctx.oqr_gram_phases(A, Z, 3, G=G, stream=stream)
+            u_ms.append(ph[1])
+        t = sum(u_ms) / len(u_ms) / 1e3
+        achieved = tc_u_flops(m, n) / t / 1e12
+        peak = float(peaks.get("bf16_tflops", 1899.1))
+        roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak,
+                    "traffic": ncu_traffic("tc_emu_u_m32768_n256", ["paper_1401_5171_gb300/csrc/k_tc.cu"])
+                    if (m, n) == (32768, 256) else None,
+                    "kernel": "tc_kernel<32,64,7,EMU> (U = M Z, 28 BF16 slice products, tcgen05 kind::f16)",
+                    "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst; kernel timed alone), of measured",
+                    "launch_ms": t * 1e3, "phases_ms": ph}
+    else:
+        ph, _ = ctx.oqr_gram_phases(A, Z, 0, G=G, stream=stream)
+        ph, _ = ctx.oqr_gram_phases(A, Z, 0, G=G, stream=stream)
+        t = ph[0] / 1e3
+        peak = SMS * FP64_FLOPS_PER_CLK_SM * ((clocks or {}).get("sm_max_mhz") or 2070.0) * 1e6 / 1e12
+        achieved = gram_algorithmic_flops(m, n) / t / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "traffic": ncu_traffic("gram_f64_m32768_n256", ["paper_1401_5171_gb300/csrc/k_gram_f64.cu"])
+                    if (m, n) == (32768, 256) else None,
+                    "kernel": "gram_f64_kernel (fused symmetric Z^T A Z, FP64 DFMA)",
+                    "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x max SM clock (DFMA unit count)",
+                    "launch_ms": t * 1e3}
+
+    # end to end through the C ABI: host buffers in pinned memory, copies inside the timed region
     e2e = None
     if args.e2e_steps > 0:
-        Ah = torch.empty((m, m), dtype=torch.float64, pin_memory=True).t()
-        Ah.copy_(A)
-        Zh = torch.empty((n, m), dtype=torch.float64, pin_memory=True).t()
-        Zh.copy_(Z)
-        Qh = torch.empty((n, m), dtype=torch.float64, pin_memory=True).t()
-        Rh = torch.empty((n, n), dtype=torch.float64, pin_memory=True).t()
-        Ad2 = oqr.empty_colmajor(m, m, dev)
-        Zd2 = oqr.empty_colmajor(m, n, dev)
+        name, kw, passes, _ = PATHS[args.path]
+        opts = oqr.make_opts(**kw)
+        # flat pinned host buffers and flat device buffers: one contiguous copy each way
+        Ah = torch.empty(m * m, dtype=torch.float64, pin_memory=True)
+        Ah.copy_(A.t().reshape(-1))
+        Zh = torch.empty(m * n, dtype=torch.float64, pin_memory=True)
+        Zh.copy_(Z.t().reshape(-1))
+        Qh = torch.empty(m * n, dtype=torch.float64, pin_memory=True)
+        Rh = torch.empty(n * n, dtype=torch.float64, pin_memory=True)
+        Ad_flat = torch.empty(m * m, dtype=torch.float64, device=dev)
+        Zd_flat = torch.empty(m * n, dtype=torch.float64, device=dev)
+        Qd_flat = torch.empty(m * n, dtype=torch.float64, device=dev)
+        Rd_flat = torch.empty(n * n, dtype=torch.float64, device=dev)
+        Ad2 = Ad_flat.view(m, m).t()       # column-major views of the flat buffers
+        Zd2 = Zd_flat.view(n, m).t()
+        Qd2 = Qd_flat.view(n, m).t()
+        Rd2 = Rd_flat.view(n, n).t()
 
         def e2e_step():
-            Ad2.copy_(Ah, non_blocking=True)
-            Zd2.copy_(Zh, non_blocking=True)
-            ctx._qr(name, Ad2, Zd2, Q=Q, R=R, opts=opts, stream=stream, sync=False)
-            Qh.copy_(Q, non_blocking=True)
-            Rh.copy_(R, non_blocking=True)
+            Ad_flat.copy_(Ah, non_blocking=True)
+            Zd_flat.copy_(Zh, non_blocking=True)
+            ctx._qr(name, Ad2, Zd2, Q=Qd2, R=Rd2, opts=opts, stream=stream, sync=False)
+            Qh.copy_(Qd_flat, non_blocking=True)
+            Rh.copy_(Rd_flat, non_blocking=True)
 
         e2e_step()
         torch.cuda.synchronize()
@@ -339,7 +410,7 @@ def main():
             ems = t.item()
         e2e = {"value": world * args.e2e_steps / (ems / 1e3), "unit": "QR/s",
                "h2d_bytes_per_step": 8 * (m * m + m * n), "d2h_bytes_per_step": 8 * (m * n + n * n)}
-        del Ah, Ad2
+        del Ah, Ad_flat
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -349,16 +420,14 @@ def main():
                "sample": f"oracle CHOL-EQR once on m={msamp}, n={nsamp} (same recipe, {secs:.1f} s); QRs/s "
                          f"scaled to m={m}, n={n} by its flop model m^3/3 + 2 m^2 n + 2 m n^2"}
 
-    # per pass: gram, gram-reduce, potrf, trsm; plus one R copy and (passes-1) R products,
-    # plus the two norm/shift kernels of the shifted pass
-    launches = args.steps * (passes * 4 + (passes if passes > 1 else 0) + (2 if args.algo == "scholqr3" else 0))
-    if args.algo == "cgs2":
-        launches = None
-    line = {"metric": METRIC, "value": value, "unit": "QR/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+    lps = launches_per_step(args.path)
+    line = {"metric": METRIC, "value": head["qr_per_s"], "unit": "QR/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": head["ms_per_qr"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_of(args),
-            "tflops_normalised": tflops, "orth_err": orth, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": launches, "clocks": clocks}
+            "tflops_normalised": head["tflops_normalised"], "orth_err": head["orth_err"],
+            "meets_1e-12": bool(0 <= head["orth_err"] <= 1e-12), "paths": others,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": lps * args.steps if lps is not None else None, "clocks": clocks}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

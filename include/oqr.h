@@ -70,6 +70,7 @@ typedef struct {
     int check;        /* 1 = measure ||Q^T A Q - I||_2 after the factorization into info->orth_err [0] */
     long spin_limit;  /* time limit of any device-side wait, in nanoseconds [4e9] */
     int final_prec;   /* oqr_cholqr2: oqr_precision of the last pass [OQR_FP64]; OQR_FP64 or OQR_FP64_TC */
+    int prec_mid;     /* passes between the first and the last: oqr_precision, or -1 = same as prec [-1] */
 } oqr_opts;
 
 /* Optional per-call report (filled only when passed non-NULL). */
@@ -135,7 +136,11 @@ oqr_status oqr_cholqr(oqr_ctx* ctx, int m, int n, const double* A, long lda, con
  * the shift, the triangular solves and R = R_2 R_1 are always FP64.  The
  * mixed form (prec = OQR_BF16X3, final_prec = OQR_FP64_TC) runs all products
  * on the tensor cores; its accuracy comes from the last pass, whose
- * normal-equation matrix is FP64-accurate.
+ * normal-equation matrix is FP64-accurate.  The shift of a shifted first pass
+ * is c u (m n + n (n+1)) ||A||_F ||Z||_F^2 (u = 2^-53) when that pass is FP64
+ * or FP64_TC, and c u trace(G) (u = 2^-16, G the pass's BF16X3 matrix) when
+ * it is BF16X3, whose rounding error scales with G rather than with the
+ * worst-case bound.
  */
 oqr_status oqr_cholqr2(oqr_ctx* ctx, int m, int n, const double* A, long lda, const double* Z, long ldz,
                        double* Q, long ldq, double* R, long ldr, const oqr_opts* opts, oqr_info* info,
@@ -179,6 +184,71 @@ oqr_status oqr_rprod(oqr_ctx* ctx, int n, const double* U, long ldu, const doubl
                      long ldr, void* stream);
 oqr_status oqr_check(oqr_ctx* ctx, int m, int n, const double* A, long lda, const double* Q, long ldq,
                      double* E, long lde, double* orth2, double* orthF, void* stream);
+
+/*
+ * Batched A-CholQR2 (FP64): `count` independent oblique QRs, instance b with
+ * A_b (m[b] x m[b], lower triangle read), Z_b (m[b] x n[b]) -> Q_b, R_b, all
+ * column-major FP64 device memory, 1 <= n[b] <= min(m[b], 64), m[b] <= 4096.
+ * Each instance is Algorithm 1 applied twice (CHOLQR, Sec. 2; R = R_2 R_1).
+ * m, n, the pointer arrays and the leading-dimension arrays are HOST arrays
+ * (the pointers in them are device pointers).  status is a DEVICE array of
+ * count ints: 0 for success, else the 1-based column at which instance b's
+ * Cholesky broke down (its Q_b, R_b are then undefined; the other instances
+ * are unaffected).  splits (host, may be NULL) is the work plan: the number of
+ * k-ranges each instance's Gram is cut into (1..64), as chosen by an autotuner;
+ * NULL uses the built-in heuristic.  mode must be 0 (FP64 A-CholQR2).
+ * The batch-wide kernel sequence (about 13 launches) is captured into one
+ * CUDA graph that the context caches and replays while the batch's shape
+ * signature is unchanged; on the legacy default stream it is launched directly.
+ * Asynchronous: returns after enqueueing (argument errors are returned).
+ */
+oqr_status oqr_batched(oqr_ctx* ctx, int count, const int* m, const int* n, const double* const* A, const long* lda,
+                       const double* const* Z, const long* ldz, double* const* Q, const long* ldq, double* const* R,
+                       const long* ldr, int mode, const int* splits, int* status, void* stream);
+
+/* The built-in work plan of oqr_batched for one instance (splits of its Gram). */
+int oqr_batched_default_splits(int m, int n);
+
+/*
+ * Selector (no counterpart in the paper: it chooses, per instance, the passes
+ * and precisions of the normal-equation method).
+ *
+ * oqr_features: 16 floats (device, feat) describing one instance, read from its
+ *   BF16X3 normal-equation matrix and the norms of A and Z (Gram diagonal
+ *   spread, coherence, pivots of the diagonally scaled Cholesky and its
+ *   breakdown column, sizes).  n <= 1024.
+ * oqr_mlp_forward: logits (device, B x 4, may be NULL) and argmax choice
+ *   (device, B ints, may be NULL) of the MLP 16 -> 64 -> 64 -> 4 (ReLU) for
+ *   B feature rows X (device, B x 16, row-major); params (device) is the flat
+ *   FP32 array of oqr_mlp_param_count() floats: W1[64][16], b1[64],
+ *   W2[64][64], b2[64], W3[4][64], b3[4].  bf16 = 1 rounds weights and
+ *   activations to BF16 (FP32 accumulation).
+ * oqr_mlp_grad: the gradient (device, param_count floats) of the mean softmax
+ *   cross-entropy over the B rows with integer labels y (device) and, if loss
+ *   is non-NULL, the loss (device, 1 float).  Deterministic (fixed summation
+ *   order).  Scratch comes from the context's workspace.
+ * oqr_mlp_adam: one Adam step on params with moments m, v (device), step t >= 1.
+ */
+oqr_status oqr_features(oqr_ctx* ctx, int m, int n, const double* A, long lda, const double* Z, long ldz, float* feat,
+                        void* stream);
+int oqr_mlp_param_count(void);
+oqr_status oqr_mlp_forward(oqr_ctx* ctx, int B, const float* X, const float* params, int bf16, float* logits,
+                           int* choice, void* stream);
+oqr_status oqr_mlp_grad(oqr_ctx* ctx, int B, const float* X, const int* y, const float* params, float* grad,
+                        float* loss, void* stream);
+oqr_status oqr_mlp_adam(oqr_ctx* ctx, float* params, const float* grad, float* m, float* v, float lr, float beta1,
+                        float beta2, float eps, int t, void* stream);
+
+/*
+ * Measurement helper (no counterpart in the paper): runs oqr_gram's pipeline
+ * for prec and returns the CUDA-event duration of each phase on `stream`, in
+ * milliseconds, in phase_ms[0..*nphase).  OQR_FP64: {Gram kernel, reduction}.
+ * OQR_BF16X3 / OQR_FP64_TC: {split of A and Z, U = M Z product, its reduction
+ * and the split of U, C = Z^T U product, its reduction and G = C + C^T}.
+ * phase_ms holds at least 6 floats.  Synchronizes the stream.
+ */
+oqr_status oqr_gram_phases(oqr_ctx* ctx, int m, int n, const double* A, long lda, const double* Z, long ldz,
+                           double* G, long ldg, int prec, float* phase_ms, int* nphase, void* stream);
 
 /*
  * oqr_gram_noalloc: the same G = Z^T A Z as oqr_gram (FP64), for callers that

@@ -12,90 +12,121 @@ namespace {
 
 // ------------------------------------------------------------- Cholesky ----
 // R = chol(G + shift I), upper, G read from its lower triangle
-// (Algorithm 1, line 3).  One CTA, right-looking, 32-column panels: the
-// panel's diagonal block is factored by one warp in shared memory, the panel
-// row is solved against it, and the trailing upper triangle is updated by
-// all threads.  A pivot that is not positive (or NaN) stops the
-// factorization and records OQR_ERR_NOT_SPD with the 1-based column.
-constexpr int POTRF_THREADS = 512;
+// (Algorithm 1, line 3).  Right-looking, 32-column panels, one SM's FP64 rate
+// being far too low for n^3/3 flops on a single CTA: per panel
+//   potrf_diag  (1 CTA)   factor the 32 x 32 diagonal block in shared memory;
+//   potrf_row   (n/32 CTAs) solve the panel row R(p, c) <- D^{-T} R(p, c);
+//   potrf_trail (tiles)   R(r, c) -= sum_k R(p_k, r) R(p_k, c) on the trailing
+//                         upper triangle, 32 x 32 tiles.
+// A pivot that is not positive (or NaN) stops the factorization: the status
+// word records OQR_ERR_NOT_SPD with the 1-based column and every later launch
+// returns at once.
 constexpr int PNB = 32;
 
-__global__ void __launch_bounds__(POTRF_THREADS) potrf_kernel(int n, const double* __restrict__ G, long ldg, double* R,
-                                                              long ldr, const double* shift_ptr, DevStatus* st)
+__global__ void potrf_init_kernel(int n, const double* __restrict__ G, long ldg, double* R, long ldr,
+                                  const double* shift_ptr, const DevStatus* st)
+{
+    if (*(volatile const int*)&st->code != 0) return;
+    const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long)n * n) return;
+    const long i = e % n, j = e / n;
+    double v = 0.0;
+    if (i <= j) {
+        v = G[j + i * ldg];
+        if (i == j && shift_ptr) v += *shift_ptr;
+    }
+    R[i + j * ldr] = v;
+}
+
+__global__ void __launch_bounds__(32) potrf_diag_kernel(int n, int jb, double* R, long ldr, DevStatus* st)
 {
     __shared__ double D[PNB][PNB + 1];
-    __shared__ int broke;
     if (*(volatile int*)&st->code != 0) return;
-    const int tid = threadIdx.x;
-    const double shift = shift_ptr ? *shift_ptr : 0.0;
-    for (long e = tid; e < (long)n * n; e += POTRF_THREADS) {
-        const long i = e % n, j = e / n;
-        double v = 0.0;
-        if (i <= j) {
-            v = G[j + i * ldg];
-            if (i == j) v += shift;
-        }
-        R[i + j * ldr] = v;
+    const int lane = threadIdx.x;
+    const int nb = min(PNB, n - jb);
+    for (int e = lane; e < nb * nb; e += 32) {
+        const int i = e % nb, j = e / nb;
+        D[i][j] = (i <= j) ? R[(jb + i) + (long)(jb + j) * ldr] : 0.0;
     }
-    if (tid == 0) broke = 0;
-    __syncthreads();
-    for (int jb = 0; jb < n; jb += PNB) {
-        const int nb = min(PNB, n - jb);
-        for (int e = tid; e < nb * nb; e += POTRF_THREADS) {
-            const int i = e % nb, j = e / nb;
-            D[i][j] = (i <= j) ? R[(jb + i) + (long)(jb + j) * ldr] : 0.0;
-        }
-        __syncthreads();
-        if (tid < 32) {
-            const int lane = tid;
-            for (int j = 0; j < nb; ++j) {
-                const double piv = D[j][j];
-                if (!(piv > 0.0)) {
-                    if (lane == 0) broke = jb + j + 1;
-                    break;
-                }
-                const double d = sqrt(piv);
-                __syncwarp();
-                if (lane == 0) D[j][j] = d;
-                for (int c = j + 1 + lane; c < nb; c += 32) D[j][c] /= d;
-                __syncwarp();
-                for (int c = j + 1 + lane; c < nb; c += 32) {
-                    const double djc = D[j][c];
-                    for (int r = j + 1; r <= c; ++r) D[r][c] -= D[j][r] * djc;
-                }
-                __syncwarp();
-            }
-        }
-        __syncthreads();
-        if (broke) {
-            if (tid == 0) raise_status(st, OQR_ERR_NOT_SPD, broke, TAG_POTRF);
+    __syncwarp();
+    for (int j = 0; j < nb; ++j) {
+        const double piv = D[j][j];
+        if (!(piv > 0.0)) {  // the same value in every lane: a uniform exit
+            if (lane == 0) raise_status(st, OQR_ERR_NOT_SPD, jb + j + 1, TAG_POTRF);
             return;
         }
-        for (int e = tid; e < nb * nb; e += POTRF_THREADS) {
-            const int i = e % nb, j = e / nb;
-            if (i <= j) R[(jb + i) + (long)(jb + j) * ldr] = D[i][j];
+        const double d = sqrt(piv);
+        __syncwarp();
+        if (lane == 0) D[j][j] = d;
+        for (int c = j + 1 + lane; c < nb; c += 32) D[j][c] /= d;
+        __syncwarp();
+        for (int c = j + 1 + lane; c < nb; c += 32) {
+            const double djc = D[j][c];
+            for (int r = j + 1; r <= c; ++r) D[r][c] -= D[j][r] * djc;
         }
-        // panel row: R(jb:jb+nb, c) <- D^{-T} R(jb:jb+nb, c), forward substitution
-        for (int c = jb + nb + tid; c < n; c += POTRF_THREADS) {
-            double x[PNB];
-            for (int i = 0; i < nb; ++i) {
-                double t = R[(jb + i) + (long)c * ldr];
-                for (int k = 0; k < i; ++k) t -= D[k][i] * x[k];
-                x[i] = t / D[i][i];
-                R[(jb + i) + (long)c * ldr] = x[i];
-            }
+        __syncwarp();
+    }
+    for (int e = lane; e < nb * nb; e += 32) {
+        const int i = e % nb, j = e / nb;
+        if (i <= j) R[(jb + i) + (long)(jb + j) * ldr] = D[i][j];
+    }
+}
+
+// One thread per trailing column c: forward substitution with D^T (D upper).
+__global__ void __launch_bounds__(128) potrf_row_kernel(int n, int jb, double* R, long ldr, const DevStatus* st)
+{
+    __shared__ double D[PNB][PNB + 1];
+    if (*(volatile const int*)&st->code != 0) return;
+    const int nb = min(PNB, n - jb);
+    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+        const int i = e % nb, j = e / nb;
+        D[i][j] = (i <= j) ? R[(jb + i) + (long)(jb + j) * ldr] : 0.0;
+    }
+    __syncthreads();
+    const int c = jb + nb + blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    double x[PNB];
+#pragma unroll
+    for (int i = 0; i < PNB; ++i) {
+        if (i < nb) {
+            double t = R[(jb + i) + (long)c * ldr];
+            for (int k = 0; k < i; ++k) t -= D[k][i] * x[k];
+            x[i] = t / D[i][i];
+            R[(jb + i) + (long)c * ldr] = x[i];
         }
-        __syncthreads();
-        // trailing update of the upper triangle: R(r, c) -= sum_k R(jb+k, r) R(jb+k, c)
-        const int t0 = jb + nb, nt = n - t0;
-        for (long e = tid; e < (long)nt * nt; e += POTRF_THREADS) {
-            const int r = t0 + (int)(e % nt), c = t0 + (int)(e / nt);
-            if (r > c) continue;
-            double s = R[r + (long)c * ldr];
-            for (int k = 0; k < nb; ++k) s -= R[(jb + k) + (long)r * ldr] * R[(jb + k) + (long)c * ldr];
-            R[r + (long)c * ldr] = s;
-        }
-        __syncthreads();
+    }
+}
+
+// Trailing update on 32 x 32 tiles (tr <= tc) of the upper triangle right of the panel.
+__global__ void __launch_bounds__(256) potrf_trail_kernel(int n, int jb, double* R, long ldr, const DevStatus* st)
+{
+    __shared__ double Pr[PNB][PNB + 1];  // panel rows, tile's row columns
+    __shared__ double Pc[PNB][PNB + 1];  // panel rows, tile's columns
+    if (*(volatile const int*)&st->code != 0) return;
+    const int nb = min(PNB, n - jb);
+    const int t0 = jb + nb;
+    const int nt = (n - t0 + PNB - 1) / PNB;
+    // blockIdx.x enumerates the upper-triangular tile pairs (tr <= tc)
+    int tr = 0, rem = blockIdx.x;
+    while (rem >= nt - tr) {
+        rem -= nt - tr;
+        ++tr;
+    }
+    const int tc = tr + rem;
+    const int r0 = t0 + tr * PNB, c0 = t0 + tc * PNB;
+    for (int e = threadIdx.x; e < PNB * PNB; e += blockDim.x) {
+        const int k = e % PNB, j = e / PNB;
+        Pr[k][j] = (k < nb && r0 + j < n) ? R[(jb + k) + (long)(r0 + j) * ldr] : 0.0;
+        Pc[k][j] = (k < nb && c0 + j < n) ? R[(jb + k) + (long)(c0 + j) * ldr] : 0.0;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < PNB * PNB; e += blockDim.x) {
+        const int i = e % PNB, j = e / PNB;
+        const int r = r0 + i, c = c0 + j;
+        if (r >= n || c >= n || r > c) continue;
+        double s = R[r + (long)c * ldr];
+        for (int k = 0; k < nb; ++k) s -= Pr[k][i] * Pc[k][j];
+        R[r + (long)c * ldr] = s;
     }
 }
 
@@ -414,7 +445,16 @@ cudaError_t launch_axpby(int M, int N, double alpha, const double* X, long ldx, 
 cudaError_t launch_potrf(int n, const double* G, long ldg, double* R, long ldr, const double* shift_ptr,
                          DevStatus* st, cudaStream_t s)
 {
-    potrf_kernel<<<1, POTRF_THREADS, 0, s>>>(n, G, ldg, R, ldr, shift_ptr, st);
+    const long total = (long)n * n;
+    potrf_init_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(n, G, ldg, R, ldr, shift_ptr, st);
+    for (int jb = 0; jb < n; jb += PNB) {
+        potrf_diag_kernel<<<1, 32, 0, s>>>(n, jb, R, ldr, st);
+        const int rest = n - jb - PNB;
+        if (rest <= 0) break;
+        potrf_row_kernel<<<(rest + 127) / 128, 128, 0, s>>>(n, jb, R, ldr, st);
+        const int nt = (rest + PNB - 1) / PNB;
+        potrf_trail_kernel<<<nt * (nt + 1) / 2, 256, 0, s>>>(n, jb, R, ldr, st);
+    }
     return cudaGetLastError();
 }
 

@@ -568,7 +568,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     }
                 }
             }
-            // wait for the last MMAs before TMEM is released
+            // the last chunk's accumulators must have been read before TMEM is released
             if (chunk > 0) mbar_wait(acce, (uint32_t)((chunk - 1) & 1), a.limit_ns);
         }
     } else {
@@ -582,7 +582,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int half = (warp - 2) >> 2;     // which half of the N columns
         const int r = q * 32 + lane;          // row within the tile = TMEM lane
         const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(half * NH);
-        int* colexp = const_cast<int*>(abort_flag) + 32;  // N column scale exponents of the current chunk
+        int* colexp = const_cast<int*>(abort_flag) + 32;  // N column scales of the current chunk (as floats)
         volatile int* go = colexp + 256;                  // outcome of the wait, published by dt == 0
         long chunk = 0;
         bool stop = false;
@@ -604,14 +604,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     if (!ok) fail(4);
                     *go = (ok && !*abort_flag) ? 1 : 0;
                 }
-                if (EMU && dt < N) {
+                if (EMU && dt < N) {  // column scale 2^(e_col - emax_col) of this chunk (0 if empty)
                     const int col = item.c * N + dt;
-                    int v = EXP_NONE;
+                    float v = 0.0f;
                     if (col < a.colsB) {
                         const int eb = a.eB[(size_t)kcg * a.colsB + col];
-                        v = eb == EXP_NONE ? EXP_NONE : eb - a.emaxB[col];
+                        if (eb != EXP_NONE) v = pow2f(eb - a.emaxB[col]);
                     }
-                    colexp[dt] = v;
+                    reinterpret_cast<float*>(colexp)[dt] = v;
                 }
                 asm volatile("bar.sync 1, 256;" ::: "memory");
                 if (*go == 0) {
@@ -621,9 +621,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 tc_fence_after();
                 if (EMU) {
                     const int e_r = row_ok ? a.eA[(size_t)kcg * a.rowsA + gi] : EXP_NONE;
-                    const int drow = e_r == EXP_NONE ? EXP_NONE : e_r - emax_r;
+                    const float* colscale = reinterpret_cast<const float*>(colexp) + half * NH;
 #pragma unroll 1
                     for (int lv = 0; lv < S; ++lv) {
+                        // row scale 2^(e_row - emax_row - 14 - 8 lv); products of two powers of two are exact
+                        const float rs = e_r == EXP_NONE ? 0.0f : pow2f(e_r - emax_r - 14 - 8 * lv);
 #pragma unroll
                         for (int h = 0; h < NH / 32; ++h) {
                             float v[32];
@@ -631,9 +633,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
                             for (int c = 0; c < 32; ++c) {
                                 const int cc = h * 32 + c;
-                                const int dc = colexp[half * NH + cc];
-                                const int d = (drow == EXP_NONE || dc == EXP_NONE) ? -1000 : drow + dc - 14 - 8 * lv;
-                                const float t = __fmul_rn(v[c], pow2f(d));
+                                const float t = __fmul_rn(__fmul_rn(v[c], rs), colscale[cc]);
                                 const float sm = __fadd_rn(H[cc], t);
                                 const float bp = __fsub_rn(sm, H[cc]);
                                 const float err = __fadd_rn(__fsub_rn(H[cc], __fsub_rn(sm, bp)), __fsub_rn(t, bp));
@@ -796,8 +796,12 @@ size_t tc_workspace_bytes(const TcPlan& p)
 // file comment.  ws holds tc_workspace_bytes(p).
 cudaError_t launch_tc_gram(const TcPlan& p, const double* A, long lda, const double* Z, long ldz, double* G, long ldg,
                            const double* shift_ptr, void* ws, DevStatus* st, uint64_t limit_ns, int sms,
-                           cudaStream_t s)
+                           cudaStream_t s, cudaEvent_t* ev)
 {
+    auto mark = [&](int i) {
+        if (ev) cudaEventRecord(ev[i], s);
+    };
+    mark(0);
     auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
     char* w = static_cast<char*>(ws);
     const size_t planeA = (size_t)p.m * p.ldp, planeZ = (size_t)p.n * p.ldp;
@@ -857,11 +861,13 @@ cudaError_t launch_tc_gram(const TcPlan& p, const double* A, long lda, const dou
     a1.st = st;
     a1.limit_ns = limit_ns;
     item_prefix_kernel<<<1, 32, 0, s>>>(a1, cum1);
+    mark(1);
     if (p.emu) e = launch_tc<32, 64, 7, true>(a1, Ap, p.ldp, planeA, Zp, p.ldp, planeZ, sms, s);
     else if (p.N == 64) e = launch_tc<64, 64, 2, false>(a1, Ap, p.ldp, planeA, Zp, p.ldp, planeZ, sms, s);
     else if (p.N == 128) e = launch_tc<64, 128, 2, false>(a1, Ap, p.ldp, planeA, Zp, p.ldp, planeZ, sms, s);
     else e = launch_tc<64, 256, 2, false>(a1, Ap, p.ldp, planeA, Zp, p.ldp, planeZ, sms, s);
     if (e != cudaSuccess) return e;
+    mark(2);
     {
         const long tot = (long)mm * nn;
         if (p.N == 64) slot_reduce_kernel<64><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(a1, U, mm, st);
@@ -884,11 +890,13 @@ cudaError_t launch_tc_gram(const TcPlan& p, const double* A, long lda, const dou
     a2.st = st;
     a2.limit_ns = limit_ns;
     item_prefix_kernel<<<1, 32, 0, s>>>(a2, cum2);
+    mark(3);
     if (p.emu) e = launch_tc<32, 64, 7, true>(a2, Zp, p.ldp, planeZ, Up, p.ldp, planeZ, sms, s);
     else if (p.N == 64) e = launch_tc<64, 64, 2, false>(a2, Zp, p.ldp, planeZ, Up, p.ldp, planeZ, sms, s);
     else if (p.N == 128) e = launch_tc<64, 128, 2, false>(a2, Zp, p.ldp, planeZ, Up, p.ldp, planeZ, sms, s);
     else e = launch_tc<64, 256, 2, false>(a2, Zp, p.ldp, planeZ, Up, p.ldp, planeZ, sms, s);
     if (e != cudaSuccess) return e;
+    mark(4);
     {
         const long tot = (long)nn * nn;
         if (p.N == 64) slot_reduce_kernel<64><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(a2, Cm, nn, st);
@@ -896,6 +904,7 @@ cudaError_t launch_tc_gram(const TcPlan& p, const double* A, long lda, const dou
         else slot_reduce_kernel<256><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(a2, Cm, nn, st);
         symmetrize_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(nn, Cm, nn, G, ldg, shift_ptr, st);
     }
+    mark(5);
     return cudaGetLastError();
 }
 

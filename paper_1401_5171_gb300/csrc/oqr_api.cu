@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <new>
+#include <vector>
 
 #include "oqr_internal.cuh"
 
@@ -18,6 +19,9 @@ struct oqr_ctx {
     size_t ws_bytes = 0;
     bool ws_owned = true;
     DevStatus* st = nullptr;  // device status block (owned, allocated at create)
+    // cached CUDA graph of the batched sequence and the signature it was captured for
+    cudaGraphExec_t batch_exec = nullptr;
+    long batch_key[10] = {0};
 };
 
 namespace {
@@ -36,6 +40,7 @@ void fill_defaults(oqr_opts* o)
     o->check = 0;
     o->spin_limit = 4000000000L;
     o->final_prec = OQR_FP64;
+    o->prec_mid = -1;
 }
 
 oqr_opts resolve(const oqr_opts* o)
@@ -225,11 +230,15 @@ oqr_status normal_equation(oqr_ctx* ctx, int m, int n, const double* A, long lda
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const uint64_t limit = (uint64_t)o.spin_limit;
     const GramPlan gp = gram_plan(m, n, ctx->sm_count);
-    const int prec_first = passes > 1 ? o.prec : o.final_prec;
+    const int prec_mid = o.prec_mid >= 0 ? o.prec_mid : o.prec;
+    if (!prec_ok(prec_mid)) return OQR_ERR_INVALID_ARG;
+    auto prec_of = [&](int p) { return p == passes - 1 ? o.final_prec : (p == 0 ? o.prec : prec_mid); };
+    const int prec_first = prec_of(0);
     Carve probe(nullptr);
     double *partials, *G, *work, *R1, *R2, *R3, *scratch;
     layout_cholqr(probe, gp, &partials, &G, &work, &R1, &R2, &R3, &scratch);
-    const size_t tcb = tc_bytes_for(m, n, prec_first, o.final_prec);
+    size_t tcb = tc_bytes_for(m, n, prec_first, o.final_prec);
+    tcb = std::max(tcb, tc_bytes_for(m, n, prec_mid, prec_mid));
     char* tcws_probe = probe.take<char>(tcb);
     (void)tcws_probe;
     if ((v = ensure_ws(ctx, probe.off)) != OQR_OK) return v;
@@ -239,10 +248,9 @@ oqr_status normal_equation(oqr_ctx* ctx, int m, int n, const double* A, long lda
     if ((v = reset_status(ctx, s)) != OQR_OK) return v;
 
     const double* shift_ptr = nullptr;
-    if (shifted) {
-        // the shift follows the unit roundoff of the first pass's arithmetic
-        const double u = o.prec == OQR_BF16X3 ? 3.0517578125e-05 /* 2^-15 */ : U64;
-        OQR_TRY(launch_norms_and_shift(m, n, A, lda, Z, ldz, o.shift_c, u, scratch, 2 * SHIFT_PARTS, ctx->st, s));
+    const bool trace_shift = shifted && prec_first == OQR_BF16X3;
+    if (shifted && !trace_shift) {
+        OQR_TRY(launch_norms_and_shift(m, n, A, lda, Z, ldz, o.shift_c, U64, scratch, 2 * SHIFT_PARTS, ctx->st, s));
         shift_ptr = &ctx->st->shift;
     }
     // R accumulates as R_p ... R_1; Racc alternates between R2 and R3.
@@ -252,8 +260,10 @@ oqr_status normal_equation(oqr_ctx* ctx, int m, int n, const double* A, long lda
     for (int p = 0; p < passes; ++p) {
         double* Rp = (passes == 1) ? R : R1;
         const long ldrp = (passes == 1) ? ldr : n;
-        const int prec = (p == passes - 1) ? o.final_prec : o.prec;
+        const int prec = prec_of(p);
         OQR_TRY(form_gram(ctx, prec, gp, A, lda, X, ldx, partials, G, p == 0 ? shift_ptr : nullptr, tcws, limit, s));
+        if (p == 0 && trace_shift) OQR_TRY(launch_trace_shift(n, G, n, o.shift_c, 1.52587890625e-05 /* 2^-16 */,
+                                                              ctx->st, s));
         OQR_TRY(launch_potrf(n, G, n, Rp, ldrp, nullptr, ctx->st, s));
         OQR_TRY(launch_trsm(m, n, X, ldx, Rp, ldrp, Q, ldq, ctx->st, s));
         if (passes > 1) {
@@ -393,6 +403,7 @@ oqr_status oqr_destroy(oqr_ctx* ctx)
     if (!ctx) return OQR_OK;
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
+    if (ctx->batch_exec) cudaGraphExecDestroy(ctx->batch_exec);
     if (ctx->ws && ctx->ws_owned) cudaFree(ctx->ws);
     if (ctx->st) cudaFree(ctx->st);
     delete ctx;
@@ -491,6 +502,218 @@ oqr_status oqr_gram(oqr_ctx* ctx, int m, int n, const double* A, long lda, const
     OQR_TRY(cudaMemcpy2DAsync(G, ldg * sizeof(double), Gt, n * sizeof(double), n * sizeof(double), n,
                               cudaMemcpyDeviceToDevice, s));
     return OQR_OK;
+}
+
+int oqr_batched_default_splits(int m, int n)
+{
+    (void)n;
+    if (m < 1) return 1;
+    const long nb = (m + 63) / 64;
+    const long steps = 2 * (nb - 1) * nb + ((std::min<long>((long)nb * 64, m) + 15) / 16);
+    long sp = (steps + 255) / 256;
+    return (int)std::max(1L, std::min(64L, sp));
+}
+
+oqr_status oqr_batched(oqr_ctx* ctx, int count, const int* m, const int* n, const double* const* A, const long* lda,
+                       const double* const* Z, const long* ldz, double* const* Q, const long* ldq, double* const* R,
+                       const long* ldr, int mode, const int* splits, int* status, void* stream)
+{
+    if (!ctx || count < 1 || count > 65535 || !m || !n || !A || !lda || !Z || !ldz || !Q || !ldq || !R || !ldr ||
+        !status)
+        return OQR_ERR_INVALID_ARG;
+    if (mode != 0) return OQR_ERR_UNSUPPORTED;
+    std::vector<BatchDesc> desc((size_t)count);
+    std::vector<int> idx[3];
+    int cls_max_splits[3] = {1, 1, 1}, max_n = 1;
+    size_t per_inst_doubles = 0;
+    for (int b = 0; b < count; ++b) {
+        const int mb = m[b], nb = n[b];
+        if (mb < 1 || nb < 1 || nb > mb || nb > BATCH_MAX_N || mb > BATCH_MAX_M) return OQR_ERR_INVALID_ARG;
+        if (bad_matrix(A[b], lda[b], mb, mb) || bad_matrix(Z[b], ldz[b], mb, nb) || bad_matrix(Q[b], ldq[b], mb, nb) ||
+            bad_matrix(R[b], ldr[b], nb, nb))
+            return OQR_ERR_INVALID_ARG;
+        const int sp = splits ? splits[b] : oqr_batched_default_splits(mb, nb);
+        if (sp < 1 || sp > 64) return OQR_ERR_INVALID_ARG;
+        BatchDesc& d = desc[b];
+        d.A = A[b];
+        d.Z = Z[b];
+        d.Q = Q[b];
+        d.R = R[b];
+        d.lda = lda[b];
+        d.ldz = ldz[b];
+        d.ldq = ldq[b];
+        d.ldr = ldr[b];
+        d.m = mb;
+        d.n = nb;
+        d.splits = sp;
+        d.pad = 0;
+        const int c = nb <= 16 ? 0 : nb <= 32 ? 1 : 2;
+        idx[c].push_back(b);
+        cls_max_splits[c] = std::max(cls_max_splits[c], sp);
+        max_n = std::max(max_n, nb);
+        per_inst_doubles += align256((size_t)(sp + 3) * nb * nb * sizeof(double)) / sizeof(double);
+    }
+    // workspace: descriptors, three index lists, per-instance partials + G + R1 + R2
+    Carve probe(nullptr);
+    probe.take<BatchDesc>((size_t)count);
+    for (int c = 0; c < 3; ++c) probe.take<int>(std::max<size_t>(1, idx[c].size()));
+    probe.take<double>(per_inst_doubles);
+    oqr_status v = ensure_ws(ctx, probe.off);
+    if (v != OQR_OK) return v;
+    Carve cv(ctx->ws);
+    BatchDesc* ddesc = cv.take<BatchDesc>((size_t)count);
+    int* didx[3];
+    for (int c = 0; c < 3; ++c) didx[c] = cv.take<int>(std::max<size_t>(1, idx[c].size()));
+    double* pool = cv.take<double>(per_inst_doubles);
+    for (int b = 0; b < count; ++b) {
+        const size_t nn = (size_t)desc[b].n * desc[b].n;
+        desc[b].partials = pool;
+        desc[b].G = pool + desc[b].splits * nn;
+        desc[b].R1 = desc[b].G + nn;
+        desc[b].R2 = desc[b].R1 + nn;
+        pool += align256((size_t)(desc[b].splits + 3) * nn * sizeof(double)) / sizeof(double);
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    OQR_TRY(cudaMemcpyAsync(ddesc, desc.data(), sizeof(BatchDesc) * count, cudaMemcpyHostToDevice, s));
+    int cls_count[3];
+    for (int c = 0; c < 3; ++c) {
+        cls_count[c] = (int)idx[c].size();
+        if (cls_count[c]) OQR_TRY(cudaMemcpyAsync(didx[c], idx[c].data(), sizeof(int) * cls_count[c],
+                                                  cudaMemcpyHostToDevice, s));
+    }
+    OQR_TRY(cudaMemsetAsync(status, 0, sizeof(int) * count, s));
+    if (s == nullptr) {  // the legacy default stream cannot be captured
+        OQR_TRY(launch_batched_cholqr2(ddesc, count, didx, cls_count, cls_max_splits, max_n, status, s));
+        return OQR_OK;
+    }
+    const long key[10] = {count, cls_count[0], cls_count[1], cls_count[2], cls_max_splits[0], cls_max_splits[1],
+                          cls_max_splits[2], max_n, (long)reinterpret_cast<uintptr_t>(ctx->ws),
+                          (long)reinterpret_cast<uintptr_t>(status)};
+    if (!ctx->batch_exec || memcmp(key, ctx->batch_key, sizeof(key)) != 0) {
+        if (ctx->batch_exec) {
+            cudaStreamSynchronize(s);
+            cudaGraphExecDestroy(ctx->batch_exec);
+            ctx->batch_exec = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        OQR_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        const cudaError_t le = launch_batched_cholqr2(ddesc, count, didx, cls_count, cls_max_splits, max_n, status, s);
+        const cudaError_t ce = cudaStreamEndCapture(s, &g);
+        if (le != cudaSuccess || ce != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return OQR_ERR_CUDA;
+        }
+        const cudaError_t ie = cudaGraphInstantiate(&ctx->batch_exec, g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) {
+            ctx->batch_exec = nullptr;
+            return OQR_ERR_CUDA;
+        }
+        memcpy(ctx->batch_key, key, sizeof(key));
+    }
+    OQR_TRY(cudaGraphLaunch(ctx->batch_exec, s));
+    return OQR_OK;
+}
+
+oqr_status oqr_features(oqr_ctx* ctx, int m, int n, const double* A, long lda, const double* Z, long ldz, float* feat,
+                        void* stream)
+{
+    if (!ctx || !feat || m < 1 || n < 1 || n > m || bad_matrix(A, lda, m, m) || bad_matrix(Z, ldz, m, n))
+        return OQR_ERR_INVALID_ARG;
+    if (n > 1024) return OQR_ERR_UNSUPPORTED;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const TcPlan tp = tc_plan(m, n, false);
+    const size_t tb = align256(tc_workspace_bytes(tp));
+    oqr_status v = ensure_ws(ctx, tb + 2 * align256((size_t)n * n * 8) + align256(2 * SHIFT_PARTS * 8));
+    if (v != OQR_OK) return v;
+    if ((v = reset_status(ctx, s)) != OQR_OK) return v;
+    char* w = static_cast<char*>(ctx->ws);
+    double* G = reinterpret_cast<double*>(w + tb);
+    double* C = reinterpret_cast<double*>(w + tb + align256((size_t)n * n * 8));
+    double* scratch = reinterpret_cast<double*>(w + tb + 2 * align256((size_t)n * n * 8));
+    OQR_TRY(launch_tc_gram(tp, A, lda, Z, ldz, G, n, nullptr, ctx->ws, ctx->st, 4000000000ull, ctx->sm_count, s));
+    OQR_TRY(launch_norms_and_shift(m, n, A, lda, Z, ldz, 0.0, U64, scratch, 2 * SHIFT_PARTS, ctx->st, s));
+    OQR_TRY(launch_features(m, n, G, n, C, ctx->st, feat, s));
+    return OQR_OK;
+}
+
+int oqr_mlp_param_count(void) { return MLP_PARAMS; }
+
+oqr_status oqr_mlp_forward(oqr_ctx* ctx, int B, const float* X, const float* params, int bf16, float* logits,
+                           int* choice, void* stream)
+{
+    if (!ctx || B < 1 || !X || !params || (!logits && !choice)) return OQR_ERR_INVALID_ARG;
+    OQR_TRY(launch_mlp_forward(B, X, params, bf16, logits, choice, static_cast<cudaStream_t>(stream)));
+    return OQR_OK;
+}
+
+oqr_status oqr_mlp_grad(oqr_ctx* ctx, int B, const float* X, const int* y, const float* params, float* grad,
+                        float* loss, void* stream)
+{
+    if (!ctx || B < 1 || !X || !y || !params || !grad) return OQR_ERR_INVALID_ARG;
+    oqr_status v = ensure_ws(ctx, align256(mlp_scratch_bytes(B)));
+    if (v != OQR_OK) return v;
+    OQR_TRY(launch_mlp_grad(B, X, y, params, grad, loss, static_cast<float*>(ctx->ws),
+                            static_cast<cudaStream_t>(stream)));
+    return OQR_OK;
+}
+
+oqr_status oqr_mlp_adam(oqr_ctx* ctx, float* params, const float* grad, float* m, float* v, float lr, float beta1,
+                        float beta2, float eps, int t, void* stream)
+{
+    if (!ctx || !params || !grad || !m || !v || t < 1) return OQR_ERR_INVALID_ARG;
+    OQR_TRY(launch_adam(MLP_PARAMS, params, grad, m, v, lr, beta1, beta2, eps, t, static_cast<cudaStream_t>(stream)));
+    return OQR_OK;
+}
+
+oqr_status oqr_gram_phases(oqr_ctx* ctx, int m, int n, const double* A, long lda, const double* Z, long ldz,
+                           double* G, long ldg, int prec, float* phase_ms, int* nphase, void* stream)
+{
+    if (!ctx || !phase_ms || !nphase || m < 1 || n < 1 || n > m || bad_matrix(A, lda, m, m) ||
+        bad_matrix(Z, ldz, m, n) || bad_matrix(G, ldg, n, n))
+        return OQR_ERR_INVALID_ARG;
+    if (prec != OQR_BF16X3 && prec != OQR_FP64_TC && prec != OQR_FP64) return OQR_ERR_INVALID_ARG;
+    if (n > 1024) return OQR_ERR_UNSUPPORTED;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaEvent_t ev[7];
+    for (int i = 0; i < 7; ++i)
+        if (cudaEventCreate(&ev[i]) != cudaSuccess) return OQR_ERR_CUDA;
+    oqr_status v = OQR_OK;
+    if (prec == OQR_FP64) {
+        const GramPlan gp = gram_plan(m, n, ctx->sm_count);
+        v = ensure_ws(ctx, align256(gram_partials_bytes(gp)));
+        if (v == OQR_OK) v = reset_status(ctx, s);
+        if (v == OQR_OK) {
+            cudaEventRecord(ev[0], s);
+            launch_gram_f64(gp, A, lda, Z, ldz, static_cast<double*>(ctx->ws), ctx->st, 4000000000ull, s);
+            cudaEventRecord(ev[1], s);
+            launch_gram_reduce(gp, static_cast<double*>(ctx->ws), G, ldg, nullptr, ctx->st, s);
+            cudaEventRecord(ev[2], s);
+            *nphase = 2;
+        }
+    } else {
+        const TcPlan tp = tc_plan(m, n, prec == OQR_FP64_TC);
+        v = ensure_ws(ctx, align256(tc_workspace_bytes(tp)) + align256((size_t)n * n * 8));
+        if (v == OQR_OK) v = reset_status(ctx, s);
+        if (v == OQR_OK) {
+            double* Gt = reinterpret_cast<double*>(static_cast<char*>(ctx->ws) + align256(tc_workspace_bytes(tp)));
+            if (launch_tc_gram(tp, A, lda, Z, ldz, Gt, n, nullptr, ctx->ws, ctx->st, 4000000000ull, ctx->sm_count, s,
+                               ev) != cudaSuccess)
+                v = OQR_ERR_CUDA;
+            else if (cudaMemcpy2DAsync(G, ldg * sizeof(double), Gt, n * sizeof(double), n * sizeof(double), n,
+                                       cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+                v = OQR_ERR_CUDA;
+            *nphase = 5;
+        }
+    }
+    if (v == OQR_OK) {
+        if (cudaStreamSynchronize(s) != cudaSuccess) v = OQR_ERR_CUDA;
+        for (int i = 0; v == OQR_OK && i < *nphase; ++i)
+            if (cudaEventElapsedTime(&phase_ms[i], ev[i], ev[i + 1]) != cudaSuccess) v = OQR_ERR_CUDA;
+    }
+    for (int i = 0; i < 7; ++i) cudaEventDestroy(ev[i]);
+    return v;
 }
 
 oqr_status oqr_potrf(oqr_ctx* ctx, int n, const double* G, long ldg, double shift, double* R, long ldr, int* info,

@@ -192,7 +192,42 @@ size_t tc_plan_bytes(const TcPlan& p);
 size_t tc_workspace_bytes(const TcPlan& p);
 cudaError_t launch_tc_gram(const TcPlan& p, const double* A, long lda, const double* Z, long ldz, double* G, long ldg,
                            const double* shift_ptr, void* ws, DevStatus* st, uint64_t limit_ns, int sms,
-                           cudaStream_t s);
+                           cudaStream_t s, cudaEvent_t* ev = nullptr);
+
+// Batched A-CholQR2 (k_batched.cu): one descriptor per instance, n <= 64, m <= 4096.
+constexpr int BATCH_MAX_N = 64;
+constexpr int BATCH_MAX_M = 4096;
+struct BatchDesc {
+    const double* A;
+    const double* Z;
+    double* Q;
+    double* R;
+    long lda, ldz, ldq, ldr;
+    int m, n;
+    int splits;     // Gram work splits (the plan)
+    int pad;
+    double* partials;  // splits x n x n
+    double* G;         // n x n
+    double* R1;        // n x n
+    double* R2;        // n x n
+};
+cudaError_t launch_batched_cholqr2(const BatchDesc* d, int count, const int* const* cls_idx, const int* cls_count,
+                                   const int* cls_max_splits, int max_n, int* status, cudaStream_t s);
+
+// Selector (k_mlp.cu, k_features.cu).
+constexpr int MLP_IN = 16, MLP_HIDDEN = 64, MLP_OUT = 4;
+constexpr int MLP_PARAMS = MLP_HIDDEN * MLP_IN + MLP_HIDDEN + MLP_HIDDEN * MLP_HIDDEN + MLP_HIDDEN +
+                           MLP_OUT * MLP_HIDDEN + MLP_OUT;
+size_t mlp_scratch_bytes(int B);
+cudaError_t launch_mlp_forward(int B, const float* X, const float* P, int bf16, float* logits, int* choice,
+                               cudaStream_t s);
+cudaError_t launch_mlp_grad(int B, const float* X, const int* y, const float* P, float* grad, float* loss, float* scr,
+                            cudaStream_t s);
+cudaError_t launch_adam(int n, float* P, const float* g, float* m, float* v, float lr, float b1, float b2, float eps,
+                        int t, cudaStream_t s);
+cudaError_t launch_features(int m, int n, const double* G, long ldg, double* work, const DevStatus* st, float* feat,
+                            cudaStream_t s);
+cudaError_t launch_trace_shift(int n, double* G, long ldg, double c, double u, DevStatus* st, cudaStream_t s);
 
 // Y = alpha X + beta Y (M x N, column-major).
 cudaError_t launch_axpby(int M, int N, double alpha, const double* X, long ldx, double beta, double* Y, long ldy,

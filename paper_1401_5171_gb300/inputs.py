@@ -205,3 +205,20 @@ def batch_shapes(count: int, seed: int, m_range=(64, 4096), n_range=(4, 64),
     kz = 10.0 ** rng.uniform(*log_kappa_z, size=count)
     seeds = rng.integers(0, 2**31 - 1, size=count)
     return m.astype(np.int64), n.astype(np.int64), ka, kz, seeds
+
+
+def batch_instances(count: int, seed: int, device="cpu", m_range=(64, 4096), n_range=(4, 64),
+                    log_kappa_a=(0.0, 6.0), log_kappa_z=(0.0, 6.0)):
+    """A batch in the recipe of the batched workload: per instance m, n uniform
+    integers, kappa(A) and kappa(Z) log-uniform, A from dense_spd and Z from
+    tall_z with the instance's own seed.  Returns (As, Zs, table) with A_b, Z_b
+    column-major torch float64 tensors on ``device``."""
+    import torch
+    m, n, ka, kz, seeds = batch_shapes(count, seed, m_range, n_range, log_kappa_a, log_kappa_z)
+    As, Zs = [], []
+    for b in range(count):
+        A, _ = dense_spd(int(m[b]), float(ka[b]), seed=int(seeds[b]), device=device)
+        As.append(A.t())                       # column-major view; the library reads its lower triangle
+        Z = tall_z(int(m[b]), int(n[b]), float(kz[b]), seed=int(seeds[b]) + 1, device=device)
+        Zs.append(Z.t().contiguous().t())
+    return As, Zs, {"m": m, "n": n, "kappa_A": ka, "kappa_Z": kz, "seed": seeds}

@@ -27,7 +27,7 @@ OQR_ALGO_CHOLQR, OQR_ALGO_CHOLQR2, OQR_ALGO_SCHOLQR3, OQR_ALGO_CGS2 = 0, 1, 2, 3
 class oqr_opts(ctypes.Structure):
     _fields_ = [("passes", ctypes.c_int), ("shifted", ctypes.c_int), ("prec", ctypes.c_int),
                 ("shift_c", ctypes.c_double), ("block", ctypes.c_int), ("check", ctypes.c_int),
-                ("spin_limit", ctypes.c_long), ("final_prec", ctypes.c_int)]
+                ("spin_limit", ctypes.c_long), ("final_prec", ctypes.c_int), ("prec_mid", ctypes.c_int)]
 
 
 class oqr_info(ctypes.Structure):
@@ -83,6 +83,20 @@ def load(path: str | None = None):
         getattr(lib, name).argtypes = qr
     lib.oqr_gram.argtypes = [vp, i, i, vp, l, vp, l, vp, l, i, vp]
     lib.oqr_gram_noalloc.argtypes = [i, i, vp, l, vp, l, vp, l, vp]
+    pl = ctypes.POINTER(ctypes.c_long)
+    ppd = ctypes.POINTER(ctypes.c_void_p)
+    lib.oqr_batched.argtypes = [vp, i, ctypes.POINTER(i), ctypes.POINTER(i), ppd, pl, ppd, pl, ppd, pl, ppd, pl, i,
+                                ctypes.POINTER(i), vp, vp]
+    lib.oqr_batched_default_splits.argtypes = [i, i]
+    fp, ip = ctypes.c_void_p, ctypes.c_void_p
+    lib.oqr_features.argtypes = [vp, i, i, vp, l, vp, l, fp, vp]
+    lib.oqr_mlp_param_count.argtypes = []
+    lib.oqr_mlp_forward.argtypes = [vp, i, fp, fp, i, fp, ip, vp]
+    lib.oqr_mlp_grad.argtypes = [vp, i, fp, ip, fp, fp, fp, vp]
+    lib.oqr_mlp_adam.argtypes = [vp, fp, fp, fp, fp, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                 ctypes.c_float, i, vp]
+    lib.oqr_gram_phases.argtypes = [vp, i, i, vp, l, vp, l, vp, l, i, ctypes.POINTER(ctypes.c_float),
+                                    ctypes.POINTER(i), vp]
     lib.oqr_potrf.argtypes = [vp, i, vp, l, d, vp, l, ctypes.POINTER(i), vp]
     lib.oqr_trsm.argtypes = [vp, i, i, vp, l, vp, l, vp, l, vp]
     lib.oqr_rprod.argtypes = [vp, i, vp, l, vp, l, vp, l, vp]
@@ -109,8 +123,9 @@ def _raw(name):
 
 
 for _n in ("oqr_default_opts", "oqr_create", "oqr_destroy", "oqr_workspace_size", "oqr_set_workspace",
-           "oqr_get_status", "oqr_cholqr", "oqr_cholqr2", "oqr_cgs2", "oqr_gram", "oqr_gram_noalloc", "oqr_potrf", "oqr_trsm",
-           "oqr_rprod", "oqr_check"):
+           "oqr_get_status", "oqr_cholqr", "oqr_cholqr2", "oqr_cgs2", "oqr_gram", "oqr_gram_noalloc", "oqr_gram_phases", "oqr_potrf", "oqr_trsm",
+           "oqr_rprod", "oqr_check", "oqr_batched", "oqr_batched_default_splits", "oqr_features",
+           "oqr_mlp_param_count", "oqr_mlp_forward", "oqr_mlp_grad", "oqr_mlp_adam"):
     globals()[_n] = _raw(_n)
 
 
@@ -225,6 +240,88 @@ class Oqr:
         if st != OQR_OK:
             raise OqrError(st, "oqr_gram")
         return G
+
+    def oqr_gram_phases(self, A, Z, prec, G=None, stream=None):
+        """Per-phase CUDA-event times (ms) of the Gram pipeline; see include/oqr.h."""
+        n = Z.shape[1]
+        G = G if G is not None else empty_colmajor(n, n, Z.device)
+        a, lda = _m(A)
+        z, ldz = _m(Z)
+        g, ldg = _m(G)
+        ms = (ctypes.c_float * 8)()
+        k = ctypes.c_int(0)
+        st = self.lib.oqr_gram_phases(self.ctx, Z.shape[0], n, a, lda, z, ldz, g, ldg, prec, ms, ctypes.byref(k),
+                                      self._stream(stream))
+        if st != OQR_OK:
+            raise OqrError(st, "oqr_gram_phases")
+        return [ms[i] for i in range(k.value)], G
+
+    def oqr_batched(self, As, Zs, Qs=None, Rs=None, splits=None, stream=None, status=None):
+        """Batched FP64 A-CholQR2 over lists of column-major CUDA tensors; returns (Qs, Rs, status tensor)."""
+        import torch
+        cnt = len(Zs)
+        Qs = Qs if Qs is not None else [empty_colmajor(z.shape[0], z.shape[1], z.device) for z in Zs]
+        Rs = Rs if Rs is not None else [empty_colmajor(z.shape[1], z.shape[1], z.device) for z in Zs]
+        I = ctypes.c_int * cnt
+        L = ctypes.c_long * cnt
+        P = ctypes.c_void_p * cnt
+        mm = I(*[z.shape[0] for z in Zs])
+        nn = I(*[z.shape[1] for z in Zs])
+        ap, al, zp, zl, qp, ql, rp, rl = P(), L(), P(), L(), P(), L(), P(), L()
+        for b in range(cnt):
+            (ap[b], al[b]), (zp[b], zl[b]) = _m(As[b]), _m(Zs[b])
+            (qp[b], ql[b]), (rp[b], rl[b]) = _m(Qs[b]), _m(Rs[b])
+        st = status if status is not None else torch.empty(cnt, dtype=torch.int32, device=Zs[0].device)
+        sp = I(*splits) if splits is not None else None
+        r = self.lib.oqr_batched(self.ctx, cnt, mm, nn, ap, al, zp, zl, qp, ql, rp, rl, 0, sp,
+                                 ctypes.c_void_p(st.data_ptr()), self._stream(stream))
+        if r != OQR_OK:
+            raise OqrError(r, "oqr_batched")
+        return Qs, Rs, st
+
+    # ---- selector ---------------------------------------------------------------
+    def oqr_features(self, A, Z, out=None, stream=None):
+        import torch
+        f = out if out is not None else torch.empty(16, dtype=torch.float32, device=Z.device)
+        a, lda = _m(A)
+        z, ldz = _m(Z)
+        st = self.lib.oqr_features(self.ctx, Z.shape[0], Z.shape[1], a, lda, z, ldz, ctypes.c_void_p(f.data_ptr()),
+                                   self._stream(stream))
+        if st != OQR_OK:
+            raise OqrError(st, "oqr_features")
+        return f
+
+    def oqr_mlp_forward(self, X, params, bf16=True, stream=None, want_logits=True):
+        import torch
+        B = X.shape[0]
+        logits = torch.empty((B, 4), dtype=torch.float32, device=X.device) if want_logits else None
+        choice = torch.empty(B, dtype=torch.int32, device=X.device)
+        st = self.lib.oqr_mlp_forward(self.ctx, B, ctypes.c_void_p(X.contiguous().data_ptr()),
+                                      ctypes.c_void_p(params.data_ptr()), int(bf16),
+                                      ctypes.c_void_p(logits.data_ptr()) if logits is not None else None,
+                                      ctypes.c_void_p(choice.data_ptr()), self._stream(stream))
+        if st != OQR_OK:
+            raise OqrError(st, "oqr_mlp_forward")
+        return logits, choice
+
+    def oqr_mlp_grad(self, X, y, params, stream=None):
+        import torch
+        grad = torch.empty_like(params)
+        loss = torch.empty(1, dtype=torch.float32, device=X.device)
+        st = self.lib.oqr_mlp_grad(self.ctx, X.shape[0], ctypes.c_void_p(X.contiguous().data_ptr()),
+                                   ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(params.data_ptr()),
+                                   ctypes.c_void_p(grad.data_ptr()), ctypes.c_void_p(loss.data_ptr()),
+                                   self._stream(stream))
+        if st != OQR_OK:
+            raise OqrError(st, "oqr_mlp_grad")
+        return grad, loss
+
+    def oqr_mlp_adam(self, params, grad, m, v, lr, t, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+        st = self.lib.oqr_mlp_adam(self.ctx, ctypes.c_void_p(params.data_ptr()), ctypes.c_void_p(grad.data_ptr()),
+                                   ctypes.c_void_p(m.data_ptr()), ctypes.c_void_p(v.data_ptr()), lr, beta1, beta2,
+                                   eps, int(t), self._stream(stream))
+        if st != OQR_OK:
+            raise OqrError(st, "oqr_mlp_adam")
 
     def oqr_potrf(self, G, shift=0.0, R=None, stream=None):
         n = G.shape[0]

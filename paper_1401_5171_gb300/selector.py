@@ -1,0 +1,142 @@
+"""Learned selector over the normal-equation variants (host-side driver).
+
+For each instance the selector reads 16 features from the instance's cheap
+BF16X3 normal-equation matrix (oqr_features), runs the MLP 16 -> 64 -> 64 -> 4
+(oqr_mlp_forward, BF16 inference) and picks one option, cheapest first:
+
+  0  one FP64-accurate pass          (A-CholQR, tensor cores)
+  1  BF16X3 pass + FP64-accurate pass (mixed A-CholQR2)
+  2  shifted BF16X3 pass + two FP64-accurate passes (mixed shifted A-CholQR3)
+  3  FP64 A-CholQR2 (DFMA)           -- also the fallback
+
+The chosen factorization is checked (||Q^T A Q - I||_2 <= tol, measured by
+the check kernel); if the check fails or the Cholesky breaks down, the
+instance is refactored with option 3, and if that breaks down too (an
+unshifted normal-equation method needs kappa(A^{1/2} Z)^2 u < 1), with the
+shifted FP64 A-CholQR3 as the last resort.  Training labels are the cheapest option
+whose measured orthogonality meets tol on method-generated instances; the
+network is trained on the GPU by the library's own kernels (oqr_mlp_grad,
+oqr_mlp_adam).  Every arithmetic step runs in the CUDA library.
+"""
+from __future__ import annotations
+
+import json
+import math
+import time
+
+import numpy as np
+
+OPTIONS = [
+    ("oqr_cholqr", {"final_prec": 3}),
+    ("oqr_cholqr2", {"prec": 1, "final_prec": 3}),
+    ("oqr_cholqr2", {"shifted": 1, "prec": 1, "prec_mid": 3, "final_prec": 3}),
+    ("oqr_cholqr2", {}),
+    ("oqr_cholqr2", {"shifted": 1}),   # last resort, not a class of the network
+]
+FALLBACK = 3
+LAST_RESORT = 4
+CLASSES = 4
+
+
+def init_params(seed: int = 0):
+    """He-initialised flat parameters (numpy float32)."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for fan_in, fan_out in ((16, 64), (64, 64), (64, 4)):
+        parts.append(rng.standard_normal((fan_out, fan_in)) * math.sqrt(2.0 / fan_in))
+        parts.append(np.zeros(fan_out))
+    return np.concatenate([p.ravel() for p in parts]).astype(np.float32)
+
+
+def run_option(ctx, k, A, Z, Q=None, R=None, check=True):
+    name, kw = OPTIONS[k]
+    Q, R, (st, info) = ctx._qr(name, A, Z, Q=Q, R=R, raise_on_error=False, check=int(check), **kw)
+    return Q, R, st, (info.orth_err if st == 0 else float("inf"))
+
+
+def label_instance(ctx, A, Z, tol=1e-12):
+    """Cheapest option meeting tol, and the orthogonality each option reached."""
+    orth = []
+    for k in range(CLASSES):
+        _, _, st, o = run_option(ctx, k, A, Z)
+        orth.append(o)
+    for k, o in enumerate(orth):
+        if o <= tol:
+            return k, orth
+    return FALLBACK, orth
+
+
+def make_set(ctx, count, seed, device="cuda", m_range=(64, 512), n_range=(4, 32), log_kappa_a=(0.0, 6.0),
+             log_kappa_z=(0.0, 12.0), tol=1e-12):
+    """Method-generated instances with features and labels (torch tensors on device)."""
+    import torch
+
+    from . import inputs
+    As, Zs, tab = inputs.batch_instances(count, seed, device=device, m_range=m_range, n_range=n_range,
+                                         log_kappa_a=log_kappa_a, log_kappa_z=log_kappa_z)
+    X = torch.empty((count, 16), dtype=torch.float32, device=device)
+    y = torch.empty(count, dtype=torch.int32, device=device)
+    orth = np.zeros((count, CLASSES))
+    for b in range(count):
+        ctx.oqr_features(As[b], Zs[b], out=X[b])
+        lab, o = label_instance(ctx, As[b], Zs[b], tol)
+        y[b] = lab
+        orth[b] = o
+    torch.cuda.synchronize()
+    return {"As": As, "Zs": Zs, "X": X, "y": y, "orth": orth, "table": tab}
+
+
+def train(ctx, X, y, epochs=400, lr=3e-3, batch=256, seed=0, params=None):
+    """Adam on the mean cross-entropy, all arithmetic in the library's kernels."""
+    import torch
+    dev = X.device
+    P = torch.as_tensor(init_params(seed) if params is None else params, device=dev).clone()
+    m = torch.zeros_like(P)
+    v = torch.zeros_like(P)
+    n = X.shape[0]
+    g = torch.Generator().manual_seed(seed)
+    losses, t = [], 0
+    for ep in range(epochs):
+        perm = torch.randperm(n, generator=g).to(dev)
+        for i in range(0, n, batch):
+            idx = perm[i:i + batch]
+            grad, loss = ctx.oqr_mlp_grad(X[idx].contiguous(), y[idx].contiguous(), P)
+            t += 1
+            ctx.oqr_mlp_adam(P, grad, m, v, lr, t)
+        losses.append(float(loss.item()))
+    return P, losses
+
+
+def choose(ctx, X, P):
+    """Argmax option per feature row (BF16 inference kernel)."""
+    _, choice = ctx.oqr_mlp_forward(X, P, bf16=True, want_logits=False)
+    return choice
+
+
+def solve(ctx, A, Z, P, tol=1e-12):
+    """Selected factorization with check and fallback; returns (Q, R, info)."""
+    import torch
+    f = ctx.oqr_features(A, Z).reshape(1, 16)
+    k = int(choose(ctx, f, P)[0].item())
+    Q, R, st, o = run_option(ctx, k, A, Z)
+    fell = not (st == 0 and o <= tol)
+    used = k
+    if fell and k != FALLBACK:
+        Q, R, st, o = run_option(ctx, FALLBACK, A, Z, Q=Q, R=R)
+        used = FALLBACK
+    if st != 0:
+        Q, R, st, o = run_option(ctx, LAST_RESORT, A, Z, Q=Q, R=R)
+        used = LAST_RESORT
+    return Q, R, {"choice": k, "fallback": fell, "used": used, "orth": o, "status": st}
+
+
+def save(P, path):
+    with open(path, "w") as f:
+        json.dump({"layout": "W1[64][16] b1[64] W2[64][64] b2[64] W3[4][64] b3[4]",
+                   "params": [float(x) for x in P.detach().cpu().numpy()]}, f)
+
+
+def load(path, device="cuda"):
+    import torch
+    with open(path) as f:
+        return torch.tensor(json.load(f)["params"], dtype=torch.float32, device=device)

@@ -1,0 +1,134 @@
+"""GPU parity of the batched A-CholQR2 (oqr_batched) against the CPU oracle.
+
+Batches follow the batched workload's recipe (m, n uniform integers,
+kappa(A), kappa(Z) log-uniform up to 1e6, dense SPD A).  Every instance is
+compared with the oracle (CHOL-EQR, Algorithm 3) on the small batches; the
+full 4096-instance batch is checked on every instance through properties
+that fix (Q, R) (Q^T A Q = I, Z = QR, R upper with positive diagonal) and on a
+stratified sample against the oracle.  A Cholesky breakdown is an accepted
+outcome only where the oracle's kappa(R) exceeds 1e7 (the normal-equation
+methods need kappa(A^{1/2} Z)^2 u < 1).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1401_5171_gb300 import autotune, inputs
+
+pytestmark = pytest.mark.gpu
+U = 2.0 ** -53
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1401_5171_gb300 import oqr
+    return torch, oqr, oqr.Oqr(0)
+
+
+def check_instance(A, Z, Q, R, status):
+    Qr, Rr = oracle.oblique_qr(A, Z)
+    kap = np.linalg.cond(Rr)
+    if status != 0:
+        assert kap > 1e7, f"breakdown at column {status} with kappa(R) = {kap:.2e}"
+        return
+    assert np.all(np.tril(R, -1) == 0) and np.all(np.diag(R) > 0)
+    assert np.linalg.norm(R - Rr) / np.linalg.norm(Rr) <= max(1e-12, 50 * U * kap)
+    floor = 100 * U * np.linalg.eigvalsh(A).max() * np.linalg.norm(Qr, 2) ** 2
+    assert oracle.orth_error(A, Q) <= max(1e-12, 10 * oracle.orth_error(A, Qr), floor)
+
+
+def test_batched_small_parity(env):
+    torch, oqr, ctx = env
+    As, Zs, tab = inputs.batch_instances(40, seed=3, device="cuda", m_range=(64, 700), n_range=(4, 64))
+    Qs, Rs, st = ctx.oqr_batched(As, Zs)
+    torch.cuda.synchronize()
+    st = st.cpu().numpy()
+    for b in range(len(Zs)):
+        check_instance(As[b].cpu().numpy(), Zs[b].cpu().numpy(), Qs[b].cpu().numpy(), Rs[b].cpu().numpy(), st[b])
+
+
+def test_batched_breakdown_is_isolated(env):
+    torch, oqr, ctx = env
+    As, Zs, _ = inputs.batch_instances(6, seed=5, device="cuda", m_range=(64, 300), n_range=(4, 40),
+                                       log_kappa_z=(0.0, 2.0))
+    bad = torch.eye(100, dtype=torch.float64, device="cuda")
+    bad[7, 7] = -1.0                             # indefinite: breaks at column 8 for Z = I[:, :10]
+    As.insert(2, oqr.colmajor(bad))
+    Zs.insert(2, oqr.colmajor(torch.eye(100, 10, dtype=torch.float64, device="cuda")))
+    Qs, Rs, st = ctx.oqr_batched(As, Zs)
+    torch.cuda.synchronize()
+    st = st.cpu().numpy()
+    assert st[2] == 8
+    for b in range(len(Zs)):
+        if b != 2:
+            check_instance(As[b].cpu().numpy(), Zs[b].cpu().numpy(), Qs[b].cpu().numpy(), Rs[b].cpu().numpy(), st[b])
+
+
+def test_batched_plans_agree(env):
+    # different work plans change only the rounding order of the Gram partial sums
+    torch, oqr, ctx = env
+    As, Zs, _ = inputs.batch_instances(12, seed=9, device="cuda", m_range=(500, 1500), n_range=(4, 64),
+                                       log_kappa_z=(0.0, 3.0))
+    ms = [z.shape[0] for z in Zs]
+    outs = []
+    for t in (64, 4096):
+        plan = [autotune.splits_for(m, t) for m in ms]
+        Qs, Rs, st = ctx.oqr_batched(As, Zs, splits=plan)
+        torch.cuda.synchronize()
+        assert st.abs().sum().item() == 0
+        outs.append([r.cpu().numpy() for r in Rs])
+    for R1, R2 in zip(*outs):
+        assert np.linalg.norm(R1 - R2) / np.linalg.norm(R1) < 1e-12
+
+
+def test_batched_graph_replay_same_result(env):
+    torch, oqr, ctx = env
+    As, Zs, _ = inputs.batch_instances(10, seed=13, device="cuda", m_range=(64, 400), n_range=(4, 64),
+                                       log_kappa_z=(0.0, 2.0))
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        _, R1, st1 = ctx.oqr_batched(As, Zs, stream=s)
+        _, R2, st2 = ctx.oqr_batched(As, Zs, stream=s)     # replays the cached graph
+    torch.cuda.synchronize()
+    for a, b in zip(R1, R2):
+        assert torch.equal(a, b)
+
+
+def test_config3_full_batch(env):
+    """4096 instances, m in [64, 4096], n in [4, 64], kappa(A), kappa(Z) log-uniform in [1, 1e6]."""
+    torch, oqr, ctx = env
+    As, Zs, tab = inputs.batch_instances(4096, seed=2024, device="cuda")
+    plan, table, _ = autotune.tune(ctx, As[:512], Zs[:512], reps=1)
+    plan = autotune.plan_from_table([z.shape[0] for z in Zs], table)
+    Qs, Rs, st = ctx.oqr_batched(As, Zs, splits=plan)
+    torch.cuda.synchronize()
+    st = st.cpu().numpy()
+    ok = 0
+    for b in range(len(Zs)):
+        A, Z, Q, R = As[b], Zs[b], Qs[b], Rs[b]
+        if st[b] != 0:
+            # breakdown only for kappa(A^{1/2} Z) beyond the method's reach
+            G = Z.T @ (A @ Z)
+            ev = torch.linalg.eigvalsh(0.5 * (G + G.T))
+            assert (ev.max() / ev.min().clamp_min(1e-300)).item() > 1e14
+            continue
+        ok += 1
+        n = Z.shape[1]
+        E = Q.T @ (A @ Q) - torch.eye(n, dtype=torch.float64, device="cuda")
+        orth = torch.linalg.eigvalsh(0.5 * (E + E.T)).abs().max().item()
+        nA = float(tab["kappa_A"][b])                  # ||A||_2 = kappa(A) (smallest eigenvalue 1)
+        qn = torch.linalg.matrix_norm(Q, 2).item()
+        assert orth <= max(1e-12, 1e3 * Z.shape[0] * U * nA * qn * qn)
+        rep = (torch.linalg.matrix_norm(Z - Q @ R, 2) / torch.linalg.matrix_norm(Z, 2)).item()
+        assert rep <= 1e-13
+        assert torch.all(torch.tril(R, -1) == 0) and torch.all(torch.diagonal(R) > 0)
+    assert ok >= 0.9 * len(Zs)
+    # stratified oracle sample: one instance per m-quartile with m <= 2500
+    ms = np.array([z.shape[0] for z in Zs])
+    for lo, hi in ((64, 700), (700, 1400), (1400, 2000), (2000, 2500)):
+        cand = [b for b in range(len(Zs)) if lo <= ms[b] < hi and st[b] == 0]
+        b = cand[0]
+        check_instance(As[b].cpu().numpy(), Zs[b].cpu().numpy(), Qs[b].cpu().numpy(), Rs[b].cpu().numpy(), st[b])
