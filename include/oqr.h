@@ -67,7 +67,8 @@ typedef struct {
     int prec;         /* oqr_precision of the preconditioning passes [OQR_FP64] */
     double shift_c;   /* constant c of the shift s = c u (m n + n (n+1)) ||A||_F ||Z||_F^2 [11] */
     int block;        /* oqr_cgs2: column block size b [64] */
-    int check;        /* 1 = measure ||Q^T A Q - I||_2 after the factorization into info->orth_err [0] */
+    int check;        /* measure ||Q^T A Q - I||_2 after the factorization into info->orth_err [0]:
+                         1 = with an FP64 Gram, 2 = with the FP64-accurate tensor-core Gram */
     long spin_limit;  /* time limit of any device-side wait, in nanoseconds [4e9] */
     int final_prec;   /* oqr_cholqr2: oqr_precision of the last pass [OQR_FP64]; OQR_FP64 or OQR_FP64_TC */
     int prec_mid;     /* passes between the first and the last: oqr_precision, or -1 = same as prec [-1] */

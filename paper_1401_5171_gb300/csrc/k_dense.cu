@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(CHECK_THREADS) check_finish_kernel(int n, cons
     for (int i = threadIdx.x; i < n; i += CHECK_THREADS) x[i] = 1.0 + 0.25 * sin(1.0 + i);
     __syncthreads();
     double best = 0.0;
-    for (int it = 0; it < 64; ++it) {
+    for (int it = 0; it < 32; ++it) {
         double sx = 0.0;
         for (int i = threadIdx.x; i < n; i += CHECK_THREADS) sx += x[i] * x[i];
         const double nx = block_sum(sx, red);

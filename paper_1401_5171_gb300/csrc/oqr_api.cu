@@ -183,10 +183,16 @@ oqr_status reset_status(oqr_ctx* ctx, cudaStream_t s)
 }
 
 oqr_status run_check(oqr_ctx* ctx, const GramPlan& gp, const double* A, long lda, const double* Q, long ldq,
-                     double* partials, double* G, double* work, double* E, long lde, uint64_t limit, cudaStream_t s)
+                     double* partials, double* G, double* work, double* E, long lde, uint64_t limit, cudaStream_t s,
+                     void* tcws = nullptr)
 {
-    OQR_TRY(launch_gram_f64(gp, A, lda, Q, ldq, partials, ctx->st, limit, s));
-    OQR_TRY(launch_gram_reduce(gp, partials, G, gp.n, nullptr, ctx->st, s));
+    if (tcws) {  // FP64-accurate Gram on the tensor cores
+        const TcPlan tp = tc_plan(gp.m, gp.n, true);
+        OQR_TRY(launch_tc_gram(tp, A, lda, Q, ldq, G, gp.n, nullptr, tcws, ctx->st, limit, ctx->sm_count, s));
+    } else {
+        OQR_TRY(launch_gram_f64(gp, A, lda, Q, ldq, partials, ctx->st, limit, s));
+        OQR_TRY(launch_gram_reduce(gp, partials, G, gp.n, nullptr, ctx->st, s));
+    }
     OQR_TRY(launch_check_finish(gp.n, G, gp.n, E, lde, work, ctx->st, s));
     return OQR_OK;
 }
@@ -239,6 +245,7 @@ oqr_status normal_equation(oqr_ctx* ctx, int m, int n, const double* A, long lda
     layout_cholqr(probe, gp, &partials, &G, &work, &R1, &R2, &R3, &scratch);
     size_t tcb = tc_bytes_for(m, n, prec_first, o.final_prec);
     tcb = std::max(tcb, tc_bytes_for(m, n, prec_mid, prec_mid));
+    if (o.check == 2) tcb = std::max(tcb, tc_bytes_for(m, n, OQR_FP64_TC, OQR_FP64_TC));
     char* tcws_probe = probe.take<char>(tcb);
     (void)tcws_probe;
     if ((v = ensure_ws(ctx, probe.off)) != OQR_OK) return v;
@@ -282,7 +289,9 @@ oqr_status normal_equation(oqr_ctx* ctx, int m, int n, const double* A, long lda
         ldx = ldq;
     }
     if (o.check) {
-        if ((v = run_check(ctx, gp, A, lda, Q, ldq, partials, G, work, nullptr, 0, limit, s)) != OQR_OK) return v;
+        if ((v = run_check(ctx, gp, A, lda, Q, ldq, partials, G, work, nullptr, 0, limit, s,
+                           o.check == 2 ? tcws : nullptr)) != OQR_OK)
+            return v;
     }
     return finish(ctx, s, info, passes, o.check != 0);
 }
