@@ -121,6 +121,35 @@ __device__ inline void emu_slices7(double x, int e, float* out)
     out[0] = (float)Y;
 }
 
+// FP8 E4M3 code of x 2^(8-e) (|x| < 2^e, so the value is below 256 <= 448),
+// round-to-nearest-even: 4 significant bits for normal values (exponent bias
+// 7), q 2^-9 (q = 0..7) below 2^-6.  Bit 7 is the sign.
+__device__ inline unsigned char e4m3_code(double x, int e)
+{
+    const Bits b = bits_of(x);
+    if (b.M == 0) return 0;
+    const int msb = 63 - __clzll((long long)b.M);
+    const int E = b.Eb - 1075;
+    int p = msb + E + 8 - e;  // unbiased exponent of the scaled value
+    unsigned int code;
+    if (p >= -6) {
+        unsigned long long q = rne_shift(b.M, msb - 3);  // 8..16
+        if (q == 16) {
+            q = 8;
+            ++p;
+        }
+        if (p > 8) {  // saturate (not reached for |x| < 2^e)
+            p = 8;
+            q = 14;
+        }
+        code = ((unsigned)(p + 7) << 3) | (unsigned)(q - 8);
+    } else {
+        const unsigned long long q = rne_shift(b.M, e - E - 17);  // RNE(value 2^9), 0..8
+        code = q >= 8 ? (1u << 3) : (unsigned)q;
+    }
+    return (unsigned char)(code | (b.neg ? 0x80u : 0u));
+}
+
 // hi = bf16(x), lo = bf16(x - hi), both round-to-nearest-even (8 significant bits).
 // Valid for |x| within the normal FP32 range, as BF16 itself.
 __device__ inline void bf16x2_split(double x, __nv_bfloat16& hi, __nv_bfloat16& lo)
@@ -169,11 +198,14 @@ __device__ inline unsigned long long warp_max_u64(unsigned long long v)
 // A (m x m, column-major, lower triangle) -> slices of M = tril(A,-1) + diag(A)/2,
 // written row-major (row i, k contiguous): planes + s*plane + i*ldp + k.
 // One CTA: 32 rows x one 128-column chunk; 8 warps.
-template <bool EMU>
+// MODE 0: BF16 hi/lo planes; 1: seven exact BF16 slices; 2: one FP8 E4M3 plane
+// (bytes).  Modes 1 and 2 record the chunk exponent of every row.
+template <int MODE>
 __global__ void __launch_bounds__(256) split_lower_kernel(int m, const double* __restrict__ A, long lda, int S,
                                                           __nv_bfloat16* planes, long ldp, size_t plane,
                                                           int* eA, int* emax)
 {
+    constexpr bool EMU = MODE != 0;  // exponents are recorded
     __shared__ double T[32][KCH + 1];
     const int kc = blockIdx.x, ib = blockIdx.y;
     const long row0 = (long)ib * 32, col0 = (long)kc * KCH;
@@ -210,6 +242,10 @@ __global__ void __launch_bounds__(256) split_lower_kernel(int m, const double* _
         for (int j = 0; j < 4; ++j) {
             const long k = col0 + lane + 32 * j;
             if (k >= m) continue;
+            if (MODE == 2) {
+                reinterpret_cast<unsigned char*>(planes)[i * ldp + k] = e == EXP_NONE ? 0 : e4m3_code(v[j], e);
+                continue;
+            }
             __nv_bfloat16* dst = planes + i * ldp + k;
             if (EMU) {
                 float sl[7];
@@ -233,11 +269,12 @@ __global__ void __launch_bounds__(256) split_lower_kernel(int m, const double* _
 
 // X (K x C, column-major) -> slices written column-major (column c, k
 // contiguous): planes + s*plane + c*ldp + k.  One warp per (chunk, column).
-template <bool EMU>
+template <int MODE>
 __global__ void __launch_bounds__(256) split_tall_kernel(int K, int C, const double* __restrict__ X, long ldx, int S,
                                                          __nv_bfloat16* planes, long ldp, size_t plane, int* eX,
                                                          int* xmax)
 {
+    constexpr bool EMU = MODE != 0;  // exponents are recorded
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int kc = blockIdx.x;
     const long c = (long)blockIdx.y * 8 + w;
@@ -262,6 +299,10 @@ __global__ void __launch_bounds__(256) split_tall_kernel(int K, int C, const dou
     for (int j = 0; j < 4; ++j) {
         const long k = k0 + lane + 32 * j;
         if (k >= K) continue;
+        if (MODE == 2) {
+            reinterpret_cast<unsigned char*>(planes)[c * ldp + k] = e == EXP_NONE ? 0 : e4m3_code(v[j], e);
+            continue;
+        }
         __nv_bfloat16* dst = planes + c * ldp + k;
         if (EMU) {
             float sl[7];
@@ -375,6 +416,21 @@ __device__ inline void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32
         : "memory");
 }
 
+// kind::f8f6f4 instruction descriptor: D = F32, A = B = E4M3 (format 0), both K-major, M = 128.
+__host__ __device__ constexpr uint32_t idesc_e4m3(int N)
+{
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+}
+
+__device__ inline void umma_e4m3(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
 __device__ inline void umma_commit(uint64_t* bar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
@@ -417,18 +473,21 @@ __device__ inline float pow2f(int d)
 }
 
 // ---------------------------------------------------------- the kernel ----
-template <int KS, int N, int S, bool EMU>
+// MODE 0: BF16X3, 1: FP64-accurate emulation, 2: FP8 E4M3 with chunk scales.
+template <int KS, int N, int S, int MODE>
 struct TcCfg {
-    static constexpr int SW = KS * 2;                  // swizzle width in bytes (row of KS BF16)
-    static constexpr int A_TILE = TM * KS * 2;         // bytes
-    static constexpr int B_TILE = N * KS * 2;
+    static constexpr int ES = MODE == 2 ? 1 : 2;      // element bytes
+    static constexpr int SW = KS * ES;                 // swizzle width = one K-major row of KS elements
+    static constexpr int A_TILE = TM * KS * ES;        // bytes
+    static constexpr int B_TILE = N * KS * ES;
     static constexpr int STAGE = S * A_TILE + S * B_TILE;
     static constexpr int STAGES = 2;
-    static constexpr int LEVELS = EMU ? S : 1;
+    static constexpr int LEVELS = MODE == 1 ? S : 1;
     static constexpr int TMEM_COLS_USED = LEVELS * N;
     static constexpr int TMEM_COLS = TMEM_COLS_USED <= 32 ? 32 : TMEM_COLS_USED <= 64 ? 64
                                    : TMEM_COLS_USED <= 128 ? 128 : TMEM_COLS_USED <= 256 ? 256 : 512;
-    static constexpr int CH_STEPS = EMU ? KCH / KS : 1 << 30;  // k-steps per drained chunk
+    static constexpr int KPI = MODE == 2 ? 32 : 16;    // K per MMA instruction (32 bytes of K)
+    static constexpr int CH_STEPS = MODE == 0 ? 1 << 30 : KCH / KS;  // k-steps per drained chunk
     static constexpr size_t SMEM = 1024 + STAGES * (size_t)STAGE + 2048;  // align slack + barriers, exponents
     static_assert(SW == 64 || SW == 128, "swizzle");
     static_assert(TMEM_COLS_USED <= 512, "TMEM");
@@ -436,11 +495,13 @@ struct TcCfg {
     static_assert(A_TILE % 1024 == 0 && B_TILE % 1024 == 0, "tile alignment");
 };
 
-template <int KS, int N, int S, bool EMU>
+template <int KS, int N, int S, int MODE>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, TcArgs a)
 {
-    using C = TcCfg<KS, N, S, EMU>;
+    using C = TcCfg<KS, N, S, MODE>;
+    constexpr bool EMU = MODE == 1;
+    constexpr bool CHUNKED = MODE != 0;  // drained every 128 of the contraction, with the chunk scales
     extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
     unsigned char* smem =
         reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~uintptr_t(1023));
@@ -512,14 +573,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     } else if (warp == 1) {
         // ------------------------------------------------ MMA issuer
         if (lane == 0) {
-            constexpr uint32_t idesc = idesc_bf16(N);
+            constexpr uint32_t idesc = MODE == 2 ? idesc_e4m3(N) : idesc_bf16(N);
             long it = 0, chunk = 0;
             for (int j = blockIdx.x; j < a.nitems && !*abort_flag; j += gridDim.x) {
                 const Item item = item_of(a, j);
                 for (int ks = item.ks0; ks < item.ks1 && !*abort_flag; ++ks, ++it) {
-                    const bool chunk_start = EMU ? ((ks - item.ks0) % C::CH_STEPS == 0) : (ks == item.ks0);
-                    const bool chunk_end = EMU ? ((ks - item.ks0 + 1) % C::CH_STEPS == 0 || ks + 1 == item.ks1)
-                                               : (ks + 1 == item.ks1);
+                    const bool chunk_start = CHUNKED ? ((ks - item.ks0) % C::CH_STEPS == 0) : (ks == item.ks0);
+                    const bool chunk_end = CHUNKED ? ((ks - item.ks0 + 1) % C::CH_STEPS == 0 || ks + 1 == item.ks1)
+                                                   : (ks + 1 == item.ks1);
                     if (chunk_start && chunk > 0) {  // the drain must have emptied the accumulators
                         if (!mbar_wait(acce, (uint32_t)((chunk - 1) & 1), a.limit_ns)) {
                             fail(2);
@@ -548,6 +609,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                     umma_bf16(d, ad, bd, idesc, (first_of_level && kk == 0) ? 0u : 1u);
                                 }
                             }
+                    } else if (MODE == 2) {
+                        // one E4M3 product per k-step, K = 32 per instruction
+#pragma unroll
+                        for (int kk = 0; kk < KS / C::KPI; ++kk) {
+                            const uint64_t ad = smem_desc(base + kk * 32, C::SW);
+                            const uint64_t bd = smem_desc(base + C::A_TILE + kk * 32, C::SW);
+                            umma_e4m3(tmem, ad, bd, idesc, (chunk_start && kk == 0) ? 0u : 1u);
+                        }
                     } else {
                         // hi*hi, hi*lo, lo*hi into one accumulator
                         const int sa[3] = {0, 0, 1}, tb[3] = {0, 1, 0};
@@ -591,12 +660,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const long gi = (long)item.I * TM + r;
             const bool row_ok = gi < a.rowsA;
             double* slot = a.slots + (size_t)j * TM * N + (size_t)r * N + half * NH;
-            float H[EMU ? NH : 1], L[EMU ? NH : 1];
+            float H[CHUNKED ? NH : 1], L[EMU ? NH : 1];
 #pragma unroll
-            for (int c = 0; c < (EMU ? NH : 1); ++c) H[c] = L[c] = 0.f;
-            const int emax_r = (EMU && row_ok) ? a.emaxA[gi] : 0;
+            for (int c = 0; c < (CHUNKED ? NH : 1); ++c) H[c] = 0.f;
+#pragma unroll
+            for (int c = 0; c < (EMU ? NH : 1); ++c) L[c] = 0.f;
+            const int emax_r = (CHUNKED && row_ok) ? a.emaxA[gi] : 0;
             const int nsteps = item.ks1 - item.ks0;
-            const int nch = EMU ? (nsteps + C::CH_STEPS - 1) / C::CH_STEPS : 1;
+            const int nch = CHUNKED ? (nsteps + C::CH_STEPS - 1) / C::CH_STEPS : 1;
             for (int ch = 0; ch < nch; ++ch, ++chunk) {
                 const int kcg = (item.ks0 * KS) / KCH + ch;  // global 128-chunk index
                 if (dt == 0) {
@@ -604,7 +675,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     if (!ok) fail(4);
                     *go = (ok && !*abort_flag) ? 1 : 0;
                 }
-                if (EMU && dt < N) {  // column scale 2^(e_col - emax_col) of this chunk (0 if empty)
+                if (CHUNKED && dt < N) {  // column scale 2^(e_col - emax_col) of this chunk (0 if empty)
                     const int col = item.c * N + dt;
                     float v = 0.0f;
                     if (col < a.colsB) {
@@ -619,7 +690,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     break;
                 }
                 tc_fence_after();
-                if (EMU) {
+                if constexpr (MODE == 2) {
+                    // products of x 2^(8-e_r) and y 2^(8-e_c): scale back by 2^(e_r + e_c - 16), relative
+                    // to the row and column maxima; FP32 accumulation is enough for this precision
+                    const int e_r = row_ok ? a.eA[(size_t)kcg * a.rowsA + gi] : EXP_NONE;
+                    const float* colscale = reinterpret_cast<const float*>(colexp) + half * NH;
+                    const float rs = e_r == EXP_NONE ? 0.0f : pow2f(e_r - emax_r - 16);
+#pragma unroll
+                    for (int h = 0; h < NH / 32; ++h) {
+                        float v[32];
+                        tmem_ld32(lane_addr + (uint32_t)(h * 32), v);
+#pragma unroll
+                        for (int c = 0; c < 32; ++c) H[h * 32 + c] = fmaf(__fmul_rn(v[c], rs), colscale[h * 32 + c],
+                                                                          H[h * 32 + c]);
+                    }
+                } else if constexpr (MODE == 1) {
                     const int e_r = row_ok ? a.eA[(size_t)kcg * a.rowsA + gi] : EXP_NONE;
                     const float* colscale = reinterpret_cast<const float*>(colexp) + half * NH;
 #pragma unroll 1
@@ -662,12 +747,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 if (dt == 0) mbar_arrive(acce);
             }
             if (stop) break;
-            if (EMU) {
+            if constexpr (CHUNKED) {
 #pragma unroll
                 for (int c = 0; c < NH; ++c) {
                     const int col = item.c * N + half * NH + c;
                     const int bmax = col < a.colsB ? __ldg(a.emaxB + col) : 0;
-                    slot[c] = ldexp((double)H[c] + (double)L[c], emax_r + bmax);
+                    double hv = (double)H[c];
+                    if constexpr (EMU) hv += (double)L[c];
+                    slot[c] = ldexp(hv, emax_r + bmax);
                 }
             }
         }
@@ -714,23 +801,22 @@ __global__ void symmetrize_kernel(int n, const double* __restrict__ Cm, long ldc
 
 // ------------------------------------------------------------ host side ----
 bool make_map_3d(CUtensorMap* map, const void* base, long kext, long rows, long ldp, size_t plane_bytes, int S,
-                 int box_k, int box_rows);
+                 int box_k, int box_rows, int elem_bytes);
 
-template <int KS, int N, int S, bool EMU>
+template <int KS, int N, int S, int MODE>
 cudaError_t launch_tc(const TcArgs& a0, const void* planesA, long ldpA, size_t planeA, const void* planesB, long ldpB,
                       size_t planeB, int sms, cudaStream_t s)
 {
-    using C = TcCfg<KS, N, S, EMU>;
+    using C = TcCfg<KS, N, S, MODE>;
     TcArgs a = a0;
     CUtensorMap mA{}, mB{};
-    const long krows_a = a.tri ? a.K : a.K;
-    if (!make_map_3d(&mA, planesA, krows_a, a.rowsA, ldpA, planeA * 2, S, KS, TM)) return cudaErrorInvalidValue;
-    if (!make_map_3d(&mB, planesB, a.K, a.colsB, ldpB, planeB * 2, S, KS, N)) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(tc_kernel<KS, N, S, EMU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (!make_map_3d(&mA, planesA, a.K, a.rowsA, ldpA, planeA * C::ES, S, KS, TM, C::ES)) return cudaErrorInvalidValue;
+    if (!make_map_3d(&mB, planesB, a.K, a.colsB, ldpB, planeB * C::ES, S, KS, N, C::ES)) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(tc_kernel<KS, N, S, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)C::SMEM);
     if (e != cudaSuccess) return e;
     const int grid = a.nitems < sms ? a.nitems : sms;
-    if (grid > 0) tc_kernel<KS, N, S, EMU><<<grid, TC_THREADS, C::SMEM, s>>>(mA, mB, a);
+    if (grid > 0) tc_kernel<KS, N, S, MODE><<<grid, TC_THREADS, C::SMEM, s>>>(mA, mB, a);
     return cudaGetLastError();
 }
 
@@ -749,8 +835,9 @@ static TcArgs make_args(const TcPlan& p, int rowsA, int colsB, int K, int tri, i
     a.colsB = colsB;
     a.K = K;
     a.tri = tri;
-    a.ks = p.emu ? 32 : 64;
-    a.piece = p.emu ? 64 : 32;
+    a.ks = p.mode == 1 ? 32 : p.mode == 2 ? 128 : 64;
+    a.piece = 2048 / a.ks;  // k-steps per item (a multiple of the 128-long chunk)
+    if (p.mode == 1) a.piece = 64;
     a.cc = (colsB + N - 1) / N;
     a.rt = (rowsA + TM - 1) / TM;
     int s = 0;
@@ -759,15 +846,17 @@ static TcArgs make_args(const TcPlan& p, int rowsA, int colsB, int K, int tri, i
     return a;
 }
 
-TcPlan tc_plan(int m, int n, bool emu)
+TcPlan tc_plan(int m, int n, int mode)
 {
     TcPlan p{};
     p.m = m;
     p.n = n;
-    p.emu = emu;
-    p.S = emu ? 7 : 2;
-    p.N = emu ? 64 : (n <= 64 ? 64 : n <= 128 ? 128 : 256);
-    p.ldp = ((long)m + 63) / 64 * 64;
+    p.mode = mode;
+    p.S = mode == 1 ? 7 : mode == 2 ? 1 : 2;
+    p.es = mode == 2 ? 1 : 2;
+    // FP8 keeps N <= 128: its drain holds N/2 FP32 sums per thread
+    p.N = mode == 1 ? 64 : (n <= 64 ? 64 : (n <= 128 || mode == 2) ? 128 : 256);
+    p.ldp = ((long)m + 127) / 128 * 128;
     p.kch = (m + KCH - 1) / KCH;
     const TcArgs u = make_args(p, m, n, m, 1, p.N);
     const TcArgs c = make_args(p, n, n, m, 0, p.N);
@@ -779,9 +868,9 @@ size_t tc_workspace_bytes(const TcPlan& p)
 {
     auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
     size_t b = 0;
-    b += al((size_t)p.S * p.m * p.ldp * 2);      // A planes (row-major, full m x ldp)
-    b += al((size_t)p.S * p.n * p.ldp * 2);      // Z planes
-    b += al((size_t)p.S * p.n * p.ldp * 2);      // U planes
+    b += al((size_t)p.S * p.m * p.ldp * p.es);   // A planes (row-major, full m x ldp)
+    b += al((size_t)p.S * p.n * p.ldp * p.es);   // Z planes
+    b += al((size_t)p.S * p.n * p.ldp * p.es);   // U planes
     b += al((size_t)p.kch * p.m * 4);            // eA
     b += al((size_t)p.kch * p.n * 4) * 2;        // eZ, eU
     b += al((size_t)p.m * 4) + al((size_t)p.n * 4) * 2;  // emaxA, emaxZ, emaxU
@@ -791,6 +880,41 @@ size_t tc_workspace_bytes(const TcPlan& p)
     b += al((size_t)p.n * p.n * 8);              // C
     return b;
 }
+
+namespace {
+template <int MODE>
+void launch_splits_lower(dim3 g, cudaStream_t s, int mm, const double* A, long lda, int S, __nv_bfloat16* P, long ldp,
+                         size_t plane, int* e, int* mx)
+{
+    split_lower_kernel<MODE><<<g, 256, 0, s>>>(mm, A, lda, S, P, ldp, plane, e, mx);
+}
+template <int MODE>
+void launch_splits_tall(dim3 g, cudaStream_t s, int K, int C, const double* X, long ldx, int S, __nv_bfloat16* P,
+                        long ldp, size_t plane, int* e, int* mx)
+{
+    split_tall_kernel<MODE><<<g, 256, 0, s>>>(K, C, X, ldx, S, P, ldp, plane, e, mx);
+}
+cudaError_t launch_tc_mode(const TcPlan& p, const TcArgs& a, const void* PA, size_t planeA, const void* PB,
+                           size_t planeB, int sms, cudaStream_t s)
+{
+    if (p.mode == 1) return launch_tc<32, 64, 7, 1>(a, PA, p.ldp, planeA, PB, p.ldp, planeB, sms, s);
+    if (p.mode == 2) {
+        if (p.N == 64) return launch_tc<128, 64, 1, 2>(a, PA, p.ldp, planeA, PB, p.ldp, planeB, sms, s);
+        return launch_tc<128, 128, 1, 2>(a, PA, p.ldp, planeA, PB, p.ldp, planeB, sms, s);
+    }
+    if (p.N == 64) return launch_tc<64, 64, 2, 0>(a, PA, p.ldp, planeA, PB, p.ldp, planeB, sms, s);
+    if (p.N == 128) return launch_tc<64, 128, 2, 0>(a, PA, p.ldp, planeA, PB, p.ldp, planeB, sms, s);
+    return launch_tc<64, 256, 2, 0>(a, PA, p.ldp, planeA, PB, p.ldp, planeB, sms, s);
+}
+void launch_slot_reduce(const TcPlan& p, const TcArgs& a, double* out, long ldo, const DevStatus* st, cudaStream_t s)
+{
+    const long tot = (long)a.rowsA * a.colsB;
+    const unsigned g = (unsigned)((tot + 255) / 256);
+    if (p.N == 64) slot_reduce_kernel<64><<<g, 256, 0, s>>>(a, out, ldo, st);
+    else if (p.N == 128) slot_reduce_kernel<128><<<g, 256, 0, s>>>(a, out, ldo, st);
+    else slot_reduce_kernel<256><<<g, 256, 0, s>>>(a, out, ldo, st);
+}
+}  // namespace
 
 // G = Z^T A Z (+ shift) from A's lower triangle on the tensor cores; see the
 // file comment.  ws holds tc_workspace_bytes(p).
@@ -804,13 +928,13 @@ cudaError_t launch_tc_gram(const TcPlan& p, const double* A, long lda, const dou
     mark(0);
     auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
     char* w = static_cast<char*>(ws);
-    const size_t planeA = (size_t)p.m * p.ldp, planeZ = (size_t)p.n * p.ldp;
+    const size_t planeA = (size_t)p.m * p.ldp, planeZ = (size_t)p.n * p.ldp;  // elements
     __nv_bfloat16* Ap = reinterpret_cast<__nv_bfloat16*>(w);
-    w += al((size_t)p.S * planeA * 2);
+    w += al((size_t)p.S * planeA * p.es);
     __nv_bfloat16* Zp = reinterpret_cast<__nv_bfloat16*>(w);
-    w += al((size_t)p.S * planeZ * 2);
+    w += al((size_t)p.S * planeZ * p.es);
     __nv_bfloat16* Up = reinterpret_cast<__nv_bfloat16*>(w);
-    w += al((size_t)p.S * planeZ * 2);
+    w += al((size_t)p.S * planeZ * p.es);
     int* eA = reinterpret_cast<int*>(w);
     w += al((size_t)p.kch * p.m * 4);
     int* eZ = reinterpret_cast<int*>(w);
@@ -835,19 +959,30 @@ cudaError_t launch_tc_gram(const TcPlan& p, const double* A, long lda, const dou
 
     const int S = p.S;
     const int mm = p.m, nn = p.n;
+    // element offsets of the slice planes are in units of the plane's element (byte planes for FP8)
+    const size_t pA = p.es == 1 ? planeA / 2 : planeA, pZ = p.es == 1 ? planeZ / 2 : planeZ;
+    const long ldpe = p.es == 1 ? p.ldp / 2 : p.ldp;
+    (void)pA;
+    (void)pZ;
+    (void)ldpe;
     cudaError_t e;
-    if (p.emu) {
+    if (p.mode != 0) {
         fill_int_kernel<<<(mm + 255) / 256, 256, 0, s>>>(mA, mm, EXP_NONE);
         fill_int_kernel<<<(nn + 255) / 256, 256, 0, s>>>(mZ, nn, EXP_NONE);
         fill_int_kernel<<<(nn + 255) / 256, 256, 0, s>>>(mU, nn, EXP_NONE);
     }
     {
-        dim3 g(p.kch, (mm + 31) / 32);
-        if (p.emu) split_lower_kernel<true><<<g, 256, 0, s>>>(mm, A, lda, S, Ap, p.ldp, planeA, eA, mA);
-        else split_lower_kernel<false><<<g, 256, 0, s>>>(mm, A, lda, S, Ap, p.ldp, planeA, eA, mA);
-        dim3 gz(p.kch, (nn + 7) / 8);
-        if (p.emu) split_tall_kernel<true><<<gz, 256, 0, s>>>(mm, nn, Z, ldz, S, Zp, p.ldp, planeZ, eZ, mZ);
-        else split_tall_kernel<false><<<gz, 256, 0, s>>>(mm, nn, Z, ldz, S, Zp, p.ldp, planeZ, eZ, mZ);
+        dim3 g(p.kch, (mm + 31) / 32), gz(p.kch, (nn + 7) / 8);
+        if (p.mode == 1) {
+            launch_splits_lower<1>(g, s, mm, A, lda, S, Ap, p.ldp, planeA, eA, mA);
+            launch_splits_tall<1>(gz, s, mm, nn, Z, ldz, S, Zp, p.ldp, planeZ, eZ, mZ);
+        } else if (p.mode == 2) {
+            launch_splits_lower<2>(g, s, mm, A, lda, S, Ap, p.ldp, planeA, eA, mA);
+            launch_splits_tall<2>(gz, s, mm, nn, Z, ldz, S, Zp, p.ldp, planeZ, eZ, mZ);
+        } else {
+            launch_splits_lower<0>(g, s, mm, A, lda, S, Ap, p.ldp, planeA, eA, mA);
+            launch_splits_tall<0>(gz, s, mm, nn, Z, ldz, S, Zp, p.ldp, planeZ, eZ, mZ);
+        }
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // U = M Z (triangular)
@@ -862,23 +997,15 @@ cudaError_t launch_tc_gram(const TcPlan& p, const double* A, long lda, const dou
     a1.limit_ns = limit_ns;
     item_prefix_kernel<<<1, 32, 0, s>>>(a1, cum1);
     mark(1);
-    if (p.emu) e = launch_tc<32, 64, 7, true>(a1, Ap, p.ldp, planeA, Zp, p.ldp, planeZ, sms, s);
-    else if (p.N == 64) e = launch_tc<64, 64, 2, false>(a1, Ap, p.ldp, planeA, Zp, p.ldp, planeZ, sms, s);
-    else if (p.N == 128) e = launch_tc<64, 128, 2, false>(a1, Ap, p.ldp, planeA, Zp, p.ldp, planeZ, sms, s);
-    else e = launch_tc<64, 256, 2, false>(a1, Ap, p.ldp, planeA, Zp, p.ldp, planeZ, sms, s);
-    if (e != cudaSuccess) return e;
+    if ((e = launch_tc_mode(p, a1, Ap, planeA, Zp, planeZ, sms, s)) != cudaSuccess) return e;
     mark(2);
-    {
-        const long tot = (long)mm * nn;
-        if (p.N == 64) slot_reduce_kernel<64><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(a1, U, mm, st);
-        else if (p.N == 128) slot_reduce_kernel<128><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(a1, U, mm, st);
-        else slot_reduce_kernel<256><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(a1, U, mm, st);
-    }
+    launch_slot_reduce(p, a1, U, mm, st, s);
     // C = Z^T U (left operand: Z's columns as rows, K-major), then G = C + C^T
     {
         dim3 gu(p.kch, (nn + 7) / 8);
-        if (p.emu) split_tall_kernel<true><<<gu, 256, 0, s>>>(mm, nn, U, mm, S, Up, p.ldp, planeZ, eU, mU);
-        else split_tall_kernel<false><<<gu, 256, 0, s>>>(mm, nn, U, mm, S, Up, p.ldp, planeZ, eU, mU);
+        if (p.mode == 1) launch_splits_tall<1>(gu, s, mm, nn, U, mm, S, Up, p.ldp, planeZ, eU, mU);
+        else if (p.mode == 2) launch_splits_tall<2>(gu, s, mm, nn, U, mm, S, Up, p.ldp, planeZ, eU, mU);
+        else launch_splits_tall<0>(gu, s, mm, nn, U, mm, S, Up, p.ldp, planeZ, eU, mU);
     }
     TcArgs a2 = make_args(p, nn, nn, mm, 0, p.N);
     a2.cum = cum2;
@@ -891,17 +1018,11 @@ cudaError_t launch_tc_gram(const TcPlan& p, const double* A, long lda, const dou
     a2.limit_ns = limit_ns;
     item_prefix_kernel<<<1, 32, 0, s>>>(a2, cum2);
     mark(3);
-    if (p.emu) e = launch_tc<32, 64, 7, true>(a2, Zp, p.ldp, planeZ, Up, p.ldp, planeZ, sms, s);
-    else if (p.N == 64) e = launch_tc<64, 64, 2, false>(a2, Zp, p.ldp, planeZ, Up, p.ldp, planeZ, sms, s);
-    else if (p.N == 128) e = launch_tc<64, 128, 2, false>(a2, Zp, p.ldp, planeZ, Up, p.ldp, planeZ, sms, s);
-    else e = launch_tc<64, 256, 2, false>(a2, Zp, p.ldp, planeZ, Up, p.ldp, planeZ, sms, s);
-    if (e != cudaSuccess) return e;
+    if ((e = launch_tc_mode(p, a2, Zp, planeZ, Up, planeZ, sms, s)) != cudaSuccess) return e;
     mark(4);
+    launch_slot_reduce(p, a2, Cm, nn, st, s);
     {
         const long tot = (long)nn * nn;
-        if (p.N == 64) slot_reduce_kernel<64><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(a2, Cm, nn, st);
-        else if (p.N == 128) slot_reduce_kernel<128><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(a2, Cm, nn, st);
-        else slot_reduce_kernel<256><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(a2, Cm, nn, st);
         symmetrize_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(nn, Cm, nn, G, ldg, shift_ptr, st);
     }
     mark(5);
@@ -933,16 +1054,17 @@ EncodeTiledFn3 encode3()
 // Slice planes: dims {K (contiguous), rows, S}; box {box_k, box_rows, 1};
 // swizzle = box_k * 2 bytes (64 or 128), matching the UMMA K-major layout.
 bool make_map_3d(CUtensorMap* map, const void* base, long kext, long rows, long ldp, size_t plane_bytes, int S,
-                 int box_k, int box_rows)
+                 int box_k, int box_rows, int elem_bytes)
 {
     EncodeTiledFn3 fn = encode3();
     if (!fn) return false;
     cuuint64_t dims[3] = {(cuuint64_t)kext, (cuuint64_t)rows, (cuuint64_t)S};
-    cuuint64_t strides[2] = {(cuuint64_t)ldp * 2, (cuuint64_t)plane_bytes};
+    cuuint64_t strides[2] = {(cuuint64_t)ldp * elem_bytes, (cuuint64_t)plane_bytes};
     cuuint32_t box[3] = {(cuuint32_t)box_k, (cuuint32_t)box_rows, 1};
     cuuint32_t estr[3] = {1, 1, 1};
-    const CUtensorMapSwizzle sw = box_k * 2 == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
-    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
+    const CUtensorMapSwizzle sw = box_k * elem_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
+    const CUtensorMapDataType dt = elem_bytes == 1 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    CUresult r = fn(map, dt, 3, const_cast<void*>(base), dims, strides, box, estr,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;

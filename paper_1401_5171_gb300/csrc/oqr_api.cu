@@ -187,7 +187,7 @@ oqr_status run_check(oqr_ctx* ctx, const GramPlan& gp, const double* A, long lda
                      void* tcws = nullptr)
 {
     if (tcws) {  // FP64-accurate Gram on the tensor cores
-        const TcPlan tp = tc_plan(gp.m, gp.n, true);
+        const TcPlan tp = tc_plan(gp.m, gp.n, 1);
         OQR_TRY(launch_tc_gram(tp, A, lda, Q, ldq, G, gp.n, nullptr, tcws, ctx->st, limit, ctx->sm_count, s));
     } else {
         OQR_TRY(launch_gram_f64(gp, A, lda, Q, ldq, partials, ctx->st, limit, s));
@@ -197,7 +197,9 @@ oqr_status run_check(oqr_ctx* ctx, const GramPlan& gp, const double* A, long lda
     return OQR_OK;
 }
 
-bool prec_ok(int p) { return p == OQR_FP64 || p == OQR_BF16X3 || p == OQR_FP64_TC; }
+bool prec_ok(int p) { return p == OQR_FP64 || p == OQR_BF16X3 || p == OQR_FP64_TC || p == OQR_FP8; }
+
+int tc_mode_of(int prec) { return prec == OQR_FP64_TC ? 1 : prec == OQR_FP8 ? 2 : 0; }
 
 // G = X^T A X (+ shift) in the requested arithmetic.
 cudaError_t form_gram(oqr_ctx* ctx, int prec, const GramPlan& gp, const double* A, long lda, const double* X,
@@ -209,15 +211,15 @@ cudaError_t form_gram(oqr_ctx* ctx, int prec, const GramPlan& gp, const double* 
         if (e != cudaSuccess) return e;
         return launch_gram_reduce(gp, partials, G, gp.n, shift_ptr, ctx->st, s);
     }
-    const TcPlan tp = tc_plan(gp.m, gp.n, prec == OQR_FP64_TC);
+    const TcPlan tp = tc_plan(gp.m, gp.n, tc_mode_of(prec));
     return launch_tc_gram(tp, A, lda, X, ldx, G, gp.n, shift_ptr, tcws, ctx->st, limit, ctx->sm_count, s);
 }
 
 size_t tc_bytes_for(int m, int n, int prec_a, int prec_b)
 {
     size_t b = 0;
-    if (prec_a == OQR_BF16X3 || prec_b == OQR_BF16X3) b = std::max(b, tc_workspace_bytes(tc_plan(m, n, false)));
-    if (prec_a == OQR_FP64_TC || prec_b == OQR_FP64_TC) b = std::max(b, tc_workspace_bytes(tc_plan(m, n, true)));
+    for (int pr : {prec_a, prec_b})
+        if (pr != OQR_FP64) b = std::max(b, tc_workspace_bytes(tc_plan(m, n, tc_mode_of(pr))));
     return b;
 }
 
@@ -228,7 +230,6 @@ oqr_status normal_equation(oqr_ctx* ctx, int m, int n, const double* A, long lda
     oqr_status v = check_common(ctx, m, n, A, lda, Z, ldz, Q, ldq, R, ldr);
     if (v != OQR_OK) return v;
     const oqr_opts o = resolve(opts_in);
-    if (o.prec == OQR_FP8 || o.final_prec == OQR_FP8) return OQR_ERR_UNSUPPORTED;
     if (!prec_ok(o.prec) || !prec_ok(o.final_prec)) return OQR_ERR_INVALID_ARG;
     int passes = forced_passes > 0 ? forced_passes : (o.shifted ? 3 : o.passes);
     if (passes > 8) return OQR_ERR_INVALID_ARG;
@@ -255,7 +256,7 @@ oqr_status normal_equation(oqr_ctx* ctx, int m, int n, const double* A, long lda
     if ((v = reset_status(ctx, s)) != OQR_OK) return v;
 
     const double* shift_ptr = nullptr;
-    const bool trace_shift = shifted && prec_first == OQR_BF16X3;
+    const bool trace_shift = shifted && (prec_first == OQR_BF16X3 || prec_first == OQR_FP8);
     if (shifted && !trace_shift) {
         OQR_TRY(launch_norms_and_shift(m, n, A, lda, Z, ldz, o.shift_c, U64, scratch, 2 * SHIFT_PARTS, ctx->st, s));
         shift_ptr = &ctx->st->shift;
@@ -269,8 +270,8 @@ oqr_status normal_equation(oqr_ctx* ctx, int m, int n, const double* A, long lda
         const long ldrp = (passes == 1) ? ldr : n;
         const int prec = prec_of(p);
         OQR_TRY(form_gram(ctx, prec, gp, A, lda, X, ldx, partials, G, p == 0 ? shift_ptr : nullptr, tcws, limit, s));
-        if (p == 0 && trace_shift) OQR_TRY(launch_trace_shift(n, G, n, o.shift_c, 1.52587890625e-05 /* 2^-16 */,
-                                                              ctx->st, s));
+        if (p == 0 && trace_shift)  // u of the first pass's products: 2^-16 (BF16X3) or 2^-4 (E4M3)
+            OQR_TRY(launch_trace_shift(n, G, n, o.shift_c, prec == OQR_FP8 ? 0.0625 : 1.52587890625e-05, ctx->st, s));
         OQR_TRY(launch_potrf(n, G, n, Rp, ldrp, nullptr, ctx->st, s));
         OQR_TRY(launch_trsm(m, n, X, ldx, Rp, ldrp, Q, ldq, ctx->st, s));
         if (passes > 1) {
@@ -488,7 +489,6 @@ oqr_status oqr_gram(oqr_ctx* ctx, int m, int n, const double* A, long lda, const
     if (!ctx || m < 1 || n < 1 || n > m || bad_matrix(A, lda, m, m) || bad_matrix(Z, ldz, m, n) ||
         bad_matrix(G, ldg, n, n))
         return OQR_ERR_INVALID_ARG;
-    if (prec == OQR_FP8) return OQR_ERR_UNSUPPORTED;
     if (!prec_ok(prec)) return OQR_ERR_INVALID_ARG;
     if (n > 1024) return OQR_ERR_UNSUPPORTED;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -501,7 +501,7 @@ oqr_status oqr_gram(oqr_ctx* ctx, int m, int n, const double* A, long lda, const
         OQR_TRY(launch_gram_reduce(gp, static_cast<double*>(ctx->ws), G, ldg, nullptr, ctx->st, s));
         return OQR_OK;
     }
-    const TcPlan tp = tc_plan(m, n, prec == OQR_FP64_TC);
+    const TcPlan tp = tc_plan(m, n, tc_mode_of(prec));
     oqr_status v = ensure_ws(ctx, align256(tc_workspace_bytes(tp)) + align256((size_t)n * n * 8));
     if (v != OQR_OK) return v;
     if ((v = reset_status(ctx, s)) != OQR_OK) return v;
@@ -632,7 +632,7 @@ oqr_status oqr_features(oqr_ctx* ctx, int m, int n, const double* A, long lda, c
         return OQR_ERR_INVALID_ARG;
     if (n > 1024) return OQR_ERR_UNSUPPORTED;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const TcPlan tp = tc_plan(m, n, false);
+    const TcPlan tp = tc_plan(m, n, 0);
     const size_t tb = align256(tc_workspace_bytes(tp));
     oqr_status v = ensure_ws(ctx, tb + 2 * align256((size_t)n * n * 8) + align256(2 * SHIFT_PARTS * 8));
     if (v != OQR_OK) return v;
@@ -682,7 +682,7 @@ oqr_status oqr_gram_phases(oqr_ctx* ctx, int m, int n, const double* A, long lda
     if (!ctx || !phase_ms || !nphase || m < 1 || n < 1 || n > m || bad_matrix(A, lda, m, m) ||
         bad_matrix(Z, ldz, m, n) || bad_matrix(G, ldg, n, n))
         return OQR_ERR_INVALID_ARG;
-    if (prec != OQR_BF16X3 && prec != OQR_FP64_TC && prec != OQR_FP64) return OQR_ERR_INVALID_ARG;
+    if (!prec_ok(prec)) return OQR_ERR_INVALID_ARG;
     if (n > 1024) return OQR_ERR_UNSUPPORTED;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaEvent_t ev[7];
@@ -702,7 +702,7 @@ oqr_status oqr_gram_phases(oqr_ctx* ctx, int m, int n, const double* A, long lda
             *nphase = 2;
         }
     } else {
-        const TcPlan tp = tc_plan(m, n, prec == OQR_FP64_TC);
+        const TcPlan tp = tc_plan(m, n, tc_mode_of(prec));
         v = ensure_ws(ctx, align256(tc_workspace_bytes(tp)) + align256((size_t)n * n * 8));
         if (v == OQR_OK) v = reset_status(ctx, s);
         if (v == OQR_OK) {

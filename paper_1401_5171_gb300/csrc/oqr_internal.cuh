@@ -180,14 +180,15 @@ cudaError_t launch_gemm_f64(GemmOp op, int M, int N, int K, double alpha, const 
 // emu = true : FP64-accurate (7 exact slices per operand, 28 products).
 struct TcPlan {
     int m, n;
-    bool emu;
+    int mode;       // 0 BF16X3, 1 FP64-accurate emulation, 2 FP8 E4M3
+    int es;         // bytes per plane element
     int S;          // slices per operand
     int N;          // UMMA N (column chunk)
     long ldp;       // leading dimension of the slice planes
     int kch;        // 128-long chunks of the contraction
     int nitems_max; // work items of the larger of the two products
 };
-TcPlan tc_plan(int m, int n, bool emu);
+TcPlan tc_plan(int m, int n, int mode);
 size_t tc_plan_bytes(const TcPlan& p);
 size_t tc_workspace_bytes(const TcPlan& p);
 cudaError_t launch_tc_gram(const TcPlan& p, const double* A, long lda, const double* Z, long ldz, double* G, long ldg,

@@ -13,6 +13,7 @@ import pytest
 
 import oracle
 from paper_1401_5171_gb300 import inputs
+from split_defs import bf16_rne, e4m3_quantize
 
 pytestmark = pytest.mark.gpu
 U = 2.0 ** -53
@@ -31,14 +32,6 @@ def dev(torch, oqr, x):
     return oqr.colmajor(torch.as_tensor(np.asarray(x), dtype=torch.float64).cuda())
 
 
-def bf16_rne(x):
-    """Round to the nearest BF16 value (8 significant bits), ties to even; exact in float64."""
-    x = np.asarray(x, dtype=np.float64)
-    m, e = np.frexp(x)                       # x = m 2^e, |m| in [0.5, 1)
-    q = np.rint(m * 256.0)                   # 8 significant bits, numpy rint = ties to even
-    return np.ldexp(q / 256.0, e)
-
-
 def split_def(x):
     hi = bf16_rne(x)
     lo = bf16_rne(x - hi)
@@ -48,14 +41,6 @@ def split_def(x):
 def lower_m(A):
     Ml = np.tril(A, -1) + 0.5 * np.diag(np.diag(A))
     return Ml
-
-
-def test_bf16_rounding_definition_matches_torch():
-    import torch
-    x = np.random.default_rng(0).standard_normal(10000) * 10.0 ** np.random.default_rng(1).integers(-20, 20, 10000)
-    t = torch.as_tensor(x.astype(np.float32)).to(torch.bfloat16).double().numpy()
-    # through float32 first only differs when the float32 rounding creates a tie; compare on float32 inputs
-    assert np.array_equal(bf16_rne(x.astype(np.float32).astype(np.float64)), t)
 
 
 SHAPES = [(1, 1), (64, 5), (200, 20), (1000, 130), (2000, 20), (3000, 300)]
@@ -128,3 +113,101 @@ def test_fp64tc_cholqr2_config0(env):
     Q, R = Q.cpu().numpy(), R.cpu().numpy()
     assert np.linalg.norm(R - Rr) / np.linalg.norm(Rr) <= 1e-12
     assert oracle.orth_error(A, Q) <= max(1e-12, 10 * oracle.orth_error(A, Qr))
+
+
+# ------------------------------------------------------------------- FP8 ----
+def chunk_exponents(X, axis_len=128):
+    """frexp exponent of each 128-row chunk's largest magnitude, per column (K x C input)."""
+    K, C = X.shape
+    out = np.zeros(((K + axis_len - 1) // axis_len, C), dtype=int)
+    for kc in range(out.shape[0]):
+        mx = np.abs(X[kc * axis_len:(kc + 1) * axis_len]).max(axis=0)
+        out[kc] = np.where(mx > 0, np.frexp(mx)[1], 0)
+    return out
+
+
+def quantize_tall(X):
+    E = chunk_exponents(X)
+    Q = np.empty_like(X, dtype=np.float64)
+    for kc in range(E.shape[0]):
+        sl = slice(kc * 128, (kc + 1) * 128)
+        Q[sl] = e4m3_quantize(X[sl], E[kc][None, :])
+    return Q
+
+
+def test_tc_gram_fp8_definition_integers(env):
+    # integer M and Z are exact in E4M3 after their power-of-two scaling; U = M Z is
+    # then exact, and only U's own quantization (defined above) enters G
+    torch, oqr, ctx = env
+    rng = np.random.default_rng(17)
+    m, n = 700, 24
+    B = rng.integers(-7, 8, size=(m, m)).astype(np.float64)
+    A = np.tril(B) + np.tril(B, -1).T
+    A[np.diag_indices(m)] = 2.0 * rng.integers(-7, 8, size=m)
+    Z = rng.integers(-15, 16, size=(m, n)).astype(np.float64)
+    M = np.tril(A, -1) + 0.5 * np.diag(np.diag(A))
+    U = M @ Z
+    Uq = quantize_tall(U)
+    C = Z.T @ Uq
+    Gdef = C + C.T
+    G = ctx.oqr_gram(dev(torch, oqr, A), dev(torch, oqr, Z), prec=oqr.OQR_FP8).cpu().numpy()
+    assert np.array_equal(G, G.T)
+    assert np.max(np.abs(G - Gdef)) <= 1e-6 * np.abs(Gdef).max()
+
+
+def test_tc_gram_fp8_error_bound(env):
+    torch, oqr, ctx = env
+    A, Z = inputs.paper_case(4, 1500, 40, 1e2, 1e1, seed=31)
+    G = ctx.oqr_gram(dev(torch, oqr, A), dev(torch, oqr, Z), prec=oqr.OQR_FP8).cpu().numpy()
+    Gr = oracle.gram(A, Z)
+    # three E4M3 roundings (M, Z, U) at 2^-4 relative each, against |Z|^T |A| |Z|
+    scale = np.abs(Z).T @ np.abs(A) @ np.abs(Z)
+    assert np.all(np.abs(G - Gr) <= 0.25 * scale)
+    assert np.linalg.norm(G - Gr) / np.linalg.norm(Gr) <= 0.1
+
+
+def test_mixed_cholqr2_fp8_first_pass(env):
+    torch, oqr, ctx = env
+    A, Z = inputs.paper_case(4, 1200, 32, 1e1, 2.0, seed=41)    # kappa(A^{1/2} Z) ~ 2
+    Qr, Rr = oracle.oblique_qr(A, Z)
+    Q, R, (st, info) = ctx.oqr_cholqr2(dev(torch, oqr, A), dev(torch, oqr, Z), prec=oqr.OQR_FP8,
+                                       final_prec=oqr.OQR_FP64_TC, raise_on_error=False)
+    assert st == 0
+    Q, R = Q.cpu().numpy(), R.cpu().numpy()
+    assert np.linalg.norm(R - Rr) / np.linalg.norm(Rr) <= 1e-12
+    assert oracle.orth_error(A, Q) <= max(1e-12, 10 * oracle.orth_error(A, Qr))
+
+
+def test_precision_study_per_kappa(env):
+    """Precision study at m=2048, n=64, kappa(A)=1e6: kappa(A^{1/2} Z) set to 1e1..1e7
+    through case-2 columns of V (the n largest eigenvalues) and kappa(Z).  Reports the
+    Gram error of BF16X3 and FP8 and the orthogonality of the mixed A-CholQR2 variants
+    against the FP64 oracle; asserts what the method guarantees."""
+    torch, oqr, ctx = env
+    m, n = 2048, 64
+    rows = []
+    for kz in (1e1, 1e3, 1e5, 1e7):
+        A, Z = inputs.paper_case(2, m, n, 1e6, kz, seed=int(np.log10(kz)))
+        Qr, Rr = oracle.oblique_qr(A, Z)
+        kap = np.linalg.cond(Rr)
+        Gr = oracle.gram(A, Z)
+        Ad, Zd = dev(torch, oqr, A), dev(torch, oqr, Z)
+        eg = {}
+        for name, prec in (("bf16x3", oqr.OQR_BF16X3), ("fp8", oqr.OQR_FP8)):
+            G = ctx.oqr_gram(Ad, Zd, prec=prec).cpu().numpy()
+            eg[name] = np.linalg.norm(G - Gr, 2) / np.linalg.norm(Gr, 2)
+        orth = {}
+        for name, kw in (("bf16x3->fp64tc", dict(prec=1, final_prec=3)),
+                         ("fp8->fp64tc", dict(prec=2, final_prec=3)),
+                         ("shifted bf16x3->fp64tc->fp64tc", dict(shifted=1, prec=1, prec_mid=3, final_prec=3)),
+                         ("shifted fp8->fp64tc->fp64tc", dict(shifted=1, prec=2, prec_mid=3, final_prec=3))):
+            Q, R, (st, info) = ctx.oqr_cholqr2(Ad, Zd, raise_on_error=False, **kw)
+            orth[name] = oracle.orth_error(A, Q.cpu().numpy()) if st == 0 else float("inf")
+        rows.append((kap, eg, orth))
+        print(f"\nkappa(A^1/2 Z)={kap:.1e}: Gram error bf16x3 {eg['bf16x3']:.1e} fp8 {eg['fp8']:.1e}; orth " +
+              ", ".join(f"{k} {v:.1e}" for k, v in orth.items()))
+        assert eg["bf16x3"] <= 1e-4 and eg["fp8"] <= 0.2
+        if kap <= 1e3:
+            assert orth["bf16x3->fp64tc"] <= max(1e-12, 10 * oracle.orth_error(A, Qr))
+        if kap <= 1e7:
+            assert orth["shifted bf16x3->fp64tc->fp64tc"] <= max(1e-12, 10 * oracle.orth_error(A, Qr))
