@@ -3,7 +3,7 @@
 //
 // The paper forms both products in FP64 (MKL).  On GB300 FP64 runs at about
 // 1/1600 of the BF16 tensor rate, so this file computes them from BF16 slices
-// of the FP64 operands on the 5th-generation tensor cores, in one of two modes:
+// of the FP64 operands on the 5th-generation tensor cores, in one of three modes:
 //
 //  * BF16X3 (preconditioning passes): x = hi + lo with hi = bf16(x),
 //    lo = bf16(x - hi); the product sums hi*hi + hi*lo + lo*hi in one FP32
@@ -13,25 +13,30 @@
 //  * EMU64 (FP64-accurate final pass; error-free slicing in the manner of
 //    Ozaki, Ogita, Oishi and Rump 2012): for every row of the left operand and
 //    every 128-long chunk of the contraction index k, a power-of-two exponent e
-//    is taken from the chunk's largest magnitude, and x 2^-e is written as
-//    sum_s x_s 2^(-7-8(s-1)) with integer x_s in [-128, 128] (exact in BF16),
-//    rounded to nearest at 2^(-7-48).
-//    The right operand is sliced the same way per column.  A product x_s y_t
-//    is an integer below 2^14; over one 128-long chunk the S-1 or fewer
-//    products of one level L = s + t sum to below 2^24 and are therefore exact
-//    in the FP32 accumulator.  Levels 2..S+1 (S(S+1)/2 products) each own a
-//    TMEM accumulator; after every chunk the drain warps scale each level by
-//    its power of two and add it into a double-float (hi, lo) register sum.
-//    With S = 7 the truncation error is about 2^-55 relative to the chunk's
-//    largest term.
+//    is taken from the chunk's largest magnitude, and x 2^(7-e) is written as
+//    sum_s d_s 2^(-8s), s = 0..6, with integers d_s in [-128, 128], rounded to
+//    nearest at 2^-48; slice s is stored as d_s 2^(-8s) (exact in BF16).  The
+//    right operand is sliced the same way per column.  The slice products
+//    (s, t) of one level L = s + t + 2 are integers below 2^14 in the units of
+//    that level; the at most 5 products of a level L <= 6 summed over one
+//    128-long chunk stay below 2^24 and are exact in their FP32 accumulator.
+//    Levels 7 and 8 share one accumulator (their rounding is below 2^-54 of
+//    the chunk's largest term).  After every chunk the drain warps scale the
+//    accumulators by the chunk's row and column powers of two and add them
+//    into a double-float (hi, lo) register sum; with 7 slices the truncation
+//    error is about 2^-55 relative to the chunk's largest term.
 //
-// Kernel structure (one CTA per SM, persistent over work items):
-//   warp 0      TMA producer: all S slice tiles of A and of B per k-step
-//   warp 1      TMEM allocation and the single MMA-issuing thread
-//   warps 2..9  drain: tcgen05.ld of the accumulators (TMEM lane = row);
-//               two warps per TMEM lane quarter, each owning half the columns
+//  * FP8 E4M3 with per-(row, 128-chunk) power-of-two scales, one product,
+//    drained every chunk.
+//
+// Kernel structure (one CTA per SM, persistent over work items): warp 0 is
+// the TMA producer (all slice tiles of A and B per k-step), warp 1 allocates
+// TMEM and holds the single MMA-issuing thread, and the remaining warps drain
+// the accumulators with tcgen05.ld (TMEM lane = row), several warps per TMEM
+// lane quarter.  tc_kernel serves BF16X3 and FP8 (one accumulator);
+// emu_kernel serves EMU64 with its drain overlapping the next chunk's MMAs.
 // An item is (128-row tile I of the left operand, a piece of its k range,
-// an N-column chunk of the right operand); its result goes to its own FP64
+// an N-column chunk of the right operand); its result goes to its own
 // slot, and a reduce kernel sums the slots of each tile in a fixed order.
 // In triangular mode the left operand is M = tril(A,-1) + diag(A)/2 (rows i,
 // columns k <= i), so row tile I stops at k = 128 (I + 1).
@@ -101,7 +106,10 @@ __device__ inline unsigned long long rne_shift(unsigned long long v, int sh)
 
 // EMU64 slices of x for chunk exponent e (|x| < 2^e): with y = x 2^(7-e),
 // Y = RNE(y 2^48) is an integer below 2^55, written in balanced base 256,
-// Y = sum_s d_s 2^(8(6-s)), d_s integers in [-128, 128]: out[s] = d_s, s = 0..6.
+// Y = sum_s d_s 2^(8(6-s)), d_s integers in [-128, 128].  The slices are
+// stored with their weight, out[s] = d_s 2^(-8s) (exact in BF16), so that
+// y = sum_s out[s] up to the rounding at 2^-48 and every slice product
+// carries the weight of its level.
 __device__ inline void emu_slices7(double x, int e, float* out)
 {
     const Bits b = bits_of(x);
@@ -115,7 +123,7 @@ __device__ inline void emu_slices7(double x, int e, float* out)
     for (int s = 6; s >= 1; --s) {
         int d = (int)(Y & 255);
         if (d > 127) d -= 256;
-        out[s] = (float)d;
+        out[s] = (float)d * __int_as_float((127 - 8 * s) << 23);  // d 2^(-8s), exact
         Y = (Y - d) >> 8;  // exact: Y - d is a multiple of 256
     }
     out[0] = (float)Y;
@@ -448,19 +456,21 @@ __device__ inline void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* 
         : "memory");
 }
 
-// 32 consecutive accumulator columns of this thread's TMEM lane.
+// 32 consecutive accumulator columns of this thread's TMEM lane; load and wait
+// in one asm statement, so no use of the values can precede the wait.
 __device__ inline void tmem_ld32(uint32_t taddr, float* v)
 {
     uint32_t r[32];
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+        "tcgen05.wait::ld.sync.aligned;"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
           "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
           "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        : "r"(taddr)
+        : "memory");
 #pragma unroll
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
@@ -473,7 +483,8 @@ __device__ inline float pow2f(int d)
 }
 
 // ---------------------------------------------------------- the kernel ----
-// MODE 0: BF16X3, 1: FP64-accurate emulation, 2: FP8 E4M3 with chunk scales.
+// BF16X3 (MODE 0) and FP8 E4M3 with chunk scales (MODE 2); the FP64-accurate
+// emulation has its own kernel below (emu_kernel).
 template <int KS, int N, int S, int MODE>
 struct TcCfg {
     static constexpr int ES = MODE == 2 ? 1 : 2;      // element bytes
@@ -482,15 +493,12 @@ struct TcCfg {
     static constexpr int B_TILE = N * KS * ES;
     static constexpr int STAGE = S * A_TILE + S * B_TILE;
     static constexpr int STAGES = 2;
-    static constexpr int LEVELS = MODE == 1 ? S : 1;
-    static constexpr int TMEM_COLS_USED = LEVELS * N;
-    static constexpr int TMEM_COLS = TMEM_COLS_USED <= 32 ? 32 : TMEM_COLS_USED <= 64 ? 64
-                                   : TMEM_COLS_USED <= 128 ? 128 : TMEM_COLS_USED <= 256 ? 256 : 512;
+    static constexpr int TMEM_COLS = N <= 32 ? 32 : N <= 64 ? 64 : N <= 128 ? 128 : N <= 256 ? 256 : 512;
     static constexpr int KPI = MODE == 2 ? 32 : 16;    // K per MMA instruction (32 bytes of K)
     static constexpr int CH_STEPS = MODE == 0 ? 1 << 30 : KCH / KS;  // k-steps per drained chunk
     static constexpr size_t SMEM = 1024 + STAGES * (size_t)STAGE + 2048;  // align slack + barriers, exponents
+    static_assert(MODE == 0 || MODE == 2, "mode");
     static_assert(SW == 64 || SW == 128, "swizzle");
-    static_assert(TMEM_COLS_USED <= 512, "TMEM");
     static_assert(N % 64 == 0 && N >= 64 && N <= 256, "N");
     static_assert(A_TILE % 1024 == 0 && B_TILE % 1024 == 0, "tile alignment");
 };
@@ -500,8 +508,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, TcArgs a)
 {
     using C = TcCfg<KS, N, S, MODE>;
-    constexpr bool EMU = MODE == 1;
-    constexpr bool CHUNKED = MODE != 0;  // drained every 128 of the contraction, with the chunk scales
+    constexpr bool CHUNKED = MODE == 2;  // drained every 128 of the contraction, with the chunk scales
     extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
     unsigned char* smem =
         reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~uintptr_t(1023));
@@ -595,21 +602,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     }
                     tc_fence_after();
                     const uint32_t base = smem_u32(smem + stg * C::STAGE);
-                    if (EMU) {
-#pragma unroll 1
-                        for (int s = 0; s < S; ++s)
-#pragma unroll 1
-                            for (int t = 0; s + t < S; ++t) {  // level L = s + t + 2 <= S + 1
-                                const uint32_t d = tmem + (uint32_t)((s + t) * N);
-                                const bool first_of_level = chunk_start && (s == 0);
-#pragma unroll
-                                for (int kk = 0; kk < KS / 16; ++kk) {
-                                    const uint64_t ad = smem_desc(base + s * C::A_TILE + kk * 32, C::SW);
-                                    const uint64_t bd = smem_desc(base + S * C::A_TILE + t * C::B_TILE + kk * 32, C::SW);
-                                    umma_bf16(d, ad, bd, idesc, (first_of_level && kk == 0) ? 0u : 1u);
-                                }
-                            }
-                    } else if (MODE == 2) {
+                    if (MODE == 2) {
                         // one E4M3 product per k-step, K = 32 per instruction
 #pragma unroll
                         for (int kk = 0; kk < KS / C::KPI; ++kk) {
@@ -660,11 +653,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const long gi = (long)item.I * TM + r;
             const bool row_ok = gi < a.rowsA;
             double* slot = a.slots + (size_t)j * TM * N + (size_t)r * N + half * NH;
-            float H[CHUNKED ? NH : 1], L[EMU ? NH : 1];
+            float H[CHUNKED ? NH : 1];
 #pragma unroll
             for (int c = 0; c < (CHUNKED ? NH : 1); ++c) H[c] = 0.f;
-#pragma unroll
-            for (int c = 0; c < (EMU ? NH : 1); ++c) L[c] = 0.f;
             const int emax_r = (CHUNKED && row_ok) ? a.emaxA[gi] : 0;
             const int nsteps = item.ks1 - item.ks0;
             const int nch = CHUNKED ? (nsteps + C::CH_STEPS - 1) / C::CH_STEPS : 1;
@@ -704,35 +695,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         for (int c = 0; c < 32; ++c) H[h * 32 + c] = fmaf(__fmul_rn(v[c], rs), colscale[h * 32 + c],
                                                                           H[h * 32 + c]);
                     }
-                } else if constexpr (MODE == 1) {
-                    const int e_r = row_ok ? a.eA[(size_t)kcg * a.rowsA + gi] : EXP_NONE;
-                    const float* colscale = reinterpret_cast<const float*>(colexp) + half * NH;
-#pragma unroll 1
-                    for (int lv = 0; lv < S; ++lv) {
-                        // row scale 2^(e_row - emax_row - 14 - 8 lv); products of two powers of two are exact
-                        const float rs = e_r == EXP_NONE ? 0.0f : pow2f(e_r - emax_r - 14 - 8 * lv);
-#pragma unroll
-                        for (int h = 0; h < NH / 32; ++h) {
-                            float v[32];
-                            tmem_ld32(lane_addr + (uint32_t)(lv * N + h * 32), v);
-#pragma unroll
-                            for (int c = 0; c < 32; ++c) {
-                                const int cc = h * 32 + c;
-                                const float t = __fmul_rn(__fmul_rn(v[c], rs), colscale[cc]);
-                                const float sm = __fadd_rn(H[cc], t);
-                                const float bp = __fsub_rn(sm, H[cc]);
-                                const float err = __fadd_rn(__fsub_rn(H[cc], __fsub_rn(sm, bp)), __fsub_rn(t, bp));
-                                H[cc] = sm;
-                                L[cc] = __fadd_rn(L[cc], err);
-                            }
-                        }
-                    }
-#pragma unroll
-                    for (int c = 0; c < NH; ++c) {  // renormalise (Fast2Sum)
-                        const float sm = __fadd_rn(H[c], L[c]);
-                        L[c] = __fsub_rn(L[c], __fsub_rn(sm, H[c]));
-                        H[c] = sm;
-                    }
                 } else {
 #pragma unroll 1
                     for (int h = 0; h < NH / 32; ++h) {
@@ -752,9 +714,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 for (int c = 0; c < NH; ++c) {
                     const int col = item.c * N + half * NH + c;
                     const int bmax = col < a.colsB ? __ldg(a.emaxB + col) : 0;
-                    double hv = (double)H[c];
-                    if constexpr (EMU) hv += (double)L[c];
-                    slot[c] = ldexp(hv, emax_r + bmax);
+                    slot[c] = ldexp((double)H[c], emax_r + bmax);
                 }
             }
         }
@@ -799,6 +759,327 @@ __global__ void symmetrize_kernel(int n, const double* __restrict__ Cm, long ldc
     G[r + c * ldg] = v;
 }
 
+// ------------------------------------------- FP64-accurate (EMU64) kernel ----
+// Levels L = s + t + 2 of the slice products (s, t) with s + t <= 6.  Each of
+// L2..L6 owns a TMEM accumulator and is exact over one 128-long chunk (at
+// most 5 products of magnitude below 2^14 in the units of its level, summed
+// over 128 terms: below 2^24).  L7 and L8 (13 products) share one accumulator;
+// their sum is below 2^-37 of the chunk's largest possible value, so FP32
+// rounding there costs below 2^-54 of it, under the slicing error itself.
+//
+// TMEM: 8 slots of 64 columns.  L2..L5 use slots 0..3 in every chunk; L6 and
+// L7+8 alternate between slots 4, 5 (even chunks) and 6, 7 (odd chunks).  The
+// first k-step of a chunk issues the L6..L8 products first (their slots were
+// drained two chunks ago) and only then waits for the drain to have read the
+// previous chunk's L2..L5: the drain of a chunk overlaps the next chunk's
+// MMAs.
+//
+// Warps: 0 TMA producer, 1 TMEM allocation + MMA issuer, 2..17 drain (four
+// warps per TMEM lane quarter, 16 columns each).
+constexpr int EMU_KS = 32;                          // k-step: one 64-byte swizzled row of BF16
+constexpr int EMU_N = 64;                           // UMMA N
+constexpr int EMU_S = 7;                            // slices per operand
+constexpr int EMU_A_TILE = TM * EMU_KS * 2;         // 8 KB
+constexpr int EMU_B_TILE = EMU_N * EMU_KS * 2;      // 4 KB
+constexpr int EMU_STAGE = EMU_S * (EMU_A_TILE + EMU_B_TILE);
+constexpr int EMU_STAGES = 2;
+constexpr int EMU_CH = KCH / EMU_KS;                // k-steps per chunk
+constexpr int EMU_DRAIN = 512;                      // drain threads
+constexpr int EMU_THREADS = 64 + EMU_DRAIN;
+constexpr int EMU_CPT = EMU_N / 4;                  // columns per drain thread
+constexpr size_t EMU_SMEM = 1024 + (size_t)EMU_STAGES * EMU_STAGE + 1024;
+static_assert(EMU_STAGE % 1024 == 0, "stage alignment");
+
+// 16 consecutive accumulator columns of this thread's TMEM lane; the load and
+// its wait are one asm statement, so no use of r can precede the wait.
+__device__ inline void tmem_ld16(uint32_t taddr, uint32_t* r)
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+}
+
+// Two such loads (columns taddr.. and taddr2..) under one wait.
+__device__ inline void tmem_ld16x2(uint32_t taddr, uint32_t taddr2, uint32_t* r, uint32_t* u)
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%32];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%33];\n"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]),
+          "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15])
+        : "r"(taddr), "r"(taddr2)
+        : "memory");
+}
+
+// The products (s, L - 2 - s) of level L: two MMAs (K = 16 each) per product.
+// desc0A / desc0B: descriptors of plane 0 of the stage; plane offsets are
+// added to the 16-byte address field (no carry: shared memory is below 256 KB).
+template <int L>
+__device__ __forceinline__ void emu_issue_level(uint32_t d, uint64_t desc0A, uint64_t desc0B, uint32_t idesc,
+                                                bool first)
+{
+#pragma unroll
+    for (int s = 0; s <= L - 2; ++s) {
+        const int t = L - 2 - s;
+#pragma unroll
+        for (int kk = 0; kk < 2; ++kk) {
+            const uint64_t ad = desc0A + (uint64_t)((s * EMU_A_TILE + kk * 32) >> 4);
+            const uint64_t bd = desc0B + (uint64_t)((t * EMU_B_TILE + kk * 32) >> 4);
+            umma_bf16(d, ad, bd, idesc, (first && s == 0 && kk == 0) ? 0u : 1u);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(EMU_THREADS, 1)
+    emu_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, TcArgs a)
+{
+    extern __shared__ __align__(1024) unsigned char emu_smem_raw[];
+    unsigned char* smem =
+        reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(emu_smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + EMU_STAGES * EMU_STAGE);
+    uint64_t* empty = full + EMU_STAGES;
+    uint64_t* accf = empty + EMU_STAGES;  // chunk's MMAs complete
+    uint64_t* lo_empty = accf + 1;        // chunk's L2..L5 read
+    uint64_t* hi_empty = lo_empty + 1;    // [2]: chunk's L6, L7+8 read, by chunk parity
+    uint64_t* done = hi_empty + 2;        // every MMA of this CTA complete
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(done + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
+    volatile int* go = abort_flag + 1;                                 // outcome of the drain's wait
+    float* colscale = reinterpret_cast<float*>(smem + EMU_STAGES * EMU_STAGE + 256);  // EMU_N floats
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (*(volatile int*)&a.st->code != 0) return;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < EMU_STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(accf, 1);
+        mbar_init(lo_empty, 1);
+        mbar_init(&hi_empty[0], 1);
+        mbar_init(&hi_empty[1], 1);
+        mbar_init(done, 1);
+        *abort_flag = 0;
+        fence_barrier_init();
+        tma_prefetch_desc(&mapA);
+        tma_prefetch_desc(&mapB);
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
+                     "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_holder;
+
+    auto fail = [&](int where_info) {
+        if (*abort_flag == 0) {
+            *abort_flag = 1;
+            raise_status(a.st, OQR_ERR_TIMEOUT, where_info, TAG_MIXED);
+        }
+    };
+
+    if (warp == 0) {
+        // ------------------------------------------------ TMA producer
+        if (lane == 0) {
+            long it = 0;
+            for (int j = blockIdx.x; j < a.nitems && !*abort_flag; j += gridDim.x) {
+                const Item item = item_of(a, j);
+                for (int ks = item.ks0; ks < item.ks1 && !*abort_flag; ++ks, ++it) {
+                    const int stg = (int)(it % EMU_STAGES);
+                    const uint32_t ph = (uint32_t)((it / EMU_STAGES) & 1);
+                    if (!mbar_wait(&empty[stg], ph ^ 1u, a.limit_ns)) {
+                        fail(11);
+                        break;
+                    }
+                    unsigned char* base = smem + stg * EMU_STAGE;
+                    mbar_expect_tx(&full[stg], EMU_STAGE);
+                    for (int s = 0; s < EMU_S; ++s)
+                        tma_load_3d(base + s * EMU_A_TILE, &mapA, &full[stg], ks * EMU_KS, item.I * TM, s);
+                    for (int t = 0; t < EMU_S; ++t)
+                        tma_load_3d(base + EMU_S * EMU_A_TILE + t * EMU_B_TILE, &mapB, &full[stg], ks * EMU_KS,
+                                    item.c * EMU_N, t);
+                }
+            }
+            const long issued = it;  // copies still in flight must land before the CTA may exit
+            for (long q = issued - EMU_STAGES; q < issued; ++q)
+                if (q >= 0) mbar_wait(&full[q % EMU_STAGES], (uint32_t)((q / EMU_STAGES) & 1), a.limit_ns);
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_bf16(EMU_N);
+            long it = 0, chunk = 0;
+            bool ok = true;
+            for (int j = blockIdx.x; j < a.nitems && ok && !*abort_flag; j += gridDim.x) {
+                const Item item = item_of(a, j);
+                for (int ks = item.ks0; ks < item.ks1 && !*abort_flag; ++ks, ++it) {
+                    const int kin = ks - item.ks0;
+                    const bool cstart = kin % EMU_CH == 0;
+                    const bool cend = (kin + 1) % EMU_CH == 0 || ks + 1 == item.ks1;
+                    const int stg = (int)(it % EMU_STAGES);
+                    if (!mbar_wait(&full[stg], (uint32_t)((it / EMU_STAGES) & 1), a.limit_ns)) {
+                        fail(13);
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t base = smem_u32(smem + stg * EMU_STAGE);
+                    const uint64_t dA = smem_desc(base, 64), dB = smem_desc(base + EMU_S * EMU_A_TILE, 64);
+                    const uint32_t hi = tmem + 256u + (uint32_t)((chunk & 1) * 128);
+                    if (cstart && chunk >= 2) {  // this parity's L6, L7+8 slots: read two chunks ago
+                        if (!mbar_wait(&hi_empty[chunk & 1], (uint32_t)(((chunk - 2) >> 1) & 1), a.limit_ns)) {
+                            fail(14);
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                    }
+                    emu_issue_level<6>(hi, dA, dB, idesc, cstart);
+                    emu_issue_level<7>(hi + 64u, dA, dB, idesc, cstart);
+                    emu_issue_level<8>(hi + 64u, dA, dB, idesc, false);
+                    if (cstart && chunk >= 1) {  // L2..L5 slots: the previous chunk's must have been read
+                        if (!mbar_wait(lo_empty, (uint32_t)((chunk - 1) & 1), a.limit_ns)) {
+                            fail(15);
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                    }
+                    emu_issue_level<2>(tmem, dA, dB, idesc, cstart);
+                    emu_issue_level<3>(tmem + 64u, dA, dB, idesc, cstart);
+                    emu_issue_level<4>(tmem + 128u, dA, dB, idesc, cstart);
+                    emu_issue_level<5>(tmem + 192u, dA, dB, idesc, cstart);
+                    umma_commit(&empty[stg]);
+                    if (cend) {
+                        umma_commit(accf);
+                        ++chunk;
+                    }
+                }
+            }
+            // every MMA issued by this thread must be complete before TMEM is released
+            umma_commit(done);
+            mbar_wait(done, 0, a.limit_ns);
+        }
+    } else {
+        // ------------------------------------------------ drain (warps 2..17)
+        // One drain thread waits on the accumulator barrier (time-limited) and
+        // publishes the outcome; the drain threads then pass a named barrier
+        // together, so every exit below is taken by all of them.
+        const int dt = threadIdx.x - 64;      // 0..511 within the drain group
+        const int q = warp & 3;               // TMEM lane quarter this warp may access
+        const int g = (warp - 2) >> 2;        // column group (EMU_CPT columns)
+        const int r = q * 32 + lane;          // row within the tile = TMEM lane
+        const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(g * EMU_CPT);
+        long chunk = 0;
+        bool stop = false;
+        for (int j = blockIdx.x; j < a.nitems && !stop; j += gridDim.x) {
+            const Item item = item_of(a, j);
+            const long gi = (long)item.I * TM + r;
+            const bool row_ok = gi < a.rowsA;
+            float H[EMU_CPT], L[EMU_CPT];
+#pragma unroll
+            for (int c = 0; c < EMU_CPT; ++c) H[c] = L[c] = 0.f;
+            const int emax_r = row_ok ? a.emaxA[gi] : 0;
+            const int nsteps = item.ks1 - item.ks0;
+            const int nch = (nsteps + EMU_CH - 1) / EMU_CH;
+            for (int ch = 0; ch < nch; ++ch, ++chunk) {
+                const int kcg = (item.ks0 * EMU_KS) / KCH + ch;  // global 128-chunk index
+                if (dt == 0) {
+                    const bool okw = mbar_wait(accf, (uint32_t)(chunk & 1), a.limit_ns);
+                    if (!okw) fail(16);
+                    *go = (okw && !*abort_flag) ? 1 : 0;
+                }
+                if (dt < EMU_N) {  // column scale 2^(e_col - emax_col) of this chunk (0 if empty)
+                    const int col = item.c * EMU_N + dt;
+                    float v = 0.0f;
+                    if (col < a.colsB) {
+                        const int eb = a.eB[(size_t)kcg * a.colsB + col];
+                        if (eb != EXP_NONE) v = pow2f(eb - a.emaxB[col]);
+                    }
+                    colscale[dt] = v;
+                }
+                asm volatile("bar.sync 1, 512;" ::: "memory");
+                if (*go == 0) {
+                    stop = true;
+                    break;
+                }
+                tc_fence_after();
+                // row scale 2^(e_row - emax_row - 14): x y = 2^(e_r + e_c - 14) sum of the slice products
+                const int e_r = row_ok ? a.eA[(size_t)kcg * a.rowsA + gi] : EXP_NONE;
+                const float rs = e_r == EXP_NONE ? 0.0f : pow2f(e_r - emax_r - 14);
+                float sc[EMU_CPT];
+#pragma unroll
+                for (int c = 0; c < EMU_CPT; ++c) sc[c] = __fmul_rn(rs, colscale[g * EMU_CPT + c]);  // exact
+                // L2..L5: exact level sums, added into (H, L) by TwoSum
+#pragma unroll
+                for (int lv = 0; lv < 4; ++lv) {
+                    uint32_t v[EMU_CPT];
+                    tmem_ld16(lane_addr + (uint32_t)(lv * 64), v);
+#pragma unroll
+                    for (int c = 0; c < EMU_CPT; ++c) {
+                        const float t = __fmul_rn(__uint_as_float(v[c]), sc[c]);
+                        const float sm = __fadd_rn(H[c], t);
+                        const float bp = __fsub_rn(sm, H[c]);
+                        const float err = __fadd_rn(__fsub_rn(H[c], __fsub_rn(sm, bp)), __fsub_rn(t, bp));
+                        H[c] = sm;
+                        L[c] = __fadd_rn(L[c], err);
+                    }
+                }
+                tc_fence_before();
+                asm volatile("bar.sync 1, 512;" ::: "memory");  // L2..L5 fully read
+                if (dt == 0) mbar_arrive(lo_empty);
+                // L6 and L7+8: below 2^-29 of the chunk's scale, added into the low part
+                const uint32_t hi = lane_addr + 256u + (uint32_t)((chunk & 1) * 128);
+                uint32_t v6[EMU_CPT], v78[EMU_CPT];
+                tmem_ld16x2(hi, hi + 64u, v6, v78);
+#pragma unroll
+                for (int c = 0; c < EMU_CPT; ++c) {
+                    L[c] = fmaf(__fadd_rn(__uint_as_float(v6[c]), __uint_as_float(v78[c])), sc[c], L[c]);
+                    const float sm = __fadd_rn(H[c], L[c]);  // renormalise (Fast2Sum)
+                    L[c] = __fsub_rn(L[c], __fsub_rn(sm, H[c]));
+                    H[c] = sm;
+                }
+                tc_fence_before();
+                asm volatile("bar.sync 1, 512;" ::: "memory");  // L6, L7+8 and colscale fully read
+                if (dt == 0) mbar_arrive(&hi_empty[chunk & 1]);
+            }
+            if (stop) break;
+            // H + L (exact in FP64) times 2^(emax_row + emax_col), into this item's FP64 slot; the FP64
+            // work overlaps the MMAs of the next item
+            double* slot = a.slots + (size_t)j * TM * EMU_N + (size_t)r * EMU_N + g * EMU_CPT;
+#pragma unroll
+            for (int c = 0; c < EMU_CPT; ++c) {
+                const int col = item.c * EMU_N + g * EMU_CPT + c;
+                const int ec = col < a.colsB ? __ldg(a.emaxB + col) : EXP_NONE;
+                const int k = emax_r + ec;
+                const double hl = (double)H[c] + (double)L[c];
+                double out = 0.0;
+                if (row_ok && emax_r != EXP_NONE && ec != EXP_NONE)
+                    out = (k >= -1022 && k <= 1023) ? hl * __longlong_as_double((long long)(k + 1023) << 52)
+                                                    : ldexp(hl, k);
+                slot[c] = out;
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+    }
+}
+
 // ------------------------------------------------------------ host side ----
 bool make_map_3d(CUtensorMap* map, const void* base, long kext, long rows, long ldp, size_t plane_bytes, int S,
                  int box_k, int box_rows, int elem_bytes);
@@ -820,6 +1101,21 @@ cudaError_t launch_tc(const TcArgs& a0, const void* planesA, long ldpA, size_t p
     return cudaGetLastError();
 }
 
+
+cudaError_t launch_emu(const TcArgs& a0, const void* planesA, long ldpA, size_t planeA, const void* planesB, long ldpB,
+                       size_t planeB, int sms, cudaStream_t s)
+{
+    TcArgs a = a0;
+    CUtensorMap mA{}, mB{};
+    if (!make_map_3d(&mA, planesA, a.K, a.rowsA, ldpA, planeA * 2, EMU_S, EMU_KS, TM, 2)) return cudaErrorInvalidValue;
+    if (!make_map_3d(&mB, planesB, a.K, a.colsB, ldpB, planeB * 2, EMU_S, EMU_KS, EMU_N, 2))
+        return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(emu_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EMU_SMEM);
+    if (e != cudaSuccess) return e;
+    const int grid = a.nitems < sms ? a.nitems : sms;
+    if (grid > 0) emu_kernel<<<grid, EMU_THREADS, EMU_SMEM, s>>>(mA, mB, a);
+    return cudaGetLastError();
+}
 }  // namespace
 
 // -------------------------------------------------------- public (internal) API
@@ -897,7 +1193,7 @@ void launch_splits_tall(dim3 g, cudaStream_t s, int K, int C, const double* X, l
 cudaError_t launch_tc_mode(const TcPlan& p, const TcArgs& a, const void* PA, size_t planeA, const void* PB,
                            size_t planeB, int sms, cudaStream_t s)
 {
-    if (p.mode == 1) return launch_tc<32, 64, 7, 1>(a, PA, p.ldp, planeA, PB, p.ldp, planeB, sms, s);
+    if (p.mode == 1) return launch_emu(a, PA, p.ldp, planeA, PB, p.ldp, planeB, sms, s);
     if (p.mode == 2) {
         if (p.N == 64) return launch_tc<128, 64, 1, 2>(a, PA, p.ldp, planeA, PB, p.ldp, planeB, sms, s);
         return launch_tc<128, 128, 1, 2>(a, PA, p.ldp, planeA, PB, p.ldp, planeB, sms, s);

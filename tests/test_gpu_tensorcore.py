@@ -91,6 +91,26 @@ def test_tc_gram_fp64tc_exact_integers(env):
     assert np.array_equal(G, Z.T @ A @ Z)
 
 
+@pytest.mark.parametrize("m,n", [(700, 24), (520, 80)])
+def test_tc_gram_fp64tc_near_exact(env, m, n):
+    # Held to Z^T A Z formed in extended precision (np.longdouble: 64- or 113-bit
+    # significand), not to the FP64 oracle: the slices keep 55 bits of each
+    # element relative to its 128-chunk maximum and the chunk sums are exact, so
+    # what remains is the double-float (about 2^-48) accumulation of U = M Z and
+    # C = Z^T U and the final FP64 sum.  Several 128-chunks, a ragged tail, and
+    # two column chunks of 64 at n = 80.
+    torch, oqr, ctx = env
+    A, Z = inputs.paper_case(4, m, n, 1e6, 1e3, seed=m + 7 * n)
+    G = ctx.oqr_gram(dev(torch, oqr, A), dev(torch, oqr, Z), prec=oqr.OQR_FP64_TC).cpu().numpy()
+    Ml = lower_m(A).astype(np.longdouble)
+    Zl = Z.astype(np.longdouble)
+    C = Zl.T @ (Ml @ Zl)
+    Gx = C + C.T
+    scale = np.abs(Z).T @ np.abs(A) @ np.abs(Z)
+    err = np.max(np.abs((G.astype(np.longdouble) - Gx) / scale))
+    assert err <= 2.0 ** -44, err
+
+
 @pytest.mark.parametrize("prec,final", [(3, 3), (1, 3), (0, 3)])
 def test_mixed_cholqr2_parity(env, prec, final):
     torch, oqr, ctx = env
