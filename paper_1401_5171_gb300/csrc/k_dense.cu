@@ -15,9 +15,9 @@ namespace {
 // (Algorithm 1, line 3).  Right-looking, 32-column panels, one SM's FP64 rate
 // being far too low for n^3/3 flops on a single CTA: per panel
 //   potrf_diag  (1 CTA)   factor the 32 x 32 diagonal block in shared memory;
-//   potrf_row   (n/32 CTAs) solve the panel row R(p, c) <- D^{-T} R(p, c);
+//   potrf_row   (CTAs of 16 columns) solve the panel row R(p, c) <- D^{-T} R(p, c);
 //   potrf_trail (tiles)   R(r, c) -= sum_k R(p_k, r) R(p_k, c) on the trailing
-//                         upper triangle, 32 x 32 tiles.
+//                         upper triangle, 16 x 16 tiles.
 // A pivot that is not positive (or NaN) stops the factorization: the status
 // word records OQR_ERR_NOT_SPD with the 1-based column and every later launch
 // returns at once.
@@ -38,74 +38,86 @@ __global__ void potrf_init_kernel(int n, const double* __restrict__ G, long ldg,
     R[i + j * ldr] = v;
 }
 
-__global__ void __launch_bounds__(32) potrf_diag_kernel(int n, int jb, double* R, long ldr, DevStatus* st)
+// Diagonal block of panel jb: one thread per element of the 32 x 32 block D
+// (thread (ty, tx) owns D[ty][tx], ty <= tx).  Step j reads the pivot
+// p = D[j][j] (every thread computes 1/p itself), writes row j of R as
+// D[j][c] / sqrt(p), and updates D[r][c] -= (D[j][r] / p) D[j][c] for
+// j < r <= c; one barrier per step.  The pivot chain is the critical path of
+// the whole factorization, so nothing else waits on the square root.
+__global__ void __launch_bounds__(1024) potrf_diag_kernel(int n, int jb, double* R, long ldr, DevStatus* st)
 {
     __shared__ double D[PNB][PNB + 1];
     if (*(volatile int*)&st->code != 0) return;
-    const int lane = threadIdx.x;
     const int nb = min(PNB, n - jb);
-    for (int e = lane; e < nb * nb; e += 32) {
-        const int i = e % nb, j = e / nb;
-        D[i][j] = (i <= j) ? R[(jb + i) + (long)(jb + j) * ldr] : 0.0;
-    }
-    __syncwarp();
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const bool mine = ty < nb && tx < nb && ty <= tx;
+    if (mine) D[ty][tx] = R[(jb + ty) + (long)(jb + tx) * ldr];
+    __syncthreads();
     for (int j = 0; j < nb; ++j) {
         const double piv = D[j][j];
-        if (!(piv > 0.0)) {  // the same value in every lane: a uniform exit
-            if (lane == 0) raise_status(st, OQR_ERR_NOT_SPD, jb + j + 1, TAG_POTRF);
+        if (!(piv > 0.0)) {  // the same value in every thread: a uniform exit
+            if (threadIdx.x == 0) raise_status(st, OQR_ERR_NOT_SPD, jb + j + 1, TAG_POTRF);
             return;
         }
-        const double d = sqrt(piv);
-        __syncwarp();
-        if (lane == 0) D[j][j] = d;
-        for (int c = j + 1 + lane; c < nb; c += 32) D[j][c] /= d;
-        __syncwarp();
-        for (int c = j + 1 + lane; c < nb; c += 32) {
-            const double djc = D[j][c];
-            for (int r = j + 1; r <= c; ++r) D[r][c] -= D[j][r] * djc;
+        if (ty == j && mine) R[(jb + j) + (long)(jb + tx) * ldr] = tx == j ? sqrt(piv) : D[j][tx] / sqrt(piv);
+        if (ty > j && mine) {
+            const double pinv = 1.0 / piv;
+            D[ty][tx] -= (D[j][ty] * pinv) * D[j][tx];
         }
-        __syncwarp();
-    }
-    for (int e = lane; e < nb * nb; e += 32) {
-        const int i = e % nb, j = e / nb;
-        if (i <= j) R[(jb + i) + (long)(jb + j) * ldr] = D[i][j];
+        __syncthreads();
     }
 }
 
-// One thread per trailing column c: forward substitution with D^T (D upper).
-__global__ void __launch_bounds__(128) potrf_row_kernel(int n, int jb, double* R, long ldr, const DevStatus* st)
+// Panel row: R(p, c) <- R(p, p)^{-T} R(p, c) for the trailing columns c, one
+// thread per column (column-oriented substitution with the reciprocals of
+// the diagonal); PROW_COLS columns per CTA spread the FP64 work over SMs.
+constexpr int PROW_COLS = 16;
+__global__ void __launch_bounds__(PROW_COLS) potrf_row_kernel(int n, int jb, double* R, long ldr,
+                                                              const DevStatus* st)
 {
     __shared__ double D[PNB][PNB + 1];
+    __shared__ double dinv[PNB];
     if (*(volatile const int*)&st->code != 0) return;
     const int nb = min(PNB, n - jb);
-    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
-        const int i = e % nb, j = e / nb;
-        D[i][j] = (i <= j) ? R[(jb + i) + (long)(jb + j) * ldr] : 0.0;
+    for (int e = threadIdx.x; e < PNB * PNB; e += PROW_COLS) {
+        const int i = e % PNB, j = e / PNB;
+        D[i][j] = (i <= j && i < nb && j < nb) ? R[(jb + i) + (long)(jb + j) * ldr] : 0.0;
     }
     __syncthreads();
-    const int c = jb + nb + blockIdx.x * blockDim.x + threadIdx.x;
+    for (int i = threadIdx.x; i < nb; i += PROW_COLS) dinv[i] = 1.0 / D[i][i];
+    __syncthreads();
+    const int c = jb + nb + blockIdx.x * PROW_COLS + threadIdx.x;
     if (c >= n) return;
-    double x[PNB];
+    double* col = R + jb + (long)c * ldr;
+    double b[PNB];
+#pragma unroll
+    for (int i = 0; i < PNB; ++i) b[i] = i < nb ? col[i] : 0.0;
 #pragma unroll
     for (int i = 0; i < PNB; ++i) {
         if (i < nb) {
-            double t = R[(jb + i) + (long)c * ldr];
-            for (int k = 0; k < i; ++k) t -= D[k][i] * x[k];
-            x[i] = t / D[i][i];
-            R[(jb + i) + (long)c * ldr] = x[i];
+            asm volatile("" ::: "memory");  // keeps only row i of D live: no hoisted loads, no spills
+            b[i] *= dinv[i];
+#pragma unroll
+            for (int k = i + 1; k < PNB; ++k) b[k] -= D[i][k] * b[i];
         }
     }
+#pragma unroll
+    for (int i = 0; i < PNB; ++i)
+        if (i < nb) col[i] = b[i];
 }
 
-// Trailing update on 32 x 32 tiles (tr <= tc) of the upper triangle right of the panel.
-__global__ void __launch_bounds__(256) potrf_trail_kernel(int n, int jb, double* R, long ldr, const DevStatus* st)
+// Trailing update on TT x TT tiles (tr <= tc) of the upper triangle right of
+// the panel: R(r, c) -= sum_k R(p_k, r) R(p_k, c); one thread per element.
+constexpr int TT = 16;
+__global__ void __launch_bounds__(TT * TT) potrf_trail_kernel(int n, int jb, double* R, long ldr,
+                                                              const DevStatus* st)
 {
-    __shared__ double Pr[PNB][PNB + 1];  // panel rows, tile's row columns
-    __shared__ double Pc[PNB][PNB + 1];  // panel rows, tile's columns
+    __shared__ double Pr[PNB][TT + 1];  // panel rows, tile's row columns
+    __shared__ double Pc[PNB][TT + 1];  // panel rows, tile's columns
     if (*(volatile const int*)&st->code != 0) return;
     const int nb = min(PNB, n - jb);
     const int t0 = jb + nb;
-    const int nt = (n - t0 + PNB - 1) / PNB;
+    const int nt = (n - t0 + TT - 1) / TT;
     // blockIdx.x enumerates the upper-triangular tile pairs (tr <= tc)
     int tr = 0, rem = blockIdx.x;
     while (rem >= nt - tr) {
@@ -113,21 +125,23 @@ __global__ void __launch_bounds__(256) potrf_trail_kernel(int n, int jb, double*
         ++tr;
     }
     const int tc = tr + rem;
-    const int r0 = t0 + tr * PNB, c0 = t0 + tc * PNB;
-    for (int e = threadIdx.x; e < PNB * PNB; e += blockDim.x) {
+    const int r0 = t0 + tr * TT, c0 = t0 + tc * TT;
+    for (int e = threadIdx.x; e < PNB * TT; e += TT * TT) {
         const int k = e % PNB, j = e / PNB;
         Pr[k][j] = (k < nb && r0 + j < n) ? R[(jb + k) + (long)(r0 + j) * ldr] : 0.0;
         Pc[k][j] = (k < nb && c0 + j < n) ? R[(jb + k) + (long)(c0 + j) * ldr] : 0.0;
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < PNB * PNB; e += blockDim.x) {
-        const int i = e % PNB, j = e / PNB;
-        const int r = r0 + i, c = c0 + j;
-        if (r >= n || c >= n || r > c) continue;
-        double s = R[r + (long)c * ldr];
-        for (int k = 0; k < nb; ++k) s -= Pr[k][i] * Pc[k][j];
-        R[r + (long)c * ldr] = s;
+    const int i = threadIdx.x % TT, j = threadIdx.x / TT;
+    const int r = r0 + i, c = c0 + j;
+    if (r >= n || c >= n || r > c) return;
+    double s0 = R[r + (long)c * ldr], s1 = 0.0;
+    for (int k = 0; k + 1 < nb; k += 2) {
+        s0 -= Pr[k][i] * Pc[k][j];
+        s1 -= Pr[k + 1][i] * Pc[k + 1][j];
     }
+    if (nb & 1) s0 -= Pr[nb - 1][i] * Pc[nb - 1][j];
+    R[r + (long)c * ldr] = s0 + s1;
 }
 
 // ----------------------------------------------------------------- TRSM ----
@@ -448,12 +462,12 @@ cudaError_t launch_potrf(int n, const double* G, long ldg, double* R, long ldr, 
     const long total = (long)n * n;
     potrf_init_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(n, G, ldg, R, ldr, shift_ptr, st);
     for (int jb = 0; jb < n; jb += PNB) {
-        potrf_diag_kernel<<<1, 32, 0, s>>>(n, jb, R, ldr, st);
+        potrf_diag_kernel<<<1, 1024, 0, s>>>(n, jb, R, ldr, st);
         const int rest = n - jb - PNB;
         if (rest <= 0) break;
-        potrf_row_kernel<<<(rest + 127) / 128, 128, 0, s>>>(n, jb, R, ldr, st);
-        const int nt = (rest + PNB - 1) / PNB;
-        potrf_trail_kernel<<<nt * (nt + 1) / 2, 256, 0, s>>>(n, jb, R, ldr, st);
+        potrf_row_kernel<<<(rest + PROW_COLS - 1) / PROW_COLS, PROW_COLS, 0, s>>>(n, jb, R, ldr, st);
+        const int nt = (rest + TT - 1) / TT;
+        potrf_trail_kernel<<<nt * (nt + 1) / 2, TT * TT, 0, s>>>(n, jb, R, ldr, st);
     }
     return cudaGetLastError();
 }
