@@ -4,9 +4,10 @@
 One step = one oblique QR factorization (Z = Q R, Q^T A Q = I) of the
 single large instance m=32768, n=256 with kappa(A)=1e6 and kappa(Z)=1e2
 (dense SPD A, lower triangle read), through the library's C ABI.  The
-headline path is the mixed A-CholQR2 (a BF16X3 pass, then an FP64-accurate
-pass, both on the tensor cores); the FP64 (DFMA) and the all-FP64-accurate
-tensor-core paths are timed beside it.  Each path's ||Q^T A Q - I||_2 is
+headline path is the mixed A-CholQR2 (a TC2 pass on the two leading slices,
+then an FP64-accurate pass, both on the tensor cores, A split once); the FP64
+(DFMA), the all-FP64-accurate tensor-core and the BF16X3-first paths are
+timed beside it.  Each path's ||Q^T A Q - I||_2 is
 measured on the timed configuration.  Inputs are synthetic (the Sec. 7
 recipe; A is 8.6 GB, larger than L2, so no flush is needed between steps).
 
@@ -44,7 +45,7 @@ def parse():
     p.add_argument("--n", type=int, default=256)
     p.add_argument("--kappa-a", type=float, default=1e6)
     p.add_argument("--kappa-z", type=float, default=1e2)
-    p.add_argument("--path", default="mixed", choices=["mixed", "fp64tc", "fp64", "scholqr3", "cgs2"])
+    p.add_argument("--path", default="mixed", choices=["mixed", "mixed_bf16x3", "fp64tc", "fp64", "scholqr3", "cgs2"])
     p.add_argument("--no-side-paths", action="store_true", help="time only the headline path")
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -221,8 +222,11 @@ def run_reference(args, rank, world):
 
 PATHS = {
     # name: (entry point, options, normal-equation passes, description)
-    "mixed": ("oqr_cholqr2", {"prec": 1, "final_prec": 3}, 2,
-              "A-CholQR2: BF16X3 pass, then FP64-accurate pass, both on tcgen05 tensor cores"),
+    "mixed": ("oqr_cholqr2", {"prec": 4, "final_prec": 3}, 2,
+              "A-CholQR2: TC2 pass (two leading FP64-accurate slices), then FP64-accurate pass, both on tcgen05 "
+              "tensor cores, one split of A shared by both passes"),
+    "mixed_bf16x3": ("oqr_cholqr2", {"prec": 1, "final_prec": 3}, 2,
+                     "A-CholQR2: BF16X3 pass, then FP64-accurate pass, both on tcgen05 tensor cores"),
     "fp64tc": ("oqr_cholqr2", {"prec": 3, "final_prec": 3}, 2,
                "A-CholQR2: two FP64-accurate tensor-core passes"),
     "fp64": ("oqr_cholqr2", {}, 2, "A-CholQR2: two FP64 DFMA passes"),
@@ -231,20 +235,28 @@ PATHS = {
 }
 
 
-def launches_per_step(path):
-    """Kernels the library launches for one factorization (counted from oqr_api.cu / k_tc.cu)."""
+def launches_per_step(path, n):
+    """Kernels the library launches for one factorization, counted from the launch
+    sequence in oqr_api.cu, k_tc.cu and k_dense.cu (checked against ncu launch lists)."""
     name, kw, passes, _ = PATHS[path]
     if name == "oqr_cgs2":
         return None
-    per_pass = []
+    panels = (n + 31) // 32
+    potrf = 1 + panels + 2 * (panels - 1)        # init, then diag (+ row + trailing update) per panel
+    total, a_split_held = 0, False
     for p in range(passes):
         prec = kw.get("final_prec", 0) if p == passes - 1 else kw.get("prec", 0)
-        gram = 2 if prec == 0 else (9 + (3 if prec == 3 else 0))
-        per_pass.append(gram + 2)  # + potrf + trsm
-    extra = passes if passes > 1 else 0          # R copy + (passes - 1) products
+        if prec == 0:
+            gram = 2                                 # FP64 Gram + reduce
+        else:
+            shared = prec in (3, 4) and a_split_held  # the EMU64-family split of A is reused
+            gram = 10 + (0 if prec == 1 else 2 if shared else 3) - (1 if shared else 0)
+            a_split_held = prec in (3, 4)
+        total += gram + potrf + 1                    # + TRSM
+    total += passes if passes > 1 else 0             # R copy + (passes - 1) products
     if kw.get("shifted"):
-        extra += 2                               # norms + shift
-    return sum(per_pass) + extra
+        total += 2                                   # norms + shift
+    return total
 
 
 def tc_u_flops(m, n):
@@ -325,7 +337,7 @@ def main():
     clocks = clk.summary()
     others = {}
     if not args.no_side_paths:
-        for p in ("fp64", "fp64tc", "mixed"):
+        for p in ("fp64", "fp64tc", "mixed", "mixed_bf16x3"):
             if p != args.path:
                 others[p] = run(p, 2, 1)
 
@@ -337,7 +349,7 @@ def main():
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except OSError:
         pass
-    if args.path in ("mixed", "fp64tc"):
+    if args.path in ("mixed", "mixed_bf16x3", "fp64tc"):
         reps = 3
         ctx.oqr_gram_phases(A, Z, 3, G=G, stream=stream)
         u_ms = []
@@ -351,7 +363,8 @@ def main():
                     "frac": achieved / peak,
                     "traffic": ncu_traffic("tc_emu_u_m32768_n256", ["paper_1401_5171_gb300/csrc/k_tc.cu"])
                     if (m, n) == (32768, 256) else None,
-                    "kernel": "tc_kernel<32,64,7,EMU> (U = M Z, 28 BF16 slice products, tcgen05 kind::f16)",
+                    "kernel": "emu_kernel (U = M Z: 28 BF16 slice products into 6 TMEM level accumulators, "
+                              "tcgen05 kind::f16, N = 64)",
                     "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst; kernel timed alone), of measured",
                     "launch_ms": t * 1e3, "phases_ms": ph}
     else:
@@ -420,7 +433,7 @@ def main():
                "sample": f"oracle CHOL-EQR once on m={msamp}, n={nsamp} (same recipe, {secs:.1f} s); QRs/s "
                          f"scaled to m={m}, n={n} by its flop model m^3/3 + 2 m^2 n + 2 m n^2"}
 
-    lps = launches_per_step(args.path)
+    lps = launches_per_step(args.path, n)
     line = {"metric": METRIC, "value": head["qr_per_s"], "unit": "QR/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": head["ms_per_qr"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_of(args),

@@ -53,9 +53,14 @@ typedef enum {
 typedef enum {
     OQR_FP64 = 0,     /* every product in FP64 (DFMA) */
     OQR_BF16X3 = 1,   /* hi/lo BF16 split, 3 products, FP32 accumulation (tensor cores) */
-    OQR_FP8 = 2,      /* E4M3 with power-of-two block scales (not in this build: OQR_ERR_UNSUPPORTED) */
-    OQR_FP64_TC = 3   /* FP64-accurate products from 7 exact BF16 slices per operand, exact FP32
+    OQR_FP8 = 2,      /* E4M3 with a power-of-two scale per (row or column, 128-long chunk of the
+                         contraction), one product, drained and scaled every chunk (tensor cores) */
+    OQR_FP64_TC = 3,  /* FP64-accurate products from 7 exact BF16 slices per operand, exact FP32
                          accumulation per 128-long chunk, double-float sum (tensor cores) */
+    OQR_TC2 = 4       /* the 2 leading slices of the OQR_FP64_TC split (16 bits of each element
+                         relative to its 128-chunk's largest magnitude), 3 products per chunk in FP32,
+                         scaled every chunk (tensor cores).  Within one factorization, passes in
+                         OQR_TC2 and OQR_FP64_TC (and an opts->check = 2) split A once and share it. */
 } oqr_precision;
 
 typedef enum { OQR_ALGO_CHOLQR = 0, OQR_ALGO_CHOLQR2 = 1, OQR_ALGO_SCHOLQR3 = 2, OQR_ALGO_CGS2 = 3 } oqr_algo;
@@ -70,7 +75,8 @@ typedef struct {
     int check;        /* measure ||Q^T A Q - I||_2 after the factorization into info->orth_err [0]:
                          1 = with an FP64 Gram, 2 = with the FP64-accurate tensor-core Gram */
     long spin_limit;  /* time limit of any device-side wait, in nanoseconds [4e9] */
-    int final_prec;   /* oqr_cholqr2: oqr_precision of the last pass [OQR_FP64]; OQR_FP64 or OQR_FP64_TC */
+    int final_prec;   /* oqr_cholqr2: oqr_precision of the last pass [OQR_FP64]; the last pass sets the
+                         final orthogonality, so FP64-level results need OQR_FP64 or OQR_FP64_TC */
     int prec_mid;     /* passes between the first and the last: oqr_precision, or -1 = same as prec [-1] */
 } oqr_opts;
 
@@ -164,7 +170,7 @@ oqr_status oqr_cgs2(oqr_ctx* ctx, int m, int n, const double* A, long lda, const
  *
  * oqr_gram: G = Z^T A Z (lines 1-2 of Algorithm 1), n x n, written in full
  *   and exactly symmetric.  prec selects the arithmetic of the products:
- *   OQR_FP64 (DFMA), OQR_BF16X3 or OQR_FP64_TC (tensor cores).
+ *   OQR_FP64 (DFMA), or OQR_BF16X3, OQR_FP8, OQR_FP64_TC, OQR_TC2 (tensor cores).
  * oqr_potrf: R = chol(G + shift I) (line 3), G read from its lower triangle,
  *   R upper with positive diagonal, zeros below.  Breakdown is reported as
  *   OQR_ERR_NOT_SPD with the 1-based column (synchronizes the stream when

@@ -203,18 +203,75 @@ __device__ inline unsigned long long warp_max_u64(unsigned long long v)
     return v;
 }
 
+// Slices of one element for chunk exponent e (MODE 1: S exact BF16 slices,
+// pre-scaled; MODE 0: BF16 hi/lo).
+template <int MODE>
+__device__ inline void slice_element(double x, int e, int S, float* sl)
+{
+    (void)S;
+    if constexpr (MODE == 0) {
+        __nv_bfloat16 hi, lo;
+        bf16x2_split(x, hi, lo);
+        sl[0] = __bfloat162float(hi);
+        sl[1] = __bfloat162float(lo);
+    } else {
+        if (e == EXP_NONE) {
+#pragma unroll
+            for (int t = 0; t < 7; ++t) sl[t] = 0.f;
+        } else {
+            emu_slices7(x, e, sl);
+        }
+    }
+}
+
+// Writes four consecutive plane elements (k .. k+3) of every slice: one 8-byte
+// (BF16) or 4-byte (E4M3) store per plane.
+template <int MODE>
+__device__ inline void store4(__nv_bfloat16* planes, size_t plane, size_t off, int S, const double* v, int e)
+{
+    if constexpr (MODE == 2) {
+        uchar4 q;
+        q.x = e == EXP_NONE ? 0 : e4m3_code(v[0], e);
+        q.y = e == EXP_NONE ? 0 : e4m3_code(v[1], e);
+        q.z = e == EXP_NONE ? 0 : e4m3_code(v[2], e);
+        q.w = e == EXP_NONE ? 0 : e4m3_code(v[3], e);
+        *reinterpret_cast<uchar4*>(reinterpret_cast<unsigned char*>(planes) + off) = q;
+    } else {
+        float sl[4][7];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) slice_element<MODE>(v[j], e, S, sl[j]);
+        const int np = MODE == 0 ? 2 : S;
+#pragma unroll
+        for (int t = 0; t < 7; ++t) {
+            if (t < np) {
+                __nv_bfloat162 lo2 = __floats2bfloat162_rn(sl[0][t], sl[1][t]);  // exact: at most 8 significant bits
+                __nv_bfloat162 hi2 = __floats2bfloat162_rn(sl[2][t], sl[3][t]);
+                uint2 w;
+                w.x = *reinterpret_cast<unsigned int*>(&lo2);
+                w.y = *reinterpret_cast<unsigned int*>(&hi2);
+                *reinterpret_cast<uint2*>(planes + t * plane + off) = w;
+            }
+        }
+    }
+}
+
 // A (m x m, column-major, lower triangle) -> slices of M = tril(A,-1) + diag(A)/2,
-// written row-major (row i, k contiguous): planes + s*plane + i*ldp + k.
-// One CTA: 32 rows x one 128-column chunk; 8 warps.
-// MODE 0: BF16 hi/lo planes; 1: seven exact BF16 slices; 2: one FP8 E4M3 plane
-// (bytes).  Modes 1 and 2 record the chunk exponent of every row.
+// written row-major (row i, k contiguous): planes + s*plane + i*ldp + k, ldp a
+// multiple of 128 (the row is written up to its 128-chunk's end).
+// One CTA: 32 rows x one 128-column chunk; 8 warps.  The tile is transposed
+// through shared memory stored as T[row][(k % 4) * 33 + k / 4], so that lane l
+// reads k = 4l .. 4l+3 of a row without bank conflicts and writes them with
+// one vector store per plane.
+// MODE 0: BF16 hi/lo planes; 1: S exact BF16 slices (S <= 7); 2: one FP8 E4M3
+// plane (bytes).  Modes 1 and 2 record the chunk exponent of every row.
+constexpr int TPAD = 4 * 33 + 1;
 template <int MODE>
 __global__ void __launch_bounds__(256) split_lower_kernel(int m, const double* __restrict__ A, long lda, int S,
                                                           __nv_bfloat16* planes, long ldp, size_t plane,
                                                           int* eA, int* emax)
 {
-    constexpr bool EMU = MODE != 0;  // exponents are recorded
-    __shared__ double T[32][KCH + 1];
+    constexpr bool SCALED = MODE != 0;  // exponents are recorded
+    __shared__ double T[32][TPAD];
     const int kc = blockIdx.x, ib = blockIdx.y;
     const long row0 = (long)ib * 32, col0 = (long)kc * KCH;
     if (row0 >= m || col0 > row0 + 31) return;
@@ -226,7 +283,7 @@ __global__ void __launch_bounds__(256) split_lower_kernel(int m, const double* _
             v = A[i + kk * lda];
             if (kk == i) v *= 0.5;  // one FP64 multiply per diagonal element
         }
-        T[lane][k] = v;
+        T[lane][(k & 3) * 33 + (k >> 2)] = v;
     }
     __syncthreads();
     for (int r = w * 4; r < w * 4 + 4; ++r) {
@@ -236,99 +293,51 @@ __global__ void __launch_bounds__(256) split_lower_kernel(int m, const double* _
         unsigned long long key = 0;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            v[j] = T[r][lane + 32 * j];
+            v[j] = T[r][j * 33 + lane];  // k = 4 lane + j
             const unsigned long long kj = mag_key(v[j]);
             key = kj > key ? kj : key;
         }
         key = warp_max_u64(key);
-        const int e = EMU ? chunk_exponent_key(key) : 0;
-        if (EMU && lane == 0) {
+        const int e = SCALED ? chunk_exponent_key(key) : 0;
+        if (SCALED && lane == 0) {
             eA[(size_t)kc * m + i] = e;
             if (e != EXP_NONE) atomicMax(&emax[i], e);
         }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const long k = col0 + lane + 32 * j;
-            if (k >= m) continue;
-            if (MODE == 2) {
-                reinterpret_cast<unsigned char*>(planes)[i * ldp + k] = e == EXP_NONE ? 0 : e4m3_code(v[j], e);
-                continue;
-            }
-            __nv_bfloat16* dst = planes + i * ldp + k;
-            if (EMU) {
-                float sl[7];
-                if (e == EXP_NONE) {
-#pragma unroll
-                    for (int s = 0; s < 7; ++s) sl[s] = 0.f;
-                } else {
-                    emu_slices7(v[j], e, sl);
-                }
-#pragma unroll
-                for (int s = 0; s < 7; ++s) dst[s * plane] = __float2bfloat16_rn(sl[s]);
-            } else {
-                __nv_bfloat16 hi, lo;
-                bf16x2_split(v[j], hi, lo);
-                dst[0] = hi;
-                dst[plane] = lo;
-            }
-        }
+        const size_t off = (size_t)i * ldp + col0 + 4 * lane;
+        store4<MODE>(planes, plane, off, S, v, e);
     }
 }
 
 // X (K x C, column-major) -> slices written column-major (column c, k
-// contiguous): planes + s*plane + c*ldp + k.  One warp per (chunk, column).
+// contiguous, ldp a multiple of 128): planes + s*plane + c*ldp + k.  One warp
+// per (chunk, column); lane l handles k = 4l .. 4l+3.
 template <int MODE>
 __global__ void __launch_bounds__(256) split_tall_kernel(int K, int C, const double* __restrict__ X, long ldx, int S,
                                                          __nv_bfloat16* planes, long ldp, size_t plane, int* eX,
                                                          int* xmax)
 {
-    constexpr bool EMU = MODE != 0;  // exponents are recorded
+    constexpr bool SCALED = MODE != 0;  // exponents are recorded
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int kc = blockIdx.x;
     const long c = (long)blockIdx.y * 8 + w;
     if (c >= C) return;
-    const long k0 = (long)kc * KCH;
+    const long k0 = (long)kc * KCH + 4 * lane;
     double v[4];
     unsigned long long key = 0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        const long k = k0 + lane + 32 * j;
+        const long k = k0 + j;
         v[j] = k < K ? X[k + c * ldx] : 0.0;
         const unsigned long long kj = mag_key(v[j]);
         key = kj > key ? kj : key;
     }
     key = warp_max_u64(key);
-    const int e = EMU ? chunk_exponent_key(key) : 0;
-    if (EMU && lane == 0) {
+    const int e = SCALED ? chunk_exponent_key(key) : 0;
+    if (SCALED && lane == 0) {
         eX[(size_t)kc * C + c] = e;
         if (e != EXP_NONE) atomicMax(&xmax[c], e);
     }
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const long k = k0 + lane + 32 * j;
-        if (k >= K) continue;
-        if (MODE == 2) {
-            reinterpret_cast<unsigned char*>(planes)[c * ldp + k] = e == EXP_NONE ? 0 : e4m3_code(v[j], e);
-            continue;
-        }
-        __nv_bfloat16* dst = planes + c * ldp + k;
-        if (EMU) {
-            float sl[7];
-            if (e == EXP_NONE) {
-#pragma unroll
-                for (int s = 0; s < 7; ++s) sl[s] = 0.f;
-            } else {
-                emu_slices7(v[j], e, sl);
-            }
-#pragma unroll
-            for (int s = 0; s < 7; ++s) dst[s * plane] = __float2bfloat16_rn(sl[s]);
-        } else {
-            __nv_bfloat16 hi, lo;
-            bf16x2_split(v[j], hi, lo);
-            dst[0] = hi;
-            dst[plane] = lo;
-        }
-    }
+    store4<MODE>(planes, plane, (size_t)c * ldp + k0, S, v, e);
 }
 
 __global__ void fill_int_kernel(int* p, long n, int v)
@@ -483,8 +492,9 @@ __device__ inline float pow2f(int d)
 }
 
 // ---------------------------------------------------------- the kernel ----
-// BF16X3 (MODE 0) and FP8 E4M3 with chunk scales (MODE 2); the FP64-accurate
-// emulation has its own kernel below (emu_kernel).
+// BF16X3 (MODE 0), FP8 E4M3 with chunk scales (MODE 2) and TC2 (MODE 3: the
+// two leading pre-scaled EMU64 slices, three products, chunk scales); the
+// FP64-accurate emulation has its own kernel below (emu_kernel).
 template <int KS, int N, int S, int MODE>
 struct TcCfg {
     static constexpr int ES = MODE == 2 ? 1 : 2;      // element bytes
@@ -497,7 +507,7 @@ struct TcCfg {
     static constexpr int KPI = MODE == 2 ? 32 : 16;    // K per MMA instruction (32 bytes of K)
     static constexpr int CH_STEPS = MODE == 0 ? 1 << 30 : KCH / KS;  // k-steps per drained chunk
     static constexpr size_t SMEM = 1024 + STAGES * (size_t)STAGE + 2048;  // align slack + barriers, exponents
-    static_assert(MODE == 0 || MODE == 2, "mode");
+    static_assert(MODE == 0 || MODE == 2 || MODE == 3, "mode");
     static_assert(SW == 64 || SW == 128, "swizzle");
     static_assert(N % 64 == 0 && N >= 64 && N <= 256, "N");
     static_assert(A_TILE % 1024 == 0 && B_TILE % 1024 == 0, "tile alignment");
@@ -508,7 +518,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, TcArgs a)
 {
     using C = TcCfg<KS, N, S, MODE>;
-    constexpr bool CHUNKED = MODE == 2;  // drained every 128 of the contraction, with the chunk scales
+    constexpr bool CHUNKED = MODE != 0;  // drained every 128 of the contraction, with the chunk scales
     extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
     unsigned char* smem =
         reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~uintptr_t(1023));
@@ -681,12 +691,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     break;
                 }
                 tc_fence_after();
-                if constexpr (MODE == 2) {
-                    // products of x 2^(8-e_r) and y 2^(8-e_c): scale back by 2^(e_r + e_c - 16), relative
-                    // to the row and column maxima; FP32 accumulation is enough for this precision
+                if constexpr (CHUNKED) {
+                    // FP8: products of x 2^(8-e_r) and y 2^(8-e_c), scaled back by 2^(e_r + e_c - 16); TC2:
+                    // products of slices of x 2^(7-e_r) and y 2^(7-e_c), scaled back by 2^(e_r + e_c - 14);
+                    // both relative to the row and column maxima; FP32 accumulation suits their precision
                     const int e_r = row_ok ? a.eA[(size_t)kcg * a.rowsA + gi] : EXP_NONE;
                     const float* colscale = reinterpret_cast<const float*>(colexp) + half * NH;
-                    const float rs = e_r == EXP_NONE ? 0.0f : pow2f(e_r - emax_r - 16);
+                    const float rs = e_r == EXP_NONE ? 0.0f : pow2f(e_r - emax_r - (MODE == 2 ? 16 : 14));
 #pragma unroll
                     for (int h = 0; h < NH / 32; ++h) {
                         float v[32];
@@ -846,8 +857,8 @@ __global__ void __launch_bounds__(EMU_THREADS, 1)
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + EMU_STAGES * EMU_STAGE);
     uint64_t* empty = full + EMU_STAGES;
     uint64_t* accf = empty + EMU_STAGES;  // chunk's MMAs complete
-    uint64_t* lo_empty = accf + 1;        // chunk's L2..L5 read
-    uint64_t* hi_empty = lo_empty + 1;    // [2]: chunk's L6, L7+8 read, by chunk parity
+    uint64_t* lo_empty = accf + 1;        // [4]: chunk's L5, L4, L3, L2 read (one barrier per level)
+    uint64_t* hi_empty = lo_empty + 4;    // [2]: chunk's L6, L7+8 read, by chunk parity
     uint64_t* done = hi_empty + 2;        // every MMA of this CTA complete
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(done + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
@@ -862,7 +873,7 @@ __global__ void __launch_bounds__(EMU_THREADS, 1)
             mbar_init(&empty[s], 1);
         }
         mbar_init(accf, 1);
-        mbar_init(lo_empty, 1);
+        for (int l = 0; l < 4; ++l) mbar_init(&lo_empty[l], EMU_DRAIN / 32);  // one arrival per drain warp
         mbar_init(&hi_empty[0], 1);
         mbar_init(&hi_empty[1], 1);
         mbar_init(done, 1);
@@ -948,18 +959,22 @@ __global__ void __launch_bounds__(EMU_THREADS, 1)
                     emu_issue_level<6>(hi, dA, dB, idesc, cstart);
                     emu_issue_level<7>(hi + 64u, dA, dB, idesc, cstart);
                     emu_issue_level<8>(hi + 64u, dA, dB, idesc, false);
-                    if (cstart && chunk >= 1) {  // L2..L5 slots: the previous chunk's must have been read
-                        if (!mbar_wait(lo_empty, (uint32_t)((chunk - 1) & 1), a.limit_ns)) {
-                            fail(15);
-                            ok = false;
-                            break;
-                        }
+                    // L5, L4, L3, L2 in the order the drain releases their slots; in a chunk's first
+                    // k-step each waits for the previous chunk's value of its level to have been read
+                    auto lo_ready = [&](int l) {
+                        if (!(cstart && chunk >= 1)) return true;
+                        if (!mbar_wait(&lo_empty[l], (uint32_t)((chunk - 1) & 1), a.limit_ns)) return false;
                         tc_fence_after();
-                    }
-                    emu_issue_level<2>(tmem, dA, dB, idesc, cstart);
-                    emu_issue_level<3>(tmem + 64u, dA, dB, idesc, cstart);
-                    emu_issue_level<4>(tmem + 128u, dA, dB, idesc, cstart);
+                        return true;
+                    };
+                    if (!lo_ready(0)) { fail(15); ok = false; break; }
                     emu_issue_level<5>(tmem + 192u, dA, dB, idesc, cstart);
+                    if (!lo_ready(1)) { fail(15); ok = false; break; }
+                    emu_issue_level<4>(tmem + 128u, dA, dB, idesc, cstart);
+                    if (!lo_ready(2)) { fail(15); ok = false; break; }
+                    emu_issue_level<3>(tmem + 64u, dA, dB, idesc, cstart);
+                    if (!lo_ready(3)) { fail(15); ok = false; break; }
+                    emu_issue_level<2>(tmem, dA, dB, idesc, cstart);
                     umma_commit(&empty[stg]);
                     if (cend) {
                         umma_commit(accf);
@@ -1021,11 +1036,15 @@ __global__ void __launch_bounds__(EMU_THREADS, 1)
                 float sc[EMU_CPT];
 #pragma unroll
                 for (int c = 0; c < EMU_CPT; ++c) sc[c] = __fmul_rn(rs, colscale[g * EMU_CPT + c]);  // exact
-                // L2..L5: exact level sums, added into (H, L) by TwoSum
+                // L5, L4, L3, L2: exact level sums, added into (H, L) by TwoSum; each level's slot is
+                // released (one arrival per warp) as soon as this warp has read it
 #pragma unroll
                 for (int lv = 0; lv < 4; ++lv) {
                     uint32_t v[EMU_CPT];
-                    tmem_ld16(lane_addr + (uint32_t)(lv * 64), v);
+                    tmem_ld16(lane_addr + (uint32_t)((3 - lv) * 64), v);
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&lo_empty[lv]);
 #pragma unroll
                     for (int c = 0; c < EMU_CPT; ++c) {
                         const float t = __fmul_rn(__uint_as_float(v[c]), sc[c]);
@@ -1036,9 +1055,6 @@ __global__ void __launch_bounds__(EMU_THREADS, 1)
                         L[c] = __fadd_rn(L[c], err);
                     }
                 }
-                tc_fence_before();
-                asm volatile("bar.sync 1, 512;" ::: "memory");  // L2..L5 fully read
-                if (dt == 0) mbar_arrive(lo_empty);
                 // L6 and L7+8: below 2^-29 of the chunk's scale, added into the low part
                 const uint32_t hi = lane_addr + 256u + (uint32_t)((chunk & 1) * 128);
                 uint32_t v6[EMU_CPT], v78[EMU_CPT];
@@ -1131,9 +1147,8 @@ static TcArgs make_args(const TcPlan& p, int rowsA, int colsB, int K, int tri, i
     a.colsB = colsB;
     a.K = K;
     a.tri = tri;
-    a.ks = p.mode == 1 ? 32 : p.mode == 2 ? 128 : 64;
+    a.ks = p.mode == 1 ? EMU_KS : p.mode == 2 ? 128 : 64;
     a.piece = 2048 / a.ks;  // k-steps per item (a multiple of the 128-long chunk)
-    if (p.mode == 1) a.piece = 64;
     a.cc = (colsB + N - 1) / N;
     a.rt = (rowsA + TM - 1) / TM;
     int s = 0;
@@ -1142,16 +1157,17 @@ static TcArgs make_args(const TcPlan& p, int rowsA, int colsB, int K, int tri, i
     return a;
 }
 
-TcPlan tc_plan(int m, int n, int mode)
+TcPlan tc_plan(int m, int n, int mode, int sa)
 {
     TcPlan p{};
     p.m = m;
     p.n = n;
     p.mode = mode;
-    p.S = mode == 1 ? 7 : mode == 2 ? 1 : 2;
+    p.S = mode == 1 ? EMU_S : mode == 2 ? 1 : 2;
+    p.SA = sa > p.S ? sa : p.S;
     p.es = mode == 2 ? 1 : 2;
-    // FP8 keeps N <= 128: its drain holds N/2 FP32 sums per thread
-    p.N = mode == 1 ? 64 : (n <= 64 ? 64 : (n <= 128 || mode == 2) ? 128 : 256);
+    // FP8 and TC2 keep N <= 128: their drain holds N/2 FP32 sums per thread
+    p.N = mode == 1 ? EMU_N : (n <= 64 ? 64 : (n <= 128 || mode >= 2) ? 128 : 256);
     p.ldp = ((long)m + 127) / 128 * 128;
     p.kch = (m + KCH - 1) / KCH;
     const TcArgs u = make_args(p, m, n, m, 1, p.N);
@@ -1160,22 +1176,47 @@ TcPlan tc_plan(int m, int n, int mode)
     return p;
 }
 
-size_t tc_workspace_bytes(const TcPlan& p)
+namespace {
+// Workspace of a plan.  The split of A (its SA planes, chunk exponents and row
+// maxima) comes first, so that plans of the same m, ldp and SA share it.
+struct TcLayout {
+    __nv_bfloat16 *Ap, *Zp, *Up;
+    int *eA, *mA, *eZ, *eU, *mZ, *mU, *cum1, *cum2;
+    double *slots, *U, *Cm;
+    size_t bytes;
+};
+TcLayout tc_layout(const TcPlan& p, void* ws)
 {
     auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
-    size_t b = 0;
-    b += al((size_t)p.S * p.m * p.ldp * p.es);   // A planes (row-major, full m x ldp)
-    b += al((size_t)p.S * p.n * p.ldp * p.es);   // Z planes
-    b += al((size_t)p.S * p.n * p.ldp * p.es);   // U planes
-    b += al((size_t)p.kch * p.m * 4);            // eA
-    b += al((size_t)p.kch * p.n * 4) * 2;        // eZ, eU
-    b += al((size_t)p.m * 4) + al((size_t)p.n * 4) * 2;  // emaxA, emaxZ, emaxU
-    b += al((size_t)((p.m + TM - 1) / TM + 2) * 4) * 2;  // item prefixes
-    b += al(tc_plan_bytes(p));                   // slots
-    b += al((size_t)p.m * p.n * 8);              // U
-    b += al((size_t)p.n * p.n * 8);              // C
-    return b;
+    char* base = static_cast<char*>(ws);
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        char* q = base ? base + o : nullptr;
+        o += al(bytes);
+        return q;
+    };
+    const size_t planeA = (size_t)p.m * p.ldp, planeZ = (size_t)p.n * p.ldp;  // elements
+    TcLayout L;
+    L.Ap = reinterpret_cast<__nv_bfloat16*>(take((size_t)p.SA * planeA * p.es));
+    L.eA = reinterpret_cast<int*>(take((size_t)p.kch * p.m * 4));
+    L.mA = reinterpret_cast<int*>(take((size_t)p.m * 4));
+    L.Zp = reinterpret_cast<__nv_bfloat16*>(take((size_t)p.S * planeZ * p.es));
+    L.Up = reinterpret_cast<__nv_bfloat16*>(take((size_t)p.S * planeZ * p.es));
+    L.eZ = reinterpret_cast<int*>(take((size_t)p.kch * p.n * 4));
+    L.eU = reinterpret_cast<int*>(take((size_t)p.kch * p.n * 4));
+    L.mZ = reinterpret_cast<int*>(take((size_t)p.n * 4));
+    L.mU = reinterpret_cast<int*>(take((size_t)p.n * 4));
+    L.cum1 = reinterpret_cast<int*>(take((size_t)((p.m + TM - 1) / TM + 2) * 4));
+    L.cum2 = reinterpret_cast<int*>(take((size_t)((p.m + TM - 1) / TM + 2) * 4));
+    L.slots = reinterpret_cast<double*>(take(tc_plan_bytes(p)));
+    L.U = reinterpret_cast<double*>(take((size_t)p.m * p.n * 8));
+    L.Cm = reinterpret_cast<double*>(take((size_t)p.n * p.n * 8));
+    L.bytes = o;
+    return L;
 }
+}  // namespace
+
+size_t tc_workspace_bytes(const TcPlan& p) { return tc_layout(p, nullptr).bytes; }
 
 namespace {
 template <int MODE>
@@ -1190,6 +1231,23 @@ void launch_splits_tall(dim3 g, cudaStream_t s, int K, int C, const double* X, l
 {
     split_tall_kernel<MODE><<<g, 256, 0, s>>>(K, C, X, ldx, S, P, ldp, plane, e, mx);
 }
+// The split kernel of a plan's mode: TC2 (mode 3) takes the leading slices of the EMU64 split.
+void split_lower_mode(const TcPlan& p, dim3 g, cudaStream_t s, const double* A, long lda, __nv_bfloat16* P, int* e,
+                      int* mx)
+{
+    const size_t plane = (size_t)p.m * p.ldp;
+    if (p.mode == 1 || p.mode == 3) launch_splits_lower<1>(g, s, p.m, A, lda, p.SA, P, p.ldp, plane, e, mx);
+    else if (p.mode == 2) launch_splits_lower<2>(g, s, p.m, A, lda, p.SA, P, p.ldp, plane, e, mx);
+    else launch_splits_lower<0>(g, s, p.m, A, lda, p.SA, P, p.ldp, plane, e, mx);
+}
+void split_tall_mode(const TcPlan& p, dim3 g, cudaStream_t s, const double* X, long ldx, __nv_bfloat16* P, int* e,
+                     int* mx)
+{
+    const size_t plane = (size_t)p.n * p.ldp;
+    if (p.mode == 1 || p.mode == 3) launch_splits_tall<1>(g, s, p.m, p.n, X, ldx, p.S, P, p.ldp, plane, e, mx);
+    else if (p.mode == 2) launch_splits_tall<2>(g, s, p.m, p.n, X, ldx, p.S, P, p.ldp, plane, e, mx);
+    else launch_splits_tall<0>(g, s, p.m, p.n, X, ldx, p.S, P, p.ldp, plane, e, mx);
+}
 cudaError_t launch_tc_mode(const TcPlan& p, const TcArgs& a, const void* PA, size_t planeA, const void* PB,
                            size_t planeB, int sms, cudaStream_t s)
 {
@@ -1197,6 +1255,10 @@ cudaError_t launch_tc_mode(const TcPlan& p, const TcArgs& a, const void* PA, siz
     if (p.mode == 2) {
         if (p.N == 64) return launch_tc<128, 64, 1, 2>(a, PA, p.ldp, planeA, PB, p.ldp, planeB, sms, s);
         return launch_tc<128, 128, 1, 2>(a, PA, p.ldp, planeA, PB, p.ldp, planeB, sms, s);
+    }
+    if (p.mode == 3) {
+        if (p.N == 64) return launch_tc<64, 64, 2, 3>(a, PA, p.ldp, planeA, PB, p.ldp, planeB, sms, s);
+        return launch_tc<64, 128, 2, 3>(a, PA, p.ldp, planeA, PB, p.ldp, planeB, sms, s);
     }
     if (p.N == 64) return launch_tc<64, 64, 2, 0>(a, PA, p.ldp, planeA, PB, p.ldp, planeB, sms, s);
     if (p.N == 128) return launch_tc<64, 128, 2, 0>(a, PA, p.ldp, planeA, PB, p.ldp, planeB, sms, s);
@@ -1213,113 +1275,64 @@ void launch_slot_reduce(const TcPlan& p, const TcArgs& a, double* out, long ldo,
 }  // namespace
 
 // G = Z^T A Z (+ shift) from A's lower triangle on the tensor cores; see the
-// file comment.  ws holds tc_workspace_bytes(p).
+// file comment.  ws holds tc_workspace_bytes(p).  a_ready: the workspace
+// already holds the split of this A (planes, exponents, row maxima) made by a
+// plan with the same m and SA, and it is not made again.
 cudaError_t launch_tc_gram(const TcPlan& p, const double* A, long lda, const double* Z, long ldz, double* G, long ldg,
                            const double* shift_ptr, void* ws, DevStatus* st, uint64_t limit_ns, int sms,
-                           cudaStream_t s, cudaEvent_t* ev)
+                           cudaStream_t s, cudaEvent_t* ev, bool a_ready)
 {
     auto mark = [&](int i) {
         if (ev) cudaEventRecord(ev[i], s);
     };
     mark(0);
-    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
-    char* w = static_cast<char*>(ws);
+    const TcLayout L = tc_layout(p, ws);
     const size_t planeA = (size_t)p.m * p.ldp, planeZ = (size_t)p.n * p.ldp;  // elements
-    __nv_bfloat16* Ap = reinterpret_cast<__nv_bfloat16*>(w);
-    w += al((size_t)p.S * planeA * p.es);
-    __nv_bfloat16* Zp = reinterpret_cast<__nv_bfloat16*>(w);
-    w += al((size_t)p.S * planeZ * p.es);
-    __nv_bfloat16* Up = reinterpret_cast<__nv_bfloat16*>(w);
-    w += al((size_t)p.S * planeZ * p.es);
-    int* eA = reinterpret_cast<int*>(w);
-    w += al((size_t)p.kch * p.m * 4);
-    int* eZ = reinterpret_cast<int*>(w);
-    w += al((size_t)p.kch * p.n * 4);
-    int* eU = reinterpret_cast<int*>(w);
-    w += al((size_t)p.kch * p.n * 4);
-    int* mA = reinterpret_cast<int*>(w);
-    w += al((size_t)p.m * 4);
-    int* mZ = reinterpret_cast<int*>(w);
-    w += al((size_t)p.n * 4);
-    int* mU = reinterpret_cast<int*>(w);
-    w += al((size_t)p.n * 4);
-    int* cum1 = reinterpret_cast<int*>(w);
-    w += al((size_t)((p.m + TM - 1) / TM + 2) * 4);
-    int* cum2 = reinterpret_cast<int*>(w);
-    w += al((size_t)((p.m + TM - 1) / TM + 2) * 4);
-    double* slots = reinterpret_cast<double*>(w);
-    w += al(tc_plan_bytes(p));
-    double* U = reinterpret_cast<double*>(w);
-    w += al((size_t)p.m * p.n * 8);
-    double* Cm = reinterpret_cast<double*>(w);
-
-    const int S = p.S;
     const int mm = p.m, nn = p.n;
-    // element offsets of the slice planes are in units of the plane's element (byte planes for FP8)
-    const size_t pA = p.es == 1 ? planeA / 2 : planeA, pZ = p.es == 1 ? planeZ / 2 : planeZ;
-    const long ldpe = p.es == 1 ? p.ldp / 2 : p.ldp;
-    (void)pA;
-    (void)pZ;
-    (void)ldpe;
     cudaError_t e;
     if (p.mode != 0) {
-        fill_int_kernel<<<(mm + 255) / 256, 256, 0, s>>>(mA, mm, EXP_NONE);
-        fill_int_kernel<<<(nn + 255) / 256, 256, 0, s>>>(mZ, nn, EXP_NONE);
-        fill_int_kernel<<<(nn + 255) / 256, 256, 0, s>>>(mU, nn, EXP_NONE);
+        if (!a_ready) fill_int_kernel<<<(mm + 255) / 256, 256, 0, s>>>(L.mA, mm, EXP_NONE);
+        fill_int_kernel<<<(nn + 255) / 256, 256, 0, s>>>(L.mZ, nn, EXP_NONE);
+        fill_int_kernel<<<(nn + 255) / 256, 256, 0, s>>>(L.mU, nn, EXP_NONE);
     }
-    {
-        dim3 g(p.kch, (mm + 31) / 32), gz(p.kch, (nn + 7) / 8);
-        if (p.mode == 1) {
-            launch_splits_lower<1>(g, s, mm, A, lda, S, Ap, p.ldp, planeA, eA, mA);
-            launch_splits_tall<1>(gz, s, mm, nn, Z, ldz, S, Zp, p.ldp, planeZ, eZ, mZ);
-        } else if (p.mode == 2) {
-            launch_splits_lower<2>(g, s, mm, A, lda, S, Ap, p.ldp, planeA, eA, mA);
-            launch_splits_tall<2>(gz, s, mm, nn, Z, ldz, S, Zp, p.ldp, planeZ, eZ, mZ);
-        } else {
-            launch_splits_lower<0>(g, s, mm, A, lda, S, Ap, p.ldp, planeA, eA, mA);
-            launch_splits_tall<0>(gz, s, mm, nn, Z, ldz, S, Zp, p.ldp, planeZ, eZ, mZ);
-        }
-    }
+    const dim3 g(p.kch, (mm + 31) / 32), gz(p.kch, (nn + 7) / 8);
+    if (!a_ready) split_lower_mode(p, g, s, A, lda, L.Ap, L.eA, L.mA);
+    split_tall_mode(p, gz, s, Z, ldz, L.Zp, L.eZ, L.mZ);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // U = M Z (triangular)
     TcArgs a1 = make_args(p, mm, nn, mm, 1, p.N);
-    a1.cum = cum1;
-    a1.slots = slots;
-    a1.eA = eA;
-    a1.eB = eZ;
-    a1.emaxA = mA;
-    a1.emaxB = mZ;
+    a1.cum = L.cum1;
+    a1.slots = L.slots;
+    a1.eA = L.eA;
+    a1.eB = L.eZ;
+    a1.emaxA = L.mA;
+    a1.emaxB = L.mZ;
     a1.st = st;
     a1.limit_ns = limit_ns;
-    item_prefix_kernel<<<1, 32, 0, s>>>(a1, cum1);
+    item_prefix_kernel<<<1, 32, 0, s>>>(a1, L.cum1);
     mark(1);
-    if ((e = launch_tc_mode(p, a1, Ap, planeA, Zp, planeZ, sms, s)) != cudaSuccess) return e;
+    if ((e = launch_tc_mode(p, a1, L.Ap, planeA, L.Zp, planeZ, sms, s)) != cudaSuccess) return e;
     mark(2);
-    launch_slot_reduce(p, a1, U, mm, st, s);
+    launch_slot_reduce(p, a1, L.U, mm, st, s);
     // C = Z^T U (left operand: Z's columns as rows, K-major), then G = C + C^T
-    {
-        dim3 gu(p.kch, (nn + 7) / 8);
-        if (p.mode == 1) launch_splits_tall<1>(gu, s, mm, nn, U, mm, S, Up, p.ldp, planeZ, eU, mU);
-        else if (p.mode == 2) launch_splits_tall<2>(gu, s, mm, nn, U, mm, S, Up, p.ldp, planeZ, eU, mU);
-        else launch_splits_tall<0>(gu, s, mm, nn, U, mm, S, Up, p.ldp, planeZ, eU, mU);
-    }
+    split_tall_mode(p, gz, s, L.U, mm, L.Up, L.eU, L.mU);
     TcArgs a2 = make_args(p, nn, nn, mm, 0, p.N);
-    a2.cum = cum2;
-    a2.slots = slots;
-    a2.eA = eZ;
-    a2.eB = eU;
-    a2.emaxA = mZ;
-    a2.emaxB = mU;
+    a2.cum = L.cum2;
+    a2.slots = L.slots;
+    a2.eA = L.eZ;
+    a2.eB = L.eU;
+    a2.emaxA = L.mZ;
+    a2.emaxB = L.mU;
     a2.st = st;
     a2.limit_ns = limit_ns;
-    item_prefix_kernel<<<1, 32, 0, s>>>(a2, cum2);
+    item_prefix_kernel<<<1, 32, 0, s>>>(a2, L.cum2);
     mark(3);
-    if ((e = launch_tc_mode(p, a2, Zp, planeZ, Up, planeZ, sms, s)) != cudaSuccess) return e;
+    if ((e = launch_tc_mode(p, a2, L.Zp, planeZ, L.Up, planeZ, sms, s)) != cudaSuccess) return e;
     mark(4);
-    launch_slot_reduce(p, a2, Cm, nn, st, s);
+    launch_slot_reduce(p, a2, L.Cm, nn, st, s);
     {
         const long tot = (long)nn * nn;
-        symmetrize_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(nn, Cm, nn, G, ldg, shift_ptr, st);
+        symmetrize_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(nn, L.Cm, nn, G, ldg, shift_ptr, st);
     }
     mark(5);
     return cudaGetLastError();

@@ -184,11 +184,12 @@ oqr_status reset_status(oqr_ctx* ctx, cudaStream_t s)
 
 oqr_status run_check(oqr_ctx* ctx, const GramPlan& gp, const double* A, long lda, const double* Q, long ldq,
                      double* partials, double* G, double* work, double* E, long lde, uint64_t limit, cudaStream_t s,
-                     void* tcws = nullptr)
+                     void* tcws = nullptr, bool a_ready = false)
 {
-    if (tcws) {  // FP64-accurate Gram on the tensor cores
+    if (tcws) {  // FP64-accurate Gram on the tensor cores (reusing the split of A when a_ready)
         const TcPlan tp = tc_plan(gp.m, gp.n, 1);
-        OQR_TRY(launch_tc_gram(tp, A, lda, Q, ldq, G, gp.n, nullptr, tcws, ctx->st, limit, ctx->sm_count, s));
+        OQR_TRY(launch_tc_gram(tp, A, lda, Q, ldq, G, gp.n, nullptr, tcws, ctx->st, limit, ctx->sm_count, s, nullptr,
+                               a_ready));
     } else {
         OQR_TRY(launch_gram_f64(gp, A, lda, Q, ldq, partials, ctx->st, limit, s));
         OQR_TRY(launch_gram_reduce(gp, partials, G, gp.n, nullptr, ctx->st, s));
@@ -197,29 +198,48 @@ oqr_status run_check(oqr_ctx* ctx, const GramPlan& gp, const double* A, long lda
     return OQR_OK;
 }
 
-bool prec_ok(int p) { return p == OQR_FP64 || p == OQR_BF16X3 || p == OQR_FP64_TC || p == OQR_FP8; }
+bool prec_ok(int p)
+{
+    return p == OQR_FP64 || p == OQR_BF16X3 || p == OQR_FP64_TC || p == OQR_FP8 || p == OQR_TC2;
+}
 
-int tc_mode_of(int prec) { return prec == OQR_FP64_TC ? 1 : prec == OQR_FP8 ? 2 : 0; }
+int tc_mode_of(int prec) { return prec == OQR_FP64_TC ? 1 : prec == OQR_FP8 ? 2 : prec == OQR_TC2 ? 3 : 0; }
+
+// Modes 1 (FP64_TC) and 3 (TC2) take their operands from the same split of A.
+bool emu_family(int prec) { return prec == OQR_FP64_TC || prec == OQR_TC2; }
+
+// Tracks which split of A the tensor-core workspace holds within one call, so
+// that passes (and the check) of the EMU64 family split A once.
+struct ASplit {
+    int sa = 0;         // planes of A kept by the EMU64-family plans of this call
+    bool emu = false;   // the workspace holds this call's EMU64-family split of A
+};
 
 // G = X^T A X (+ shift) in the requested arithmetic.
 cudaError_t form_gram(oqr_ctx* ctx, int prec, const GramPlan& gp, const double* A, long lda, const double* X,
                       long ldx, double* partials, double* G, const double* shift_ptr, void* tcws, uint64_t limit,
-                      cudaStream_t s)
+                      cudaStream_t s, ASplit* as = nullptr)
 {
     if (prec == OQR_FP64) {
         cudaError_t e = launch_gram_f64(gp, A, lda, X, ldx, partials, ctx->st, limit, s);
         if (e != cudaSuccess) return e;
         return launch_gram_reduce(gp, partials, G, gp.n, shift_ptr, ctx->st, s);
     }
-    const TcPlan tp = tc_plan(gp.m, gp.n, tc_mode_of(prec));
-    return launch_tc_gram(tp, A, lda, X, ldx, G, gp.n, shift_ptr, tcws, ctx->st, limit, ctx->sm_count, s);
+    const bool fam = emu_family(prec);
+    const TcPlan tp = tc_plan(gp.m, gp.n, tc_mode_of(prec), (fam && as) ? as->sa : 0);
+    const bool ready = fam && as && as->emu;
+    cudaError_t e = launch_tc_gram(tp, A, lda, X, ldx, G, gp.n, shift_ptr, tcws, ctx->st, limit, ctx->sm_count, s,
+                                   nullptr, ready);
+    if (as) as->emu = fam;  // any other tensor-core mode overwrites the region
+    return e;
 }
 
-size_t tc_bytes_for(int m, int n, int prec_a, int prec_b)
+size_t tc_bytes_for(int m, int n, int prec_a, int prec_b, int sa = 0)
 {
     size_t b = 0;
     for (int pr : {prec_a, prec_b})
-        if (pr != OQR_FP64) b = std::max(b, tc_workspace_bytes(tc_plan(m, n, tc_mode_of(pr))));
+        if (pr != OQR_FP64)
+            b = std::max(b, tc_workspace_bytes(tc_plan(m, n, tc_mode_of(pr), emu_family(pr) ? sa : 0)));
     return b;
 }
 
@@ -244,9 +264,14 @@ oqr_status normal_equation(oqr_ctx* ctx, int m, int n, const double* A, long lda
     Carve probe(nullptr);
     double *partials, *G, *work, *R1, *R2, *R3, *scratch;
     layout_cholqr(probe, gp, &partials, &G, &work, &R1, &R2, &R3, &scratch);
-    size_t tcb = tc_bytes_for(m, n, prec_first, o.final_prec);
-    tcb = std::max(tcb, tc_bytes_for(m, n, prec_mid, prec_mid));
-    if (o.check == 2) tcb = std::max(tcb, tc_bytes_for(m, n, OQR_FP64_TC, OQR_FP64_TC));
+    // one split of A for the EMU64-family passes and the tensor-core check: 7 planes when any of them is FP64_TC
+    ASplit as;
+    as.sa = (prec_first == OQR_FP64_TC || prec_mid == OQR_FP64_TC || o.final_prec == OQR_FP64_TC || o.check == 2)
+                ? 7
+                : 0;
+    size_t tcb = tc_bytes_for(m, n, prec_first, o.final_prec, as.sa);
+    tcb = std::max(tcb, tc_bytes_for(m, n, prec_mid, prec_mid, as.sa));
+    if (o.check == 2) tcb = std::max(tcb, tc_bytes_for(m, n, OQR_FP64_TC, OQR_FP64_TC, as.sa));
     char* tcws_probe = probe.take<char>(tcb);
     (void)tcws_probe;
     if ((v = ensure_ws(ctx, probe.off)) != OQR_OK) return v;
@@ -256,7 +281,7 @@ oqr_status normal_equation(oqr_ctx* ctx, int m, int n, const double* A, long lda
     if ((v = reset_status(ctx, s)) != OQR_OK) return v;
 
     const double* shift_ptr = nullptr;
-    const bool trace_shift = shifted && (prec_first == OQR_BF16X3 || prec_first == OQR_FP8);
+    const bool trace_shift = shifted && (prec_first == OQR_BF16X3 || prec_first == OQR_FP8 || prec_first == OQR_TC2);
     if (shifted && !trace_shift) {
         OQR_TRY(launch_norms_and_shift(m, n, A, lda, Z, ldz, o.shift_c, U64, scratch, 2 * SHIFT_PARTS, ctx->st, s));
         shift_ptr = &ctx->st->shift;
@@ -269,8 +294,9 @@ oqr_status normal_equation(oqr_ctx* ctx, int m, int n, const double* A, long lda
         double* Rp = (passes == 1) ? R : R1;
         const long ldrp = (passes == 1) ? ldr : n;
         const int prec = prec_of(p);
-        OQR_TRY(form_gram(ctx, prec, gp, A, lda, X, ldx, partials, G, p == 0 ? shift_ptr : nullptr, tcws, limit, s));
-        if (p == 0 && trace_shift)  // u of the first pass's products: 2^-16 (BF16X3) or 2^-4 (E4M3)
+        OQR_TRY(form_gram(ctx, prec, gp, A, lda, X, ldx, partials, G, p == 0 ? shift_ptr : nullptr, tcws, limit, s,
+                          &as));
+        if (p == 0 && trace_shift)  // u of the first pass's products: 2^-16 (BF16X3, TC2) or 2^-4 (E4M3)
             OQR_TRY(launch_trace_shift(n, G, n, o.shift_c, prec == OQR_FP8 ? 0.0625 : 1.52587890625e-05, ctx->st, s));
         OQR_TRY(launch_potrf(n, G, n, Rp, ldrp, nullptr, ctx->st, s));
         OQR_TRY(launch_trsm(m, n, X, ldx, Rp, ldrp, Q, ldq, ctx->st, s));
@@ -291,7 +317,7 @@ oqr_status normal_equation(oqr_ctx* ctx, int m, int n, const double* A, long lda
     }
     if (o.check) {
         if ((v = run_check(ctx, gp, A, lda, Q, ldq, partials, G, work, nullptr, 0, limit, s,
-                           o.check == 2 ? tcws : nullptr)) != OQR_OK)
+                           o.check == 2 ? tcws : nullptr, as.emu && as.sa == 7)) != OQR_OK)
             return v;
     }
     return finish(ctx, s, info, passes, o.check != 0);

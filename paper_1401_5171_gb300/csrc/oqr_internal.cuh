@@ -175,25 +175,25 @@ cudaError_t launch_gemm_f64(GemmOp op, int M, int N, int K, double alpha, const 
                             const double* B, long ldb, double beta, double* C, long ldc, double* splitk_ws,
                             int splits, cudaStream_t s);
 
-// Tensor-core normal-equation matrix (k_tc.cu): G = Z^T A Z from BF16 slices.
-// emu = false: BF16X3 (hi/lo, 3 products, FP32 accumulation);
-// emu = true : FP64-accurate (7 exact slices per operand, 28 products).
+// Tensor-core normal-equation matrix (k_tc.cu): G = Z^T A Z from BF16 (or
+// E4M3) slices of the FP64 operands.
 struct TcPlan {
     int m, n;
-    int mode;       // 0 BF16X3, 1 FP64-accurate emulation, 2 FP8 E4M3
+    int mode;       // 0 BF16X3, 1 FP64-accurate emulation, 2 FP8 E4M3, 3 TC2 (two leading emulation slices)
     int es;         // bytes per plane element
-    int S;          // slices per operand
+    int S;          // slices per operand used by the products
+    int SA;         // slices of A made and kept in the workspace (>= S; 7 when shared with mode 1)
     int N;          // UMMA N (column chunk)
     long ldp;       // leading dimension of the slice planes
     int kch;        // 128-long chunks of the contraction
     int nitems_max; // work items of the larger of the two products
 };
-TcPlan tc_plan(int m, int n, int mode);
+TcPlan tc_plan(int m, int n, int mode, int sa = 0);
 size_t tc_plan_bytes(const TcPlan& p);
 size_t tc_workspace_bytes(const TcPlan& p);
 cudaError_t launch_tc_gram(const TcPlan& p, const double* A, long lda, const double* Z, long ldz, double* G, long ldg,
                            const double* shift_ptr, void* ws, DevStatus* st, uint64_t limit_ns, int sms,
-                           cudaStream_t s, cudaEvent_t* ev = nullptr);
+                           cudaStream_t s, cudaEvent_t* ev = nullptr, bool a_ready = false);
 
 // Batched A-CholQR2 (k_batched.cu): one descriptor per instance, n <= 64, m <= 4096.
 constexpr int BATCH_MAX_N = 64;

@@ -20,7 +20,7 @@ HEADERS = [os.path.join(os.path.dirname(HERE), "include", "oqr.h")]
 
 OQR_OK, OQR_ERR_INVALID_ARG, OQR_ERR_NOT_SPD, OQR_ERR_CHECK_FAILED = 0, 1, 2, 3
 OQR_ERR_CUDA, OQR_ERR_NO_MEMORY, OQR_ERR_TIMEOUT, OQR_ERR_UNSUPPORTED = 4, 5, 6, 7
-OQR_FP64, OQR_BF16X3, OQR_FP8, OQR_FP64_TC = 0, 1, 2, 3
+OQR_FP64, OQR_BF16X3, OQR_FP8, OQR_FP64_TC, OQR_TC2 = 0, 1, 2, 3, 4
 OQR_ALGO_CHOLQR, OQR_ALGO_CHOLQR2, OQR_ALGO_SCHOLQR3, OQR_ALGO_CGS2 = 0, 1, 2, 3
 
 

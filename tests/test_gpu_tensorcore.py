@@ -13,7 +13,7 @@ import pytest
 
 import oracle
 from paper_1401_5171_gb300 import inputs
-from split_defs import bf16_rne, e4m3_quantize
+from split_defs import bf16_rne, e4m3_quantize, tc2_cols, tc2_rows
 
 pytestmark = pytest.mark.gpu
 U = 2.0 ** -53
@@ -111,7 +111,43 @@ def test_tc_gram_fp64tc_near_exact(env, m, n):
     assert err <= 2.0 ** -44, err
 
 
-@pytest.mark.parametrize("prec,final", [(3, 3), (1, 3), (0, 3)])
+@pytest.mark.parametrize("m,n", [(64, 5), (300, 20), (1000, 130), (2000, 200)])
+def test_tc_gram_tc2_definition(env, m, n):
+    # TC2 keeps the two leading FP64_TC slices: M~ per (row, 128-chunk), Z~ per (column, 128-chunk);
+    # G_def = Z~^T U~ + (Z~^T U~)^T with U~ the same truncation of U_def = M~ Z~.  The GPU differs by
+    # FP32 accumulation, and U~ by one truncation step where U and U_def straddle a boundary.
+    torch, oqr, ctx = env
+    A, Z = inputs.paper_case(4, m, n, 1e4, 1e2, seed=m + 11 * n)
+    G = ctx.oqr_gram(dev(torch, oqr, A), dev(torch, oqr, Z), prec=oqr.OQR_TC2).cpu().numpy()
+    Mt, Zt = tc2_rows(lower_m(A)), tc2_cols(Z)
+    Ut = tc2_cols(Mt @ Zt)
+    C = Zt.T @ Ut
+    Gdef = C + C.T
+    scale = np.abs(Z).T @ np.abs(A) @ np.abs(Z)
+    assert np.array_equal(G, G.T)
+    assert np.all(np.abs(G - Gdef) <= 2.0 ** -14 * scale + 1e-300)
+    assert np.all(np.abs(G - oracle.gram(A, Z)) <= 2.0 ** -11 * scale + 1e-300)
+
+
+def test_shared_split_matches_separate_steps(env):
+    # A-CholQR2 with a TC2 then an FP64_TC pass splits A once for both passes; composing the same
+    # steps from separate calls (each splitting A itself) must give bit-identical Q and R
+    torch, oqr, ctx = env
+    A, Z = inputs.paper_case(4, 1100, 70, 1e5, 1e2, seed=21)
+    Ad, Zd = dev(torch, oqr, A), dev(torch, oqr, Z)
+    Q, R, (st, _) = ctx.oqr_cholqr2(Ad, Zd, prec=oqr.OQR_TC2, final_prec=oqr.OQR_FP64_TC)
+    G1 = ctx.oqr_gram(Ad, Zd, prec=oqr.OQR_TC2)
+    R1, st1, _ = ctx.oqr_potrf(G1)
+    Q1 = ctx.oqr_trsm(Zd, R1)
+    G2 = ctx.oqr_gram(Ad, Q1, prec=oqr.OQR_FP64_TC)
+    R2, st2, _ = ctx.oqr_potrf(G2)
+    Q2 = ctx.oqr_trsm(Q1, R2)
+    Rm = ctx.oqr_rprod(R2, R1)
+    assert st == st1 == st2 == oqr.OQR_OK
+    assert torch.equal(Q, Q2) and torch.equal(R, Rm)
+
+
+@pytest.mark.parametrize("prec,final", [(3, 3), (1, 3), (0, 3), (4, 3)])
 def test_mixed_cholqr2_parity(env, prec, final):
     torch, oqr, ctx = env
     # kappa(A^{1/2} Z) ~ 1e2: the BF16X3 first pass completes
