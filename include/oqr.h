@@ -176,6 +176,12 @@ oqr_status oqr_cgs2(oqr_ctx* ctx, int m, int n, const double* A, long lda, const
  *   OQR_ERR_NOT_SPD with the 1-based column (synchronizes the stream when
  *   info != NULL).
  * oqr_trsm: Q = Z / R (line 4), row-wise substitution; Q may alias Z.
+ * oqr_trsm_tc: the same solve in 64-column blocks: for each block, the
+ *   product of the already solved columns with R's block column is formed
+ *   FP64-accurately on the tensor cores (the OQR_FP64_TC slices), and the
+ *   64 x 64 diagonal block is solved by FP64 row-wise substitution.  The
+ *   factorizations use it in every pass whose Gram runs on the tensor cores.
+ *   Uses the context's workspace; Q may alias Z.
  * oqr_rprod: R = U S for upper triangular U, S (R must not alias U or S).
  * oqr_check: E = Q^T A Q - I (n x n, written in full when E != NULL), and
  *   the estimate of ||E||_2 (Sec. 7's orthogonality measure) in *orth2 and
@@ -185,6 +191,8 @@ oqr_status oqr_gram(oqr_ctx* ctx, int m, int n, const double* A, long lda, const
                     double* G, long ldg, int prec, void* stream);
 oqr_status oqr_potrf(oqr_ctx* ctx, int n, const double* G, long ldg, double shift, double* R, long ldr,
                      int* info, void* stream);
+oqr_status oqr_trsm_tc(oqr_ctx* ctx, int m, int n, const double* Z, long ldz, const double* R, long ldr,
+                       double* Q, long ldq, void* stream);
 oqr_status oqr_trsm(oqr_ctx* ctx, int m, int n, const double* Z, long ldz, const double* R, long ldr,
                     double* Q, long ldq, void* stream);
 oqr_status oqr_rprod(oqr_ctx* ctx, int n, const double* U, long ldu, const double* S, long lds, double* R,

@@ -225,6 +225,52 @@ __global__ void __launch_bounds__(TRSM_THREADS) trsm_kernel(int m, int n, int ro
     }
 }
 
+// ------------------------------------------------- TRSM, one column block ----
+// Q(:, jb:jb+bw) = (Z(:, jb:jb+bw) - U) R(jb:jb+bw, jb:jb+bw)^{-1}, bw <= 64:
+// row-wise substitution, one thread per row (column-oriented order with the
+// reciprocals of the diagonal), the row's 64 values in registers.  U (m x bw,
+// column-major) is the product of the already solved columns with
+// R(0:jb, jb:jb+bw), formed elsewhere (NULL for the first block).  In place
+// when Q aliases Z.
+constexpr int TBW = 64;
+constexpr int TB_THREADS = 128;
+__global__ void __launch_bounds__(TB_THREADS) trsm_block_kernel(int m, int jb, int bw, const double* Z, long ldz,
+                                                                const double* __restrict__ U, long ldu,
+                                                                const double* __restrict__ R, long ldr, double* Q,
+                                                                long ldq, const DevStatus* st)
+{
+    __shared__ double D[TBW][TBW + 1];
+    __shared__ double dinv[TBW];
+    if (*(volatile const int*)&st->code != 0) return;
+    for (int e = threadIdx.x; e < TBW * TBW; e += TB_THREADS) {
+        const int i = e % TBW, j = e / TBW;
+        D[i][j] = (i <= j && j < bw) ? R[(jb + i) + (long)(jb + j) * ldr] : 0.0;
+    }
+    __syncthreads();
+    if (threadIdx.x < bw) dinv[threadIdx.x] = 1.0 / D[threadIdx.x][threadIdx.x];
+    __syncthreads();
+    const long i = (long)blockIdx.x * TB_THREADS + threadIdx.x;
+    if (i >= m) return;
+    double b[TBW];
+#pragma unroll
+    for (int c = 0; c < TBW; ++c) {
+        b[c] = 0.0;
+        if (c < bw) b[c] = Z[i + (long)(jb + c) * ldz] - (U ? U[i + (long)c * ldu] : 0.0);
+    }
+#pragma unroll
+    for (int c = 0; c < TBW; ++c) {
+        if (c < bw) {
+            asm volatile("" ::: "memory");  // keeps only row c of D live: no hoisted loads, no spills
+            b[c] *= dinv[c];
+#pragma unroll
+            for (int k = c + 1; k < TBW; ++k) b[k] -= D[c][k] * b[c];
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < TBW; ++c)
+        if (c < bw) Q[i + (long)(jb + c) * ldq] = b[c];
+}
+
 // ------------------------------------------------------------ R = U S ------
 __global__ void rprod_kernel(int n, const double* __restrict__ U, long ldu, const double* __restrict__ S, long lds,
                              double* R, long ldr)
@@ -469,6 +515,16 @@ cudaError_t launch_potrf(int n, const double* G, long ldg, double* R, long ldr, 
         const int nt = (rest + TT - 1) / TT;
         potrf_trail_kernel<<<nt * (nt + 1) / 2, TT * TT, 0, s>>>(n, jb, R, ldr, st);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_trsm_block(int m, int jb, int bw, const double* Z, long ldz, const double* U, long ldu,
+                              const double* R, long ldr, double* Q, long ldq, DevStatus* st, cudaStream_t s)
+{
+    if (m <= 0 || bw <= 0) return cudaSuccess;
+    if (bw > TBW) return cudaErrorInvalidValue;
+    trsm_block_kernel<<<(unsigned)((m + TB_THREADS - 1) / TB_THREADS), TB_THREADS, 0, s>>>(m, jb, bw, Z, ldz, U, ldu, R,
+                                                                                          ldr, Q, ldq, st);
     return cudaGetLastError();
 }
 

@@ -255,8 +255,9 @@ __device__ inline void store4(__nv_bfloat16* planes, size_t plane, size_t off, i
     }
 }
 
-// A (m x m, column-major, lower triangle) -> slices of M = tril(A,-1) + diag(A)/2,
-// written row-major (row i, k contiguous): planes + s*plane + i*ldp + k, ldp a
+// TRI: A (m x m, column-major, lower triangle) -> slices of
+// M = tril(A,-1) + diag(A)/2; otherwise a general column-major m x K matrix.
+// Written row-major (row i, k contiguous): planes + s*plane + i*ldp + k, ldp a
 // multiple of 128 (the row is written up to its 128-chunk's end).
 // One CTA: 32 rows x one 128-column chunk; 8 warps.  The tile is transposed
 // through shared memory stored as T[row][(k % 4) * 33 + k / 4], so that lane l
@@ -265,8 +266,8 @@ __device__ inline void store4(__nv_bfloat16* planes, size_t plane, size_t off, i
 // MODE 0: BF16 hi/lo planes; 1: S exact BF16 slices (S <= 7); 2: one FP8 E4M3
 // plane (bytes).  Modes 1 and 2 record the chunk exponent of every row.
 constexpr int TPAD = 4 * 33 + 1;
-template <int MODE>
-__global__ void __launch_bounds__(256) split_lower_kernel(int m, const double* __restrict__ A, long lda, int S,
+template <int MODE, bool TRI = true>
+__global__ void __launch_bounds__(256) split_lower_kernel(int m, int K, const double* __restrict__ A, long lda, int S,
                                                           __nv_bfloat16* planes, long ldp, size_t plane,
                                                           int* eA, int* emax)
 {
@@ -274,16 +275,24 @@ __global__ void __launch_bounds__(256) split_lower_kernel(int m, const double* _
     __shared__ double T[32][TPAD];
     const int kc = blockIdx.x, ib = blockIdx.y;
     const long row0 = (long)ib * 32, col0 = (long)kc * KCH;
-    if (row0 >= m || col0 > row0 + 31) return;
+    if (row0 >= m || (TRI && col0 > row0 + 31)) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int k = w; k < KCH; k += 8) {
+    double ld[KCH / 8];  // all of this thread's loads in flight before the first store
+#pragma unroll
+    for (int t = 0; t < KCH / 8; ++t) {
+        const int k = w + 8 * t;
         const long i = row0 + lane, kk = col0 + k;
         double v = 0.0;
-        if (i < m && kk < m && kk <= i) {
+        if (i < m && kk < K && (!TRI || kk <= i)) {
             v = A[i + kk * lda];
-            if (kk == i) v *= 0.5;  // one FP64 multiply per diagonal element
+            if (TRI && kk == i) v *= 0.5;  // one FP64 multiply per diagonal element
         }
-        T[lane][(k & 3) * 33 + (k >> 2)] = v;
+        ld[t] = v;
+    }
+#pragma unroll
+    for (int t = 0; t < KCH / 8; ++t) {
+        const int k = w + 8 * t;
+        T[lane][(k & 3) * 33 + (k >> 2)] = ld[t];
     }
     __syncthreads();
     for (int r = w * 4; r < w * 4 + 4; ++r) {
@@ -1223,7 +1232,7 @@ template <int MODE>
 void launch_splits_lower(dim3 g, cudaStream_t s, int mm, const double* A, long lda, int S, __nv_bfloat16* P, long ldp,
                          size_t plane, int* e, int* mx)
 {
-    split_lower_kernel<MODE><<<g, 256, 0, s>>>(mm, A, lda, S, P, ldp, plane, e, mx);
+    split_lower_kernel<MODE><<<g, 256, 0, s>>>(mm, mm, A, lda, S, P, ldp, plane, e, mx);
 }
 template <int MODE>
 void launch_splits_tall(dim3 g, cudaStream_t s, int K, int C, const double* X, long ldx, int S, __nv_bfloat16* P,
@@ -1335,6 +1344,94 @@ cudaError_t launch_tc_gram(const TcPlan& p, const double* A, long lda, const dou
         symmetrize_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(nn, L.Cm, nn, G, ldg, shift_ptr, st);
     }
     mark(5);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------ blocked TRSM ----
+// Q = Z / R (Algorithm 1, line 4) in 64-column blocks: for block J,
+//   U = Q(:, 0:64J) R(0:64J, block)      FP64-accurate EMU64 product (tensor cores)
+//   Q(:, block) = (Z(:, block) - U) R(block, block)^{-1}   FP64 row-wise substitution.
+// The products carry the m n^2 / 2 - m n 32 FMAs of the off-diagonal part; the
+// substitution keeps the diagonal blocks' m n 32 FMAs on the FP64 pipe.
+namespace {
+constexpr int TRSM_BW = 64;
+struct TrsmLayout {
+    __nv_bfloat16 *Xp, *Yp;
+    int *eX, *mX, *eY, *mY, *cum;
+    double *slots, *U;
+    long ldp;
+    int kch;
+    size_t bytes;
+};
+TrsmLayout trsm_layout(int m, int n, void* ws)
+{
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    char* base = static_cast<char*>(ws);
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        char* q = base ? base + o : nullptr;
+        o += al(bytes);
+        return q;
+    };
+    TrsmLayout L;
+    const int kmax = n > TRSM_BW ? ((n - 1) / TRSM_BW) * TRSM_BW : 1;  // largest off-diagonal K
+    L.ldp = ((long)kmax + 127) / 128 * 128;
+    L.kch = (kmax + KCH - 1) / KCH;
+    const int rt = (m + TM - 1) / TM;
+    const int pieces = (int)((L.ldp / EMU_KS + 63) / 64);
+    L.Xp = reinterpret_cast<__nv_bfloat16*>(take((size_t)EMU_S * m * L.ldp * 2));
+    L.Yp = reinterpret_cast<__nv_bfloat16*>(take((size_t)EMU_S * TRSM_BW * L.ldp * 2));
+    L.eX = reinterpret_cast<int*>(take((size_t)L.kch * m * 4));
+    L.mX = reinterpret_cast<int*>(take((size_t)m * 4));
+    L.eY = reinterpret_cast<int*>(take((size_t)L.kch * TRSM_BW * 4));
+    L.mY = reinterpret_cast<int*>(take((size_t)TRSM_BW * 4));
+    L.cum = reinterpret_cast<int*>(take((size_t)(rt + 2) * 4));
+    L.slots = reinterpret_cast<double*>(take((size_t)rt * pieces * TM * EMU_N * 8));
+    L.U = reinterpret_cast<double*>(take((size_t)m * TRSM_BW * 8));
+    L.bytes = o;
+    return L;
+}
+}  // namespace
+
+size_t trsm_tc_workspace_bytes(int m, int n) { return trsm_layout(m, n, nullptr).bytes; }
+
+cudaError_t launch_trsm_tc(int m, int n, const double* Z, long ldz, const double* R, long ldr, double* Q, long ldq,
+                           void* ws, DevStatus* st, uint64_t limit_ns, int sms, cudaStream_t s)
+{
+    if (m <= 0 || n <= 0) return cudaSuccess;
+    const TrsmLayout L = trsm_layout(m, n, ws);
+    TcPlan p{};
+    p.mode = 1;  // make_args: EMU64 k-step and piece
+    cudaError_t e;
+    for (int jb = 0; jb < n; jb += TRSM_BW) {
+        const int bw = n - jb < TRSM_BW ? n - jb : TRSM_BW;
+        const double* U = nullptr;
+        if (jb > 0) {
+            const int K = jb;
+            const int kch = (K + KCH - 1) / KCH;
+            fill_int_kernel<<<(m + 255) / 256, 256, 0, s>>>(L.mX, m, EXP_NONE);
+            fill_int_kernel<<<1, TRSM_BW, 0, s>>>(L.mY, bw, EXP_NONE);
+            const size_t planeX = (size_t)m * L.ldp, planeY = (size_t)TRSM_BW * L.ldp;
+            split_lower_kernel<1, false><<<dim3(kch, (m + 31) / 32), 256, 0, s>>>(m, K, Q, ldq, EMU_S, L.Xp, L.ldp,
+                                                                                  planeX, L.eX, L.mX);
+            split_tall_kernel<1><<<dim3(kch, (bw + 7) / 8), 256, 0, s>>>(K, bw, R + (long)jb * ldr, ldr, EMU_S, L.Yp,
+                                                                         L.ldp, planeY, L.eY, L.mY);
+            TcArgs a = make_args(p, m, bw, K, 0, EMU_N);
+            a.cum = L.cum;
+            a.slots = L.slots;
+            a.eA = L.eX;
+            a.eB = L.eY;
+            a.emaxA = L.mX;
+            a.emaxB = L.mY;
+            a.st = st;
+            a.limit_ns = limit_ns;
+            item_prefix_kernel<<<1, 32, 0, s>>>(a, L.cum);
+            if ((e = launch_emu(a, L.Xp, L.ldp, planeX, L.Yp, L.ldp, planeY, sms, s)) != cudaSuccess) return e;
+            slot_reduce_kernel<EMU_N><<<(unsigned)(((long)m * bw + 255) / 256), 256, 0, s>>>(a, L.U, m, st);
+            U = L.U;
+        }
+        if ((e = launch_trsm_block(m, jb, bw, Z, ldz, U, m, R, ldr, Q, ldq, st, s)) != cudaSuccess) return e;
+    }
     return cudaGetLastError();
 }
 

@@ -274,10 +274,15 @@ oqr_status normal_equation(oqr_ctx* ctx, int m, int n, const double* A, long lda
     if (o.check == 2) tcb = std::max(tcb, tc_bytes_for(m, n, OQR_FP64_TC, OQR_FP64_TC, as.sa));
     char* tcws_probe = probe.take<char>(tcb);
     (void)tcws_probe;
+    // passes whose Gram runs on the tensor cores also solve Q = X / R with tensor-core products
+    const bool any_tc = prec_first != OQR_FP64 || prec_mid != OQR_FP64 || o.final_prec != OQR_FP64;
+    const size_t trb = any_tc ? trsm_tc_workspace_bytes(m, n) : 0;
+    probe.take<char>(trb);
     if ((v = ensure_ws(ctx, probe.off)) != OQR_OK) return v;
     Carve c(ctx->ws);
     layout_cholqr(c, gp, &partials, &G, &work, &R1, &R2, &R3, &scratch);
     void* tcws = c.take<char>(tcb);
+    void* trws = c.take<char>(trb);
     if ((v = reset_status(ctx, s)) != OQR_OK) return v;
 
     const double* shift_ptr = nullptr;
@@ -299,7 +304,10 @@ oqr_status normal_equation(oqr_ctx* ctx, int m, int n, const double* A, long lda
         if (p == 0 && trace_shift)  // u of the first pass's products: 2^-16 (BF16X3, TC2) or 2^-4 (E4M3)
             OQR_TRY(launch_trace_shift(n, G, n, o.shift_c, prec == OQR_FP8 ? 0.0625 : 1.52587890625e-05, ctx->st, s));
         OQR_TRY(launch_potrf(n, G, n, Rp, ldrp, nullptr, ctx->st, s));
-        OQR_TRY(launch_trsm(m, n, X, ldx, Rp, ldrp, Q, ldq, ctx->st, s));
+        if (prec != OQR_FP64)
+            OQR_TRY(launch_trsm_tc(m, n, X, ldx, Rp, ldrp, Q, ldq, trws, ctx->st, limit, ctx->sm_count, s));
+        else
+            OQR_TRY(launch_trsm(m, n, X, ldx, Rp, ldrp, Q, ldq, ctx->st, s));
         if (passes > 1) {
             if (p == 0) {
                 OQR_TRY(launch_copy_upper(n, R1, n, R2, n, s));
@@ -777,6 +785,19 @@ oqr_status oqr_trsm(oqr_ctx* ctx, int m, int n, const double* Z, long ldz, const
     oqr_status v = reset_status(ctx, s);
     if (v != OQR_OK) return v;
     OQR_TRY(launch_trsm(m, n, Z, ldz, R, ldr, Q, ldq, ctx->st, s));
+    return OQR_OK;
+}
+
+oqr_status oqr_trsm_tc(oqr_ctx* ctx, int m, int n, const double* Z, long ldz, const double* R, long ldr, double* Q,
+                       long ldq, void* stream)
+{
+    if (!ctx || m < 1 || n < 1 || bad_matrix(Z, ldz, m, n) || bad_matrix(R, ldr, n, n) || bad_matrix(Q, ldq, m, n))
+        return OQR_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    oqr_status v = ensure_ws(ctx, trsm_tc_workspace_bytes(m, n));
+    if (v != OQR_OK) return v;
+    if ((v = reset_status(ctx, s)) != OQR_OK) return v;
+    OQR_TRY(launch_trsm_tc(m, n, Z, ldz, R, ldr, Q, ldq, ctx->ws, ctx->st, 4000000000ull, ctx->sm_count, s));
     return OQR_OK;
 }
 

@@ -153,6 +153,9 @@ cudaError_t launch_potrf(int n, const double* G, long ldg, double* R, long ldr, 
                          DevStatus* st, cudaStream_t s);
 cudaError_t launch_trsm(int m, int n, const double* Z, long ldz, const double* R, long ldr, double* Q, long ldq,
                         DevStatus* st, cudaStream_t s);
+// One 64-column block of the blocked TRSM: Q(:, jb:jb+bw) = (Z(:, jb:jb+bw) - U) R_bb^{-1}.
+cudaError_t launch_trsm_block(int m, int jb, int bw, const double* Z, long ldz, const double* U, long ldu,
+                              const double* R, long ldr, double* Q, long ldq, DevStatus* st, cudaStream_t s);
 cudaError_t launch_rprod(int n, const double* U, long ldu, const double* S, long lds, double* R, long ldr,
                          cudaStream_t s);
 cudaError_t launch_copy_upper(int n, const double* S, long lds, double* D, long ldd, cudaStream_t s);
@@ -194,6 +197,13 @@ size_t tc_workspace_bytes(const TcPlan& p);
 cudaError_t launch_tc_gram(const TcPlan& p, const double* A, long lda, const double* Z, long ldz, double* G, long ldg,
                            const double* shift_ptr, void* ws, DevStatus* st, uint64_t limit_ns, int sms,
                            cudaStream_t s, cudaEvent_t* ev = nullptr, bool a_ready = false);
+
+// Blocked TRSM Q = Z / R with FP64-accurate tensor-core products for the
+// off-diagonal blocks and FP64 substitution for the 64 x 64 diagonal blocks
+// (k_tc.cu).  ws holds trsm_tc_workspace_bytes(m, n).
+size_t trsm_tc_workspace_bytes(int m, int n);
+cudaError_t launch_trsm_tc(int m, int n, const double* Z, long ldz, const double* R, long ldr, double* Q, long ldq,
+                           void* ws, DevStatus* st, uint64_t limit_ns, int sms, cudaStream_t s);
 
 // Batched A-CholQR2 (k_batched.cu): one descriptor per instance, n <= 64, m <= 4096.
 constexpr int BATCH_MAX_N = 64;

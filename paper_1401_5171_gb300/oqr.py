@@ -99,6 +99,7 @@ def load(path: str | None = None):
                                     ctypes.POINTER(i), vp]
     lib.oqr_potrf.argtypes = [vp, i, vp, l, d, vp, l, ctypes.POINTER(i), vp]
     lib.oqr_trsm.argtypes = [vp, i, i, vp, l, vp, l, vp, l, vp]
+    lib.oqr_trsm_tc.argtypes = [vp, i, i, vp, l, vp, l, vp, l, vp]
     lib.oqr_rprod.argtypes = [vp, i, vp, l, vp, l, vp, l, vp]
     lib.oqr_check.argtypes = [vp, i, i, vp, l, vp, l, vp, l, ctypes.POINTER(d), ctypes.POINTER(d), vp]
     for name in declared_functions():
@@ -123,7 +124,7 @@ def _raw(name):
 
 
 for _n in ("oqr_default_opts", "oqr_create", "oqr_destroy", "oqr_workspace_size", "oqr_set_workspace",
-           "oqr_get_status", "oqr_cholqr", "oqr_cholqr2", "oqr_cgs2", "oqr_gram", "oqr_gram_noalloc", "oqr_gram_phases", "oqr_potrf", "oqr_trsm",
+           "oqr_get_status", "oqr_cholqr", "oqr_cholqr2", "oqr_cgs2", "oqr_gram", "oqr_gram_noalloc", "oqr_gram_phases", "oqr_potrf", "oqr_trsm", "oqr_trsm_tc",
            "oqr_rprod", "oqr_check", "oqr_batched", "oqr_batched_default_splits", "oqr_features",
            "oqr_mlp_param_count", "oqr_mlp_forward", "oqr_mlp_grad", "oqr_mlp_adam"):
     globals()[_n] = _raw(_n)
@@ -332,16 +333,19 @@ class Oqr:
         st = self.lib.oqr_potrf(self.ctx, n, g, ldg, float(shift), r, ldr, ctypes.byref(info), self._stream(stream))
         return R, st, info.value
 
-    def oqr_trsm(self, Z, R, Q=None, stream=None):
+    def oqr_trsm(self, Z, R, Q=None, stream=None, name="oqr_trsm"):
         m, n = Z.shape
         Q = Q if Q is not None else empty_colmajor(m, n, Z.device)
         z, ldz = _m(Z)
         r, ldr = _m(R)
         q, ldq = _m(Q)
-        st = self.lib.oqr_trsm(self.ctx, m, n, z, ldz, r, ldr, q, ldq, self._stream(stream))
+        st = getattr(self.lib, name)(self.ctx, m, n, z, ldz, r, ldr, q, ldq, self._stream(stream))
         if st != OQR_OK:
-            raise OqrError(st, "oqr_trsm")
+            raise OqrError(st, name)
         return Q
+
+    def oqr_trsm_tc(self, Z, R, Q=None, stream=None):
+        return self.oqr_trsm(Z, R, Q=Q, stream=stream, name="oqr_trsm_tc")
 
     def oqr_rprod(self, U, S, R=None, stream=None):
         n = U.shape[0]

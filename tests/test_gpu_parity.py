@@ -124,6 +124,36 @@ def test_potrf_shift(env):
     assert rel(host(R), oracle.chol_upper(G + 2.5 * np.eye(n))) < 1e-13
 
 
+@pytest.mark.parametrize("m,n", [(1, 1), (63, 20), (1000, 33), (3000, 64), (3000, 65), (2000, 129), (4097, 300),
+                                 (640, 512)])
+def test_trsm_tc_matches_oracle(env, m, n):
+    # blocked solve: FP64-accurate tensor-core products off the diagonal, FP64 substitution in the
+    # 64 x 64 diagonal blocks; single block, a ragged last block and several blocks
+    torch, oqr, ctx = env
+    rng = np.random.default_rng(m + 7 * n)
+    R = np.triu(rng.standard_normal((n, n))) + 3 * np.eye(n)
+    Z = rng.standard_normal((m, n))
+    Qr = oracle.trsm_right_upper(Z, R)
+    Q = host(ctx.oqr_trsm_tc(dev(torch, Z, oqr), dev(torch, R, oqr)))
+    assert rel(Q, Qr) < 1e-13
+    Zd = dev(torch, Z, oqr)
+    ctx.oqr_trsm_tc(Zd, dev(torch, R, oqr), Q=Zd)
+    assert rel(host(Zd), Qr) < 1e-13
+
+
+def test_trsm_tc_rowwise_backward_error(env):
+    # R the Cholesky factor of an ill-conditioned Gram (kappa(R) ~ 1e6): every row q of Q = Z / R
+    # satisfies |z - q R| <= c u |q| |R| up to a modest constant, as row-wise substitution does (Sec. 2)
+    torch, oqr, ctx = env
+    A, Z = inputs.paper_case(4, 2500, 150, 1e4, 1e5, seed=4)
+    R = oracle.chol_upper(oracle.gram(A, Z))
+    Q = host(ctx.oqr_trsm_tc(dev(torch, Z, oqr), dev(torch, R, oqr)))
+    Qf = host(ctx.oqr_trsm(dev(torch, Z, oqr), dev(torch, R, oqr)))
+    res = np.abs(Z - Q @ R).max(axis=1) / (np.abs(Q) @ np.abs(R)).max(axis=1)
+    res_f = np.abs(Z - Qf @ R).max(axis=1) / (np.abs(Qf) @ np.abs(R)).max(axis=1)
+    assert res.max() <= 4 * 150 * 2.0 ** -53, (res.max(), res_f.max())
+
+
 @pytest.mark.parametrize("m,n", [(1, 1), (63, 20), (1000, 33), (2000, 20), (4097, 300), (640, 512)])
 def test_trsm_matches_oracle(env, m, n):
     torch, oqr, ctx = env
