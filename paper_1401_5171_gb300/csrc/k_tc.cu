@@ -511,11 +511,15 @@ struct TcCfg {
     static constexpr int A_TILE = TM * KS * ES;        // bytes
     static constexpr int B_TILE = N * KS * ES;
     static constexpr int STAGE = S * A_TILE + S * B_TILE;
-    static constexpr int STAGES = 2;
-    static constexpr int TMEM_COLS = N <= 32 ? 32 : N <= 64 ? 64 : N <= 128 ? 128 : N <= 256 ? 256 : 512;
+    // as many stages as ~192 KB holds (2..6): a short k-step needs more bytes in flight
+    static constexpr int STAGES = 196608 / STAGE < 2 ? 2 : 196608 / STAGE > 6 ? 6 : 196608 / STAGE;
+    static constexpr int TMEM_COLS = 2 * N <= 128 ? 128 : 2 * N <= 256 ? 256 : 512;  // two accumulator buffers
     static constexpr int KPI = MODE == 2 ? 32 : 16;    // K per MMA instruction (32 bytes of K)
     static constexpr int CH_STEPS = MODE == 0 ? 1 << 30 : KCH / KS;  // k-steps per drained chunk
-    static constexpr size_t SMEM = 1024 + STAGES * (size_t)STAGE + 2048;  // align slack + barriers, exponents
+    static constexpr int MAXCH = 16;                   // chunks per item (items are 2048 long)
+    // align slack + barriers and drain flags + (chunked modes) an item's row and column chunk scales
+    static constexpr size_t SMEM =
+        1024 + STAGES * (size_t)STAGE + 2048 + (MODE != 0 ? (size_t)MAXCH * (TM + N) * sizeof(float) : 0);
     static_assert(MODE == 0 || MODE == 2 || MODE == 3, "mode");
     static_assert(SW == 64 || SW == 128, "swizzle");
     static_assert(N % 64 == 0 && N >= 64 && N <= 256, "N");
@@ -533,10 +537,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE);
     uint64_t* empty = full + C::STAGES;
-    uint64_t* accf = empty + C::STAGES;
-    uint64_t* acce = accf + 1;
-    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(acce + 1);
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);  // colexp follows at +32 ints
+    uint64_t* accf = empty + C::STAGES;  // [2]: accumulator buffer b complete (by chunk parity)
+    uint64_t* acce = accf + 2;           // [2]: accumulator buffer b read by the drain
+    uint64_t* done = acce + 2;           // every MMA of this CTA complete
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(done + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);  // the drain's flag at +32 ints
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (*(volatile int*)&a.st->code != 0) return;
@@ -545,8 +550,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(accf, 1);
-        mbar_init(acce, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&accf[b], 1);
+            mbar_init(&acce[b], 1);
+        }
+        mbar_init(done, 1);
         *abort_flag = 0;
         fence_barrier_init();
         tma_prefetch_desc(&mapA);
@@ -607,8 +615,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     const bool chunk_start = CHUNKED ? ((ks - item.ks0) % C::CH_STEPS == 0) : (ks == item.ks0);
                     const bool chunk_end = CHUNKED ? ((ks - item.ks0 + 1) % C::CH_STEPS == 0 || ks + 1 == item.ks1)
                                                    : (ks + 1 == item.ks1);
-                    if (chunk_start && chunk > 0) {  // the drain must have emptied the accumulators
-                        if (!mbar_wait(acce, (uint32_t)((chunk - 1) & 1), a.limit_ns)) {
+                    const int b = (int)(chunk & 1);  // accumulator buffer of this chunk
+                    const uint32_t d = tmem + (uint32_t)(b * N);
+                    if (chunk_start && chunk >= 2) {  // the drain must have emptied this buffer (two chunks ago)
+                        if (!mbar_wait(&acce[b], (uint32_t)(((chunk - 2) >> 1) & 1), a.limit_ns)) {
                             fail(2);
                             break;
                         }
@@ -627,7 +637,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         for (int kk = 0; kk < KS / C::KPI; ++kk) {
                             const uint64_t ad = smem_desc(base + kk * 32, C::SW);
                             const uint64_t bd = smem_desc(base + C::A_TILE + kk * 32, C::SW);
-                            umma_e4m3(tmem, ad, bd, idesc, (chunk_start && kk == 0) ? 0u : 1u);
+                            umma_e4m3(d, ad, bd, idesc, (chunk_start && kk == 0) ? 0u : 1u);
                         }
                     } else {
                         // hi*hi, hi*lo, lo*hi into one accumulator
@@ -639,18 +649,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                 const uint64_t ad = smem_desc(base + sa[p] * C::A_TILE + kk * 32, C::SW);
                                 const uint64_t bd =
                                     smem_desc(base + S * C::A_TILE + tb[p] * C::B_TILE + kk * 32, C::SW);
-                                umma_bf16(tmem, ad, bd, idesc, (chunk_start && p == 0 && kk == 0) ? 0u : 1u);
+                                umma_bf16(d, ad, bd, idesc, (chunk_start && p == 0 && kk == 0) ? 0u : 1u);
                             }
                     }
                     umma_commit(&empty[stg]);
                     if (chunk_end) {
-                        umma_commit(accf);
+                        umma_commit(&accf[b]);
                         ++chunk;
                     }
                 }
             }
-            // the last chunk's accumulators must have been read before TMEM is released
-            if (chunk > 0) mbar_wait(acce, (uint32_t)((chunk - 1) & 1), a.limit_ns);
+            // every MMA issued by this thread must be complete before TMEM is released
+            umma_commit(done);
+            mbar_wait(done, 0, a.limit_ns);
         }
     } else {
         // ------------------------------------------------ drain (warps 2..9)
@@ -663,36 +674,55 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int half = (warp - 2) >> 2;     // which half of the N columns
         const int r = q * 32 + lane;          // row within the tile = TMEM lane
         const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(half * NH);
-        int* colexp = const_cast<int*>(abort_flag) + 32;  // N column scales of the current chunk (as floats)
-        volatile int* go = colexp + 256;                  // outcome of the wait, published by dt == 0
+        volatile int* go = const_cast<int*>(abort_flag) + 32;  // outcome of the wait, published by dt == 0
+        // chunked modes: the item's row scales [chunk][row] and column scales [chunk][column]
+        float* rowsc = reinterpret_cast<float*>(smem + C::STAGES * C::STAGE + 2048);
+        float* colsc = rowsc + C::MAXCH * TM;
         long chunk = 0;
         bool stop = false;
         for (int j = blockIdx.x; j < a.nitems && !stop; j += gridDim.x) {
             const Item item = item_of(a, j);
-            const long gi = (long)item.I * TM + r;
-            const bool row_ok = gi < a.rowsA;
-            double* slot = a.slots + (size_t)j * TM * N + (size_t)r * N + half * NH;
+            double* slot = a.slots + (size_t)j * TM * N + (size_t)r * N + half * NH;  // MODE 0: FP64 slots
             float H[CHUNKED ? NH : 1];
 #pragma unroll
             for (int c = 0; c < (CHUNKED ? NH : 1); ++c) H[c] = 0.f;
-            const int emax_r = (CHUNKED && row_ok) ? a.emaxA[gi] : 0;
             const int nsteps = item.ks1 - item.ks0;
             const int nch = CHUNKED ? (nsteps + C::CH_STEPS - 1) / C::CH_STEPS : 1;
-            for (int ch = 0; ch < nch; ++ch, ++chunk) {
-                const int kcg = (item.ks0 * KS) / KCH + ch;  // global 128-chunk index
-                if (dt == 0) {
-                    const bool ok = mbar_wait(accf, (uint32_t)(chunk & 1), a.limit_ns);
-                    if (!ok) fail(4);
-                    *go = (ok && !*abort_flag) ? 1 : 0;
+            if constexpr (CHUNKED) {
+                // FP8: products of x 2^(8-e_r) and y 2^(8-e_c), scaled back by 2^(e_r + e_c - 16); TC2:
+                // products of slices of x 2^(7-e_r) and y 2^(7-e_c), scaled back by 2^(e_r + e_c - 14);
+                // both relative to the row and column maxima.  All of the item's scales are loaded
+                // once, so no global load sits between a chunk's accumulators and their drain.
+                const int kc0 = (item.ks0 * KS) / KCH;
+                for (int e = dt; e < nch * TM; e += 256) {
+                    const int ch = e / TM, rr = e % TM;
+                    const long g = (long)item.I * TM + rr;
+                    float v = 0.0f;
+                    if (g < a.rowsA) {
+                        const int er = a.eA[(size_t)(kc0 + ch) * a.rowsA + g];
+                        if (er != EXP_NONE) v = pow2f(er - a.emaxA[g] - (MODE == 2 ? 16 : 14));
+                    }
+                    rowsc[ch * TM + rr] = v;
                 }
-                if (CHUNKED && dt < N) {  // column scale 2^(e_col - emax_col) of this chunk (0 if empty)
-                    const int col = item.c * N + dt;
+                for (int e = dt; e < nch * N; e += 256) {
+                    const int ch = e / N, cc = e % N;
+                    const int col = item.c * N + cc;
                     float v = 0.0f;
                     if (col < a.colsB) {
-                        const int eb = a.eB[(size_t)kcg * a.colsB + col];
+                        const int eb = a.eB[(size_t)(kc0 + ch) * a.colsB + col];
                         if (eb != EXP_NONE) v = pow2f(eb - a.emaxB[col]);
                     }
-                    reinterpret_cast<float*>(colexp)[dt] = v;
+                    colsc[ch * N + cc] = v;
+                }
+                asm volatile("bar.sync 1, 256;" ::: "memory");
+            }
+            for (int ch = 0; ch < nch; ++ch, ++chunk) {
+                const int b = (int)(chunk & 1);
+                const uint32_t buf = lane_addr + (uint32_t)(b * N);
+                if (dt == 0) {
+                    const bool ok = mbar_wait(&accf[b], (uint32_t)((chunk >> 1) & 1), a.limit_ns);
+                    if (!ok) fail(4);
+                    *go = (ok && !*abort_flag) ? 1 : 0;
                 }
                 asm volatile("bar.sync 1, 256;" ::: "memory");
                 if (*go == 0) {
@@ -700,17 +730,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     break;
                 }
                 tc_fence_after();
-                if constexpr (CHUNKED) {
-                    // FP8: products of x 2^(8-e_r) and y 2^(8-e_c), scaled back by 2^(e_r + e_c - 16); TC2:
-                    // products of slices of x 2^(7-e_r) and y 2^(7-e_c), scaled back by 2^(e_r + e_c - 14);
-                    // both relative to the row and column maxima; FP32 accumulation suits their precision
-                    const int e_r = row_ok ? a.eA[(size_t)kcg * a.rowsA + gi] : EXP_NONE;
-                    const float* colscale = reinterpret_cast<const float*>(colexp) + half * NH;
-                    const float rs = e_r == EXP_NONE ? 0.0f : pow2f(e_r - emax_r - (MODE == 2 ? 16 : 14));
+                if constexpr (CHUNKED) {  // FP32 accumulation suits these precisions
+                    const float* colscale = colsc + ch * N + half * NH;
+                    const float rs = rowsc[ch * TM + r];
 #pragma unroll
                     for (int h = 0; h < NH / 32; ++h) {
                         float v[32];
-                        tmem_ld32(lane_addr + (uint32_t)(h * 32), v);
+                        tmem_ld32(buf + (uint32_t)(h * 32), v);
 #pragma unroll
                         for (int c = 0; c < 32; ++c) H[h * 32 + c] = fmaf(__fmul_rn(v[c], rs), colscale[h * 32 + c],
                                                                           H[h * 32 + c]);
@@ -719,23 +745,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll 1
                     for (int h = 0; h < NH / 32; ++h) {
                         float v[32];
-                        tmem_ld32(lane_addr + (uint32_t)(h * 32), v);
+                        tmem_ld32(buf + (uint32_t)(h * 32), v);
 #pragma unroll
                         for (int c = 0; c < 32; ++c) slot[h * 32 + c] = (double)v[c];
                     }
                 }
                 tc_fence_before();
-                asm volatile("bar.sync 1, 256;" ::: "memory");  // TMEM and colexp fully read
-                if (dt == 0) mbar_arrive(acce);
+                asm volatile("bar.sync 1, 256;" ::: "memory");  // TMEM and the scales fully read
+                if (dt == 0) mbar_arrive(&acce[b]);
             }
             if (stop) break;
             if constexpr (CHUNKED) {
+                // FP32 slots relative to 2^(emax_row + emax_col): the reduce sums the pieces and scales
+                // once per output element (no FP64 work here)
+                float* fslot = reinterpret_cast<float*>(a.slots) + (size_t)j * TM * N + (size_t)r * N + half * NH;
 #pragma unroll
-                for (int c = 0; c < NH; ++c) {
-                    const int col = item.c * N + half * NH + c;
-                    const int bmax = col < a.colsB ? __ldg(a.emaxB + col) : 0;
-                    slot[c] = ldexp((double)H[c], emax_r + bmax);
-                }
+                for (int c = 0; c < NH; c += 4)
+                    *reinterpret_cast<float4*>(fslot + c) = make_float4(H[c], H[c + 1], H[c + 2], H[c + 3]);
             }
         }
     }
@@ -764,6 +790,27 @@ __global__ void slot_reduce_kernel(TcArgs a, double* out, long ldo, const DevSta
         s += a.slots[(size_t)j * TM * N + (size_t)(row % TM) * N + (col % N)];
     }
     out[row + (long)col * ldo] = s;
+}
+
+// Chunked modes (FP8, TC2): out = (sum over the pieces of the FP32 slots, in
+// piece order) 2^(emax_row + emax_col).
+template <int N>
+__global__ void slot_reduce_f32_kernel(TcArgs a, double* out, long ldo, const DevStatus* st)
+{
+    if (*(volatile const int*)&st->code != 0) return;
+    const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long)a.rowsA * a.colsB) return;
+    const int col = (int)(e / a.rowsA), row = (int)(e % a.rowsA);
+    const int I = row / TM, c = col / N;
+    const int np = pieces_of(a, I);
+    const float* slots = reinterpret_cast<const float*>(a.slots);
+    float s = 0.0f;
+    for (int p = 0; p < np; ++p) {
+        const int j = a.cum[I] + p * a.cc + c;
+        s += slots[(size_t)j * TM * N + (size_t)(row % TM) * N + (col % N)];
+    }
+    const int er = a.emaxA[row], ec = a.emaxB[col];
+    out[row + (long)col * ldo] = (er == EXP_NONE || ec == EXP_NONE) ? 0.0 : ldexp((double)s, er + ec);
 }
 
 // G = C + C^T (+ shift I), exactly symmetric.
@@ -807,8 +854,26 @@ constexpr int EMU_CH = KCH / EMU_KS;                // k-steps per chunk
 constexpr int EMU_DRAIN = 512;                      // drain threads
 constexpr int EMU_THREADS = 64 + EMU_DRAIN;
 constexpr int EMU_CPT = EMU_N / 4;                  // columns per drain thread
-constexpr size_t EMU_SMEM = 1024 + (size_t)EMU_STAGES * EMU_STAGE + 1024;
+constexpr int EMU_MAXCH = 16;                       // chunks per item (items are 2048 long)
+// align slack + stages + barriers and flags + an item's row and column chunk scales
+constexpr size_t EMU_SMEM = 1024 + (size_t)EMU_STAGES * EMU_STAGE + 1024 + (size_t)EMU_MAXCH * (TM + EMU_N) * 4;
 static_assert(EMU_STAGE % 1024 == 0, "stage alignment");
+
+// x 2^k as a double, exact: for a normal x with the result in the normal range
+// the double is assembled from x's sign, exponent and significand with integer
+// operations (no FP64 instruction); otherwise by conversion and ldexp.
+__device__ inline double f32_scaled_to_f64(float x, int k)
+{
+    const unsigned u = __float_as_uint(x);
+    const int ex = (int)((u >> 23) & 0xFF);
+    const int e64 = ex - 127 + k + 1023;
+    if (ex != 0 && ex != 0xFF && e64 >= 1 && e64 <= 2046) {
+        const unsigned long long b = ((unsigned long long)(u >> 31) << 63) | ((unsigned long long)e64 << 52) |
+                                     ((unsigned long long)(u & 0x7FFFFF) << 29);
+        return __longlong_as_double((long long)b);
+    }
+    return x == 0.0f ? 0.0 : ldexp((double)x, k);
+}
 
 // 16 consecutive accumulator columns of this thread's TMEM lane; the load and
 // its wait are one asm statement, so no use of r can precede the wait.
@@ -866,13 +931,15 @@ __global__ void __launch_bounds__(EMU_THREADS, 1)
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + EMU_STAGES * EMU_STAGE);
     uint64_t* empty = full + EMU_STAGES;
     uint64_t* accf = empty + EMU_STAGES;  // chunk's MMAs complete
-    uint64_t* lo_empty = accf + 1;        // [4]: chunk's L5, L4, L3, L2 read (one barrier per level)
-    uint64_t* hi_empty = lo_empty + 4;    // [2]: chunk's L6, L7+8 read, by chunk parity
+    uint64_t* lo_empty = accf + 1;        // chunk's L2..L5 read
+    uint64_t* hi_empty = lo_empty + 1;    // [2]: chunk's L6, L7+8 read, by chunk parity
     uint64_t* done = hi_empty + 2;        // every MMA of this CTA complete
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(done + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
     volatile int* go = abort_flag + 1;                                 // outcome of the drain's wait
-    float* colscale = reinterpret_cast<float*>(smem + EMU_STAGES * EMU_STAGE + 256);  // EMU_N floats
+    // the item's row scales [chunk][row] and column scales [chunk][column]
+    float* rowsc = reinterpret_cast<float*>(smem + EMU_STAGES * EMU_STAGE + 1024);
+    float* colsc = rowsc + EMU_MAXCH * TM;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (*(volatile int*)&a.st->code != 0) return;
@@ -882,7 +949,7 @@ __global__ void __launch_bounds__(EMU_THREADS, 1)
             mbar_init(&empty[s], 1);
         }
         mbar_init(accf, 1);
-        for (int l = 0; l < 4; ++l) mbar_init(&lo_empty[l], EMU_DRAIN / 32);  // one arrival per drain warp
+        mbar_init(lo_empty, 1);
         mbar_init(&hi_empty[0], 1);
         mbar_init(&hi_empty[1], 1);
         mbar_init(done, 1);
@@ -968,21 +1035,17 @@ __global__ void __launch_bounds__(EMU_THREADS, 1)
                     emu_issue_level<6>(hi, dA, dB, idesc, cstart);
                     emu_issue_level<7>(hi + 64u, dA, dB, idesc, cstart);
                     emu_issue_level<8>(hi + 64u, dA, dB, idesc, false);
-                    // L5, L4, L3, L2 in the order the drain releases their slots; in a chunk's first
-                    // k-step each waits for the previous chunk's value of its level to have been read
-                    auto lo_ready = [&](int l) {
-                        if (!(cstart && chunk >= 1)) return true;
-                        if (!mbar_wait(&lo_empty[l], (uint32_t)((chunk - 1) & 1), a.limit_ns)) return false;
+                    if (cstart && chunk >= 1) {  // L2..L5 slots: the previous chunk's must have been read
+                        if (!mbar_wait(lo_empty, (uint32_t)((chunk - 1) & 1), a.limit_ns)) {
+                            fail(15);
+                            ok = false;
+                            break;
+                        }
                         tc_fence_after();
-                        return true;
-                    };
-                    if (!lo_ready(0)) { fail(15); ok = false; break; }
+                    }
                     emu_issue_level<5>(tmem + 192u, dA, dB, idesc, cstart);
-                    if (!lo_ready(1)) { fail(15); ok = false; break; }
                     emu_issue_level<4>(tmem + 128u, dA, dB, idesc, cstart);
-                    if (!lo_ready(2)) { fail(15); ok = false; break; }
                     emu_issue_level<3>(tmem + 64u, dA, dB, idesc, cstart);
-                    if (!lo_ready(3)) { fail(15); ok = false; break; }
                     emu_issue_level<2>(tmem, dA, dB, idesc, cstart);
                     umma_commit(&empty[stg]);
                     if (cend) {
@@ -1017,43 +1080,54 @@ __global__ void __launch_bounds__(EMU_THREADS, 1)
             const int emax_r = row_ok ? a.emaxA[gi] : 0;
             const int nsteps = item.ks1 - item.ks0;
             const int nch = (nsteps + EMU_CH - 1) / EMU_CH;
+            {
+                // all of the item's scales, loaded once: row scale 2^(e_row - emax_row - 14) (x y =
+                // 2^(e_r + e_c - 14) times the sum of the slice products) and column scale
+                // 2^(e_col - emax_col), 0 for an all-zero chunk; no global load then sits between a
+                // chunk's accumulators and their drain
+                const int kc0 = (item.ks0 * EMU_KS) / KCH;
+                for (int e = dt; e < nch * TM; e += EMU_DRAIN) {
+                    const int ch = e / TM, rr = e % TM;
+                    const long gr = (long)item.I * TM + rr;
+                    float v = 0.0f;
+                    if (gr < a.rowsA) {
+                        const int er = a.eA[(size_t)(kc0 + ch) * a.rowsA + gr];
+                        if (er != EXP_NONE) v = pow2f(er - a.emaxA[gr] - 14);
+                    }
+                    rowsc[ch * TM + rr] = v;
+                }
+                for (int e = dt; e < nch * EMU_N; e += EMU_DRAIN) {
+                    const int ch = e / EMU_N, cc = e % EMU_N;
+                    const int col = item.c * EMU_N + cc;
+                    float v = 0.0f;
+                    if (col < a.colsB) {
+                        const int eb = a.eB[(size_t)(kc0 + ch) * a.colsB + col];
+                        if (eb != EXP_NONE) v = pow2f(eb - a.emaxB[col]);
+                    }
+                    colsc[ch * EMU_N + cc] = v;
+                }
+            }
             for (int ch = 0; ch < nch; ++ch, ++chunk) {
-                const int kcg = (item.ks0 * EMU_KS) / KCH + ch;  // global 128-chunk index
                 if (dt == 0) {
                     const bool okw = mbar_wait(accf, (uint32_t)(chunk & 1), a.limit_ns);
                     if (!okw) fail(16);
                     *go = (okw && !*abort_flag) ? 1 : 0;
                 }
-                if (dt < EMU_N) {  // column scale 2^(e_col - emax_col) of this chunk (0 if empty)
-                    const int col = item.c * EMU_N + dt;
-                    float v = 0.0f;
-                    if (col < a.colsB) {
-                        const int eb = a.eB[(size_t)kcg * a.colsB + col];
-                        if (eb != EXP_NONE) v = pow2f(eb - a.emaxB[col]);
-                    }
-                    colscale[dt] = v;
-                }
-                asm volatile("bar.sync 1, 512;" ::: "memory");
+                asm volatile("bar.sync 1, 512;" ::: "memory");  // also publishes the item's scales
                 if (*go == 0) {
                     stop = true;
                     break;
                 }
                 tc_fence_after();
-                // row scale 2^(e_row - emax_row - 14): x y = 2^(e_r + e_c - 14) sum of the slice products
-                const int e_r = row_ok ? a.eA[(size_t)kcg * a.rowsA + gi] : EXP_NONE;
-                const float rs = e_r == EXP_NONE ? 0.0f : pow2f(e_r - emax_r - 14);
+                const float rs = rowsc[ch * TM + r];
                 float sc[EMU_CPT];
 #pragma unroll
-                for (int c = 0; c < EMU_CPT; ++c) sc[c] = __fmul_rn(rs, colscale[g * EMU_CPT + c]);  // exact
-                // L5, L4, L3, L2: exact level sums, added into (H, L) by TwoSum; each level's slot is
-                // released (one arrival per warp) as soon as this warp has read it
+                for (int c = 0; c < EMU_CPT; ++c) sc[c] = __fmul_rn(rs, colsc[ch * EMU_N + g * EMU_CPT + c]);  // exact
+                // L5, L4, L3, L2: exact level sums, added into (H, L) by TwoSum
 #pragma unroll
                 for (int lv = 0; lv < 4; ++lv) {
                     uint32_t v[EMU_CPT];
                     tmem_ld16(lane_addr + (uint32_t)((3 - lv) * 64), v);
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&lo_empty[lv]);
 #pragma unroll
                     for (int c = 0; c < EMU_CPT; ++c) {
                         const float t = __fmul_rn(__uint_as_float(v[c]), sc[c]);
@@ -1064,6 +1138,9 @@ __global__ void __launch_bounds__(EMU_THREADS, 1)
                         L[c] = __fadd_rn(L[c], err);
                     }
                 }
+                tc_fence_before();
+                asm volatile("bar.sync 1, 512;" ::: "memory");  // L2..L5 fully read
+                if (dt == 0) mbar_arrive(lo_empty);
                 // L6 and L7+8: below 2^-29 of the chunk's scale, added into the low part
                 const uint32_t hi = lane_addr + 256u + (uint32_t)((chunk & 1) * 128);
                 uint32_t v6[EMU_CPT], v78[EMU_CPT];
@@ -1076,23 +1153,22 @@ __global__ void __launch_bounds__(EMU_THREADS, 1)
                     H[c] = sm;
                 }
                 tc_fence_before();
-                asm volatile("bar.sync 1, 512;" ::: "memory");  // L6, L7+8 and colscale fully read
+                asm volatile("bar.sync 1, 512;" ::: "memory");  // L6, L7+8 and the scales fully read
                 if (dt == 0) mbar_arrive(&hi_empty[chunk & 1]);
             }
             if (stop) break;
-            // H + L (exact in FP64) times 2^(emax_row + emax_col), into this item's FP64 slot; the FP64
-            // work overlaps the MMAs of the next item
+            // (H + L) 2^(emax_row + emax_col) into this item's FP64 slot: H and L become scaled doubles
+            // by integer operations, and one FP64 add (exact: H and L do not overlap) joins them
             double* slot = a.slots + (size_t)j * TM * EMU_N + (size_t)r * EMU_N + g * EMU_CPT;
 #pragma unroll
             for (int c = 0; c < EMU_CPT; ++c) {
                 const int col = item.c * EMU_N + g * EMU_CPT + c;
                 const int ec = col < a.colsB ? __ldg(a.emaxB + col) : EXP_NONE;
-                const int k = emax_r + ec;
-                const double hl = (double)H[c] + (double)L[c];
                 double out = 0.0;
-                if (row_ok && emax_r != EXP_NONE && ec != EXP_NONE)
-                    out = (k >= -1022 && k <= 1023) ? hl * __longlong_as_double((long long)(k + 1023) << 52)
-                                                    : ldexp(hl, k);
+                if (row_ok && emax_r != EXP_NONE && ec != EXP_NONE) {
+                    const int k = emax_r + ec;
+                    out = f32_scaled_to_f64(H[c], k) + f32_scaled_to_f64(L[c], k);
+                }
                 slot[c] = out;
             }
         }
@@ -1277,6 +1353,11 @@ void launch_slot_reduce(const TcPlan& p, const TcArgs& a, double* out, long ldo,
 {
     const long tot = (long)a.rowsA * a.colsB;
     const unsigned g = (unsigned)((tot + 255) / 256);
+    if (p.mode == 2 || p.mode == 3) {
+        if (p.N == 64) slot_reduce_f32_kernel<64><<<g, 256, 0, s>>>(a, out, ldo, st);
+        else slot_reduce_f32_kernel<128><<<g, 256, 0, s>>>(a, out, ldo, st);
+        return;
+    }
     if (p.N == 64) slot_reduce_kernel<64><<<g, 256, 0, s>>>(a, out, ldo, st);
     else if (p.N == 128) slot_reduce_kernel<128><<<g, 256, 0, s>>>(a, out, ldo, st);
     else slot_reduce_kernel<256><<<g, 256, 0, s>>>(a, out, ldo, st);
