@@ -252,7 +252,11 @@ def launches_per_step(path, n):
             shared = prec in (3, 4) and a_split_held  # the EMU64-family split of A is reused
             gram = 10 + (0 if prec == 1 else 2 if shared else 3) - (1 if shared else 0)
             a_split_held = prec in (3, 4)
-        total += gram + potrf + 1                    # + TRSM
+        # TRSM: FP64 substitution (1 kernel), or in 64-column blocks with tensor-core products:
+        # 1 kernel for the first block, then fills x2, row split, column split, item prefix, product,
+        # reduce and the block solve
+        trsm = 1 if prec == 0 else 1 + 8 * ((n + 63) // 64 - 1)
+        total += gram + potrf + trsm
     total += passes if passes > 1 else 0             # R copy + (passes - 1) products
     if kw.get("shifted"):
         total += 2                                   # norms + shift
@@ -361,7 +365,7 @@ def main():
         peak = float(peaks.get("bf16_tflops", 1899.1))
         roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak,
-                    "traffic": ncu_traffic("tc_emu_u_m32768_n256", ["paper_1401_5171_gb300/csrc/k_tc.cu"])
+                    "traffic": ncu_traffic("emu_kernel_u_m32768_n256", ["paper_1401_5171_gb300/csrc/k_tc.cu"])
                     if (m, n) == (32768, 256) else None,
                     "kernel": "emu_kernel (U = M Z: 28 BF16 slice products into 6 TMEM level accumulators, "
                               "tcgen05 kind::f16, N = 64)",
