@@ -15,7 +15,7 @@ namespace {
 // (Algorithm 1, line 3).  Right-looking, 32-column panels, one SM's FP64 rate
 // being far too low for n^3/3 flops on a single CTA: per panel
 //   potrf_diag  (1 CTA)   factor the 32 x 32 diagonal block in shared memory;
-//   potrf_row   (CTAs of 16 columns) solve the panel row R(p, c) <- D^{-T} R(p, c);
+//   potrf_row   (a warp per column) solve the panel row R(p, c) <- D^{-T} R(p, c);
 //   potrf_trail (tiles)   R(r, c) -= sum_k R(p_k, r) R(p_k, c) on the trailing
 //                         upper triangle, 16 x 16 tiles.
 // A pivot that is not positive (or NaN) stops the factorization: the status
@@ -38,72 +38,103 @@ __global__ void potrf_init_kernel(int n, const double* __restrict__ G, long ldg,
     R[i + j * ldr] = v;
 }
 
-// Diagonal block of panel jb: one thread per element of the 32 x 32 block D
-// (thread (ty, tx) owns D[ty][tx], ty <= tx).  Step j reads the pivot
-// p = D[j][j] (every thread computes 1/p itself), writes row j of R as
-// D[j][c] / sqrt(p), and updates D[r][c] -= (D[j][r] / p) D[j][c] for
-// j < r <= c; one barrier per step.  The pivot chain is the critical path of
-// the whole factorization, so nothing else waits on the square root.
-__global__ void __launch_bounds__(1024) potrf_diag_kernel(int n, int jb, double* R, long ldr, DevStatus* st)
+// GB300's FP64 pipe holds a sub-partition for about 64 clocks per 32-lane FP64
+// instruction, so the factorization's dependent pivot chain is costed in FP64
+// warp-instructions: the kernels below keep them few and densely packed.
+//
+// Diagonal block of panel jb.  The pairs (r, c), 0 < r <= c < 32, are listed
+// by decreasing r; at pivot step j the pairs still updated (r > j) are a
+// prefix of that list, (31 - j)(32 - j)/2 long, so the update runs on densely
+// packed threads.  The thread that owns (j+1, j+1) computes the next pivot's
+// reciprocal right after updating it, so the division overlaps the rest of the
+// update.  R's rows are written at the end (row r scaled by 1/sqrt(pivot r)).
+constexpr int PAIRS = PNB * (PNB - 1) / 2;  // 496
+__global__ void __launch_bounds__(512) potrf_diag_kernel(int n, int jb, double* R, long ldr, DevStatus* st)
 {
     __shared__ double D[PNB][PNB + 1];
+    __shared__ double pinv[2];
+    __shared__ int bad;
     if (*(volatile int*)&st->code != 0) return;
     const int nb = min(PNB, n - jb);
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    const bool mine = ty < nb && tx < nb && ty <= tx;
-    if (mine) D[ty][tx] = R[(jb + ty) + (long)(jb + tx) * ldr];
+    for (int e = threadIdx.x; e < PNB * PNB; e += blockDim.x) {
+        const int i = e % PNB, j = e / PNB;
+        D[i][j] = (i <= j && j < nb) ? R[(jb + i) + (long)(jb + j) * ldr] : (i == j ? 1.0 : 0.0);
+    }
+    // this thread's pair: index t in the list ordered by decreasing r, then increasing c
+    const int t = threadIdx.x;
+    int pr = 0, pc = 0;
+    if (t < PAIRS) {
+        int rem = t, r = PNB - 1;
+        while (rem >= PNB - r) {
+            rem -= PNB - r;
+            --r;
+        }
+        pr = r;
+        pc = r + rem;
+    }
+    if (t == 0) bad = 0;
+    __syncthreads();
+    if (t == 0) {
+        const double p0 = D[0][0];
+        if (!(p0 > 0.0)) bad = jb + 1;
+        pinv[0] = 1.0 / p0;
+    }
     __syncthreads();
     for (int j = 0; j < nb; ++j) {
-        const double piv = D[j][j];
-        if (!(piv > 0.0)) {  // the same value in every thread: a uniform exit
-            if (threadIdx.x == 0) raise_status(st, OQR_ERR_NOT_SPD, jb + j + 1, TAG_POTRF);
+        if (bad) {  // the same value in every thread: a uniform exit
+            if (t == 0) raise_status(st, OQR_ERR_NOT_SPD, bad, TAG_POTRF);
             return;
         }
-        if (ty == j && mine) R[(jb + j) + (long)(jb + tx) * ldr] = tx == j ? sqrt(piv) : D[j][tx] / sqrt(piv);
-        if (ty > j && mine) {
-            const double pinv = 1.0 / piv;
-            D[ty][tx] -= (D[j][ty] * pinv) * D[j][tx];
+        const int active = (PNB - 1 - j) * (PNB - j) / 2;
+        if (t < active) {  // pr > j
+            const double v = D[pr][pc] - (D[j][pr] * pinv[j & 1]) * D[j][pc];
+            D[pr][pc] = v;
+            if (pr == j + 1 && pc == j + 1 && j + 1 < nb) {  // look-ahead: the next pivot is final now
+                if (!(v > 0.0)) bad = jb + j + 2;
+                pinv[(j + 1) & 1] = 1.0 / v;
+            }
         }
         __syncthreads();
     }
+    // R(block) rows: R[r][r] = sqrt(d_r), R[r][c] = D[r][c] / sqrt(d_r)
+    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+        const int i = e % nb, c = e / nb;
+        if (i > c) continue;
+        const double sd = sqrt(D[i][i]);
+        R[(jb + i) + (long)(jb + c) * ldr] = i == c ? sd : D[i][c] / sd;
+    }
 }
 
-// Panel row: R(p, c) <- R(p, p)^{-T} R(p, c) for the trailing columns c, one
-// thread per column (column-oriented substitution with the reciprocals of
-// the diagonal); PROW_COLS columns per CTA spread the FP64 work over SMs.
-constexpr int PROW_COLS = 16;
-__global__ void __launch_bounds__(PROW_COLS) potrf_row_kernel(int n, int jb, double* R, long ldr,
-                                                              const DevStatus* st)
+// Panel row: R(p, c) <- R(p, p)^{-T} R(p, c) for the trailing columns c.  One
+// warp per column, lane i = row i: column-oriented substitution, x_i = b_i /
+// d_i broadcast by a shuffle, then b_k -= R(i, k) x_i on lanes k > i (two FP64
+// instructions per step); PROW_WARPS columns per CTA.
+constexpr int PROW_WARPS = 4;
+__global__ void __launch_bounds__(32 * PROW_WARPS) potrf_row_kernel(int n, int jb, double* R, long ldr,
+                                                                    const DevStatus* st)
 {
     __shared__ double D[PNB][PNB + 1];
     __shared__ double dinv[PNB];
     if (*(volatile const int*)&st->code != 0) return;
     const int nb = min(PNB, n - jb);
-    for (int e = threadIdx.x; e < PNB * PNB; e += PROW_COLS) {
+    for (int e = threadIdx.x; e < PNB * PNB; e += blockDim.x) {
         const int i = e % PNB, j = e / PNB;
         D[i][j] = (i <= j && i < nb && j < nb) ? R[(jb + i) + (long)(jb + j) * ldr] : 0.0;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < nb; i += PROW_COLS) dinv[i] = 1.0 / D[i][i];
+    if (threadIdx.x < nb) dinv[threadIdx.x] = 1.0 / D[threadIdx.x][threadIdx.x];
     __syncthreads();
-    const int c = jb + nb + blockIdx.x * PROW_COLS + threadIdx.x;
-    if (c >= n) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int c = jb + nb + blockIdx.x * PROW_WARPS + w;
+    if (c >= n) return;  // a whole warp leaves together
     double* col = R + jb + (long)c * ldr;
-    double b[PNB];
-#pragma unroll
-    for (int i = 0; i < PNB; ++i) b[i] = i < nb ? col[i] : 0.0;
-#pragma unroll
-    for (int i = 0; i < PNB; ++i) {
-        if (i < nb) {
-            asm volatile("" ::: "memory");  // keeps only row i of D live: no hoisted loads, no spills
-            b[i] *= dinv[i];
-#pragma unroll
-            for (int k = i + 1; k < PNB; ++k) b[k] -= D[i][k] * b[i];
-        }
+    double b = lane < nb ? col[lane] : 0.0;
+    for (int i = 0; i < nb; ++i) {
+        const double x = __shfl_sync(0xffffffffu, b, i) * dinv[i];
+        if (lane == i) b = x;
+        else if (lane > i) b -= D[i][lane] * x;
     }
-#pragma unroll
-    for (int i = 0; i < PNB; ++i)
-        if (i < nb) col[i] = b[i];
+    if (lane < nb) col[lane] = b;
 }
 
 // Trailing update on TT x TT tiles (tr <= tc) of the upper triangle right of
@@ -508,10 +539,10 @@ cudaError_t launch_potrf(int n, const double* G, long ldg, double* R, long ldr, 
     const long total = (long)n * n;
     potrf_init_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(n, G, ldg, R, ldr, shift_ptr, st);
     for (int jb = 0; jb < n; jb += PNB) {
-        potrf_diag_kernel<<<1, 1024, 0, s>>>(n, jb, R, ldr, st);
+        potrf_diag_kernel<<<1, 512, 0, s>>>(n, jb, R, ldr, st);
         const int rest = n - jb - PNB;
         if (rest <= 0) break;
-        potrf_row_kernel<<<(rest + PROW_COLS - 1) / PROW_COLS, PROW_COLS, 0, s>>>(n, jb, R, ldr, st);
+        potrf_row_kernel<<<(rest + PROW_WARPS - 1) / PROW_WARPS, 32 * PROW_WARPS, 0, s>>>(n, jb, R, ldr, st);
         const int nt = (rest + TT - 1) / TT;
         potrf_trail_kernel<<<nt * (nt + 1) / 2, TT * TT, 0, s>>>(n, jb, R, ldr, st);
     }

@@ -119,14 +119,24 @@ __device__ inline void emu_slices7(double x, int e, float* out)
         const unsigned long long mag = k >= 0 ? (b.M << k) : rne_shift(b.M, -k);
         Y = b.neg ? -(long long)mag : (long long)mag;
     }
+    // Balanced digits from the bytes of Y's two's complement, lowest first: with carry c in, the
+    // digit is d = byte + c - 256 c' where c' = (byte + c >= 128); v = byte + c + 128 gives
+    // d + 128 = v & 255 and c' = v >> 8.  d 2^(-8s) is then formed exactly from d + 128 by a
+    // magic-number float: 2^(23-8s) + (d + 128) 2^(-8s), minus 2^(23-8s) + 128 2^(-8s).
+    const unsigned lo = (unsigned)(unsigned long long)Y;
+    const unsigned hi = (unsigned)((unsigned long long)Y >> 32);
+    unsigned c = 0;
 #pragma unroll
-    for (int s = 6; s >= 1; --s) {
-        int d = (int)(Y & 255);
-        if (d > 127) d -= 256;
-        out[s] = (float)d * __int_as_float((127 - 8 * s) << 23);  // d 2^(-8s), exact
-        Y = (Y - d) >> 8;  // exact: Y - d is a multiple of 256
+    for (int t = 0; t < 6; ++t) {  // byte t of Y -> digit s = 6 - t
+        const int sd = 6 - t;
+        const unsigned byte = t < 4 ? (lo >> (8 * t)) & 255u : (hi >> (8 * (t - 4))) & 255u;
+        const unsigned v = byte + c + 128u;
+        c = v >> 8;
+        const int base = 0x4B000000 - ((8 * sd) << 23);
+        out[sd] = __int_as_float(base + (int)(v & 255u)) - __int_as_float(base + 128);
     }
-    out[0] = (float)Y;
+    const int top = ((int)hi >> 16) + (int)c;  // d_0 = floor(Y / 2^48) + carry, in [-128, 128]
+    out[0] = __int_as_float(0x4B000000 + top + 128) - __int_as_float(0x4B000000 + 128);
 }
 
 // FP8 E4M3 code of x 2^(8-e) (|x| < 2^e, so the value is below 256 <= 448),

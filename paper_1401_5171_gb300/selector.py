@@ -5,7 +5,7 @@ BF16X3 normal-equation matrix (oqr_features), runs the MLP 16 -> 64 -> 64 -> 4
 (oqr_mlp_forward, BF16 inference) and picks one option, cheapest first:
 
   0  one FP64-accurate pass          (A-CholQR, tensor cores)
-  1  BF16X3 pass + FP64-accurate pass (mixed A-CholQR2)
+  1  TC2 pass + FP64-accurate pass    (mixed A-CholQR2, one split of A for both)
   2  shifted A-CholQR3, all three passes FP64-accurate on the tensor cores
   3  FP64 A-CholQR2 (DFMA)           -- also the fallback
 
@@ -30,7 +30,7 @@ import numpy as np
 
 OPTIONS = [
     ("oqr_cholqr", {"final_prec": 3}),
-    ("oqr_cholqr2", {"prec": 1, "final_prec": 3}),
+    ("oqr_cholqr2", {"prec": 4, "final_prec": 3}),
     ("oqr_cholqr2", {"shifted": 1, "prec": 3, "prec_mid": 3, "final_prec": 3}),
     ("oqr_cholqr2", {}),
     ("oqr_cholqr2", {"shifted": 1}),   # last resort, not a class of the network
