@@ -56,9 +56,9 @@ typedef enum {
     OQR_FP8 = 2,      /* E4M3 with a power-of-two scale per (row or column, 128-long chunk of the
                          contraction), one product, drained and scaled every chunk (tensor cores) */
     OQR_FP64_TC = 3,  /* FP64-accurate products from 7 exact BF16 slices per operand, exact FP32
-                         accumulation per 128-long chunk, double-float sum (tensor cores) */
+                         accumulation per 256-long chunk, double-float sum (tensor cores) */
     OQR_TC2 = 4       /* the 2 leading slices of the OQR_FP64_TC split (16 bits of each element
-                         relative to its 128-chunk's largest magnitude), 3 products per chunk in FP32,
+                         relative to its 256-chunk's largest magnitude), 3 products per chunk in FP32,
                          scaled every chunk (tensor cores).  Within one factorization, passes in
                          OQR_TC2 and OQR_FP64_TC (and an opts->check = 2) split A once and share it. */
 } oqr_precision;

@@ -12,16 +12,18 @@
 //
 //  * EMU64 (FP64-accurate final pass; error-free slicing in the manner of
 //    Ozaki, Ogita, Oishi and Rump 2012): for every row of the left operand and
-//    every 128-long chunk of the contraction index k, a power-of-two exponent e
+//    every 256-long chunk of the contraction index k, a power-of-two exponent e
 //    is taken from the chunk's largest magnitude, and x 2^(7-e) is written as
 //    sum_s d_s 2^(-8s), s = 0..6, with integers d_s in [-128, 128], rounded to
 //    nearest at 2^-48; slice s is stored as d_s 2^(-8s) (exact in BF16).  The
 //    right operand is sliced the same way per column.  The slice products
-//    (s, t) of one level L = s + t + 2 are integers below 2^14 in the units of
-//    that level; the at most 5 products of a level L <= 6 summed over one
-//    128-long chunk stay below 2^24 and are exact in their FP32 accumulator.
-//    Levels 7 and 8 share one accumulator (their rounding is below 2^-54 of
-//    the chunk's largest term).  After every chunk the drain warps scale the
+//    (s, t) of one level L = s + t + 2 are integers of magnitude at most 2^14
+//    in the units of that level; the at most 4 products of a level L <= 5
+//    summed over one 256-long chunk stay within 2^24 and are exact in their
+//    FP32 accumulator; L6 (5 products) is exact unless its sum passes 2^24,
+//    and then rounds by at most 2^0.32 units, below 2^-53 of the chunk's
+//    largest possible value.  Levels 7 and 8 share one accumulator (their
+//    rounding is below 2^-58 of it).  After every chunk the drain warps scale the
 //    accumulators by the chunk's row and column powers of two and add them
 //    into a double-float (hi, lo) register sum; with 7 slices the truncation
 //    error is about 2^-55 relative to the chunk's largest term.
@@ -53,7 +55,11 @@ namespace oqr {
 namespace {
 
 constexpr int TM = 128;            // UMMA M (rows of the left operand per tile)
-constexpr int KCH = 128;           // exact chunk (EMU64) and exponent chunk
+constexpr int KCH_EMU = 256;       // exponent chunk of the EMU64 family (FP64_TC, TC2): exact level sums
+constexpr int KCH_FP8 = 128;       // exponent chunk of FP8 (128-long scale blocks)
+// exponent chunk (and split tile width) of a mode: 256 for the EMU64 family (1, 3), 128 for FP8 (2) and for
+// the BF16X3 split (0, which records no exponents)
+__host__ __device__ constexpr int kch_of(int mode) { return (mode == 1 || mode == 3) ? KCH_EMU : KCH_FP8; }
 constexpr int EXP_NONE = -100000;  // exponent of an all-zero chunk
 constexpr int TC_THREADS = 320;   // producer warp, MMA warp, 8 drain warps
 
@@ -79,20 +85,6 @@ __device__ inline Bits bits_of(double x)
     r.Eb = b ? b : 1;
     r.neg = (u >> 63) != 0;
     return r;
-}
-
-// |x| as an integer key that orders like the magnitude (finite x).
-__device__ inline unsigned long long mag_key(double x)
-{
-    return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
-}
-
-// Chunk exponent e from the largest magnitude key: amax = f 2^e, f in [0.5, 1).
-__device__ inline int chunk_exponent_key(unsigned long long key)
-{
-    if (key == 0) return EXP_NONE;
-    const int b = (int)(key >> 52);
-    return b ? b - 1022 : -1021;
 }
 
 // Round-to-nearest-even right shift of a non-negative integer.
@@ -204,15 +196,6 @@ __device__ inline void bf16x2_split(double x, __nv_bfloat16& hi, __nv_bfloat16& 
     lo = __float2bfloat16_rn(lf);
 }
 
-__device__ inline unsigned long long warp_max_u64(unsigned long long v)
-{
-    for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
-        v = w > v ? w : v;
-    }
-    return v;
-}
-
 // Slices of one element for chunk exponent e (MODE 1: S exact BF16 slices,
 // pre-scaled; MODE 0: BF16 hi/lo).
 template <int MODE>
@@ -234,32 +217,61 @@ __device__ inline void slice_element(double x, int e, int S, float* sl)
     }
 }
 
-// Writes four consecutive plane elements (k .. k+3) of every slice: one 8-byte
-// (BF16) or 4-byte (E4M3) store per plane.
-template <int MODE>
-__device__ inline void store4(__nv_bfloat16* planes, size_t plane, size_t off, int S, const double* v, int e)
+// Chunk exponent of the magnitudes held by a warp (VPL values per lane): the
+// exponent field's maximum over the high words (32-bit warp reductions), and
+// EXP_NONE when every value is zero.
+template <int VPL>
+__device__ inline int warp_chunk_exponent(const double* v)
+{
+    unsigned hk = 0, nz = 0;
+#pragma unroll
+    for (int j = 0; j < VPL; ++j) {
+        const unsigned long long u = (unsigned long long)__double_as_longlong(v[j]);
+        const unsigned h = (unsigned)(u >> 32) & 0x7FFFFFFFu;
+        hk = h > hk ? h : hk;
+        nz |= h | (unsigned)u;
+    }
+    hk = __reduce_max_sync(0xffffffffu, hk);
+    nz = __reduce_or_sync(0xffffffffu, nz);
+    if (nz == 0) return EXP_NONE;
+    const int b = (int)(hk >> 20);
+    return b ? b - 1022 : -1021;
+}
+
+// Writes VPL consecutive plane elements (k .. k+VPL-1) of every slice: one
+// vector store per plane (2 B per element for BF16 planes, 1 B for E4M3).
+template <int MODE, int VPL>
+__device__ inline void store_run(__nv_bfloat16* planes, size_t plane, size_t off, int S, const double* v, int e)
 {
     if constexpr (MODE == 2) {
-        uchar4 q;
-        q.x = e == EXP_NONE ? 0 : e4m3_code(v[0], e);
-        q.y = e == EXP_NONE ? 0 : e4m3_code(v[1], e);
-        q.z = e == EXP_NONE ? 0 : e4m3_code(v[2], e);
-        q.w = e == EXP_NONE ? 0 : e4m3_code(v[3], e);
-        *reinterpret_cast<uchar4*>(reinterpret_cast<unsigned char*>(planes) + off) = q;
-    } else {
-        float sl[4][7];
+        unsigned w[VPL / 4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) slice_element<MODE>(v[j], e, S, sl[j]);
+        for (int q = 0; q < VPL / 4; ++q) {
+            unsigned word = 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                word |= (unsigned)(e == EXP_NONE ? 0 : e4m3_code(v[4 * q + j], e)) << (8 * j);
+            w[q] = word;
+        }
+        unsigned char* dst = reinterpret_cast<unsigned char*>(planes) + off;
+        if constexpr (VPL == 4) *reinterpret_cast<unsigned*>(dst) = w[0];
+        else *reinterpret_cast<uint2*>(dst) = make_uint2(w[0], w[1]);
+    } else {
+        // runs of four elements: 28 live slice values, one 8-byte store per plane and run
         const int np = MODE == 0 ? 2 : S;
 #pragma unroll
-        for (int t = 0; t < 7; ++t) {
-            if (t < np) {
-                __nv_bfloat162 lo2 = __floats2bfloat162_rn(sl[0][t], sl[1][t]);  // exact: at most 8 significant bits
-                __nv_bfloat162 hi2 = __floats2bfloat162_rn(sl[2][t], sl[3][t]);
-                uint2 w;
-                w.x = *reinterpret_cast<unsigned int*>(&lo2);
-                w.y = *reinterpret_cast<unsigned int*>(&hi2);
-                *reinterpret_cast<uint2*>(planes + t * plane + off) = w;
+        for (int h = 0; h < VPL / 4; ++h) {
+            float sl[4][7];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) slice_element<MODE>(v[4 * h + j], e, S, sl[j]);
+#pragma unroll
+            for (int t = 0; t < 7; ++t) {
+                if (t < np) {
+                    __nv_bfloat162 lo2 = __floats2bfloat162_rn(sl[0][t], sl[1][t]);  // exact: <= 8 significant bits
+                    __nv_bfloat162 hi2 = __floats2bfloat162_rn(sl[2][t], sl[3][t]);
+                    *reinterpret_cast<uint2*>(planes + t * plane + off + 4 * h) =
+                        make_uint2(*reinterpret_cast<unsigned int*>(&lo2), *reinterpret_cast<unsigned int*>(&hi2));
+                }
             }
         }
     }
@@ -268,30 +280,34 @@ __device__ inline void store4(__nv_bfloat16* planes, size_t plane, size_t off, i
 // TRI: A (m x m, column-major, lower triangle) -> slices of
 // M = tril(A,-1) + diag(A)/2; otherwise a general column-major m x K matrix.
 // Written row-major (row i, k contiguous): planes + s*plane + i*ldp + k, ldp a
-// multiple of 128 (the row is written up to its 128-chunk's end).
-// One CTA: 32 rows x one 128-column chunk; 8 warps.  The tile is transposed
-// through shared memory stored as T[row][(k % 4) * 33 + k / 4], so that lane l
-// reads k = 4l .. 4l+3 of a row without bank conflicts and writes them with
-// one vector store per plane.
+// multiple of CW (the row is written up to its chunk's end).
+// One CTA: 4096 / CW rows x one CW-column chunk (CW = 128 or 256); 8 warps.
+// The tile is transposed through shared memory stored as
+// T[row][(k % VPL) * 33 + k / VPL], VPL = CW / 32, so that lane l reads
+// k = VPL l .. VPL l + VPL-1 of a row without bank conflicts and writes them
+// with one vector store per plane.
 // MODE 0: BF16 hi/lo planes; 1: S exact BF16 slices (S <= 7); 2: one FP8 E4M3
 // plane (bytes).  Modes 1 and 2 record the chunk exponent of every row.
-constexpr int TPAD = 4 * 33 + 1;
-template <int MODE, bool TRI = true>
+template <int MODE, bool TRI, int CW>
 __global__ void __launch_bounds__(256) split_lower_kernel(int m, int K, const double* __restrict__ A, long lda, int S,
                                                           __nv_bfloat16* planes, long ldp, size_t plane,
                                                           int* eA, int* emax)
 {
     constexpr bool SCALED = MODE != 0;  // exponents are recorded
-    __shared__ double T[32][TPAD];
+    constexpr int VPL = CW / 32;        // values per lane
+    constexpr int ROWS = 4096 / CW;     // rows per tile
+    constexpr int CG = 256 / ROWS;      // column groups in the load phase
+    __shared__ double T[ROWS][VPL * 33 + 1];
     const int kc = blockIdx.x, ib = blockIdx.y;
-    const long row0 = (long)ib * 32, col0 = (long)kc * KCH;
-    if (row0 >= m || (TRI && col0 > row0 + 31)) return;
+    const long row0 = (long)ib * ROWS, col0 = (long)kc * CW;
+    if (row0 >= m || (TRI && col0 > row0 + ROWS - 1)) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    double ld[KCH / 8];  // all of this thread's loads in flight before the first store
+    const int lr = threadIdx.x % ROWS, lg = threadIdx.x / ROWS;  // load phase: row, column group
+    double ld[16];  // all of this thread's loads in flight before the first store
 #pragma unroll
-    for (int t = 0; t < KCH / 8; ++t) {
-        const int k = w + 8 * t;
-        const long i = row0 + lane, kk = col0 + k;
+    for (int t = 0; t < 16; ++t) {
+        const int k = lg + CG * t;
+        const long i = row0 + lr, kk = col0 + k;
         double v = 0.0;
         if (i < m && kk < K && (!TRI || kk <= i)) {
             v = A[i + kk * lda];
@@ -300,63 +316,54 @@ __global__ void __launch_bounds__(256) split_lower_kernel(int m, int K, const do
         ld[t] = v;
     }
 #pragma unroll
-    for (int t = 0; t < KCH / 8; ++t) {
-        const int k = w + 8 * t;
-        T[lane][(k & 3) * 33 + (k >> 2)] = ld[t];
+    for (int t = 0; t < 16; ++t) {
+        const int k = lg + CG * t;
+        T[lr][(k % VPL) * 33 + k / VPL] = ld[t];
     }
     __syncthreads();
-    for (int r = w * 4; r < w * 4 + 4; ++r) {
+    constexpr int RPW = ROWS / 8;  // rows per warp
+    for (int r = w * RPW; r < w * RPW + RPW; ++r) {
         const long i = row0 + r;
         if (i >= m) break;
-        double v[4];
-        unsigned long long key = 0;
+        double v[VPL];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            v[j] = T[r][j * 33 + lane];  // k = 4 lane + j
-            const unsigned long long kj = mag_key(v[j]);
-            key = kj > key ? kj : key;
-        }
-        key = warp_max_u64(key);
-        const int e = SCALED ? chunk_exponent_key(key) : 0;
+        for (int j = 0; j < VPL; ++j) v[j] = T[r][j * 33 + lane];  // k = VPL lane + j
+        const int e = SCALED ? warp_chunk_exponent<VPL>(v) : 0;
         if (SCALED && lane == 0) {
             eA[(size_t)kc * m + i] = e;
             if (e != EXP_NONE) atomicMax(&emax[i], e);
         }
-        const size_t off = (size_t)i * ldp + col0 + 4 * lane;
-        store4<MODE>(planes, plane, off, S, v, e);
+        store_run<MODE, VPL>(planes, plane, (size_t)i * ldp + col0 + VPL * lane, S, v, e);
     }
 }
 
 // X (K x C, column-major) -> slices written column-major (column c, k
-// contiguous, ldp a multiple of 128): planes + s*plane + c*ldp + k.  One warp
-// per (chunk, column); lane l handles k = 4l .. 4l+3.
-template <int MODE>
+// contiguous, ldp a multiple of CW): planes + s*plane + c*ldp + k.  One warp
+// per (CW-chunk, column); lane l handles k = VPL l .. VPL l + VPL-1.
+template <int MODE, int CW>
 __global__ void __launch_bounds__(256) split_tall_kernel(int K, int C, const double* __restrict__ X, long ldx, int S,
                                                          __nv_bfloat16* planes, long ldp, size_t plane, int* eX,
                                                          int* xmax)
 {
     constexpr bool SCALED = MODE != 0;  // exponents are recorded
+    constexpr int VPL = CW / 32;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int kc = blockIdx.x;
     const long c = (long)blockIdx.y * 8 + w;
     if (c >= C) return;
-    const long k0 = (long)kc * KCH + 4 * lane;
-    double v[4];
-    unsigned long long key = 0;
+    const long k0 = (long)kc * CW + VPL * lane;
+    double v[VPL];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < VPL; ++j) {
         const long k = k0 + j;
         v[j] = k < K ? X[k + c * ldx] : 0.0;
-        const unsigned long long kj = mag_key(v[j]);
-        key = kj > key ? kj : key;
     }
-    key = warp_max_u64(key);
-    const int e = SCALED ? chunk_exponent_key(key) : 0;
+    const int e = SCALED ? warp_chunk_exponent<VPL>(v) : 0;
     if (SCALED && lane == 0) {
         eX[(size_t)kc * C + c] = e;
         if (e != EXP_NONE) atomicMax(&xmax[c], e);
     }
-    store4<MODE>(planes, plane, (size_t)c * ldp + k0, S, v, e);
+    store_run<MODE, VPL>(planes, plane, (size_t)c * ldp + k0, S, v, e);
 }
 
 __global__ void fill_int_kernel(int* p, long n, int v)
@@ -525,8 +532,9 @@ struct TcCfg {
     static constexpr int STAGES = 196608 / STAGE < 2 ? 2 : 196608 / STAGE > 6 ? 6 : 196608 / STAGE;
     static constexpr int TMEM_COLS = 2 * N <= 128 ? 128 : 2 * N <= 256 ? 256 : 512;  // two accumulator buffers
     static constexpr int KPI = MODE == 2 ? 32 : 16;    // K per MMA instruction (32 bytes of K)
+    static constexpr int KCH = kch_of(MODE);           // exponent chunk of this mode
     static constexpr int CH_STEPS = MODE == 0 ? 1 << 30 : KCH / KS;  // k-steps per drained chunk
-    static constexpr int MAXCH = 16;                   // chunks per item (items are 2048 long)
+    static constexpr int MAXCH = 2048 / KCH;           // chunks per item (items are 2048 long)
     // align slack + barriers and drain flags + (chunked modes) an item's row and column chunk scales
     static constexpr size_t SMEM =
         1024 + STAGES * (size_t)STAGE + 2048 + (MODE != 0 ? (size_t)MAXCH * (TM + N) * sizeof(float) : 0);
@@ -703,7 +711,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 // products of slices of x 2^(7-e_r) and y 2^(7-e_c), scaled back by 2^(e_r + e_c - 14);
                 // both relative to the row and column maxima.  All of the item's scales are loaded
                 // once, so no global load sits between a chunk's accumulators and their drain.
-                const int kc0 = (item.ks0 * KS) / KCH;
+                const int kc0 = (item.ks0 * KS) / C::KCH;
                 for (int e = dt; e < nch * TM; e += 256) {
                     const int ch = e / TM, rr = e % TM;
                     const long g = (long)item.I * TM + rr;
@@ -838,11 +846,12 @@ __global__ void symmetrize_kernel(int n, const double* __restrict__ Cm, long ldc
 
 // ------------------------------------------- FP64-accurate (EMU64) kernel ----
 // Levels L = s + t + 2 of the slice products (s, t) with s + t <= 6.  Each of
-// L2..L6 owns a TMEM accumulator and is exact over one 128-long chunk (at
-// most 5 products of magnitude below 2^14 in the units of its level, summed
-// over 128 terms: below 2^24).  L7 and L8 (13 products) share one accumulator;
-// their sum is below 2^-37 of the chunk's largest possible value, so FP32
-// rounding there costs below 2^-54 of it, under the slicing error itself.
+// L2..L6 owns a TMEM accumulator.  Over one 256-long chunk L2..L5 are exact
+// (at most 4 products of magnitude at most 2^14 in the units of their level,
+// 256 terms: within 2^24); L6 (5 products) can pass 2^24 by at most 2^0.32,
+// so its FP32 rounding stays below 2^-53 of the chunk's largest possible
+// value.  L7 and L8 (13 products) share one accumulator; their sum is below
+// 2^-37 of that value, so FP32 rounding there costs below 2^-58 of it.
 //
 // TMEM: 8 slots of 64 columns.  L2..L5 use slots 0..3 in every chunk; L6 and
 // L7+8 alternate between slots 4, 5 (even chunks) and 6, 7 (odd chunks).  The
@@ -860,11 +869,11 @@ constexpr int EMU_A_TILE = TM * EMU_KS * 2;         // 8 KB
 constexpr int EMU_B_TILE = EMU_N * EMU_KS * 2;      // 4 KB
 constexpr int EMU_STAGE = EMU_S * (EMU_A_TILE + EMU_B_TILE);
 constexpr int EMU_STAGES = 2;
-constexpr int EMU_CH = KCH / EMU_KS;                // k-steps per chunk
+constexpr int EMU_CH = KCH_EMU / EMU_KS;            // k-steps per chunk
 constexpr int EMU_DRAIN = 512;                      // drain threads
 constexpr int EMU_THREADS = 64 + EMU_DRAIN;
 constexpr int EMU_CPT = EMU_N / 4;                  // columns per drain thread
-constexpr int EMU_MAXCH = 16;                       // chunks per item (items are 2048 long)
+constexpr int EMU_MAXCH = 2048 / KCH_EMU;           // chunks per item (items are 2048 long)
 // align slack + stages + barriers and flags + an item's row and column chunk scales
 constexpr size_t EMU_SMEM = 1024 + (size_t)EMU_STAGES * EMU_STAGE + 1024 + (size_t)EMU_MAXCH * (TM + EMU_N) * 4;
 static_assert(EMU_STAGE % 1024 == 0, "stage alignment");
@@ -1095,7 +1104,7 @@ __global__ void __launch_bounds__(EMU_THREADS, 1)
                 // 2^(e_r + e_c - 14) times the sum of the slice products) and column scale
                 // 2^(e_col - emax_col), 0 for an all-zero chunk; no global load then sits between a
                 // chunk's accumulators and their drain
-                const int kc0 = (item.ks0 * EMU_KS) / KCH;
+                const int kc0 = (item.ks0 * EMU_KS) / KCH_EMU;
                 for (int e = dt; e < nch * TM; e += EMU_DRAIN) {
                     const int ch = e / TM, rr = e % TM;
                     const long gr = (long)item.I * TM + rr;
@@ -1243,7 +1252,7 @@ static TcArgs make_args(const TcPlan& p, int rowsA, int colsB, int K, int tri, i
     a.K = K;
     a.tri = tri;
     a.ks = p.mode == 1 ? EMU_KS : p.mode == 2 ? 128 : 64;
-    a.piece = 2048 / a.ks;  // k-steps per item (a multiple of the 128-long chunk)
+    a.piece = 2048 / a.ks;  // k-steps per item (a multiple of the exponent chunk)
     a.cc = (colsB + N - 1) / N;
     a.rt = (rowsA + TM - 1) / TM;
     int s = 0;
@@ -1263,8 +1272,8 @@ TcPlan tc_plan(int m, int n, int mode, int sa)
     p.es = mode == 2 ? 1 : 2;
     // FP8 and TC2 keep N <= 128: their drain holds N/2 FP32 sums per thread
     p.N = mode == 1 ? EMU_N : (n <= 64 ? 64 : (n <= 128 || mode >= 2) ? 128 : 256);
-    p.ldp = ((long)m + 127) / 128 * 128;
-    p.kch = (m + KCH - 1) / KCH;
+    p.ldp = ((long)m + 255) / 256 * 256;  // the splits write to the end of their chunk
+    p.kch = (m + kch_of(mode) - 1) / kch_of(mode);
     const TcArgs u = make_args(p, m, n, m, 1, p.N);
     const TcArgs c = make_args(p, n, n, m, 0, p.N);
     p.nitems_max = u.nitems > c.nitems ? u.nitems : c.nitems;
@@ -1314,34 +1323,31 @@ TcLayout tc_layout(const TcPlan& p, void* ws)
 size_t tc_workspace_bytes(const TcPlan& p) { return tc_layout(p, nullptr).bytes; }
 
 namespace {
-template <int MODE>
-void launch_splits_lower(dim3 g, cudaStream_t s, int mm, const double* A, long lda, int S, __nv_bfloat16* P, long ldp,
-                         size_t plane, int* e, int* mx)
-{
-    split_lower_kernel<MODE><<<g, 256, 0, s>>>(mm, mm, A, lda, S, P, ldp, plane, e, mx);
-}
-template <int MODE>
-void launch_splits_tall(dim3 g, cudaStream_t s, int K, int C, const double* X, long ldx, int S, __nv_bfloat16* P,
-                        long ldp, size_t plane, int* e, int* mx)
-{
-    split_tall_kernel<MODE><<<g, 256, 0, s>>>(K, C, X, ldx, S, P, ldp, plane, e, mx);
-}
-// The split kernel of a plan's mode: TC2 (mode 3) takes the leading slices of the EMU64 split.
-void split_lower_mode(const TcPlan& p, dim3 g, cudaStream_t s, const double* A, long lda, __nv_bfloat16* P, int* e,
-                      int* mx)
+// The split kernels of a plan's mode: TC2 (mode 3) takes the leading slices of the EMU64 split;
+// the EMU64 family uses 256-long exponent chunks (16-row tiles), FP8 and BF16X3 128-long ones.
+void split_lower_mode(const TcPlan& p, cudaStream_t s, const double* A, long lda, __nv_bfloat16* P, int* e, int* mx)
 {
     const size_t plane = (size_t)p.m * p.ldp;
-    if (p.mode == 1 || p.mode == 3) launch_splits_lower<1>(g, s, p.m, A, lda, p.SA, P, p.ldp, plane, e, mx);
-    else if (p.mode == 2) launch_splits_lower<2>(g, s, p.m, A, lda, p.SA, P, p.ldp, plane, e, mx);
-    else launch_splits_lower<0>(g, s, p.m, A, lda, p.SA, P, p.ldp, plane, e, mx);
+    if (p.mode == 1 || p.mode == 3)
+        split_lower_kernel<1, true, KCH_EMU><<<dim3(p.kch, (p.m + 15) / 16), 256, 0, s>>>(p.m, p.m, A, lda, p.SA, P,
+                                                                                        p.ldp, plane, e, mx);
+    else if (p.mode == 2)
+        split_lower_kernel<2, true, KCH_FP8><<<dim3(p.kch, (p.m + 31) / 32), 256, 0, s>>>(p.m, p.m, A, lda, p.SA, P,
+                                                                                        p.ldp, plane, e, mx);
+    else
+        split_lower_kernel<0, true, KCH_FP8><<<dim3(p.kch, (p.m + 31) / 32), 256, 0, s>>>(p.m, p.m, A, lda, p.SA, P,
+                                                                                        p.ldp, plane, e, mx);
 }
-void split_tall_mode(const TcPlan& p, dim3 g, cudaStream_t s, const double* X, long ldx, __nv_bfloat16* P, int* e,
-                     int* mx)
+void split_tall_mode(const TcPlan& p, cudaStream_t s, const double* X, long ldx, __nv_bfloat16* P, int* e, int* mx)
 {
     const size_t plane = (size_t)p.n * p.ldp;
-    if (p.mode == 1 || p.mode == 3) launch_splits_tall<1>(g, s, p.m, p.n, X, ldx, p.S, P, p.ldp, plane, e, mx);
-    else if (p.mode == 2) launch_splits_tall<2>(g, s, p.m, p.n, X, ldx, p.S, P, p.ldp, plane, e, mx);
-    else launch_splits_tall<0>(g, s, p.m, p.n, X, ldx, p.S, P, p.ldp, plane, e, mx);
+    const dim3 g(p.kch, (p.n + 7) / 8);
+    if (p.mode == 1 || p.mode == 3)
+        split_tall_kernel<1, KCH_EMU><<<g, 256, 0, s>>>(p.m, p.n, X, ldx, p.S, P, p.ldp, plane, e, mx);
+    else if (p.mode == 2)
+        split_tall_kernel<2, KCH_FP8><<<g, 256, 0, s>>>(p.m, p.n, X, ldx, p.S, P, p.ldp, plane, e, mx);
+    else
+        split_tall_kernel<0, KCH_FP8><<<g, 256, 0, s>>>(p.m, p.n, X, ldx, p.S, P, p.ldp, plane, e, mx);
 }
 cudaError_t launch_tc_mode(const TcPlan& p, const TcArgs& a, const void* PA, size_t planeA, const void* PB,
                            size_t planeB, int sms, cudaStream_t s)
@@ -1395,9 +1401,8 @@ cudaError_t launch_tc_gram(const TcPlan& p, const double* A, long lda, const dou
         fill_int_kernel<<<(nn + 255) / 256, 256, 0, s>>>(L.mZ, nn, EXP_NONE);
         fill_int_kernel<<<(nn + 255) / 256, 256, 0, s>>>(L.mU, nn, EXP_NONE);
     }
-    const dim3 g(p.kch, (mm + 31) / 32), gz(p.kch, (nn + 7) / 8);
-    if (!a_ready) split_lower_mode(p, g, s, A, lda, L.Ap, L.eA, L.mA);
-    split_tall_mode(p, gz, s, Z, ldz, L.Zp, L.eZ, L.mZ);
+    if (!a_ready) split_lower_mode(p, s, A, lda, L.Ap, L.eA, L.mA);
+    split_tall_mode(p, s, Z, ldz, L.Zp, L.eZ, L.mZ);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // U = M Z (triangular)
     TcArgs a1 = make_args(p, mm, nn, mm, 1, p.N);
@@ -1415,7 +1420,7 @@ cudaError_t launch_tc_gram(const TcPlan& p, const double* A, long lda, const dou
     mark(2);
     launch_slot_reduce(p, a1, L.U, mm, st, s);
     // C = Z^T U (left operand: Z's columns as rows, K-major), then G = C + C^T
-    split_tall_mode(p, gz, s, L.U, mm, L.Up, L.eU, L.mU);
+    split_tall_mode(p, s, L.U, mm, L.Up, L.eU, L.mU);
     TcArgs a2 = make_args(p, nn, nn, mm, 0, p.N);
     a2.cum = L.cum2;
     a2.slots = L.slots;
@@ -1466,8 +1471,8 @@ TrsmLayout trsm_layout(int m, int n, void* ws)
     };
     TrsmLayout L;
     const int kmax = n > TRSM_BW ? ((n - 1) / TRSM_BW) * TRSM_BW : 1;  // largest off-diagonal K
-    L.ldp = ((long)kmax + 127) / 128 * 128;
-    L.kch = (kmax + KCH - 1) / KCH;
+    L.ldp = ((long)kmax + KCH_EMU - 1) / KCH_EMU * KCH_EMU;
+    L.kch = (kmax + KCH_EMU - 1) / KCH_EMU;
     const int rt = (m + TM - 1) / TM;
     const int pieces = (int)((L.ldp / EMU_KS + 63) / 64);
     L.Xp = reinterpret_cast<__nv_bfloat16*>(take((size_t)EMU_S * m * L.ldp * 2));
@@ -1499,14 +1504,14 @@ cudaError_t launch_trsm_tc(int m, int n, const double* Z, long ldz, const double
         const double* U = nullptr;
         if (jb > 0) {
             const int K = jb;
-            const int kch = (K + KCH - 1) / KCH;
+            const int kch = (K + KCH_EMU - 1) / KCH_EMU;
             fill_int_kernel<<<(m + 255) / 256, 256, 0, s>>>(L.mX, m, EXP_NONE);
             fill_int_kernel<<<1, TRSM_BW, 0, s>>>(L.mY, bw, EXP_NONE);
             const size_t planeX = (size_t)m * L.ldp, planeY = (size_t)TRSM_BW * L.ldp;
-            split_lower_kernel<1, false><<<dim3(kch, (m + 31) / 32), 256, 0, s>>>(m, K, Q, ldq, EMU_S, L.Xp, L.ldp,
-                                                                                  planeX, L.eX, L.mX);
-            split_tall_kernel<1><<<dim3(kch, (bw + 7) / 8), 256, 0, s>>>(K, bw, R + (long)jb * ldr, ldr, EMU_S, L.Yp,
-                                                                         L.ldp, planeY, L.eY, L.mY);
+            split_lower_kernel<1, false, KCH_EMU><<<dim3(kch, (m + 15) / 16), 256, 0, s>>>(
+                m, K, Q, ldq, EMU_S, L.Xp, L.ldp, planeX, L.eX, L.mX);
+            split_tall_kernel<1, KCH_EMU><<<dim3(kch, (bw + 7) / 8), 256, 0, s>>>(K, bw, R + (long)jb * ldr, ldr, EMU_S,
+                                                                                  L.Yp, L.ldp, planeY, L.eY, L.mY);
             TcArgs a = make_args(p, m, bw, K, 0, EMU_N);
             a.cum = L.cum;
             a.slots = L.slots;

@@ -188,7 +188,7 @@ struct TcPlan {
     int SA;         // slices of A made and kept in the workspace (>= S; 7 when shared with mode 1)
     int N;          // UMMA N (column chunk)
     long ldp;       // leading dimension of the slice planes
-    int kch;        // 128-long chunks of the contraction
+    int kch;        // exponent chunks of the contraction (256 long; 128 for FP8)
     int nitems_max; // work items of the larger of the two products
 };
 TcPlan tc_plan(int m, int n, int mode, int sa = 0);

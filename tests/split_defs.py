@@ -6,7 +6,7 @@ subnormal steps of 2^-9 below 2^-6) of x 2^(8-e), scaled back.  Both are exact
 in float64; tests/test_split_definitions.py pins them to torch's conversions.
 emu_digits: the balanced base-256 digits of the FP64-accurate slicing, and
 tc2_rows / tc2_cols: the value that the two leading slices keep of every
-element, per 128-long chunk (integer arithmetic, exact).
+element, per 256-long chunk (integer arithmetic, exact).
 """
 import numpy as np
 
@@ -57,9 +57,9 @@ def _tc2_value(x, e):
     return np.ldexp(d[0] + np.ldexp(d[1].astype(np.float64), -8), np.asarray(e) - 7)
 
 
-def tc2_rows(M, chunk=128):
+def tc2_rows(M, chunk=256):
     """Value kept by the two leading slices of every element of M, with one
-    exponent per (row, chunk of columns)."""
+    exponent per (row, 256-long chunk of columns) as in the FP64_TC/TC2 split."""
     M = np.asarray(M, dtype=np.float64)
     out = np.zeros_like(M)
     for k0 in range(0, M.shape[1], chunk):
@@ -69,7 +69,7 @@ def tc2_rows(M, chunk=128):
     return out
 
 
-def tc2_cols(X, chunk=128):
+def tc2_cols(X, chunk=256):
     """tc2_rows with one exponent per (column, chunk of rows)."""
     return tc2_rows(np.asarray(X).T, chunk).T
 

@@ -95,9 +95,9 @@ def test_tc_gram_fp64tc_exact_integers(env):
 def test_tc_gram_fp64tc_near_exact(env, m, n):
     # Held to Z^T A Z formed in extended precision (np.longdouble: 64- or 113-bit
     # significand), not to the FP64 oracle: the slices keep 55 bits of each
-    # element relative to its 128-chunk maximum and the chunk sums are exact, so
+    # element relative to its 256-chunk maximum and the chunk sums are exact, so
     # what remains is the double-float (about 2^-48) accumulation of U = M Z and
-    # C = Z^T U and the final FP64 sum.  Several 128-chunks, a ragged tail, and
+    # C = Z^T U and the final FP64 sum.  Several 256-chunks, a ragged tail, and
     # two column chunks of 64 at n = 80.
     torch, oqr, ctx = env
     A, Z = inputs.paper_case(4, m, n, 1e6, 1e3, seed=m + 7 * n)
@@ -113,7 +113,7 @@ def test_tc_gram_fp64tc_near_exact(env, m, n):
 
 @pytest.mark.parametrize("m,n", [(64, 5), (300, 20), (1000, 130), (2000, 200)])
 def test_tc_gram_tc2_definition(env, m, n):
-    # TC2 keeps the two leading FP64_TC slices: M~ per (row, 128-chunk), Z~ per (column, 128-chunk);
+    # TC2 keeps the two leading FP64_TC slices: M~ per (row, 256-chunk), Z~ per (column, 256-chunk);
     # G_def = Z~^T U~ + (Z~^T U~)^T with U~ the same truncation of U_def = M~ Z~.  The GPU differs by
     # FP32 accumulation, and U~ by one truncation step where U and U_def straddle a boundary.
     torch, oqr, ctx = env
