@@ -161,6 +161,25 @@ oqr_status oqr_cholqr2(oqr_ctx* ctx, int m, int n, const double* A, long lda, co
  * then A-CholQR2 of the block against S_j; A Q is kept so that each block
  * costs one product with A.  Needs an extra m x n of workspace for A Q.
  */
+/*
+ * oqr_cholqr2_host: oqr_cholqr2 with A, Z, Q and R in HOST memory (column-major,
+ * the same meaning, layouts and options).  Only A's lower triangle is copied to
+ * the device, in panels of 256 columns (rows j0..m-1 of each), on an internal
+ * copy stream; when the first pass runs in OQR_TC2 or OQR_FP64_TC, each panel's
+ * slices are made on `stream` as soon as the panel has arrived, under the
+ * copies of the later panels.  Z is copied in one piece; Q and R are copied
+ * back on `stream` at the end.  For the copies to run asynchronously the host
+ * buffers must be pinned (cudaHostAlloc or cudaHostRegister); with pageable
+ * memory the call still gives the same results.  The device copies of A, Z, Q
+ * and R are held by the context and reused; the call must not overlap another
+ * call on the same context.  Returns when the work is enqueued, unless info is
+ * non-NULL (then it synchronizes and reports as oqr_cholqr2 does).  The paper
+ * has no counterpart: it is the host-to-result form of the same factorization.
+ */
+oqr_status oqr_cholqr2_host(oqr_ctx* ctx, int m, int n, const double* A, long lda, const double* Z, long ldz,
+                            double* Q, long ldq, double* R, long ldr, const oqr_opts* opts, oqr_info* info,
+                            void* stream);
+
 oqr_status oqr_cgs2(oqr_ctx* ctx, int m, int n, const double* A, long lda, const double* Z, long ldz,
                     double* Q, long ldq, double* R, long ldr, const oqr_opts* opts, oqr_info* info,
                     void* stream);

@@ -291,14 +291,14 @@ __device__ inline void store_run(__nv_bfloat16* planes, size_t plane, size_t off
 template <int MODE, bool TRI, int CW>
 __global__ void __launch_bounds__(256) split_lower_kernel(int m, int K, const double* __restrict__ A, long lda, int S,
                                                           __nv_bfloat16* planes, long ldp, size_t plane,
-                                                          int* eA, int* emax)
+                                                          int* eA, int* emax, int kc0 = 0)
 {
     constexpr bool SCALED = MODE != 0;  // exponents are recorded
     constexpr int VPL = CW / 32;        // values per lane
     constexpr int ROWS = 4096 / CW;     // rows per tile
     constexpr int CG = 256 / ROWS;      // column groups in the load phase
     __shared__ double T[ROWS][VPL * 33 + 1];
-    const int kc = blockIdx.x, ib = blockIdx.y;
+    const int kc = kc0 + blockIdx.x, ib = blockIdx.y;  // kc0: first chunk of this launch
     const long row0 = (long)ib * ROWS, col0 = (long)kc * CW;
     if (row0 >= m || (TRI && col0 > row0 + ROWS - 1)) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -1321,6 +1321,29 @@ TcLayout tc_layout(const TcPlan& p, void* ws)
 }  // namespace
 
 size_t tc_workspace_bytes(const TcPlan& p) { return tc_layout(p, nullptr).bytes; }
+
+// The EMU64-family split of A made one 256-column chunk at a time (as the
+// chunks' columns arrive): tc_split_a_begin once, then tc_split_a_chunk for
+// chunks kc = 0, 1, ... in any order; the result equals the split made inside
+// launch_tc_gram for the same plan (mode 1 or 3, same SA).
+cudaError_t tc_split_a_begin(const TcPlan& p, void* ws, cudaStream_t s)
+{
+    const TcLayout L = tc_layout(p, ws);
+    fill_int_kernel<<<(p.m + 255) / 256, 256, 0, s>>>(L.mA, p.m, EXP_NONE);
+    return cudaGetLastError();
+}
+cudaError_t tc_split_a_chunk(const TcPlan& p, const double* A, long lda, int kc, void* ws, cudaStream_t s)
+{
+    if (p.mode != 1 && p.mode != 3) return cudaErrorInvalidValue;
+    const TcLayout L = tc_layout(p, ws);
+    const int row0 = kc * KCH_EMU;  // rows above the chunk's first column hold only upper-triangle tiles
+    const int rows = p.m - row0;
+    if (rows <= 0) return cudaSuccess;
+    const size_t plane = (size_t)p.m * p.ldp;
+    split_lower_kernel<1, true, KCH_EMU><<<dim3(1, (p.m + 15) / 16), 256, 0, s>>>(p.m, p.m, A, lda, p.SA, L.Ap, p.ldp,
+                                                                                plane, L.eA, L.mA, kc);
+    return cudaGetLastError();
+}
 
 namespace {
 // The split kernels of a plan's mode: TC2 (mode 3) takes the leading slices of the EMU64 split;

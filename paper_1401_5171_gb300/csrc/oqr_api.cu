@@ -22,6 +22,11 @@ struct oqr_ctx {
     // cached CUDA graph of the batched sequence and the signature it was captured for
     cudaGraphExec_t batch_exec = nullptr;
     long batch_key[10] = {0};
+    // host-buffer path: device staging (A, Z, Q, R), a copy stream and one event per panel of A
+    void* stage = nullptr;
+    size_t stage_bytes = 0;
+    cudaStream_t copy_stream = nullptr;
+    std::vector<cudaEvent_t> events;
 };
 
 namespace {
@@ -29,6 +34,7 @@ namespace {
 constexpr double U64 = 1.1102230246251565e-16;  // 2^-53
 constexpr int SHIFT_PARTS = 1024;
 constexpr int CGS_MAX_SPLITS = 64;
+constexpr int KCH_PANEL = 256;  // host-buffer path: columns per panel of A (the EMU64 exponent chunk)
 
 void fill_defaults(oqr_opts* o)
 {
@@ -243,46 +249,86 @@ size_t tc_bytes_for(int m, int n, int prec_a, int prec_b, int sa = 0)
     return b;
 }
 
+// Workspace plan of one normal-equation call: the FP64 layout (layout_cholqr),
+// then the tensor-core Gram region shared by the passes (A's split first),
+// then the blocked-TRSM region.
+struct NePlan {
+    int passes = 0;
+    bool shifted = false;
+    int prec_first = 0, prec_mid = 0, prec_final = 0;
+    int sa = 0;        // planes of A kept for the EMU64-family passes (7 with any FP64_TC, else 0)
+    size_t tcb = 0;    // tensor-core Gram region
+    size_t trb = 0;    // blocked-TRSM region
+    int prec_of(int p) const { return p == passes - 1 ? prec_final : (p == 0 ? prec_first : prec_mid); }
+};
+
+oqr_status ne_plan(const oqr_opts& o, int forced_passes, int m, int n, NePlan* P)
+{
+    if (!prec_ok(o.prec) || !prec_ok(o.final_prec)) return OQR_ERR_INVALID_ARG;
+    P->passes = forced_passes > 0 ? forced_passes : (o.shifted ? 3 : o.passes);
+    if (P->passes < 1 || P->passes > 8) return OQR_ERR_INVALID_ARG;
+    P->shifted = forced_passes == 0 && o.shifted;
+    P->prec_mid = o.prec_mid >= 0 ? o.prec_mid : o.prec;
+    if (!prec_ok(P->prec_mid)) return OQR_ERR_INVALID_ARG;
+    P->prec_final = o.final_prec;
+    P->prec_first = P->passes == 1 ? o.final_prec : o.prec;
+    // one split of A for the EMU64-family passes and the tensor-core check: 7 planes when any of them is FP64_TC
+    P->sa = (P->prec_first == OQR_FP64_TC || P->prec_mid == OQR_FP64_TC || P->prec_final == OQR_FP64_TC ||
+             o.check == 2)
+                ? 7
+                : 0;
+    P->tcb = tc_bytes_for(m, n, P->prec_first, P->prec_final, P->sa);
+    P->tcb = std::max(P->tcb, tc_bytes_for(m, n, P->prec_mid, P->prec_mid, P->sa));
+    if (o.check == 2) P->tcb = std::max(P->tcb, tc_bytes_for(m, n, OQR_FP64_TC, OQR_FP64_TC, P->sa));
+    // passes whose Gram runs on the tensor cores also solve Q = X / R with tensor-core products
+    const bool any_tc = P->prec_first != OQR_FP64 || P->prec_mid != OQR_FP64 || P->prec_final != OQR_FP64;
+    P->trb = any_tc ? trsm_tc_workspace_bytes(m, n) : 0;
+    return OQR_OK;
+}
+
+struct NeBuffers {
+    double *partials, *G, *work, *R1, *R2, *R3, *scratch;
+    void *tcws, *trws;
+};
+// base == nullptr: offsets only; returns the bytes.
+size_t ne_carve(void* base, const GramPlan& gp, const NePlan& P, NeBuffers* B)
+{
+    Carve c(base);
+    layout_cholqr(c, gp, &B->partials, &B->G, &B->work, &B->R1, &B->R2, &B->R3, &B->scratch);
+    B->tcws = c.take<char>(P.tcb);
+    B->trws = c.take<char>(P.trb);
+    return c.off;
+}
+
+// a_split_ready: the workspace's tensor-core region already holds the split of
+// this A made for the first pass's plan (the host-buffer path makes it while A
+// arrives), so the first EMU64-family pass does not make it again.
 oqr_status normal_equation(oqr_ctx* ctx, int m, int n, const double* A, long lda, const double* Z, long ldz,
                            double* Q, long ldq, double* R, long ldr, const oqr_opts* opts_in, oqr_info* info,
-                           void* stream, int forced_passes)
+                           void* stream, int forced_passes, bool a_split_ready = false)
 {
     oqr_status v = check_common(ctx, m, n, A, lda, Z, ldz, Q, ldq, R, ldr);
     if (v != OQR_OK) return v;
     const oqr_opts o = resolve(opts_in);
-    if (!prec_ok(o.prec) || !prec_ok(o.final_prec)) return OQR_ERR_INVALID_ARG;
-    int passes = forced_passes > 0 ? forced_passes : (o.shifted ? 3 : o.passes);
-    if (passes > 8) return OQR_ERR_INVALID_ARG;
-    const bool shifted = forced_passes == 0 && o.shifted;
+    NePlan P;
+    if ((v = ne_plan(o, forced_passes, m, n, &P)) != OQR_OK) return v;
+    const int passes = P.passes;
+    const bool shifted = P.shifted;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const uint64_t limit = (uint64_t)o.spin_limit;
     const GramPlan gp = gram_plan(m, n, ctx->sm_count);
-    const int prec_mid = o.prec_mid >= 0 ? o.prec_mid : o.prec;
-    if (!prec_ok(prec_mid)) return OQR_ERR_INVALID_ARG;
-    auto prec_of = [&](int p) { return p == passes - 1 ? o.final_prec : (p == 0 ? o.prec : prec_mid); };
-    const int prec_first = prec_of(0);
-    Carve probe(nullptr);
-    double *partials, *G, *work, *R1, *R2, *R3, *scratch;
-    layout_cholqr(probe, gp, &partials, &G, &work, &R1, &R2, &R3, &scratch);
-    // one split of A for the EMU64-family passes and the tensor-core check: 7 planes when any of them is FP64_TC
+    const int prec_first = P.prec_first;
+    auto prec_of = [&](int p) { return P.prec_of(p); };
+    NeBuffers B;
+    if ((v = ensure_ws(ctx, ne_carve(nullptr, gp, P, &B))) != OQR_OK) return v;
+    ne_carve(ctx->ws, gp, P, &B);
+    double *partials = B.partials, *G = B.G, *work = B.work, *R1 = B.R1, *R2 = B.R2, *R3 = B.R3,
+           *scratch = B.scratch;
+    void* tcws = B.tcws;
+    void* trws = B.trws;
     ASplit as;
-    as.sa = (prec_first == OQR_FP64_TC || prec_mid == OQR_FP64_TC || o.final_prec == OQR_FP64_TC || o.check == 2)
-                ? 7
-                : 0;
-    size_t tcb = tc_bytes_for(m, n, prec_first, o.final_prec, as.sa);
-    tcb = std::max(tcb, tc_bytes_for(m, n, prec_mid, prec_mid, as.sa));
-    if (o.check == 2) tcb = std::max(tcb, tc_bytes_for(m, n, OQR_FP64_TC, OQR_FP64_TC, as.sa));
-    char* tcws_probe = probe.take<char>(tcb);
-    (void)tcws_probe;
-    // passes whose Gram runs on the tensor cores also solve Q = X / R with tensor-core products
-    const bool any_tc = prec_first != OQR_FP64 || prec_mid != OQR_FP64 || o.final_prec != OQR_FP64;
-    const size_t trb = any_tc ? trsm_tc_workspace_bytes(m, n) : 0;
-    probe.take<char>(trb);
-    if ((v = ensure_ws(ctx, probe.off)) != OQR_OK) return v;
-    Carve c(ctx->ws);
-    layout_cholqr(c, gp, &partials, &G, &work, &R1, &R2, &R3, &scratch);
-    void* tcws = c.take<char>(tcb);
-    void* trws = c.take<char>(trb);
+    as.sa = P.sa;
+    as.emu = a_split_ready && emu_family(prec_first);
     if ((v = reset_status(ctx, s)) != OQR_OK) return v;
 
     const double* shift_ptr = nullptr;
@@ -448,6 +494,9 @@ oqr_status oqr_destroy(oqr_ctx* ctx)
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
     if (ctx->batch_exec) cudaGraphExecDestroy(ctx->batch_exec);
+    if (ctx->stage) cudaFree(ctx->stage);
+    for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
+    if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
     if (ctx->ws && ctx->ws_owned) cudaFree(ctx->ws);
     if (ctx->st) cudaFree(ctx->st);
     delete ctx;
@@ -468,10 +517,18 @@ oqr_status oqr_workspace_size(oqr_ctx* ctx, int algo, int m, int n, const oqr_op
         L.gp = gram_plan(m, L.b, ctx->sm_count);
         L.splits = CGS_MAX_SPLITS;
         layout_cgs2(c, L, m, n);
-    } else if (algo < 0 || algo > OQR_ALGO_CGS2) {
-        return OQR_ERR_INVALID_ARG;
+        *bytes = c.off;
+        return OQR_OK;
     }
-    *bytes = c.off;
+    if (algo < 0 || algo > OQR_ALGO_CGS2) return OQR_ERR_INVALID_ARG;
+    // the normal-equation algorithms: the same plan as the call itself, tensor-core regions included
+    oqr_opts oa = o;
+    if (algo == OQR_ALGO_SCHOLQR3) oa.shifted = 1;
+    NePlan P;
+    oqr_status v = ne_plan(oa, algo == OQR_ALGO_CHOLQR ? 1 : 0, m, n, &P);
+    if (v != OQR_OK) return v;
+    NeBuffers B;
+    *bytes = ne_carve(nullptr, gp, P, &B);
     return OQR_OK;
 }
 
@@ -509,6 +566,86 @@ oqr_status oqr_cholqr2(oqr_ctx* ctx, int m, int n, const double* A, long lda, co
                        double* Q, long ldq, double* R, long ldr, const oqr_opts* opts, oqr_info* info, void* stream)
 {
     return normal_equation(ctx, m, n, A, lda, Z, ldz, Q, ldq, R, ldr, opts, info, stream, 0);
+}
+
+oqr_status oqr_cholqr2_host(oqr_ctx* ctx, int m, int n, const double* A, long lda, const double* Z, long ldz,
+                            double* Q, long ldq, double* R, long ldr, const oqr_opts* opts, oqr_info* info,
+                            void* stream)
+{
+    if (!ctx || m < 1 || n < 1 || n > m || !A || !Z || !Q || !R || lda < m || ldz < m || ldq < m || ldr < n)
+        return OQR_ERR_INVALID_ARG;
+    const oqr_opts o = resolve(opts);
+    NePlan P;
+    oqr_status v = ne_plan(o, 0, m, n, &P);
+    if (v != OQR_OK) return v;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return OQR_ERR_CUDA;
+    // device staging: A (lower triangle only is copied; leading dimension even for 16-byte columns), Z, Q, R
+    const long ldA = (m + 1) & ~1L;
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    const size_t bA = al((size_t)ldA * m * 8), bZ = al((size_t)m * n * 8), bR = al((size_t)n * n * 8);
+    const size_t need = bA + 2 * bZ + bR;
+    if (ctx->stage_bytes < need) {
+        if (ctx->stage) {
+            cudaStreamSynchronize(s);
+            cudaFree(ctx->stage);
+            ctx->stage = nullptr;
+            ctx->stage_bytes = 0;
+        }
+        if (cudaMalloc(&ctx->stage, need) != cudaSuccess) {
+            cudaGetLastError();
+            return OQR_ERR_NO_MEMORY;
+        }
+        ctx->stage_bytes = need;
+    }
+    char* sb = static_cast<char*>(ctx->stage);
+    double* Ad = reinterpret_cast<double*>(sb);
+    double* Zd = reinterpret_cast<double*>(sb + bA);
+    double* Qd = reinterpret_cast<double*>(sb + bA + bZ);
+    double* Rd = reinterpret_cast<double*>(sb + bA + 2 * bZ);
+    // the factorization's workspace, planned exactly as the call below plans it
+    const GramPlan gp = gram_plan(m, n, ctx->sm_count);
+    NeBuffers B;
+    if ((v = ensure_ws(ctx, ne_carve(nullptr, gp, P, &B))) != OQR_OK) return v;
+    ne_carve(ctx->ws, gp, P, &B);
+    const int panels = (m + KCH_PANEL - 1) / KCH_PANEL;
+    if (!ctx->copy_stream && cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return OQR_ERR_CUDA;
+    while ((int)ctx->events.size() < panels + 2) {
+        cudaEvent_t e;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return OQR_ERR_CUDA;
+        ctx->events.push_back(e);
+    }
+    cudaStream_t cs = ctx->copy_stream;
+    cudaEvent_t ev_start = ctx->events[panels], ev_z = ctx->events[panels + 1];
+    // the copies start after the work already queued on `stream` (which may still use the staging)
+    OQR_TRY(cudaEventRecord(ev_start, s));
+    OQR_TRY(cudaStreamWaitEvent(cs, ev_start, 0));
+    OQR_TRY(cudaMemcpy2DAsync(Zd, (size_t)m * 8, Z, (size_t)ldz * 8, (size_t)m * 8, n, cudaMemcpyHostToDevice, cs));
+    OQR_TRY(cudaEventRecord(ev_z, cs));
+    // A's lower triangle in panels of KCH_PANEL columns (rows j0..m-1 of each), each split on `stream`
+    // as soon as it has arrived when the first pass takes the EMU64-family split
+    const bool split_early = emu_family(P.prec_first);
+    const TcPlan tp = tc_plan(m, n, tc_mode_of(P.prec_first), emu_family(P.prec_first) ? P.sa : 0);
+    if (split_early) OQR_TRY(tc_split_a_begin(tp, B.tcws, s));
+    for (int k = 0; k < panels; ++k) {
+        const long j0 = (long)k * KCH_PANEL;
+        const long w = std::min<long>(KCH_PANEL, m - j0);
+        OQR_TRY(cudaMemcpy2DAsync(Ad + j0 + j0 * ldA, (size_t)ldA * 8, A + j0 + j0 * lda, (size_t)lda * 8,
+                                  (size_t)(m - j0) * 8, (size_t)w, cudaMemcpyHostToDevice, cs));
+        OQR_TRY(cudaEventRecord(ctx->events[k], cs));
+        if (split_early) {
+            OQR_TRY(cudaStreamWaitEvent(s, ctx->events[k], 0));
+            OQR_TRY(tc_split_a_chunk(tp, Ad, ldA, k, B.tcws, s));
+        }
+    }
+    if (!split_early) OQR_TRY(cudaStreamWaitEvent(s, ctx->events[panels - 1], 0));
+    OQR_TRY(cudaStreamWaitEvent(s, ev_z, 0));
+    if ((v = normal_equation(ctx, m, n, Ad, ldA, Zd, m, Qd, m, Rd, n, &o, nullptr, stream, 0, split_early)) != OQR_OK)
+        return v;
+    OQR_TRY(cudaMemcpy2DAsync(Q, (size_t)ldq * 8, Qd, (size_t)m * 8, (size_t)m * 8, n, cudaMemcpyDeviceToHost, s));
+    OQR_TRY(cudaMemcpy2DAsync(R, (size_t)ldr * 8, Rd, (size_t)n * 8, (size_t)n * 8, n, cudaMemcpyDeviceToHost, s));
+    return finish(ctx, s, info, P.passes, o.check != 0);
 }
 
 oqr_status oqr_cgs2(oqr_ctx* ctx, int m, int n, const double* A, long lda, const double* Z, long ldz, double* Q,

@@ -194,6 +194,9 @@ struct TcPlan {
 TcPlan tc_plan(int m, int n, int mode, int sa = 0);
 size_t tc_plan_bytes(const TcPlan& p);
 size_t tc_workspace_bytes(const TcPlan& p);
+// The split of A made chunk by chunk (host-buffer path: each 256-column chunk as it arrives).
+cudaError_t tc_split_a_begin(const TcPlan& p, void* ws, cudaStream_t s);
+cudaError_t tc_split_a_chunk(const TcPlan& p, const double* A, long lda, int kc, void* ws, cudaStream_t s);
 cudaError_t launch_tc_gram(const TcPlan& p, const double* A, long lda, const double* Z, long ldz, double* G, long ldg,
                            const double* shift_ptr, void* ws, DevStatus* st, uint64_t limit_ns, int sms,
                            cudaStream_t s, cudaEvent_t* ev = nullptr, bool a_ready = false);

@@ -100,6 +100,7 @@ def load(path: str | None = None):
     lib.oqr_potrf.argtypes = [vp, i, vp, l, d, vp, l, ctypes.POINTER(i), vp]
     lib.oqr_trsm.argtypes = [vp, i, i, vp, l, vp, l, vp, l, vp]
     lib.oqr_trsm_tc.argtypes = [vp, i, i, vp, l, vp, l, vp, l, vp]
+    lib.oqr_cholqr2_host.argtypes = [vp, i, i, vp, l, vp, l, vp, l, vp, l, po, pi, vp]
     lib.oqr_rprod.argtypes = [vp, i, vp, l, vp, l, vp, l, vp]
     lib.oqr_check.argtypes = [vp, i, i, vp, l, vp, l, vp, l, ctypes.POINTER(d), ctypes.POINTER(d), vp]
     for name in declared_functions():
@@ -124,7 +125,7 @@ def _raw(name):
 
 
 for _n in ("oqr_default_opts", "oqr_create", "oqr_destroy", "oqr_workspace_size", "oqr_set_workspace",
-           "oqr_get_status", "oqr_cholqr", "oqr_cholqr2", "oqr_cgs2", "oqr_gram", "oqr_gram_noalloc", "oqr_gram_phases", "oqr_potrf", "oqr_trsm", "oqr_trsm_tc",
+           "oqr_get_status", "oqr_cholqr", "oqr_cholqr2", "oqr_cholqr2_host", "oqr_cgs2", "oqr_gram", "oqr_gram_noalloc", "oqr_gram_phases", "oqr_potrf", "oqr_trsm", "oqr_trsm_tc",
            "oqr_rprod", "oqr_check", "oqr_batched", "oqr_batched_default_splits", "oqr_features",
            "oqr_mlp_param_count", "oqr_mlp_forward", "oqr_mlp_grad", "oqr_mlp_adam"):
     globals()[_n] = _raw(_n)
@@ -154,11 +155,11 @@ def colmajor(x):
     return x.t().contiguous().t()
 
 
-def _m(x):
+def _m(x, host=False):
     if x.dtype.is_floating_point is False or x.element_size() != 8:
         raise TypeError("liboqr matrices are float64")
-    if not x.is_cuda:
-        raise TypeError("liboqr matrices live in device memory")
+    if x.is_cuda == host:
+        raise TypeError("this call takes host matrices" if host else "liboqr matrices live in device memory")
     ld = _leading_dim(x) if x.dim() == 2 else None
     if ld is None:
         raise ValueError("matrix must be 2-D column-major (stride(0) == 1); use colmajor()")
@@ -227,6 +228,24 @@ class Oqr:
 
     def oqr_cholqr2(self, A, Z, **kw):
         return self._qr("oqr_cholqr2", A, Z, **kw)
+
+    def oqr_cholqr2_host(self, A, Z, Q=None, R=None, opts=None, stream=None, sync=True, raise_on_error=True, **kw):
+        """oqr_cholqr2 on host (CPU, preferably pinned) column-major tensors; returns (Q, R, (status, info))."""
+        import torch
+        m, n = Z.shape
+        Q = Q if Q is not None else torch.empty((n, m), dtype=torch.float64, pin_memory=True).t()
+        R = R if R is not None else torch.empty((n, n), dtype=torch.float64, pin_memory=True).t()
+        o = opts if opts is not None else make_opts(**kw)
+        info = oqr_info()
+        a, lda = _m(A, host=True)
+        z, ldz = _m(Z, host=True)
+        q, ldq = _m(Q, host=True)
+        r, ldr = _m(R, host=True)
+        st = self.lib.oqr_cholqr2_host(self.ctx, m, n, a, lda, z, ldz, q, ldq, r, ldr, ctypes.byref(o),
+                                       ctypes.byref(info) if sync else None, self._stream(stream))
+        if st != OQR_OK and raise_on_error:
+            raise OqrError(st, "oqr_cholqr2_host", info.info)
+        return Q, R, (st, info)
 
     def oqr_cgs2(self, A, Z, **kw):
         return self._qr("oqr_cgs2", A, Z, **kw)

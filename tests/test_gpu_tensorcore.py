@@ -268,3 +268,40 @@ def test_precision_study_per_kappa(env):
             assert orth["bf16x3->fp64tc"] <= max(1e-12, 10 * oracle.orth_error(A, Qr))
         if kap <= 1e7:
             assert orth["shifted bf16x3->fp64tc->fp64tc"] <= max(1e-12, 10 * oracle.orth_error(A, Qr))
+
+
+# ------------------------------------------------------- host-buffer path ----
+@pytest.mark.parametrize("prec,final", [(4, 3), (0, 0), (3, 3)])
+def test_cholqr2_host_matches_device(env, prec, final):
+    # host buffers: A's lower triangle copied in 256-column panels (m = 1100: a ragged last panel), the
+    # split of A made panel by panel; Q and R must equal the device-buffer call bit for bit
+    import torch
+    torch_, oqr, ctx = env
+    m, n = 1100, 70
+    A, Z = inputs.paper_case(4, m, n, 1e5, 1e2, seed=33)
+    Qd, Rd, (st, _) = ctx.oqr_cholqr2(dev(torch, oqr, A), dev(torch, oqr, Z), prec=prec, final_prec=final)
+    Ah = torch.from_numpy(np.asfortranarray(A)).t().contiguous().pin_memory().t()
+    Ah[torch.triu_indices(m, m, 1).unbind()] = float("nan")        # the upper triangle is never read
+    Zh = torch.from_numpy(np.asfortranarray(Z)).t().contiguous().pin_memory().t()
+    Qh, Rh, (sth, info) = ctx.oqr_cholqr2_host(Ah, Zh, prec=prec, final_prec=final)
+    assert st == sth == oqr.OQR_OK
+    assert torch.equal(Qh, Qd.cpu()) and torch.equal(Rh, Rd.cpu())
+
+
+def test_cholqr2_host_padded_pageable(env):
+    # leading dimensions larger than m and n, pageable (not pinned) host memory
+    import torch
+    torch_, oqr, ctx = env
+    m, n = 700, 24
+    A, Z = inputs.paper_case(4, m, n, 1e4, 1e2, seed=34)
+    Apad = np.zeros((m + 5, m), order="F"); Apad[:m] = A
+    Zpad = np.zeros((m + 3, n), order="F"); Zpad[:m] = Z
+    Ah = torch.from_numpy(Apad)[:m]
+    Zh = torch.from_numpy(Zpad)[:m]
+    Qh = torch.zeros((n, m + 2), dtype=torch.float64).t()[:m]
+    Rh = torch.zeros((n, n + 1), dtype=torch.float64).t()[:n]
+    Qh2, Rh2, (st, _) = ctx.oqr_cholqr2_host(Ah, Zh, Q=Qh, R=Rh, prec=oqr.OQR_TC2, final_prec=oqr.OQR_FP64_TC)
+    Qr, Rr = oracle.oblique_qr(A, Z)
+    assert st == oqr.OQR_OK
+    assert np.linalg.norm(Rh.numpy() - Rr) / np.linalg.norm(Rr) <= 1e-12
+    assert oracle.orth_error(A, Qh.numpy()) <= max(1e-12, 10 * oracle.orth_error(A, Qr))
