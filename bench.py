@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--no-side-paths", action="store_true", help="time only the headline path")
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--batch-count", type=int, default=512,
+                   help="side measurement: a batch of this many instances of the batched workload (0: none)")
     return p.parse_args()
 
 
@@ -281,6 +283,40 @@ def config_of(args):
             "l2": "inputs larger than L2 (A alone is 8.6 GB), no flush"}
 
 
+def run_batch(ctx, torch, dev, count, stream, steps=2):
+    """QRs/s of oqr_batched over one batch (FP64; tensor cores with every pass FP64-accurate; TC2 first pass),
+    with the number of instances that completed and their largest ||Q^T A Q - I||_2 (checked outside the
+    timing)."""
+    from paper_1401_5171_gb300 import inputs
+    As, Zs, tab = inputs.batch_instances(count, seed=4242, device=dev)
+    sigma_a = sum(int(m) ** 2 for m in tab["m"]) * 8
+    out = {"instances": count, "sum_A_bytes": sigma_a,
+           "recipe": "m ~ U[64, 4096], n ~ U[4, 64], kappa(A), kappa(Z) log-uniform in [1, 1e6], seed 4242"}
+    for label, mode in (("fp64", 0), ("fp64tc", 1), ("tc2_first", 2)):
+        Qs, Rs, st = ctx.oqr_batched(As, Zs, mode=mode, stream=stream)     # captures the graph
+        torch.cuda.synchronize()
+        stc = st.cpu().tolist()
+        worst = 0.0
+        for b in range(count):
+            if stc[b] != 0:
+                continue
+            n = Zs[b].shape[1]
+            E = Qs[b].T @ (As[b] @ Qs[b]) - torch.eye(n, dtype=torch.float64, device=dev)
+            worst = max(worst, torch.linalg.eigvalsh(0.5 * (E + E.T)).abs().max().item())
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            ctx.oqr_batched(As, Zs, Qs=Qs, Rs=Rs, mode=mode, stream=stream, status=st)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        out[label] = {"qr_per_s": count / (ms / 1e3), "ms_per_batch": ms,
+                      "completed": sum(1 for x in stc if x == 0), "max_orth_err_completed": worst}
+    del As, Zs
+    torch.cuda.empty_cache()
+    return out
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -344,6 +380,12 @@ def main():
         for p in ("fp64", "fp64tc", "mixed", "mixed_bf16x3"):
             if p != args.path:
                 others[p] = run(p, 2, 1)
+
+    # side measurement: the batched workload (m ~ U[64, 4096], n ~ U[4, 64], kappa(A), kappa(Z) log-uniform
+    # to 1e6), a sample of args.batch_count instances; every path factors the whole batch per step
+    batch = None
+    if args.batch_count > 0:
+        batch = run_batch(ctx, torch, dev, args.batch_count, stream)
 
     # dominant kernel of the headline path, timed alone with CUDA events on the same stream
     G = oqr.empty_colmajor(n, n, dev)
@@ -433,7 +475,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": head["ms_per_qr"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_of(args),
             "tflops_normalised": head["tflops_normalised"], "orth_err": head["orth_err"],
-            "meets_1e-12": bool(0 <= head["orth_err"] <= 1e-12), "paths": others,
+            "meets_1e-12": bool(0 <= head["orth_err"] <= 1e-12), "paths": others, "batched": batch,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": lps * args.steps if lps is not None else None, "clocks": clocks}
     if rank == 0:

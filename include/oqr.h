@@ -230,7 +230,9 @@ oqr_status oqr_check(oqr_ctx* ctx, int m, int n, const double* A, long lda, cons
  * Cholesky broke down (its Q_b, R_b are then undefined; the other instances
  * are unaffected).  splits (host, may be NULL) is the work plan: the number of
  * k-ranges each instance's Gram is cut into (1..64), as chosen by an autotuner;
- * NULL uses the built-in heuristic.  mode must be 0 (FP64 A-CholQR2).
+ * NULL uses the built-in heuristic.  mode: 0 FP64 A-CholQR2 (FP64 FMA Gram);
+ * 1 and 2 the tensor-core form of oqr_batched_mixed with every first pass
+ * OQR_FP64_TC (mode 1) or OQR_TC2 (mode 2); splits is then ignored.
  * The batch-wide kernel sequence (about 13 launches) is captured into one
  * CUDA graph that the context caches and replays while the batch's shape
  * signature is unchanged; on the legacy default stream it is launched directly.
@@ -239,6 +241,27 @@ oqr_status oqr_check(oqr_ctx* ctx, int m, int n, const double* A, long lda, cons
 oqr_status oqr_batched(oqr_ctx* ctx, int count, const int* m, const int* n, const double* const* A, const long* lda,
                        const double* const* Z, const long* ldz, double* const* Q, const long* ldq, double* const* R,
                        const long* ldr, int mode, const int* splits, int* status, void* stream);
+
+/*
+ * Batched A-CholQR2 on the tensor cores: the same instances, arguments and
+ * status words as oqr_batched, with each instance's Gram G = Z^T A Z
+ * (Algorithm 1, line 1; Sec. 2) formed on the BF16 tensor cores:
+ * first_prec[b] (host array; NULL = all OQR_FP64_TC) is OQR_TC2 or
+ * OQR_FP64_TC for instance b's first pass, and the second pass is OQR_FP64_TC
+ * for every instance.  The Cholesky factors, Q = Z R^{-1} and R = R_2 R_1 are
+ * FP64.  An instance's results do not depend on the other instances of the
+ * batch.  Instances run in waves (largest m first) whose BF16 slice planes
+ * (14 bytes per element of A, Z and Z^T A) fit 16 GiB of workspace; A is
+ * split once per wave and read by both passes.  status[b] = -1 for every
+ * instance when a tensor-core wait timed out (the context's status then
+ * reports OQR_ERR_TIMEOUT).  The sequence is captured into one CUDA graph,
+ * cached while every instance's (m, n, first_prec) is unchanged.
+ * Asynchronous: returns after enqueueing (argument errors are returned).
+ */
+oqr_status oqr_batched_mixed(oqr_ctx* ctx, int count, const int* m, const int* n, const double* const* A,
+                             const long* lda, const double* const* Z, const long* ldz, double* const* Q,
+                             const long* ldq, double* const* R, const long* ldr, const int* first_prec, int* status,
+                             void* stream);
 
 /* The built-in work plan of oqr_batched for one instance (splits of its Gram). */
 int oqr_batched_default_splits(int m, int n);

@@ -254,6 +254,15 @@ __global__ void rprod_batched_kernel(const BatchDesc* __restrict__ d, const int*
     D.R[i + (long)j * D.ldr] = s;
 }
 
+// status[perm[i]] = st_sorted[i]; -1 for all when a kernel of the context timed out.
+__global__ void status_scatter_kernel(const int* st_sorted, const int* perm, int count, const DevStatus* st,
+                                      int* status)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    status[perm[i]] = st->code != 0 ? -1 : st_sorted[i];
+}
+
 }  // namespace
 
 // Gram kernels take the instances of one tile class through an index list.
@@ -276,6 +285,30 @@ cudaError_t launch_batched_cholqr2(const BatchDesc* d, int count, const int* con
     }
     dim3 gp((64 * 64 + 255) / 256, count);
     rprod_batched_kernel<<<gp, 256, 0, s>>>(d, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batched_factor(const BatchDesc* d, int count, int* status, int pass, cudaStream_t s)
+{
+    dim3 gr((BATCH_MAX_N * BATCH_MAX_N + 255) / 256, count);
+    reduce_batched_kernel<<<gr, 256, 0, s>>>(d, status, nullptr);
+    potrf_batched_kernel<<<count, 256, 0, s>>>(d, status, pass);
+    dim3 gt(BATCH_MAX_M / 128, count);
+    trsm_batched_kernel<<<gt, 128, 0, s>>>(d, status, pass, pass);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batched_rprod(const BatchDesc* d, int count, int* status, cudaStream_t s)
+{
+    dim3 gp((BATCH_MAX_N * BATCH_MAX_N + 255) / 256, count);
+    rprod_batched_kernel<<<gp, 256, 0, s>>>(d, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_status_scatter(const int* st_sorted, const int* perm, int count, const DevStatus* st,
+                                        int* status, cudaStream_t s)
+{
+    status_scatter_kernel<<<(count + 255) / 256, 256, 0, s>>>(st_sorted, perm, count, st, status);
     return cudaGetLastError();
 }
 

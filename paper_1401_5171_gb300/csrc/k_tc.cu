@@ -288,17 +288,19 @@ __device__ inline void store_run(__nv_bfloat16* planes, size_t plane, size_t off
 // with one vector store per plane.
 // MODE 0: BF16 hi/lo planes; 1: S exact BF16 slices (S <= 7); 2: one FP8 E4M3
 // plane (bytes).  Modes 1 and 2 record the chunk exponent of every row.
+// One tile of the row split: rows [row0, row0 + ROWS) of A (m x K, column-major)
+// and the CW-chunk kc; the output rows are offset by roff (a packed batch) and
+// the exponents are strided by erows (the packed row count).
 template <int MODE, bool TRI, int CW>
-__global__ void __launch_bounds__(256) split_lower_kernel(int m, int K, const double* __restrict__ A, long lda, int S,
-                                                          __nv_bfloat16* planes, long ldp, size_t plane,
-                                                          int* eA, int* emax, int kc0 = 0)
+__device__ __forceinline__ void split_lower_tile(int m, int K, const double* __restrict__ A, long lda, int S,
+                                                 __nv_bfloat16* planes, long ldp, size_t plane, int* eA, int* emax,
+                                                 int kc, int ib, long roff, long erows)
 {
     constexpr bool SCALED = MODE != 0;  // exponents are recorded
     constexpr int VPL = CW / 32;        // values per lane
     constexpr int ROWS = 4096 / CW;     // rows per tile
     constexpr int CG = 256 / ROWS;      // column groups in the load phase
     __shared__ double T[ROWS][VPL * 33 + 1];
-    const int kc = kc0 + blockIdx.x, ib = blockIdx.y;  // kc0: first chunk of this launch
     const long row0 = (long)ib * ROWS, col0 = (long)kc * CW;
     if (row0 >= m || (TRI && col0 > row0 + ROWS - 1)) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -330,27 +332,74 @@ __global__ void __launch_bounds__(256) split_lower_kernel(int m, int K, const do
         for (int j = 0; j < VPL; ++j) v[j] = T[r][j * 33 + lane];  // k = VPL lane + j
         const int e = SCALED ? warp_chunk_exponent<VPL>(v) : 0;
         if (SCALED && lane == 0) {
-            eA[(size_t)kc * m + i] = e;
-            if (e != EXP_NONE) atomicMax(&emax[i], e);
+            eA[(size_t)kc * erows + roff + i] = e;
+            if (e != EXP_NONE) atomicMax(&emax[roff + i], e);
         }
-        store_run<MODE, VPL>(planes, plane, (size_t)i * ldp + col0 + VPL * lane, S, v, e);
+        store_run<MODE, VPL>(planes, plane, (size_t)(roff + i) * ldp + col0 + VPL * lane, S, v, e);
     }
+}
+
+template <int MODE, bool TRI, int CW>
+__global__ void __launch_bounds__(256) split_lower_kernel(int m, int K, const double* __restrict__ A, long lda, int S,
+                                                          __nv_bfloat16* planes, long ldp, size_t plane,
+                                                          int* eA, int* emax, int kc0 = 0)
+{
+    split_lower_tile<MODE, TRI, CW>(m, K, A, lda, S, planes, ldp, plane, eA, emax, kc0 + blockIdx.x, blockIdx.y, 0,
+                                    m);
+}
+
+// One instance of a batched split: its matrix X (rows x K, column-major, ldx)
+// goes to packed rows (or columns) [off, off + rows or cols); its tiles or
+// columns start at first in the launch's flat enumeration.
+struct SplitInst {
+    const double* X;
+    long ldx;
+    int rows, K, cols;
+    long off;
+    int first;
+    int kch;
+};
+
+__device__ inline int last_le_split(const SplitInst* v, int n, int j)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (v[mid].first <= j) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// The triangular row split of a packed batch of A's: blockIdx.x enumerates every
+// instance's (chunk, 16-row block) tiles; upper-triangle tiles return at once.
+__global__ void __launch_bounds__(256) split_lower_batch_kernel(const SplitInst* __restrict__ inst, int ninst, int S,
+                                                                __nv_bfloat16* planes, long ldp, size_t plane, int* eA,
+                                                                int* emax, long erows)
+{
+    const int j = blockIdx.x;
+    const int b = last_le_split(inst, ninst, j);
+    const SplitInst I = inst[b];
+    const int nrb = (I.rows + 15) / 16;
+    const int t = j - I.first;
+    if (t >= I.kch * nrb) return;
+    split_lower_tile<1, true, KCH_EMU>(I.rows, I.rows, I.X, I.ldx, S, planes, ldp, plane, eA, emax, t / nrb, t % nrb,
+                                       I.off, erows);
 }
 
 // X (K x C, column-major) -> slices written column-major (column c, k
 // contiguous, ldp a multiple of CW): planes + s*plane + c*ldp + k.  One warp
-// per (CW-chunk, column); lane l handles k = VPL l .. VPL l + VPL-1.
+// per (CW-chunk, column); lane l handles k = VPL l .. VPL l + VPL-1.  The
+// output column is offset by coff and the exponents are strided by ecols (a
+// packed batch).
 template <int MODE, int CW>
-__global__ void __launch_bounds__(256) split_tall_kernel(int K, int C, const double* __restrict__ X, long ldx, int S,
-                                                         __nv_bfloat16* planes, long ldp, size_t plane, int* eX,
-                                                         int* xmax)
+__device__ __forceinline__ void split_tall_column(int K, const double* __restrict__ X, long ldx, long c, int S,
+                                                  __nv_bfloat16* planes, long ldp, size_t plane, int* eX, int* xmax,
+                                                  int kc, long coff, long ecols)
 {
     constexpr bool SCALED = MODE != 0;  // exponents are recorded
     constexpr int VPL = CW / 32;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int kc = blockIdx.x;
-    const long c = (long)blockIdx.y * 8 + w;
-    if (c >= C) return;
+    const int lane = threadIdx.x & 31;
     const long k0 = (long)kc * CW + VPL * lane;
     double v[VPL];
 #pragma unroll
@@ -360,10 +409,35 @@ __global__ void __launch_bounds__(256) split_tall_kernel(int K, int C, const dou
     }
     const int e = SCALED ? warp_chunk_exponent<VPL>(v) : 0;
     if (SCALED && lane == 0) {
-        eX[(size_t)kc * C + c] = e;
-        if (e != EXP_NONE) atomicMax(&xmax[c], e);
+        eX[(size_t)kc * ecols + coff + c] = e;
+        if (e != EXP_NONE) atomicMax(&xmax[coff + c], e);
     }
-    store_run<MODE, VPL>(planes, plane, (size_t)c * ldp + k0, S, v, e);
+    store_run<MODE, VPL>(planes, plane, (size_t)(coff + c) * ldp + k0, S, v, e);
+}
+
+template <int MODE, int CW>
+__global__ void __launch_bounds__(256) split_tall_kernel(int K, int C, const double* __restrict__ X, long ldx, int S,
+                                                         __nv_bfloat16* planes, long ldp, size_t plane, int* eX,
+                                                         int* xmax)
+{
+    const long c = (long)blockIdx.y * 8 + (threadIdx.x >> 5);
+    if (c >= C) return;
+    split_tall_column<MODE, CW>(K, X, ldx, c, S, planes, ldp, plane, eX, xmax, blockIdx.x, 0, C);
+}
+
+// The column split of a packed batch: warp w of block y takes packed column
+// 8y + w, found in its instance by the column offsets (first = off there).
+__global__ void __launch_bounds__(256) split_tall_batch_kernel(const SplitInst* __restrict__ inst, int ninst, int S,
+                                                               __nv_bfloat16* planes, long ldp, size_t plane, int* eX,
+                                                               int* xmax, long ecols)
+{
+    const long gc = (long)blockIdx.y * 8 + (threadIdx.x >> 5);
+    if (gc >= ecols) return;
+    const int b = last_le_split(inst, ninst, (int)gc);
+    const SplitInst I = inst[b];
+    const int kc = blockIdx.x;
+    if (kc >= I.kch) return;
+    split_tall_column<1, KCH_EMU>(I.K, I.X, I.ldx, gc - I.off, S, planes, ldp, plane, eX, xmax, kc, I.off, ecols);
 }
 
 __global__ void fill_int_kernel(int* p, long n, int v)
@@ -373,34 +447,56 @@ __global__ void fill_int_kernel(int* p, long n, int v)
 }
 
 // ---------------------------------------------------------- work items ----
+// One instance of a packed batch: its left operand occupies rows
+// [roff, roff + rows) of the packed left planes, its right operand columns
+// [coff, coff + cols) of the packed right planes; K is its contraction length.
+// Its items are [item0, item0 + items); cum + cum0 holds its per-row-tile
+// item prefix (rt + 1 entries).  Its output (rows x cols, column-major, ldo)
+// starts at out; elements [e0, e0 + rows cols) of the batch's reduction.
+struct TcInst {
+    int rows, cols, K, tri;
+    int roff, coff;
+    int rt, cc;
+    int item0, cum0;
+    long e0;
+    double* out;
+    long ldo;
+};
+
 struct TcArgs {
-    int rowsA, colsB, K;  // left operand rows, right operand columns, contraction length
+    int rowsA, colsB, K;  // one instance: its sizes; a packed batch: total rows, total columns, largest K
     int tri;              // 1: row tile I stops at k = 128 (I + 1)
     int ks;               // k-step (elements)
     int piece;            // k-steps per item
-    int cc;               // column chunks
-    int rt;               // row tiles
+    int cc;               // column chunks (one instance)
+    int rt;               // row tiles (one instance)
     int nitems;
-    const int* cum;       // rt + 1 item offsets
-    double* slots;        // nitems x 128 x N, row-major per slot
-    const int* eA;        // [K/128][rowsA]
-    const int* eB;        // [K/128][colsB]
+    const int* cum;       // one instance: rt + 1 item offsets; a batch: the instances' prefixes
+    double* slots;        // nitems x 128 x N, row-major per slot (FP32 slots use the first half)
+    const int* eA;        // [chunks][rowsA]
+    const int* eB;        // [chunks][colsB]
     const int* emaxA;     // [rowsA]
     const int* emaxB;     // [colsB]
     DevStatus* st;
     uint64_t limit_ns;
+    int ninst;            // 0: one instance; > 0: a packed batch of ninst instances
+    const TcInst* inst;   // [ninst]
+    const int* inst_item0;  // [ninst + 1]: first item of each instance, then the total
+    long nout;            // a batch: total output elements
 };
 
-__device__ __host__ inline int kend_of(const TcArgs& a, int I)
+__device__ __host__ inline int kend_of(int K, int tri, int I)
 {
-    if (!a.tri) return a.K;
+    if (!tri) return K;
     const long e = (long)(I + 1) * TM;
-    return e < a.K ? (int)e : a.K;
+    return e < K ? (int)e : K;
 }
-
-__device__ __host__ inline int nks_of(const TcArgs& a, int I) { return (kend_of(a, I) + a.ks - 1) / a.ks; }
-
-__device__ __host__ inline int pieces_of(const TcArgs& a, int I) { return (nks_of(a, I) + a.piece - 1) / a.piece; }
+__device__ __host__ inline int nks_of(int K, int tri, int ks, int I) { return (kend_of(K, tri, I) + ks - 1) / ks; }
+__device__ __host__ inline int pieces_of(int K, int tri, int ks, int piece, int I)
+{
+    return (nks_of(K, tri, ks, I) + piece - 1) / piece;
+}
+__device__ __host__ inline int pieces_of(const TcArgs& a, int I) { return pieces_of(a.K, a.tri, a.ks, a.piece, I); }
 
 __global__ void item_prefix_kernel(TcArgs a, int* cum)
 {
@@ -413,26 +509,53 @@ __global__ void item_prefix_kernel(TcArgs a, int* cum)
     cum[a.rt] = s;
 }
 
+// A work item: row tile I, k-steps [ks0, ks1), column chunk c, of the
+// instance whose operands start at row roff / column coff and have rows x cols
+// valid entries.
 struct Item {
     int I, ks0, ks1, c;
+    int roff, coff, rows, cols;
 };
+
+__device__ inline int last_le(const int* v, int lo, int hi, int j)  // last index i in [lo, hi] with v[i] <= j
+{
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (v[mid] <= j) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
 
 __device__ inline Item item_of(const TcArgs& a, int j)
 {
-    int lo = 0, hi = a.rt - 1;
-    while (lo < hi) {  // last I with cum[I] <= j
-        const int mid = (lo + hi + 1) >> 1;
-        if (a.cum[mid] <= j) lo = mid;
-        else hi = mid - 1;
-    }
     Item it;
-    it.I = lo;
-    const int rem = j - a.cum[lo];
-    const int p = rem / a.cc;
-    it.c = rem % a.cc;
+    int K = a.K, tri = a.tri, cc = a.cc, rt = a.rt, jl = j;
+    const int* cum = a.cum;
+    it.roff = 0;
+    it.coff = 0;
+    it.rows = a.rowsA;
+    it.cols = a.colsB;
+    if (a.ninst > 0) {
+        const int b = last_le(a.inst_item0, 0, a.ninst - 1, j);
+        const TcInst& I = a.inst[b];
+        K = I.K;
+        tri = I.tri;
+        cc = I.cc;
+        rt = I.rt;
+        jl = j - I.item0;
+        cum = a.cum + I.cum0;
+        it.roff = I.roff;
+        it.coff = I.coff;
+        it.rows = I.rows;
+        it.cols = I.cols;
+    }
+    it.I = last_le(cum, 0, rt - 1, jl);
+    const int rem = jl - cum[it.I];
+    const int p = rem / cc;
+    it.c = rem % cc;
     it.ks0 = p * a.piece;
-    const int n = nks_of(a, lo);
-    it.ks1 = min(n, it.ks0 + a.piece);
+    it.ks1 = min(nks_of(K, tri, a.ks, it.I), it.ks0 + a.piece);
     return it;
 }
 
@@ -612,9 +735,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     unsigned char* base = smem + stg * C::STAGE;
                     mbar_expect_tx(&full[stg], C::STAGE);
                     for (int s = 0; s < S; ++s)
-                        tma_load_3d(base + s * C::A_TILE, &mapA, &full[stg], ks * KS, item.I * TM, s);
+                        tma_load_3d(base + s * C::A_TILE, &mapA, &full[stg], ks * KS, item.roff + item.I * TM, s);
                     for (int t = 0; t < S; ++t)
-                        tma_load_3d(base + S * C::A_TILE + t * C::B_TILE, &mapB, &full[stg], ks * KS, item.c * N, t);
+                        tma_load_3d(base + S * C::A_TILE + t * C::B_TILE, &mapB, &full[stg], ks * KS,
+                                    item.coff + item.c * N, t);
                 }
             }
             // copies still in flight must land before the CTA may exit
@@ -714,21 +838,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const int kc0 = (item.ks0 * KS) / C::KCH;
                 for (int e = dt; e < nch * TM; e += 256) {
                     const int ch = e / TM, rr = e % TM;
-                    const long g = (long)item.I * TM + rr;
+                    const int g = item.I * TM + rr;  // row within the instance
                     float v = 0.0f;
-                    if (g < a.rowsA) {
-                        const int er = a.eA[(size_t)(kc0 + ch) * a.rowsA + g];
-                        if (er != EXP_NONE) v = pow2f(er - a.emaxA[g] - (MODE == 2 ? 16 : 14));
+                    if (g < item.rows) {
+                        const long gr = item.roff + g;
+                        const int er = a.eA[(size_t)(kc0 + ch) * a.rowsA + gr];
+                        if (er != EXP_NONE) v = pow2f(er - a.emaxA[gr] - (MODE == 2 ? 16 : 14));
                     }
                     rowsc[ch * TM + rr] = v;
                 }
                 for (int e = dt; e < nch * N; e += 256) {
                     const int ch = e / N, cc = e % N;
-                    const int col = item.c * N + cc;
+                    const int col = item.c * N + cc;  // column within the instance
                     float v = 0.0f;
-                    if (col < a.colsB) {
-                        const int eb = a.eB[(size_t)(kc0 + ch) * a.colsB + col];
-                        if (eb != EXP_NONE) v = pow2f(eb - a.emaxB[col]);
+                    if (col < item.cols) {
+                        const long gc = item.coff + col;
+                        const int eb = a.eB[(size_t)(kc0 + ch) * a.colsB + gc];
+                        if (eb != EXP_NONE) v = pow2f(eb - a.emaxB[gc]);
                     }
                     colsc[ch * N + cc] = v;
                 }
@@ -829,6 +955,53 @@ __global__ void slot_reduce_f32_kernel(TcArgs a, double* out, long ldo, const De
     }
     const int er = a.emaxA[row], ec = a.emaxB[col];
     out[row + (long)col * ldo] = (er == EXP_NONE || ec == EXP_NONE) ? 0.0 : ldexp((double)s, er + ec);
+}
+
+// A packed batch: every instance's output (rows x cols, column-major, ldo) is
+// the sum over the pieces of each tile of its slots, in piece order; F32: FP32
+// slots scaled by 2^(emax_row + emax_col) (TC2), else FP64 slots (EMU64).
+__device__ inline int last_le_e0(const TcInst* v, int n, long e)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (v[mid].e0 <= e) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int N, bool F32>
+__global__ void slot_reduce_batch_kernel(TcArgs a)
+{
+    if (*(volatile const int*)&a.st->code != 0) return;
+    const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= a.nout) return;
+    const TcInst I = a.inst[last_le_e0(a.inst, a.ninst, e)];
+    const long el = e - I.e0;
+    const int col = (int)(el / I.rows), row = (int)(el % I.rows);
+    const int T = row / TM, c = col / N;
+    const int np = pieces_of(I.K, I.tri, a.ks, a.piece, T);
+    const int* cum = a.cum + I.cum0;
+    double r;
+    if constexpr (F32) {
+        const float* slots = reinterpret_cast<const float*>(a.slots);
+        float s = 0.0f;
+        for (int p = 0; p < np; ++p) {
+            const int j = I.item0 + cum[T] + p * I.cc + c;
+            s += slots[(size_t)j * TM * N + (size_t)(row % TM) * N + (col % N)];
+        }
+        const int er = a.emaxA[I.roff + row], ec = a.emaxB[I.coff + col];
+        r = (er == EXP_NONE || ec == EXP_NONE) ? 0.0 : ldexp((double)s, er + ec);
+    } else {
+        double s = 0.0;
+        for (int p = 0; p < np; ++p) {
+            const int j = I.item0 + cum[T] + p * I.cc + c;
+            s += a.slots[(size_t)j * TM * N + (size_t)(row % TM) * N + (col % N)];
+        }
+        r = s;
+    }
+    I.out[row + (long)col * I.ldo] = r;
 }
 
 // G = C + C^T (+ shift I), exactly symmetric.
@@ -1011,10 +1184,11 @@ __global__ void __launch_bounds__(EMU_THREADS, 1)
                     unsigned char* base = smem + stg * EMU_STAGE;
                     mbar_expect_tx(&full[stg], EMU_STAGE);
                     for (int s = 0; s < EMU_S; ++s)
-                        tma_load_3d(base + s * EMU_A_TILE, &mapA, &full[stg], ks * EMU_KS, item.I * TM, s);
+                        tma_load_3d(base + s * EMU_A_TILE, &mapA, &full[stg], ks * EMU_KS, item.roff + item.I * TM,
+                                    s);
                     for (int t = 0; t < EMU_S; ++t)
                         tma_load_3d(base + EMU_S * EMU_A_TILE + t * EMU_B_TILE, &mapB, &full[stg], ks * EMU_KS,
-                                    item.c * EMU_N, t);
+                                    item.coff + item.c * EMU_N, t);
                 }
             }
             const long issued = it;  // copies still in flight must land before the CTA may exit
@@ -1091,12 +1265,12 @@ __global__ void __launch_bounds__(EMU_THREADS, 1)
         bool stop = false;
         for (int j = blockIdx.x; j < a.nitems && !stop; j += gridDim.x) {
             const Item item = item_of(a, j);
-            const long gi = (long)item.I * TM + r;
-            const bool row_ok = gi < a.rowsA;
+            const int gi = item.I * TM + r;  // row within the instance
+            const bool row_ok = gi < item.rows;
             float H[EMU_CPT], L[EMU_CPT];
 #pragma unroll
             for (int c = 0; c < EMU_CPT; ++c) H[c] = L[c] = 0.f;
-            const int emax_r = row_ok ? a.emaxA[gi] : 0;
+            const int emax_r = row_ok ? a.emaxA[item.roff + gi] : 0;
             const int nsteps = item.ks1 - item.ks0;
             const int nch = (nsteps + EMU_CH - 1) / EMU_CH;
             {
@@ -1107,9 +1281,10 @@ __global__ void __launch_bounds__(EMU_THREADS, 1)
                 const int kc0 = (item.ks0 * EMU_KS) / KCH_EMU;
                 for (int e = dt; e < nch * TM; e += EMU_DRAIN) {
                     const int ch = e / TM, rr = e % TM;
-                    const long gr = (long)item.I * TM + rr;
+                    const int g = item.I * TM + rr;  // row within the instance
                     float v = 0.0f;
-                    if (gr < a.rowsA) {
+                    if (g < item.rows) {
+                        const long gr = item.roff + g;
                         const int er = a.eA[(size_t)(kc0 + ch) * a.rowsA + gr];
                         if (er != EXP_NONE) v = pow2f(er - a.emaxA[gr] - 14);
                     }
@@ -1117,11 +1292,12 @@ __global__ void __launch_bounds__(EMU_THREADS, 1)
                 }
                 for (int e = dt; e < nch * EMU_N; e += EMU_DRAIN) {
                     const int ch = e / EMU_N, cc = e % EMU_N;
-                    const int col = item.c * EMU_N + cc;
+                    const int col = item.c * EMU_N + cc;  // column within the instance
                     float v = 0.0f;
-                    if (col < a.colsB) {
-                        const int eb = a.eB[(size_t)(kc0 + ch) * a.colsB + col];
-                        if (eb != EXP_NONE) v = pow2f(eb - a.emaxB[col]);
+                    if (col < item.cols) {
+                        const long gc = item.coff + col;
+                        const int eb = a.eB[(size_t)(kc0 + ch) * a.colsB + gc];
+                        if (eb != EXP_NONE) v = pow2f(eb - a.emaxB[gc]);
                     }
                     colsc[ch * EMU_N + cc] = v;
                 }
@@ -1181,8 +1357,8 @@ __global__ void __launch_bounds__(EMU_THREADS, 1)
             double* slot = a.slots + (size_t)j * TM * EMU_N + (size_t)r * EMU_N + g * EMU_CPT;
 #pragma unroll
             for (int c = 0; c < EMU_CPT; ++c) {
-                const int col = item.c * EMU_N + g * EMU_CPT + c;
-                const int ec = col < a.colsB ? __ldg(a.emaxB + col) : EXP_NONE;
+                const int col = item.c * EMU_N + g * EMU_CPT + c;  // column within the instance
+                const int ec = col < item.cols ? __ldg(a.emaxB + item.coff + col) : EXP_NONE;
                 double out = 0.0;
                 if (row_ok && emax_r != EXP_NONE && ec != EXP_NONE) {
                     const int k = emax_r + ec;
@@ -1550,6 +1726,289 @@ cudaError_t launch_trsm_tc(int m, int n, const double* Z, long ldz, const double
             U = L.U;
         }
         if ((e = launch_trsm_block(m, jb, bw, Z, ldz, U, m, R, ldr, Q, ldq, st, s)) != cudaSuccess) return e;
+    }
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------ packed batches ----
+// Waves of instances (see oqr_internal.cuh): per wave the A planes hold the
+// instances' rows one after another (instance b at packed row r_b) and the Z
+// and U planes their columns (instance b at packed column c_b).  A work item
+// of instance b reads its own rows and columns; rows and columns of a tile
+// that pass the instance's end belong to the next instance (or are zero
+// filled by the tensor map) and only touch outputs that the drain discards.
+namespace {
+struct WaveLayout {
+    __nv_bfloat16 *Ap, *Zp, *Up;
+    int *eA, *mA, *eZ, *mZ, *eU, *mU;
+    double* slots;
+    size_t bytes;
+};
+WaveLayout wave_layout(const TcBatchWave& w, void* ws)
+{
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    char* base = static_cast<char*>(ws);
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        char* q = base ? base + o : nullptr;
+        o += al(bytes);
+        return q;
+    };
+    WaveLayout L;
+    L.Ap = reinterpret_cast<__nv_bfloat16*>(take((size_t)EMU_S * w.rows * w.ldp * 2));
+    L.eA = reinterpret_cast<int*>(take((size_t)w.kch * w.rows * 4));
+    L.mA = reinterpret_cast<int*>(take((size_t)w.rows * 4));
+    L.Zp = reinterpret_cast<__nv_bfloat16*>(take((size_t)EMU_S * w.cols * w.ldp * 2));
+    L.Up = reinterpret_cast<__nv_bfloat16*>(take((size_t)EMU_S * w.cols * w.ldp * 2));
+    L.eZ = reinterpret_cast<int*>(take((size_t)w.kch * w.cols * 4));
+    L.eU = reinterpret_cast<int*>(take((size_t)w.kch * w.cols * 4));
+    L.mZ = reinterpret_cast<int*>(take((size_t)w.cols * 4));
+    L.mU = reinterpret_cast<int*>(take((size_t)w.cols * 4));
+    L.slots = reinterpret_cast<double*>(take((size_t)w.max_items * TM * EMU_N * 8));
+    L.bytes = o;
+    return L;
+}
+int batch_ks(int mode) { return mode == 1 ? EMU_KS : 64; }
+// Items of one instance's product: U = M Z (tri, rows m) or C = Z^T U (rows n).
+int batch_items(int rows, int cols, int K, int tri, int mode)
+{
+    const int ks = batch_ks(mode), piece = 2048 / ks;
+    const int rt = (rows + TM - 1) / TM, cc = (cols + EMU_N - 1) / EMU_N;
+    int s = 0;
+    for (int I = 0; I < rt; ++I) s += pieces_of(K, tri, ks, piece, I) * cc;
+    return s;
+}
+// Members of launch li of a pass: pass 0 has one launch per first-pass mode present (TC2, then
+// EMU64); pass 1 runs every instance of the wave in EMU64.
+std::vector<int> launch_members(const std::vector<TcBatchShape>& sh, const TcBatchWave& w, int pass, int mode)
+{
+    std::vector<int> v;
+    for (int b = w.first; b < w.first + w.count; ++b)
+        if (pass == 1 || sh[b].mode0 == mode) v.push_back(b);
+    return v;
+}
+}  // namespace
+
+TcBatchPlan tc_batch_plan(const std::vector<TcBatchShape>& sh, size_t budget)
+{
+    TcBatchPlan p;
+    const int count = (int)sh.size();
+    size_t tab = 0;
+    auto tk = [&](size_t bytes) {
+        const size_t o = tab;
+        tab += (bytes + 255) & ~size_t(255);
+        return o;
+    };
+    int b = 0;
+    while (b < count) {
+        TcBatchWave w{};
+        w.first = b;
+        w.K = sh[b].m;  // the largest m of the wave (sorted order)
+        w.ldp = ((long)w.K + KCH_EMU - 1) / KCH_EMU * KCH_EMU;
+        w.kch = (int)(w.ldp / KCH_EMU);
+        long rows = 0, cols = 0;
+        int e = b;
+        while (e < count) {
+            const long r2 = rows + sh[e].m, c2 = cols + sh[e].n;
+            if (e > b && (size_t)EMU_S * 2 * w.ldp * (r2 + 2 * c2) > budget) break;
+            rows = r2;
+            cols = c2;
+            ++e;
+        }
+        w.count = e - b;
+        w.rows = rows;
+        w.cols = cols;
+        w.splitA = tk((size_t)w.count * sizeof(SplitInst));
+        w.splitZ = tk((size_t)w.count * sizeof(SplitInst));
+        w.splitQ = tk((size_t)w.count * sizeof(SplitInst));
+        w.splitU = tk((size_t)w.count * sizeof(SplitInst));
+        w.tilesA = 0;
+        w.upool = 0;
+        for (int i = b; i < e; ++i) {
+            w.tilesA += ((sh[i].m + KCH_EMU - 1) / KCH_EMU) * ((sh[i].m + 15) / 16);
+            w.upool += (long)sh[i].m * sh[i].n;
+        }
+        w.max_items = 1;
+        for (int pass = 0; pass < 2; ++pass) {
+            w.nl[pass] = 0;
+            const int modes[2] = {3, 1};
+            for (int k = 0; k < 2; ++k) {
+                if (pass == 1 && k == 0) continue;
+                const std::vector<int> mem = launch_members(sh, w, pass, modes[k]);
+                if (mem.empty()) continue;
+                const int li = w.nl[pass]++;
+                for (int prod = 0; prod < 2; ++prod) {
+                    TcBatchLaunch& L = prod == 0 ? w.u[pass][li] : w.c[pass][li];
+                    L.mode = modes[k];
+                    L.ninst = (int)mem.size();
+                    L.nitems = 0;
+                    L.nout = 0;
+                    long ncum = 0;
+                    for (int i : mem) {
+                        const int rows_i = prod == 0 ? sh[i].m : sh[i].n;
+                        L.nitems += batch_items(rows_i, sh[i].n, sh[i].m, prod == 0, L.mode);
+                        L.nout += (long)rows_i * sh[i].n;
+                        ncum += (rows_i + TM - 1) / TM + 1;
+                    }
+                    L.inst = tk((size_t)L.ninst * sizeof(TcInst));
+                    L.item0 = tk((size_t)(L.ninst + 1) * 4);
+                    L.cum = tk((size_t)ncum * 4);
+                    if (L.nitems > w.max_items) w.max_items = L.nitems;
+                }
+            }
+        }
+        const size_t sb = wave_layout(w, nullptr).bytes;
+        if (sb > p.scratch_bytes) p.scratch_bytes = sb;
+        if (w.upool > p.upool_doubles) p.upool_doubles = w.upool;
+        p.waves.push_back(w);
+        b = e;
+    }
+    p.table_bytes = tab;
+    return p;
+}
+
+void tc_batch_tables(const TcBatchPlan& p, const std::vector<TcBatchShape>& sh, const std::vector<TcBatchIn>& in,
+                     const void* table_dev, double* upool, std::vector<char>& image)
+{
+    (void)table_dev;
+    image.assign(p.table_bytes, 0);
+    char* img = image.data();
+    for (const TcBatchWave& w : p.waves) {
+        std::vector<long> roff(w.count), coff(w.count), uoff(w.count);
+        long r = 0, c = 0, u = 0;
+        for (int i = 0; i < w.count; ++i) {
+            roff[i] = r;
+            coff[i] = c;
+            uoff[i] = u;
+            r += sh[w.first + i].m;
+            c += sh[w.first + i].n;
+            u += (long)sh[w.first + i].m * sh[w.first + i].n;
+        }
+        SplitInst* sa = reinterpret_cast<SplitInst*>(img + w.splitA);
+        SplitInst* sz = reinterpret_cast<SplitInst*>(img + w.splitZ);
+        SplitInst* sq = reinterpret_cast<SplitInst*>(img + w.splitQ);
+        SplitInst* su = reinterpret_cast<SplitInst*>(img + w.splitU);
+        int tiles = 0;
+        for (int i = 0; i < w.count; ++i) {
+            const int b = w.first + i, m = sh[b].m, n = sh[b].n, kch = (m + KCH_EMU - 1) / KCH_EMU;
+            sa[i] = SplitInst{in[b].A, in[b].lda, m, m, 0, roff[i], tiles, kch};
+            tiles += kch * ((m + 15) / 16);
+            sz[i] = SplitInst{in[b].Z, in[b].ldz, 0, m, n, coff[i], (int)coff[i], kch};
+            sq[i] = SplitInst{in[b].Q, in[b].ldq, 0, m, n, coff[i], (int)coff[i], kch};
+            su[i] = SplitInst{upool + uoff[i], (long)m, 0, m, n, coff[i], (int)coff[i], kch};
+        }
+        for (int pass = 0; pass < 2; ++pass)
+            for (int li = 0; li < w.nl[pass]; ++li)
+                for (int prod = 0; prod < 2; ++prod) {
+                    const TcBatchLaunch& L = prod == 0 ? w.u[pass][li] : w.c[pass][li];
+                    const std::vector<int> mem = launch_members(sh, w, pass, L.mode);
+                    TcInst* ti = reinterpret_cast<TcInst*>(img + L.inst);
+                    int* item0 = reinterpret_cast<int*>(img + L.item0);
+                    int* cum = reinterpret_cast<int*>(img + L.cum);
+                    const int ks = batch_ks(L.mode), piece = 2048 / ks;
+                    int it = 0, cm = 0;
+                    long e0 = 0;
+                    for (size_t k = 0; k < mem.size(); ++k) {
+                        const int b = mem[k], i = b - w.first, m = sh[b].m, n = sh[b].n;
+                        TcInst t{};
+                        t.rows = prod == 0 ? m : n;
+                        t.cols = n;
+                        t.K = m;
+                        t.tri = prod == 0;
+                        t.roff = (int)(prod == 0 ? roff[i] : coff[i]);
+                        t.coff = (int)coff[i];
+                        t.rt = (t.rows + TM - 1) / TM;
+                        t.cc = (t.cols + EMU_N - 1) / EMU_N;
+                        t.item0 = it;
+                        t.cum0 = cm;
+                        t.e0 = e0;
+                        t.out = prod == 0 ? upool + uoff[i] : in[b].C;
+                        t.ldo = t.rows;
+                        int s = 0;
+                        for (int I = 0; I < t.rt; ++I) {
+                            cum[cm + I] = s;
+                            s += pieces_of(t.K, t.tri, ks, piece, I) * t.cc;
+                        }
+                        cum[cm + t.rt] = s;
+                        ti[k] = t;
+                        item0[k] = it;
+                        it += s;
+                        cm += t.rt + 1;
+                        e0 += (long)t.rows * t.cols;
+                    }
+                    item0[mem.size()] = it;
+                }
+    }
+}
+
+cudaError_t tc_batch_split_a(const TcBatchPlan& p, int w, const void* table_dev, void* scratch, cudaStream_t s)
+{
+    const TcBatchWave& W = p.waves[w];
+    const WaveLayout L = wave_layout(W, scratch);
+    const char* tab = static_cast<const char*>(table_dev);
+    fill_int_kernel<<<(unsigned)((W.rows + 255) / 256), 256, 0, s>>>(L.mA, W.rows, EXP_NONE);
+    split_lower_batch_kernel<<<W.tilesA, 256, 0, s>>>(reinterpret_cast<const SplitInst*>(tab + W.splitA), W.count,
+                                                      EMU_S, L.Ap, W.ldp, (size_t)W.rows * W.ldp, L.eA, L.mA, W.rows);
+    return cudaGetLastError();
+}
+
+cudaError_t tc_batch_gram(const TcBatchPlan& p, int w, int pass, const void* table_dev, void* scratch,
+                          DevStatus* st, uint64_t limit_ns, int sms, cudaStream_t s)
+{
+    const TcBatchWave& W = p.waves[w];
+    const WaveLayout L = wave_layout(W, scratch);
+    const char* tab = static_cast<const char*>(table_dev);
+    const size_t planeA = (size_t)W.rows * W.ldp, planeZ = (size_t)W.cols * W.ldp;  // elements
+    const dim3 gt(W.kch, (unsigned)((W.cols + 7) / 8));
+    auto args = [&](const TcBatchLaunch& B, long rowsA, const int* eA, const int* eB, const int* mA,
+                    const int* mB) {
+        TcArgs a{};
+        a.rowsA = (int)rowsA;
+        a.colsB = (int)W.cols;
+        a.K = W.K;
+        a.ks = batch_ks(B.mode);
+        a.piece = 2048 / a.ks;
+        a.nitems = B.nitems;
+        a.cum = reinterpret_cast<const int*>(tab + B.cum);
+        a.slots = L.slots;
+        a.eA = eA;
+        a.eB = eB;
+        a.emaxA = mA;
+        a.emaxB = mB;
+        a.st = st;
+        a.limit_ns = limit_ns;
+        a.ninst = B.ninst;
+        a.inst = reinterpret_cast<const TcInst*>(tab + B.inst);
+        a.inst_item0 = reinterpret_cast<const int*>(tab + B.item0);
+        a.nout = B.nout;
+        return a;
+    };
+    auto product = [&](const TcBatchLaunch& B, const TcArgs& a, const void* PA, size_t plA, const void* PB) {
+        cudaError_t e;
+        if (B.mode == 1) e = launch_emu(a, PA, W.ldp, plA, PB, W.ldp, planeZ, sms, s);
+        else e = launch_tc<64, 64, 2, 3>(a, PA, W.ldp, plA, PB, W.ldp, planeZ, sms, s);
+        if (e != cudaSuccess) return e;
+        const unsigned g = (unsigned)((B.nout + 255) / 256);
+        if (B.mode == 1) slot_reduce_batch_kernel<EMU_N, false><<<g, 256, 0, s>>>(a);
+        else slot_reduce_batch_kernel<EMU_N, true><<<g, 256, 0, s>>>(a);
+        return cudaGetLastError();
+    };
+    cudaError_t e;
+    // the split of X (Z in pass 0, Q in pass 1), then U = M X for every launch of the pass
+    fill_int_kernel<<<(unsigned)((W.cols + 255) / 256), 256, 0, s>>>(L.mZ, W.cols, EXP_NONE);
+    split_tall_batch_kernel<<<gt, 256, 0, s>>>(reinterpret_cast<const SplitInst*>(tab + (pass ? W.splitQ : W.splitZ)),
+                                               W.count, EMU_S, L.Zp, W.ldp, planeZ, L.eZ, L.mZ, W.cols);
+    for (int li = 0; li < W.nl[pass]; ++li) {
+        const TcBatchLaunch& B = W.u[pass][li];
+        if ((e = product(B, args(B, W.rows, L.eA, L.eZ, L.mA, L.mZ), L.Ap, planeA, L.Zp)) != cudaSuccess) return e;
+    }
+    // the split of U, then C = X^T U
+    fill_int_kernel<<<(unsigned)((W.cols + 255) / 256), 256, 0, s>>>(L.mU, W.cols, EXP_NONE);
+    split_tall_batch_kernel<<<gt, 256, 0, s>>>(reinterpret_cast<const SplitInst*>(tab + W.splitU), W.count, EMU_S,
+                                               L.Up, W.ldp, planeZ, L.eU, L.mU, W.cols);
+    for (int li = 0; li < W.nl[pass]; ++li) {
+        const TcBatchLaunch& B = W.c[pass][li];
+        if ((e = product(B, args(B, W.cols, L.eZ, L.eU, L.mZ, L.mU), L.Zp, planeZ, L.Up)) != cudaSuccess) return e;
     }
     return cudaGetLastError();
 }

@@ -22,6 +22,9 @@ struct oqr_ctx {
     // cached CUDA graph of the batched sequence and the signature it was captured for
     cudaGraphExec_t batch_exec = nullptr;
     long batch_key[10] = {0};
+    // the same for the batched tensor-core (mixed) sequence: its signature is every instance's shape
+    cudaGraphExec_t mixed_exec = nullptr;
+    std::vector<long> mixed_key;
     // host-buffer path: device staging (A, Z, Q, R), a copy stream and one event per panel of A
     void* stage = nullptr;
     size_t stage_bytes = 0;
@@ -443,6 +446,48 @@ oqr_status cgs2_impl(oqr_ctx* ctx, int m, int n, const double* A, long lda, cons
 
 }  // namespace
 
+namespace {
+// Slice planes of one wave of the batched tensor-core path (the packed A, Z and U planes).
+constexpr size_t BATCH_WAVE_BYTES = size_t(16) << 30;
+
+// Captures seq into the context's cached graph for key (or replays the cached
+// one), then launches it on s; on the legacy default stream seq runs directly.
+template <class F>
+oqr_status run_cached_graph(oqr_ctx* ctx, const std::vector<long>& key, F seq, cudaStream_t s)
+{
+    if (s == nullptr) {
+        OQR_TRY(seq());
+        return OQR_OK;
+    }
+    if (!ctx->mixed_exec || key != ctx->mixed_key) {
+        if (ctx->mixed_exec) {
+            cudaStreamSynchronize(s);
+            cudaGraphExecDestroy(ctx->mixed_exec);
+            ctx->mixed_exec = nullptr;
+            ctx->mixed_key.clear();
+        }
+        cudaGraph_t g = nullptr;
+        OQR_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        const cudaError_t le = seq();
+        const cudaError_t ce = cudaStreamEndCapture(s, &g);
+        if (le != cudaSuccess || ce != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return OQR_ERR_CUDA;
+        }
+        const cudaError_t ie = cudaGraphInstantiate(&ctx->mixed_exec, g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) {
+            ctx->mixed_exec = nullptr;
+            return OQR_ERR_CUDA;
+        }
+        ctx->mixed_key = key;
+    }
+    OQR_TRY(cudaGraphLaunch(ctx->mixed_exec, s));
+    return OQR_OK;
+}
+}  // namespace
+
 extern "C" {
 
 void oqr_default_opts(oqr_opts* opts)
@@ -494,6 +539,7 @@ oqr_status oqr_destroy(oqr_ctx* ctx)
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
     if (ctx->batch_exec) cudaGraphExecDestroy(ctx->batch_exec);
+    if (ctx->mixed_exec) cudaGraphExecDestroy(ctx->mixed_exec);
     if (ctx->stage) cudaFree(ctx->stage);
     for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
     if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
@@ -701,7 +747,11 @@ oqr_status oqr_batched(oqr_ctx* ctx, int count, const int* m, const int* n, cons
     if (!ctx || count < 1 || count > 65535 || !m || !n || !A || !lda || !Z || !ldz || !Q || !ldq || !R || !ldr ||
         !status)
         return OQR_ERR_INVALID_ARG;
-    if (mode != 0) return OQR_ERR_UNSUPPORTED;
+    if (mode == 1 || mode == 2) {
+        std::vector<int> fp((size_t)count, mode == 1 ? OQR_FP64_TC : OQR_TC2);
+        return oqr_batched_mixed(ctx, count, m, n, A, lda, Z, ldz, Q, ldq, R, ldr, fp.data(), status, stream);
+    }
+    if (mode != 0) return OQR_ERR_INVALID_ARG;
     std::vector<BatchDesc> desc((size_t)count);
     std::vector<int> idx[3];
     int cls_max_splits[3] = {1, 1, 1}, max_n = 1;
@@ -794,6 +844,113 @@ oqr_status oqr_batched(oqr_ctx* ctx, int count, const int* m, const int* n, cons
     }
     OQR_TRY(cudaGraphLaunch(ctx->batch_exec, s));
     return OQR_OK;
+}
+
+oqr_status oqr_batched_mixed(oqr_ctx* ctx, int count, const int* m, const int* n, const double* const* A,
+                             const long* lda, const double* const* Z, const long* ldz, double* const* Q,
+                             const long* ldq, double* const* R, const long* ldr, const int* first_prec, int* status,
+                             void* stream)
+{
+    if (!ctx || count < 1 || count > 65535 || !m || !n || !A || !lda || !Z || !ldz || !Q || !ldq || !R || !ldr ||
+        !status)
+        return OQR_ERR_INVALID_ARG;
+    for (int b = 0; b < count; ++b) {
+        const int mb = m[b], nb = n[b];
+        if (mb < 1 || nb < 1 || nb > mb || nb > BATCH_MAX_N || mb > BATCH_MAX_M) return OQR_ERR_INVALID_ARG;
+        if (bad_matrix(A[b], lda[b], mb, mb) || bad_matrix(Z[b], ldz[b], mb, nb) || bad_matrix(Q[b], ldq[b], mb, nb) ||
+            bad_matrix(R[b], ldr[b], nb, nb))
+            return OQR_ERR_INVALID_ARG;
+        if (first_prec && first_prec[b] != OQR_TC2 && first_prec[b] != OQR_FP64_TC) return OQR_ERR_INVALID_ARG;
+    }
+    // largest m first: a wave's plane pitch is its first instance's m
+    std::vector<int> perm((size_t)count);
+    for (int b = 0; b < count; ++b) perm[b] = b;
+    std::stable_sort(perm.begin(), perm.end(), [&](int x, int y) { return m[x] > m[y]; });
+    std::vector<TcBatchShape> sh((size_t)count);
+    std::vector<long> key{count, 0, (long)reinterpret_cast<uintptr_t>(status)};
+    size_t pool_doubles = 0;
+    for (int i = 0; i < count; ++i) {
+        const int b = perm[i];
+        sh[i] = TcBatchShape{m[b], n[b], (first_prec && first_prec[b] == OQR_TC2) ? 3 : 1};
+        key.push_back(((long)m[b] << 32) | ((long)n[b] << 8) | sh[i].mode0);
+        pool_doubles += align256((size_t)4 * n[b] * n[b] * sizeof(double)) / sizeof(double);
+    }
+    const TcBatchPlan plan = tc_batch_plan(sh, BATCH_WAVE_BYTES);
+    auto layout = [&](Carve& c, char** tab, BatchDesc** d, int** sts, int** dperm, double** pool, double** upool,
+                      void** scratch) {
+        *tab = c.take<char>(plan.table_bytes);
+        *d = c.take<BatchDesc>((size_t)count);
+        *sts = c.take<int>((size_t)count);
+        *dperm = c.take<int>((size_t)count);
+        *pool = c.take<double>(pool_doubles);
+        *upool = c.take<double>((size_t)plan.upool_doubles);
+        *scratch = c.take<char>(plan.scratch_bytes);
+    };
+    char* tab;
+    BatchDesc* ddesc;
+    int *sts, *dperm;
+    double *pool, *upool;
+    void* scratch;
+    Carve probe(nullptr);
+    layout(probe, &tab, &ddesc, &sts, &dperm, &pool, &upool, &scratch);
+    oqr_status v = ensure_ws(ctx, probe.off);
+    if (v != OQR_OK) return v;
+    Carve cv(ctx->ws);
+    layout(cv, &tab, &ddesc, &sts, &dperm, &pool, &upool, &scratch);
+    key[1] = (long)reinterpret_cast<uintptr_t>(ctx->ws);
+    // per instance (sorted order): its descriptor (one Gram partial = the product's half C) and tensor-core inputs
+    std::vector<BatchDesc> desc((size_t)count);
+    std::vector<TcBatchIn> in((size_t)count);
+    double* q = pool;
+    for (int i = 0; i < count; ++i) {
+        const int b = perm[i];
+        const size_t nn = (size_t)n[b] * n[b];
+        BatchDesc& d = desc[i];
+        d.A = A[b];
+        d.Z = Z[b];
+        d.Q = Q[b];
+        d.R = R[b];
+        d.lda = lda[b];
+        d.ldz = ldz[b];
+        d.ldq = ldq[b];
+        d.ldr = ldr[b];
+        d.m = m[b];
+        d.n = n[b];
+        d.splits = 1;
+        d.pad = 0;
+        d.partials = q;
+        d.G = q + nn;
+        d.R1 = d.G + nn;
+        d.R2 = d.R1 + nn;
+        q += align256(4 * nn * sizeof(double)) / sizeof(double);
+        in[i] = TcBatchIn{A[b], lda[b], Z[b], ldz[b], Q[b], ldq[b], d.partials};
+    }
+    std::vector<char> image;
+    tc_batch_tables(plan, sh, in, tab, upool, image);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    OQR_TRY(cudaMemcpyAsync(tab, image.data(), image.size(), cudaMemcpyHostToDevice, s));
+    OQR_TRY(cudaMemcpyAsync(ddesc, desc.data(), sizeof(BatchDesc) * count, cudaMemcpyHostToDevice, s));
+    OQR_TRY(cudaMemcpyAsync(dperm, perm.data(), sizeof(int) * count, cudaMemcpyHostToDevice, s));
+    OQR_TRY(cudaMemsetAsync(sts, 0, sizeof(int) * count, s));
+    if ((v = reset_status(ctx, s)) != OQR_OK) return v;
+    const uint64_t limit = 4000000000ull;
+    auto seq = [&]() -> cudaError_t {
+        cudaError_t e;
+        for (int w = 0; w < (int)plan.waves.size(); ++w) {
+            const TcBatchWave& W = plan.waves[w];
+            const BatchDesc* dw = ddesc + W.first;
+            int* sw = sts + W.first;
+            if ((e = tc_batch_split_a(plan, w, tab, scratch, s)) != cudaSuccess) return e;
+            for (int pass = 0; pass < 2; ++pass) {
+                if ((e = tc_batch_gram(plan, w, pass, tab, scratch, ctx->st, limit, ctx->sm_count, s)) != cudaSuccess)
+                    return e;
+                if ((e = launch_batched_factor(dw, W.count, sw, pass, s)) != cudaSuccess) return e;
+            }
+            if ((e = launch_batched_rprod(dw, W.count, sw, s)) != cudaSuccess) return e;
+        }
+        return launch_batch_status_scatter(sts, dperm, count, ctx->st, status, s);
+    };
+    return run_cached_graph(ctx, key, seq, s);
 }
 
 oqr_status oqr_features(oqr_ctx* ctx, int m, int n, const double* A, long lda, const double* Z, long ldz, float* feat,

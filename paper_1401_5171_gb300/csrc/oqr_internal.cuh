@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/oqr.h"
 
 namespace oqr {
@@ -227,6 +229,65 @@ struct BatchDesc {
 };
 cudaError_t launch_batched_cholqr2(const BatchDesc* d, int count, const int* const* cls_idx, const int* cls_count,
                                    const int* cls_max_splits, int max_n, int* status, cudaStream_t s);
+// Pieces of the batched sequence over a sub-range of BatchDesc (k_batched.cu):
+//   factor: G_b = P_b + P_b^T from one partial (splits = 1), R = chol(G_b)
+//           (R1 for pass 0, R2 for pass 1), Q_b = X_b / R (X = Z in pass 0, Q in place in pass 1);
+//   rprod:  R_b = R2 R1;
+//   scatter: status[perm[i]] = st_sorted[i], or -1 for every instance when a
+//           tensor-core wait of the context timed out.
+cudaError_t launch_batched_factor(const BatchDesc* d, int count, int* status, int pass, cudaStream_t s);
+cudaError_t launch_batched_rprod(const BatchDesc* d, int count, int* status, cudaStream_t s);
+cudaError_t launch_batch_status_scatter(const int* st_sorted, const int* perm, int count, const DevStatus* st,
+                                        int* status, cudaStream_t s);
+
+// Packed tensor-core batches (k_tc.cu).  Instances (sorted by m, largest
+// first) are cut into waves whose slice planes fit a byte budget; a wave's A
+// planes are stacked by rows and its Z and U planes by columns, so that one
+// tensor map per operand and one persistent launch per product cover every
+// instance of the wave.  A is split once per wave and read by both passes.
+struct TcBatchShape {
+    int m, n;
+    int mode0;  // tensor-core mode of pass 0 (1: EMU64, 3: TC2); pass 1 is EMU64
+};
+struct TcBatchIn {
+    const double* A;
+    long lda;
+    const double* Z;
+    long ldz;
+    double* Q;
+    long ldq;
+    double* C;  // n x n product Z^T A Z's half (the BatchDesc partial), column-major
+};
+struct TcBatchLaunch {
+    int mode;              // 1 EMU64, 3 TC2
+    int ninst, nitems;
+    long nout;
+    size_t inst, item0, cum;  // byte offsets of the launch's tables
+};
+struct TcBatchWave {
+    int first, count;     // instances [first, first + count) of the sorted order
+    long rows, cols, ldp;  // packed rows (sum of m), packed columns (sum of n), plane row pitch
+    int K, kch, tilesA, max_items;
+    size_t splitA, splitZ, splitQ, splitU;  // SplitInst tables (byte offsets)
+    TcBatchLaunch u[2][2], c[2][2];         // [pass][launch]: pass 0 one launch per mode present
+    int nl[2];
+    long upool;  // U pool doubles
+};
+struct TcBatchPlan {
+    std::vector<TcBatchWave> waves;
+    size_t table_bytes = 0;    // device tables
+    size_t scratch_bytes = 0;  // the largest wave's planes, exponents and slots
+    long upool_doubles = 0;    // the largest wave's U pool
+};
+TcBatchPlan tc_batch_plan(const std::vector<TcBatchShape>& sh, size_t budget);
+// Host image of the tables for the given device addresses (table, U pool).
+void tc_batch_tables(const TcBatchPlan& p, const std::vector<TcBatchShape>& sh, const std::vector<TcBatchIn>& in,
+                     const void* table_dev, double* upool, std::vector<char>& image);
+// Wave w: the split of A (once), then the Gram of pass 0 or 1 into each instance's C.
+cudaError_t tc_batch_split_a(const TcBatchPlan& p, int w, const void* table_dev, void* scratch, cudaStream_t s);
+cudaError_t tc_batch_gram(const TcBatchPlan& p, int w, int pass, const void* table_dev, void* scratch,
+                          DevStatus* st, uint64_t limit_ns, int sms, cudaStream_t s);
+
 
 // Selector (k_mlp.cu, k_features.cu).
 constexpr int MLP_IN = 16, MLP_HIDDEN = 64, MLP_OUT = 4;

@@ -87,6 +87,8 @@ def load(path: str | None = None):
     ppd = ctypes.POINTER(ctypes.c_void_p)
     lib.oqr_batched.argtypes = [vp, i, ctypes.POINTER(i), ctypes.POINTER(i), ppd, pl, ppd, pl, ppd, pl, ppd, pl, i,
                                 ctypes.POINTER(i), vp, vp]
+    lib.oqr_batched_mixed.argtypes = [vp, i, ctypes.POINTER(i), ctypes.POINTER(i), ppd, pl, ppd, pl, ppd, pl, ppd,
+                                      pl, ctypes.POINTER(i), vp, vp]
     lib.oqr_batched_default_splits.argtypes = [i, i]
     fp, ip = ctypes.c_void_p, ctypes.c_void_p
     lib.oqr_features.argtypes = [vp, i, i, vp, l, vp, l, fp, vp]
@@ -126,7 +128,7 @@ def _raw(name):
 
 for _n in ("oqr_default_opts", "oqr_create", "oqr_destroy", "oqr_workspace_size", "oqr_set_workspace",
            "oqr_get_status", "oqr_cholqr", "oqr_cholqr2", "oqr_cholqr2_host", "oqr_cgs2", "oqr_gram", "oqr_gram_noalloc", "oqr_gram_phases", "oqr_potrf", "oqr_trsm", "oqr_trsm_tc",
-           "oqr_rprod", "oqr_check", "oqr_batched", "oqr_batched_default_splits", "oqr_features",
+           "oqr_rprod", "oqr_check", "oqr_batched", "oqr_batched_mixed", "oqr_batched_default_splits", "oqr_features",
            "oqr_mlp_param_count", "oqr_mlp_forward", "oqr_mlp_grad", "oqr_mlp_adam"):
     globals()[_n] = _raw(_n)
 
@@ -276,8 +278,7 @@ class Oqr:
             raise OqrError(st, "oqr_gram_phases")
         return [ms[i] for i in range(k.value)], G
 
-    def oqr_batched(self, As, Zs, Qs=None, Rs=None, splits=None, stream=None, status=None):
-        """Batched FP64 A-CholQR2 over lists of column-major CUDA tensors; returns (Qs, Rs, status tensor)."""
+    def _batch_args(self, As, Zs, Qs, Rs, status):
         import torch
         cnt = len(Zs)
         Qs = Qs if Qs is not None else [empty_colmajor(z.shape[0], z.shape[1], z.device) for z in Zs]
@@ -292,11 +293,27 @@ class Oqr:
             (ap[b], al[b]), (zp[b], zl[b]) = _m(As[b]), _m(Zs[b])
             (qp[b], ql[b]), (rp[b], rl[b]) = _m(Qs[b]), _m(Rs[b])
         st = status if status is not None else torch.empty(cnt, dtype=torch.int32, device=Zs[0].device)
-        sp = I(*splits) if splits is not None else None
-        r = self.lib.oqr_batched(self.ctx, cnt, mm, nn, ap, al, zp, zl, qp, ql, rp, rl, 0, sp,
-                                 ctypes.c_void_p(st.data_ptr()), self._stream(stream))
+        return Qs, Rs, st, (cnt, mm, nn, ap, al, zp, zl, qp, ql, rp, rl)
+
+    def oqr_batched(self, As, Zs, Qs=None, Rs=None, splits=None, stream=None, status=None, mode=0):
+        """Batched A-CholQR2 over lists of column-major CUDA tensors; returns (Qs, Rs, status tensor).
+
+        mode 0: FP64; 1: tensor cores, every pass OQR_FP64_TC; 2: tensor cores, first pass OQR_TC2."""
+        Qs, Rs, st, a = self._batch_args(As, Zs, Qs, Rs, status)
+        sp = (ctypes.c_int * a[0])(*splits) if splits is not None else None
+        r = self.lib.oqr_batched(self.ctx, *a, int(mode), sp, ctypes.c_void_p(st.data_ptr()), self._stream(stream))
         if r != OQR_OK:
             raise OqrError(r, "oqr_batched")
+        return Qs, Rs, st
+
+    def oqr_batched_mixed(self, As, Zs, first_prec=None, Qs=None, Rs=None, stream=None, status=None):
+        """Batched A-CholQR2 on the tensor cores; first_prec: per-instance OQR_TC2 / OQR_FP64_TC (None: all
+        OQR_FP64_TC).  Returns (Qs, Rs, status tensor)."""
+        Qs, Rs, st, a = self._batch_args(As, Zs, Qs, Rs, status)
+        fp = (ctypes.c_int * a[0])(*[int(x) for x in first_prec]) if first_prec is not None else None
+        r = self.lib.oqr_batched_mixed(self.ctx, *a, fp, ctypes.c_void_p(st.data_ptr()), self._stream(stream))
+        if r != OQR_OK:
+            raise OqrError(r, "oqr_batched_mixed")
         return Qs, Rs, st
 
     # ---- selector ---------------------------------------------------------------

@@ -97,15 +97,8 @@ def test_batched_graph_replay_same_result(env):
         assert torch.equal(a, b)
 
 
-def test_config3_full_batch(env):
-    """4096 instances, m in [64, 4096], n in [4, 64], kappa(A), kappa(Z) log-uniform in [1, 1e6]."""
-    torch, oqr, ctx = env
-    As, Zs, tab = inputs.batch_instances(4096, seed=2024, device="cuda")
-    plan, table, _ = autotune.tune(ctx, As[:512], Zs[:512], reps=1)
-    plan = autotune.plan_from_table([z.shape[0] for z in Zs], table)
-    Qs, Rs, st = ctx.oqr_batched(As, Zs, splits=plan)
-    torch.cuda.synchronize()
-    st = st.cpu().numpy()
+def check_full_batch(torch, As, Zs, Qs, Rs, st, tab):
+    """Properties that fix (Q, R) on every instance; returns the number of completed instances."""
     ok = 0
     for b in range(len(Zs)):
         A, Z, Q, R = As[b], Zs[b], Qs[b], Rs[b]
@@ -126,9 +119,114 @@ def test_config3_full_batch(env):
         assert rep <= 1e-13
         assert torch.all(torch.tril(R, -1) == 0) and torch.all(torch.diagonal(R) > 0)
     assert ok >= 0.9 * len(Zs)
+    return ok
+
+
+def test_config3_full_batch(env):
+    """4096 instances, m in [64, 4096], n in [4, 64], kappa(A), kappa(Z) log-uniform in [1, 1e6]; the FP64
+    path, then the tensor-core path (every pass FP64-accurate; about 20 waves of packed instances)."""
+    torch, oqr, ctx = env
+    As, Zs, tab = inputs.batch_instances(4096, seed=2024, device="cuda")
+    plan, table, _ = autotune.tune(ctx, As[:512], Zs[:512], reps=1)
+    plan = autotune.plan_from_table([z.shape[0] for z in Zs], table)
+    Qs, Rs, st = ctx.oqr_batched(As, Zs, splits=plan)
+    torch.cuda.synchronize()
+    st = st.cpu().numpy()
+    check_full_batch(torch, As, Zs, Qs, Rs, st, tab)
     # stratified oracle sample: one instance per m-quartile with m <= 2500
     ms = np.array([z.shape[0] for z in Zs])
     for lo, hi in ((64, 700), (700, 1400), (1400, 2000), (2000, 2500)):
         cand = [b for b in range(len(Zs)) if lo <= ms[b] < hi and st[b] == 0]
         b = cand[0]
         check_instance(As[b].cpu().numpy(), Zs[b].cpu().numpy(), Qs[b].cpu().numpy(), Rs[b].cpu().numpy(), st[b])
+    # the tensor-core path on the same batch: same properties, and R agrees with the FP64 path's
+    torch.cuda.empty_cache()
+    Qm, Rm, stm = ctx.oqr_batched(As, Zs, Qs=Qs, mode=1)
+    torch.cuda.synchronize()
+    stm = stm.cpu().numpy()
+    check_full_batch(torch, As, Zs, Qm, Rm, stm, tab)
+    for b in range(len(Zs)):
+        if st[b] == 0 and stm[b] == 0:
+            kap = torch.linalg.cond(Rs[b]).item()
+            assert (torch.linalg.norm(Rm[b] - Rs[b]) / torch.linalg.norm(Rs[b])).item() <= max(1e-12, 100 * U * kap)
+
+
+# ---- the tensor-core form (oqr_batched_mixed; oqr_batched modes 1 and 2) -------------------------
+
+def test_batched_mixed_parity(env):
+    """Every pass FP64-accurate on the tensor cores (mode 1): the FP64 path's tolerances."""
+    torch, oqr, ctx = env
+    As, Zs, _ = inputs.batch_instances(40, seed=3, device="cuda", m_range=(64, 700), n_range=(4, 64))
+    Qs, Rs, st = ctx.oqr_batched(As, Zs, mode=1)
+    torch.cuda.synchronize()
+    st = st.cpu().numpy()
+    for b in range(len(Zs)):
+        check_instance(As[b].cpu().numpy(), Zs[b].cpu().numpy(), Qs[b].cpu().numpy(), Rs[b].cpu().numpy(), st[b])
+
+
+def test_batched_mixed_tc2_first_pass(env):
+    """TC2 first pass (mode 2) on instances within its reach (kappa(A^{1/2} Z) <= 1e2), ragged m and n,
+    m spanning one to several 256-column chunks and 128-row tiles."""
+    torch, oqr, ctx = env
+    As, Zs, _ = inputs.batch_instances(24, seed=11, device="cuda", m_range=(64, 1300), n_range=(1, 64),
+                                       log_kappa_a=(0.0, 2.0), log_kappa_z=(0.0, 1.0))
+    Qs, Rs, st = ctx.oqr_batched(As, Zs, mode=2)
+    torch.cuda.synchronize()
+    assert st.abs().sum().item() == 0
+    for b in range(len(Zs)):
+        check_instance(As[b].cpu().numpy(), Zs[b].cpu().numpy(), Qs[b].cpu().numpy(), Rs[b].cpu().numpy(), 0)
+
+
+def test_batched_mixed_instances_independent(env):
+    """An instance's (Q, R) are bit-identical whether it runs alone or packed with others, with either
+    first-pass precision mixed in one wave."""
+    torch, oqr, ctx = env
+    As, Zs, _ = inputs.batch_instances(9, seed=17, device="cuda", m_range=(64, 900), n_range=(1, 64),
+                                       log_kappa_a=(0.0, 2.0), log_kappa_z=(0.0, 1.0))
+    fp = [oqr.OQR_TC2 if b % 2 else oqr.OQR_FP64_TC for b in range(len(Zs))]
+    Qs, Rs, st = ctx.oqr_batched_mixed(As, Zs, first_prec=fp)
+    torch.cuda.synchronize()
+    assert st.abs().sum().item() == 0
+    for b in (0, 3, 4, 8):
+        Q1, R1, s1 = ctx.oqr_batched_mixed([As[b]], [Zs[b]], first_prec=[fp[b]])
+        torch.cuda.synchronize()
+        assert s1.item() == 0
+        assert torch.equal(Q1[0], Qs[b]) and torch.equal(R1[0], Rs[b])
+
+
+def test_batched_mixed_breakdown_is_isolated(env):
+    torch, oqr, ctx = env
+    As, Zs, _ = inputs.batch_instances(6, seed=5, device="cuda", m_range=(64, 300), n_range=(4, 40),
+                                       log_kappa_z=(0.0, 2.0))
+    bad = torch.eye(100, dtype=torch.float64, device="cuda")
+    bad[7, 7] = -1.0                             # indefinite: breaks at column 8 for Z = I[:, :10]
+    As.insert(2, oqr.colmajor(bad))
+    Zs.insert(2, oqr.colmajor(torch.eye(100, 10, dtype=torch.float64, device="cuda")))
+    Qs, Rs, st = ctx.oqr_batched(As, Zs, mode=1)
+    torch.cuda.synchronize()
+    st = st.cpu().numpy()
+    assert st[2] == 8
+    for b in range(len(Zs)):
+        if b != 2:
+            check_instance(As[b].cpu().numpy(), Zs[b].cpu().numpy(), Qs[b].cpu().numpy(), Rs[b].cpu().numpy(), st[b])
+
+
+def test_batched_mixed_graph_replay_same_result(env):
+    torch, oqr, ctx = env
+    As, Zs, _ = inputs.batch_instances(10, seed=13, device="cuda", m_range=(64, 400), n_range=(4, 64),
+                                       log_kappa_z=(0.0, 2.0))
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        _, R1, st1 = ctx.oqr_batched(As, Zs, mode=1, stream=s)
+        _, R2, st2 = ctx.oqr_batched(As, Zs, mode=1, stream=s)     # replays the cached graph
+    torch.cuda.synchronize()
+    assert st1.abs().sum().item() == 0 and torch.equal(st1, st2)
+    for a, b in zip(R1, R2):
+        assert torch.equal(a, b)
+
+
+def test_batched_mixed_rejects_bad_first_prec(env):
+    torch, oqr, ctx = env
+    As, Zs, _ = inputs.batch_instances(2, seed=1, device="cuda", m_range=(64, 128), n_range=(4, 8))
+    with pytest.raises(oqr.OqrError):
+        ctx.oqr_batched_mixed(As, Zs, first_prec=[oqr.OQR_FP64, oqr.OQR_TC2])
