@@ -208,6 +208,7 @@ __global__ void __launch_bounds__(128) trsm_batched_kernel(const BatchDesc* __re
                                                            int pass_in_place, int which)
 {
     __shared__ double Rs[64][65];
+    __shared__ double dinv[64];
     const int b = blockIdx.y;
     const BatchDesc D = d[b];
     if (status[b] != 0) return;
@@ -219,6 +220,7 @@ __global__ void __launch_bounds__(128) trsm_batched_kernel(const BatchDesc* __re
         const int i = e % n, j = e / n;
         Rs[i][j] = Rin[i + (size_t)j * n];
     }
+    if (threadIdx.x < n) dinv[threadIdx.x] = 1.0 / Rin[threadIdx.x + (size_t)threadIdx.x * n];
     __syncthreads();
     const long r = row0 + threadIdx.x;
     if (r >= m) return;
@@ -230,7 +232,7 @@ __global__ void __launch_bounds__(128) trsm_batched_kernel(const BatchDesc* __re
         if (j < n) {
             double t = X[r + (long)j * ldx];
             for (int k = 0; k < j; ++k) t -= q[k] * Rs[k][j];
-            q[j] = t / Rs[j][j];
+            q[j] = t * dinv[j];  // one division per column and CTA, not per element
         }
     }
 #pragma unroll

@@ -349,42 +349,28 @@ __global__ void __launch_bounds__(256) split_lower_kernel(int m, int K, const do
 }
 
 // One instance of a batched split: its matrix X (rows x K, column-major, ldx)
-// goes to packed rows (or columns) [off, off + rows or cols); its tiles or
-// columns start at first in the launch's flat enumeration.
+// goes to packed rows (or columns) [off, off + rows or cols), in kch chunks.
 struct SplitInst {
     const double* X;
     long ldx;
     int rows, K, cols;
     long off;
-    int first;
     int kch;
 };
+static_assert(BATCH_MAX_M <= 4096, "tile codes hold 4 chunk bits, 8 row-block bits; reduce codes 10 block bits");
 
-__device__ inline int last_le_split(const SplitInst* v, int n, int j)
-{
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (v[mid].first <= j) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
-
-// The triangular row split of a packed batch of A's: blockIdx.x enumerates every
-// instance's (chunk, 16-row block) tiles; upper-triangle tiles return at once.
-__global__ void __launch_bounds__(256) split_lower_batch_kernel(const SplitInst* __restrict__ inst, int ninst, int S,
+// The triangular row split of a packed batch of A's: block j takes the tile
+// tiles[j] = (instance << 12) | (chunk << 8) | 16-row block, listed for the
+// lower-triangle tiles only.
+__global__ void __launch_bounds__(256) split_lower_batch_kernel(const SplitInst* __restrict__ inst,
+                                                                const int* __restrict__ tiles, int S,
                                                                 __nv_bfloat16* planes, long ldp, size_t plane, int* eA,
                                                                 int* emax, long erows)
 {
-    const int j = blockIdx.x;
-    const int b = last_le_split(inst, ninst, j);
-    const SplitInst I = inst[b];
-    const int nrb = (I.rows + 15) / 16;
-    const int t = j - I.first;
-    if (t >= I.kch * nrb) return;
-    split_lower_tile<1, true, KCH_EMU>(I.rows, I.rows, I.X, I.ldx, S, planes, ldp, plane, eA, emax, t / nrb, t % nrb,
-                                       I.off, erows);
+    const int code = tiles[blockIdx.x];
+    const SplitInst I = inst[code >> 12];
+    split_lower_tile<1, true, KCH_EMU>(I.rows, I.rows, I.X, I.ldx, S, planes, ldp, plane, eA, emax, (code >> 8) & 15,
+                                       code & 255, I.off, erows);
 }
 
 // X (K x C, column-major) -> slices written column-major (column c, k
@@ -426,15 +412,15 @@ __global__ void __launch_bounds__(256) split_tall_kernel(int K, int C, const dou
 }
 
 // The column split of a packed batch: warp w of block y takes packed column
-// 8y + w, found in its instance by the column offsets (first = off there).
-__global__ void __launch_bounds__(256) split_tall_batch_kernel(const SplitInst* __restrict__ inst, int ninst, int S,
+// 8y + w, of instance colinst[8y + w].
+__global__ void __launch_bounds__(256) split_tall_batch_kernel(const SplitInst* __restrict__ inst,
+                                                               const int* __restrict__ colinst, int S,
                                                                __nv_bfloat16* planes, long ldp, size_t plane, int* eX,
                                                                int* xmax, long ecols)
 {
     const long gc = (long)blockIdx.y * 8 + (threadIdx.x >> 5);
     if (gc >= ecols) return;
-    const int b = last_le_split(inst, ninst, (int)gc);
-    const SplitInst I = inst[b];
+    const SplitInst I = inst[colinst[gc]];
     const int kc = blockIdx.x;
     if (kc >= I.kch) return;
     split_tall_column<1, KCH_EMU>(I.K, I.X, I.ldx, gc - I.off, S, planes, ldp, plane, eX, xmax, kc, I.off, ecols);
@@ -452,13 +438,12 @@ __global__ void fill_int_kernel(int* p, long n, int v)
 // [coff, coff + cols) of the packed right planes; K is its contraction length.
 // Its items are [item0, item0 + items); cum + cum0 holds its per-row-tile
 // item prefix (rt + 1 entries).  Its output (rows x cols, column-major, ldo)
-// starts at out; elements [e0, e0 + rows cols) of the batch's reduction.
+// starts at out.
 struct TcInst {
     int rows, cols, K, tri;
     int roff, coff;
     int rt, cc;
     int item0, cum0;
-    long e0;
     double* out;
     long ldo;
 };
@@ -482,7 +467,7 @@ struct TcArgs {
     int ninst;            // 0: one instance; > 0: a packed batch of ninst instances
     const TcInst* inst;   // [ninst]
     const int* inst_item0;  // [ninst + 1]: first item of each instance, then the total
-    long nout;            // a batch: total output elements
+    const int* rblk;      // a batch: the reduction's blocks (instance << 10 | block)
 };
 
 __device__ __host__ inline int kend_of(int K, int tri, int I)
@@ -960,25 +945,16 @@ __global__ void slot_reduce_f32_kernel(TcArgs a, double* out, long ldo, const De
 // A packed batch: every instance's output (rows x cols, column-major, ldo) is
 // the sum over the pieces of each tile of its slots, in piece order; F32: FP32
 // slots scaled by 2^(emax_row + emax_col) (TC2), else FP64 slots (EMU64).
-__device__ inline int last_le_e0(const TcInst* v, int n, long e)
-{
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (v[mid].e0 <= e) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
-
+// Block j reduces elements [256 b, 256 b + 256) of instance k, where
+// rblk[j] = (k << 10) | b.
 template <int N, bool F32>
 __global__ void slot_reduce_batch_kernel(TcArgs a)
 {
     if (*(volatile const int*)&a.st->code != 0) return;
-    const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= a.nout) return;
-    const TcInst I = a.inst[last_le_e0(a.inst, a.ninst, e)];
-    const long el = e - I.e0;
+    const int code = a.rblk[blockIdx.x];
+    const TcInst I = a.inst[code >> 10];
+    const long el = (long)(code & 1023) * 256 + threadIdx.x;
+    if (el >= (long)I.rows * I.cols) return;
     const int col = (int)(el / I.rows), row = (int)(el % I.rows);
     const int T = row / TM, c = col / N;
     const int np = pieces_of(I.K, I.tri, a.ks, a.piece, T);
@@ -1731,6 +1707,7 @@ cudaError_t launch_trsm_tc(int m, int n, const double* Z, long ldz, const double
 }
 
 // ------------------------------------------------------ packed batches ----
+constexpr int BATCH_ITEMS_TARGET = 4 * 152;  // items of an n x n product: a few per SM
 // Waves of instances (see oqr_internal.cuh): per wave the A planes hold the
 // instances' rows one after another (instance b at packed row r_b) and the Z
 // and U planes their columns (instance b at packed column c_b).  A work item
@@ -1769,10 +1746,11 @@ WaveLayout wave_layout(const TcBatchWave& w, void* ws)
     return L;
 }
 int batch_ks(int mode) { return mode == 1 ? EMU_KS : 64; }
-// Items of one instance's product: U = M Z (tri, rows m) or C = Z^T U (rows n).
-int batch_items(int rows, int cols, int K, int tri, int mode)
+// Items of one instance's product: U = M Z (tri, rows m) or C = Z^T U (rows n),
+// in pieces of piece_k along k (a multiple of the 256-long exponent chunk).
+int batch_items(int rows, int cols, int K, int tri, int mode, int piece_k)
 {
-    const int ks = batch_ks(mode), piece = 2048 / ks;
+    const int ks = batch_ks(mode), piece = piece_k / ks;
     const int rt = (rows + TM - 1) / TM, cc = (cols + EMU_N - 1) / EMU_N;
     int s = 0;
     for (int I = 0; I < rt; ++I) s += pieces_of(K, tri, ks, piece, I) * cc;
@@ -1825,9 +1803,12 @@ TcBatchPlan tc_batch_plan(const std::vector<TcBatchShape>& sh, size_t budget)
         w.tilesA = 0;
         w.upool = 0;
         for (int i = b; i < e; ++i) {
-            w.tilesA += ((sh[i].m + KCH_EMU - 1) / KCH_EMU) * ((sh[i].m + 15) / 16);
+            const int nrb = (sh[i].m + 15) / 16;
+            for (int kc = 0; kc * KCH_EMU < sh[i].m; ++kc) w.tilesA += nrb - 16 * kc;  // lower-triangle tiles
             w.upool += (long)sh[i].m * sh[i].n;
         }
+        w.tileTab = tk((size_t)w.tilesA * 4);
+        w.colTab = tk((size_t)w.cols * 4);
         w.max_items = 1;
         for (int pass = 0; pass < 2; ++pass) {
             w.nl[pass] = 0;
@@ -1841,18 +1822,28 @@ TcBatchPlan tc_batch_plan(const std::vector<TcBatchShape>& sh, size_t budget)
                     TcBatchLaunch& L = prod == 0 ? w.u[pass][li] : w.c[pass][li];
                     L.mode = modes[k];
                     L.ninst = (int)mem.size();
-                    L.nitems = 0;
-                    L.nout = 0;
+                    // the n x n products have few tiles: shorter pieces until every SM has a few items
+                    L.piece_k = 2048;
+                    for (;;) {
+                        L.nitems = 0;
+                        for (int i : mem) {
+                            const int rows_i = prod == 0 ? sh[i].m : sh[i].n;
+                            L.nitems += batch_items(rows_i, sh[i].n, sh[i].m, prod == 0, L.mode, L.piece_k);
+                        }
+                        if (prod == 0 || L.piece_k == KCH_EMU || L.nitems >= BATCH_ITEMS_TARGET) break;
+                        L.piece_k /= 2;
+                    }
+                    L.nrblk = 0;
                     long ncum = 0;
                     for (int i : mem) {
                         const int rows_i = prod == 0 ? sh[i].m : sh[i].n;
-                        L.nitems += batch_items(rows_i, sh[i].n, sh[i].m, prod == 0, L.mode);
-                        L.nout += (long)rows_i * sh[i].n;
+                        L.nrblk += (int)(((long)rows_i * sh[i].n + 255) / 256);
                         ncum += (rows_i + TM - 1) / TM + 1;
                     }
                     L.inst = tk((size_t)L.ninst * sizeof(TcInst));
                     L.item0 = tk((size_t)(L.ninst + 1) * 4);
                     L.cum = tk((size_t)ncum * 4);
+                    L.rblk = tk((size_t)L.nrblk * 4);
                     if (L.nitems > w.max_items) w.max_items = L.nitems;
                 }
             }
@@ -1888,14 +1879,19 @@ void tc_batch_tables(const TcBatchPlan& p, const std::vector<TcBatchShape>& sh, 
         SplitInst* sz = reinterpret_cast<SplitInst*>(img + w.splitZ);
         SplitInst* sq = reinterpret_cast<SplitInst*>(img + w.splitQ);
         SplitInst* su = reinterpret_cast<SplitInst*>(img + w.splitU);
-        int tiles = 0;
+        int* tiles = reinterpret_cast<int*>(img + w.tileTab);
+        int* colinst = reinterpret_cast<int*>(img + w.colTab);
+        int nt = 0;
         for (int i = 0; i < w.count; ++i) {
             const int b = w.first + i, m = sh[b].m, n = sh[b].n, kch = (m + KCH_EMU - 1) / KCH_EMU;
-            sa[i] = SplitInst{in[b].A, in[b].lda, m, m, 0, roff[i], tiles, kch};
-            tiles += kch * ((m + 15) / 16);
-            sz[i] = SplitInst{in[b].Z, in[b].ldz, 0, m, n, coff[i], (int)coff[i], kch};
-            sq[i] = SplitInst{in[b].Q, in[b].ldq, 0, m, n, coff[i], (int)coff[i], kch};
-            su[i] = SplitInst{upool + uoff[i], (long)m, 0, m, n, coff[i], (int)coff[i], kch};
+            sa[i] = SplitInst{in[b].A, in[b].lda, m, m, 0, roff[i], kch};
+            sz[i] = SplitInst{in[b].Z, in[b].ldz, 0, m, n, coff[i], kch};
+            sq[i] = SplitInst{in[b].Q, in[b].ldq, 0, m, n, coff[i], kch};
+            su[i] = SplitInst{upool + uoff[i], (long)m, 0, m, n, coff[i], kch};
+            const int nrb = (m + 15) / 16;
+            for (int kc = 0; kc < kch; ++kc)
+                for (int ib = 16 * kc; ib < nrb; ++ib) tiles[nt++] = (i << 12) | (kc << 8) | ib;
+            for (int c = 0; c < n; ++c) colinst[coff[i] + c] = i;
         }
         for (int pass = 0; pass < 2; ++pass)
             for (int li = 0; li < w.nl[pass]; ++li)
@@ -1905,9 +1901,9 @@ void tc_batch_tables(const TcBatchPlan& p, const std::vector<TcBatchShape>& sh, 
                     TcInst* ti = reinterpret_cast<TcInst*>(img + L.inst);
                     int* item0 = reinterpret_cast<int*>(img + L.item0);
                     int* cum = reinterpret_cast<int*>(img + L.cum);
-                    const int ks = batch_ks(L.mode), piece = 2048 / ks;
-                    int it = 0, cm = 0;
-                    long e0 = 0;
+                    int* rblk = reinterpret_cast<int*>(img + L.rblk);
+                    const int ks = batch_ks(L.mode), piece = L.piece_k / ks;
+                    int it = 0, cm = 0, nb = 0;
                     for (size_t k = 0; k < mem.size(); ++k) {
                         const int b = mem[k], i = b - w.first, m = sh[b].m, n = sh[b].n;
                         TcInst t{};
@@ -1921,7 +1917,6 @@ void tc_batch_tables(const TcBatchPlan& p, const std::vector<TcBatchShape>& sh, 
                         t.cc = (t.cols + EMU_N - 1) / EMU_N;
                         t.item0 = it;
                         t.cum0 = cm;
-                        t.e0 = e0;
                         t.out = prod == 0 ? upool + uoff[i] : in[b].C;
                         t.ldo = t.rows;
                         int s = 0;
@@ -1934,7 +1929,8 @@ void tc_batch_tables(const TcBatchPlan& p, const std::vector<TcBatchShape>& sh, 
                         item0[k] = it;
                         it += s;
                         cm += t.rt + 1;
-                        e0 += (long)t.rows * t.cols;
+                        const int blocks = (int)(((long)t.rows * t.cols + 255) / 256);
+                        for (int q = 0; q < blocks; ++q) rblk[nb++] = ((int)k << 10) | q;
                     }
                     item0[mem.size()] = it;
                 }
@@ -1947,8 +1943,9 @@ cudaError_t tc_batch_split_a(const TcBatchPlan& p, int w, const void* table_dev,
     const WaveLayout L = wave_layout(W, scratch);
     const char* tab = static_cast<const char*>(table_dev);
     fill_int_kernel<<<(unsigned)((W.rows + 255) / 256), 256, 0, s>>>(L.mA, W.rows, EXP_NONE);
-    split_lower_batch_kernel<<<W.tilesA, 256, 0, s>>>(reinterpret_cast<const SplitInst*>(tab + W.splitA), W.count,
-                                                      EMU_S, L.Ap, W.ldp, (size_t)W.rows * W.ldp, L.eA, L.mA, W.rows);
+    split_lower_batch_kernel<<<W.tilesA, 256, 0, s>>>(reinterpret_cast<const SplitInst*>(tab + W.splitA),
+                                                      reinterpret_cast<const int*>(tab + W.tileTab), EMU_S, L.Ap,
+                                                      W.ldp, (size_t)W.rows * W.ldp, L.eA, L.mA, W.rows);
     return cudaGetLastError();
 }
 
@@ -1967,7 +1964,7 @@ cudaError_t tc_batch_gram(const TcBatchPlan& p, int w, int pass, const void* tab
         a.colsB = (int)W.cols;
         a.K = W.K;
         a.ks = batch_ks(B.mode);
-        a.piece = 2048 / a.ks;
+        a.piece = B.piece_k / a.ks;
         a.nitems = B.nitems;
         a.cum = reinterpret_cast<const int*>(tab + B.cum);
         a.slots = L.slots;
@@ -1980,7 +1977,7 @@ cudaError_t tc_batch_gram(const TcBatchPlan& p, int w, int pass, const void* tab
         a.ninst = B.ninst;
         a.inst = reinterpret_cast<const TcInst*>(tab + B.inst);
         a.inst_item0 = reinterpret_cast<const int*>(tab + B.item0);
-        a.nout = B.nout;
+        a.rblk = reinterpret_cast<const int*>(tab + B.rblk);
         return a;
     };
     auto product = [&](const TcBatchLaunch& B, const TcArgs& a, const void* PA, size_t plA, const void* PB) {
@@ -1988,7 +1985,7 @@ cudaError_t tc_batch_gram(const TcBatchPlan& p, int w, int pass, const void* tab
         if (B.mode == 1) e = launch_emu(a, PA, W.ldp, plA, PB, W.ldp, planeZ, sms, s);
         else e = launch_tc<64, 64, 2, 3>(a, PA, W.ldp, plA, PB, W.ldp, planeZ, sms, s);
         if (e != cudaSuccess) return e;
-        const unsigned g = (unsigned)((B.nout + 255) / 256);
+        const unsigned g = (unsigned)B.nrblk;
         if (B.mode == 1) slot_reduce_batch_kernel<EMU_N, false><<<g, 256, 0, s>>>(a);
         else slot_reduce_batch_kernel<EMU_N, true><<<g, 256, 0, s>>>(a);
         return cudaGetLastError();
@@ -1996,15 +1993,16 @@ cudaError_t tc_batch_gram(const TcBatchPlan& p, int w, int pass, const void* tab
     cudaError_t e;
     // the split of X (Z in pass 0, Q in pass 1), then U = M X for every launch of the pass
     fill_int_kernel<<<(unsigned)((W.cols + 255) / 256), 256, 0, s>>>(L.mZ, W.cols, EXP_NONE);
+    const int* colinst = reinterpret_cast<const int*>(tab + W.colTab);
     split_tall_batch_kernel<<<gt, 256, 0, s>>>(reinterpret_cast<const SplitInst*>(tab + (pass ? W.splitQ : W.splitZ)),
-                                               W.count, EMU_S, L.Zp, W.ldp, planeZ, L.eZ, L.mZ, W.cols);
+                                               colinst, EMU_S, L.Zp, W.ldp, planeZ, L.eZ, L.mZ, W.cols);
     for (int li = 0; li < W.nl[pass]; ++li) {
         const TcBatchLaunch& B = W.u[pass][li];
         if ((e = product(B, args(B, W.rows, L.eA, L.eZ, L.mA, L.mZ), L.Ap, planeA, L.Zp)) != cudaSuccess) return e;
     }
     // the split of U, then C = X^T U
     fill_int_kernel<<<(unsigned)((W.cols + 255) / 256), 256, 0, s>>>(L.mU, W.cols, EXP_NONE);
-    split_tall_batch_kernel<<<gt, 256, 0, s>>>(reinterpret_cast<const SplitInst*>(tab + W.splitU), W.count, EMU_S,
+    split_tall_batch_kernel<<<gt, 256, 0, s>>>(reinterpret_cast<const SplitInst*>(tab + W.splitU), colinst, EMU_S,
                                                L.Up, W.ldp, planeZ, L.eU, L.mU, W.cols);
     for (int li = 0; li < W.nl[pass]; ++li) {
         const TcBatchLaunch& B = W.c[pass][li];

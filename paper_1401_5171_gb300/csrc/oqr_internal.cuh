@@ -261,14 +261,16 @@ struct TcBatchIn {
 struct TcBatchLaunch {
     int mode;              // 1 EMU64, 3 TC2
     int ninst, nitems;
-    long nout;
-    size_t inst, item0, cum;  // byte offsets of the launch's tables
+    int piece_k;           // k per work item
+    int nrblk;             // blocks of the reduction
+    size_t inst, item0, cum, rblk;  // byte offsets of the launch's tables
 };
 struct TcBatchWave {
     int first, count;     // instances [first, first + count) of the sorted order
     long rows, cols, ldp;  // packed rows (sum of m), packed columns (sum of n), plane row pitch
     int K, kch, tilesA, max_items;
     size_t splitA, splitZ, splitQ, splitU;  // SplitInst tables (byte offsets)
+    size_t tileTab, colTab;                 // the A split's tiles, the packed columns' instances
     TcBatchLaunch u[2][2], c[2][2];         // [pass][launch]: pass 0 one launch per mode present
     int nl[2];
     long upool;  // U pool doubles
