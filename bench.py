@@ -51,6 +51,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--batch-count", type=int, default=512,
                    help="side measurement: a batch of this many instances of the batched workload (0: none)")
+    p.add_argument("--batch-profile", type=int, default=None, choices=[0, 1, 2, 3],
+                   help="only: one oqr_batched call of this mode on the batch sample, inside a profiler range "
+                        "(for ncu --profile-from-start off)")
     return p.parse_args()
 
 
@@ -284,7 +287,8 @@ def config_of(args):
 
 
 def run_batch(ctx, torch, dev, count, stream, steps=2):
-    """QRs/s of oqr_batched over one batch (FP64; tensor cores with every pass FP64-accurate; TC2 first pass),
+    """QRs/s of oqr_batched over one batch (FP64 A-CholQR2; on the tensor cores: A-CholQR2 with every pass
+    FP64-accurate, with a TC2 first pass, and shifted A-CholQR3),
     with the number of instances that completed and their largest ||Q^T A Q - I||_2 (checked outside the
     timing)."""
     from paper_1401_5171_gb300 import inputs
@@ -292,7 +296,7 @@ def run_batch(ctx, torch, dev, count, stream, steps=2):
     sigma_a = sum(int(m) ** 2 for m in tab["m"]) * 8
     out = {"instances": count, "sum_A_bytes": sigma_a,
            "recipe": "m ~ U[64, 4096], n ~ U[4, 64], kappa(A), kappa(Z) log-uniform in [1, 1e6], seed 4242"}
-    for label, mode in (("fp64", 0), ("fp64tc", 1), ("tc2_first", 2)):
+    for label, mode in (("fp64", 0), ("fp64tc", 1), ("tc2_first", 2), ("shifted3_fp64tc", 3)):
         Qs, Rs, st = ctx.oqr_batched(As, Zs, mode=mode, stream=stream)     # captures the graph
         torch.cuda.synchronize()
         stc = st.cpu().tolist()
@@ -317,6 +321,26 @@ def run_batch(ctx, torch, dev, count, stream, steps=2):
     return out
 
 
+def profile_batch(ctx, torch, dev, count, mode):
+    """One oqr_batched call (after a warm-up call that captures its graph) inside cudaProfilerStart/Stop."""
+    from paper_1401_5171_gb300 import inputs
+    As, Zs, _ = inputs.batch_instances(count, seed=4242, device=dev)
+    s = torch.cuda.current_stream(dev)
+    Qs, Rs, st = ctx.oqr_batched(As, Zs, mode=mode, stream=s)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    ctx.oqr_batched(As, Zs, Qs=Qs, Rs=Rs, mode=mode, stream=s, status=st)
+    e1.record(s)
+    torch.cuda.synchronize()
+    print(json.dumps({"batch_mode": mode, "instances": count, "ms": e0.elapsed_time(e1),
+                      "completed": int((st == 0).sum().item())}), flush=True)
+    torch.cuda.profiler.start()
+    ctx.oqr_batched(As, Zs, Qs=Qs, Rs=Rs, mode=mode, stream=s, status=st)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -335,6 +359,9 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
+    if args.batch_profile is not None:
+        profile_batch(oqr.Oqr(local), torch, dev, args.batch_count, args.batch_profile)
+        return
     m, n = args.m, args.n
     # inputs resident in HBM before the timed region
     Af, _ = inputs.dense_spd(m, args.kappa_a, seed=1000 + rank, device=dev)

@@ -231,8 +231,9 @@ oqr_status oqr_check(oqr_ctx* ctx, int m, int n, const double* A, long lda, cons
  * are unaffected).  splits (host, may be NULL) is the work plan: the number of
  * k-ranges each instance's Gram is cut into (1..64), as chosen by an autotuner;
  * NULL uses the built-in heuristic.  mode: 0 FP64 A-CholQR2 (FP64 FMA Gram);
- * 1 and 2 the tensor-core form of oqr_batched_mixed with every first pass
- * OQR_FP64_TC (mode 1) or OQR_TC2 (mode 2); splits is then ignored.
+ * 1, 2, 3 the tensor-core form (oqr_batched_mixed) with every instance's
+ * program OQR_BATCH_CHOLQR2_TC (1), OQR_BATCH_CHOLQR2_TC2 (2) or
+ * OQR_BATCH_SCHOLQR3_TC (3); splits is then ignored.
  * The batch-wide kernel sequence (about 13 launches) is captured into one
  * CUDA graph that the context caches and replays while the batch's shape
  * signature is unchanged; on the legacy default stream it is launched directly.
@@ -242,26 +243,39 @@ oqr_status oqr_batched(oqr_ctx* ctx, int count, const int* m, const int* n, cons
                        const double* const* Z, const long* ldz, double* const* Q, const long* ldq, double* const* R,
                        const long* ldr, int mode, const int* splits, int* status, void* stream);
 
+/* Per-instance programs of the batched tensor-core path. */
+typedef enum {
+    OQR_BATCH_CHOLQR_TC = 0,    /* Algorithm 1 once (CHOLQR), FP64_TC Gram */
+    OQR_BATCH_CHOLQR2_TC2 = 1,  /* A-CholQR2: TC2 pass, then FP64_TC pass */
+    OQR_BATCH_CHOLQR2_TC = 2,   /* A-CholQR2: two FP64_TC passes */
+    OQR_BATCH_SCHOLQR3_TC = 3   /* shifted A-CholQR3: FP64_TC pass on G + sI, then two FP64_TC passes;
+                                   s = 11 u (m n + n (n + 1)) ||A||_F ||Z||_F^2, u = 2^-53 */
+} oqr_batch_program;
+
 /*
- * Batched A-CholQR2 on the tensor cores: the same instances, arguments and
- * status words as oqr_batched, with each instance's Gram G = Z^T A Z
- * (Algorithm 1, line 1; Sec. 2) formed on the BF16 tensor cores:
- * first_prec[b] (host array; NULL = all OQR_FP64_TC) is OQR_TC2 or
- * OQR_FP64_TC for instance b's first pass, and the second pass is OQR_FP64_TC
- * for every instance.  The Cholesky factors, Q = Z R^{-1} and R = R_2 R_1 are
- * FP64.  An instance's results do not depend on the other instances of the
- * batch.  Instances run in waves (largest m first) whose BF16 slice planes
- * (14 bytes per element of A, Z and Z^T A) fit 16 GiB of workspace; A is
- * split once per wave and read by both passes.  status[b] = -1 for every
- * instance when a tensor-core wait timed out (the context's status then
- * reports OQR_ERR_TIMEOUT).  The sequence is captured into one CUDA graph,
- * cached while every instance's (m, n, first_prec) is unchanged.
- * Asynchronous: returns after enqueueing (argument errors are returned).
+ * Batched oblique QR on the tensor cores: the same instances, arguments and
+ * status words as oqr_batched, each instance running its own program
+ * (program[b], host array; NULL = all OQR_BATCH_CHOLQR2_TC): Algorithm 1
+ * repeated 1 to 3 times (Sec. 2), every Gram G = Z^T A Z formed on the BF16
+ * tensor cores (OQR_TC2 or OQR_FP64_TC), and the Cholesky factors,
+ * Q = Z R^{-1} and R = R_p ... R_1 in FP64.  An instance's results do not
+ * depend on the other instances of the batch.  Instances run in waves
+ * (largest m first) whose BF16 slice planes (14 bytes per element of A, Z
+ * and Z^T A) fit 16 GiB of workspace; A is split once per wave and read by
+ * every pass.  orth (device, count doubles, may be NULL): when given, each
+ * instance's result is checked, orth[b] = an estimate of ||Q_b^T A_b Q_b - I||_2
+ * (Sec. 7's orthogonality measure; power iteration, a lower bound) from one
+ * more FP64_TC Gram of the final Q, or +inf after a breakdown.
+ * status[b] = -1 for every instance when a tensor-core wait
+ * timed out (the context's status then reports OQR_ERR_TIMEOUT).  The
+ * sequence is captured into one CUDA graph, cached while every instance's
+ * (m, n, program) and the use of orth are unchanged.  Asynchronous: returns after enqueueing
+ * (argument errors, including a program outside the enum, are returned).
  */
 oqr_status oqr_batched_mixed(oqr_ctx* ctx, int count, const int* m, const int* n, const double* const* A,
                              const long* lda, const double* const* Z, const long* ldz, double* const* Q,
-                             const long* ldq, double* const* R, const long* ldr, const int* first_prec, int* status,
-                             void* stream);
+                             const long* ldq, double* const* R, const long* ldr, const int* program, int* status,
+                             double* orth, void* stream);
 
 /* The built-in work plan of oqr_batched for one instance (splits of its Gram). */
 int oqr_batched_default_splits(int m, int n);

@@ -138,11 +138,12 @@ __global__ void __launch_bounds__(BTHREADS) gram_batched_kernel(const BatchDesc*
         for (int e = tid; e < n * n; e += BTHREADS) P[e] = 0.0;
 }
 
-__global__ void reduce_batched_kernel(const BatchDesc* __restrict__ d, const int* status, double* shift_or_null)
+__global__ void reduce_batched_kernel(const BatchDesc* __restrict__ d, const int* status, const double* shifts,
+                                      int pass)
 {
     const int b = blockIdx.y;
     const BatchDesc D = d[b];
-    if (status[b] != 0) return;
+    if (status[b] != 0 || pass >= D.npass) return;
     const int n = D.n;
     const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (long)n * n) return;
@@ -153,18 +154,20 @@ __global__ void reduce_batched_kernel(const BatchDesc* __restrict__ d, const int
         const double* P = D.partials + p * nn;
         s += P[(size_t)r * n + c] + P[(size_t)c * n + r];
     }
+    if (shifts && r == c) s += shifts[b];  // G + s I (the shifted first pass)
     D.G[r + (size_t)c * n] = s;
 }
 
 // One CTA per instance: R = chol(G), G n x n (n <= 64) in shared memory,
 // right-looking, column by column.  Writes R (upper, zeros below) into Rout.
-__global__ void __launch_bounds__(256) potrf_batched_kernel(const BatchDesc* __restrict__ d, int* status, int which)
+__global__ void __launch_bounds__(256) potrf_batched_kernel(const BatchDesc* __restrict__ d, int* status, int which,
+                                                            int pass)
 {
     __shared__ double S[64][65];
     __shared__ int broke;
     const int b = blockIdx.x;
     const BatchDesc D = d[b];
-    if (status[b] != 0) return;
+    if (status[b] != 0 || pass >= D.npass) return;
     const int n = D.n;
     double* Rout = which == 0 ? D.R1 : D.R2;
     const int tid = threadIdx.x;
@@ -205,13 +208,13 @@ __global__ void __launch_bounds__(256) potrf_batched_kernel(const BatchDesc* __r
 
 // Q = X / R row by row, 128 rows per CTA, R (<= 64 x 64) in shared memory.
 __global__ void __launch_bounds__(128) trsm_batched_kernel(const BatchDesc* __restrict__ d, const int* status,
-                                                           int pass_in_place, int which)
+                                                           int pass_in_place, int which, int pass)
 {
     __shared__ double Rs[64][65];
     __shared__ double dinv[64];
     const int b = blockIdx.y;
     const BatchDesc D = d[b];
-    if (status[b] != 0) return;
+    if (status[b] != 0 || pass >= D.npass) return;
     const int m = D.m, n = D.n;
     const long row0 = (long)blockIdx.x * 128;
     if (row0 >= m) return;  // the grid covers the largest m of the batch
@@ -256,6 +259,161 @@ __global__ void rprod_batched_kernel(const BatchDesc* __restrict__ d, const int*
     D.R[i + (long)j * D.ldr] = s;
 }
 
+// R1 <- R2 R1 (upper x upper) after a later pass: one CTA per instance, the
+// product held in shared memory until every thread has read R1.
+__global__ void __launch_bounds__(256) racc_batched_kernel(const BatchDesc* __restrict__ d, const int* status,
+                                                           int pass)
+{
+    __shared__ double T[64][65];
+    const int b = blockIdx.x;
+    const BatchDesc D = d[b];
+    if (status[b] != 0 || pass >= D.npass) return;
+    const int n = D.n;
+    for (int e = threadIdx.x; e < n * n; e += 256) {
+        const int i = e % n, j = e / n;
+        double s = 0.0;
+        for (int k = i; k <= j; ++k) s += D.R2[i + (size_t)k * n] * D.R1[k + (size_t)j * n];
+        T[i][j] = s;  // 0 below the diagonal
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * n; e += 256) {
+        const int i = e % n, j = e / n;
+        D.R1[i + (size_t)j * n] = T[i][j];
+    }
+}
+
+// The caller's R = R1 (upper, zeros below the diagonal).
+__global__ void rfinal_batched_kernel(const BatchDesc* __restrict__ d, const int* status)
+{
+    const int b = blockIdx.y;
+    const BatchDesc D = d[b];
+    if (status[b] != 0) return;
+    const int n = D.n;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * n) return;
+    const int i = e % n, j = e / n;
+    D.R[i + (long)j * D.ldr] = i <= j ? D.R1[i + (size_t)j * n] : 0.0;
+}
+
+// ||A||_F^2 (from A's lower triangle) and ||Z||_F^2 of the instances with a
+// shifted first pass, summed into sums[2b], sums[2b + 1] by gridDim.x blocks
+// per instance (columns j = x, x + gridDim.x, ...).
+constexpr int NORM_BLOCKS = 64;
+__global__ void __launch_bounds__(256) norms_batched_kernel(const BatchDesc* __restrict__ d,
+                                                            const int* __restrict__ shifted, double* sums)
+{
+    __shared__ double red[2][8];
+    const int b = blockIdx.y;
+    if (!shifted[b]) return;
+    const BatchDesc D = d[b];
+    const int m = D.m, n = D.n;
+    double sa = 0.0, sz = 0.0;
+    for (int j = blockIdx.x; j < m; j += gridDim.x) {
+        for (int i = j + threadIdx.x; i < m; i += 256) {
+            const double v = D.A[i + (long)j * D.lda];
+            sa += (i == j ? 1.0 : 2.0) * v * v;
+        }
+        if (j < n)
+            for (int i = threadIdx.x; i < m; i += 256) {
+                const double v = D.Z[i + (long)j * D.ldz];
+                sz += v * v;
+            }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        sa += __shfl_xor_sync(0xffffffffu, sa, o);
+        sz += __shfl_xor_sync(0xffffffffu, sz, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = sa;
+        red[1][threadIdx.x >> 5] = sz;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double ta = 0.0, tz = 0.0;
+        for (int w = 0; w < 8; ++w) {
+            ta += red[0][w];
+            tz += red[1][w];
+        }
+        atomicAdd(&sums[2 * b], ta);
+        atomicAdd(&sums[2 * b + 1], tz);
+    }
+}
+
+// s_b = c u (m n + n (n + 1)) ||A||_F ||Z||_F^2 for a shifted instance, else 0.
+__global__ void shift_batched_kernel(const BatchDesc* __restrict__ d, int count, const int* __restrict__ shifted,
+                                     const double* sums, double c, double u, double* shifts)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= count) return;
+    const BatchDesc D = d[b];
+    shifts[b] = shifted[b] ? c * u * ((double)D.m * D.n + (double)D.n * (D.n + 1)) * sqrt(sums[2 * b]) * sums[2 * b + 1]
+                           : 0.0;
+}
+
+// ||E||_2 estimate of E = G - I for the instances checked at this pass (one CTA each).
+constexpr int BCHECK_ITERS = 40;
+__global__ void __launch_bounds__(256) check_batched_kernel(const BatchDesc* __restrict__ d, const int* status,
+                                                            int pass, double* orth)
+{
+    __shared__ double E[64][65];
+    __shared__ double x[64], y[64];
+    __shared__ double red[8];
+    const int b = blockIdx.x;
+    const BatchDesc D = d[b];
+    if (D.npass != pass) return;
+    if (status[b] != 0) {
+        if (threadIdx.x == 0) orth[b] = INFINITY;
+        return;
+    }
+    const int n = D.n;
+    const double* P = D.partials;
+    for (int e = threadIdx.x; e < n * n; e += 256) {
+        const int i = e % n, j = e / n;
+        E[i][j] = P[(size_t)i * n + j] + P[(size_t)j * n + i] - (i == j ? 1.0 : 0.0);
+    }
+    if (threadIdx.x < n) x[threadIdx.x] = 1.0 + 0.01 * threadIdx.x;  // not orthogonal to a dominant vector
+    __syncthreads();
+    double best = 0.0;
+    for (int it = 0; it < BCHECK_ITERS; ++it) {
+        // y = E x (one warp per 8 rows), then ||y|| / ||x|| and x = y / ||y||
+        const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        for (int i = w; i < n; i += 8) {
+            double t = 0.0;
+            for (int k = lane; k < n; k += 32) t += E[i][k] * x[k];
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            if (lane == 0) y[i] = t;
+        }
+        __syncthreads();
+        if (w == 0) {
+            double ny = 0.0, nx = 0.0;
+            for (int k = lane; k < n; k += 32) {
+                ny += y[k] * y[k];
+                nx += x[k] * x[k];
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                ny += __shfl_xor_sync(0xffffffffu, ny, o);
+                nx += __shfl_xor_sync(0xffffffffu, nx, o);
+            }
+            if (lane == 0) {
+                red[0] = sqrt(ny / nx);
+                red[1] = ny > 0.0 ? 1.0 / sqrt(ny) : 0.0;
+            }
+        }
+        __syncthreads();
+        best = fmax(best, red[0]);
+        if (red[1] == 0.0) break;  // E x = 0
+        if (threadIdx.x < n) x[threadIdx.x] = y[threadIdx.x] * red[1];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) orth[b] = best;
+}
+
+__global__ void scatter_f64_kernel(const double* in, const int* perm, int count, double* out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) out[perm[i]] = in[i];
+}
+
 // status[perm[i]] = st_sorted[i]; -1 for all when a kernel of the context timed out.
 __global__ void status_scatter_kernel(const int* st_sorted, const int* perm, int count, const DevStatus* st,
                                       int* status)
@@ -280,30 +438,43 @@ cudaError_t launch_batched_cholqr2(const BatchDesc* d, int count, const int* con
             else gram_batched_kernel<64><<<g, BTHREADS, 0, s>>>(d, cls_idx[c], status, pass);
         }
         dim3 gr((max_n * max_n + 255) / 256, count);
-        reduce_batched_kernel<<<gr, 256, 0, s>>>(d, status, nullptr);
-        potrf_batched_kernel<<<count, 256, 0, s>>>(d, status, pass);
+        reduce_batched_kernel<<<gr, 256, 0, s>>>(d, status, nullptr, pass);
+        potrf_batched_kernel<<<count, 256, 0, s>>>(d, status, pass, pass);
         dim3 gt(BATCH_MAX_M / 128, count);
-        trsm_batched_kernel<<<gt, 128, 0, s>>>(d, status, pass, pass);
+        trsm_batched_kernel<<<gt, 128, 0, s>>>(d, status, pass, pass, pass);
     }
     dim3 gp((64 * 64 + 255) / 256, count);
     rprod_batched_kernel<<<gp, 256, 0, s>>>(d, status);
     return cudaGetLastError();
 }
 
-cudaError_t launch_batched_factor(const BatchDesc* d, int count, int* status, int pass, cudaStream_t s)
+cudaError_t launch_batched_factor(const BatchDesc* d, int count, int* status, int pass, const double* shifts,
+                                  cudaStream_t s)
 {
+    const int which = pass == 0 ? 0 : 1;
     dim3 gr((BATCH_MAX_N * BATCH_MAX_N + 255) / 256, count);
-    reduce_batched_kernel<<<gr, 256, 0, s>>>(d, status, nullptr);
-    potrf_batched_kernel<<<count, 256, 0, s>>>(d, status, pass);
+    reduce_batched_kernel<<<gr, 256, 0, s>>>(d, status, pass == 0 ? shifts : nullptr, pass);
+    potrf_batched_kernel<<<count, 256, 0, s>>>(d, status, which, pass);
     dim3 gt(BATCH_MAX_M / 128, count);
-    trsm_batched_kernel<<<gt, 128, 0, s>>>(d, status, pass, pass);
+    trsm_batched_kernel<<<gt, 128, 0, s>>>(d, status, pass > 0, which, pass);
+    if (pass > 0) racc_batched_kernel<<<count, 256, 0, s>>>(d, status, pass);
     return cudaGetLastError();
 }
 
-cudaError_t launch_batched_rprod(const BatchDesc* d, int count, int* status, cudaStream_t s)
+cudaError_t launch_batched_rfinal(const BatchDesc* d, int count, int* status, cudaStream_t s)
 {
     dim3 gp((BATCH_MAX_N * BATCH_MAX_N + 255) / 256, count);
-    rprod_batched_kernel<<<gp, 256, 0, s>>>(d, status);
+    rfinal_batched_kernel<<<gp, 256, 0, s>>>(d, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batched_shifts(const BatchDesc* d, int count, const int* shifted, double* sums, double c,
+                                  double u, double* shifts, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(sums, 0, sizeof(double) * 2 * count, s);
+    if (e != cudaSuccess) return e;
+    norms_batched_kernel<<<dim3(NORM_BLOCKS, count), 256, 0, s>>>(d, shifted, sums);
+    shift_batched_kernel<<<(count + 255) / 256, 256, 0, s>>>(d, count, shifted, sums, c, u, shifts);
     return cudaGetLastError();
 }
 
@@ -311,6 +482,19 @@ cudaError_t launch_batch_status_scatter(const int* st_sorted, const int* perm, i
                                         int* status, cudaStream_t s)
 {
     status_scatter_kernel<<<(count + 255) / 256, 256, 0, s>>>(st_sorted, perm, count, st, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batched_check(const BatchDesc* d, int count, const int* status, int pass, double* orth,
+                                 cudaStream_t s)
+{
+    check_batched_kernel<<<count, 256, 0, s>>>(d, status, pass, orth);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_scatter_f64(const double* in, const int* perm, int count, double* out, cudaStream_t s)
+{
+    scatter_f64_kernel<<<(count + 255) / 256, 256, 0, s>>>(in, perm, count, out);
     return cudaGetLastError();
 }
 

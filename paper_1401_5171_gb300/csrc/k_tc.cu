@@ -1756,13 +1756,13 @@ int batch_items(int rows, int cols, int K, int tri, int mode, int piece_k)
     for (int I = 0; I < rt; ++I) s += pieces_of(K, tri, ks, piece, I) * cc;
     return s;
 }
-// Members of launch li of a pass: pass 0 has one launch per first-pass mode present (TC2, then
-// EMU64); pass 1 runs every instance of the wave in EMU64.
+// Members of a launch of pass p: the instances with more than p passes; pass 0 has one launch per
+// first-pass mode present (TC2, then EMU64), later passes one EMU64 launch.
 std::vector<int> launch_members(const std::vector<TcBatchShape>& sh, const TcBatchWave& w, int pass, int mode)
 {
     std::vector<int> v;
     for (int b = w.first; b < w.first + w.count; ++b)
-        if (pass == 1 || sh[b].mode0 == mode) v.push_back(b);
+        if (sh[b].npass > pass && (pass > 0 || sh[b].mode0 == mode)) v.push_back(b);
     return v;
 }
 }  // namespace
@@ -1810,11 +1810,14 @@ TcBatchPlan tc_batch_plan(const std::vector<TcBatchShape>& sh, size_t budget)
         w.tileTab = tk((size_t)w.tilesA * 4);
         w.colTab = tk((size_t)w.cols * 4);
         w.max_items = 1;
-        for (int pass = 0; pass < 2; ++pass) {
+        w.maxpass = 1;
+        for (int i = b; i < e; ++i)
+            if (sh[i].npass > w.maxpass) w.maxpass = sh[i].npass;
+        for (int pass = 0; pass < TC_BATCH_MAX_PASS; ++pass) {
             w.nl[pass] = 0;
             const int modes[2] = {3, 1};
-            for (int k = 0; k < 2; ++k) {
-                if (pass == 1 && k == 0) continue;
+            for (int k = 0; k < 2 && pass < w.maxpass; ++k) {
+                if (pass > 0 && k == 0) continue;
                 const std::vector<int> mem = launch_members(sh, w, pass, modes[k]);
                 if (mem.empty()) continue;
                 const int li = w.nl[pass]++;
@@ -1893,7 +1896,7 @@ void tc_batch_tables(const TcBatchPlan& p, const std::vector<TcBatchShape>& sh, 
                 for (int ib = 16 * kc; ib < nrb; ++ib) tiles[nt++] = (i << 12) | (kc << 8) | ib;
             for (int c = 0; c < n; ++c) colinst[coff[i] + c] = i;
         }
-        for (int pass = 0; pass < 2; ++pass)
+        for (int pass = 0; pass < w.maxpass; ++pass)
             for (int li = 0; li < w.nl[pass]; ++li)
                 for (int prod = 0; prod < 2; ++prod) {
                     const TcBatchLaunch& L = prod == 0 ? w.u[pass][li] : w.c[pass][li];

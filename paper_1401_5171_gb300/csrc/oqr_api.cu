@@ -747,9 +747,11 @@ oqr_status oqr_batched(oqr_ctx* ctx, int count, const int* m, const int* n, cons
     if (!ctx || count < 1 || count > 65535 || !m || !n || !A || !lda || !Z || !ldz || !Q || !ldq || !R || !ldr ||
         !status)
         return OQR_ERR_INVALID_ARG;
-    if (mode == 1 || mode == 2) {
-        std::vector<int> fp((size_t)count, mode == 1 ? OQR_FP64_TC : OQR_TC2);
-        return oqr_batched_mixed(ctx, count, m, n, A, lda, Z, ldz, Q, ldq, R, ldr, fp.data(), status, stream);
+    if (mode >= 1 && mode <= 3) {
+        const int prog = mode == 1 ? OQR_BATCH_CHOLQR2_TC : mode == 2 ? OQR_BATCH_CHOLQR2_TC2 : OQR_BATCH_SCHOLQR3_TC;
+        std::vector<int> pr((size_t)count, prog);
+        return oqr_batched_mixed(ctx, count, m, n, A, lda, Z, ldz, Q, ldq, R, ldr, pr.data(), status, nullptr,
+                                 stream);
     }
     if (mode != 0) return OQR_ERR_INVALID_ARG;
     std::vector<BatchDesc> desc((size_t)count);
@@ -776,7 +778,7 @@ oqr_status oqr_batched(oqr_ctx* ctx, int count, const int* m, const int* n, cons
         d.m = mb;
         d.n = nb;
         d.splits = sp;
-        d.pad = 0;
+        d.npass = 2;
         const int c = nb <= 16 ? 0 : nb <= 32 ? 1 : 2;
         idx[c].push_back(b);
         cls_max_splits[c] = std::max(cls_max_splits[c], sp);
@@ -848,8 +850,8 @@ oqr_status oqr_batched(oqr_ctx* ctx, int count, const int* m, const int* n, cons
 
 oqr_status oqr_batched_mixed(oqr_ctx* ctx, int count, const int* m, const int* n, const double* const* A,
                              const long* lda, const double* const* Z, const long* ldz, double* const* Q,
-                             const long* ldq, double* const* R, const long* ldr, const int* first_prec, int* status,
-                             void* stream)
+                             const long* ldq, double* const* R, const long* ldr, const int* program, int* status,
+                             double* orth, void* stream)
 {
     if (!ctx || count < 1 || count > 65535 || !m || !n || !A || !lda || !Z || !ldz || !Q || !ldq || !R || !ldr ||
         !status)
@@ -860,43 +862,52 @@ oqr_status oqr_batched_mixed(oqr_ctx* ctx, int count, const int* m, const int* n
         if (bad_matrix(A[b], lda[b], mb, mb) || bad_matrix(Z[b], ldz[b], mb, nb) || bad_matrix(Q[b], ldq[b], mb, nb) ||
             bad_matrix(R[b], ldr[b], nb, nb))
             return OQR_ERR_INVALID_ARG;
-        if (first_prec && first_prec[b] != OQR_TC2 && first_prec[b] != OQR_FP64_TC) return OQR_ERR_INVALID_ARG;
+        if (program && (program[b] < OQR_BATCH_CHOLQR_TC || program[b] > OQR_BATCH_SCHOLQR3_TC))
+            return OQR_ERR_INVALID_ARG;
     }
     // largest m first: a wave's plane pitch is its first instance's m
     std::vector<int> perm((size_t)count);
     for (int b = 0; b < count; ++b) perm[b] = b;
     std::stable_sort(perm.begin(), perm.end(), [&](int x, int y) { return m[x] > m[y]; });
     std::vector<TcBatchShape> sh((size_t)count);
+    std::vector<int> shifted((size_t)count, 0);
     std::vector<long> key{count, 0, (long)reinterpret_cast<uintptr_t>(status)};
     size_t pool_doubles = 0;
     for (int i = 0; i < count; ++i) {
         const int b = perm[i];
-        sh[i] = TcBatchShape{m[b], n[b], (first_prec && first_prec[b] == OQR_TC2) ? 3 : 1};
-        key.push_back(((long)m[b] << 32) | ((long)n[b] << 8) | sh[i].mode0);
+        const int pr = program ? program[b] : OQR_BATCH_CHOLQR2_TC;
+        const int npass = pr == OQR_BATCH_CHOLQR_TC ? 1 : pr == OQR_BATCH_SCHOLQR3_TC ? 3 : 2;
+        sh[i] = TcBatchShape{m[b], n[b], pr == OQR_BATCH_CHOLQR2_TC2 ? 3 : 1, npass + (orth ? 1 : 0)};
+        shifted[i] = pr == OQR_BATCH_SCHOLQR3_TC;
+        key.push_back(((long)m[b] << 32) | ((long)n[b] << 8) | (orth ? 4 : 0) | pr);
         pool_doubles += align256((size_t)4 * n[b] * n[b] * sizeof(double)) / sizeof(double);
     }
     const TcBatchPlan plan = tc_batch_plan(sh, BATCH_WAVE_BYTES);
-    auto layout = [&](Carve& c, char** tab, BatchDesc** d, int** sts, int** dperm, double** pool, double** upool,
-                      void** scratch) {
+    auto layout = [&](Carve& c, char** tab, BatchDesc** d, int** sts, int** dperm, int** dshifted, double** sums,
+                      double** shifts, double** orths, double** pool, double** upool, void** scratch) {
         *tab = c.take<char>(plan.table_bytes);
+        *orths = c.take<double>((size_t)count);
         *d = c.take<BatchDesc>((size_t)count);
         *sts = c.take<int>((size_t)count);
         *dperm = c.take<int>((size_t)count);
+        *dshifted = c.take<int>((size_t)count);
+        *sums = c.take<double>((size_t)2 * count);
+        *shifts = c.take<double>((size_t)count);
         *pool = c.take<double>(pool_doubles);
         *upool = c.take<double>((size_t)plan.upool_doubles);
         *scratch = c.take<char>(plan.scratch_bytes);
     };
     char* tab;
     BatchDesc* ddesc;
-    int *sts, *dperm;
-    double *pool, *upool;
+    int *sts, *dperm, *dshifted;
+    double *sums, *shifts, *orths, *pool, *upool;
     void* scratch;
     Carve probe(nullptr);
-    layout(probe, &tab, &ddesc, &sts, &dperm, &pool, &upool, &scratch);
+    layout(probe, &tab, &ddesc, &sts, &dperm, &dshifted, &sums, &shifts, &orths, &pool, &upool, &scratch);
     oqr_status v = ensure_ws(ctx, probe.off);
     if (v != OQR_OK) return v;
     Carve cv(ctx->ws);
-    layout(cv, &tab, &ddesc, &sts, &dperm, &pool, &upool, &scratch);
+    layout(cv, &tab, &ddesc, &sts, &dperm, &dshifted, &sums, &shifts, &orths, &pool, &upool, &scratch);
     key[1] = (long)reinterpret_cast<uintptr_t>(ctx->ws);
     // per instance (sorted order): its descriptor (one Gram partial = the product's half C) and tensor-core inputs
     std::vector<BatchDesc> desc((size_t)count);
@@ -917,7 +928,7 @@ oqr_status oqr_batched_mixed(oqr_ctx* ctx, int count, const int* m, const int* n
         d.m = m[b];
         d.n = n[b];
         d.splits = 1;
-        d.pad = 0;
+        d.npass = sh[i].npass - (orth ? 1 : 0);  // factor passes
         d.partials = q;
         d.G = q + nn;
         d.R1 = d.G + nn;
@@ -931,6 +942,7 @@ oqr_status oqr_batched_mixed(oqr_ctx* ctx, int count, const int* m, const int* n
     OQR_TRY(cudaMemcpyAsync(tab, image.data(), image.size(), cudaMemcpyHostToDevice, s));
     OQR_TRY(cudaMemcpyAsync(ddesc, desc.data(), sizeof(BatchDesc) * count, cudaMemcpyHostToDevice, s));
     OQR_TRY(cudaMemcpyAsync(dperm, perm.data(), sizeof(int) * count, cudaMemcpyHostToDevice, s));
+    OQR_TRY(cudaMemcpyAsync(dshifted, shifted.data(), sizeof(int) * count, cudaMemcpyHostToDevice, s));
     OQR_TRY(cudaMemsetAsync(sts, 0, sizeof(int) * count, s));
     if ((v = reset_status(ctx, s)) != OQR_OK) return v;
     const uint64_t limit = 4000000000ull;
@@ -940,14 +952,25 @@ oqr_status oqr_batched_mixed(oqr_ctx* ctx, int count, const int* m, const int* n
             const TcBatchWave& W = plan.waves[w];
             const BatchDesc* dw = ddesc + W.first;
             int* sw = sts + W.first;
+            bool any_shift = false;
+            for (int i = W.first; i < W.first + W.count; ++i) any_shift = any_shift || shifted[i];
             if ((e = tc_batch_split_a(plan, w, tab, scratch, s)) != cudaSuccess) return e;
-            for (int pass = 0; pass < 2; ++pass) {
+            if (any_shift &&
+                (e = launch_batched_shifts(dw, W.count, dshifted + W.first, sums + 2 * W.first, 11.0, U64,
+                                           shifts + W.first, s)) != cudaSuccess)
+                return e;
+            for (int pass = 0; pass < W.maxpass; ++pass) {
                 if ((e = tc_batch_gram(plan, w, pass, tab, scratch, ctx->st, limit, ctx->sm_count, s)) != cudaSuccess)
                     return e;
-                if ((e = launch_batched_factor(dw, W.count, sw, pass, s)) != cudaSuccess) return e;
+                if ((e = launch_batched_factor(dw, W.count, sw, pass, any_shift ? shifts + W.first : nullptr, s)) !=
+                    cudaSuccess)
+                    return e;
+                if (orth && (e = launch_batched_check(dw, W.count, sw, pass, orths + W.first, s)) != cudaSuccess)
+                    return e;
             }
-            if ((e = launch_batched_rprod(dw, W.count, sw, s)) != cudaSuccess) return e;
+            if ((e = launch_batched_rfinal(dw, W.count, sw, s)) != cudaSuccess) return e;
         }
+        if (orth && (e = launch_batch_scatter_f64(orths, dperm, count, orth, s)) != cudaSuccess) return e;
         return launch_batch_status_scatter(sts, dperm, count, ctx->st, status, s);
     };
     return run_cached_graph(ctx, key, seq, s);

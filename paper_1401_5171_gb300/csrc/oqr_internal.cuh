@@ -221,7 +221,7 @@ struct BatchDesc {
     long lda, ldz, ldq, ldr;
     int m, n;
     int splits;     // Gram work splits (the plan)
-    int pad;
+    int npass;      // normal-equation passes of this instance (the FP64 path: 2)
     double* partials;  // splits x n x n
     double* G;         // n x n
     double* R1;        // n x n
@@ -229,16 +229,31 @@ struct BatchDesc {
 };
 cudaError_t launch_batched_cholqr2(const BatchDesc* d, int count, const int* const* cls_idx, const int* cls_count,
                                    const int* cls_max_splits, int max_n, int* status, cudaStream_t s);
-// Pieces of the batched sequence over a sub-range of BatchDesc (k_batched.cu):
-//   factor: G_b = P_b + P_b^T from one partial (splits = 1), R = chol(G_b)
-//           (R1 for pass 0, R2 for pass 1), Q_b = X_b / R (X = Z in pass 0, Q in place in pass 1);
-//   rprod:  R_b = R2 R1;
+// Pieces of the batched sequence over a sub-range of BatchDesc (k_batched.cu);
+// instances whose npass <= pass sit the pass out:
+//   factor: G_b = P_b + P_b^T from one partial (splits = 1), + shifts[b] I in
+//           pass 0 (shifts may be NULL), R = chol(G_b) (R1 for pass 0, R2
+//           later), Q_b = X_b / R (X = Z in pass 0, Q in place later), and for
+//           pass > 0 R1 <- R2 R1;
+//   rfinal: the caller's R_b = R1;
+//   shifts: shifts[b] = c u (m n + n (n + 1)) ||A_b||_F ||Z_b||_F^2 where
+//           shifted[b], else 0 (sums: 2 count doubles of scratch);
 //   scatter: status[perm[i]] = st_sorted[i], or -1 for every instance when a
 //           tensor-core wait of the context timed out.
-cudaError_t launch_batched_factor(const BatchDesc* d, int count, int* status, int pass, cudaStream_t s);
-cudaError_t launch_batched_rprod(const BatchDesc* d, int count, int* status, cudaStream_t s);
+cudaError_t launch_batched_factor(const BatchDesc* d, int count, int* status, int pass, const double* shifts,
+                                  cudaStream_t s);
+cudaError_t launch_batched_rfinal(const BatchDesc* d, int count, int* status, cudaStream_t s);
+cudaError_t launch_batched_shifts(const BatchDesc* d, int count, const int* shifted, double* sums, double c,
+                                  double u, double* shifts, cudaStream_t s);
 cudaError_t launch_batch_status_scatter(const int* st_sorted, const int* perm, int count, const DevStatus* st,
                                         int* status, cudaStream_t s);
+// The check of the instances whose factor passes end at pass (npass == pass):
+// E = P + P^T - I from the partial of Q^T A Q, orth[b] = an estimate of
+// ||E||_2 (power iteration, a lower bound); orth[b] = inf after a breakdown.
+cudaError_t launch_batched_check(const BatchDesc* d, int count, const int* status, int pass, double* orth,
+                                 cudaStream_t s);
+// out[perm[i]] = in[i] (count doubles).
+cudaError_t launch_batch_scatter_f64(const double* in, const int* perm, int count, double* out, cudaStream_t s);
 
 // Packed tensor-core batches (k_tc.cu).  Instances (sorted by m, largest
 // first) are cut into waves whose slice planes fit a byte budget; a wave's A
@@ -247,8 +262,10 @@ cudaError_t launch_batch_status_scatter(const int* st_sorted, const int* perm, i
 // instance of the wave.  A is split once per wave and read by both passes.
 struct TcBatchShape {
     int m, n;
-    int mode0;  // tensor-core mode of pass 0 (1: EMU64, 3: TC2); pass 1 is EMU64
+    int mode0;  // tensor-core mode of pass 0 (1: EMU64, 3: TC2); later passes are EMU64
+    int npass;  // Gram passes: 1..3 normal-equation passes, + 1 when the result is checked (Q^T A Q)
 };
+constexpr int TC_BATCH_MAX_PASS = 4;
 struct TcBatchIn {
     const double* A;
     long lda;
@@ -271,8 +288,9 @@ struct TcBatchWave {
     int K, kch, tilesA, max_items;
     size_t splitA, splitZ, splitQ, splitU;  // SplitInst tables (byte offsets)
     size_t tileTab, colTab;                 // the A split's tiles, the packed columns' instances
-    TcBatchLaunch u[2][2], c[2][2];         // [pass][launch]: pass 0 one launch per mode present
-    int nl[2];
+    TcBatchLaunch u[TC_BATCH_MAX_PASS][2], c[TC_BATCH_MAX_PASS][2];  // [pass][launch]: pass 0 one per mode present
+    int nl[TC_BATCH_MAX_PASS];
+    int maxpass;
     long upool;  // U pool doubles
 };
 struct TcBatchPlan {
@@ -285,7 +303,8 @@ TcBatchPlan tc_batch_plan(const std::vector<TcBatchShape>& sh, size_t budget);
 // Host image of the tables for the given device addresses (table, U pool).
 void tc_batch_tables(const TcBatchPlan& p, const std::vector<TcBatchShape>& sh, const std::vector<TcBatchIn>& in,
                      const void* table_dev, double* upool, std::vector<char>& image);
-// Wave w: the split of A (once), then the Gram of pass 0 or 1 into each instance's C.
+// Wave w: the split of A (once), then the Gram of pass p into the C of each
+// instance with npass > p (X = Z in pass 0, Q later).
 cudaError_t tc_batch_split_a(const TcBatchPlan& p, int w, const void* table_dev, void* scratch, cudaStream_t s);
 cudaError_t tc_batch_gram(const TcBatchPlan& p, int w, int pass, const void* table_dev, void* scratch,
                           DevStatus* st, uint64_t limit_ns, int sms, cudaStream_t s);

@@ -21,6 +21,7 @@ HEADERS = [os.path.join(os.path.dirname(HERE), "include", "oqr.h")]
 OQR_OK, OQR_ERR_INVALID_ARG, OQR_ERR_NOT_SPD, OQR_ERR_CHECK_FAILED = 0, 1, 2, 3
 OQR_ERR_CUDA, OQR_ERR_NO_MEMORY, OQR_ERR_TIMEOUT, OQR_ERR_UNSUPPORTED = 4, 5, 6, 7
 OQR_FP64, OQR_BF16X3, OQR_FP8, OQR_FP64_TC, OQR_TC2 = 0, 1, 2, 3, 4
+OQR_BATCH_CHOLQR_TC, OQR_BATCH_CHOLQR2_TC2, OQR_BATCH_CHOLQR2_TC, OQR_BATCH_SCHOLQR3_TC = 0, 1, 2, 3
 OQR_ALGO_CHOLQR, OQR_ALGO_CHOLQR2, OQR_ALGO_SCHOLQR3, OQR_ALGO_CGS2 = 0, 1, 2, 3
 
 
@@ -88,7 +89,7 @@ def load(path: str | None = None):
     lib.oqr_batched.argtypes = [vp, i, ctypes.POINTER(i), ctypes.POINTER(i), ppd, pl, ppd, pl, ppd, pl, ppd, pl, i,
                                 ctypes.POINTER(i), vp, vp]
     lib.oqr_batched_mixed.argtypes = [vp, i, ctypes.POINTER(i), ctypes.POINTER(i), ppd, pl, ppd, pl, ppd, pl, ppd,
-                                      pl, ctypes.POINTER(i), vp, vp]
+                                      pl, ctypes.POINTER(i), vp, vp, vp]
     lib.oqr_batched_default_splits.argtypes = [i, i]
     fp, ip = ctypes.c_void_p, ctypes.c_void_p
     lib.oqr_features.argtypes = [vp, i, i, vp, l, vp, l, fp, vp]
@@ -298,7 +299,7 @@ class Oqr:
     def oqr_batched(self, As, Zs, Qs=None, Rs=None, splits=None, stream=None, status=None, mode=0):
         """Batched A-CholQR2 over lists of column-major CUDA tensors; returns (Qs, Rs, status tensor).
 
-        mode 0: FP64; 1: tensor cores, every pass OQR_FP64_TC; 2: tensor cores, first pass OQR_TC2."""
+        mode 0: FP64; tensor cores: 1 OQR_BATCH_CHOLQR2_TC, 2 OQR_BATCH_CHOLQR2_TC2, 3 OQR_BATCH_SCHOLQR3_TC."""
         Qs, Rs, st, a = self._batch_args(As, Zs, Qs, Rs, status)
         sp = (ctypes.c_int * a[0])(*splits) if splits is not None else None
         r = self.lib.oqr_batched(self.ctx, *a, int(mode), sp, ctypes.c_void_p(st.data_ptr()), self._stream(stream))
@@ -306,15 +307,19 @@ class Oqr:
             raise OqrError(r, "oqr_batched")
         return Qs, Rs, st
 
-    def oqr_batched_mixed(self, As, Zs, first_prec=None, Qs=None, Rs=None, stream=None, status=None):
-        """Batched A-CholQR2 on the tensor cores; first_prec: per-instance OQR_TC2 / OQR_FP64_TC (None: all
-        OQR_FP64_TC).  Returns (Qs, Rs, status tensor)."""
+    def oqr_batched_mixed(self, As, Zs, program=None, Qs=None, Rs=None, stream=None, status=None, check=False):
+        """Batched oblique QR on the tensor cores; program: per-instance OQR_BATCH_* (None: all
+        OQR_BATCH_CHOLQR2_TC).  Returns (Qs, Rs, status tensor), and with check=True also the tensor of
+        per-instance ||Q^T A Q - I||_2 estimates."""
+        import torch
         Qs, Rs, st, a = self._batch_args(As, Zs, Qs, Rs, status)
-        fp = (ctypes.c_int * a[0])(*[int(x) for x in first_prec]) if first_prec is not None else None
-        r = self.lib.oqr_batched_mixed(self.ctx, *a, fp, ctypes.c_void_p(st.data_ptr()), self._stream(stream))
+        pr = (ctypes.c_int * a[0])(*[int(x) for x in program]) if program is not None else None
+        orth = torch.empty(a[0], dtype=torch.float64, device=Zs[0].device) if check else None
+        r = self.lib.oqr_batched_mixed(self.ctx, *a, pr, ctypes.c_void_p(st.data_ptr()),
+                                       ctypes.c_void_p(orth.data_ptr()) if check else None, self._stream(stream))
         if r != OQR_OK:
             raise OqrError(r, "oqr_batched_mixed")
-        return Qs, Rs, st
+        return (Qs, Rs, st, orth) if check else (Qs, Rs, st)
 
     # ---- selector ---------------------------------------------------------------
     def oqr_features(self, A, Z, out=None, stream=None):

@@ -156,6 +156,74 @@ def solve(ctx, A, Z, P, tol=1e-12):
     return Q, R, {"choice": k, "fallback": fell, "used": used, "orth": o, "status": st}
 
 
+# options -> programs of the batched tensor-core path (option 3, FP64 A-CholQR2, is oqr_batched mode 0)
+BATCH_PROGRAMS = {0: 0, 1: 1, 2: 3}   # OQR_BATCH_CHOLQR_TC, OQR_BATCH_CHOLQR2_TC2, OQR_BATCH_SCHOLQR3_TC
+
+
+def solve_batch(ctx, As, Zs, P, tol=1e-12, stream=None):
+    """The selector over a batch.  Per-instance features (oqr_features), one MLP forward over the batch,
+    then the chosen tensor-core programs in one checked oqr_batched_mixed call and the FP64 A-CholQR2
+    choices in one oqr_batched call.  Options 0 and 1 are accepted when their check meets tol, option 2
+    and 3 once they complete (the network's answer for hard instances).  Every other instance goes down
+    the fallback chain in batches: shifted A-CholQR3 on the tensor cores (checked), then FP64 A-CholQR2,
+    keeping the most orthogonal completed result.  Returns (Qs, Rs, info) with per-instance lists
+    choice, used, orth (nan where the result was not checked) and status."""
+    import torch
+    from . import oqr as _oqr
+    B = len(Zs)
+    dev = Zs[0].device
+    X = torch.empty((B, 16), dtype=torch.float32, device=dev)
+    for b in range(B):
+        ctx.oqr_features(As[b], Zs[b], out=X[b], stream=stream)
+    choice = [int(c) for c in choose(ctx, X, P).cpu().tolist()]
+    Qs = [_oqr.empty_colmajor(z.shape[0], z.shape[1], dev) for z in Zs]
+    Rs = [_oqr.empty_colmajor(z.shape[1], z.shape[1], dev) for z in Zs]
+    used = [None] * B
+    orth = [float("inf")] * B
+    status = [1] * B
+    accepted = [False] * B
+
+    def run_tc(idx, programs):
+        Qt = [_oqr.empty_colmajor(Zs[b].shape[0], Zs[b].shape[1], dev) for b in idx]
+        Rt = [_oqr.empty_colmajor(Zs[b].shape[1], Zs[b].shape[1], dev) for b in idx]
+        _, _, st, o = ctx.oqr_batched_mixed([As[b] for b in idx], [Zs[b] for b in idx], program=programs,
+                                            Qs=Qt, Rs=Rt, stream=stream, check=True)
+        return Qt, Rt, st.cpu().tolist(), o.cpu().tolist()
+
+    def run_fp64(idx):
+        Qt = [_oqr.empty_colmajor(Zs[b].shape[0], Zs[b].shape[1], dev) for b in idx]
+        Rt = [_oqr.empty_colmajor(Zs[b].shape[1], Zs[b].shape[1], dev) for b in idx]
+        _, _, st = ctx.oqr_batched([As[b] for b in idx], [Zs[b] for b in idx], Qs=Qt, Rs=Rt, stream=stream)
+        return Qt, Rt, st.cpu().tolist(), [float("nan")] * len(idx)
+
+    def take(idx, res, options):
+        """Keeps each completed result that is the instance's first or more orthogonal than its last."""
+        Qt, Rt, st, o = res
+        for k, b in enumerate(idx):
+            if st[k] != 0:
+                continue
+            if status[b] != 0 or o[k] < orth[b]:
+                Qs[b].copy_(Qt[k])
+                Rs[b].copy_(Rt[k])
+                status[b], orth[b], used[b] = 0, o[k], options[k]
+            if options[k] in (2, 3) or o[k] <= tol:
+                accepted[b] = True
+
+    tc = [b for b in range(B) if choice[b] != 3]
+    if tc:
+        take(tc, run_tc(tc, [BATCH_PROGRAMS[choice[b]] for b in tc]), [choice[b] for b in tc])
+    fp = [b for b in range(B) if choice[b] == 3]
+    if fp:
+        take(fp, run_fp64(fp), [3] * len(fp))
+    rest = [b for b in range(B) if not accepted[b]]
+    if rest:
+        take(rest, run_tc(rest, [BATCH_PROGRAMS[2]] * len(rest)), [2] * len(rest))
+    rest = [b for b in range(B) if status[b] != 0]
+    if rest:
+        take(rest, run_fp64(rest), [3] * len(rest))
+    return Qs, Rs, {"choice": choice, "used": used, "orth": orth, "status": status}
+
+
 def save(P, path):
     with open(path, "w") as f:
         json.dump({"layout": "W1[64][16] b1[64] W2[64][64] b2[64] W3[4][64] b3[4]",

@@ -178,17 +178,18 @@ def test_batched_mixed_tc2_first_pass(env):
 
 
 def test_batched_mixed_instances_independent(env):
-    """An instance's (Q, R) are bit-identical whether it runs alone or packed with others, with either
-    first-pass precision mixed in one wave."""
+    """An instance's (Q, R) are bit-identical whether it runs alone or packed with others, with the four
+    programs (1 to 3 passes, TC2 or FP64_TC first, shifted first pass) mixed in one wave."""
     torch, oqr, ctx = env
     As, Zs, _ = inputs.batch_instances(9, seed=17, device="cuda", m_range=(64, 900), n_range=(1, 64),
                                        log_kappa_a=(0.0, 2.0), log_kappa_z=(0.0, 1.0))
-    fp = [oqr.OQR_TC2 if b % 2 else oqr.OQR_FP64_TC for b in range(len(Zs))]
-    Qs, Rs, st = ctx.oqr_batched_mixed(As, Zs, first_prec=fp)
+    progs = (oqr.OQR_BATCH_CHOLQR2_TC, oqr.OQR_BATCH_CHOLQR2_TC2, oqr.OQR_BATCH_SCHOLQR3_TC, oqr.OQR_BATCH_CHOLQR_TC)
+    fp = [progs[b % 4] for b in range(len(Zs))]
+    Qs, Rs, st = ctx.oqr_batched_mixed(As, Zs, program=fp)
     torch.cuda.synchronize()
     assert st.abs().sum().item() == 0
-    for b in (0, 3, 4, 8):
-        Q1, R1, s1 = ctx.oqr_batched_mixed([As[b]], [Zs[b]], first_prec=[fp[b]])
+    for b in (0, 1, 2, 3, 4, 8):
+        Q1, R1, s1 = ctx.oqr_batched_mixed([As[b]], [Zs[b]], program=[fp[b]])
         torch.cuda.synchronize()
         assert s1.item() == 0
         assert torch.equal(Q1[0], Qs[b]) and torch.equal(R1[0], Rs[b])
@@ -225,8 +226,92 @@ def test_batched_mixed_graph_replay_same_result(env):
         assert torch.equal(a, b)
 
 
-def test_batched_mixed_rejects_bad_first_prec(env):
+def test_batched_mixed_rejects_bad_program(env):
     torch, oqr, ctx = env
     As, Zs, _ = inputs.batch_instances(2, seed=1, device="cuda", m_range=(64, 128), n_range=(4, 8))
     with pytest.raises(oqr.OqrError):
-        ctx.oqr_batched_mixed(As, Zs, first_prec=[oqr.OQR_FP64, oqr.OQR_TC2])
+        ctx.oqr_batched_mixed(As, Zs, program=[oqr.OQR_BATCH_CHOLQR2_TC, 4])
+
+
+def test_batched_one_pass_matches_oracle(env):
+    """One FP64_TC pass (Algorithm 1): R within the one-pass bound, T2.1's kappa^2 u growth of the
+    orthogonality (reading: kappa(A^{1/2} Z) <= 1e3)."""
+    torch, oqr, ctx = env
+    As, Zs, _ = inputs.batch_instances(12, seed=21, device="cuda", m_range=(64, 900), n_range=(1, 64),
+                                       log_kappa_a=(0.0, 2.0), log_kappa_z=(0.0, 1.0))
+    Qs, Rs, st = ctx.oqr_batched_mixed(As, Zs, program=[oqr.OQR_BATCH_CHOLQR_TC] * len(Zs))
+    torch.cuda.synchronize()
+    assert st.abs().sum().item() == 0
+    for b in range(len(Zs)):
+        A, Z, Q, R = (x.cpu().numpy() for x in (As[b], Zs[b], Qs[b], Rs[b]))
+        Qr, Rr = oracle.oblique_qr(A, Z)
+        kap = np.linalg.cond(Rr)
+        assert np.all(np.tril(R, -1) == 0) and np.all(np.diag(R) > 0)
+        assert np.linalg.norm(R - Rr) / np.linalg.norm(Rr) <= max(1e-13, 50 * U * kap * kap)
+        assert oracle.orth_error(A, Q) <= max(1e-13, 100 * U * kap * kap * np.linalg.eigvalsh(A).max())
+
+
+def test_batched_shifted_reaches_ill_conditioned(env):
+    """Shifted A-CholQR3 on the tensor cores (mode 3) completes where A-CholQR2 breaks down:
+    kappa(A^{1/2} Z) up to ~1e11, orthogonality at the oracle's level, Z = QR."""
+    torch, oqr, ctx = env
+    As, Zs, tab = inputs.batch_instances(10, seed=31, device="cuda", m_range=(200, 1200), n_range=(8, 64),
+                                         log_kappa_a=(2.0, 4.0), log_kappa_z=(8.0, 9.0))
+    _, _, st2 = ctx.oqr_batched(As, Zs, mode=1)
+    Qs, Rs, st = ctx.oqr_batched(As, Zs, mode=3)
+    torch.cuda.synchronize()
+    assert st2.ne(0).sum().item() > 0          # beyond A-CholQR2's reach on some instances
+    assert st.abs().sum().item() == 0
+    for b in range(len(Zs)):
+        A, Z, Q, R = (x.cpu().numpy() for x in (As[b], Zs[b], Qs[b], Rs[b]))
+        Qr, _ = oracle.oblique_qr(A, Z)
+        floor = 100 * U * np.linalg.eigvalsh(A).max() * np.linalg.norm(Qr, 2) ** 2
+        assert oracle.orth_error(A, Q) <= max(1e-12, 10 * oracle.orth_error(A, Qr), floor)
+        assert np.linalg.norm(Z - Q @ R, 2) / np.linalg.norm(Z, 2) <= 1e-13
+        assert np.all(np.tril(R, -1) == 0) and np.all(np.diag(R) > 0)
+
+
+def test_batched_check_estimates_orthogonality(env):
+    """check=True: orth[b] estimates ||Q_b^T A_b Q_b - I||_2 from an FP64-accurate Gram of the final Q
+    (power iteration, a lower bound); +inf after a breakdown."""
+    torch, oqr, ctx = env
+    As, Zs, _ = inputs.batch_instances(10, seed=41, device="cuda", m_range=(64, 700), n_range=(2, 64),
+                                       log_kappa_a=(0.0, 2.0), log_kappa_z=(3.0, 4.0))
+    bad = torch.eye(100, dtype=torch.float64, device="cuda")
+    bad[7, 7] = -1.0
+    As.append(oqr.colmajor(bad))
+    Zs.append(oqr.colmajor(torch.eye(100, 10, dtype=torch.float64, device="cuda")))
+    progs = [oqr.OQR_BATCH_CHOLQR_TC, oqr.OQR_BATCH_CHOLQR2_TC] * 5 + [oqr.OQR_BATCH_CHOLQR2_TC]
+    Qs, Rs, st, orth = ctx.oqr_batched_mixed(As, Zs, program=progs, check=True)
+    torch.cuda.synchronize()
+    st, orth = st.cpu().numpy(), orth.cpu().numpy()
+    assert st[-1] == 8 and np.isinf(orth[-1])
+    for b in range(len(Zs) - 1):
+        assert st[b] == 0
+        A = As[b].cpu().numpy()
+        ref = oracle.orth_error(A, Qs[b].cpu().numpy())
+        # the check's own Gram rounds at about sqrt(m) u ||A|| ||Q||^2 (here ||Q||_2 <= 1: smallest eigenvalue 1)
+        slack = 2 * np.sqrt(A.shape[0]) * U * np.linalg.eigvalsh(A).max()
+        assert orth[b] <= 1.05 * ref + slack
+        assert orth[b] >= 0.2 * ref - slack
+        if b % 2 == 0:                     # one pass: kappa^2 u, well above the rounding level
+            assert ref > 10 * slack and 0.9 * ref <= orth[b] <= 1.05 * ref
+
+
+def test_selector_solve_batch_completes(env):
+    """The batched selector with an untrained network (arbitrary choices): checks and the fallback chain
+    give every instance the attainable orthogonality (kappa(A^{1/2} Z) up to ~1e12)."""
+    torch, oqr, ctx = env
+    from paper_1401_5171_gb300 import selector
+    P = torch.as_tensor(selector.init_params(3), device="cuda")
+    As, Zs, _ = inputs.batch_instances(16, seed=51, device="cuda", m_range=(64, 600), n_range=(4, 40),
+                                       log_kappa_a=(0.0, 4.0), log_kappa_z=(0.0, 8.0))
+    Qs, Rs, info = selector.solve_batch(ctx, As, Zs, P)
+    torch.cuda.synchronize()
+    for b in range(len(Zs)):
+        A, Z, Q, R = (x.cpu().numpy() for x in (As[b], Zs[b], Qs[b], Rs[b]))
+        assert info["status"][b] == 0
+        Qr, _ = oracle.oblique_qr(A, Z)
+        floor = 100 * U * np.linalg.eigvalsh(A).max() * np.linalg.norm(Qr, 2) ** 2
+        assert oracle.orth_error(A, Q) <= max(1e-12, 10 * oracle.orth_error(A, Qr), floor)
+        assert np.linalg.norm(Z - Q @ R, 2) / np.linalg.norm(Z, 2) <= 1e-13
