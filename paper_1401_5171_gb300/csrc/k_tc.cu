@@ -108,26 +108,33 @@ __device__ inline void emu_slices7(double x, int e, float* out)
     const int k = b.Eb - e - 1020;  // y 2^48 = M 2^k, k <= 2 because |x| < 2^e
     long long Y = 0;
     if (b.M != 0) {
-        const unsigned long long mag = k >= 0 ? (b.M << k) : rne_shift(b.M, -k);
+        // k < 0: round M 2^k to the nearest integer, ties to even, as (M + 2^(-k-1) - 1 + lsb) >> -k with
+        // lsb the kept part's last bit (no overflow: M < 2^53); M 2^k < 1/2 for -k >= 54
+        unsigned long long mag;
+        if (k >= 0) {
+            mag = b.M << k;
+        } else {
+            const int sh = -k;
+            mag = sh >= 54 ? 0ull : (b.M + ((1ull << (sh - 1)) - 1ull) + ((b.M >> sh) & 1ull)) >> sh;
+        }
         Y = b.neg ? -(long long)mag : (long long)mag;
     }
-    // Balanced digits from the bytes of Y's two's complement, lowest first: with carry c in, the
-    // digit is d = byte + c - 256 c' where c' = (byte + c >= 128); v = byte + c + 128 gives
-    // d + 128 = v & 255 and c' = v >> 8.  d 2^(-8s) is then formed exactly from d + 128 by a
-    // magic-number float: 2^(23-8s) + (d + 128) 2^(-8s), minus 2^(23-8s) + 128 2^(-8s).
-    const unsigned lo = (unsigned)(unsigned long long)Y;
-    const unsigned hi = (unsigned)((unsigned long long)Y >> 32);
-    unsigned c = 0;
+    // Balanced digits: with W = Y + sum_{t<7} 128 256^t, byte t of W is d + 128 for the digit of weight
+    // 256^t (the digits d + 128 lie in [0, 255], so the representation of W has no carries), and
+    // d_0 = W / 2^48 - 128 in [-128, 128].  One 64-bit add replaces a carry chain.  d 2^(-8s) is then
+    // formed exactly from the byte by a magic-number float: 2^(23-8s) + (d + 128) 2^(-8s) (the byte
+    // placed in the low mantissa bits), minus 2^(23-8s) + 128 2^(-8s).
+    const unsigned long long W = (unsigned long long)Y + 0x0080808080808080ull;
+    const unsigned lo = (unsigned)W;
+    const unsigned hi = (unsigned)(W >> 32);
 #pragma unroll
-    for (int t = 0; t < 6; ++t) {  // byte t of Y -> digit s = 6 - t
+    for (int t = 0; t < 6; ++t) {  // byte t of W -> digit s = 6 - t
         const int sd = 6 - t;
-        const unsigned byte = t < 4 ? (lo >> (8 * t)) & 255u : (hi >> (8 * (t - 4))) & 255u;
-        const unsigned v = byte + c + 128u;
-        c = v >> 8;
-        const int base = 0x4B000000 - ((8 * sd) << 23);
-        out[sd] = __int_as_float(base + (int)(v & 255u)) - __int_as_float(base + 128);
+        const unsigned base = 0x4B000000u - ((8u * sd) << 23);
+        const unsigned bits = __byte_perm(t < 4 ? lo : hi, base, 0x7650u | (unsigned)(t & 3));
+        out[sd] = __uint_as_float(bits) - __uint_as_float(base + 128u);
     }
-    const int top = ((int)hi >> 16) + (int)c;  // d_0 = floor(Y / 2^48) + carry, in [-128, 128]
+    const int top = (int)((long long)W >> 48) - 128;  // d_0
     out[0] = __int_as_float(0x4B000000 + top + 128) - __int_as_float(0x4B000000 + 128);
 }
 
@@ -256,6 +263,23 @@ __device__ inline void store_run(__nv_bfloat16* planes, size_t plane, size_t off
         unsigned char* dst = reinterpret_cast<unsigned char*>(planes) + off;
         if constexpr (VPL == 4) *reinterpret_cast<unsigned*>(dst) = w[0];
         else *reinterpret_cast<uint2*>(dst) = make_uint2(w[0], w[1]);
+    } else if (MODE == 1 && VPL == 8) {
+        // element pairs packed as BF16x2 words as they are sliced (28 live words), then one 16-byte
+        // store per plane: the warp writes 512 contiguous bytes of each plane
+        unsigned wd[7][4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float a[7], c[7];
+            slice_element<1>(v[2 * q], e, S, a);
+            slice_element<1>(v[2 * q + 1], e, S, c);
+#pragma unroll
+            for (int t = 0; t < 7; ++t)  // at most 8 significant bits: BF16 is the float's upper half
+                wd[t][q] = __byte_perm(__float_as_uint(a[t]), __float_as_uint(c[t]), 0x7632u);
+        }
+#pragma unroll
+        for (int t = 0; t < 7; ++t)
+            if (t < S)
+                *reinterpret_cast<uint4*>(planes + t * plane + off) = make_uint4(wd[t][0], wd[t][1], wd[t][2], wd[t][3]);
     } else {
         // runs of four elements: 28 live slice values, one 8-byte store per plane and run
         const int np = MODE == 0 ? 2 : S;
@@ -267,10 +291,10 @@ __device__ inline void store_run(__nv_bfloat16* planes, size_t plane, size_t off
 #pragma unroll
             for (int t = 0; t < 7; ++t) {
                 if (t < np) {
-                    __nv_bfloat162 lo2 = __floats2bfloat162_rn(sl[0][t], sl[1][t]);  // exact: <= 8 significant bits
-                    __nv_bfloat162 hi2 = __floats2bfloat162_rn(sl[2][t], sl[3][t]);
-                    *reinterpret_cast<uint2*>(planes + t * plane + off + 4 * h) =
-                        make_uint2(*reinterpret_cast<unsigned int*>(&lo2), *reinterpret_cast<unsigned int*>(&hi2));
+                    // the values have at most 8 significant bits, so BF16 is the float's upper half
+                    const unsigned lo2 = __byte_perm(__float_as_uint(sl[0][t]), __float_as_uint(sl[1][t]), 0x7632u);
+                    const unsigned hi2 = __byte_perm(__float_as_uint(sl[2][t]), __float_as_uint(sl[3][t]), 0x7632u);
+                    *reinterpret_cast<uint2*>(planes + t * plane + off + 4 * h) = make_uint2(lo2, hi2);
                 }
             }
         }
@@ -306,16 +330,20 @@ __device__ __forceinline__ void split_lower_tile(int m, int K, const double* __r
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int lr = threadIdx.x % ROWS, lg = threadIdx.x / ROWS;  // load phase: row, column group
     double ld[16];  // all of this thread's loads in flight before the first store
+    if (row0 + ROWS <= m && col0 + CW <= K && (!TRI || col0 + CW <= row0 + 1)) {
+        // a tile inside the matrix (and below the diagonal): no per-element bounds
+        const double* p = A + (row0 + lr) + (col0 + lg) * lda;
 #pragma unroll
-    for (int t = 0; t < 16; ++t) {
-        const int k = lg + CG * t;
-        const long i = row0 + lr, kk = col0 + k;
-        double v = 0.0;
-        if (i < m && kk < K && (!TRI || kk <= i)) {
-            v = A[i + kk * lda];
-            if (TRI && kk == i) v *= 0.5;  // one FP64 multiply per diagonal element
+        for (int t = 0; t < 16; ++t) ld[t] = p[(long)CG * t * lda];
+    } else {
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+            const int k = lg + CG * t;
+            const long i = row0 + lr, kk = col0 + k;
+            double v = 0.0;
+            if (i < m && kk < K && (!TRI || kk <= i)) v = A[i + kk * lda];
+            ld[t] = v;
         }
-        ld[t] = v;
     }
 #pragma unroll
     for (int t = 0; t < 16; ++t) {
@@ -323,6 +351,18 @@ __device__ __forceinline__ void split_lower_tile(int m, int K, const double* __r
         T[lr][(k % VPL) * 33 + k / VPL] = ld[t];
     }
     __syncthreads();
+    if constexpr (TRI) {
+        // M's diagonal is A's halved: one FP64 multiply per diagonal element, only in the tiles that
+        // hold the diagonal (FP64 instructions are scarce, so none sits in the load loop)
+        if (col0 < row0 + ROWS && row0 < col0 + CW) {  // the same for the whole block
+            if (threadIdx.x < ROWS) {
+                const long kk = row0 + threadIdx.x - col0;
+                if (kk >= 0 && kk < CW && row0 + threadIdx.x < m)
+                    T[threadIdx.x][(kk % VPL) * 33 + kk / VPL] *= 0.5;
+            }
+            __syncthreads();
+        }
+    }
     constexpr int RPW = ROWS / 8;  // rows per warp
     for (int r = w * RPW; r < w * RPW + RPW; ++r) {
         const long i = row0 + r;
@@ -340,7 +380,7 @@ __device__ __forceinline__ void split_lower_tile(int m, int K, const double* __r
 }
 
 template <int MODE, bool TRI, int CW>
-__global__ void __launch_bounds__(256) split_lower_kernel(int m, int K, const double* __restrict__ A, long lda, int S,
+__global__ void __launch_bounds__(256, 4) split_lower_kernel(int m, int K, const double* __restrict__ A, long lda, int S,
                                                           __nv_bfloat16* planes, long ldp, size_t plane,
                                                           int* eA, int* emax, int kc0 = 0)
 {
@@ -362,7 +402,7 @@ static_assert(BATCH_MAX_M <= 4096, "tile codes hold 4 chunk bits, 8 row-block bi
 // The triangular row split of a packed batch of A's: block j takes the tile
 // tiles[j] = (instance << 12) | (chunk << 8) | 16-row block, listed for the
 // lower-triangle tiles only.
-__global__ void __launch_bounds__(256) split_lower_batch_kernel(const SplitInst* __restrict__ inst,
+__global__ void __launch_bounds__(256, 4) split_lower_batch_kernel(const SplitInst* __restrict__ inst,
                                                                 const int* __restrict__ tiles, int S,
                                                                 __nv_bfloat16* planes, long ldp, size_t plane, int* eA,
                                                                 int* emax, long erows)
