@@ -175,24 +175,35 @@ __global__ void __launch_bounds__(256) potrf_batched_kernel(const BatchDesc* __r
         const int i = e % n, j = e / n;
         S[i][j] = (i <= j) ? D.G[j + (size_t)i * n] : 0.0;  // lower triangle of G -> upper of S
     }
+    __shared__ double rinv;
     if (tid == 0) broke = 0;
     __syncthreads();
     for (int j = 0; j < n; ++j) {
-        const double piv = S[j][j];
-        if (!(piv > 0.0)) {
-            if (tid == 0) broke = j + 1;
+        // one thread takes the pivot's square root and reciprocal (FP64 is scarce: not once per thread)
+        if (tid == 0) {
+            const double piv = S[j][j];
+            if (!(piv > 0.0)) {
+                broke = j + 1;
+            } else {
+                const double dj = sqrt(piv);
+                S[j][j] = dj;
+                rinv = 1.0 / dj;
+            }
         }
         __syncthreads();
         if (broke) break;
-        const double dj = sqrt(piv);
+        const double rj = rinv;
+        for (int c = j + 1 + tid; c < n; c += 256) S[j][c] *= rj;
         __syncthreads();
-        if (tid == 0) S[j][j] = dj;
-        for (int c = j + 1 + tid; c < n; c += 256) S[j][c] /= dj;
-        __syncthreads();
-        // trailing update of the upper triangle
-        for (int e = tid; e < (n - j - 1) * (n - j - 1); e += 256) {
-            const int r = j + 1 + e % (n - j - 1), c = j + 1 + e / (n - j - 1);
-            if (r <= c) S[r][c] -= S[j][r] * S[j][c];
+        // trailing update of the upper triangle, its w (w + 1) / 2 pairs (r <= c) enumerated densely:
+        // pair e is column c' = max{c : c (c + 1) / 2 <= e}, row r' = e - c' (c' + 1) / 2
+        const int w = n - j - 1;
+        for (int e = tid; e < w * (w + 1) / 2; e += 256) {
+            int cp = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+            while (cp * (cp + 1) / 2 > e) --cp;
+            while ((cp + 1) * (cp + 2) / 2 <= e) ++cp;
+            const int r = j + 1 + (e - cp * (cp + 1) / 2), c = j + 1 + cp;
+            S[r][c] -= S[j][r] * S[j][c];
         }
         __syncthreads();
     }
