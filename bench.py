@@ -35,6 +35,27 @@ METRIC = "oblique QRs/sec and TFLOP/s at ||Q^T A Q - I|| <= 1e-12, mixed vs FP64
 SMS, FP64_FLOPS_PER_CLK_SM = 152, 4      # GB300: 2 FP64 FMAs per clock per SM
 
 
+# ---- multi-rank logic (replicas: every rank factors its own instance; no data-path collective) ----
+def instance_seeds(rank):
+    """Seeds of rank's instance: A from 1000 + rank, Z from 2000 + rank (distinct per rank)."""
+    return 1000 + rank, 2000 + rank
+
+
+def max_over_ranks(ms, world, dist=None, device="cpu"):
+    """The job's time: the maximum of the ranks' times (all_reduce MAX; the value itself at N = 1)."""
+    if world <= 1:
+        return ms
+    import torch
+    t = torch.tensor([float(ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+def whole_job_rate(world, units_per_rank, ms):
+    """Units per second over all ranks: every rank processed units_per_rank in (at most) ms."""
+    return world * units_per_rank / (ms / 1e3)
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -364,10 +385,11 @@ def main():
         return
     m, n = args.m, args.n
     # inputs resident in HBM before the timed region
-    Af, _ = inputs.dense_spd(m, args.kappa_a, seed=1000 + rank, device=dev)
+    seed_a, seed_z = instance_seeds(rank)
+    Af, _ = inputs.dense_spd(m, args.kappa_a, seed=seed_a, device=dev)
     A = oqr.colmajor(Af)
     del Af
-    Z = oqr.colmajor(inputs.tall_z(m, n, args.kappa_z, seed=2000 + rank, device=dev))
+    Z = oqr.colmajor(inputs.tall_z(m, n, args.kappa_z, seed=seed_z, device=dev))
     Q = oqr.empty_colmajor(m, n, dev)
     R = oqr.empty_colmajor(n, n, dev)
     ctx = oqr.Oqr(local)
@@ -389,13 +411,10 @@ def main():
             ctx._qr(name, A, Z, Q=Q, R=R, opts=opts, stream=stream, sync=False)
         e1.record(stream)
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
+        ms = max_over_ranks(e0.elapsed_time(e1), world, dist, dev)
         if world > 1:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = t.item()
             dist.barrier()
-        return {"qr_per_s": world * steps / (ms / 1e3), "ms_per_qr": ms / steps,
+        return {"qr_per_s": whole_job_rate(world, steps, ms), "ms_per_qr": ms / steps,
                 "tflops_normalised": world * normalised_flops(m, n, passes) * steps / (ms / 1e3) / 1e12,
                 "orth_err": info.orth_err, "status": st, "steps": steps}
 
@@ -411,7 +430,7 @@ def main():
     # side measurement: the batched workload (m ~ U[64, 4096], n ~ U[4, 64], kappa(A), kappa(Z) log-uniform
     # to 1e6), a sample of args.batch_count instances; every path factors the whole batch per step
     batch = None
-    if args.batch_count > 0:
+    if args.batch_count > 0 and world == 1:  # a single-GPU side measurement
         batch = run_batch(ctx, torch, dev, args.batch_count, stream)
 
     # dominant kernel of the headline path, timed alone with CUDA events on the same stream
@@ -478,13 +497,9 @@ def main():
             e2e_step()
         x1.record(stream)
         torch.cuda.synchronize()
-        ems = x0.elapsed_time(x1)
-        if world > 1:
-            t = torch.tensor([ems], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = t.item()
+        ems = max_over_ranks(x0.elapsed_time(x1), world, dist, dev)
         tri = sum((m - j0) * min(256, m - j0) for j0 in range(0, m, 256))  # lower-triangle panels
-        e2e = {"value": world * args.e2e_steps / (ems / 1e3), "unit": "QR/s",
+        e2e = {"value": whole_job_rate(world, args.e2e_steps, ems), "unit": "QR/s",
                "h2d_bytes_per_step": 8 * (tri + m * n), "d2h_bytes_per_step": 8 * (m * n + n * n),
                "call": "oqr_cholqr2_host (pinned host buffers; lower triangle of A copied in 256-column panels)"}
         del Ah
