@@ -907,8 +907,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         float v[32];
                         tmem_ld32(buf + (uint32_t)(h * 32), v);
 #pragma unroll
-                        for (int c = 0; c < 32; ++c) H[h * 32 + c] = fmaf(__fmul_rn(v[c], rs), colscale[h * 32 + c],
-                                                                          H[h * 32 + c]);
+                        for (int c = 0; c < 32; c += 2) {  // two columns per FP32x2 instruction
+                            const float2 p = __fmul2_rn(make_float2(v[c], v[c + 1]), make_float2(rs, rs));
+                            const float2 hh = __ffma2_rn(p, make_float2(colscale[h * 32 + c], colscale[h * 32 + c + 1]),
+                                                         make_float2(H[h * 32 + c], H[h * 32 + c + 1]));
+                            H[h * 32 + c] = hh.x;
+                            H[h * 32 + c + 1] = hh.y;
+                        }
                     }
                 } else {
 #pragma unroll 1
@@ -1083,32 +1088,43 @@ __device__ inline double f32_scaled_to_f64(float x, int k)
     return x == 0.0f ? 0.0 : ldexp((double)x, k);
 }
 
-// 16 consecutive accumulator columns of this thread's TMEM lane; the load and
+// 8 consecutive accumulator columns of this thread's TMEM lane; the load and
 // its wait are one asm statement, so no use of r can precede the wait.
-__device__ inline void tmem_ld16(uint32_t taddr, uint32_t* r)
+__device__ inline void tmem_ld8(uint32_t taddr, uint32_t* r)
 {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
         "tcgen05.wait::ld.sync.aligned;"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
         : "r"(taddr)
         : "memory");
 }
 
-// Two such loads (columns taddr.. and taddr2..) under one wait.
-__device__ inline void tmem_ld16x2(uint32_t taddr, uint32_t taddr2, uint32_t* r, uint32_t* u)
+// 8 consecutive columns at taddr and at taddr2, under one wait.
+__device__ inline void tmem_ld8x2(uint32_t taddr, uint32_t taddr2, uint32_t* r, uint32_t* u)
 {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%32];\n"
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%33];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%16];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%17];\n"
         "tcgen05.wait::ld.sync.aligned;"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]),
-          "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15])
+          "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7])
         : "r"(taddr), "r"(taddr2)
         : "memory");
+}
+
+// (H, L) += t by TwoSum, two columns per FP32x2 instruction.  The roundings are
+// those of the scalar form: fma(x, -1, y) is y - x rounded once.
+__device__ __forceinline__ void two_sum2(float2& H, float2& L, float2 t)
+{
+    const float2 m1 = make_float2(-1.0f, -1.0f);
+    const float2 sm = __fadd2_rn(H, t);
+    const float2 bp = __ffma2_rn(H, m1, sm);  // sm - H
+    const float2 q = __ffma2_rn(bp, m1, sm);  // sm - bp
+    const float2 e1 = __ffma2_rn(q, m1, H);   // H - (sm - bp)
+    const float2 e2 = __ffma2_rn(bp, m1, t);  // t - bp
+    H = sm;
+    L = __fadd2_rn(L, __fadd2_rn(e1, e2));
 }
 
 // The products (s, L - 2 - s) of level L: two MMAs (K = 16 each) per product.
@@ -1283,9 +1299,9 @@ __global__ void __launch_bounds__(EMU_THREADS, 1)
             const Item item = item_of(a, j);
             const int gi = item.I * TM + r;  // row within the instance
             const bool row_ok = gi < item.rows;
-            float H[EMU_CPT], L[EMU_CPT];
+            float2 H[EMU_CPT / 2], L[EMU_CPT / 2];  // column pairs
 #pragma unroll
-            for (int c = 0; c < EMU_CPT; ++c) H[c] = L[c] = 0.f;
+            for (int c = 0; c < EMU_CPT / 2; ++c) H[c] = L[c] = make_float2(0.f, 0.f);
             const int emax_r = row_ok ? a.emaxA[item.roff + gi] : 0;
             const int nsteps = item.ks1 - item.ks0;
             const int nch = (nsteps + EMU_CH - 1) / EMU_CH;
@@ -1331,37 +1347,47 @@ __global__ void __launch_bounds__(EMU_THREADS, 1)
                 }
                 tc_fence_after();
                 const float rs = rowsc[ch * TM + r];
-                float sc[EMU_CPT];
+                float2 sc[EMU_CPT / 2];
 #pragma unroll
-                for (int c = 0; c < EMU_CPT; ++c) sc[c] = __fmul_rn(rs, colsc[ch * EMU_N + g * EMU_CPT + c]);  // exact
+                for (int c = 0; c < EMU_CPT / 2; ++c)  // exact
+                    sc[c] = __fmul2_rn(make_float2(rs, rs), make_float2(colsc[ch * EMU_N + g * EMU_CPT + 2 * c],
+                                                                      colsc[ch * EMU_N + g * EMU_CPT + 2 * c + 1]));
                 // L5, L4, L3, L2: exact level sums, added into (H, L) by TwoSum
 #pragma unroll
-                for (int lv = 0; lv < 4; ++lv) {
-                    uint32_t v[EMU_CPT];
-                    tmem_ld16(lane_addr + (uint32_t)((3 - lv) * 64), v);
+                for (int lv = 0; lv < 4; ++lv)
 #pragma unroll
-                    for (int c = 0; c < EMU_CPT; ++c) {
-                        const float t = __fmul_rn(__uint_as_float(v[c]), sc[c]);
-                        const float sm = __fadd_rn(H[c], t);
-                        const float bp = __fsub_rn(sm, H[c]);
-                        const float err = __fadd_rn(__fsub_rn(H[c], __fsub_rn(sm, bp)), __fsub_rn(t, bp));
-                        H[c] = sm;
-                        L[c] = __fadd_rn(L[c], err);
+                    for (int half = 0; half < 2; ++half) {  // 8 columns at a time: fewer live registers
+                        uint32_t v[EMU_CPT / 2];
+                        tmem_ld8(lane_addr + (uint32_t)((3 - lv) * 64 + 8 * half), v);
+#pragma unroll
+                        for (int cc = 0; cc < EMU_CPT / 4; ++cc) {
+                            const int c = half * (EMU_CPT / 4) + cc;
+                            two_sum2(H[c], L[c],
+                                     __fmul2_rn(make_float2(__uint_as_float(v[2 * cc]), __uint_as_float(v[2 * cc + 1])),
+                                                sc[c]));
+                        }
                     }
-                }
                 tc_fence_before();
                 asm volatile("bar.sync 1, 512;" ::: "memory");  // L2..L5 fully read
                 if (dt == 0) mbar_arrive(lo_empty);
                 // L6 and L7+8: below 2^-29 of the chunk's scale, added into the low part
                 const uint32_t hi = lane_addr + 256u + (uint32_t)((chunk & 1) * 128);
-                uint32_t v6[EMU_CPT], v78[EMU_CPT];
-                tmem_ld16x2(hi, hi + 64u, v6, v78);
 #pragma unroll
-                for (int c = 0; c < EMU_CPT; ++c) {
-                    L[c] = fmaf(__fadd_rn(__uint_as_float(v6[c]), __uint_as_float(v78[c])), sc[c], L[c]);
-                    const float sm = __fadd_rn(H[c], L[c]);  // renormalise (Fast2Sum)
-                    L[c] = __fsub_rn(L[c], __fsub_rn(sm, H[c]));
-                    H[c] = sm;
+                for (int half = 0; half < 2; ++half) {  // 8 columns at a time: fewer live registers
+                    uint32_t v6[EMU_CPT / 2], v78[EMU_CPT / 2];
+                    tmem_ld8x2(hi + (uint32_t)(8 * half), hi + 64u + (uint32_t)(8 * half), v6, v78);
+#pragma unroll
+                    for (int cc = 0; cc < EMU_CPT / 4; ++cc) {
+                        const int c = half * (EMU_CPT / 4) + cc;
+                        const float2 m1 = make_float2(-1.0f, -1.0f);
+                        const float2 h =
+                            __fadd2_rn(make_float2(__uint_as_float(v6[2 * cc]), __uint_as_float(v6[2 * cc + 1])),
+                                       make_float2(__uint_as_float(v78[2 * cc]), __uint_as_float(v78[2 * cc + 1])));
+                        L[c] = __ffma2_rn(h, sc[c], L[c]);
+                        const float2 sm = __fadd2_rn(H[c], L[c]);              // renormalise (Fast2Sum)
+                        L[c] = __ffma2_rn(__ffma2_rn(H[c], m1, sm), m1, L[c]);  // L - (sm - H)
+                        H[c] = sm;
+                    }
                 }
                 tc_fence_before();
                 asm volatile("bar.sync 1, 512;" ::: "memory");  // L6, L7+8 and the scales fully read
@@ -1378,7 +1404,8 @@ __global__ void __launch_bounds__(EMU_THREADS, 1)
                 double out = 0.0;
                 if (row_ok && emax_r != EXP_NONE && ec != EXP_NONE) {
                     const int k = emax_r + ec;
-                    out = f32_scaled_to_f64(H[c], k) + f32_scaled_to_f64(L[c], k);
+                    const float hc = (c & 1) ? H[c / 2].y : H[c / 2].x, lc = (c & 1) ? L[c / 2].y : L[c / 2].x;
+                    out = f32_scaled_to_f64(hc, k) + f32_scaled_to_f64(lc, k);
                 }
                 slot[c] = out;
             }
