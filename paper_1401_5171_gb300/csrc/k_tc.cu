@@ -523,15 +523,33 @@ __device__ __host__ inline int pieces_of(int K, int tri, int ks, int piece, int 
 }
 __device__ __host__ inline int pieces_of(const TcArgs& a, int I) { return pieces_of(a.K, a.tri, a.ks, a.piece, I); }
 
-__global__ void item_prefix_kernel(TcArgs a, int* cum)
+// cum[I] = items of row tiles 0..I-1 (I = 0..rt).  One block of 256 threads:
+// each thread sums a contiguous run of tiles, the runs' sums are scanned by
+// warp shuffles, and each thread then writes its run's prefixes.
+constexpr int PREFIX_THREADS = 256;
+__global__ void __launch_bounds__(PREFIX_THREADS) item_prefix_kernel(TcArgs a, int* cum)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    int s = 0;
-    for (int I = 0; I < a.rt; ++I) {
+    __shared__ int wsum[PREFIX_THREADS / 32];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int run = (a.rt + PREFIX_THREADS - 1) / PREFIX_THREADS;
+    const int I0 = t * run, I1 = min(a.rt, I0 + run);
+    int mine = 0;
+    for (int I = I0; I < I1; ++I) mine += pieces_of(a, I) * a.cc;
+    int incl = mine;  // inclusive scan within the warp
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    int base = 0;
+    for (int k = 0; k < w; ++k) base += wsum[k];
+    int s = base + incl - mine;  // exclusive prefix of this thread's run
+    for (int I = I0; I < I1; ++I) {
         cum[I] = s;
         s += pieces_of(a, I) * a.cc;
     }
-    cum[a.rt] = s;
+    if (t == PREFIX_THREADS - 1) cum[a.rt] = s;  // the last run ends at rt (its run may be empty)
 }
 
 // A work item: row tile I, k-steps [ks0, ks1), column chunk c, of the
@@ -948,6 +966,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
 }
 
+// x 2^k as a double, exact: for a normal x with the result in the normal range
+// the double is assembled from x's sign, exponent and significand with integer
+// operations (no FP64 instruction); otherwise by conversion and ldexp.
+__device__ inline double f32_scaled_to_f64(float x, int k)
+{
+    const unsigned u = __float_as_uint(x);
+    const int ex = (int)((u >> 23) & 0xFF);
+    const int e64 = ex - 127 + k + 1023;
+    if (ex != 0 && ex != 0xFF && e64 >= 1 && e64 <= 2046) {
+        const unsigned long long b = ((unsigned long long)(u >> 31) << 63) | ((unsigned long long)e64 << 52) |
+                                     ((unsigned long long)(u & 0x7FFFFF) << 29);
+        return __longlong_as_double((long long)b);
+    }
+    return x == 0.0f ? 0.0 : ldexp((double)x, k);
+}
+
 // out (rowsA x colsB, column-major, ldo) = sum over the pieces of each tile.
 template <int N>
 __global__ void slot_reduce_kernel(TcArgs a, double* out, long ldo, const DevStatus* st)
@@ -984,7 +1018,7 @@ __global__ void slot_reduce_f32_kernel(TcArgs a, double* out, long ldo, const De
         s += slots[(size_t)j * TM * N + (size_t)(row % TM) * N + (col % N)];
     }
     const int er = a.emaxA[row], ec = a.emaxB[col];
-    out[row + (long)col * ldo] = (er == EXP_NONE || ec == EXP_NONE) ? 0.0 : ldexp((double)s, er + ec);
+    out[row + (long)col * ldo] = (er == EXP_NONE || ec == EXP_NONE) ? 0.0 : f32_scaled_to_f64(s, er + ec);
 }
 
 // A packed batch: every instance's output (rows x cols, column-major, ldo) is
@@ -1013,7 +1047,7 @@ __global__ void slot_reduce_batch_kernel(TcArgs a)
             s += slots[(size_t)j * TM * N + (size_t)(row % TM) * N + (col % N)];
         }
         const int er = a.emaxA[I.roff + row], ec = a.emaxB[I.coff + col];
-        r = (er == EXP_NONE || ec == EXP_NONE) ? 0.0 : ldexp((double)s, er + ec);
+        r = (er == EXP_NONE || ec == EXP_NONE) ? 0.0 : f32_scaled_to_f64(s, er + ec);
     } else {
         double s = 0.0;
         for (int p = 0; p < np; ++p) {
@@ -1071,22 +1105,6 @@ constexpr int EMU_MAXCH = 2048 / KCH_EMU;           // chunks per item (items ar
 // align slack + stages + barriers and flags + an item's row and column chunk scales
 constexpr size_t EMU_SMEM = 1024 + (size_t)EMU_STAGES * EMU_STAGE + 1024 + (size_t)EMU_MAXCH * (TM + EMU_N) * 4;
 static_assert(EMU_STAGE % 1024 == 0, "stage alignment");
-
-// x 2^k as a double, exact: for a normal x with the result in the normal range
-// the double is assembled from x's sign, exponent and significand with integer
-// operations (no FP64 instruction); otherwise by conversion and ldexp.
-__device__ inline double f32_scaled_to_f64(float x, int k)
-{
-    const unsigned u = __float_as_uint(x);
-    const int ex = (int)((u >> 23) & 0xFF);
-    const int e64 = ex - 127 + k + 1023;
-    if (ex != 0 && ex != 0xFF && e64 >= 1 && e64 <= 2046) {
-        const unsigned long long b = ((unsigned long long)(u >> 31) << 63) | ((unsigned long long)e64 << 52) |
-                                     ((unsigned long long)(u & 0x7FFFFF) << 29);
-        return __longlong_as_double((long long)b);
-    }
-    return x == 0.0f ? 0.0 : ldexp((double)x, k);
-}
 
 // 8 consecutive accumulator columns of this thread's TMEM lane; the load and
 // its wait are one asm statement, so no use of r can precede the wait.
@@ -1656,7 +1674,7 @@ cudaError_t launch_tc_gram(const TcPlan& p, const double* A, long lda, const dou
     a1.emaxB = L.mZ;
     a1.st = st;
     a1.limit_ns = limit_ns;
-    item_prefix_kernel<<<1, 32, 0, s>>>(a1, L.cum1);
+    item_prefix_kernel<<<1, PREFIX_THREADS, 0, s>>>(a1, L.cum1);
     mark(1);
     if ((e = launch_tc_mode(p, a1, L.Ap, planeA, L.Zp, planeZ, sms, s)) != cudaSuccess) return e;
     mark(2);
@@ -1672,7 +1690,7 @@ cudaError_t launch_tc_gram(const TcPlan& p, const double* A, long lda, const dou
     a2.emaxB = L.mU;
     a2.st = st;
     a2.limit_ns = limit_ns;
-    item_prefix_kernel<<<1, 32, 0, s>>>(a2, L.cum2);
+    item_prefix_kernel<<<1, PREFIX_THREADS, 0, s>>>(a2, L.cum2);
     mark(3);
     if ((e = launch_tc_mode(p, a2, L.Zp, planeZ, L.Up, planeZ, sms, s)) != cudaSuccess) return e;
     mark(4);
@@ -1763,7 +1781,7 @@ cudaError_t launch_trsm_tc(int m, int n, const double* Z, long ldz, const double
             a.emaxB = L.mY;
             a.st = st;
             a.limit_ns = limit_ns;
-            item_prefix_kernel<<<1, 32, 0, s>>>(a, L.cum);
+            item_prefix_kernel<<<1, PREFIX_THREADS, 0, s>>>(a, L.cum);
             if ((e = launch_emu(a, L.Xp, L.ldp, planeX, L.Yp, L.ldp, planeY, sms, s)) != cudaSuccess) return e;
             slot_reduce_kernel<EMU_N><<<(unsigned)(((long)m * bw + 255) / 256), 256, 0, s>>>(a, L.U, m, st);
             U = L.U;
