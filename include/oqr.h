@@ -47,7 +47,7 @@ typedef enum {
     OQR_ERR_CUDA = 4,          /* a CUDA runtime call failed */
     OQR_ERR_NO_MEMORY = 5,     /* workspace could not be allocated or is too small */
     OQR_ERR_TIMEOUT = 6,       /* a device-side wait ran past spin_limit */
-    OQR_ERR_UNSUPPORTED = 7    /* size or option outside what this build supports */
+    OQR_ERR_UNSUPPORTED = 7    /* size or option outside what the library supports */
 } oqr_status;
 
 typedef enum {

@@ -505,7 +505,7 @@ const char* oqr_status_string(oqr_status s)
         case OQR_ERR_CUDA: return "OQR_ERR_CUDA: CUDA runtime error";
         case OQR_ERR_NO_MEMORY: return "OQR_ERR_NO_MEMORY: workspace unavailable";
         case OQR_ERR_TIMEOUT: return "OQR_ERR_TIMEOUT: device-side wait timed out";
-        case OQR_ERR_UNSUPPORTED: return "OQR_ERR_UNSUPPORTED: not supported by this build";
+        case OQR_ERR_UNSUPPORTED: return "OQR_ERR_UNSUPPORTED: size or option not supported by the library";
     }
     return "unknown oqr_status";
 }
