@@ -871,7 +871,8 @@ oqr_status oqr_batched_mixed(oqr_ctx* ctx, int count, const int* m, const int* n
     std::stable_sort(perm.begin(), perm.end(), [&](int x, int y) { return m[x] > m[y]; });
     std::vector<TcBatchShape> sh((size_t)count);
     std::vector<int> shifted((size_t)count, 0);
-    std::vector<long> key{count, 0, (long)reinterpret_cast<uintptr_t>(status)};
+    // the graph writes status (and orth) directly: their addresses are part of its signature
+    std::vector<long> key{count, 0, (long)reinterpret_cast<uintptr_t>(status), (long)reinterpret_cast<uintptr_t>(orth)};
     size_t pool_doubles = 0;
     for (int i = 0; i < count; ++i) {
         const int b = perm[i];

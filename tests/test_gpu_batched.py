@@ -315,3 +315,22 @@ def test_selector_solve_batch_completes(env):
         floor = 100 * U * np.linalg.eigvalsh(A).max() * np.linalg.norm(Qr, 2) ** 2
         assert oracle.orth_error(A, Q) <= max(1e-12, 10 * oracle.orth_error(A, Qr), floor)
         assert np.linalg.norm(Z - Q @ R, 2) / np.linalg.norm(Z, 2) <= 1e-13
+
+
+def test_batched_check_graph_replay_new_outputs(env):
+    """A replay of the cached graph writes this call's status and orth arrays, not the first call's."""
+    torch, oqr, ctx = env
+    As, Zs, _ = inputs.batch_instances(5, seed=61, device="cuda", m_range=(64, 300), n_range=(4, 32),
+                                       log_kappa_a=(0.0, 2.0), log_kappa_z=(2.0, 3.0))
+    s = torch.cuda.Stream()
+    progs = [oqr.OQR_BATCH_CHOLQR_TC] * len(Zs)
+    with torch.cuda.stream(s):
+        _, R1, st1, o1 = ctx.oqr_batched_mixed(As, Zs, program=progs, stream=s, check=True)
+        st2 = torch.full_like(st1, 77)
+        _, R2, st2, o2 = ctx.oqr_batched_mixed(As, Zs, program=progs, stream=s, check=True, status=st2)
+    torch.cuda.synchronize()
+    assert o1.data_ptr() != o2.data_ptr()
+    assert torch.equal(st2, st1) and st1.abs().sum().item() == 0
+    assert torch.equal(o1, o2) and bool(torch.all(o2 > 0))
+    for a, b in zip(R1, R2):
+        assert torch.equal(a, b)
