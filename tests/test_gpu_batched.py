@@ -326,10 +326,10 @@ def test_batched_check_graph_replay_new_outputs(env):
     progs = [oqr.OQR_BATCH_CHOLQR_TC] * len(Zs)
     with torch.cuda.stream(s):
         _, R1, st1, o1 = ctx.oqr_batched_mixed(As, Zs, program=progs, stream=s, check=True)
-        o1 = o1.clone()
-        # the same status array, a new orth array (the binding allocates one per call)
+        # the same status array, a new orth array (the binding allocates one per call; o1 stays alive)
         _, R2, st2, o2 = ctx.oqr_batched_mixed(As, Zs, program=progs, stream=s, check=True, status=st1)
     torch.cuda.synchronize()
+    assert o1.data_ptr() != o2.data_ptr()
     assert st1.abs().sum().item() == 0
     assert torch.equal(o1, o2) and bool(torch.all(o2 > 0))
     for a, b in zip(R1, R2):
