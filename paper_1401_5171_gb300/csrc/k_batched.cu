@@ -12,6 +12,13 @@
 //   potrf_batched  one CTA per instance, G_b (<= 64 x 64) in shared memory.
 //   trsm_batched   grid (row block, instance): Q_b = Z_b / R_b row by row.
 //   rprod_batched  R_b = R_2 R_1.
+// The tensor-core batches (packed waves, k_tc.cu) form the Grams' halves C_b
+// on the tensor cores and use the same descriptors for the FP64 steps, with
+// 1 to 3 passes per instance (BatchDesc.npass; instances whose passes are done
+// sit later passes out): reduce (+ s_b I on a shifted first pass), potrf,
+// trsm, racc_batched (R1 <- R2 R1 after every later pass), rfinal_batched
+// (the caller's R = R1), norms/shift_batched (the first pass's shift) and
+// check_batched (||Q^T A Q - I||_2 from one more Gram of Q).
 // A Cholesky breakdown is recorded in the instance's own status word and that
 // instance's later kernels skip it; other instances are unaffected.
 #include <math.h>
