@@ -220,6 +220,19 @@ oqr_status oqr_check(oqr_ctx* ctx, int m, int n, const double* A, long lda, cons
                      double* E, long lde, double* orth2, double* orthF, void* stream);
 
 /*
+ * oqr_repres: Sec. 7's representativity measure of a factorization,
+ * ||Z - Q R||_2 / ||Z||_2, in *res2 (the two 2-norms estimated by power
+ * iteration on D^T D and Z^T Z, D = Z - Q R formed in FP64; lower bounds that
+ * converge to them), and ||Z - Q R||_F / ||Z||_F in *resF (host pointers, may
+ * be NULL).  Z, Q (m x n) and R (n x n, read in full) are column-major device
+ * memory; 1 <= n <= min(m, 1024) (n above 1024 returns OQR_ERR_UNSUPPORTED).
+ * Uses the context's workspace (m n + 2 n^2 doubles and split-K partials) and
+ * synchronizes the stream.
+ */
+oqr_status oqr_repres(oqr_ctx* ctx, int m, int n, const double* Z, long ldz, const double* Q, long ldq,
+                      const double* R, long ldr, double* res2, double* resF, void* stream);
+
+/*
  * Batched A-CholQR2 (FP64): `count` independent oblique QRs, instance b with
  * A_b (m[b] x m[b], lower triangle read), Z_b (m[b] x n[b]) -> Q_b, R_b, all
  * column-major FP64 device memory, 1 <= n[b] <= min(m[b], 64), m[b] <= 4096.

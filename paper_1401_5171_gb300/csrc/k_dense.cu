@@ -323,6 +323,61 @@ __global__ void copy_upper_kernel(int n, const double* __restrict__ S, long lds,
     D[i + (long)j * ldd] = i <= j ? S[i + (long)j * lds] : 0.0;
 }
 
+// --------------------------------------------------- 2-norm of a Gram -----
+// For symmetric positive semidefinite S (n x n, column-major): out[0] = an
+// estimate of lambda_max(S) (power iteration, a lower bound that converges to
+// it), out[1] = trace(S).  One CTA; x and y in shared memory.
+constexpr int LMAX_THREADS = 256;
+constexpr int LMAX_ITERS = 60;
+__global__ void __launch_bounds__(LMAX_THREADS) lambda_max_kernel(int n, const double* __restrict__ S, long lds,
+                                                                  double* x, double* y, double* out)
+{
+    __shared__ double red[LMAX_THREADS / 32];
+    __shared__ double bc[2];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    auto bsum = [&](double v) {
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        __syncthreads();
+        if (lane == 0) red[w] = v;
+        __syncthreads();
+        double r = 0.0;
+        for (int k = 0; k < LMAX_THREADS / 32; ++k) r += red[k];
+        return r;
+    };
+    double tr = 0.0;
+    for (int i = t; i < n; i += LMAX_THREADS) {
+        tr += S[i + (long)i * lds];
+        x[i] = 1.0 + 1e-3 * (i % 7);  // not orthogonal to the dominant eigenvector of a nonnegative S
+    }
+    tr = bsum(tr);
+    double best = 0.0;
+    for (int it = 0; it < LMAX_ITERS; ++it) {
+        __syncthreads();
+        double ny = 0.0, nx = 0.0;
+        for (int i = t; i < n; i += LMAX_THREADS) {
+            double v = 0.0;
+            for (int j = 0; j < n; ++j) v = fma(S[j + (long)i * lds], x[j], v);  // S symmetric: row i = column i
+            y[i] = v;
+            ny += v * v;
+            nx += x[i] * x[i];
+        }
+        ny = bsum(ny);
+        nx = bsum(nx);
+        if (t == 0) {
+            bc[0] = nx > 0.0 ? sqrt(ny / nx) : 0.0;
+            bc[1] = ny > 0.0 ? 1.0 / sqrt(ny) : 0.0;
+        }
+        __syncthreads();
+        best = fmax(best, bc[0]);
+        if (bc[1] == 0.0) break;
+        for (int i = t; i < n; i += LMAX_THREADS) x[i] = y[i] * bc[1];
+    }
+    if (t == 0) {
+        out[0] = best;
+        out[1] = tr;
+    }
+}
+
 // ------------------------------------------------------- norms and shift ---
 // Partial sums of ||A||_F^2 over the lower triangle (off-diagonal twice) and
 // of ||Z||_F^2; block b handles columns b, b + gridDim.x, ...
@@ -623,6 +678,12 @@ cudaError_t launch_gemm_f64(GemmOp op, int M, int N, int K, double alpha, const 
         gemm_splitk_reduce_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(M, N, splits, alpha, splitk_ws,
                                                                                  beta, C, ldc);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lambda_max(int n, const double* S, long lds, double* work, double* out, cudaStream_t s)
+{
+    lambda_max_kernel<<<1, LMAX_THREADS, 0, s>>>(n, S, lds, work, work + n, out);
     return cudaGetLastError();
 }
 

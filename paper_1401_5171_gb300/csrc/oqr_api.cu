@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <new>
 #include <vector>
 
@@ -1154,6 +1155,45 @@ oqr_status oqr_check(oqr_ctx* ctx, int m, int n, const double* A, long lda, cons
         if (orthF) *orthF = h.orthF;
         return static_cast<oqr_status>(h.code);
     }
+    return OQR_OK;
+}
+
+oqr_status oqr_repres(oqr_ctx* ctx, int m, int n, const double* Z, long ldz, const double* Q, long ldq,
+                      const double* R, long ldr, double* res2, double* resF, void* stream)
+{
+    if (!ctx || m < 1 || n < 1 || n > m || bad_matrix(Z, ldz, m, n) || bad_matrix(Q, ldq, m, n) ||
+        bad_matrix(R, ldr, n, n))
+        return OQR_ERR_INVALID_ARG;
+    if (n > 1024) return OQR_ERR_UNSUPPORTED;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // D = Z - Q R (m x n), S = D^T D and T = Z^T Z (split along m), then their largest eigenvalues and traces
+    const int splits = std::max(1, std::min(64, m / 512));
+    Carve probe(nullptr);
+    auto layout = [&](Carve& c, double** D, double** S, double** T, double** ws, double** work, double** out) {
+        *D = c.take<double>((size_t)m * n);
+        *S = c.take<double>((size_t)n * n);
+        *T = c.take<double>((size_t)n * n);
+        *ws = c.take<double>(gemm_splitk_bytes(n, n, splits) / sizeof(double) + 1);
+        *work = c.take<double>((size_t)2 * n);
+        *out = c.take<double>(4);
+    };
+    double *D, *S, *T, *ws, *work, *out;
+    layout(probe, &D, &S, &T, &ws, &work, &out);
+    oqr_status v = ensure_ws(ctx, probe.off);
+    if (v != OQR_OK) return v;
+    Carve c(ctx->ws);
+    layout(c, &D, &S, &T, &ws, &work, &out);
+    OQR_TRY(cudaMemcpy2DAsync(D, (size_t)m * 8, Z, (size_t)ldz * 8, (size_t)m * 8, n, cudaMemcpyDeviceToDevice, s));
+    OQR_TRY(launch_gemm_f64(GEMM_N, m, n, n, -1.0, Q, ldq, R, ldr, 1.0, D, m, nullptr, 1, s));
+    OQR_TRY(launch_gemm_f64(GEMM_T, n, n, m, 1.0, D, m, D, m, 0.0, S, n, ws, splits, s));
+    OQR_TRY(launch_gemm_f64(GEMM_T, n, n, m, 1.0, Z, ldz, Z, ldz, 0.0, T, n, ws, splits, s));
+    OQR_TRY(launch_lambda_max(n, S, n, work, out, s));
+    OQR_TRY(launch_lambda_max(n, T, n, work, out + 2, s));
+    double h[4];
+    OQR_TRY(cudaMemcpyAsync(h, out, sizeof(h), cudaMemcpyDeviceToHost, s));
+    if (cudaStreamSynchronize(s) != cudaSuccess) return OQR_ERR_CUDA;
+    if (res2) *res2 = h[2] > 0.0 ? std::sqrt(h[0] / h[2]) : 0.0;
+    if (resF) *resF = h[3] > 0.0 ? std::sqrt(h[1] / h[3]) : 0.0;
     return OQR_OK;
 }
 

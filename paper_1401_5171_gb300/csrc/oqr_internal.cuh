@@ -168,6 +168,9 @@ cudaError_t launch_norms_and_shift(int m, int n, const double* A, long lda, cons
 // Orthogonality check: E = G - I given G (n x n); writes E (if non-NULL),
 // orth2 (power-iteration estimate of ||E||_2) and orthF into st.  work holds
 // n*n + 2n doubles.
+// out[0] = lambda_max(S) estimate (power iteration), out[1] = trace(S), for
+// symmetric positive semidefinite S (n x n); work: 2 n doubles.
+cudaError_t launch_lambda_max(int n, const double* S, long lds, double* work, double* out, cudaStream_t s);
 cudaError_t launch_check_finish(int n, const double* G, long ldg, double* E, long lde, double* work,
                                 DevStatus* st, cudaStream_t s);
 

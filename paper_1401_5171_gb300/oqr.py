@@ -106,6 +106,7 @@ def load(path: str | None = None):
     lib.oqr_cholqr2_host.argtypes = [vp, i, i, vp, l, vp, l, vp, l, vp, l, po, pi, vp]
     lib.oqr_rprod.argtypes = [vp, i, vp, l, vp, l, vp, l, vp]
     lib.oqr_check.argtypes = [vp, i, i, vp, l, vp, l, vp, l, ctypes.POINTER(d), ctypes.POINTER(d), vp]
+    lib.oqr_repres.argtypes = [vp, i, i, vp, l, vp, l, vp, l, ctypes.POINTER(d), ctypes.POINTER(d), vp]
     for name in declared_functions():
         f = getattr(lib, name)
         if f.restype is ctypes.c_int or name not in ("oqr_default_opts", "oqr_status_string"):
@@ -129,7 +130,7 @@ def _raw(name):
 
 for _n in ("oqr_default_opts", "oqr_create", "oqr_destroy", "oqr_workspace_size", "oqr_set_workspace",
            "oqr_get_status", "oqr_cholqr", "oqr_cholqr2", "oqr_cholqr2_host", "oqr_cgs2", "oqr_gram", "oqr_gram_noalloc", "oqr_gram_phases", "oqr_potrf", "oqr_trsm", "oqr_trsm_tc",
-           "oqr_rprod", "oqr_check", "oqr_batched", "oqr_batched_mixed", "oqr_batched_default_splits", "oqr_features",
+           "oqr_rprod", "oqr_check", "oqr_repres", "oqr_batched", "oqr_batched_mixed", "oqr_batched_default_splits", "oqr_features",
            "oqr_mlp_param_count", "oqr_mlp_forward", "oqr_mlp_grad", "oqr_mlp_adam"):
     globals()[_n] = _raw(_n)
 
@@ -411,3 +412,16 @@ class Oqr:
         if st != OQR_OK:
             raise OqrError(st, "oqr_check")
         return o2.value, of.value, E
+
+    def oqr_repres(self, Z, Q, R, stream=None):
+        """(||Z - Q R||_2 / ||Z||_2 estimate, ||Z - Q R||_F / ||Z||_F)."""
+        m, n = Z.shape
+        z, ldz = _m(Z)
+        q, ldq = _m(Q)
+        r, ldr = _m(R)
+        r2, rf = ctypes.c_double(), ctypes.c_double()
+        st = self.lib.oqr_repres(self.ctx, m, n, z, ldz, q, ldq, r, ldr, ctypes.byref(r2), ctypes.byref(rf),
+                                 self._stream(stream))
+        if st != OQR_OK:
+            raise OqrError(st, "oqr_repres")
+        return r2.value, rf.value

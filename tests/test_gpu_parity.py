@@ -313,3 +313,38 @@ def test_config1_full_size_properties(env, shifted):
     assert orth < 1e-11 and rep < 1e-13
     del Af, A, AQ, G
     torch.cuda.empty_cache()
+
+
+def test_repres_planted_residual(env):
+    """oqr_repres on Z' = Q R + E with a planted rank-one E and a clear top singular value of Z':
+    both ratios against numpy's norms."""
+    torch, oqr, ctx = env
+    rng = np.random.default_rng(71)
+    m, n = 900, 40
+    Uz, _ = np.linalg.qr(rng.standard_normal((m, n)))
+    Wz, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    sig = np.concatenate([[10.0], np.linspace(1.0, 0.1, n - 1)])
+    Z = (Uz * sig) @ Wz.T
+    Qh, Rh = np.linalg.qr(Z)
+    D = np.sign(np.diag(Rh))
+    Q, R = Qh * D, (Rh.T * D).T                        # Z = Q R, R upper with a positive diagonal
+    u, v = rng.standard_normal(m), rng.standard_normal(n)
+    E = 1e-5 * np.outer(u / np.linalg.norm(u), v / np.linalg.norm(v))   # far above Q R's rounding
+    Zp = Z + E
+    r2, rf = ctx.oqr_repres(*(oqr.colmajor(torch.as_tensor(x).cuda()) for x in (Zp, Q, R)))
+    ref2 = np.linalg.norm(Zp - Q @ R, 2) / np.linalg.norm(Zp, 2)
+    refF = np.linalg.norm(Zp - Q @ R) / np.linalg.norm(Zp)
+    assert abs(r2 - ref2) <= 1e-6 * ref2
+    assert abs(rf - refF) <= 1e-6 * refF
+
+
+def test_repres_of_factorization(env):
+    """The representativity of an A-CholQR2 result is at the rounding level (Sec. 7: about 1e-15)."""
+    torch, oqr, ctx = env
+    A, Z = inputs.paper_case(4, 700, 30, 1e6, 1e4, seed=3)
+    Ad, Zd = (oqr.colmajor(torch.as_tensor(x).cuda()) for x in (A, Z))
+    Q, R, _ = ctx.oqr_cholqr2(Ad, Zd)
+    r2, rf = ctx.oqr_repres(Zd, Q, R)
+    ref = oracle.repres_error(Z, Q.cpu().numpy(), R.cpu().numpy())
+    assert r2 <= max(4 * ref, 1e-15) and r2 <= 1e-13
+    assert rf <= 1e-13
