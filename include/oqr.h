@@ -220,6 +220,16 @@ oqr_status oqr_check(oqr_ctx* ctx, int m, int n, const double* A, long lda, cons
                      double* E, long lde, double* orth2, double* orthF, void* stream);
 
 /*
+ * Diagnostic of the failure path: one device-side wait that nothing
+ * completes, limited to limit_ns (1 ns .. 10 s), after which the kernel records
+ * OQR_ERR_TIMEOUT in the context's status (read it with oqr_get_status), as
+ * every time-limited wait of the library does.  Nothing asynchronous is in
+ * flight when it gives up, so the context stays usable; the next call resets
+ * the status.  Asynchronous.
+ */
+oqr_status oqr_diag_timeout(oqr_ctx* ctx, long limit_ns, void* stream);
+
+/*
  * oqr_repres: Sec. 7's representativity measure of a factorization,
  * ||Z - Q R||_2 / ||Z||_2, in *res2 (the two 2-norms estimated by power
  * iteration on D^T D and Z^T Z, D = Z - Q R formed in FP64; lower bounds that

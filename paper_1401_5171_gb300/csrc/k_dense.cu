@@ -323,6 +323,19 @@ __global__ void copy_upper_kernel(int n, const double* __restrict__ S, long lds,
     D[i + (long)j * ldd] = i <= j ? S[i + (long)j * lds] : 0.0;
 }
 
+// ------------------------------------------------------ timeout probe ------
+// One thread waits on an mbarrier that no thread arrives at, for limit_ns, then
+// records OQR_ERR_TIMEOUT: the path every time-limited wait of the library takes,
+// here with no copy or MMA in flight, so the context stays usable.
+__global__ void timeout_probe_kernel(DevStatus* st, uint64_t limit_ns)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    fence_barrier_init();
+    if (!mbar_wait(&bar, 0, limit_ns)) raise_status(st, OQR_ERR_TIMEOUT, 0, TAG_DIAG);
+}
+
 // --------------------------------------------------- 2-norm of a Gram -----
 // For symmetric positive semidefinite S (n x n, column-major): out[0] = an
 // estimate of lambda_max(S) (power iteration, a lower bound that converges to
@@ -684,6 +697,12 @@ cudaError_t launch_gemm_f64(GemmOp op, int M, int N, int K, double alpha, const 
 cudaError_t launch_lambda_max(int n, const double* S, long lds, double* work, double* out, cudaStream_t s)
 {
     lambda_max_kernel<<<1, LMAX_THREADS, 0, s>>>(n, S, lds, work, work + n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_timeout_probe(DevStatus* st, uint64_t limit_ns, cudaStream_t s)
+{
+    timeout_probe_kernel<<<1, 32, 0, s>>>(st, limit_ns);
     return cudaGetLastError();
 }
 

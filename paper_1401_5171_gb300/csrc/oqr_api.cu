@@ -1158,6 +1158,16 @@ oqr_status oqr_check(oqr_ctx* ctx, int m, int n, const double* A, long lda, cons
     return OQR_OK;
 }
 
+oqr_status oqr_diag_timeout(oqr_ctx* ctx, long limit_ns, void* stream)
+{
+    if (!ctx || limit_ns < 1 || limit_ns > 10000000000L) return OQR_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    oqr_status v = reset_status(ctx, s);
+    if (v != OQR_OK) return v;
+    OQR_TRY(launch_timeout_probe(ctx->st, (uint64_t)limit_ns, s));
+    return OQR_OK;
+}
+
 oqr_status oqr_repres(oqr_ctx* ctx, int m, int n, const double* Z, long ldz, const double* Q, long ldq,
                       const double* R, long ldr, double* res2, double* resF, void* stream)
 {

@@ -32,7 +32,7 @@ struct DevStatus {
 static_assert(sizeof(DevStatus) == 96, "status layout");
 
 enum KernelTag { TAG_GRAM = 1, TAG_POTRF = 2, TAG_TRSM = 3, TAG_GEMM = 4, TAG_CHECK = 5, TAG_MIXED = 6,
-                 TAG_BATCH = 7 };
+                 TAG_BATCH = 7, TAG_DIAG = 8 };
 
 __device__ inline void raise_status(DevStatus* st, int code, int info, int where)
 {
@@ -168,6 +168,9 @@ cudaError_t launch_norms_and_shift(int m, int n, const double* A, long lda, cons
 // Orthogonality check: E = G - I given G (n x n); writes E (if non-NULL),
 // orth2 (power-iteration estimate of ||E||_2) and orthF into st.  work holds
 // n*n + 2n doubles.
+// A device-side wait that nothing completes, limited to limit_ns; records
+// OQR_ERR_TIMEOUT (the timeout path, with nothing asynchronous in flight).
+cudaError_t launch_timeout_probe(DevStatus* st, uint64_t limit_ns, cudaStream_t s);
 // out[0] = lambda_max(S) estimate (power iteration), out[1] = trace(S), for
 // symmetric positive semidefinite S (n x n); work: 2 n doubles.
 cudaError_t launch_lambda_max(int n, const double* S, long lds, double* work, double* out, cudaStream_t s);

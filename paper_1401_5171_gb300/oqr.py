@@ -107,6 +107,7 @@ def load(path: str | None = None):
     lib.oqr_rprod.argtypes = [vp, i, vp, l, vp, l, vp, l, vp]
     lib.oqr_check.argtypes = [vp, i, i, vp, l, vp, l, vp, l, ctypes.POINTER(d), ctypes.POINTER(d), vp]
     lib.oqr_repres.argtypes = [vp, i, i, vp, l, vp, l, vp, l, ctypes.POINTER(d), ctypes.POINTER(d), vp]
+    lib.oqr_diag_timeout.argtypes = [vp, l, vp]
     for name in declared_functions():
         f = getattr(lib, name)
         if f.restype is ctypes.c_int or name not in ("oqr_default_opts", "oqr_status_string"):
@@ -130,7 +131,7 @@ def _raw(name):
 
 for _n in ("oqr_default_opts", "oqr_create", "oqr_destroy", "oqr_workspace_size", "oqr_set_workspace",
            "oqr_get_status", "oqr_cholqr", "oqr_cholqr2", "oqr_cholqr2_host", "oqr_cgs2", "oqr_gram", "oqr_gram_noalloc", "oqr_gram_phases", "oqr_potrf", "oqr_trsm", "oqr_trsm_tc",
-           "oqr_rprod", "oqr_check", "oqr_repres", "oqr_batched", "oqr_batched_mixed", "oqr_batched_default_splits", "oqr_features",
+           "oqr_rprod", "oqr_check", "oqr_repres", "oqr_diag_timeout", "oqr_batched", "oqr_batched_mixed", "oqr_batched_default_splits", "oqr_features",
            "oqr_mlp_param_count", "oqr_mlp_forward", "oqr_mlp_grad", "oqr_mlp_adam"):
     globals()[_n] = _raw(_n)
 
@@ -412,6 +413,24 @@ class Oqr:
         if st != OQR_OK:
             raise OqrError(st, "oqr_check")
         return o2.value, of.value, E
+
+    def oqr_diag_timeout(self, limit_ns, stream=None):
+        """One device-side wait that nothing completes; returns the context's status afterwards."""
+        st = self.lib.oqr_diag_timeout(self.ctx, int(limit_ns), self._stream(stream))
+        if st != OQR_OK:
+            raise OqrError(st, "oqr_diag_timeout")
+        return self.status(stream)
+
+    def status(self, stream=None):
+        """The context's device-side status (synchronizes the stream)."""
+        info = ctypes.c_int(0)
+        return self.lib.oqr_get_status(self.ctx, self._stream(stream), ctypes.byref(info))
+
+    def set_workspace(self, ptr, nbytes):
+        """Hands the context a caller-owned device buffer (ptr = 0: the context allocates again)."""
+        st = self.lib.oqr_set_workspace(self.ctx, ctypes.c_void_p(ptr) if ptr else None, int(nbytes))
+        if st != OQR_OK:
+            raise OqrError(st, "oqr_set_workspace")
 
     def oqr_repres(self, Z, Q, R, stream=None):
         """(||Z - Q R||_2 / ||Z||_2 estimate, ||Z - Q R||_F / ||Z||_F)."""
