@@ -2,12 +2,15 @@
 // the step kernels into A-CholQR, A-CholQR2, shifted A-CholQR3 and A-CGS2.
 // Every arithmetic step runs in this library's CUDA kernels; the host only
 // validates, carves workspace and enqueues.
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
 #include <cmath>
 #include <new>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "oqr_internal.cuh"
 
@@ -36,6 +39,20 @@ struct oqr_ctx {
 namespace {
 
 constexpr double U64 = 1.1102230246251565e-16;  // 2^-53
+
+// An NVTX range over a scope (host side: the enqueue of a pass or a wave), for
+// profilers' timelines and for filtering kernels by range.
+struct NvtxRange {
+    explicit NvtxRange(const char* fmt, int k)
+    {
+        char buf[64];
+        snprintf(buf, sizeof(buf), fmt, k);
+        nvtxRangePushA(buf);
+    }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 constexpr int SHIFT_PARTS = 1024;
 constexpr int CGS_MAX_SPLITS = 64;
 constexpr int KCH_PANEL = 256;  // host-buffer path: columns per panel of A (the EMU64 exponent chunk)
@@ -346,6 +363,7 @@ oqr_status normal_equation(oqr_ctx* ctx, int m, int n, const double* A, long lda
     long ldx = ldz;
     double* Racc = nullptr;
     for (int p = 0; p < passes; ++p) {
+        const NvtxRange range("oqr: normal-equation pass %d", p + 1);
         double* Rp = (passes == 1) ? R : R1;
         const long ldrp = (passes == 1) ? ldr : n;
         const int prec = prec_of(p);
@@ -951,6 +969,7 @@ oqr_status oqr_batched_mixed(oqr_ctx* ctx, int count, const int* m, const int* n
     auto seq = [&]() -> cudaError_t {
         cudaError_t e;
         for (int w = 0; w < (int)plan.waves.size(); ++w) {
+            const NvtxRange range("oqr: batched wave %d", w);
             const TcBatchWave& W = plan.waves[w];
             const BatchDesc* dw = ddesc + W.first;
             int* sw = sts + W.first;
