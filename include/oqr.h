@@ -300,6 +300,12 @@ oqr_status oqr_batched_mixed(oqr_ctx* ctx, int count, const int* m, const int* n
                              const long* ldq, double* const* R, const long* ldr, const int* program, int* status,
                              double* orth, void* stream);
 
+/* The slice-plane bytes per wave of the tensor-core batches (oqr_batched_mixed;
+ * 0 restores the default of 16 GiB).  A wave always holds at least one
+ * instance, so a small budget gives one instance per wave.  Results do not
+ * depend on it; memory and the number of launches do. */
+oqr_status oqr_set_batch_budget(oqr_ctx* ctx, size_t bytes);
+
 /* The built-in work plan of oqr_batched for one instance (splits of its Gram). */
 int oqr_batched_default_splits(int m, int n);
 

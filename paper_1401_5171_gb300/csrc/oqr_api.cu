@@ -29,6 +29,7 @@ struct oqr_ctx {
     // the same for the batched tensor-core (mixed) sequence: its signature is every instance's shape
     cudaGraphExec_t mixed_exec = nullptr;
     std::vector<long> mixed_key;
+    size_t batch_budget = 0;  // slice-plane bytes per wave of the tensor-core batches (0: the default)
     // host-buffer path: device staging (A, Z, Q, R), a copy stream and one event per panel of A
     void* stage = nullptr;
     size_t stage_bytes = 0;
@@ -902,7 +903,9 @@ oqr_status oqr_batched_mixed(oqr_ctx* ctx, int count, const int* m, const int* n
         key.push_back(((long)m[b] << 32) | ((long)n[b] << 8) | (orth ? 4 : 0) | pr);
         pool_doubles += align256((size_t)4 * n[b] * n[b] * sizeof(double)) / sizeof(double);
     }
-    const TcBatchPlan plan = tc_batch_plan(sh, BATCH_WAVE_BYTES);
+    const size_t budget = ctx->batch_budget ? ctx->batch_budget : BATCH_WAVE_BYTES;
+    key.push_back((long)budget);
+    const TcBatchPlan plan = tc_batch_plan(sh, budget);
     auto layout = [&](Carve& c, char** tab, BatchDesc** d, int** sts, int** dperm, int** dshifted, double** sums,
                       double** shifts, double** orths, double** pool, double** upool, void** scratch) {
         *tab = c.take<char>(plan.table_bytes);
@@ -1174,6 +1177,13 @@ oqr_status oqr_check(oqr_ctx* ctx, int m, int n, const double* A, long lda, cons
         if (orthF) *orthF = h.orthF;
         return static_cast<oqr_status>(h.code);
     }
+    return OQR_OK;
+}
+
+oqr_status oqr_set_batch_budget(oqr_ctx* ctx, size_t bytes)
+{
+    if (!ctx) return OQR_ERR_INVALID_ARG;
+    ctx->batch_budget = bytes;
     return OQR_OK;
 }
 

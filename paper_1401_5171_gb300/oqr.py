@@ -108,6 +108,7 @@ def load(path: str | None = None):
     lib.oqr_check.argtypes = [vp, i, i, vp, l, vp, l, vp, l, ctypes.POINTER(d), ctypes.POINTER(d), vp]
     lib.oqr_repres.argtypes = [vp, i, i, vp, l, vp, l, vp, l, ctypes.POINTER(d), ctypes.POINTER(d), vp]
     lib.oqr_diag_timeout.argtypes = [vp, l, vp]
+    lib.oqr_set_batch_budget.argtypes = [vp, ctypes.c_size_t]
     for name in declared_functions():
         f = getattr(lib, name)
         if f.restype is ctypes.c_int or name not in ("oqr_default_opts", "oqr_status_string"):
@@ -131,7 +132,7 @@ def _raw(name):
 
 for _n in ("oqr_default_opts", "oqr_create", "oqr_destroy", "oqr_workspace_size", "oqr_set_workspace",
            "oqr_get_status", "oqr_cholqr", "oqr_cholqr2", "oqr_cholqr2_host", "oqr_cgs2", "oqr_gram", "oqr_gram_noalloc", "oqr_gram_phases", "oqr_potrf", "oqr_trsm", "oqr_trsm_tc",
-           "oqr_rprod", "oqr_check", "oqr_repres", "oqr_diag_timeout", "oqr_batched", "oqr_batched_mixed", "oqr_batched_default_splits", "oqr_features",
+           "oqr_rprod", "oqr_check", "oqr_repres", "oqr_diag_timeout", "oqr_set_batch_budget", "oqr_batched", "oqr_batched_mixed", "oqr_batched_default_splits", "oqr_features",
            "oqr_mlp_param_count", "oqr_mlp_forward", "oqr_mlp_grad", "oqr_mlp_adam"):
     globals()[_n] = _raw(_n)
 
@@ -425,6 +426,12 @@ class Oqr:
         """The context's device-side status (synchronizes the stream)."""
         info = ctypes.c_int(0)
         return self.lib.oqr_get_status(self.ctx, self._stream(stream), ctypes.byref(info))
+
+    def set_batch_budget(self, nbytes):
+        """Slice-plane bytes per wave of the tensor-core batches (0: the default)."""
+        st = self.lib.oqr_set_batch_budget(self.ctx, int(nbytes))
+        if st != OQR_OK:
+            raise OqrError(st, "oqr_set_batch_budget")
 
     def set_workspace(self, ptr, nbytes):
         """Hands the context a caller-owned device buffer (ptr = 0: the context allocates again)."""

@@ -334,3 +334,24 @@ def test_batched_check_graph_replay_new_outputs(env):
     assert torch.equal(o1, o2) and bool(torch.all(o2 > 0))
     for a, b in zip(R1, R2):
         assert torch.equal(a, b)
+
+
+def test_batched_waves_do_not_change_results(env):
+    """One wave for the whole batch, or one instance per wave (a 1 MiB plane budget): (Q, R, status,
+    orth) bit-identical, with every program in the batch."""
+    torch, oqr, ctx = env
+    As, Zs, _ = inputs.batch_instances(12, seed=81, device="cuda", m_range=(64, 1100), n_range=(1, 64),
+                                       log_kappa_a=(0.0, 2.0), log_kappa_z=(0.0, 2.0))
+    progs = [(oqr.OQR_BATCH_CHOLQR_TC, oqr.OQR_BATCH_CHOLQR2_TC2, oqr.OQR_BATCH_CHOLQR2_TC,
+              oqr.OQR_BATCH_SCHOLQR3_TC)[b % 4] for b in range(len(Zs))]
+    Q1, R1, s1, o1 = ctx.oqr_batched_mixed(As, Zs, program=progs, check=True)
+    torch.cuda.synchronize()
+    try:
+        ctx.set_batch_budget(1 << 20)
+        Q2, R2, s2, o2 = ctx.oqr_batched_mixed(As, Zs, program=progs, check=True)
+        torch.cuda.synchronize()
+    finally:
+        ctx.set_batch_budget(0)
+    assert s1.abs().sum().item() == 0 and torch.equal(s1, s2) and torch.equal(o1, o2)
+    for b in range(len(Zs)):
+        assert torch.equal(Q1[b], Q2[b]) and torch.equal(R1[b], R2[b])
