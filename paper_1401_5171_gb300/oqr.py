@@ -285,6 +285,8 @@ class Oqr:
     def _batch_args(self, As, Zs, Qs, Rs, status):
         import torch
         cnt = len(Zs)
+        if len(As) != cnt or (Qs is not None and len(Qs) != cnt) or (Rs is not None and len(Rs) != cnt):
+            raise ValueError("As, Zs, Qs and Rs need one entry per instance")
         Qs = Qs if Qs is not None else [empty_colmajor(z.shape[0], z.shape[1], z.device) for z in Zs]
         Rs = Rs if Rs is not None else [empty_colmajor(z.shape[1], z.shape[1], z.device) for z in Zs]
         I = ctypes.c_int * cnt
@@ -304,6 +306,8 @@ class Oqr:
 
         mode 0: FP64; tensor cores: 1 OQR_BATCH_CHOLQR2_TC, 2 OQR_BATCH_CHOLQR2_TC2, 3 OQR_BATCH_SCHOLQR3_TC."""
         Qs, Rs, st, a = self._batch_args(As, Zs, Qs, Rs, status)
+        if splits is not None and len(splits) != a[0]:
+            raise ValueError("splits needs one entry per instance")
         sp = (ctypes.c_int * a[0])(*splits) if splits is not None else None
         r = self.lib.oqr_batched(self.ctx, *a, int(mode), sp, ctypes.c_void_p(st.data_ptr()), self._stream(stream))
         if r != OQR_OK:
@@ -316,6 +320,8 @@ class Oqr:
         per-instance ||Q^T A Q - I||_2 estimates."""
         import torch
         Qs, Rs, st, a = self._batch_args(As, Zs, Qs, Rs, status)
+        if program is not None and len(program) != a[0]:
+            raise ValueError("program needs one entry per instance")
         pr = (ctypes.c_int * a[0])(*[int(x) for x in program]) if program is not None else None
         orth = torch.empty(a[0], dtype=torch.float64, device=Zs[0].device) if check else None
         r = self.lib.oqr_batched_mixed(self.ctx, *a, pr, ctypes.c_void_p(st.data_ptr()),
