@@ -284,16 +284,18 @@ typedef enum {
  * Q = Z R^{-1} and R = R_p ... R_1 in FP64.  An instance's results do not
  * depend on the other instances of the batch.  Instances run in waves
  * (largest m first) whose BF16 slice planes (14 bytes per element of A, Z
- * and Z^T A) fit 16 GiB of workspace; A is split once per wave and read by
- * every pass.  orth (device, count doubles, may be NULL): when given, each
+ * and Z^T A) fit 16 GiB of workspace (oqr_set_batch_budget); A is split once
+ * per wave and read by every pass.  orth (device, count doubles, may be NULL): when given, each
  * instance's result is checked, orth[b] = an estimate of ||Q_b^T A_b Q_b - I||_2
  * (Sec. 7's orthogonality measure; power iteration, a lower bound) from one
  * more FP64_TC Gram of the final Q, or +inf after a breakdown.
- * status[b] = -1 for every instance when a tensor-core wait
- * timed out (the context's status then reports OQR_ERR_TIMEOUT).  The
- * sequence is captured into one CUDA graph, cached while every instance's
- * (m, n, program) and the use of orth are unchanged.  Asynchronous: returns after enqueueing
- * (argument errors, including a program outside the enum, are returned).
+ * status[b] = -1 for every instance when a tensor-core wait timed out (the
+ * context's status then reports OQR_ERR_TIMEOUT).  Q may alias Z (each row is
+ * solved in place).  The sequence is captured into one CUDA graph, cached
+ * while every instance's (m, n, program), the status and orth addresses and
+ * the wave budget are unchanged (on the legacy default stream it runs
+ * directly).  Asynchronous: returns after enqueueing (argument errors,
+ * including a program outside the enum, are returned).
  */
 oqr_status oqr_batched_mixed(oqr_ctx* ctx, int count, const int* m, const int* n, const double* const* A,
                              const long* lda, const double* const* Z, const long* ldz, double* const* Q,
