@@ -355,3 +355,19 @@ def test_batched_waves_do_not_change_results(env):
     assert s1.abs().sum().item() == 0 and torch.equal(s1, s2) and torch.equal(o1, o2)
     for b in range(len(Zs)):
         assert torch.equal(Q1[b], Q2[b]) and torch.equal(R1[b], R2[b])
+
+
+def test_batched_mixed_in_place(env):
+    """Q aliasing Z (the factorization overwrites Z): bit-identical to the separate-output run."""
+    torch, oqr, ctx = env
+    As, Zs, _ = inputs.batch_instances(6, seed=91, device="cuda", m_range=(64, 600), n_range=(2, 48),
+                                       log_kappa_a=(0.0, 2.0), log_kappa_z=(0.0, 2.0))
+    progs = [oqr.OQR_BATCH_CHOLQR2_TC2, oqr.OQR_BATCH_SCHOLQR3_TC, oqr.OQR_BATCH_CHOLQR_TC] * 2
+    Q1, R1, s1 = ctx.oqr_batched_mixed(As, Zs, program=progs)
+    Zc = [oqr.colmajor(z.clone()) for z in Zs]
+    Q2, R2, s2 = ctx.oqr_batched_mixed(As, Zc, program=progs, Qs=Zc)
+    torch.cuda.synchronize()
+    assert s1.abs().sum().item() == 0 and torch.equal(s1, s2)
+    for b in range(len(Zs)):
+        assert Q2[b].data_ptr() == Zc[b].data_ptr()
+        assert torch.equal(Q1[b], Q2[b]) and torch.equal(R1[b], R2[b])
