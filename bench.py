@@ -33,6 +33,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "oblique QRs/sec and TFLOP/s at ||Q^T A Q - I|| <= 1e-12, mixed vs FP64 on one GB300"
 SMS, FP64_FLOPS_PER_CLK_SM = 152, 4      # GB300: 2 FP64 FMAs per clock per SM
+L2_BYTES = 129 * 2 ** 20
 
 
 # ---- multi-rank logic (replicas: every rank factors its own instance; no data-path collective) ----
@@ -304,7 +305,9 @@ def config_of(args):
                         f"kappa(Z)={args.kappa_z:g}, random U (Sec. 7 case 4 recipe)",
             "m": args.m, "n": args.n, "kappa_A": args.kappa_a, "kappa_Z": args.kappa_z, "path": args.path,
             "path_desc": PATHS[args.path][3],
-            "l2": "inputs larger than L2 (A alone is 8.6 GB), no flush"}
+            "l2": (f"inputs larger than L2 (A alone is {8 * args.m * args.m / 1e9:.2f} GB, L2 129 MB), no flush"
+                   if 8 * args.m * args.m > L2_BYTES else
+                   f"A ({8 * args.m * args.m / 1e6:.0f} MB) fits in L2 (129 MB): timings include L2 reuse")}
 
 
 def run_batch(ctx, torch, dev, count, stream, steps=2):
