@@ -1,5 +1,6 @@
-"""Autotuner for the batched path's work plan.
+"""Autotuners for the batched paths' work plans.
 
+FP64 path:
 oqr_batched cuts each instance's Gram (A_b's lower triangle, in k-steps of 16
 over 64-row blocks) into `splits` ranges, one CTA each.  Too few ranges leave
 SMs idle on a skewed batch; too many add partial sums and epilogues.  The tuner
@@ -8,6 +9,13 @@ device for a family of target k-steps per CTA, and keeps the fastest target per
 bucket.  The resulting plan (splits per instance) and the table
 {bucket: target} are returned; the table can be saved as JSON and reused for
 batches with the same size mix.
+
+Tensor-core path (oqr_batched_mixed): the instances run in waves whose slice
+planes fit a byte budget.  A small budget gives more waves, each with fewer
+work items for the persistent product kernels and a longer tail; a large one
+holds more workspace.  tune_waves times a family of budgets on a sample batch
+and returns the fastest (set it with Oqr.set_batch_budget); the results do not
+depend on it.
 """
 from __future__ import annotations
 
@@ -80,3 +88,30 @@ def load_table(path):
     with open(path) as f:
         raw = json.load(f)
     return {tuple(int(x) for x in k.split("-")): v for k, v in raw.items()}
+
+
+WAVE_BUDGETS = (2 << 30, 4 << 30, 8 << 30, 16 << 30, 32 << 30)
+
+
+def tune_waves(ctx, As, Zs, program=None, reps: int = 2, budgets=WAVE_BUDGETS, stream=None):
+    """Times oqr_batched_mixed on (As, Zs) for every plane budget; returns (best budget, {budget: ms}).
+    The context's budget is left at the best one."""
+    import torch
+    from .oqr import empty_colmajor
+    Qs = [empty_colmajor(z.shape[0], z.shape[1], z.device) for z in Zs]
+    Rs = [empty_colmajor(z.shape[1], z.shape[1], z.device) for z in Zs]
+    timings = {}
+    for b in budgets:
+        ctx.set_batch_budget(b)
+        ctx.oqr_batched_mixed(As, Zs, program=program, Qs=Qs, Rs=Rs, stream=stream)   # capture / warm
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            ctx.oqr_batched_mixed(As, Zs, program=program, Qs=Qs, Rs=Rs, stream=stream)
+        e1.record()
+        torch.cuda.synchronize()
+        timings[b] = e0.elapsed_time(e1) / reps
+    best = min(timings, key=timings.get)
+    ctx.set_batch_budget(best)
+    return best, timings

@@ -371,3 +371,22 @@ def test_batched_mixed_in_place(env):
     for b in range(len(Zs)):
         assert Q2[b].data_ptr() == Zc[b].data_ptr()
         assert torch.equal(Q1[b], Q2[b]) and torch.equal(R1[b], R2[b])
+
+
+def test_wave_budget_autotuner(env):
+    """tune_waves times every budget and leaves the fastest set; the results do not depend on it."""
+    torch, oqr, ctx = env
+    As, Zs, _ = inputs.batch_instances(24, seed=101, device="cuda", m_range=(64, 2000), n_range=(4, 64),
+                                       log_kappa_a=(0.0, 2.0), log_kappa_z=(0.0, 2.0))
+    Q0, R0, s0 = ctx.oqr_batched_mixed(As, Zs)
+    torch.cuda.synchronize()
+    try:
+        best, timings = autotune.tune_waves(ctx, As, Zs, reps=1, budgets=(1 << 24, 1 << 27, 16 << 30))
+        assert best in timings and len(timings) == 3 and all(t > 0 for t in timings.values())
+        Q1, R1, s1 = ctx.oqr_batched_mixed(As, Zs)
+        torch.cuda.synchronize()
+    finally:
+        ctx.set_batch_budget(0)
+    assert torch.equal(s0, s1)
+    for b in range(len(Zs)):
+        assert torch.equal(Q0[b], Q1[b]) and torch.equal(R0[b], R1[b])
