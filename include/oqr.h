@@ -364,10 +364,13 @@ oqr_status oqr_gram_phases(oqr_ctx* ctx, int m, int n, const double* A, long lda
  *   memory on the current device; A is read from its lower triangle.
  *   Limits: n <= 1024 (n above that returns OQR_ERR_UNSUPPORTED); the
  *   partial count is capped at floor(8 MiB / (8 n^2)), so large n runs on
- *   fewer CTAs than oqr_gram.  The first call on a device looks up the
- *   array's device address and should come before any stream capture on that
- *   device.  All calls share the array: calls that overlap on the GPU race.
- *   Device-side timeouts are not reported (there is no context to hold them).
+ *   fewer CTAs than oqr_gram: for n > 724 one partial, i.e. ceil(n / 64)
+ *   CTAs (16 at n = 1024).  The first call on a device looks up the array's
+ *   device address and should come before any stream capture on that
+ *   device; cudaDeviceReset after it is not supported.  All calls share the
+ *   array: calls that overlap on the GPU race.  There is no context to hold
+ *   a device-side outcome, so when a time-limited wait of the kernel gives up
+ *   every element of G is set to NaN.
  */
 oqr_status oqr_gram_noalloc(int m, int n, const double* A, long lda, const double* Z, long ldz, double* G,
                             long ldg, void* stream);

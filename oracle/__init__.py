@@ -20,6 +20,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oqr_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "cpu_method.c")]   # the oracle, and the CPU restatement of the method
 _LIB = os.path.join(_HERE, "liboqr_oracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -27,9 +28,9 @@ _lib = None
 
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (OpenMP, IEEE semantics, no FMA contraction)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    if force or not os.path.exists(_LIB) or any(os.path.getmtime(_LIB) < os.path.getmtime(s) for s in _SRCS):
         cmd = ["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
-               "-fno-fast-math", "-std=c99", _SRC, "-o", _LIB + ".tmp", "-lm"]
+               "-fno-fast-math", "-std=c99", *_SRCS, "-o", _LIB + ".tmp", "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(_LIB + ".tmp", _LIB)
     return _LIB
@@ -58,6 +59,10 @@ def _load():
             lib.orc_oblique_qr.restype = i
             lib.orc_orth_defect.argtypes = [i, i, dp, l, dp, l, dp, l]
             lib.orc_repres_residual.argtypes = [i, i, dp, l, dp, l, dp, l, dp, l]
+            lib.orc_cpu_cholqr2.argtypes = [i, i, dp, l, dp, l, dp, l, dp, l]
+            lib.orc_cpu_cholqr2.restype = i
+            lib.orc_cpu_threads.argtypes = []
+            lib.orc_cpu_threads.restype = i
             _lib = lib
     return _lib
 
@@ -192,3 +197,21 @@ def repres_error(Z, Q, R):
     """||Z - Q R||_2 / ||Z||_2 (Sec. 7's representativity measure)."""
     D = repres_residual(Z, Q, R)
     return float(np.linalg.norm(D, 2) / np.linalg.norm(np.asarray(Z), 2))
+
+
+def cpu_cholqr2(A, Z):
+    """A-CholQR2 (Algorithm 1 twice, R = R_2 R_1) restated on the CPU with row-block loops over all host
+    cores: the benchmark's timed CPU baseline of the method itself (not the oracle).  A is read in full."""
+    A, Z = _f(A), _f(Z)
+    m, n = Z.shape
+    Q = np.zeros((m, n), order="F")
+    R = np.zeros((n, n), order="F")
+    info = _load().orc_cpu_cholqr2(m, n, _p(A), _ld(A), _p(Z), _ld(Z), _p(Q), _ld(Q), _p(R), _ld(R))
+    if info:
+        raise OracleBreakdown("cpu_cholqr2", info)
+    return Q, R
+
+
+def cpu_threads():
+    """OpenMP threads the CPU code uses (all host cores unless OMP_NUM_THREADS says otherwise)."""
+    return int(_load().orc_cpu_threads())

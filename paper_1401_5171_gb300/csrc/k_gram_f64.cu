@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(THREADS, 2)
                         // drain what is still in flight before the CTA exits
                         for (long q = it; q < nk && q < it + STAGES; ++q) {
                             const int sl = (int)((g + q) % STAGES);
-                            mbar_wait(&full[sl], (uint32_t)(((g + q) / STAGES) & 1), a.limit_ns);
+                            mbar_wait(&full[sl], (uint32_t)(((g + q) / STAGES) & 1), exit_drain_ns(a.limit_ns));
                         }
                     }
                     return;

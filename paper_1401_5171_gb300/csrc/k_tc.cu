@@ -787,7 +787,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             // copies still in flight must land before the CTA may exit
             const long issued = it;
             for (long q = issued - C::STAGES; q < issued; ++q)
-                if (q >= 0) mbar_wait(&full[q % C::STAGES], (uint32_t)((q / C::STAGES) & 1), a.limit_ns);
+                if (q >= 0)
+                    mbar_wait(&full[q % C::STAGES], (uint32_t)((q / C::STAGES) & 1), exit_drain_ns(a.limit_ns));
         }
     } else if (warp == 1) {
         // ------------------------------------------------ MMA issuer
@@ -846,7 +847,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
             // every MMA issued by this thread must be complete before TMEM is released
             umma_commit(done);
-            mbar_wait(done, 0, a.limit_ns);
+            mbar_wait(done, 0, exit_drain_ns(a.limit_ns));
         }
     } else {
         // ------------------------------------------------ drain (warps 2..9)
@@ -1243,7 +1244,8 @@ __global__ void __launch_bounds__(EMU_THREADS, 1)
             }
             const long issued = it;  // copies still in flight must land before the CTA may exit
             for (long q = issued - EMU_STAGES; q < issued; ++q)
-                if (q >= 0) mbar_wait(&full[q % EMU_STAGES], (uint32_t)((q / EMU_STAGES) & 1), a.limit_ns);
+                if (q >= 0)
+                    mbar_wait(&full[q % EMU_STAGES], (uint32_t)((q / EMU_STAGES) & 1), exit_drain_ns(a.limit_ns));
         }
     } else if (warp == 1) {
         // ------------------------------------------------ MMA issuer
@@ -1299,7 +1301,7 @@ __global__ void __launch_bounds__(EMU_THREADS, 1)
             }
             // every MMA issued by this thread must be complete before TMEM is released
             umma_commit(done);
-            mbar_wait(done, 0, a.limit_ns);
+            mbar_wait(done, 0, exit_drain_ns(a.limit_ns));
         }
     } else {
         // ------------------------------------------------ drain (warps 2..17)

@@ -94,6 +94,18 @@ __device__ inline bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_
     return true;
 }
 
+// Bound of the waits on a kernel's exit path, for bulk copies or MMAs that may
+// still be in flight after an abort.  Their shared or tensor memory must not be
+// released (by the CTA's exit, or by tcgen05.dealloc) while the hardware can
+// still write or read it, so these waits never give up sooner than
+// EXIT_DRAIN_NS, however small the caller's spin_limit: a copy or MMA that was
+// issued completes in microseconds unless the GPU itself has stopped.
+constexpr uint64_t EXIT_DRAIN_NS = 2000000000ull;
+__host__ __device__ inline uint64_t exit_drain_ns(uint64_t limit_ns)
+{
+    return limit_ns > EXIT_DRAIN_NS ? limit_ns : EXIT_DRAIN_NS;
+}
+
 __device__ inline void fence_barrier_init()
 {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");

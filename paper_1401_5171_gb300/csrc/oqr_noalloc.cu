@@ -21,6 +21,15 @@
 // (different streams, no ordering) race on it; the status word is cleared at
 // the start of every call and the partials are overwritten, never
 // accumulated into, so nothing is left over from an earlier call.
+//
+// There is no context to report a device-side failure to, so a failure is
+// made visible in the result itself: if a time-limited wait of the Gram
+// kernel gives up, every element of G is set to NaN (the reduction then
+// skips its writes, and the last kernel of the call fills G).
+//
+// The cached address belongs to the device's primary context as it was at the
+// first call; cudaDeviceReset after that call is not supported (the module
+// reloads and the array may move).
 #include <mutex>
 
 #include "oqr_internal.cuh"
@@ -66,6 +75,15 @@ oqr_status scratch_on_current_device(void** out)
     return OQR_OK;
 }
 
+// G (n x n, ldg) = NaN everywhere when the call's status word records an error.
+__global__ void noalloc_fail_fill_kernel(int n, double* G, long ldg, const DevStatus* st)
+{
+    if (*(volatile const int*)&st->code == 0) return;
+    const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long)n * n) return;
+    G[(e % n) + (e / n) * ldg] = __longlong_as_double(0x7FF8000000000000LL);
+}
+
 }  // namespace
 
 extern "C" oqr_status oqr_gram_noalloc(int m, int n, const double* A, long lda, const double* Z, long ldz,
@@ -93,5 +111,8 @@ extern "C" oqr_status oqr_gram_noalloc(int m, int n, const double* A, long lda, 
     if (cudaMemsetAsync(st, 0, sizeof(DevStatus), s) != cudaSuccess) return OQR_ERR_CUDA;
     if (launch_gram_f64(p, A, lda, Z, ldz, partials, st, 4000000000ull, s) != cudaSuccess) return OQR_ERR_CUDA;
     if (launch_gram_reduce(p, partials, G, ldg, nullptr, st, s) != cudaSuccess) return OQR_ERR_CUDA;
+    const long tot = (long)n * n;
+    noalloc_fail_fill_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(n, G, ldg, st);
+    if (cudaGetLastError() != cudaSuccess) return OQR_ERR_CUDA;
     return OQR_OK;
 }

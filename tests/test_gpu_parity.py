@@ -285,34 +285,59 @@ def test_check_matches_oracle(env):
 
 
 # ---------------------------------------------------- full size, properties --
-@pytest.mark.parametrize("shifted", [0, 1])
-def test_config1_full_size_properties(env, shifted):
-    """m=32768, n=256, kappa(A)=1e6, kappa(Z)=1e2: the benchmark's launch configuration.
+FULL_PATHS = {
+    # name: (kwargs of oqr_cholqr2)
+    "fp64": {},
+    "fp64_shifted": {"shifted": 1},
+    "mixed_tc2_fp64tc": {"prec": 4, "final_prec": 3},        # the benchmark's headline path
+    "all_fp64tc": {"prec": 3, "final_prec": 3},
+    "bf16x3_fp64tc": {"prec": 1, "final_prec": 3},
+    "shifted_all_fp64tc": {"shifted": 1, "prec": 3, "final_prec": 3},
+}
 
-    No oracle at this size: Q^T A Q = I, Z = Q R, R upper with positive
-    diagonal, and sigma(R)^2 = eig(Z^T A Z) (Thm 1.1) together fix (Q, R);
-    each is measured with torch's own FP64 GEMM/eigensolver on the GPU.
-    """
+
+@pytest.fixture(scope="module")
+def full_size(env):
+    """m=32768, n=256, kappa(A)=1e6, kappa(Z)=1e2: the benchmark's workload, and the R of the
+    FP64 (DFMA) A-CholQR2, the path pinned to the oracle element by element at small sizes."""
     torch, oqr, ctx = env
     m, n = 32768, 256
     Af, _ = inputs.dense_spd(m, 1e6, seed=101, device="cuda")
     Z = inputs.tall_z(m, n, 1e2, seed=102, device="cuda")
     A = oqr.colmajor(Af)
-    Zc = oqr.colmajor(Z.clone())
-    Q, R, (st, info) = ctx.oqr_cholqr2(A, Zc, shifted=shifted)
+    _, R64, (st, _) = ctx.oqr_cholqr2(A, oqr.colmajor(Z.clone()))
     assert st == 0
-    AQ = Af @ Q
-    E = Q.T @ AQ - torch.eye(n, dtype=torch.float64, device="cuda")
+    G = Z.T @ (Af @ Z)
+    ev = torch.linalg.eigvalsh(0.5 * (G + G.T)).clamp_min(0).sqrt().sort().values
+    yield {"Af": Af, "A": A, "Z": Z, "R64": R64, "ev": ev}
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("path", list(FULL_PATHS))
+def test_config1_full_size_properties(env, full_size, path):
+    """Every A-CholQR2 path at the benchmark's launch configuration (m=32768, n=256).
+
+    No oracle runs at this size: Q^T A Q = I, Z = Q R, R upper with a positive
+    diagonal and sigma(R)^2 = eig(Z^T A Z) (Thm 1.1) together fix (Q, R); each is
+    measured with torch's own FP64 GEMM/eigensolver on the GPU.  R is also
+    compared with the DFMA path's R within max(1e-12, 100 u kappa(R)): the
+    forward error of a normal-equation R grows with kappa(A^{1/2} Z) (Thm 2.1).
+    """
+    torch, oqr, ctx = env
+    Af, A, Z, R64, ev = (full_size[k] for k in ("Af", "A", "Z", "R64", "ev"))
+    n = Z.shape[1]
+    Q, R, (st, info) = ctx.oqr_cholqr2(A, oqr.colmajor(Z.clone()), **FULL_PATHS[path])
+    assert st == 0
+    E = Q.T @ (Af @ Q) - torch.eye(n, dtype=torch.float64, device="cuda")
     orth = torch.linalg.eigvalsh(0.5 * (E + E.T)).abs().max().item()
     rep = (torch.linalg.matrix_norm(Z - Q @ R, 2) / torch.linalg.matrix_norm(Z, 2)).item()
     assert torch.all(torch.tril(R, -1) == 0) and torch.all(torch.diagonal(R) > 0)
     sv = torch.linalg.svdvals(R).sort().values
-    G = Z.T @ (Af @ Z)
-    ev = torch.linalg.eigvalsh(0.5 * (G + G.T)).clamp_min(0).sqrt().sort().values
     assert torch.max((sv - ev).abs() / ev.max()).item() < 1e-10
-    assert orth < 1e-11 and rep < 1e-13
-    del Af, A, AQ, G
-    torch.cuda.empty_cache()
+    kappa = (ev[-1] / ev[0]).item()
+    relR = (torch.linalg.matrix_norm(R - R64) / torch.linalg.matrix_norm(R64)).item()
+    assert relR <= max(1e-12, 100 * U * kappa), (relR, kappa)
+    assert orth < 1e-11 and rep < 1e-13, (orth, rep)
 
 
 def test_repres_planted_residual(env):
@@ -348,3 +373,31 @@ def test_repres_of_factorization(env):
     ref = oracle.repres_error(Z, Q.cpu().numpy(), R.cpu().numpy())
     assert r2 <= max(4 * ref, 1e-15) and r2 <= 1e-13
     assert rf <= 1e-13
+
+
+# ------------------------------------------------------------- shift value --
+@pytest.mark.parametrize("prec", ["fp64", "fp64tc", "bf16x3", "tc2"])
+def test_shift_value_matches_its_formula(env, prec):
+    """The shift of shifted A-CholQR3's first pass, recomputed on the CPU from its definition.
+
+    FP64 or FP64-accurate first pass: s = 11 u (m n + n (n + 1)) ||A||_F ||Z||_F^2, u = 2^-53
+    (||A||_F of the symmetric A whose lower triangle is read).  BF16X3 or TC2 first pass:
+    s = 11 u_eff trace(G), u_eff = 2^-16, G that pass's low-precision Z^T A Z, whose trace agrees
+    with the exact trace(Z^T A Z) to about 2^-16.  A wrong constant, norm or unit roundoff
+    changes s by far more than these tolerances.
+    """
+    torch, oqr, ctx = env
+    m, n = 1500, 48
+    A, Z = inputs.paper_case(4, m, n, 1e4, 1e6, seed=17)
+    P = np.tril(A)                                       # the upper triangle must not enter ||A||_F
+    P[np.triu_indices(m, 1)] = 7.0
+    code = {"fp64": (0, 0), "fp64tc": (3, 3), "bf16x3": (1, 3), "tc2": (4, 3)}[prec]
+    _, _, (st, info) = ctx.oqr_cholqr2(dev(torch, P, oqr), dev(torch, Z, oqr), shifted=1, prec=code[0],
+                                       final_prec=code[1])
+    assert st == 0
+    if prec in ("fp64", "fp64tc"):
+        ref = 11 * U * (m * n + n * (n + 1)) * np.linalg.norm(A) * np.linalg.norm(Z) ** 2
+        assert abs(info.shift - ref) <= 1e-12 * ref, (info.shift, ref)
+    else:
+        ref = 11 * 2.0 ** -16 * np.trace(Z.T @ A @ Z)
+        assert abs(info.shift - ref) <= 1e-3 * ref, (info.shift, ref)

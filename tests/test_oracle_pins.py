@@ -285,3 +285,20 @@ def test_cholqr_restatement_agrees_when_well_conditioned():
     Q0, R0 = oracle.oblique_qr(A, Z)
     Q1, R1 = oracle.cholqr(A, Z)
     assert rel(R1, R0) < 1e-12 and rel(Q1, Q0) < 1e-11
+
+
+def test_cpu_method_cholqr2_reaches_the_oracle():
+    """The CPU A-CholQR2 restatement (the benchmark's timed baseline of the method) reaches the oracle's
+    unique (Q, R) on config 0; ragged row blocks (m not a multiple of 64)
+    and column counts not a multiple of the 8-column step are covered."""
+    A, Z = inputs.config0(seed=0)
+    Qr, Rr = oracle.oblique_qr(A, Z)
+    Q, R = oracle.cpu_cholqr2(A, Z)
+    assert np.linalg.norm(R - Rr) / np.linalg.norm(Rr) <= 1e-12
+    assert oracle.orth_error(A, Q) <= 1e-12
+    # ragged sizes: m = 203 (3 row blocks, the last 11 rows; 203 = 25*8 + 3 columns of A)
+    A, Z = inputs.paper_case(4, 203, 9, 1e3, 1e2, seed=8)
+    Qr, Rr = oracle.oblique_qr(A, Z)
+    Q, R = oracle.cpu_cholqr2(A, Z)
+    assert np.linalg.norm(R - Rr) / np.linalg.norm(Rr) <= 1e-12
+    assert oracle.orth_error(A, Q) <= 1e-12

@@ -62,3 +62,53 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(env):
     Z = oqr.empty_colmajor(m, n, "cuda")
     G = oqr.empty_colmajor(n, n, "cuda")
     assert _call_noalloc(lib, torch, oqr, A, Z, G) == oqr.OQR_ERR_UNSUPPORTED
+
+
+def _padded(torch, X, pad):
+    """A column-major copy of X whose leading dimension is rows + pad (an odd pad: a byte stride that
+    is not a multiple of 16, which TMA cannot address, so the kernel takes its plain-load path)."""
+    rows, cols = X.shape
+    buf = torch.zeros((cols, rows + pad), dtype=torch.float64, device="cuda")
+    buf[:, :rows] = torch.as_tensor(X.T)
+    return buf.t()[:rows]
+
+
+def test_noalloc_padded_leading_dimensions_plain_path(env):
+    """lda, ldz and ldg padded by an odd count of doubles: the Gram kernel's plain-load path and a G
+    with ldg > n, against oqr_gram on the same padded operands (same tolerance)."""
+    torch, oqr, lib = env
+    ctx = oqr.Oqr(0)
+    m, n = 1201, 70
+    A_np, Z_np = inputs.paper_case(4, m, n, 1e3, 1e2, seed=5)
+    A, Z = _padded(torch, A_np, 3), _padded(torch, Z_np, 1)
+    assert A.stride(1) == m + 3 and Z.stride(1) == m + 1
+    G_ref = ctx.oqr_gram(A, Z)
+    Gbuf = torch.full((n, n + 5), float("nan"), dtype=torch.float64, device="cuda")
+    G = Gbuf.t()[:n]                                   # ldg = n + 5
+    for _ in range(2):                                 # two calls in a row
+        assert _call_noalloc(lib, torch, oqr, A, Z, G) == oqr.OQR_OK
+        torch.cuda.synchronize()
+        Gh, Gr = G.cpu().numpy(), G_ref.cpu().numpy()
+        scale = np.abs(Z_np).T @ np.abs(A_np) @ np.abs(Z_np)
+        assert np.all(np.isfinite(Gh)) and np.array_equal(Gh, Gh.T)
+        assert np.all(np.abs(Gh - Gr) <= 8 * m * U * scale)
+    ctx.close()
+
+
+def test_noalloc_leaves_free_device_memory_unchanged(env):
+    """After a first call (which looks up the array's address), further calls change the device's free
+    memory by nothing: the entry point allocates no device memory."""
+    torch, oqr, lib = env
+    m, n = 2048, 128
+    A_np, Z_np = inputs.paper_case(4, m, n, 1e3, 1e2, seed=6)
+    A = oqr.colmajor(torch.as_tensor(A_np).cuda())
+    Z = oqr.colmajor(torch.as_tensor(Z_np).cuda())
+    G = oqr.empty_colmajor(n, n, "cuda")
+    assert _call_noalloc(lib, torch, oqr, A, Z, G) == oqr.OQR_OK
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        assert _call_noalloc(lib, torch, oqr, A, Z, G) == oqr.OQR_OK
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
