@@ -243,6 +243,50 @@ oqr_status oqr_repres(oqr_ctx* ctx, int m, int n, const double* Z, long ldz, con
                       const double* R, long ldr, double* res2, double* resF, void* stream);
 
 /*
+ * Tridiagonal A (Sec. 8's second workload): A = T with diagonal d (m
+ * doubles) and off-diagonal e (m - 1 doubles; may be NULL when m = 1),
+ * T(i, i) = d[i], T(i + 1, i) = T(i, i + 1) = e[i]; d and e are device
+ * memory.  Products with T cost O(m n), so each pass is O(m n^2), the
+ * paper's normalised count 2 m n^2 per CHOLQR.
+ *
+ * oqr_cholqr2_tridiag: the normal-equation method of oqr_cholqr2 (and
+ *   oqr_cholqr with opts->passes = 1, shifted A-CholQR3 with opts->shifted)
+ *   for A = T, with the same options, outputs, aliasing and reporting.  Each
+ *   pass forms U = M X (M = tril(T, -1) + diag(T) / 2, written once, m x n),
+ *   then C = X^T U in the pass's precision (FP64 GEMM, or the tensor cores
+ *   for OQR_FP64_TC, OQR_TC2, OQR_BF16X3, OQR_FP8) and G = C + C^T; the
+ *   Cholesky factorization, Q = X / R and R = R_2 R_1 are as in oqr_cholqr2.
+ *   The shift of a shifted FP64 or FP64_TC first pass uses ||T||_F.
+ * oqr_gram_tridiag: that pass's G = Z^T T Z (n x n, exactly symmetric) alone.
+ */
+oqr_status oqr_cholqr2_tridiag(oqr_ctx* ctx, int m, int n, const double* d, const double* e, const double* Z, long ldz,
+                               double* Q, long ldq, double* R, long ldr, const oqr_opts* opts, oqr_info* info,
+                               void* stream);
+oqr_status oqr_gram_tridiag(oqr_ctx* ctx, int m, int n, const double* d, const double* e, const double* Z, long ldz,
+                            double* G, long ldg, int prec, void* stream);
+
+/*
+ * oqr_glls: the generalized least-squares application of Sec. 1,
+ *   x = argmin ||Z x - b||_A = R^{-1} Q^T A b,
+ *   for k right-hand sides B (m x k, column-major device memory) given the
+ *   oblique QR (Q, R) of Z (from any factorization above; Q m x n, R n x n
+ *   upper triangular, read in full).  X (n x k, device) receives the
+ *   solutions.  A is read from its lower triangle, once per group of 8
+ *   right-hand sides (the step that HBM bandwidth bounds); Q^T (A B) and the
+ *   back substitution with R are FP64.  Uses the context's workspace (per
+ *   64 x 64 tile of A's lower triangle, 1 KB per right-hand side up to 8, and
+ *   m k + n k doubles).  Asynchronous; argument errors are returned.
+ * oqr_symm: C = A B (m x k) for the symmetric A of this library's
+ *   convention (lower triangle read), the first step of oqr_glls: 64 x 64
+ *   tiles of A's lower triangle, each read once, every row of C summed in a
+ *   fixed order (deterministic).  C must not overlap A or B.
+ */
+oqr_status oqr_glls(oqr_ctx* ctx, int m, int n, int k, const double* A, long lda, const double* Q, long ldq,
+                    const double* R, long ldr, const double* B, long ldb, double* X, long ldx, void* stream);
+oqr_status oqr_symm(oqr_ctx* ctx, int m, int k, const double* A, long lda, const double* B, long ldb, double* C,
+                    long ldc, void* stream);
+
+/*
  * Batched A-CholQR2 (FP64): `count` independent oblique QRs, instance b with
  * A_b (m[b] x m[b], lower triangle read), Z_b (m[b] x n[b]) -> Q_b, R_b, all
  * column-major FP64 device memory, 1 <= n[b] <= min(m[b], 64), m[b] <= 4096.

@@ -59,6 +59,9 @@ def _load():
             lib.orc_oblique_qr.restype = i
             lib.orc_orth_defect.argtypes = [i, i, dp, l, dp, l, dp, l]
             lib.orc_repres_residual.argtypes = [i, i, dp, l, dp, l, dp, l, dp, l]
+            lib.orc_oblique_qr_tridiag.argtypes = [i, i, dp, dp, dp, l, dp, l, dp, l]
+            lib.orc_oblique_qr_tridiag.restype = i
+            lib.orc_orth_defect_tridiag.argtypes = [i, i, dp, dp, dp, l, dp, l]
             lib.orc_cpu_cholqr2.argtypes = [i, i, dp, l, dp, l, dp, l, dp, l]
             lib.orc_cpu_cholqr2.restype = i
             lib.orc_cpu_threads.argtypes = []
@@ -215,3 +218,54 @@ def cpu_cholqr2(A, Z):
 def cpu_threads():
     """OpenMP threads the CPU code uses (all host cores unless OMP_NUM_THREADS says otherwise)."""
     return int(_load().orc_cpu_threads())
+
+
+def glls(A, Z, B):
+    """The generalized least-squares solution of Sec. 1, x = R^{-1} Q^T A b for each column b of B, from the
+    oracle's own (Q, R) (CHOL-EQR), its product with A and a back substitution with R."""
+    Q, R = oblique_qr(A, Z)
+    C = symm_times(A, _f(B))
+    Y = np.asarray(Q).T @ C
+    n = R.shape[0]
+    X = np.zeros_like(Y)
+    for i in range(n - 1, -1, -1):               # R x = y, last row first
+        X[i] = (Y[i] - R[i, i + 1:] @ X[i + 1:]) / R[i, i]
+    return X
+
+
+def _vec1(x):
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.float64).ravel())
+    return x if x.size else np.zeros(1)
+
+
+def oblique_qr_tridiag(d, e, Z):
+    """The oracle for tridiagonal A = T (diagonal d, off-diagonal e): CHOL-EQR (Algorithm 3) with T's
+    bidiagonal Cholesky factor."""
+    Z = _f(Z)
+    m, n = Z.shape
+    d, e = _vec1(d), _vec1(e)
+    Q = np.zeros((m, n), order="F")
+    R = np.zeros((n, n), order="F")
+    info = _load().orc_oblique_qr_tridiag(m, n, _p(d), _p(e), _p(Z), _ld(Z), _p(Q), _ld(Q), _p(R), _ld(R))
+    if info:
+        raise OracleBreakdown("oblique_qr_tridiag", info)
+    return Q, R
+
+
+def orth_error_tridiag(d, e, Q):
+    """||Q^T T Q - I||_2 for tridiagonal T, the defect summed in long double."""
+    Q = _f(Q)
+    m, n = Q.shape
+    d, e = _vec1(d), _vec1(e)
+    E = np.zeros((n, n), order="F")
+    _load().orc_orth_defect_tridiag(m, n, _p(d), _p(e), _p(Q), _ld(Q), _p(E), _ld(E))
+    return float(np.max(np.abs(np.linalg.eigvalsh(0.5 * (E + E.T))))) if E.size else 0.0
+
+
+def tridiag_dense(d, e):
+    """The dense T of a tridiagonal (d, e), for comparisons with the dense oracle at small m."""
+    m = len(d)
+    T = np.diag(np.asarray(d, dtype=np.float64))
+    if m > 1:
+        T += np.diag(np.asarray(e, dtype=np.float64)[:m - 1], -1) + np.diag(np.asarray(e, dtype=np.float64)[:m - 1], 1)
+    return T

@@ -334,3 +334,94 @@ void orc_repres_residual(int m, int n, const double *Z, long ldz,
             AT(D, i, j, ldd) = (double)((long double)AT(Z, i, j, ldz) - s);
         }
 }
+
+/*
+ * The oracle for a tridiagonal A (Sec. 8's second workload, where the paper
+ * notes that factoring A is cheap, so CHOL-EQR is viable): Algorithm 3 with
+ * A = T, T(i, i) = d_i, T(i + 1, i) = T(i, i + 1) = e_i.
+ *   1. T = C^T C with C upper bidiagonal (the Cholesky recurrence of
+ *      orc_chol_upper restricted to T's nonzeros):
+ *        c_00 = sqrt(d_0),  c_{i-1,i} = e_{i-1} / c_{i-1,i-1},
+ *        c_ii = sqrt(d_i - c_{i-1,i}^2).
+ *   2. W = C Z: w_ic = c_ii z_ic + c_{i,i+1} z_{i+1,c}.
+ *   3. Householder QR of W (orc_householder_qr), 4. sign normalisation,
+ *   5. Q = C^{-1} Y by bidiagonal back substitution,
+ *        q_{m-1} = y_{m-1} / c_{m-1,m-1},  q_i = (y_i - c_{i,i+1} q_{i+1}) / c_ii.
+ * Returns 0, or the 1-based row at which a pivot of T is not positive.
+ */
+int orc_oblique_qr_tridiag(int m, int n, const double *d, const double *e,
+                           const double *Z, long ldz, double *Q, long ldq,
+                           double *R, long ldr)
+{
+    double *cd = (double *)malloc(sizeof(double) * (size_t)m);
+    double *cu = (double *)malloc(sizeof(double) * (size_t)m); /* cu[i] = c_{i,i+1} */
+    double *W = (double *)malloc(sizeof(double) * (size_t)m * (size_t)n);
+    for (long i = 0; i < m; ++i) {
+        double p = d[i];
+        if (i > 0)
+            p -= cu[i - 1] * cu[i - 1];
+        if (!(p > 0.0)) {
+            free(W);
+            free(cu);
+            free(cd);
+            return (int)(i + 1);
+        }
+        cd[i] = sqrt(p);
+        cu[i] = (i + 1 < m) ? e[i] / cd[i] : 0.0;
+    }
+#pragma omp parallel for schedule(static)
+    for (long c = 0; c < n; ++c)
+        for (long i = 0; i < m; ++i)
+            AT(W, i, c, m) = cd[i] * AT(Z, i, c, ldz) +
+                             ((i + 1 < m) ? cu[i] * AT(Z, i + 1, c, ldz) : 0.0);
+    orc_householder_qr(m, n, W, m, Q, ldq, R, ldr);
+    for (long j = 0; j < n; ++j) {
+        if (AT(R, j, j, ldr) < 0.0) {
+            for (long c = j; c < n; ++c)
+                AT(R, j, c, ldr) = -AT(R, j, c, ldr);
+            for (long i = 0; i < m; ++i)
+                AT(Q, i, j, ldq) = -AT(Q, i, j, ldq);
+        }
+    }
+#pragma omp parallel for schedule(static)
+    for (long c = 0; c < n; ++c)
+        for (long i = m - 1; i >= 0; --i) {
+            double t = AT(Q, i, c, ldq);
+            if (i + 1 < m)
+                t -= cu[i] * AT(Q, i + 1, c, ldq);
+            AT(Q, i, c, ldq) = t / cd[i];
+        }
+    free(W);
+    free(cu);
+    free(cd);
+    return 0;
+}
+
+/*
+ * E = Q^T T Q - I for tridiagonal T, every entry summed in long double:
+ * (T Q)_ic = e_{i-1} q_{i-1,c} + d_i q_ic + e_i q_{i+1,c}.
+ */
+void orc_orth_defect_tridiag(int m, int n, const double *d, const double *e,
+                             const double *Q, long ldq, double *E, long lde)
+{
+    long double *TQ = (long double *)malloc(sizeof(long double) * (size_t)m * (size_t)n);
+#pragma omp parallel for schedule(static)
+    for (long c = 0; c < n; ++c)
+        for (long i = 0; i < m; ++i) {
+            long double s = (long double)d[i] * (long double)AT(Q, i, c, ldq);
+            if (i > 0)
+                s += (long double)e[i - 1] * (long double)AT(Q, i - 1, c, ldq);
+            if (i + 1 < m)
+                s += (long double)e[i] * (long double)AT(Q, i + 1, c, ldq);
+            TQ[(size_t)i + (size_t)c * (size_t)m] = s;
+        }
+#pragma omp parallel for schedule(static)
+    for (long c = 0; c < n; ++c)
+        for (long r = 0; r < n; ++r) {
+            long double s = 0.0L;
+            for (long i = 0; i < m; ++i)
+                s += (long double)AT(Q, i, r, ldq) * TQ[(size_t)i + (size_t)c * (size_t)m];
+            AT(E, r, c, lde) = (double)(s - (r == c ? 1.0L : 0.0L));
+        }
+    free(TQ);
+}

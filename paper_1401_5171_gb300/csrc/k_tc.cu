@@ -1500,12 +1500,13 @@ static TcArgs make_args(const TcPlan& p, int rowsA, int colsB, int K, int tri, i
     return a;
 }
 
-TcPlan tc_plan(int m, int n, int mode, int sa)
+TcPlan tc_plan(int m, int n, int mode, int sa, bool no_a)
 {
     TcPlan p{};
     p.m = m;
     p.n = n;
     p.mode = mode;
+    p.noA = no_a ? 1 : 0;
     p.S = mode == 1 ? EMU_S : mode == 2 ? 1 : 2;
     p.SA = sa > p.S ? sa : p.S;
     p.es = mode == 2 ? 1 : 2;
@@ -1513,8 +1514,12 @@ TcPlan tc_plan(int m, int n, int mode, int sa)
     p.N = mode == 1 ? EMU_N : (n <= 64 ? 64 : (n <= 128 || mode >= 2) ? 128 : 256);
     p.ldp = ((long)m + 255) / 256 * 256;  // the splits write to the end of their chunk
     p.kch = (m + kch_of(mode) - 1) / kch_of(mode);
-    const TcArgs u = make_args(p, m, n, m, 1, p.N);
     const TcArgs c = make_args(p, n, n, m, 0, p.N);
+    if (p.noA) {  // only the product C = X^T U
+        p.nitems_max = c.nitems;
+        return p;
+    }
+    const TcArgs u = make_args(p, m, n, m, 1, p.N);
     p.nitems_max = u.nitems > c.nitems ? u.nitems : c.nitems;
     return p;
 }
@@ -1538,11 +1543,12 @@ TcLayout tc_layout(const TcPlan& p, void* ws)
         o += al(bytes);
         return q;
     };
-    const size_t planeA = (size_t)p.m * p.ldp, planeZ = (size_t)p.n * p.ldp;  // elements
+    const size_t planeA = p.noA ? 0 : (size_t)p.m * p.ldp, planeZ = (size_t)p.n * p.ldp;  // elements
+    const size_t rowsA = p.noA ? 0 : (size_t)p.m;
     TcLayout L;
     L.Ap = reinterpret_cast<__nv_bfloat16*>(take((size_t)p.SA * planeA * p.es));
-    L.eA = reinterpret_cast<int*>(take((size_t)p.kch * p.m * 4));
-    L.mA = reinterpret_cast<int*>(take((size_t)p.m * 4));
+    L.eA = reinterpret_cast<int*>(take((size_t)p.kch * rowsA * 4));
+    L.mA = reinterpret_cast<int*>(take(rowsA * 4));
     L.Zp = reinterpret_cast<__nv_bfloat16*>(take((size_t)p.S * planeZ * p.es));
     L.Up = reinterpret_cast<__nv_bfloat16*>(take((size_t)p.S * planeZ * p.es));
     L.eZ = reinterpret_cast<int*>(take((size_t)p.kch * p.n * 4));
@@ -1552,7 +1558,7 @@ TcLayout tc_layout(const TcPlan& p, void* ws)
     L.cum1 = reinterpret_cast<int*>(take((size_t)((p.m + TM - 1) / TM + 2) * 4));
     L.cum2 = reinterpret_cast<int*>(take((size_t)((p.m + TM - 1) / TM + 2) * 4));
     L.slots = reinterpret_cast<double*>(take(tc_plan_bytes(p)));
-    L.U = reinterpret_cast<double*>(take((size_t)p.m * p.n * 8));
+    L.U = reinterpret_cast<double*>(take(p.noA ? 0 : (size_t)p.m * p.n * 8));
     L.Cm = reinterpret_cast<double*>(take((size_t)p.n * p.n * 8));
     L.bytes = o;
     return L;
@@ -1642,6 +1648,60 @@ void launch_slot_reduce(const TcPlan& p, const TcArgs& a, double* out, long ldo,
 }
 }  // namespace
 
+namespace {
+// The second product of the normal-equation matrix: C = X^T U on the tensor
+// cores (X's planes already made), then G = C + C^T (+ shift).  U is FP64,
+// m x n with leading dimension ldu.
+cudaError_t tc_cross_phase(const TcPlan& p, const TcLayout& L, const double* U, long ldu, double* G, long ldg,
+                           const double* shift_ptr, DevStatus* st, uint64_t limit_ns, int sms, cudaStream_t s,
+                           cudaEvent_t* ev)
+{
+    const size_t planeZ = (size_t)p.n * p.ldp;
+    const int mm = p.m, nn = p.n;
+    split_tall_mode(p, s, U, ldu, L.Up, L.eU, L.mU);
+    TcArgs a2 = make_args(p, nn, nn, mm, 0, p.N);
+    a2.cum = L.cum2;
+    a2.slots = L.slots;
+    a2.eA = L.eZ;
+    a2.eB = L.eU;
+    a2.emaxA = L.mZ;
+    a2.emaxB = L.mU;
+    a2.st = st;
+    a2.limit_ns = limit_ns;
+    item_prefix_kernel<<<1, PREFIX_THREADS, 0, s>>>(a2, L.cum2);
+    if (ev) cudaEventRecord(ev[3], s);
+    cudaError_t e;
+    if ((e = launch_tc_mode(p, a2, L.Zp, planeZ, L.Up, planeZ, sms, s)) != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[4], s);
+    launch_slot_reduce(p, a2, L.Cm, nn, st, s);
+    {
+        const long tot = (long)nn * nn;
+        symmetrize_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(nn, L.Cm, nn, G, ldg, shift_ptr, st);
+    }
+    if (ev) cudaEventRecord(ev[5], s);
+    return cudaGetLastError();
+}
+}  // namespace
+
+// G = X^T (M + M^T) X = C + C^T with C = X^T U, U = M X given (FP64, m x n):
+// the normal-equation matrix of an A whose product M X the caller formed
+// (tridiagonal A).  The plan has no planes of A (tc_plan(..., no_a = true)).
+cudaError_t launch_tc_cross(const TcPlan& p, const double* X, long ldx, const double* U, long ldu, double* G, long ldg,
+                            const double* shift_ptr, void* ws, DevStatus* st, uint64_t limit_ns, int sms,
+                            cudaStream_t s)
+{
+    const TcLayout L = tc_layout(p, ws);
+    const int nn = p.n;
+    if (p.mode != 0) {
+        fill_int_kernel<<<(nn + 255) / 256, 256, 0, s>>>(L.mZ, nn, EXP_NONE);
+        fill_int_kernel<<<(nn + 255) / 256, 256, 0, s>>>(L.mU, nn, EXP_NONE);
+    }
+    split_tall_mode(p, s, X, ldx, L.Zp, L.eZ, L.mZ);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return tc_cross_phase(p, L, U, ldu, G, ldg, shift_ptr, st, limit_ns, sms, s, nullptr);
+}
+
 // G = Z^T A Z (+ shift) from A's lower triangle on the tensor cores; see the
 // file comment.  ws holds tc_workspace_bytes(p).  a_ready: the workspace
 // already holds the split of this A (planes, exponents, row maxima) made by a
@@ -1682,27 +1742,7 @@ cudaError_t launch_tc_gram(const TcPlan& p, const double* A, long lda, const dou
     mark(2);
     launch_slot_reduce(p, a1, L.U, mm, st, s);
     // C = Z^T U (left operand: Z's columns as rows, K-major), then G = C + C^T
-    split_tall_mode(p, s, L.U, mm, L.Up, L.eU, L.mU);
-    TcArgs a2 = make_args(p, nn, nn, mm, 0, p.N);
-    a2.cum = L.cum2;
-    a2.slots = L.slots;
-    a2.eA = L.eZ;
-    a2.eB = L.eU;
-    a2.emaxA = L.mZ;
-    a2.emaxB = L.mU;
-    a2.st = st;
-    a2.limit_ns = limit_ns;
-    item_prefix_kernel<<<1, PREFIX_THREADS, 0, s>>>(a2, L.cum2);
-    mark(3);
-    if ((e = launch_tc_mode(p, a2, L.Zp, planeZ, L.Up, planeZ, sms, s)) != cudaSuccess) return e;
-    mark(4);
-    launch_slot_reduce(p, a2, L.Cm, nn, st, s);
-    {
-        const long tot = (long)nn * nn;
-        symmetrize_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(nn, L.Cm, nn, G, ldg, shift_ptr, st);
-    }
-    mark(5);
-    return cudaGetLastError();
+    return tc_cross_phase(p, L, L.U, mm, G, ldg, shift_ptr, st, limit_ns, sms, s, ev);
 }
 
 // ------------------------------------------------------ blocked TRSM ----

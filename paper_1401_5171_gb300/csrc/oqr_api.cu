@@ -243,31 +243,71 @@ struct ASplit {
     bool emu = false;   // the workspace holds this call's EMU64-family split of A
 };
 
-// G = X^T A X (+ shift) in the requested arithmetic.
-cudaError_t form_gram(oqr_ctx* ctx, int prec, const GramPlan& gp, const double* A, long lda, const double* X,
-                      long ldx, double* partials, double* G, const double* shift_ptr, void* tcws, uint64_t limit,
-                      cudaStream_t s, ASplit* as = nullptr)
+// The operator A of a factorization: a dense SPD matrix read from its lower
+// triangle (A, lda), or a tridiagonal one (d: diagonal, m entries; e:
+// off-diagonal, m - 1 entries), Sec. 8's two workloads.
+struct AOp {
+    const double* A = nullptr;
+    long lda = 0;
+    const double* d = nullptr;
+    const double* e = nullptr;
+    bool tri() const { return d != nullptr; }
+};
+AOp dense_op(const double* A, long lda)
 {
+    AOp o;
+    o.A = A;
+    o.lda = lda;
+    return o;
+}
+
+// Splits of the FP64 GEMM X^T U of a tridiagonal pass (at most the dense plan's partial count, whose
+// buffer it reuses).
+int tri_splits(const GramPlan& gp, int sms)
+{
+    const int tiles = ((gp.n + 63) / 64) * ((gp.n + 63) / 64);
+    return std::max(1, std::min(std::min(64, gp.splits), 2 * sms / tiles));
+}
+
+// G = X^T A X (+ shift) in the requested arithmetic.  Tridiagonal A: U = M X
+// into Ubuf (m x n), C = X^T U (FP64 GEMM into Cbuf, n x n, or the tensor
+// cores), G = C + C^T.
+cudaError_t form_gram(oqr_ctx* ctx, int prec, const GramPlan& gp, const AOp& op, const double* X, long ldx,
+                      double* partials, double* G, const double* shift_ptr, void* tcws, uint64_t limit,
+                      cudaStream_t s, ASplit* as = nullptr, double* Ubuf = nullptr, double* Cbuf = nullptr)
+{
+    if (op.tri()) {
+        cudaError_t e = launch_tridiag_u(gp.m, gp.n, op.d, op.e, X, ldx, Ubuf, gp.m, s);
+        if (e != cudaSuccess) return e;
+        if (prec == OQR_FP64) {
+            e = launch_gemm_f64(GEMM_T, gp.n, gp.n, gp.m, 1.0, X, ldx, Ubuf, gp.m, 0.0, Cbuf, gp.n, partials,
+                                tri_splits(gp, ctx->sm_count), s);
+            if (e != cudaSuccess) return e;
+            return launch_sym_plus_transpose(gp.n, Cbuf, gp.n, G, gp.n, shift_ptr, ctx->st, s);
+        }
+        const TcPlan tp = tc_plan(gp.m, gp.n, tc_mode_of(prec), 0, true);
+        return launch_tc_cross(tp, X, ldx, Ubuf, gp.m, G, gp.n, shift_ptr, tcws, ctx->st, limit, ctx->sm_count, s);
+    }
     if (prec == OQR_FP64) {
-        cudaError_t e = launch_gram_f64(gp, A, lda, X, ldx, partials, ctx->st, limit, s);
+        cudaError_t e = launch_gram_f64(gp, op.A, op.lda, X, ldx, partials, ctx->st, limit, s);
         if (e != cudaSuccess) return e;
         return launch_gram_reduce(gp, partials, G, gp.n, shift_ptr, ctx->st, s);
     }
     const bool fam = emu_family(prec);
     const TcPlan tp = tc_plan(gp.m, gp.n, tc_mode_of(prec), (fam && as) ? as->sa : 0);
     const bool ready = fam && as && as->emu;
-    cudaError_t e = launch_tc_gram(tp, A, lda, X, ldx, G, gp.n, shift_ptr, tcws, ctx->st, limit, ctx->sm_count, s,
-                                   nullptr, ready);
+    cudaError_t e = launch_tc_gram(tp, op.A, op.lda, X, ldx, G, gp.n, shift_ptr, tcws, ctx->st, limit, ctx->sm_count,
+                                   s, nullptr, ready);
     if (as) as->emu = fam;  // any other tensor-core mode overwrites the region
     return e;
 }
 
-size_t tc_bytes_for(int m, int n, int prec_a, int prec_b, int sa = 0)
+size_t tc_bytes_for(int m, int n, int prec_a, int prec_b, int sa = 0, bool tri = false)
 {
     size_t b = 0;
     for (int pr : {prec_a, prec_b})
         if (pr != OQR_FP64)
-            b = std::max(b, tc_workspace_bytes(tc_plan(m, n, tc_mode_of(pr), emu_family(pr) ? sa : 0)));
+            b = std::max(b, tc_workspace_bytes(tc_plan(m, n, tc_mode_of(pr), (emu_family(pr) && !tri) ? sa : 0, tri)));
     return b;
 }
 
@@ -277,6 +317,7 @@ size_t tc_bytes_for(int m, int n, int prec_a, int prec_b, int sa = 0)
 struct NePlan {
     int passes = 0;
     bool shifted = false;
+    bool tri = false;  // tridiagonal A: no split of A, U = M X buffer (m x n) and C (n x n)
     int prec_first = 0, prec_mid = 0, prec_final = 0;
     int sa = 0;        // planes of A kept for the EMU64-family passes (7 with any FP64_TC, else 0)
     size_t tcb = 0;    // tensor-core Gram region
@@ -284,8 +325,9 @@ struct NePlan {
     int prec_of(int p) const { return p == passes - 1 ? prec_final : (p == 0 ? prec_first : prec_mid); }
 };
 
-oqr_status ne_plan(const oqr_opts& o, int forced_passes, int m, int n, NePlan* P)
+oqr_status ne_plan(const oqr_opts& o, int forced_passes, int m, int n, NePlan* P, bool tri = false)
 {
+    P->tri = tri;
     if (!prec_ok(o.prec) || !prec_ok(o.final_prec)) return OQR_ERR_INVALID_ARG;
     P->passes = forced_passes > 0 ? forced_passes : (o.shifted ? 3 : o.passes);
     if (P->passes < 1 || P->passes > 8) return OQR_ERR_INVALID_ARG;
@@ -295,13 +337,13 @@ oqr_status ne_plan(const oqr_opts& o, int forced_passes, int m, int n, NePlan* P
     P->prec_final = o.final_prec;
     P->prec_first = P->passes == 1 ? o.final_prec : o.prec;
     // one split of A for the EMU64-family passes and the tensor-core check: 7 planes when any of them is FP64_TC
-    P->sa = (P->prec_first == OQR_FP64_TC || P->prec_mid == OQR_FP64_TC || P->prec_final == OQR_FP64_TC ||
-             o.check == 2)
+    P->sa = (!tri && (P->prec_first == OQR_FP64_TC || P->prec_mid == OQR_FP64_TC || P->prec_final == OQR_FP64_TC ||
+                      o.check == 2))
                 ? 7
                 : 0;
-    P->tcb = tc_bytes_for(m, n, P->prec_first, P->prec_final, P->sa);
-    P->tcb = std::max(P->tcb, tc_bytes_for(m, n, P->prec_mid, P->prec_mid, P->sa));
-    if (o.check == 2) P->tcb = std::max(P->tcb, tc_bytes_for(m, n, OQR_FP64_TC, OQR_FP64_TC, P->sa));
+    P->tcb = tc_bytes_for(m, n, P->prec_first, P->prec_final, P->sa, tri);
+    P->tcb = std::max(P->tcb, tc_bytes_for(m, n, P->prec_mid, P->prec_mid, P->sa, tri));
+    if (o.check == 2) P->tcb = std::max(P->tcb, tc_bytes_for(m, n, OQR_FP64_TC, OQR_FP64_TC, P->sa, tri));
     // passes whose Gram runs on the tensor cores also solve Q = X / R with tensor-core products
     const bool any_tc = P->prec_first != OQR_FP64 || P->prec_mid != OQR_FP64 || P->prec_final != OQR_FP64;
     P->trb = any_tc ? trsm_tc_workspace_bytes(m, n) : 0;
@@ -311,6 +353,7 @@ oqr_status ne_plan(const oqr_opts& o, int forced_passes, int m, int n, NePlan* P
 struct NeBuffers {
     double *partials, *G, *work, *R1, *R2, *R3, *scratch;
     void *tcws, *trws;
+    double *U, *C;  // tridiagonal A: U = M X (m x n) and C = X^T U (n x n)
 };
 // base == nullptr: offsets only; returns the bytes.
 size_t ne_carve(void* base, const GramPlan& gp, const NePlan& P, NeBuffers* B)
@@ -319,21 +362,35 @@ size_t ne_carve(void* base, const GramPlan& gp, const NePlan& P, NeBuffers* B)
     layout_cholqr(c, gp, &B->partials, &B->G, &B->work, &B->R1, &B->R2, &B->R3, &B->scratch);
     B->tcws = c.take<char>(P.tcb);
     B->trws = c.take<char>(P.trb);
+    B->U = c.take<double>(P.tri ? (size_t)gp.m * gp.n : 0);
+    B->C = c.take<double>(P.tri ? (size_t)gp.n * gp.n : 0);
     return c.off;
 }
 
 // a_split_ready: the workspace's tensor-core region already holds the split of
 // this A made for the first pass's plan (the host-buffer path makes it while A
 // arrives), so the first EMU64-family pass does not make it again.
-oqr_status normal_equation(oqr_ctx* ctx, int m, int n, const double* A, long lda, const double* Z, long ldz,
-                           double* Q, long ldq, double* R, long ldr, const oqr_opts* opts_in, oqr_info* info,
-                           void* stream, int forced_passes, bool a_split_ready = false)
+oqr_status normal_equation(oqr_ctx* ctx, int m, int n, const AOp& op, const double* Z, long ldz, double* Q, long ldq,
+                           double* R, long ldr, const oqr_opts* opts_in, oqr_info* info, void* stream,
+                           int forced_passes, bool a_split_ready = false)
 {
-    oqr_status v = check_common(ctx, m, n, A, lda, Z, ldz, Q, ldq, R, ldr);
-    if (v != OQR_OK) return v;
+    oqr_status v;
+    if (op.tri()) {
+        if (!ctx || m < 1 || n < 1 || n > m || (m > 1 && !op.e) || bad_matrix(Z, ldz, m, n) ||
+            bad_matrix(Q, ldq, m, n) || bad_matrix(R, ldr, n, n))
+            return OQR_ERR_INVALID_ARG;
+        if (n > 1024) return OQR_ERR_UNSUPPORTED;
+        if (Q != Z) {
+            const char *q0 = reinterpret_cast<const char*>(Q), *q1 = reinterpret_cast<const char*>(Q + (size_t)ldq * (n - 1) + m);
+            const char *z0 = reinterpret_cast<const char*>(Z), *z1 = reinterpret_cast<const char*>(Z + (size_t)ldz * (n - 1) + m);
+            if (q0 < z1 && z0 < q1) return OQR_ERR_INVALID_ARG;
+        }
+    } else if ((v = check_common(ctx, m, n, op.A, op.lda, Z, ldz, Q, ldq, R, ldr)) != OQR_OK) {
+        return v;
+    }
     const oqr_opts o = resolve(opts_in);
     NePlan P;
-    if ((v = ne_plan(o, forced_passes, m, n, &P)) != OQR_OK) return v;
+    if ((v = ne_plan(o, forced_passes, m, n, &P, op.tri())) != OQR_OK) return v;
     const int passes = P.passes;
     const bool shifted = P.shifted;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -351,12 +408,18 @@ oqr_status normal_equation(oqr_ctx* ctx, int m, int n, const double* A, long lda
     ASplit as;
     as.sa = P.sa;
     as.emu = a_split_ready && emu_family(prec_first);
+    ASplit* asp = op.tri() ? nullptr : &as;  // a tridiagonal A has no split to share
     if ((v = reset_status(ctx, s)) != OQR_OK) return v;
 
     const double* shift_ptr = nullptr;
     const bool trace_shift = shifted && (prec_first == OQR_BF16X3 || prec_first == OQR_FP8 || prec_first == OQR_TC2);
     if (shifted && !trace_shift) {
-        OQR_TRY(launch_norms_and_shift(m, n, A, lda, Z, ldz, o.shift_c, U64, scratch, 2 * SHIFT_PARTS, ctx->st, s));
+        if (op.tri())
+            OQR_TRY(launch_tridiag_norms_and_shift(m, n, op.d, op.e, Z, ldz, o.shift_c, U64, scratch, 2 * SHIFT_PARTS,
+                                                   ctx->st, s));
+        else
+            OQR_TRY(launch_norms_and_shift(m, n, op.A, op.lda, Z, ldz, o.shift_c, U64, scratch, 2 * SHIFT_PARTS,
+                                           ctx->st, s));
         shift_ptr = &ctx->st->shift;
     }
     // R accumulates as R_p ... R_1; Racc alternates between R2 and R3.
@@ -368,8 +431,8 @@ oqr_status normal_equation(oqr_ctx* ctx, int m, int n, const double* A, long lda
         double* Rp = (passes == 1) ? R : R1;
         const long ldrp = (passes == 1) ? ldr : n;
         const int prec = prec_of(p);
-        OQR_TRY(form_gram(ctx, prec, gp, A, lda, X, ldx, partials, G, p == 0 ? shift_ptr : nullptr, tcws, limit, s,
-                          &as));
+        OQR_TRY(form_gram(ctx, prec, gp, op, X, ldx, partials, G, p == 0 ? shift_ptr : nullptr, tcws, limit, s, asp,
+                          B.U, B.C));
         if (p == 0 && trace_shift)  // u of the first pass's products: 2^-16 (BF16X3, TC2) or 2^-4 (E4M3)
             OQR_TRY(launch_trace_shift(n, G, n, o.shift_c, prec == OQR_FP8 ? 0.0625 : 1.52587890625e-05, ctx->st, s));
         OQR_TRY(launch_potrf(n, G, n, Rp, ldrp, nullptr, ctx->st, s));
@@ -393,9 +456,14 @@ oqr_status normal_equation(oqr_ctx* ctx, int m, int n, const double* A, long lda
         ldx = ldq;
     }
     if (o.check) {
-        if ((v = run_check(ctx, gp, A, lda, Q, ldq, partials, G, work, nullptr, 0, limit, s,
-                           o.check == 2 ? tcws : nullptr, as.emu && as.sa == 7)) != OQR_OK)
+        if (op.tri()) {
+            OQR_TRY(form_gram(ctx, o.check == 2 ? OQR_FP64_TC : OQR_FP64, gp, op, Q, ldq, partials, G, nullptr, tcws,
+                              limit, s, nullptr, B.U, B.C));
+            OQR_TRY(launch_check_finish(n, G, n, nullptr, 0, work, ctx->st, s));
+        } else if ((v = run_check(ctx, gp, op.A, op.lda, Q, ldq, partials, G, work, nullptr, 0, limit, s,
+                                  o.check == 2 ? tcws : nullptr, as.emu && as.sa == 7)) != OQR_OK) {
             return v;
+        }
     }
     return finish(ctx, s, info, passes, o.check != 0);
 }
@@ -625,13 +693,13 @@ oqr_status oqr_get_status(oqr_ctx* ctx, void* stream, int* info)
 oqr_status oqr_cholqr(oqr_ctx* ctx, int m, int n, const double* A, long lda, const double* Z, long ldz, double* Q,
                       long ldq, double* R, long ldr, const oqr_opts* opts, oqr_info* info, void* stream)
 {
-    return normal_equation(ctx, m, n, A, lda, Z, ldz, Q, ldq, R, ldr, opts, info, stream, 1);
+    return normal_equation(ctx, m, n, dense_op(A, lda), Z, ldz, Q, ldq, R, ldr, opts, info, stream, 1);
 }
 
 oqr_status oqr_cholqr2(oqr_ctx* ctx, int m, int n, const double* A, long lda, const double* Z, long ldz,
                        double* Q, long ldq, double* R, long ldr, const oqr_opts* opts, oqr_info* info, void* stream)
 {
-    return normal_equation(ctx, m, n, A, lda, Z, ldz, Q, ldq, R, ldr, opts, info, stream, 0);
+    return normal_equation(ctx, m, n, dense_op(A, lda), Z, ldz, Q, ldq, R, ldr, opts, info, stream, 0);
 }
 
 oqr_status oqr_cholqr2_host(oqr_ctx* ctx, int m, int n, const double* A, long lda, const double* Z, long ldz,
@@ -707,7 +775,8 @@ oqr_status oqr_cholqr2_host(oqr_ctx* ctx, int m, int n, const double* A, long ld
     }
     if (!split_early) OQR_TRY(cudaStreamWaitEvent(s, ctx->events[panels - 1], 0));
     OQR_TRY(cudaStreamWaitEvent(s, ev_z, 0));
-    if ((v = normal_equation(ctx, m, n, Ad, ldA, Zd, m, Qd, m, Rd, n, &o, nullptr, stream, 0, split_early)) != OQR_OK)
+    if ((v = normal_equation(ctx, m, n, dense_op(Ad, ldA), Zd, m, Qd, m, Rd, n, &o, nullptr, stream, 0,
+                             split_early)) != OQR_OK)
         return v;
     OQR_TRY(cudaMemcpy2DAsync(Q, (size_t)ldq * 8, Qd, (size_t)m * 8, (size_t)m * 8, n, cudaMemcpyDeviceToHost, s));
     OQR_TRY(cudaMemcpy2DAsync(R, (size_t)ldr * 8, Rd, (size_t)n * 8, (size_t)n * 8, n, cudaMemcpyDeviceToHost, s));
@@ -1233,6 +1302,94 @@ oqr_status oqr_repres(oqr_ctx* ctx, int m, int n, const double* Z, long ldz, con
     if (cudaStreamSynchronize(s) != cudaSuccess) return OQR_ERR_CUDA;
     if (res2) *res2 = h[2] > 0.0 ? std::sqrt(h[0] / h[2]) : 0.0;
     if (resF) *resF = h[3] > 0.0 ? std::sqrt(h[1] / h[3]) : 0.0;
+    return OQR_OK;
+}
+
+oqr_status oqr_cholqr2_tridiag(oqr_ctx* ctx, int m, int n, const double* d, const double* e, const double* Z, long ldz,
+                               double* Q, long ldq, double* R, long ldr, const oqr_opts* opts, oqr_info* info,
+                               void* stream)
+{
+    if (!d) return OQR_ERR_INVALID_ARG;
+    AOp op;
+    op.d = d;
+    op.e = e;
+    return normal_equation(ctx, m, n, op, Z, ldz, Q, ldq, R, ldr, opts, info, stream, 0);
+}
+
+oqr_status oqr_gram_tridiag(oqr_ctx* ctx, int m, int n, const double* d, const double* e, const double* Z, long ldz,
+                            double* G, long ldg, int prec, void* stream)
+{
+    if (!ctx || !d || (m > 1 && !e) || m < 1 || n < 1 || n > m || bad_matrix(Z, ldz, m, n) ||
+        bad_matrix(G, ldg, n, n))
+        return OQR_ERR_INVALID_ARG;
+    if (!prec_ok(prec)) return OQR_ERR_INVALID_ARG;
+    if (n > 1024) return OQR_ERR_UNSUPPORTED;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const GramPlan gp = gram_plan(m, n, ctx->sm_count);
+    AOp op;
+    op.d = d;
+    op.e = e;
+    const size_t tcb = prec == OQR_FP64 ? 0 : tc_workspace_bytes(tc_plan(m, n, tc_mode_of(prec), 0, true));
+    auto layout = [&](Carve& c, double** part, double** Ub, double** Cb, double** Gt, void** tcws) {
+        *part = c.take<double>(gram_partials_bytes(gp) / sizeof(double));
+        *Ub = c.take<double>((size_t)m * n);
+        *Cb = c.take<double>((size_t)n * n);
+        *Gt = c.take<double>((size_t)n * n);
+        *tcws = c.take<char>(tcb);
+    };
+    double *part, *Ub, *Cb, *Gt;
+    void* tcws;
+    Carve probe(nullptr);
+    layout(probe, &part, &Ub, &Cb, &Gt, &tcws);
+    oqr_status v = ensure_ws(ctx, probe.off);
+    if (v != OQR_OK) return v;
+    Carve c(ctx->ws);
+    layout(c, &part, &Ub, &Cb, &Gt, &tcws);
+    if ((v = reset_status(ctx, s)) != OQR_OK) return v;
+    OQR_TRY(form_gram(ctx, prec, gp, op, Z, ldz, part, Gt, nullptr, tcws, 4000000000ull, s, nullptr, Ub, Cb));
+    OQR_TRY(cudaMemcpy2DAsync(G, ldg * sizeof(double), Gt, n * sizeof(double), n * sizeof(double), n,
+                              cudaMemcpyDeviceToDevice, s));
+    return OQR_OK;
+}
+
+oqr_status oqr_symm(oqr_ctx* ctx, int m, int k, const double* A, long lda, const double* B, long ldb, double* C,
+                    long ldc, void* stream)
+{
+    if (!ctx || m < 1 || k < 1 || bad_matrix(A, lda, m, m) || bad_matrix(B, ldb, m, k) || bad_matrix(C, ldc, m, k))
+        return OQR_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    oqr_status v = ensure_ws(ctx, align256(symm_workspace_doubles(m, k) * sizeof(double)));
+    if (v != OQR_OK) return v;
+    OQR_TRY(launch_symm(m, k, A, lda, B, ldb, C, ldc, static_cast<double*>(ctx->ws), ctx->sm_count, s));
+    return OQR_OK;
+}
+
+oqr_status oqr_glls(oqr_ctx* ctx, int m, int n, int k, const double* A, long lda, const double* Q, long ldq,
+                    const double* R, long ldr, const double* B, long ldb, double* X, long ldx, void* stream)
+{
+    if (!ctx || m < 1 || n < 1 || n > m || k < 1 || bad_matrix(A, lda, m, m) || bad_matrix(Q, ldq, m, n) ||
+        bad_matrix(R, ldr, n, n) || bad_matrix(B, ldb, m, k) || bad_matrix(X, ldx, n, k))
+        return OQR_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // C = A B (m x k), Y = Q^T C (n x k, split along m), X = R^{-1} Y
+    const int tiles = ((n + 63) / 64) * ((k + 63) / 64);
+    const int splits = std::max(1, std::min(64, 2 * ctx->sm_count / tiles));
+    auto layout = [&](Carve& c, double** part, double** Cm, double** Y, double** ws) {
+        *part = c.take<double>(symm_workspace_doubles(m, k));
+        *Cm = c.take<double>((size_t)m * k);
+        *Y = c.take<double>((size_t)n * k);
+        *ws = c.take<double>(gemm_splitk_bytes(n, k, splits) / sizeof(double) + 1);
+    };
+    Carve probe(nullptr);
+    double *part, *Cm, *Y, *ws;
+    layout(probe, &part, &Cm, &Y, &ws);
+    oqr_status v = ensure_ws(ctx, probe.off);
+    if (v != OQR_OK) return v;
+    Carve c(ctx->ws);
+    layout(c, &part, &Cm, &Y, &ws);
+    OQR_TRY(launch_symm(m, k, A, lda, B, ldb, Cm, m, part, ctx->sm_count, s));
+    OQR_TRY(launch_gemm_f64(GEMM_T, n, k, m, 1.0, Q, ldq, Cm, m, 0.0, Y, n, ws, splits, s));
+    OQR_TRY(launch_upper_solve(n, k, R, ldr, Y, n, X, ldx, s));
     return OQR_OK;
 }
 

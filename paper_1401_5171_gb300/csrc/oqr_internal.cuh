@@ -210,8 +210,9 @@ struct TcPlan {
     long ldp;       // leading dimension of the slice planes
     int kch;        // exponent chunks of the contraction (256 long; 128 for FP8)
     int nitems_max; // work items of the larger of the two products
+    int noA;        // 1: no planes of A (only C = X^T U; launch_tc_cross)
 };
-TcPlan tc_plan(int m, int n, int mode, int sa = 0);
+TcPlan tc_plan(int m, int n, int mode, int sa = 0, bool no_a = false);
 size_t tc_plan_bytes(const TcPlan& p);
 size_t tc_workspace_bytes(const TcPlan& p);
 // The split of A made chunk by chunk (host-buffer path: each 256-column chunk as it arrives).
@@ -220,6 +221,22 @@ cudaError_t tc_split_a_chunk(const TcPlan& p, const double* A, long lda, int kc,
 cudaError_t launch_tc_gram(const TcPlan& p, const double* A, long lda, const double* Z, long ldz, double* G, long ldg,
                            const double* shift_ptr, void* ws, DevStatus* st, uint64_t limit_ns, int sms,
                            cudaStream_t s, cudaEvent_t* ev = nullptr, bool a_ready = false);
+
+// G = C + C^T (+ shift) with C = X^T U on the tensor cores, U = M X formed by
+// the caller (FP64, m x n); p from tc_plan(m, n, mode, 0, true).
+cudaError_t launch_tc_cross(const TcPlan& p, const double* X, long ldx, const double* U, long ldu, double* G, long ldg,
+                            const double* shift_ptr, void* ws, DevStatus* st, uint64_t limit_ns, int sms,
+                            cudaStream_t s);
+
+// Tridiagonal A (k_tridiag.cu): d (m), e (m - 1); U = M X with M = tril(T, -1) + diag(T) / 2.
+cudaError_t launch_tridiag_u(int m, int n, const double* d, const double* e, const double* X, long ldx, double* U,
+                             long ldu, cudaStream_t s);
+cudaError_t launch_tridiag_norms_and_shift(int m, int n, const double* d, const double* e, const double* X, long ldx,
+                                           double c, double u, double* scratch, int scratch_len, DevStatus* st,
+                                           cudaStream_t s);
+// G = C + C^T (+ shift I), n x n (FP64).
+cudaError_t launch_sym_plus_transpose(int n, const double* C, long ldc, double* G, long ldg, const double* shift_ptr,
+                                      const DevStatus* st, cudaStream_t s);
 
 // Blocked TRSM Q = Z / R with FP64-accurate tensor-core products for the
 // off-diagonal blocks and FP64 substitution for the 64 x 64 diagonal blocks
@@ -342,6 +359,15 @@ cudaError_t launch_adam(int n, float* P, const float* g, float* m, float* v, flo
 cudaError_t launch_features(int m, int n, const double* G, long ldg, double* work, const DevStatus* st, float* feat,
                             cudaStream_t s);
 cudaError_t launch_trace_shift(int n, double* G, long ldg, double c, double u, DevStatus* st, cudaStream_t s);
+
+// C = A B (m x k) for symmetric A read from its lower triangle (k_glls.cu): 64 x 64 tiles of the
+// lower triangle, per-tile partials (symm_workspace_doubles(m, k) doubles), fixed-order sum.
+size_t symm_workspace_doubles(int m, int k);
+cudaError_t launch_symm(int m, int k, const double* A, long lda, const double* B, long ldb, double* C, long ldc,
+                        double* part, int sms, cudaStream_t s);
+// X = R^{-1} Y for upper triangular R (n x n) and k right-hand sides; X may alias Y.
+cudaError_t launch_upper_solve(int n, int k, const double* R, long ldr, const double* Y, long ldy, double* X,
+                               long ldx, cudaStream_t s);
 
 // Y = alpha X + beta Y (M x N, column-major).
 cudaError_t launch_axpby(int M, int N, double alpha, const double* X, long ldx, double beta, double* Y, long ldy,

@@ -36,7 +36,7 @@ import numpy as np
 
 __all__ = [
     "eigenvalues", "singular_values", "haar", "paper_case", "config0",
-    "DenseSPD", "dense_spd", "tall_z", "batch_shapes",
+    "DenseSPD", "dense_spd", "tall_z", "batch_shapes", "tridiag_spd", "laplacian_eigvec",
 ]
 
 
@@ -222,3 +222,24 @@ def batch_instances(count: int, seed: int, device="cpu", m_range=(64, 4096), n_r
         Z = tall_z(int(m[b]), int(n[b]), float(kz[b]), seed=int(seeds[b]) + 1, device=device)
         Zs.append(Z.t().contiguous().t())
     return As, Zs, {"m": m, "n": n, "kappa_A": ka, "kappa_Z": kz, "seed": seeds}
+
+
+def tridiag_spd(m: int, kappa: float):
+    """Tridiagonal SPD T for Sec. 8's tridiagonal workload (the paper does not give its entries): the
+    1-D Laplacian tridiag(-1, 2, -1) shifted by mu I, with mu chosen so that kappa(T) = kappa exactly.
+    Its eigenvalues are mu + 2 - 2 cos(k pi / (m + 1)), k = 1..m.  Returns (d, e) as float64 arrays
+    (e has m - 1 entries)."""
+    if m == 1:
+        return np.ones(1), np.zeros(0)
+    a = 2.0 - 2.0 * math.cos(math.pi / (m + 1))        # smallest Laplacian eigenvalue
+    b = 2.0 + 2.0 * math.cos(math.pi / (m + 1))        # largest
+    mu = (b - kappa * a) / (kappa - 1.0) if kappa > 1.0 else 1.0
+    return np.full(m, 2.0 + mu), np.full(m - 1, -1.0)
+
+
+def laplacian_eigvec(m: int, ks) -> np.ndarray:
+    """Orthonormal eigenvectors of tridiag(-1, 2, -1) (any diagonal shift), v_k(i) =
+    sqrt(2 / (m + 1)) sin(i k pi / (m + 1)), i, k = 1..m; columns for the given k (1-based)."""
+    i = np.arange(1, m + 1, dtype=np.float64)[:, None]
+    k = np.asarray(ks, dtype=np.float64)[None, :]
+    return np.sqrt(2.0 / (m + 1)) * np.sin(i * k * math.pi / (m + 1))

@@ -109,6 +109,10 @@ def load(path: str | None = None):
     lib.oqr_repres.argtypes = [vp, i, i, vp, l, vp, l, vp, l, ctypes.POINTER(d), ctypes.POINTER(d), vp]
     lib.oqr_diag_timeout.argtypes = [vp, l, vp]
     lib.oqr_set_batch_budget.argtypes = [vp, ctypes.c_size_t]
+    lib.oqr_glls.argtypes = [vp, i, i, i, vp, l, vp, l, vp, l, vp, l, vp, l, vp]
+    lib.oqr_cholqr2_tridiag.argtypes = [vp, i, i, vp, vp, vp, l, vp, l, vp, l, po, pi, vp]
+    lib.oqr_gram_tridiag.argtypes = [vp, i, i, vp, vp, vp, l, vp, l, i, vp]
+    lib.oqr_symm.argtypes = [vp, i, i, vp, l, vp, l, vp, l, vp]
     for name in declared_functions():
         f = getattr(lib, name)
         if f.restype is ctypes.c_int or name not in ("oqr_default_opts", "oqr_status_string"):
@@ -133,7 +137,7 @@ def _raw(name):
 for _n in ("oqr_default_opts", "oqr_create", "oqr_destroy", "oqr_workspace_size", "oqr_set_workspace",
            "oqr_get_status", "oqr_cholqr", "oqr_cholqr2", "oqr_cholqr2_host", "oqr_cgs2", "oqr_gram", "oqr_gram_noalloc", "oqr_gram_phases", "oqr_potrf", "oqr_trsm", "oqr_trsm_tc",
            "oqr_rprod", "oqr_check", "oqr_repres", "oqr_diag_timeout", "oqr_set_batch_budget", "oqr_batched", "oqr_batched_mixed", "oqr_batched_default_splits", "oqr_features",
-           "oqr_mlp_param_count", "oqr_mlp_forward", "oqr_mlp_grad", "oqr_mlp_adam"):
+           "oqr_mlp_param_count", "oqr_mlp_forward", "oqr_mlp_grad", "oqr_mlp_adam", "oqr_glls", "oqr_symm", "oqr_cholqr2_tridiag", "oqr_gram_tridiag"):
     globals()[_n] = _raw(_n)
 
 
@@ -170,6 +174,15 @@ def _m(x, host=False):
     if ld is None:
         raise ValueError("matrix must be 2-D column-major (stride(0) == 1); use colmajor()")
     return ctypes.c_void_p(x.data_ptr()), ctypes.c_long(max(1, ld))
+
+
+def _vec(x, length):
+    """Device pointer of a contiguous 1-D float64 CUDA tensor of at least `length` entries (None if length 0)."""
+    if length <= 0:
+        return None if x is None else ctypes.c_void_p(x.data_ptr())
+    if x is None or x.dim() != 1 or x.dtype.itemsize != 8 or not x.is_cuda or x.stride(0) != 1 or x.numel() < length:
+        raise ValueError("expected a contiguous 1-D float64 CUDA tensor")
+    return ctypes.c_void_p(x.data_ptr())
 
 
 def empty_colmajor(rows, cols, device, dtype=None):
@@ -444,6 +457,62 @@ class Oqr:
         st = self.lib.oqr_set_workspace(self.ctx, ctypes.c_void_p(ptr) if ptr else None, int(nbytes))
         if st != OQR_OK:
             raise OqrError(st, "oqr_set_workspace")
+
+    def oqr_cholqr2_tridiag(self, d, e, Z, Q=None, R=None, opts=None, stream=None, sync=True, raise_on_error=True,
+                            **kw):
+        """The normal-equation method for tridiagonal A (diagonal d, off-diagonal e: 1-D float64 CUDA tensors);
+        returns (Q, R, (status, info))."""
+        m, n = Z.shape
+        Q = Q if Q is not None else empty_colmajor(m, n, Z.device)
+        R = R if R is not None else empty_colmajor(n, n, Z.device)
+        o = opts if opts is not None else make_opts(**kw)
+        info = oqr_info()
+        z, ldz = _m(Z)
+        q, ldq = _m(Q)
+        r, ldr = _m(R)
+        st = self.lib.oqr_cholqr2_tridiag(self.ctx, m, n, _vec(d, m), _vec(e, m - 1), z, ldz, q, ldq, r, ldr,
+                                          ctypes.byref(o), ctypes.byref(info) if sync else None, self._stream(stream))
+        if st != OQR_OK and raise_on_error:
+            raise OqrError(st, "oqr_cholqr2_tridiag", info.info)
+        return Q, R, (st, info)
+
+    def oqr_gram_tridiag(self, d, e, Z, G=None, prec=OQR_FP64, stream=None):
+        m, n = Z.shape
+        G = G if G is not None else empty_colmajor(n, n, Z.device)
+        z, ldz = _m(Z)
+        g, ldg = _m(G)
+        st = self.lib.oqr_gram_tridiag(self.ctx, m, n, _vec(d, m), _vec(e, m - 1), z, ldz, g, ldg, prec,
+                                       self._stream(stream))
+        if st != OQR_OK:
+            raise OqrError(st, "oqr_gram_tridiag")
+        return G
+
+    def oqr_symm(self, A, B, C=None, stream=None):
+        """C = A B for symmetric A (lower triangle read)."""
+        m, k = B.shape
+        C = C if C is not None else empty_colmajor(m, k, B.device)
+        a, lda = _m(A)
+        b, ldb = _m(B)
+        c, ldc = _m(C)
+        st = self.lib.oqr_symm(self.ctx, m, k, a, lda, b, ldb, c, ldc, self._stream(stream))
+        if st != OQR_OK:
+            raise OqrError(st, "oqr_symm")
+        return C
+
+    def oqr_glls(self, A, Q, R, B, X=None, stream=None):
+        """x = R^{-1} Q^T A b for each column b of B (Sec. 1's generalized least squares)."""
+        m, n = Q.shape
+        k = B.shape[1]
+        X = X if X is not None else empty_colmajor(n, k, B.device)
+        a, lda = _m(A)
+        q, ldq = _m(Q)
+        r, ldr = _m(R)
+        b, ldb = _m(B)
+        x, ldx = _m(X)
+        st = self.lib.oqr_glls(self.ctx, m, n, k, a, lda, q, ldq, r, ldr, b, ldb, x, ldx, self._stream(stream))
+        if st != OQR_OK:
+            raise OqrError(st, "oqr_glls")
+        return X
 
     def oqr_repres(self, Z, Q, R, stream=None):
         """(||Z - Q R||_2 / ||Z||_2 estimate, ||Z - Q R||_F / ||Z||_F)."""

@@ -391,9 +391,10 @@ def test_shift_value_matches_its_formula(env, prec):
     A, Z = inputs.paper_case(4, m, n, 1e4, 1e6, seed=17)
     P = np.tril(A)                                       # the upper triangle must not enter ||A||_F
     P[np.triu_indices(m, 1)] = 7.0
+    # (first pass, later passes): a low-precision first pass is followed by FP64-accurate passes
     code = {"fp64": (0, 0), "fp64tc": (3, 3), "bf16x3": (1, 3), "tc2": (4, 3)}[prec]
     _, _, (st, info) = ctx.oqr_cholqr2(dev(torch, P, oqr), dev(torch, Z, oqr), shifted=1, prec=code[0],
-                                       final_prec=code[1])
+                                       prec_mid=code[1], final_prec=code[1])
     assert st == 0
     if prec in ("fp64", "fp64tc"):
         ref = 11 * U * (m * n + n * (n + 1)) * np.linalg.norm(A) * np.linalg.norm(Z) ** 2

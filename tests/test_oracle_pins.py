@@ -302,3 +302,53 @@ def test_cpu_method_cholqr2_reaches_the_oracle():
     Q, R = oracle.cpu_cholqr2(A, Z)
     assert np.linalg.norm(R - Rr) / np.linalg.norm(Rr) <= 1e-12
     assert oracle.orth_error(A, Q) <= 1e-12
+
+
+def test_glls_oracle_pins():
+    """The oracle's GLLS (x = R^{-1} Q^T A b, Sec. 1) against what fixes it: a consistent system returns
+    its planted solution, A = I reduces to LAPACK's least squares, and the residual is A-orthogonal to
+    range(Z) (the normal equations Z^T A (b - Z x) = 0)."""
+    rng = np.random.default_rng(12)
+    A, Z = inputs.paper_case(4, 300, 12, 1e3, 1e2, seed=12)
+    x0 = rng.standard_normal((12, 2))
+    X = oracle.glls(A, Z, Z @ x0)
+    assert np.abs(X - x0).max() <= 1e-10 * np.abs(x0).max()
+    B = rng.standard_normal((300, 3))
+    X = oracle.glls(np.eye(300), Z, B)
+    Xl = np.linalg.lstsq(Z, B, rcond=None)[0]
+    assert np.abs(X - Xl).max() <= 1e-10 * np.abs(Xl).max()
+    X = oracle.glls(A, Z, B)
+    g = Z.T @ A @ (B - Z @ X)
+    assert np.abs(g).max() <= 1e-10 * (np.abs(Z).T @ np.abs(A) @ np.abs(B)).max()
+
+
+def test_tridiag_oracle_pins():
+    """The tridiagonal oracle (CHOL-EQR with T's bidiagonal Cholesky factor) against the dense oracle on
+    the same T, against LAPACK's QR for T = I, and against the closed form of an eigenvector basis:
+    Z = V_k diag(lambda_k^(-1/2)) with T v_k = lambda_k v_k gives Z^T T Z = I, so R = I and Q = Z."""
+    m, n = 300, 11
+    d, e = inputs.tridiag_spd(m, 1e4)
+    T = oracle.tridiag_dense(d, e)
+    lam = np.linalg.eigvalsh(T)
+    assert abs(lam.max() / lam.min() / 1e4 - 1) < 1e-9
+    _, Z = inputs.paper_case(4, m, n, 1e2, 1e3, seed=14)
+    Qd, Rd = oracle.oblique_qr(T, Z)
+    Qt, Rt = oracle.oblique_qr_tridiag(d, e, Z)
+    assert np.linalg.norm(Rt - Rd) / np.linalg.norm(Rd) <= 1e-13
+    assert np.linalg.norm(Qt - Qd) / np.linalg.norm(Qd) <= 1e-12
+    assert abs(oracle.orth_error_tridiag(d, e, Qt) - oracle.orth_error(T, Qt)) <= 1e-15
+    Qi, Ri = oracle.oblique_qr_tridiag(np.ones(m), np.zeros(m - 1), Z)
+    Ql, Rl = np.linalg.qr(Z)
+    D = np.sign(np.diag(Rl))
+    assert np.abs(Ri - (Rl.T * D).T).max() <= 1e-13 * np.abs(Rl).max()
+    assert np.abs(Qi - Ql * D).max() <= 10 * 1e3 * 2.0 ** -53 * 300    # Q is kappa(Z) u sensitive
+    ks = [1, 2, 5, 150, 299, 300]
+    V = inputs.laplacian_eigvec(m, ks)
+    lamk = (d[0] - 2.0) + 2.0 - 2.0 * np.cos(np.asarray(ks) * np.pi / (m + 1))
+    Z5 = V / np.sqrt(lamk)
+    Q5, R5 = oracle.oblique_qr_tridiag(d, e, Z5)
+    assert np.abs(R5 - np.eye(len(ks))).max() <= 1e-10
+    assert np.abs(Q5 - Z5).max() <= 1e-10 * np.abs(Z5).max()
+    with pytest.raises(oracle.OracleBreakdown) as err:
+        oracle.oblique_qr_tridiag(np.array([1.0, 1.0, 1.0]), np.array([0.0, 2.0]), Z[:3, :2])
+    assert err.value.column == 3
