@@ -78,6 +78,8 @@ typedef struct {
     int final_prec;   /* oqr_cholqr2: oqr_precision of the last pass [OQR_FP64]; the last pass sets the
                          final orthogonality, so FP64-level results need OQR_FP64 or OQR_FP64_TC */
     int prec_mid;     /* passes between the first and the last: oqr_precision, or -1 = same as prec [-1] */
+    int reuse_w;      /* oqr_cholqr2 (FP64, two passes, dense A): 1 = form W = A Z once and take the second
+                         pass's A Q_1 as W R_1^{-1} instead of a second product with A [0] */
 } oqr_opts;
 
 /* Optional per-call report (filled only when passed non-NULL). */
@@ -148,6 +150,15 @@ oqr_status oqr_cholqr(oqr_ctx* ctx, int m, int n, const double* A, long lda, con
  * or FP64_TC, and c u trace(G) (u = 2^-16, G the pass's BF16X3 matrix) when
  * it is BF16X3, whose rounding error scales with G rather than with the
  * worst-case bound.
+ * With opts->reuse_w = 1 (FP64 only, two passes, not shifted; anything else
+ * returns OQR_ERR_UNSUPPORTED) the first pass keeps W = A Z (one FP64 product
+ * over A's lower triangle, m x n of workspace) and the second pass takes
+ * A Q_1 = W R_1^{-1} (a triangular solve, O(m n^2)) instead of a second
+ * product with A: Q_1 = Z R_1^{-1}, G_2 = Q_1^T (W R_1^{-1}), R_2 = chol(G_2),
+ * Q = Q_1 R_2^{-1}, R = R_2 R_1.  The paper has no such variant; it trades
+ * accuracy (A Q_1's rounding is no longer that of a fresh product, so the
+ * loss of orthogonality keeps one factor of kappa(A^{1/2} Z)) for the second
+ * product with A.
  */
 oqr_status oqr_cholqr2(oqr_ctx* ctx, int m, int n, const double* A, long lda, const double* Z, long ldz,
                        double* Q, long ldq, double* R, long ldr, const oqr_opts* opts, oqr_info* info,

@@ -269,3 +269,17 @@ def tridiag_dense(d, e):
     if m > 1:
         T += np.diag(np.asarray(e, dtype=np.float64)[:m - 1], -1) + np.diag(np.asarray(e, dtype=np.float64)[:m - 1], 1)
     return T
+
+
+def cholqr2_reuse_w(A, Z):
+    """A-CholQR2 with the first pass's W = A Z kept (not in the paper), restated on the CPU from the oracle's
+    pinned steps: W = A Z; R_1 = chol(Z^T W); Q_1 = Z / R_1; W_1 = W / R_1; R_2 = chol(Q_1^T W_1);
+    Q = Q_1 / R_2; R = R_2 R_1.  The reference for the GPU variant's own rounding, not the oracle of the
+    result (that is oblique_qr)."""
+    A, Z = _f(A), _f(Z)
+    W = symm_times(A, Z)
+    R1 = chol_upper(Z.T @ W)
+    Q1 = trsm_right_upper(Z, R1)
+    W1 = trsm_right_upper(W, R1)
+    R2 = chol_upper(Q1.T @ W1)
+    return trsm_right_upper(Q1, R2), upper_times_upper(R2, R1)

@@ -69,6 +69,7 @@ void fill_defaults(oqr_opts* o)
     o->spin_limit = 4000000000L;
     o->final_prec = OQR_FP64;
     o->prec_mid = -1;
+    o->reuse_w = 0;
 }
 
 oqr_opts resolve(const oqr_opts* o)
@@ -468,6 +469,54 @@ oqr_status normal_equation(oqr_ctx* ctx, int m, int n, const AOp& op, const doub
     return finish(ctx, s, info, passes, o.check != 0);
 }
 
+// A-CholQR2 with the first pass's W = A Z kept: A Q_1 = W R_1^{-1} replaces the
+// second product with A (FP64, dense A).
+oqr_status cholqr2_reuse_w(oqr_ctx* ctx, int m, int n, const double* A, long lda, const double* Z, long ldz,
+                           double* Q, long ldq, double* R, long ldr, const oqr_opts& o, oqr_info* info,
+                           cudaStream_t s)
+{
+    oqr_status v = check_common(ctx, m, n, A, lda, Z, ldz, Q, ldq, R, ldr);
+    if (v != OQR_OK) return v;
+    if (o.shifted || o.passes != 2 || o.prec != OQR_FP64 || o.final_prec != OQR_FP64 ||
+        (o.prec_mid != -1 && o.prec_mid != OQR_FP64) || o.check == 2)
+        return OQR_ERR_UNSUPPORTED;
+    const uint64_t limit = (uint64_t)o.spin_limit;
+    const GramPlan gp = gram_plan(m, n, ctx->sm_count);
+    const int tiles = ((n + 63) / 64) * ((n + 63) / 64);
+    const int splits = std::max(1, std::min(64, 2 * ctx->sm_count / tiles));
+    auto layout = [&](Carve& c, double** W, double** sk, double** G, double** R1, double** R2, double** partials,
+                      double** work) {
+        *W = c.take<double>((size_t)m * n);
+        *sk = c.take<double>(gemm_splitk_bytes(n, n, splits) / sizeof(double) + 1);
+        *G = c.take<double>((size_t)n * n);
+        *R1 = c.take<double>((size_t)n * n);
+        *R2 = c.take<double>((size_t)n * n);
+        *partials = c.take<double>(o.check ? gram_partials_bytes(gp) / sizeof(double) : 0);
+        *work = c.take<double>((size_t)n * n + 2 * n);
+    };
+    double *W, *sk, *G, *R1, *R2, *partials, *work;
+    Carve probe(nullptr);
+    layout(probe, &W, &sk, &G, &R1, &R2, &partials, &work);
+    if ((v = ensure_ws(ctx, probe.off)) != OQR_OK) return v;
+    Carve c(ctx->ws);
+    layout(c, &W, &sk, &G, &R1, &R2, &partials, &work);
+    if ((v = reset_status(ctx, s)) != OQR_OK) return v;
+    // pass 1: W = A Z, G_1 = Z^T W, R_1 = chol(G_1), Q_1 = Z / R_1, then W <- W / R_1 (= A Q_1 up to rounding)
+    OQR_TRY(launch_gemm_f64(GEMM_SYML, m, n, m, 1.0, A, lda, Z, ldz, 0.0, W, m, nullptr, 1, s));
+    OQR_TRY(launch_gemm_f64(GEMM_T, n, n, m, 1.0, Z, ldz, W, m, 0.0, G, n, sk, splits, s));
+    OQR_TRY(launch_potrf(n, G, n, R1, n, nullptr, ctx->st, s));
+    OQR_TRY(launch_trsm(m, n, Z, ldz, R1, n, Q, ldq, ctx->st, s));
+    OQR_TRY(launch_trsm(m, n, W, m, R1, n, W, m, ctx->st, s));
+    // pass 2: G_2 = Q_1^T (W R_1^{-1}), R_2 = chol(G_2), Q = Q_1 / R_2, R = R_2 R_1
+    OQR_TRY(launch_gemm_f64(GEMM_T, n, n, m, 1.0, Q, ldq, W, m, 0.0, G, n, sk, splits, s));
+    OQR_TRY(launch_potrf(n, G, n, R2, n, nullptr, ctx->st, s));
+    OQR_TRY(launch_trsm(m, n, Q, ldq, R2, n, Q, ldq, ctx->st, s));
+    OQR_TRY(launch_rprod(n, R2, n, R1, n, R, ldr, s));
+    if (o.check && (v = run_check(ctx, gp, A, lda, Q, ldq, partials, G, work, nullptr, 0, limit, s)) != OQR_OK)
+        return v;
+    return finish(ctx, s, info, 2, o.check != 0);
+}
+
 oqr_status cgs2_impl(oqr_ctx* ctx, int m, int n, const double* A, long lda, const double* Z, long ldz, double* Q,
                      long ldq, double* R, long ldr, const oqr_opts* opts_in, oqr_info* info, void* stream)
 {
@@ -699,6 +748,9 @@ oqr_status oqr_cholqr(oqr_ctx* ctx, int m, int n, const double* A, long lda, con
 oqr_status oqr_cholqr2(oqr_ctx* ctx, int m, int n, const double* A, long lda, const double* Z, long ldz,
                        double* Q, long ldq, double* R, long ldr, const oqr_opts* opts, oqr_info* info, void* stream)
 {
+    if (opts && opts->reuse_w)
+        return cholqr2_reuse_w(ctx, m, n, A, lda, Z, ldz, Q, ldq, R, ldr, resolve(opts), info,
+                               static_cast<cudaStream_t>(stream));
     return normal_equation(ctx, m, n, dense_op(A, lda), Z, ldz, Q, ldq, R, ldr, opts, info, stream, 0);
 }
 

@@ -28,7 +28,8 @@ OQR_ALGO_CHOLQR, OQR_ALGO_CHOLQR2, OQR_ALGO_SCHOLQR3, OQR_ALGO_CGS2 = 0, 1, 2, 3
 class oqr_opts(ctypes.Structure):
     _fields_ = [("passes", ctypes.c_int), ("shifted", ctypes.c_int), ("prec", ctypes.c_int),
                 ("shift_c", ctypes.c_double), ("block", ctypes.c_int), ("check", ctypes.c_int),
-                ("spin_limit", ctypes.c_long), ("final_prec", ctypes.c_int), ("prec_mid", ctypes.c_int)]
+                ("spin_limit", ctypes.c_long), ("final_prec", ctypes.c_int), ("prec_mid", ctypes.c_int),
+                ("reuse_w", ctypes.c_int)]
 
 
 class oqr_info(ctypes.Structure):

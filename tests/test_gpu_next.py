@@ -112,6 +112,36 @@ def test_glls_full_size_normal_equations(env):
     torch.cuda.empty_cache()
 
 
+# ------------------------------------------------------- A-CholQR2 reusing W --
+def test_cholqr2_reuse_w_against_its_restatement(env):
+    """A-CholQR2 with W = A Z kept (A Q_1 = W R_1^{-1}) on config 0 and on a ragged shape, against the same
+    steps restated on the CPU: R and the orthogonality within 100 x the restatement's own error (the
+    variant is not exact: its loss of orthogonality keeps one factor of kappa), and never worse than
+    one-pass CHOLQR."""
+    torch, oqr, ctx = env
+    for A, Z in (inputs.config0(seed=0), inputs.paper_case(4, 777, 33, 1e4, 1e3, seed=6)):
+        Qr, Rr = oracle.oblique_qr(A, Z)
+        Qc, Rc = oracle.cholqr2_reuse_w(A, Z)
+        Q, R, (st, info) = ctx.oqr_cholqr2(dev(torch, A, oqr), dev(torch, Z, oqr), reuse_w=1, check=1)
+        Q, R = host(Q), host(R)
+        assert st == 0 and np.all(np.tril(R, -1) == 0) and np.all(np.diag(R) > 0)
+        relR, relRc = (np.linalg.norm(X - Rr) / np.linalg.norm(Rr) for X in (R, Rc))
+        orth, orthc = oracle.orth_error(A, Q), oracle.orth_error(A, Qc)
+        assert relR <= max(1e-12, 100 * relRc)
+        assert orth <= max(1e-13, 100 * orthc)
+        assert orth <= oracle.orth_error(A, oracle.cholqr(A, Z)[0])
+        assert oracle.repres_error(Z, Q, R) <= 1e-13
+
+
+def test_cholqr2_reuse_w_rejects_other_options(env):
+    torch, oqr, ctx = env
+    A, Z = inputs.paper_case(4, 200, 8, 1e2, 1e1, seed=2)
+    for kw in ({"shifted": 1}, {"prec": 3, "final_prec": 3}, {"passes": 3}):
+        _, _, (st, _) = ctx.oqr_cholqr2(dev(torch, A, oqr), dev(torch, Z, oqr), reuse_w=1, raise_on_error=False,
+                                        **kw)
+        assert st == oqr.OQR_ERR_UNSUPPORTED
+
+
 # ------------------------------------------------------------- tridiagonal A --
 def _tri(torch, d, e):
     return (torch.as_tensor(np.ascontiguousarray(d), dtype=torch.float64).cuda(),

@@ -352,3 +352,23 @@ def test_tridiag_oracle_pins():
     with pytest.raises(oracle.OracleBreakdown) as err:
         oracle.oblique_qr_tridiag(np.array([1.0, 1.0, 1.0]), np.array([0.0, 2.0]), Z[:3, :2])
     assert err.value.column == 3
+
+
+def test_reuse_w_restatement_pins():
+    """The CPU restatement of A-CholQR2 with W reused (not in the paper): on a well-conditioned instance it
+    reaches the oracle's unique (Q, R); on case 5 (Z^T A Z = I exactly) it returns R = I, Q = Z; and its
+    orthogonality lies between CholQR2's and one-pass CholQR's on an ill-conditioned instance (the second
+    pass corrects the Gram's kappa^2 loss but keeps A Z's rounding)."""
+    A, Z = inputs.paper_case(4, 400, 10, 1e2, 1e1, seed=3)
+    Qr, Rr = oracle.oblique_qr(A, Z)
+    Q, R = oracle.cholqr2_reuse_w(A, Z)
+    assert np.linalg.norm(R - Rr) / np.linalg.norm(Rr) <= 1e-13
+    A5, Z5 = inputs.paper_case(5, 80, 10, 1e6, None, seed=45)
+    Q5, R5 = oracle.cholqr2_reuse_w(A5, Z5)
+    assert np.abs(R5 - np.eye(10)).max() <= 1e-9
+    A, Z = inputs.config0(seed=0)
+    Q, R = oracle.cholqr2_reuse_w(A, Z)
+    Q1, _ = oracle.cholqr(A, Z)
+    Q2, _ = oracle.cpu_cholqr2(A, Z)
+    o_reuse, o_one, o_two = oracle.orth_error(A, Q), oracle.orth_error(A, Q1), oracle.orth_error(A, Q2)
+    assert o_two <= 10 * o_reuse and o_reuse <= o_one, (o_two, o_reuse, o_one)
