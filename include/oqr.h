@@ -254,6 +254,29 @@ oqr_status oqr_repres(oqr_ctx* ctx, int m, int n, const double* Z, long ldz, con
                       const double* R, long ldr, double* res2, double* resF, void* stream);
 
 /*
+ * PRE-CHOLQR (Algorithm 2, Sec. 3): [Y, S] = qr(Z) (Euclidean), then
+ * [Q, U] = CHOLQR(A, Y), R = U S.  The Euclidean QR is Householder QR on a
+ * reduction tree (oqr_tsqr, FP64), so Y is orthonormal to working precision
+ * and the loss of orthogonality of Q no longer depends on kappa(Z)
+ * (Thm 3.1: ||Q^T A Q - I||_2 <= c m n^2 u ||Q||_2^2 ||A||_2).  The CHOLQR
+ * pass runs in opts->final_prec (OQR_FP64 or OQR_FP64_TC; opts->check as for
+ * oqr_cholqr2); R has a positive diagonal.  Q may alias Z.  Workspace: the
+ * tree's blocks (about 2 m n + 4 n^2 log2(m / 256) doubles) and the pass's.
+ * oqr_precholqr_tridiag: the same for a tridiagonal A (d, e as for
+ *   oqr_cholqr2_tridiag).
+ * oqr_tsqr: the Euclidean step alone, Z = Y S with Y (m x n, device) having
+ *   orthonormal columns and S (n x n, device) upper triangular with a
+ *   positive diagonal (zeros below).  Y must not overlap Z.
+ */
+oqr_status oqr_precholqr(oqr_ctx* ctx, int m, int n, const double* A, long lda, const double* Z, long ldz, double* Q,
+                         long ldq, double* R, long ldr, const oqr_opts* opts, oqr_info* info, void* stream);
+oqr_status oqr_precholqr_tridiag(oqr_ctx* ctx, int m, int n, const double* d, const double* e, const double* Z,
+                                 long ldz, double* Q, long ldq, double* R, long ldr, const oqr_opts* opts,
+                                 oqr_info* info, void* stream);
+oqr_status oqr_tsqr(oqr_ctx* ctx, int m, int n, const double* Z, long ldz, double* Y, long ldy, double* S, long lds,
+                    void* stream);
+
+/*
  * Tridiagonal A (Sec. 8's second workload): A = T with diagonal d (m
  * doubles) and off-diagonal e (m - 1 doubles; may be NULL when m = 1),
  * T(i, i) = d[i], T(i + 1, i) = T(i, i + 1) = e[i]; d and e are device

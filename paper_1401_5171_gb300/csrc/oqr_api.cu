@@ -371,9 +371,11 @@ size_t ne_carve(void* base, const GramPlan& gp, const NePlan& P, NeBuffers* B)
 // a_split_ready: the workspace's tensor-core region already holds the split of
 // this A made for the first pass's plan (the host-buffer path makes it while A
 // arrives), so the first EMU64-family pass does not make it again.
+// ws_reserve: bytes at the start of the workspace that the caller keeps (the
+// call carves its buffers after them; the caller has grown the workspace).
 oqr_status normal_equation(oqr_ctx* ctx, int m, int n, const AOp& op, const double* Z, long ldz, double* Q, long ldq,
                            double* R, long ldr, const oqr_opts* opts_in, oqr_info* info, void* stream,
-                           int forced_passes, bool a_split_ready = false)
+                           int forced_passes, bool a_split_ready = false, size_t ws_reserve = 0)
 {
     oqr_status v;
     if (op.tri()) {
@@ -400,8 +402,8 @@ oqr_status normal_equation(oqr_ctx* ctx, int m, int n, const AOp& op, const doub
     const int prec_first = P.prec_first;
     auto prec_of = [&](int p) { return P.prec_of(p); };
     NeBuffers B;
-    if ((v = ensure_ws(ctx, ne_carve(nullptr, gp, P, &B))) != OQR_OK) return v;
-    ne_carve(ctx->ws, gp, P, &B);
+    if ((v = ensure_ws(ctx, ws_reserve + ne_carve(nullptr, gp, P, &B))) != OQR_OK) return v;
+    ne_carve(static_cast<char*>(ctx->ws) + ws_reserve, gp, P, &B);
     double *partials = B.partials, *G = B.G, *work = B.work, *R1 = B.R1, *R2 = B.R2, *R3 = B.R3,
            *scratch = B.scratch;
     void* tcws = B.tcws;
@@ -515,6 +517,44 @@ oqr_status cholqr2_reuse_w(oqr_ctx* ctx, int m, int n, const double* A, long lda
     if (o.check && (v = run_check(ctx, gp, A, lda, Q, ldq, partials, G, work, nullptr, 0, limit, s)) != OQR_OK)
         return v;
     return finish(ctx, s, info, 2, o.check != 0);
+}
+
+// PRE-CHOLQR (Algorithm 2, Sec. 3): [Y, S] = qr(Z) by Householder TSQR,
+// [Q, U] = CHOLQR(A, Y) (one pass in opts->final_prec), R = U S.
+oqr_status precholqr_impl(oqr_ctx* ctx, int m, int n, const AOp& op, const double* Z, long ldz, double* Q, long ldq,
+                          double* R, long ldr, const oqr_opts* opts, oqr_info* info, cudaStream_t s)
+{
+    if (!ctx || m < 1 || n < 1 || n > m || bad_matrix(Z, ldz, m, n) || bad_matrix(Q, ldq, m, n) ||
+        bad_matrix(R, ldr, n, n) || (!op.tri() && bad_matrix(op.A, op.lda, m, m)) || (op.tri() && m > 1 && !op.e))
+        return OQR_ERR_INVALID_ARG;
+    if (n > 1024) return OQR_ERR_UNSUPPORTED;
+    if (Q != Z) {
+        const char *q0 = reinterpret_cast<const char*>(Q), *q1 = reinterpret_cast<const char*>(Q + (size_t)ldq * (n - 1) + m);
+        const char *z0 = reinterpret_cast<const char*>(Z), *z1 = reinterpret_cast<const char*>(Z + (size_t)ldz * (n - 1) + m);
+        if (q0 < z1 && z0 < q1) return OQR_ERR_INVALID_ARG;
+    }
+    const oqr_opts o = resolve(opts);
+    NePlan P;
+    oqr_status v = ne_plan(o, 1, m, n, &P, op.tri());
+    if (v != OQR_OK) return v;
+    const GramPlan gp = gram_plan(m, n, ctx->sm_count);
+    NeBuffers B;
+    const size_t reserve = align256((size_t)2 * n * n * sizeof(double));  // S, U
+    const TsqrPlan tp = tsqr_plan(m, n);
+    const size_t need = reserve + std::max(align256(tp.doubles * sizeof(double)), ne_carve(nullptr, gp, P, &B));
+    if ((v = ensure_ws(ctx, need)) != OQR_OK) return v;
+    double* S = static_cast<double*>(ctx->ws);
+    double* Uf = S + (size_t)n * n;
+    double* tws = reinterpret_cast<double*>(static_cast<char*>(ctx->ws) + reserve);
+    {
+        const NvtxRange range("oqr: Householder TSQR %d", n);
+        OQR_TRY(launch_tsqr(tp, Z, ldz, Q, ldq, S, n, tws, s));  // Y into Q
+    }
+    // CHOLQR on Y in place (Q aliases Y), its factor into U; no synchronization yet
+    if ((v = normal_equation(ctx, m, n, op, Q, ldq, Q, ldq, Uf, n, &o, nullptr, s, 1, false, reserve)) != OQR_OK)
+        return v;
+    OQR_TRY(launch_rprod(n, Uf, n, S, n, R, ldr, s));
+    return finish(ctx, s, info, 1, o.check != 0);
 }
 
 oqr_status cgs2_impl(oqr_ctx* ctx, int m, int n, const double* A, long lda, const double* Z, long ldz, double* Q,
@@ -1401,6 +1441,38 @@ oqr_status oqr_gram_tridiag(oqr_ctx* ctx, int m, int n, const double* d, const d
     OQR_TRY(form_gram(ctx, prec, gp, op, Z, ldz, part, Gt, nullptr, tcws, 4000000000ull, s, nullptr, Ub, Cb));
     OQR_TRY(cudaMemcpy2DAsync(G, ldg * sizeof(double), Gt, n * sizeof(double), n * sizeof(double), n,
                               cudaMemcpyDeviceToDevice, s));
+    return OQR_OK;
+}
+
+oqr_status oqr_precholqr(oqr_ctx* ctx, int m, int n, const double* A, long lda, const double* Z, long ldz, double* Q,
+                         long ldq, double* R, long ldr, const oqr_opts* opts, oqr_info* info, void* stream)
+{
+    return precholqr_impl(ctx, m, n, dense_op(A, lda), Z, ldz, Q, ldq, R, ldr, opts, info,
+                          static_cast<cudaStream_t>(stream));
+}
+
+oqr_status oqr_precholqr_tridiag(oqr_ctx* ctx, int m, int n, const double* d, const double* e, const double* Z,
+                                 long ldz, double* Q, long ldq, double* R, long ldr, const oqr_opts* opts,
+                                 oqr_info* info, void* stream)
+{
+    if (!d) return OQR_ERR_INVALID_ARG;
+    AOp op;
+    op.d = d;
+    op.e = e;
+    return precholqr_impl(ctx, m, n, op, Z, ldz, Q, ldq, R, ldr, opts, info, static_cast<cudaStream_t>(stream));
+}
+
+oqr_status oqr_tsqr(oqr_ctx* ctx, int m, int n, const double* Z, long ldz, double* Y, long ldy, double* S, long lds,
+                    void* stream)
+{
+    if (!ctx || m < 1 || n < 1 || n > m || bad_matrix(Z, ldz, m, n) || bad_matrix(Y, ldy, m, n) ||
+        bad_matrix(S, lds, n, n))
+        return OQR_ERR_INVALID_ARG;
+    if (n > 1024) return OQR_ERR_UNSUPPORTED;
+    const TsqrPlan tp = tsqr_plan(m, n);
+    oqr_status v = ensure_ws(ctx, align256(tp.doubles * sizeof(double)));
+    if (v != OQR_OK) return v;
+    OQR_TRY(launch_tsqr(tp, Z, ldz, Y, ldy, S, lds, static_cast<double*>(ctx->ws), static_cast<cudaStream_t>(stream)));
     return OQR_OK;
 }
 

@@ -228,6 +228,20 @@ cudaError_t launch_tc_cross(const TcPlan& p, const double* X, long ldx, const do
                             const double* shift_ptr, void* ws, DevStatus* st, uint64_t limit_ns, int sms,
                             cudaStream_t s);
 
+// Euclidean Householder QR of a tall-skinny Z on a reduction tree (k_tsqr.cu):
+// Z = Y S with Y (m x n) orthonormal and S upper triangular with a positive
+// diagonal; the workspace holds tsqr_plan(m, n).doubles doubles.
+struct TsqrPlan {
+    int m, n;
+    int b0;               // rows per leaf (the last leaf takes the rest: b0 <= rows < 2 b0)
+    int leaves, levels;
+    int level_count[32];  // nodes per tree level (each node stacks 2 children's R, or 3 for the last of an odd count)
+    size_t doubles;       // workspace
+};
+TsqrPlan tsqr_plan(int m, int n);
+cudaError_t launch_tsqr(const TsqrPlan& p, const double* Z, long ldz, double* Y, long ldy, double* S, long lds,
+                        double* ws, cudaStream_t s);
+
 // Tridiagonal A (k_tridiag.cu): d (m), e (m - 1); U = M X with M = tril(T, -1) + diag(T) / 2.
 cudaError_t launch_tridiag_u(int m, int n, const double* d, const double* e, const double* X, long ldx, double* U,
                              long ldu, cudaStream_t s);

@@ -112,6 +112,9 @@ def load(path: str | None = None):
     lib.oqr_set_batch_budget.argtypes = [vp, ctypes.c_size_t]
     lib.oqr_glls.argtypes = [vp, i, i, i, vp, l, vp, l, vp, l, vp, l, vp, l, vp]
     lib.oqr_cholqr2_tridiag.argtypes = [vp, i, i, vp, vp, vp, l, vp, l, vp, l, po, pi, vp]
+    lib.oqr_precholqr.argtypes = qr
+    lib.oqr_precholqr_tridiag.argtypes = [vp, i, i, vp, vp, vp, l, vp, l, vp, l, po, pi, vp]
+    lib.oqr_tsqr.argtypes = [vp, i, i, vp, l, vp, l, vp, l, vp]
     lib.oqr_gram_tridiag.argtypes = [vp, i, i, vp, vp, vp, l, vp, l, i, vp]
     lib.oqr_symm.argtypes = [vp, i, i, vp, l, vp, l, vp, l, vp]
     for name in declared_functions():
@@ -138,7 +141,8 @@ def _raw(name):
 for _n in ("oqr_default_opts", "oqr_create", "oqr_destroy", "oqr_workspace_size", "oqr_set_workspace",
            "oqr_get_status", "oqr_cholqr", "oqr_cholqr2", "oqr_cholqr2_host", "oqr_cgs2", "oqr_gram", "oqr_gram_noalloc", "oqr_gram_phases", "oqr_potrf", "oqr_trsm", "oqr_trsm_tc",
            "oqr_rprod", "oqr_check", "oqr_repres", "oqr_diag_timeout", "oqr_set_batch_budget", "oqr_batched", "oqr_batched_mixed", "oqr_batched_default_splits", "oqr_features",
-           "oqr_mlp_param_count", "oqr_mlp_forward", "oqr_mlp_grad", "oqr_mlp_adam", "oqr_glls", "oqr_symm", "oqr_cholqr2_tridiag", "oqr_gram_tridiag"):
+           "oqr_mlp_param_count", "oqr_mlp_forward", "oqr_mlp_grad", "oqr_mlp_adam", "oqr_glls", "oqr_symm", "oqr_cholqr2_tridiag", "oqr_gram_tridiag",
+           "oqr_precholqr", "oqr_precholqr_tridiag", "oqr_tsqr"):
     globals()[_n] = _raw(_n)
 
 
@@ -459,8 +463,27 @@ class Oqr:
         if st != OQR_OK:
             raise OqrError(st, "oqr_set_workspace")
 
+    def oqr_precholqr(self, A, Z, **kw):
+        return self._qr("oqr_precholqr", A, Z, **kw)
+
+    def oqr_precholqr_tridiag(self, d, e, Z, **kw):
+        return self.oqr_cholqr2_tridiag(d, e, Z, _name="oqr_precholqr_tridiag", **kw)
+
+    def oqr_tsqr(self, Z, Y=None, S=None, stream=None):
+        """Euclidean Householder QR Z = Y S (S upper triangular with a positive diagonal)."""
+        m, n = Z.shape
+        Y = Y if Y is not None else empty_colmajor(m, n, Z.device)
+        S = S if S is not None else empty_colmajor(n, n, Z.device)
+        z, ldz = _m(Z)
+        y, ldy = _m(Y)
+        s_, lds = _m(S)
+        st = self.lib.oqr_tsqr(self.ctx, m, n, z, ldz, y, ldy, s_, lds, self._stream(stream))
+        if st != OQR_OK:
+            raise OqrError(st, "oqr_tsqr")
+        return Y, S
+
     def oqr_cholqr2_tridiag(self, d, e, Z, Q=None, R=None, opts=None, stream=None, sync=True, raise_on_error=True,
-                            **kw):
+                            _name="oqr_cholqr2_tridiag", **kw):
         """The normal-equation method for tridiagonal A (diagonal d, off-diagonal e: 1-D float64 CUDA tensors);
         returns (Q, R, (status, info))."""
         m, n = Z.shape
@@ -471,10 +494,10 @@ class Oqr:
         z, ldz = _m(Z)
         q, ldq = _m(Q)
         r, ldr = _m(R)
-        st = self.lib.oqr_cholqr2_tridiag(self.ctx, m, n, _vec(d, m), _vec(e, m - 1), z, ldz, q, ldq, r, ldr,
-                                          ctypes.byref(o), ctypes.byref(info) if sync else None, self._stream(stream))
+        st = getattr(self.lib, _name)(self.ctx, m, n, _vec(d, m), _vec(e, m - 1), z, ldz, q, ldq, r, ldr,
+                                      ctypes.byref(o), ctypes.byref(info) if sync else None, self._stream(stream))
         if st != OQR_OK and raise_on_error:
-            raise OqrError(st, "oqr_cholqr2_tridiag", info.info)
+            raise OqrError(st, _name, info.info)
         return Q, R, (st, info)
 
     def oqr_gram_tridiag(self, d, e, Z, G=None, prec=OQR_FP64, stream=None):

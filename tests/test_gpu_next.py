@@ -222,3 +222,92 @@ def test_cholqr2_tridiag_paper_size(env, n):
         rep = (torch.linalg.matrix_norm(Zt - Q @ R, 2) / torch.linalg.matrix_norm(Zt, 2)).item()
         assert relR <= max(1e-12, 100 * U * kappa), (kw, relR)
         assert orth <= 1e-12 and rep <= 1e-13, (kw, orth, rep)
+
+
+# ------------------------------------------------------------- PRE-CHOLQR --
+@pytest.mark.parametrize("m,n", [(1, 1), (5, 3), (256, 256), (300, 20), (2000, 20), (4097, 64), (3000, 300),
+                                 (70001, 8), (9000, 1)])
+def test_tsqr_matches_lapack(env, m, n):
+    """The Euclidean Householder TSQR (one leaf; odd and even node counts; a deep tree; n = 1) against
+    LAPACK's QR with its signs normalised: S within 1e-13 of R_lapack, Y orthonormal to working precision
+    and within kappa(Z) u of Q_lapack."""
+    torch, oqr, ctx = env
+    rng = np.random.default_rng(m + 7 * n)
+    Z = rng.standard_normal((m, n)) @ np.diag(np.logspace(0, 3, n))
+    Y, S = ctx.oqr_tsqr(dev(torch, Z, oqr))
+    Y, S = host(Y), host(S)
+    Ql, Rl = np.linalg.qr(Z)
+    D = np.where(np.diag(Rl) < 0, -1.0, 1.0)
+    Ql, Rl = Ql * D, (Rl.T * D).T
+    assert np.all(np.tril(S, -1) == 0) and np.all(np.diag(S) > 0)
+    assert np.linalg.norm(S - Rl) / np.linalg.norm(Rl) <= 1e-13
+    assert np.abs(Y.T @ Y - np.eye(n)).max() <= 20 * np.sqrt(m) * n * U
+    assert np.abs(Y - Ql).max() <= 100 * np.linalg.cond(Z) * U
+    assert np.linalg.norm(Z - Y @ S) / np.linalg.norm(Z) <= 10 * n * U
+
+
+def _pre_orth_bound(A, Q, m, n):
+    """Thm 3.1's bound c m n^2 u ||Q||_2^2 ||A||_2 with c = 1."""
+    return m * n * n * U * np.linalg.norm(Q, 2) ** 2 * np.linalg.eigvalsh(A).max()
+
+
+@pytest.mark.parametrize("final_prec", [0, 3])
+def test_precholqr_config0_parity(env, final_prec):
+    """PRE-CHOLQR (Algorithm 2) on config 0, FP64 and FP64-accurate CHOLQR pass: the oracle's (Q, R)."""
+    torch, oqr, ctx = env
+    A, Z = inputs.config0(seed=0)
+    m, n = Z.shape
+    Qr, Rr = oracle.oblique_qr(A, Z)
+    Q, R, (st, _) = ctx.oqr_precholqr(dev(torch, A, oqr), dev(torch, Z, oqr), final_prec=final_prec)
+    Q, R = host(Q), host(R)
+    assert st == 0 and np.all(np.tril(R, -1) == 0) and np.all(np.diag(R) > 0)
+    kappa = np.linalg.cond(Rr)
+    assert np.linalg.norm(R - Rr) / np.linalg.norm(Rr) <= max(1e-12, 100 * U * kappa)
+    orth = oracle.orth_error(A, Q)
+    assert orth <= min(_pre_orth_bound(A, Q, m, n), max(1e-11, 100 * oracle.orth_error(A, Qr)))
+    assert oracle.repres_error(Z, Q, R) <= 1e-13
+
+
+def test_precholqr_orthogonality_independent_of_kappa_z(env):
+    """Thm 3.1: PRE-CHOLQR's loss of orthogonality does not grow with kappa(Z).  The same A (m = 2000,
+    kappa(A) = 1e4), kappa(Z) = 1e2 and 1e8: the orthogonality stays within 10x, inside the theorem's
+    bound, while one-pass CHOLQR at kappa(Z) = 1e8 breaks down; R is the oracle's within 100 u kappa(R)."""
+    torch, oqr, ctx = env
+    m, n = 2000, 20
+    orths = []
+    for kz in (1e2, 1e8):
+        A, Z = inputs.paper_case(4, m, n, 1e4, kz, seed=8)
+        Qr, Rr = oracle.oblique_qr(A, Z)
+        Ad = dev(torch, A, oqr)
+        Q, R, (st, _) = ctx.oqr_precholqr(Ad, dev(torch, Z, oqr))
+        Q, R = host(Q), host(R)
+        assert st == 0
+        assert np.linalg.norm(R - Rr) / np.linalg.norm(Rr) <= max(1e-12, 100 * U * np.linalg.cond(Rr))
+        orths.append(oracle.orth_error(A, Q))
+        assert orths[-1] <= _pre_orth_bound(A, Q, m, n)
+        assert oracle.repres_error(Z, Q, R) <= 1e-13
+        if kz == 1e8:
+            _, _, (st1, _) = ctx.oqr_cholqr(Ad, dev(torch, Z, oqr), raise_on_error=False)
+            assert st1 == oqr.OQR_ERR_NOT_SPD
+    assert orths[1] <= 10 * orths[0] + 1e-15, orths
+
+
+def test_precholqr_in_place_and_tridiagonal(env):
+    """Q aliasing Z, and PRE-CHOLQR on a tridiagonal A against the tridiagonal oracle (kappa(Z) = 1e8)."""
+    torch, oqr, ctx = env
+    A, Z = inputs.paper_case(4, 900, 30, 1e3, 1e2, seed=5)
+    Qr, Rr = oracle.oblique_qr(A, Z)
+    Zd = dev(torch, Z, oqr)
+    Q, R, _ = ctx.oqr_precholqr(dev(torch, A, oqr), Zd, Q=Zd)
+    assert Q.data_ptr() == Zd.data_ptr()
+    assert np.linalg.norm(host(R) - Rr) / np.linalg.norm(Rr) <= 1e-12
+    m, n = 5000, 40
+    d, e = inputs.tridiag_spd(m, 1e4)
+    _, Z = inputs.paper_case(4, m, n, 1e2, 1e8, seed=15)
+    Qr, Rr = oracle.oblique_qr_tridiag(d, e, Z)
+    dd, ed = _tri(torch, d, e)
+    Q, R, (st, _) = ctx.oqr_precholqr_tridiag(dd, ed, dev(torch, Z, oqr))
+    Q, R = host(Q), host(R)
+    assert st == 0
+    assert np.linalg.norm(R - Rr) / np.linalg.norm(Rr) <= max(1e-12, 100 * U * np.linalg.cond(Rr))
+    assert oracle.orth_error_tridiag(d, e, Q) <= max(1e-12, 100 * oracle.orth_error_tridiag(d, e, Qr))
