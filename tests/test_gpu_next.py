@@ -271,7 +271,8 @@ def test_precholqr_config0_parity(env, final_prec):
 def test_precholqr_orthogonality_independent_of_kappa_z(env):
     """Thm 3.1: PRE-CHOLQR's loss of orthogonality does not grow with kappa(Z).  The same A (m = 2000,
     kappa(A) = 1e4), kappa(Z) = 1e2 and 1e8: the orthogonality stays within 10x, inside the theorem's
-    bound, while one-pass CHOLQR at kappa(Z) = 1e8 breaks down; R is the oracle's within 100 u kappa(R)."""
+    bound, while one-pass CHOLQR at kappa(Z) = 1e8 breaks down or loses at least 1000x more; R is the
+    oracle's within 100 u kappa(R)."""
     torch, oqr, ctx = env
     m, n = 2000, 20
     orths = []
@@ -286,9 +287,9 @@ def test_precholqr_orthogonality_independent_of_kappa_z(env):
         orths.append(oracle.orth_error(A, Q))
         assert orths[-1] <= _pre_orth_bound(A, Q, m, n)
         assert oracle.repres_error(Z, Q, R) <= 1e-13
-        if kz == 1e8:
-            _, _, (st1, _) = ctx.oqr_cholqr(Ad, dev(torch, Z, oqr), raise_on_error=False)
-            assert st1 == oqr.OQR_ERR_NOT_SPD
+        if kz == 1e8:   # one-pass CHOLQR breaks down or loses orthogonality (Thm 2.1: u kappa^2)
+            Q1, _, (st1, _) = ctx.oqr_cholqr(Ad, dev(torch, Z, oqr), raise_on_error=False)
+            assert st1 == oqr.OQR_ERR_NOT_SPD or oracle.orth_error(A, host(Q1)) >= 1e3 * orths[-1]
     assert orths[1] <= 10 * orths[0] + 1e-15, orths
 
 
