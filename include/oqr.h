@@ -80,6 +80,22 @@ typedef struct {
     int prec_mid;     /* passes between the first and the last: oqr_precision, or -1 = same as prec [-1] */
     int reuse_w;      /* oqr_cholqr2 (FP64, two passes, dense A): 1 = form W = A Z once and take the second
                          pass's A Q_1 as W R_1^{-1} instead of a second product with A [0] */
+    /* oqr_batched only: */
+    const int* batch_splits;      /* OQR_BATCHED_FP64: the work plan, the number of k-ranges each instance's Gram
+                                     is cut into (host, count ints in 1..64, as an autotuner chose them); NULL =
+                                     the built-in heuristic [NULL] */
+    const float* selector_params; /* OQR_BATCHED_SELECTOR: the trained network (device, oqr_mlp_param_count()
+                                     FP32 values, the layout of oqr_mlp_forward) [NULL] */
+    double selector_tol;          /* OQR_BATCHED_SELECTOR: the largest ||Q^T A Q - I||_2 a checked result may
+                                     keep [1e-12] */
+    int selector_check;           /* OQR_BATCHED_SELECTOR: 0 = check the one-pass choices only, 1 = check every
+                                     tensor-core result [0] */
+    double* batch_orth;           /* optional device output (count doubles): ||Q_b^T A_b Q_b - I||_2 estimates
+                                     (power iteration on one more FP64-accurate Gram of Q_b; NaN where the mode
+                                     did not check the instance, +inf after a breakdown) [NULL] */
+    int* batch_choice;            /* OQR_BATCHED_SELECTOR: optional device output (count ints), the option whose
+                                     result each instance holds: 0 one pass, 1 two passes, 2 shifted three passes
+                                     (all FP64-accurate on the tensor cores), 3 FP64 A-CholQR2 [NULL] */
 } oqr_opts;
 
 /* Optional per-call report (filled only when passed non-NULL). */
@@ -321,28 +337,67 @@ oqr_status oqr_symm(oqr_ctx* ctx, int m, int k, const double* A, long lda, const
                     long ldc, void* stream);
 
 /*
- * Batched A-CholQR2 (FP64): `count` independent oblique QRs, instance b with
- * A_b (m[b] x m[b], lower triangle read), Z_b (m[b] x n[b]) -> Q_b, R_b, all
+ * Batched oblique QR: `count` independent instances, instance b with A_b
+ * (m[b] x m[b], lower triangle read), Z_b (m[b] x n[b]) -> Q_b, R_b, all
  * column-major FP64 device memory, 1 <= n[b] <= min(m[b], 64), m[b] <= 4096.
- * Each instance is Algorithm 1 applied twice (CHOLQR, Sec. 2; R = R_2 R_1).
  * m, n, the pointer arrays and the leading-dimension arrays are HOST arrays
  * (the pointers in them are device pointers).  status is a DEVICE array of
  * count ints: 0 for success, else the 1-based column at which instance b's
  * Cholesky broke down (its Q_b, R_b are then undefined; the other instances
- * are unaffected).  splits (host, may be NULL) is the work plan: the number of
- * k-ranges each instance's Gram is cut into (1..64), as chosen by an autotuner;
- * NULL uses the built-in heuristic.  mode: 0 FP64 A-CholQR2 (FP64 FMA Gram);
- * 1, 2, 3 the tensor-core form (oqr_batched_mixed) with every instance's
- * program OQR_BATCH_CHOLQR2_TC (1), OQR_BATCH_CHOLQR2_TC2 (2) or
- * OQR_BATCH_SCHOLQR3_TC (3); splits is then ignored.
- * The batch-wide kernel sequence (about 13 launches) is captured into one
- * CUDA graph that the context caches and replays while the batch's shape
- * signature is unchanged; on the legacy default stream it is launched directly.
- * Asynchronous: returns after enqueueing (argument errors are returned).
+ * are unaffected), or -1 for every instance when a tensor-core wait timed out.
+ * mode (oqr_batched_mode):
+ *   OQR_BATCHED_FP64: A-CholQR2, Algorithm 1 twice (CHOLQR, Sec. 2;
+ *     R = R_2 R_1), every Gram in FP64 FMA; opts->batch_splits is the work
+ *     plan.  The batch-wide kernel sequence (about 13 launches) is captured into
+ *     one CUDA graph that the context caches and replays while the batch's
+ *     shape signature is unchanged; on the legacy default stream it runs directly.
+ *   OQR_BATCHED_TC, OQR_BATCHED_TC2_FIRST, OQR_BATCHED_SHIFTED_TC: the
+ *     tensor-core form (oqr_batched_mixed) with every instance's program
+ *     OQR_BATCH_CHOLQR2_TC, OQR_BATCH_CHOLQR2_TC2 or OQR_BATCH_SCHOLQR3_TC;
+ *     opts->batch_orth, when given, receives each instance's check.
+ *   OQR_BATCHED_SELECTOR: the learned selector (no counterpart in the paper).
+ *     Every instance first runs one FP64-accurate pass on the tensor cores
+ *     (its Gram G_0 = Z^T A Z and Cholesky factor R_1); 16 features of G_0 and
+ *     R_1 (Gram diagonal spread, coherence and pivots of the diagonally scaled
+ *     G_0, breakdown, a sketched estimate of kappa(R_1) from an n x 2n Gaussian
+ *     sketch, sizes) go through the MLP 16 -> 64 -> 64 -> 4 (opts->
+ *     selector_params, BF16 inference), whose argmax says how the instance
+ *     finishes: 0 with Q = Z R_1^{-1} (one pass), 1 with one more pass
+ *     (A-CholQR2), 2 with a shifted first pass refactored from the same G_0
+ *     and two more passes (shifted A-CholQR3), 3 with FP64 A-CholQR2.  The
+ *     passes of options 0-2 run in the same packed waves as the first, reading
+ *     the wave's one split of A.  One-pass results (all results when
+ *     opts->selector_check = 1) are checked: ||Q^T A Q - I||_2 above
+ *     opts->selector_tol, or a breakdown, sends the instance down the fallback
+ *     chain: shifted A-CholQR3 on the tensor cores (checked), then FP64
+ *     A-CholQR2 (accepted once it completes).  opts->batch_orth and
+ *     opts->batch_choice, when given, receive the checks and the option each
+ *     result comes from.  This mode synchronizes the stream (the choices are
+ *     read between the passes) and is not captured into a graph.
+ * Argument errors are returned; otherwise every mode but the selector returns
+ * after enqueueing.
  */
+typedef enum {
+    OQR_BATCHED_FP64 = 0,
+    OQR_BATCHED_TC = 1,
+    OQR_BATCHED_TC2_FIRST = 2,
+    OQR_BATCHED_SHIFTED_TC = 3,
+    OQR_BATCHED_SELECTOR = 4
+} oqr_batched_mode;
+
 oqr_status oqr_batched(oqr_ctx* ctx, int count, const int* m, const int* n, const double* const* A, const long* lda,
                        const double* const* Z, const long* ldz, double* const* Q, const long* ldq, double* const* R,
-                       const long* ldr, int mode, const int* splits, int* status, void* stream);
+                       const long* ldr, int mode, const oqr_opts* opts, int* status, void* stream);
+
+/*
+ * oqr_batched_features: the selector's 16 features of each instance (device,
+ * count x 16 floats, row-major, in the callers' instance order) after the
+ * first FP64-accurate pass that OQR_BATCHED_SELECTOR runs, without the rest:
+ * the training inputs of the selector's network.  Same instance limits as
+ * oqr_batched.  Synchronizes the stream.
+ */
+oqr_status oqr_batched_features(oqr_ctx* ctx, int count, const int* m, const int* n, const double* const* A,
+                                const long* lda, const double* const* Z, const long* ldz, float* feat, void* stream);
 
 /* Per-instance programs of the batched tensor-core path. */
 typedef enum {

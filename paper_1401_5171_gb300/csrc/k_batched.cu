@@ -426,6 +426,13 @@ __global__ void __launch_bounds__(256) check_batched_kernel(const BatchDesc* __r
     if (threadIdx.x == 0) orth[b] = best;
 }
 
+__global__ void scatter_rows_f32_kernel(const float* in, const int* perm, int count, int width, float* out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    for (int k = 0; k < width; ++k) out[(long)perm[i] * width + k] = in[(long)i * width + k];
+}
+
 __global__ void scatter_f64_kernel(const double* in, const int* perm, int count, double* out)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -479,6 +486,14 @@ cudaError_t launch_batched_factor(const BatchDesc* d, int count, int* status, in
     return cudaGetLastError();
 }
 
+cudaError_t launch_batched_gram_chol(const BatchDesc* d, int count, int* status, cudaStream_t s)
+{
+    dim3 gr((BATCH_MAX_N * BATCH_MAX_N + 255) / 256, count);
+    reduce_batched_kernel<<<gr, 256, 0, s>>>(d, status, nullptr, 0);
+    potrf_batched_kernel<<<count, 256, 0, s>>>(d, status, 0, 0);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_batched_rfinal(const BatchDesc* d, int count, int* status, cudaStream_t s)
 {
     dim3 gp((BATCH_MAX_N * BATCH_MAX_N + 255) / 256, count);
@@ -507,6 +522,13 @@ cudaError_t launch_batched_check(const BatchDesc* d, int count, const int* statu
                                  cudaStream_t s)
 {
     check_batched_kernel<<<count, 256, 0, s>>>(d, status, pass, orth);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_scatter_rows_f32(const float* in, const int* perm, int count, int width, float* out,
+                                          cudaStream_t s)
+{
+    scatter_rows_f32_kernel<<<(count + 255) / 256, 256, 0, s>>>(in, perm, count, width, out);
     return cudaGetLastError();
 }
 

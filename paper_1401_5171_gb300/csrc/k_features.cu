@@ -121,7 +121,151 @@ __global__ void trace_shift_kernel(int n, double* G, long ldg, double c, double 
     if (threadIdx.x == 0) st->shift = s;
 }
 
+// ---- features of a batch (the selector behind oqr_batched) -----------------
+// Read after the first FP64-accurate normal-equation pass of each instance:
+// G0 = Z^T A Z (exact to rounding, in the descriptor's G), the pass's Cholesky
+// status and, when it completed, its factor R1 (descriptor's R1).  Scale-free:
+//   f0 log10(m)/4       f1 log10(n)/2       f2 n/m
+//   f3 log10(max G_ii / min G_ii)/6                      (Gram diagonal spread)
+//   f4 max_{i!=j} |C_ij|, C = D^{-1/2} G0 D^{-1/2}       (coherence)
+//   f5 1 if the Cholesky of C breaks down, f6 its column / n
+//   f7 -log10(min pivot of C)/6, f8 log10(max pivot of C)/6
+//   f9 log10(trace G0 / max G_ii)/3
+//   f10 1 if the pass's Cholesky of G0 broke down, f11 its column / n
+//   f12 log10(kappa_sketch)/8, kappa_sketch = ||R1||_F ||R1^{-1} W||_F / ||W||_F
+//       with W an n x 2n Gaussian sketch (0 after a breakdown)
+//   f13..f15 0
+// W(i, j) comes from a counter-based generator both the library and its
+// tests implement from the published definitions: SplitMix64 (Steele, Lea and
+// Flood, 2014) on counters 2c and 2c + 1, c = j n + i, seed SKETCH_SEED,
+// turned into two uniforms (the top 53 bits; the first shifted to (0, 1]) and
+// one normal deviate by the Box-Muller transform sqrt(-2 ln u1) cos(2 pi u2).
+constexpr unsigned long long SKETCH_SEED = 0x0123456789ABCDEFull;
+
+__device__ inline unsigned long long splitmix64_at(unsigned long long counter)
+{
+    unsigned long long z = SKETCH_SEED + (counter + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ inline double sketch_gauss(int i, int j, int n)
+{
+    const unsigned long long c = (unsigned long long)j * n + i;
+    const double u1 = (double)((splitmix64_at(2 * c) >> 11) + 1ull) * 0x1.0p-53;
+    const double u2 = (double)(splitmix64_at(2 * c + 1) >> 11) * 0x1.0p-53;
+    return sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2);
+}
+
+__global__ void __launch_bounds__(256) features_batched_kernel(const BatchDesc* __restrict__ d, const int* status,
+                                                               float* feat)
+{
+    __shared__ double C[64][65];
+    __shared__ double red[8];
+    __shared__ int broke;
+    const int b = blockIdx.x, tid = threadIdx.x;
+    const BatchDesc D = d[b];
+    const int n = D.n, m = D.m;
+    const double* G = D.G;
+    const int probe = status[b];
+    double dmax = 0.0, dmin = INFINITY, dsum = 0.0;
+    for (int i = tid; i < n; i += 256) {
+        const double v = G[i + (long)i * n];
+        dmax = fmax(dmax, v);
+        dmin = fmin(dmin, v);
+        dsum += v;
+    }
+    dmax = bmax(dmax, red);
+    dmin = -bmax(-dmin, red);
+    dsum = bsum(dsum, red);
+    double coh = 0.0;
+    for (int e = tid; e < n * n; e += 256) {
+        const int i = e % n, j = e / n;
+        if (i > j) continue;
+        const double di = G[i + (long)i * n], dj = G[j + (long)j * n];
+        const double sc = (di > 0.0 && dj > 0.0) ? 1.0 / sqrt(di * dj) : 0.0;
+        const double v = G[j + (long)i * n] * sc;  // G's lower triangle
+        C[i][j] = v;
+        if (i != j) coh = fmax(coh, fabs(v));
+    }
+    coh = bmax(coh, red);
+    if (tid == 0) broke = 0;
+    __syncthreads();
+    double pmin = INFINITY, pmax = 0.0;
+    for (int j = 0; j < n; ++j) {
+        const double piv = C[j][j];
+        if (!(piv > 0.0) && tid == 0) broke = j + 1;
+        __syncthreads();
+        if (broke) break;
+        pmin = fmin(pmin, piv);
+        pmax = fmax(pmax, piv);
+        const double dj = sqrt(piv);
+        __syncthreads();
+        for (int c = j + 1 + tid; c < n; c += 256) C[j][c] /= dj;
+        __syncthreads();
+        const int w = n - j - 1;
+        for (int e = tid; e < w * w; e += 256) {
+            const int r = j + 1 + e % w, c = j + 1 + e / w;
+            if (r <= c) C[r][c] -= C[j][r] * C[j][c];
+        }
+        __syncthreads();
+    }
+    // sketched kappa(R1): ||R1||_F ||R1^{-1} W||_F / ||W||_F, one column of W per thread
+    double ksk = 0.0;
+    if (probe == 0) {
+        __syncthreads();
+        for (int e = tid; e < n * n; e += 256) {
+            const int i = e % n, j = e / n;
+            C[i][j] = i <= j ? D.R1[i + (long)j * n] : 0.0;
+        }
+        __syncthreads();
+        double rf = 0.0, xf = 0.0, wf = 0.0;
+        for (int e = tid; e < n * n; e += 256) rf += C[e % n][e / n] * C[e % n][e / n];
+        if (tid < 2 * n) {
+            double x[64];
+            for (int i = n - 1; i >= 0; --i) {
+                const double w = sketch_gauss(i, tid, n);
+                wf += w * w;
+                double t = w;
+                for (int l = i + 1; l < n; ++l) t -= C[i][l] * x[l];
+                x[i] = t / C[i][i];
+                xf += x[i] * x[i];
+            }
+        }
+        rf = bsum(rf, red);
+        xf = bsum(xf, red);
+        wf = bsum(wf, red);
+        ksk = sqrt(rf) * sqrt(xf / wf);
+    }
+    if (tid == 0) {
+        float f[MLP_IN];
+        for (int i = 0; i < MLP_IN; ++i) f[i] = 0.f;
+        f[0] = (float)(log10((double)m) / 4.0);
+        f[1] = (float)(log10((double)n) / 2.0);
+        f[2] = (float)((double)n / m);
+        f[3] = (dmin > 0.0) ? (float)(log10(dmax / dmin) / 6.0) : 4.f;
+        f[4] = (float)coh;
+        f[5] = broke ? 1.f : 0.f;
+        f[6] = broke ? (float)broke / n : 0.f;
+        f[7] = (pmin > 0.0 && pmin < INFINITY) ? (float)(-log10(pmin) / 6.0) : 0.f;
+        f[8] = (pmax > 0.0) ? (float)(log10(pmax) / 6.0) : 0.f;
+        f[9] = (dmax > 0.0 && dsum > 0.0) ? (float)(log10(dsum / dmax) / 3.0) : 0.f;
+        f[10] = probe ? 1.f : 0.f;
+        f[11] = probe > 0 ? (float)probe / n : 0.f;
+        f[12] = ksk > 0.0 ? (float)(log10(ksk) / 8.0) : 0.f;
+        for (int i = 0; i < MLP_IN; ++i) feat[(long)b * MLP_IN + i] = f[i];
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_features_batched(const BatchDesc* d, int count, const int* status, float* feat, cudaStream_t s)
+{
+    if (count <= 0) return cudaSuccess;
+    features_batched_kernel<<<count, 256, 0, s>>>(d, status, feat);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_features(int m, int n, const double* G, long ldg, double* work, const DevStatus* st, float* feat,
                             cudaStream_t s)

@@ -35,6 +35,9 @@ struct oqr_ctx {
     size_t stage_bytes = 0;
     cudaStream_t copy_stream = nullptr;
     std::vector<cudaEvent_t> events;
+    // the selector's fallback calls: their per-instance status and orth (device)
+    void* sel_buf = nullptr;
+    size_t sel_bytes = 0;
 };
 
 namespace {
@@ -70,6 +73,12 @@ void fill_defaults(oqr_opts* o)
     o->final_prec = OQR_FP64;
     o->prec_mid = -1;
     o->reuse_w = 0;
+    o->batch_splits = nullptr;
+    o->selector_params = nullptr;
+    o->selector_tol = 1e-12;
+    o->selector_check = 0;
+    o->batch_orth = nullptr;
+    o->batch_choice = nullptr;
 }
 
 oqr_opts resolve(const oqr_opts* o)
@@ -665,6 +674,411 @@ oqr_status run_cached_graph(oqr_ctx* ctx, const std::vector<long>& key, F seq, c
 }
 }  // namespace
 
+namespace {
+// FP64 A-CholQR2 over a batch (oqr_batched mode 0).
+oqr_status batched_fp64_impl(oqr_ctx* ctx, int count, const int* m, const int* n, const double* const* A,
+                             const long* lda, const double* const* Z, const long* ldz, double* const* Q,
+                             const long* ldq, double* const* R, const long* ldr, const int* splits, int* status,
+                             cudaStream_t stream)
+{
+    std::vector<BatchDesc> desc((size_t)count);
+    std::vector<int> idx[3];
+    int cls_max_splits[3] = {1, 1, 1}, max_n = 1;
+    size_t per_inst_doubles = 0;
+    for (int b = 0; b < count; ++b) {
+        const int mb = m[b], nb = n[b];
+        if (mb < 1 || nb < 1 || nb > mb || nb > BATCH_MAX_N || mb > BATCH_MAX_M) return OQR_ERR_INVALID_ARG;
+        if (bad_matrix(A[b], lda[b], mb, mb) || bad_matrix(Z[b], ldz[b], mb, nb) || bad_matrix(Q[b], ldq[b], mb, nb) ||
+            bad_matrix(R[b], ldr[b], nb, nb))
+            return OQR_ERR_INVALID_ARG;
+        const int sp = splits ? splits[b] : oqr_batched_default_splits(mb, nb);
+        if (sp < 1 || sp > 64) return OQR_ERR_INVALID_ARG;
+        BatchDesc& d = desc[b];
+        d.A = A[b];
+        d.Z = Z[b];
+        d.Q = Q[b];
+        d.R = R[b];
+        d.lda = lda[b];
+        d.ldz = ldz[b];
+        d.ldq = ldq[b];
+        d.ldr = ldr[b];
+        d.m = mb;
+        d.n = nb;
+        d.splits = sp;
+        d.npass = 2;
+        const int c = nb <= 16 ? 0 : nb <= 32 ? 1 : 2;
+        idx[c].push_back(b);
+        cls_max_splits[c] = std::max(cls_max_splits[c], sp);
+        max_n = std::max(max_n, nb);
+        per_inst_doubles += align256((size_t)(sp + 3) * nb * nb * sizeof(double)) / sizeof(double);
+    }
+    // workspace: descriptors, three index lists, per-instance partials + G + R1 + R2
+    Carve probe(nullptr);
+    probe.take<BatchDesc>((size_t)count);
+    for (int c = 0; c < 3; ++c) probe.take<int>(std::max<size_t>(1, idx[c].size()));
+    probe.take<double>(per_inst_doubles);
+    oqr_status v = ensure_ws(ctx, probe.off);
+    if (v != OQR_OK) return v;
+    Carve cv(ctx->ws);
+    BatchDesc* ddesc = cv.take<BatchDesc>((size_t)count);
+    int* didx[3];
+    for (int c = 0; c < 3; ++c) didx[c] = cv.take<int>(std::max<size_t>(1, idx[c].size()));
+    double* pool = cv.take<double>(per_inst_doubles);
+    for (int b = 0; b < count; ++b) {
+        const size_t nn = (size_t)desc[b].n * desc[b].n;
+        desc[b].partials = pool;
+        desc[b].G = pool + desc[b].splits * nn;
+        desc[b].R1 = desc[b].G + nn;
+        desc[b].R2 = desc[b].R1 + nn;
+        pool += align256((size_t)(desc[b].splits + 3) * nn * sizeof(double)) / sizeof(double);
+    }
+    cudaStream_t s = stream;
+    OQR_TRY(cudaMemcpyAsync(ddesc, desc.data(), sizeof(BatchDesc) * count, cudaMemcpyHostToDevice, s));
+    int cls_count[3];
+    for (int c = 0; c < 3; ++c) {
+        cls_count[c] = (int)idx[c].size();
+        if (cls_count[c]) OQR_TRY(cudaMemcpyAsync(didx[c], idx[c].data(), sizeof(int) * cls_count[c],
+                                                  cudaMemcpyHostToDevice, s));
+    }
+    OQR_TRY(cudaMemsetAsync(status, 0, sizeof(int) * count, s));
+    if (s == nullptr) {  // the legacy default stream cannot be captured
+        OQR_TRY(launch_batched_cholqr2(ddesc, count, didx, cls_count, cls_max_splits, max_n, status, s));
+        return OQR_OK;
+    }
+    const long key[10] = {count, cls_count[0], cls_count[1], cls_count[2], cls_max_splits[0], cls_max_splits[1],
+                          cls_max_splits[2], max_n, (long)reinterpret_cast<uintptr_t>(ctx->ws),
+                          (long)reinterpret_cast<uintptr_t>(status)};
+    if (!ctx->batch_exec || memcmp(key, ctx->batch_key, sizeof(key)) != 0) {
+        if (ctx->batch_exec) {
+            cudaStreamSynchronize(s);
+            cudaGraphExecDestroy(ctx->batch_exec);
+            ctx->batch_exec = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        OQR_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        const cudaError_t le = launch_batched_cholqr2(ddesc, count, didx, cls_count, cls_max_splits, max_n, status, s);
+        const cudaError_t ce = cudaStreamEndCapture(s, &g);
+        if (le != cudaSuccess || ce != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return OQR_ERR_CUDA;
+        }
+        const cudaError_t ie = cudaGraphInstantiate(&ctx->batch_exec, g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) {
+            ctx->batch_exec = nullptr;
+            return OQR_ERR_CUDA;
+        }
+        memcpy(ctx->batch_key, key, sizeof(key));
+    }
+    OQR_TRY(cudaGraphLaunch(ctx->batch_exec, s));
+    return OQR_OK;
+}
+
+}  // namespace
+
+// ---- the learned selector over a batch -------------------------------------
+// (oqr_batched in OQR_BATCHED_SELECTOR mode, and oqr_batched_features.)
+// Every option of the selector starts with the same first pass, an
+// FP64-accurate Gram G0 = Z^T A Z on the tensor cores, so that pass runs
+// first for the whole wave (the probe); its Gram and Cholesky factor give the
+// features, the MLP picks an option per instance, and each option finishes
+// from the probe in the same wave, reading the wave's split of A again:
+//   0 one pass:   Q = Z R1^{-1} is the result (checked: ||Q^T A Q - I||_2)
+//   1 two passes: one more FP64-accurate pass on Q (A-CholQR2)
+//   2 shifted:    R1 = chol(G0 + s I) from the same G0, then two more passes
+//                 (shifted A-CholQR3); also taken when the probe's Cholesky
+//                 broke down and the network chose 0 or 1
+//   3 FP64 A-CholQR2 (DFMA), run after the waves.
+// A failed check or a breakdown goes down the fallback chain: shifted
+// A-CholQR3 on the tensor cores (checked), then FP64 A-CholQR2.
+namespace {
+constexpr int SEL_ONE = 0, SEL_TWO = 1, SEL_SHIFTED = 2, SEL_FP64 = 3;
+
+struct SelInputs {
+    int count;
+    const int *m, *n;
+    const double* const* A;
+    const long* lda;
+    const double* const* Z;
+    const long* ldz;
+    double* const* Q;  // nullptr: features only
+    const long* ldq;
+    double* const* R;
+    const long* ldr;
+};
+
+// Host-side outcome per instance (caller order).
+struct SelResult {
+    std::vector<int> status, choice;
+    std::vector<double> orth;  // NaN where not checked
+};
+
+oqr_status selector_waves(oqr_ctx* ctx, const SelInputs& I, const float* params, bool check_all, float* feat_out,
+                          SelResult* res, cudaStream_t s)
+{
+    const int count = I.count;
+    const bool features_only = I.Q == nullptr;
+    std::vector<int> perm((size_t)count);
+    for (int b = 0; b < count; ++b) perm[b] = b;
+    std::stable_sort(perm.begin(), perm.end(), [&](int x, int y) { return I.m[x] > I.m[y]; });
+    std::vector<TcBatchShape> sh1((size_t)count), shmax((size_t)count);
+    size_t pool_doubles = 0;
+    for (int i = 0; i < count; ++i) {
+        const int b = perm[i];
+        sh1[i] = TcBatchShape{I.m[b], I.n[b], 1, 1};
+        shmax[i] = TcBatchShape{I.m[b], I.n[b], 1, TC_BATCH_MAX_PASS};
+        pool_doubles += align256((size_t)4 * I.n[b] * I.n[b] * sizeof(double)) / sizeof(double);
+    }
+    const size_t budget = ctx->batch_budget ? ctx->batch_budget : BATCH_WAVE_BYTES;
+    const TcBatchPlan plan = tc_batch_plan(sh1, budget);
+    const TcBatchPlan pmax = tc_batch_plan(shmax, budget);  // bounds every per-wave plan of the later passes
+    if (pmax.waves.size() != plan.waves.size()) return OQR_ERR_UNSUPPORTED;
+    auto layout = [&](Carve& c, char** tab1, char** tab2, BatchDesc** d, int** sts, int** dshifted, double** sums,
+                      double** shifts, double** orths, float** feat, int** choice, double** pool, double** upool,
+                      void** scratch) {
+        *tab1 = c.take<char>(plan.table_bytes);
+        *tab2 = c.take<char>(pmax.table_bytes);
+        *d = c.take<BatchDesc>((size_t)count);
+        *sts = c.take<int>((size_t)count);
+        *dshifted = c.take<int>((size_t)count);
+        *sums = c.take<double>((size_t)2 * count);
+        *shifts = c.take<double>((size_t)count);
+        *orths = c.take<double>((size_t)count);
+        *feat = c.take<float>((size_t)count * MLP_IN);
+        *choice = c.take<int>((size_t)count);
+        *pool = c.take<double>(pool_doubles);
+        *upool = c.take<double>((size_t)std::max(plan.upool_doubles, pmax.upool_doubles));
+        *scratch = c.take<char>(std::max(plan.scratch_bytes, pmax.scratch_bytes));
+    };
+    char *tab1, *tab2;
+    BatchDesc* ddesc;
+    int *sts, *dshifted, *dchoice;
+    double *sums, *shifts, *orths, *pool, *upool;
+    float* feat;
+    void* scratch;
+    Carve probe(nullptr);
+    layout(probe, &tab1, &tab2, &ddesc, &sts, &dshifted, &sums, &shifts, &orths, &feat, &dchoice, &pool, &upool,
+           &scratch);
+    oqr_status v = ensure_ws(ctx, probe.off);
+    if (v != OQR_OK) return v;
+    Carve cv(ctx->ws);
+    layout(cv, &tab1, &tab2, &ddesc, &sts, &dshifted, &sums, &shifts, &orths, &feat, &dchoice, &pool, &upool,
+           &scratch);
+    std::vector<BatchDesc> desc((size_t)count);
+    std::vector<TcBatchIn> in((size_t)count);
+    double* q = pool;
+    for (int i = 0; i < count; ++i) {
+        const int b = perm[i];
+        const size_t nn = (size_t)I.n[b] * I.n[b];
+        BatchDesc& d = desc[i];
+        d.A = I.A[b];
+        d.Z = I.Z[b];
+        d.Q = features_only ? nullptr : I.Q[b];
+        d.R = features_only ? nullptr : I.R[b];
+        d.lda = I.lda[b];
+        d.ldz = I.ldz[b];
+        d.ldq = features_only ? I.m[b] : I.ldq[b];
+        d.ldr = features_only ? I.n[b] : I.ldr[b];
+        d.m = I.m[b];
+        d.n = I.n[b];
+        d.splits = 1;
+        d.npass = 1;
+        d.partials = q;
+        d.G = q + nn;
+        d.R1 = d.G + nn;
+        d.R2 = d.R1 + nn;
+        q += align256(4 * nn * sizeof(double)) / sizeof(double);
+        in[i] = TcBatchIn{I.A[b], I.lda[b], I.Z[b], I.ldz[b], features_only ? const_cast<double*>(I.Z[b]) : I.Q[b],
+                          features_only ? I.ldz[b] : I.ldq[b], d.partials};
+    }
+    std::vector<char> image;
+    tc_batch_tables(plan, sh1, in, tab1, upool, image);
+    OQR_TRY(cudaMemcpyAsync(tab1, image.data(), image.size(), cudaMemcpyHostToDevice, s));
+    OQR_TRY(cudaMemcpyAsync(ddesc, desc.data(), sizeof(BatchDesc) * count, cudaMemcpyHostToDevice, s));
+    OQR_TRY(cudaMemsetAsync(sts, 0, sizeof(int) * count, s));
+    if ((v = reset_status(ctx, s)) != OQR_OK) return v;
+    const uint64_t limit = 4000000000ull;
+    std::vector<int> hst((size_t)count, 0), hch((size_t)count, 0), opt((size_t)count, 0), chk((size_t)count, 0);
+    for (int w = 0; w < (int)plan.waves.size(); ++w) {
+        const NvtxRange range("oqr: selector wave %d", w);
+        const TcBatchWave& W = plan.waves[w];
+        const int f = W.first, cnt = W.count;
+        BatchDesc* dw = ddesc + f;
+        int* sw = sts + f;
+        OQR_TRY(tc_batch_split_a(plan, w, tab1, scratch, s));
+        OQR_TRY(tc_batch_gram(plan, w, 0, tab1, scratch, ctx->st, limit, ctx->sm_count, s));
+        if (features_only) OQR_TRY(launch_batched_gram_chol(dw, cnt, sw, s));
+        else OQR_TRY(launch_batched_factor(dw, cnt, sw, 0, nullptr, s));
+        OQR_TRY(launch_features_batched(dw, cnt, sw, feat + (size_t)f * MLP_IN, s));
+        if (features_only) continue;
+        OQR_TRY(launch_mlp_forward(cnt, feat + (size_t)f * MLP_IN, params, 1, nullptr, dchoice + f, s));
+        OQR_TRY(cudaMemcpyAsync(hch.data() + f, dchoice + f, sizeof(int) * cnt, cudaMemcpyDeviceToHost, s));
+        OQR_TRY(cudaMemcpyAsync(hst.data() + f, sw, sizeof(int) * cnt, cudaMemcpyDeviceToHost, s));
+        if (cudaStreamSynchronize(s) != cudaSuccess) return OQR_ERR_CUDA;
+        // the option each instance finishes with, and its passes
+        std::vector<TcBatchShape> sh2((size_t)cnt);
+        std::vector<int> shifted((size_t)cnt, 0);
+        bool any_shift = false;
+        for (int k = 0; k < cnt; ++k) {
+            const int i = f + k;
+            int o = hch[i] < 0 || hch[i] > 3 ? SEL_SHIFTED : hch[i];
+            if ((o == SEL_ONE || o == SEL_TWO) && hst[i] != 0) o = SEL_SHIFTED;  // the unshifted probe broke down
+            opt[i] = o;
+            chk[i] = o == SEL_ONE || (check_all && o != SEL_FP64);
+            const int np = o == SEL_ONE ? 1 : o == SEL_TWO ? 2 : o == SEL_SHIFTED ? 3 : 1;
+            sh2[k] = TcBatchShape{sh1[i].m, sh1[i].n, 1, np + chk[i]};
+            shifted[k] = o == SEL_SHIFTED;
+            any_shift = any_shift || shifted[k];
+            desc[i].npass = shifted[k] ? 3 : 0;
+        }
+        if (any_shift) {  // the shifted first pass from the same G0
+            for (int k = 0; k < cnt; ++k)
+                if (shifted[k]) hst[f + k] = 0;
+            OQR_TRY(cudaMemcpyAsync(dw, desc.data() + f, sizeof(BatchDesc) * cnt, cudaMemcpyHostToDevice, s));
+            OQR_TRY(cudaMemcpyAsync(sw, hst.data() + f, sizeof(int) * cnt, cudaMemcpyHostToDevice, s));
+            OQR_TRY(cudaMemcpyAsync(dshifted + f, shifted.data(), sizeof(int) * cnt, cudaMemcpyHostToDevice, s));
+            OQR_TRY(launch_batched_shifts(dw, cnt, dshifted + f, sums + 2 * f, 11.0, U64, shifts + f, s));
+            OQR_TRY(launch_batched_factor(dw, cnt, sw, 0, shifts + f, s));
+        }
+        for (int k = 0; k < cnt; ++k) desc[f + k].npass = sh2[k].npass - chk[f + k];
+        OQR_TRY(cudaMemcpyAsync(dw, desc.data() + f, sizeof(BatchDesc) * cnt, cudaMemcpyHostToDevice, s));
+        // the later passes of the wave, with tables for exactly this wave (same packing as the probe's)
+        const std::vector<TcBatchIn> in2(in.begin() + f, in.begin() + f + cnt);
+        const TcBatchPlan p2 = tc_batch_plan(sh2, budget);
+        if (p2.waves.size() != 1 || p2.table_bytes > pmax.table_bytes || p2.scratch_bytes > pmax.scratch_bytes)
+            return OQR_ERR_UNSUPPORTED;
+        std::vector<char> image2;
+        tc_batch_tables(p2, sh2, in2, tab2, upool, image2);
+        OQR_TRY(cudaMemcpyAsync(tab2, image2.data(), image2.size(), cudaMemcpyHostToDevice, s));
+        for (int pass = 1; pass < p2.waves[0].maxpass; ++pass) {
+            OQR_TRY(tc_batch_gram(p2, 0, pass, tab2, scratch, ctx->st, limit, ctx->sm_count, s));
+            OQR_TRY(launch_batched_factor(dw, cnt, sw, pass, nullptr, s));
+            OQR_TRY(launch_batched_check(dw, cnt, sw, pass, orths + f, s));
+        }
+        OQR_TRY(launch_batched_rfinal(dw, cnt, sw, s));
+        // the host images must outlive their asynchronous copies
+        if (cudaStreamSynchronize(s) != cudaSuccess) return OQR_ERR_CUDA;
+    }
+    if (features_only) {
+        std::vector<int> hperm(perm);
+        int* dperm = dchoice;  // free by now: the permutation for the scatter
+        OQR_TRY(cudaMemcpyAsync(dperm, hperm.data(), sizeof(int) * count, cudaMemcpyHostToDevice, s));
+        OQR_TRY(launch_batch_scatter_rows_f32(feat, dperm, count, MLP_IN, feat_out, s));
+        if (cudaStreamSynchronize(s) != cudaSuccess) return OQR_ERR_CUDA;
+        return OQR_OK;
+    }
+    std::vector<double> hor((size_t)count);
+    OQR_TRY(cudaMemcpyAsync(hst.data(), sts, sizeof(int) * count, cudaMemcpyDeviceToHost, s));
+    OQR_TRY(cudaMemcpyAsync(hor.data(), orths, sizeof(double) * count, cudaMemcpyDeviceToHost, s));
+    DevStatus hs;
+    OQR_TRY(cudaMemcpyAsync(&hs, ctx->st, sizeof(hs), cudaMemcpyDeviceToHost, s));
+    if (cudaStreamSynchronize(s) != cudaSuccess) return OQR_ERR_CUDA;
+    res->status.assign((size_t)count, 0);
+    res->choice.assign((size_t)count, 0);
+    res->orth.assign((size_t)count, std::nan(""));
+    for (int i = 0; i < count; ++i) {
+        const int b = perm[i];
+        res->status[b] = hs.code != 0 ? -1 : hst[i];
+        res->choice[b] = opt[i];
+        if (chk[i]) res->orth[b] = hst[i] == 0 ? hor[i] : INFINITY;
+    }
+    return hs.code != 0 ? OQR_ERR_TIMEOUT : OQR_OK;
+}
+
+// A sub-batch call for the fallback chain: outputs into the caller's Q and R of
+// those instances; status (and orth) through the context's small selector buffer.
+oqr_status selector_subset(oqr_ctx* ctx, const SelInputs& I, const std::vector<int>& idx, int mode,
+                           SelResult* res, cudaStream_t s)
+{
+    const int k = (int)idx.size();
+    if (k == 0) return OQR_OK;
+    std::vector<int> m(k), n(k), pr(k, OQR_BATCH_SCHOLQR3_TC);
+    std::vector<const double*> A(k), Z(k);
+    std::vector<double*> Q(k), R(k);
+    std::vector<long> lda(k), ldz(k), ldq(k), ldr(k);
+    for (int j = 0; j < k; ++j) {
+        const int b = idx[j];
+        m[j] = I.m[b];
+        n[j] = I.n[b];
+        A[j] = I.A[b];
+        Z[j] = I.Z[b];
+        Q[j] = I.Q[b];
+        R[j] = I.R[b];
+        lda[j] = I.lda[b];
+        ldz[j] = I.ldz[b];
+        ldq[j] = I.ldq[b];
+        ldr[j] = I.ldr[b];
+    }
+    const size_t need = (size_t)k * (sizeof(int) + sizeof(double)) + 256;
+    if (ctx->sel_bytes < need) {
+        if (ctx->sel_buf) {
+            cudaStreamSynchronize(s);
+            cudaFree(ctx->sel_buf);
+            ctx->sel_buf = nullptr;
+            ctx->sel_bytes = 0;
+        }
+        if (cudaMalloc(&ctx->sel_buf, need) != cudaSuccess) {
+            cudaGetLastError();
+            return OQR_ERR_NO_MEMORY;
+        }
+        ctx->sel_bytes = need;
+    }
+    double* dorth = static_cast<double*>(ctx->sel_buf);
+    int* dst = reinterpret_cast<int*>(dorth + k);
+    oqr_status v;
+    if (mode == 0) {
+        v = batched_fp64_impl(ctx, k, m.data(), n.data(), A.data(), lda.data(), Z.data(), ldz.data(), Q.data(),
+                              ldq.data(), R.data(), ldr.data(), nullptr, dst, s);
+    } else {
+        v = oqr_batched_mixed(ctx, k, m.data(), n.data(), A.data(), lda.data(), Z.data(), ldz.data(), Q.data(),
+                              ldq.data(), R.data(), ldr.data(), pr.data(), dst, dorth, s);
+    }
+    if (v != OQR_OK) return v;
+    std::vector<int> hst(k);
+    std::vector<double> hor(k);
+    OQR_TRY(cudaMemcpyAsync(hst.data(), dst, sizeof(int) * k, cudaMemcpyDeviceToHost, s));
+    if (mode != 0) OQR_TRY(cudaMemcpyAsync(hor.data(), dorth, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+    if (cudaStreamSynchronize(s) != cudaSuccess) return OQR_ERR_CUDA;
+    for (int j = 0; j < k; ++j) {
+        const int b = idx[j];
+        res->status[b] = hst[j];
+        res->choice[b] = mode == 0 ? SEL_FP64 : SEL_SHIFTED;
+        res->orth[b] = mode == 0 ? std::nan("") : (hst[j] == 0 ? hor[j] : INFINITY);
+    }
+    return OQR_OK;
+}
+
+oqr_status selector_batch(oqr_ctx* ctx, const SelInputs& I, const oqr_opts& o, int* status, cudaStream_t s)
+{
+    if (!o.selector_params) return OQR_ERR_INVALID_ARG;
+    SelResult res;
+    oqr_status v = selector_waves(ctx, I, o.selector_params, o.selector_check != 0, nullptr, &res, s);
+    if (v != OQR_OK && v != OQR_ERR_TIMEOUT) return v;
+    const double tol = o.selector_tol > 0 ? o.selector_tol : 1e-12;
+    if (v == OQR_OK) {
+        auto failed = [&](int b) {
+            return res.status[b] != 0 || (!std::isnan(res.orth[b]) && !(res.orth[b] <= tol));
+        };
+        // fallback 1: shifted A-CholQR3 on the tensor cores for a failed check or a breakdown of an unshifted option
+        std::vector<int> fb1, fb2;
+        for (int b = 0; b < I.count; ++b)
+            if (res.choice[b] != SEL_SHIFTED && res.choice[b] != SEL_FP64 && failed(b)) fb1.push_back(b);
+        if ((v = selector_subset(ctx, I, fb1, 1, &res, s)) != OQR_OK) return v;
+        // fallback 2 (and the network's own FP64 choices): FP64 A-CholQR2
+        for (int b = 0; b < I.count; ++b)
+            if (res.choice[b] == SEL_FP64 || failed(b)) fb2.push_back(b);
+        if ((v = selector_subset(ctx, I, fb2, 0, &res, s)) != OQR_OK) return v;
+    }
+    OQR_TRY(cudaMemcpy(status, res.status.data(), sizeof(int) * I.count, cudaMemcpyHostToDevice));
+    if (o.batch_orth)
+        OQR_TRY(cudaMemcpy(o.batch_orth, res.orth.data(), sizeof(double) * I.count, cudaMemcpyHostToDevice));
+    if (o.batch_choice)
+        OQR_TRY(cudaMemcpy(o.batch_choice, res.choice.data(), sizeof(int) * I.count, cudaMemcpyHostToDevice));
+    return v;
+}
+}  // namespace
+
 extern "C" {
 
 void oqr_default_opts(oqr_opts* opts)
@@ -718,6 +1132,7 @@ oqr_status oqr_destroy(oqr_ctx* ctx)
     if (ctx->batch_exec) cudaGraphExecDestroy(ctx->batch_exec);
     if (ctx->mixed_exec) cudaGraphExecDestroy(ctx->mixed_exec);
     if (ctx->stage) cudaFree(ctx->stage);
+    if (ctx->sel_buf) cudaFree(ctx->sel_buf);
     for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
     if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
     if (ctx->ws && ctx->ws_owned) cudaFree(ctx->ws);
@@ -923,110 +1338,46 @@ int oqr_batched_default_splits(int m, int n)
 
 oqr_status oqr_batched(oqr_ctx* ctx, int count, const int* m, const int* n, const double* const* A, const long* lda,
                        const double* const* Z, const long* ldz, double* const* Q, const long* ldq, double* const* R,
-                       const long* ldr, int mode, const int* splits, int* status, void* stream)
+                       const long* ldr, int mode, const oqr_opts* opts, int* status, void* stream)
 {
     if (!ctx || count < 1 || count > 65535 || !m || !n || !A || !lda || !Z || !ldz || !Q || !ldq || !R || !ldr ||
         !status)
         return OQR_ERR_INVALID_ARG;
-    if (mode >= 1 && mode <= 3) {
-        const int prog = mode == 1 ? OQR_BATCH_CHOLQR2_TC : mode == 2 ? OQR_BATCH_CHOLQR2_TC2 : OQR_BATCH_SCHOLQR3_TC;
+    const oqr_opts o = resolve(opts);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (mode >= OQR_BATCHED_TC && mode <= OQR_BATCHED_SHIFTED_TC) {
+        const int prog = mode == OQR_BATCHED_TC ? OQR_BATCH_CHOLQR2_TC
+                         : mode == OQR_BATCHED_TC2_FIRST ? OQR_BATCH_CHOLQR2_TC2
+                                                         : OQR_BATCH_SCHOLQR3_TC;
         std::vector<int> pr((size_t)count, prog);
-        return oqr_batched_mixed(ctx, count, m, n, A, lda, Z, ldz, Q, ldq, R, ldr, pr.data(), status, nullptr,
+        return oqr_batched_mixed(ctx, count, m, n, A, lda, Z, ldz, Q, ldq, R, ldr, pr.data(), status, o.batch_orth,
                                  stream);
     }
-    if (mode != 0) return OQR_ERR_INVALID_ARG;
-    std::vector<BatchDesc> desc((size_t)count);
-    std::vector<int> idx[3];
-    int cls_max_splits[3] = {1, 1, 1}, max_n = 1;
-    size_t per_inst_doubles = 0;
+    if (mode == OQR_BATCHED_FP64)
+        return batched_fp64_impl(ctx, count, m, n, A, lda, Z, ldz, Q, ldq, R, ldr, o.batch_splits, status, s);
+    if (mode != OQR_BATCHED_SELECTOR) return OQR_ERR_INVALID_ARG;
     for (int b = 0; b < count; ++b) {
         const int mb = m[b], nb = n[b];
         if (mb < 1 || nb < 1 || nb > mb || nb > BATCH_MAX_N || mb > BATCH_MAX_M) return OQR_ERR_INVALID_ARG;
         if (bad_matrix(A[b], lda[b], mb, mb) || bad_matrix(Z[b], ldz[b], mb, nb) || bad_matrix(Q[b], ldq[b], mb, nb) ||
             bad_matrix(R[b], ldr[b], nb, nb))
             return OQR_ERR_INVALID_ARG;
-        const int sp = splits ? splits[b] : oqr_batched_default_splits(mb, nb);
-        if (sp < 1 || sp > 64) return OQR_ERR_INVALID_ARG;
-        BatchDesc& d = desc[b];
-        d.A = A[b];
-        d.Z = Z[b];
-        d.Q = Q[b];
-        d.R = R[b];
-        d.lda = lda[b];
-        d.ldz = ldz[b];
-        d.ldq = ldq[b];
-        d.ldr = ldr[b];
-        d.m = mb;
-        d.n = nb;
-        d.splits = sp;
-        d.npass = 2;
-        const int c = nb <= 16 ? 0 : nb <= 32 ? 1 : 2;
-        idx[c].push_back(b);
-        cls_max_splits[c] = std::max(cls_max_splits[c], sp);
-        max_n = std::max(max_n, nb);
-        per_inst_doubles += align256((size_t)(sp + 3) * nb * nb * sizeof(double)) / sizeof(double);
     }
-    // workspace: descriptors, three index lists, per-instance partials + G + R1 + R2
-    Carve probe(nullptr);
-    probe.take<BatchDesc>((size_t)count);
-    for (int c = 0; c < 3; ++c) probe.take<int>(std::max<size_t>(1, idx[c].size()));
-    probe.take<double>(per_inst_doubles);
-    oqr_status v = ensure_ws(ctx, probe.off);
-    if (v != OQR_OK) return v;
-    Carve cv(ctx->ws);
-    BatchDesc* ddesc = cv.take<BatchDesc>((size_t)count);
-    int* didx[3];
-    for (int c = 0; c < 3; ++c) didx[c] = cv.take<int>(std::max<size_t>(1, idx[c].size()));
-    double* pool = cv.take<double>(per_inst_doubles);
+    const SelInputs in{count, m, n, A, lda, Z, ldz, Q, ldq, R, ldr};
+    return selector_batch(ctx, in, o, status, s);
+}
+
+oqr_status oqr_batched_features(oqr_ctx* ctx, int count, const int* m, const int* n, const double* const* A,
+                                const long* lda, const double* const* Z, const long* ldz, float* feat, void* stream)
+{
+    if (!ctx || count < 1 || count > 65535 || !m || !n || !A || !lda || !Z || !ldz || !feat) return OQR_ERR_INVALID_ARG;
     for (int b = 0; b < count; ++b) {
-        const size_t nn = (size_t)desc[b].n * desc[b].n;
-        desc[b].partials = pool;
-        desc[b].G = pool + desc[b].splits * nn;
-        desc[b].R1 = desc[b].G + nn;
-        desc[b].R2 = desc[b].R1 + nn;
-        pool += align256((size_t)(desc[b].splits + 3) * nn * sizeof(double)) / sizeof(double);
+        const int mb = m[b], nb = n[b];
+        if (mb < 1 || nb < 1 || nb > mb || nb > BATCH_MAX_N || mb > BATCH_MAX_M) return OQR_ERR_INVALID_ARG;
+        if (bad_matrix(A[b], lda[b], mb, mb) || bad_matrix(Z[b], ldz[b], mb, nb)) return OQR_ERR_INVALID_ARG;
     }
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    OQR_TRY(cudaMemcpyAsync(ddesc, desc.data(), sizeof(BatchDesc) * count, cudaMemcpyHostToDevice, s));
-    int cls_count[3];
-    for (int c = 0; c < 3; ++c) {
-        cls_count[c] = (int)idx[c].size();
-        if (cls_count[c]) OQR_TRY(cudaMemcpyAsync(didx[c], idx[c].data(), sizeof(int) * cls_count[c],
-                                                  cudaMemcpyHostToDevice, s));
-    }
-    OQR_TRY(cudaMemsetAsync(status, 0, sizeof(int) * count, s));
-    if (s == nullptr) {  // the legacy default stream cannot be captured
-        OQR_TRY(launch_batched_cholqr2(ddesc, count, didx, cls_count, cls_max_splits, max_n, status, s));
-        return OQR_OK;
-    }
-    const long key[10] = {count, cls_count[0], cls_count[1], cls_count[2], cls_max_splits[0], cls_max_splits[1],
-                          cls_max_splits[2], max_n, (long)reinterpret_cast<uintptr_t>(ctx->ws),
-                          (long)reinterpret_cast<uintptr_t>(status)};
-    if (!ctx->batch_exec || memcmp(key, ctx->batch_key, sizeof(key)) != 0) {
-        if (ctx->batch_exec) {
-            cudaStreamSynchronize(s);
-            cudaGraphExecDestroy(ctx->batch_exec);
-            ctx->batch_exec = nullptr;
-        }
-        cudaGraph_t g = nullptr;
-        OQR_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-        const cudaError_t le = launch_batched_cholqr2(ddesc, count, didx, cls_count, cls_max_splits, max_n, status, s);
-        const cudaError_t ce = cudaStreamEndCapture(s, &g);
-        if (le != cudaSuccess || ce != cudaSuccess) {
-            if (g) cudaGraphDestroy(g);
-            cudaGetLastError();
-            return OQR_ERR_CUDA;
-        }
-        const cudaError_t ie = cudaGraphInstantiate(&ctx->batch_exec, g, 0);
-        cudaGraphDestroy(g);
-        if (ie != cudaSuccess) {
-            ctx->batch_exec = nullptr;
-            return OQR_ERR_CUDA;
-        }
-        memcpy(ctx->batch_key, key, sizeof(key));
-    }
-    OQR_TRY(cudaGraphLaunch(ctx->batch_exec, s));
-    return OQR_OK;
+    const SelInputs in{count, m, n, A, lda, Z, ldz, nullptr, nullptr, nullptr, nullptr};
+    return selector_waves(ctx, in, nullptr, false, feat, nullptr, static_cast<cudaStream_t>(stream));
 }
 
 oqr_status oqr_batched_mixed(oqr_ctx* ctx, int count, const int* m, const int* n, const double* const* A,

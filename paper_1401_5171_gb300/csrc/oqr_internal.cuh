@@ -301,6 +301,13 @@ cudaError_t launch_batch_status_scatter(const int* st_sorted, const int* perm, i
 // ||E||_2 (power iteration, a lower bound); orth[b] = inf after a breakdown.
 cudaError_t launch_batched_check(const BatchDesc* d, int count, const int* status, int pass, double* orth,
                                  cudaStream_t s);
+// Pass 0's G = P + P^T and R1 = chol(G) only (no solve; the selector's features of a batch).
+cudaError_t launch_batched_gram_chol(const BatchDesc* d, int count, int* status, cudaStream_t s);
+// Rows of width floats: out[perm[i]] = in[i].
+cudaError_t launch_batch_scatter_rows_f32(const float* in, const int* perm, int count, int width, float* out,
+                                          cudaStream_t s);
+// The selector's 16 features of each instance of a batch after its first FP64-accurate pass (k_features.cu).
+cudaError_t launch_features_batched(const BatchDesc* d, int count, const int* status, float* feat, cudaStream_t s);
 // out[perm[i]] = in[i] (count doubles).
 cudaError_t launch_batch_scatter_f64(const double* in, const int* perm, int count, double* out, cudaStream_t s);
 

@@ -23,13 +23,16 @@ OQR_ERR_CUDA, OQR_ERR_NO_MEMORY, OQR_ERR_TIMEOUT, OQR_ERR_UNSUPPORTED = 4, 5, 6,
 OQR_FP64, OQR_BF16X3, OQR_FP8, OQR_FP64_TC, OQR_TC2 = 0, 1, 2, 3, 4
 OQR_BATCH_CHOLQR_TC, OQR_BATCH_CHOLQR2_TC2, OQR_BATCH_CHOLQR2_TC, OQR_BATCH_SCHOLQR3_TC = 0, 1, 2, 3
 OQR_ALGO_CHOLQR, OQR_ALGO_CHOLQR2, OQR_ALGO_SCHOLQR3, OQR_ALGO_CGS2 = 0, 1, 2, 3
+OQR_BATCHED_FP64, OQR_BATCHED_TC, OQR_BATCHED_TC2_FIRST, OQR_BATCHED_SHIFTED_TC, OQR_BATCHED_SELECTOR = 0, 1, 2, 3, 4
 
 
 class oqr_opts(ctypes.Structure):
     _fields_ = [("passes", ctypes.c_int), ("shifted", ctypes.c_int), ("prec", ctypes.c_int),
                 ("shift_c", ctypes.c_double), ("block", ctypes.c_int), ("check", ctypes.c_int),
                 ("spin_limit", ctypes.c_long), ("final_prec", ctypes.c_int), ("prec_mid", ctypes.c_int),
-                ("reuse_w", ctypes.c_int)]
+                ("reuse_w", ctypes.c_int), ("batch_splits", ctypes.c_void_p), ("selector_params", ctypes.c_void_p),
+                ("selector_tol", ctypes.c_double), ("selector_check", ctypes.c_int), ("batch_orth", ctypes.c_void_p),
+                ("batch_choice", ctypes.c_void_p)]
 
 
 class oqr_info(ctypes.Structure):
@@ -88,7 +91,8 @@ def load(path: str | None = None):
     pl = ctypes.POINTER(ctypes.c_long)
     ppd = ctypes.POINTER(ctypes.c_void_p)
     lib.oqr_batched.argtypes = [vp, i, ctypes.POINTER(i), ctypes.POINTER(i), ppd, pl, ppd, pl, ppd, pl, ppd, pl, i,
-                                ctypes.POINTER(i), vp, vp]
+                                po, vp, vp]
+    lib.oqr_batched_features.argtypes = [vp, i, ctypes.POINTER(i), ctypes.POINTER(i), ppd, pl, ppd, pl, vp, vp]
     lib.oqr_batched_mixed.argtypes = [vp, i, ctypes.POINTER(i), ctypes.POINTER(i), ppd, pl, ppd, pl, ppd, pl, ppd,
                                       pl, ctypes.POINTER(i), vp, vp, vp]
     lib.oqr_batched_default_splits.argtypes = [i, i]
@@ -142,7 +146,7 @@ for _n in ("oqr_default_opts", "oqr_create", "oqr_destroy", "oqr_workspace_size"
            "oqr_get_status", "oqr_cholqr", "oqr_cholqr2", "oqr_cholqr2_host", "oqr_cgs2", "oqr_gram", "oqr_gram_noalloc", "oqr_gram_phases", "oqr_potrf", "oqr_trsm", "oqr_trsm_tc",
            "oqr_rprod", "oqr_check", "oqr_repres", "oqr_diag_timeout", "oqr_set_batch_budget", "oqr_batched", "oqr_batched_mixed", "oqr_batched_default_splits", "oqr_features",
            "oqr_mlp_param_count", "oqr_mlp_forward", "oqr_mlp_grad", "oqr_mlp_adam", "oqr_glls", "oqr_symm", "oqr_cholqr2_tridiag", "oqr_gram_tridiag",
-           "oqr_precholqr", "oqr_precholqr_tridiag", "oqr_tsqr"):
+           "oqr_precholqr", "oqr_precholqr_tridiag", "oqr_tsqr", "oqr_batched_features"):
     globals()[_n] = _raw(_n)
 
 
@@ -319,18 +323,50 @@ class Oqr:
         st = status if status is not None else torch.empty(cnt, dtype=torch.int32, device=Zs[0].device)
         return Qs, Rs, st, (cnt, mm, nn, ap, al, zp, zl, qp, ql, rp, rl)
 
-    def oqr_batched(self, As, Zs, Qs=None, Rs=None, splits=None, stream=None, status=None, mode=0):
-        """Batched A-CholQR2 over lists of column-major CUDA tensors; returns (Qs, Rs, status tensor).
+    def oqr_batched(self, As, Zs, Qs=None, Rs=None, splits=None, stream=None, status=None, mode=0, params=None,
+                    tol=1e-12, check_all=False, orth=None, choice=None):
+        """Batched oblique QR over lists of column-major CUDA tensors; returns (Qs, Rs, status tensor).
 
-        mode 0: FP64; tensor cores: 1 OQR_BATCH_CHOLQR2_TC, 2 OQR_BATCH_CHOLQR2_TC2, 3 OQR_BATCH_SCHOLQR3_TC."""
+        mode: OQR_BATCHED_FP64 (splits: the work plan), OQR_BATCHED_TC, OQR_BATCHED_TC2_FIRST,
+        OQR_BATCHED_SHIFTED_TC, or OQR_BATCHED_SELECTOR (params: the trained network, a float32 CUDA tensor;
+        tol, check_all: the selector's check).  orth (float64) and choice (int32) CUDA tensors of one entry
+        per instance, when given, receive the checks and (selector) the options used."""
         Qs, Rs, st, a = self._batch_args(As, Zs, Qs, Rs, status)
         if splits is not None and len(splits) != a[0]:
             raise ValueError("splits needs one entry per instance")
         sp = (ctypes.c_int * a[0])(*splits) if splits is not None else None
-        r = self.lib.oqr_batched(self.ctx, *a, int(mode), sp, ctypes.c_void_p(st.data_ptr()), self._stream(stream))
+        o = make_opts()
+        o.batch_splits = ctypes.cast(sp, ctypes.c_void_p) if sp is not None else None
+        o.selector_params = params.data_ptr() if params is not None else None
+        o.selector_tol = float(tol)
+        o.selector_check = 1 if check_all else 0
+        o.batch_orth = orth.data_ptr() if orth is not None else None
+        o.batch_choice = choice.data_ptr() if choice is not None else None
+        r = self.lib.oqr_batched(self.ctx, *a, int(mode), ctypes.byref(o), ctypes.c_void_p(st.data_ptr()),
+                                 self._stream(stream))
         if r != OQR_OK:
             raise OqrError(r, "oqr_batched")
         return Qs, Rs, st
+
+    def oqr_batched_features(self, As, Zs, stream=None):
+        """The selector's features (count x 16 float32 CUDA tensor) after each instance's first FP64-accurate
+        pass."""
+        import torch
+        cnt = len(Zs)
+        I = ctypes.c_int * cnt
+        L = ctypes.c_long * cnt
+        P = ctypes.c_void_p * cnt
+        mm = I(*[z.shape[0] for z in Zs])
+        nn = I(*[z.shape[1] for z in Zs])
+        ap, al, zp, zl = P(), L(), P(), L()
+        for b in range(cnt):
+            (ap[b], al[b]), (zp[b], zl[b]) = _m(As[b]), _m(Zs[b])
+        feat = torch.empty((cnt, 16), dtype=torch.float32, device=Zs[0].device)
+        r = self.lib.oqr_batched_features(self.ctx, cnt, mm, nn, ap, al, zp, zl, ctypes.c_void_p(feat.data_ptr()),
+                                          self._stream(stream))
+        if r != OQR_OK:
+            raise OqrError(r, "oqr_batched_features")
+        return feat
 
     def oqr_batched_mixed(self, As, Zs, program=None, Qs=None, Rs=None, stream=None, status=None, check=False):
         """Batched oblique QR on the tensor cores; program: per-instance OQR_BATCH_* (None: all

@@ -1,47 +1,46 @@
-"""Learned selector over the normal-equation variants (host-side driver).
+"""Learned selector over the normal-equation variants: training-set generation, training and marshalling.
 
-For each instance the selector reads 16 features from the instance's cheap
-BF16X3 normal-equation matrix (oqr_features), runs the MLP 16 -> 64 -> 64 -> 4
-(oqr_mlp_forward, BF16 inference) and picks one option, cheapest first:
+The selector itself runs inside the C library (``oqr_batched`` in ``OQR_BATCHED_SELECTOR`` mode): every
+instance of a batch first runs one FP64-accurate pass on the tensor cores; 16 features of that pass's
+Gram G0 and Cholesky factor R1 go through the MLP 16 -> 64 -> 64 -> 4 (BF16 inference), whose argmax says
+how the instance finishes:
 
-  0  one FP64-accurate pass          (A-CholQR, tensor cores)
-  1  TC2 pass + FP64-accurate pass    (mixed A-CholQR2, one split of A for both)
-  2  shifted A-CholQR3, all three passes FP64-accurate on the tensor cores
-  3  FP64 A-CholQR2 (DFMA)           -- also the fallback
+  0  one pass         Q = Z R1^{-1}                        (its result is checked)
+  1  two passes       one more FP64-accurate pass          (A-CholQR2)
+  2  shifted          chol(G0 + s I), then two more passes (shifted A-CholQR3)
+  3  FP64 A-CholQR2   (DFMA)                               -- also the end of the fallback chain
 
-A choice of option 0 or 1 is checked (||Q^T A Q - I||_2 <= tol, measured on
-the FP64-accurate tensor-core Gram); if the check fails or a Cholesky breaks
-down, the instance is refactored with option 3, and if that does not meet tol
-either (an unshifted normal-equation method needs kappa(A^{1/2} Z)^2 u < 1),
-with the shifted FP64 A-CholQR3 and then option 2, keeping the most
-orthogonal result.  A choice of option 2 or 3 is the network's answer for an
-ill-conditioned instance and is accepted once it completes.  Training labels are the cheapest option
-whose measured orthogonality meets tol on method-generated instances; the
-network is trained on the GPU by the library's own kernels (oqr_mlp_grad,
-oqr_mlp_adam).  Every arithmetic step runs in the CUDA library.
+A failed check or a breakdown goes to shifted A-CholQR3 on the tensor cores, then to FP64 A-CholQR2.
+
+This module makes the network's training data and trains it, with the library's own kernels: the
+features come from ``oqr_batched_features`` (the same first pass), and the label of an instance is the
+cheapest option whose measured ||Q^T A Q - I||_2 meets the tolerance, measured by running the three
+tensor-core programs on the batch (``oqr_batched_mixed`` with its check).  Those programs produce exactly
+the selector's options: the same first pass, then the same later passes.  Training is Adam on the mean
+cross-entropy (``oqr_mlp_grad``, ``oqr_mlp_adam``).  Nothing here computes a factorization.
 """
 from __future__ import annotations
 
 import json
 import math
-import time
+import os
 
 import numpy as np
 
-OPTIONS = [
-    ("oqr_cholqr", {"final_prec": 3}),
-    ("oqr_cholqr2", {"prec": 4, "final_prec": 3}),
-    ("oqr_cholqr2", {"shifted": 1, "prec": 3, "prec_mid": 3, "final_prec": 3}),
-    ("oqr_cholqr2", {}),
-    ("oqr_cholqr2", {"shifted": 1}),   # last resort, not a class of the network
-]
-FALLBACK = 3
-LAST_RESORT = 4
 CLASSES = 4
+ONE, TWO, SHIFTED, FP64 = 0, 1, 2, 3
+# the tensor-core program of each option (oqr_batch_program), for labelling
+PROGRAMS = {ONE: 0, TWO: 2, SHIFTED: 3}          # OQR_BATCH_CHOLQR_TC, _CHOLQR2_TC, _SCHOLQR3_TC
+WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "selector_weights.json")
+
+# the selector's workload: kappa(A) log-uniform to 1e6, kappa(Z) log-uniform to 1e12 (random U), so that
+# kappa(A^{1/2} Z) spreads over 1e0 .. 1e12
+KAPPA_A = (0.0, 6.0)
+KAPPA_Z = (0.0, 12.0)
 
 
 def init_params(seed: int = 0):
-    """He-initialised flat parameters (numpy float32)."""
+    """He-initialised flat parameters (numpy float32), layout W1[64][16] b1[64] W2[64][64] b2[64] W3[4][64] b3[4]."""
     rng = np.random.default_rng(seed)
     parts = []
     for fan_in, fan_out in ((16, 64), (64, 64), (64, 4)):
@@ -50,61 +49,52 @@ def init_params(seed: int = 0):
     return np.concatenate([p.ravel() for p in parts]).astype(np.float32)
 
 
-def run_option(ctx, k, A, Z, Q=None, R=None, check=True):
-    """Option k with the orthogonality check on the FP64-accurate tensor-core Gram."""
-    name, kw = OPTIONS[k]
-    Q, R, (st, info) = ctx._qr(name, A, Z, Q=Q, R=R, raise_on_error=False, check=2 if check else 0, **kw)
-    return Q, R, st, (info.orth_err if st == 0 else float("inf"))
-
-
-def label_instance(ctx, A, Z, tol=1e-12):
-    """The cheapest option meeting tol; if none does, the most orthogonal option that
-    completes (the shifted mixed A-CholQR3 when every option breaks down).  Also
-    returns the orthogonality each option reached (inf for a breakdown)."""
-    orth = []
-    for k in range(CLASSES):
-        _, _, st, o = run_option(ctx, k, A, Z)
-        orth.append(o)
-    for k, o in enumerate(orth):
-        if o <= tol:
-            return k, orth
-    if np.all(np.isinf(orth)):
-        return 2, orth
-    return int(np.argmin(orth)), orth
-
-
-def instances(count, seed, device="cuda", m_range=(64, 512), n_range=(4, 32), log_kappa_a=(0.0, 6.0),
-              log_kappa_z=(0.0, 12.0)):
-    """Yields (A, Z) of the selector's workload one at a time (kappa(A^{1/2} Z) log-uniform
-    up to ~1e12 through kappa(Z) with a random U), so that large sets need not be resident."""
+def batch(count, seed, device="cuda", m_range=(64, 1024), n_range=(4, 64), log_kappa_a=KAPPA_A,
+          log_kappa_z=KAPPA_Z):
+    """A batch of the selector's workload (inputs.batch_instances with its kappa laws)."""
     from . import inputs
-    m, n, ka, kz, seeds = inputs.batch_shapes(count, seed, m_range, n_range, log_kappa_a, log_kappa_z)
-    for b in range(count):
-        A, _ = inputs.dense_spd(int(m[b]), float(ka[b]), seed=int(seeds[b]), device=device)
-        Z = inputs.tall_z(int(m[b]), int(n[b]), float(kz[b]), seed=int(seeds[b]) + 1, device=device)
-        yield A.t(), Z.t().contiguous().t()
+    return inputs.batch_instances(count, seed, device=device, m_range=m_range, n_range=n_range,
+                                  log_kappa_a=log_kappa_a, log_kappa_z=log_kappa_z)
 
 
-def make_set(ctx, count, seed, device="cuda", tol=1e-12, keep=False, **kw):
-    """Method-generated instances with features and labels (torch tensors on device)."""
+def option_orth(ctx, As, Zs):
+    """||Q^T A Q - I||_2 of options 0-2 on every instance (inf after a breakdown): (count, 3) numpy array."""
+    out = np.zeros((len(Zs), 3))
+    for k in (ONE, TWO, SHIFTED):
+        _, _, st, orth = ctx.oqr_batched_mixed(As, Zs, program=[PROGRAMS[k]] * len(Zs), check=True)
+        o = orth.cpu().numpy()
+        o[st.cpu().numpy() != 0] = np.inf
+        out[:, k] = o
+    return out
+
+
+def labels_from(orth, tol=1e-12):
+    """The cheapest option meeting tol; where none does, the shifted option (the most robust one)."""
+    y = np.full(len(orth), SHIFTED, dtype=np.int32)
+    for b in range(len(orth)):
+        for k in (ONE, TWO, SHIFTED):
+            if orth[b, k] <= tol:
+                y[b] = k
+                break
+    return y
+
+
+def make_set(ctx, count, seed, batch_size=1024, tol=1e-12, **kw):
+    """Method-generated training data: features and labels of `count` instances, made batch by batch."""
     import torch
-    X = torch.empty((count, 16), dtype=torch.float32, device=device)
-    y = torch.empty(count, dtype=torch.int32, device=device)
-    orth = np.zeros((count, CLASSES))
-    As, Zs = [], []
-    for b, (A, Z) in enumerate(instances(count, seed, device, **kw)):
-        ctx.oqr_features(A, Z, out=X[b])
-        lab, o = label_instance(ctx, A, Z, tol)
-        y[b] = lab
-        orth[b] = o
-        if keep:
-            As.append(A)
-            Zs.append(Z)
-    torch.cuda.synchronize()
-    return {"As": As, "Zs": Zs, "X": X, "y": y, "orth": orth}
+    X, y, orths = [], [], []
+    for i, s in enumerate(range(0, count, batch_size)):
+        As, Zs, _ = batch(min(batch_size, count - s), seed * 100003 + i, **kw)
+        X.append(ctx.oqr_batched_features(As, Zs))
+        o = option_orth(ctx, As, Zs)
+        orths.append(o)
+        y.append(torch.as_tensor(labels_from(o, tol), device=X[-1].device))
+        del As, Zs
+        torch.cuda.empty_cache()
+    return {"X": torch.cat(X), "y": torch.cat(y), "orth": np.concatenate(orths)}
 
 
-def train(ctx, X, y, epochs=400, lr=3e-3, batch=256, seed=0, params=None):
+def train(ctx, X, y, epochs=60, lr=3e-3, batch=512, seed=0, params=None):
     """Adam on the mean cross-entropy, all arithmetic in the library's kernels."""
     import torch
     dev = X.device
@@ -114,14 +104,16 @@ def train(ctx, X, y, epochs=400, lr=3e-3, batch=256, seed=0, params=None):
     n = X.shape[0]
     g = torch.Generator().manual_seed(seed)
     losses, t = [], 0
-    for ep in range(epochs):
+    for _ in range(epochs):
         perm = torch.randperm(n, generator=g).to(dev)
+        acc = 0.0
         for i in range(0, n, batch):
             idx = perm[i:i + batch]
             grad, loss = ctx.oqr_mlp_grad(X[idx].contiguous(), y[idx].contiguous(), P)
             t += 1
             ctx.oqr_mlp_adam(P, grad, m, v, lr, t)
-        losses.append(float(loss.item()))
+            acc += float(loss.item()) * len(idx)
+        losses.append(acc / n)
     return P, losses
 
 
@@ -131,106 +123,27 @@ def choose(ctx, X, P):
     return choice
 
 
-def solve(ctx, A, Z, P, tol=1e-12):
-    """Selected factorization with check and fallback; returns (Q, R, info)."""
+def solve_batch(ctx, As, Zs, P, tol=1e-12, check_all=False, stream=None):
+    """The selector over a batch through the C ABI (oqr_batched, OQR_BATCHED_SELECTOR); returns
+    (Qs, Rs, status, orth, choice) with orth NaN where the instance was not checked."""
     import torch
-    f = ctx.oqr_features(A, Z).reshape(1, 16)
-    k = int(choose(ctx, f, P)[0].item())
-    # options 0 and 1 are only right for well-conditioned instances: their result is checked;
-    # options 2 and 3 are the network's answer for hard instances and are accepted once they complete
-    risky = k in (0, 1)
-    Q, R, st, o = run_option(ctx, k, A, Z, check=risky)
-    ok = st == 0 and (o <= tol or not risky)
-    fell = not ok
-    used = k
-    # fallback chain: FP64 A-CholQR2, then the shifted methods, keeping the most orthogonal result
-    for fb in (FALLBACK, LAST_RESORT, 2):
-        if ok:
-            break
-        if fb == k:
-            continue
-        Q2, R2, st2, o2 = run_option(ctx, fb, A, Z)
-        if st2 == 0 and (st != 0 or o2 < o):
-            Q, R, st, o, used = Q2, R2, st2, o2, fb
-        ok = st == 0 and o <= tol
-    return Q, R, {"choice": k, "fallback": fell, "used": used, "orth": o, "status": st}
 
-
-# options -> programs of the batched tensor-core path (option 3, FP64 A-CholQR2, is oqr_batched mode 0)
-BATCH_PROGRAMS = {0: 0, 1: 1, 2: 3}   # OQR_BATCH_CHOLQR_TC, OQR_BATCH_CHOLQR2_TC2, OQR_BATCH_SCHOLQR3_TC
-
-
-def solve_batch(ctx, As, Zs, P, tol=1e-12, stream=None):
-    """The selector over a batch.  Per-instance features (oqr_features), one MLP forward over the batch,
-    then the chosen tensor-core programs in one checked oqr_batched_mixed call and the FP64 A-CholQR2
-    choices in one oqr_batched call.  Options 0 and 1 are accepted when their check meets tol, option 2
-    and 3 once they complete (the network's answer for hard instances).  Every other instance goes down
-    the fallback chain in batches: shifted A-CholQR3 on the tensor cores (checked), then FP64 A-CholQR2,
-    keeping the most orthogonal completed result.  Returns (Qs, Rs, info) with per-instance lists
-    choice, used, orth (nan where the result was not checked) and status."""
-    import torch
     from . import oqr as _oqr
-    B = len(Zs)
     dev = Zs[0].device
-    X = torch.empty((B, 16), dtype=torch.float32, device=dev)
-    for b in range(B):
-        ctx.oqr_features(As[b], Zs[b], out=X[b], stream=stream)
-    choice = [int(c) for c in choose(ctx, X, P).cpu().tolist()]
-    Qs = [_oqr.empty_colmajor(z.shape[0], z.shape[1], dev) for z in Zs]
-    Rs = [_oqr.empty_colmajor(z.shape[1], z.shape[1], dev) for z in Zs]
-    used = [None] * B
-    orth = [float("inf")] * B
-    status = [1] * B
-    accepted = [False] * B
-
-    def run_tc(idx, programs):
-        Qt = [_oqr.empty_colmajor(Zs[b].shape[0], Zs[b].shape[1], dev) for b in idx]
-        Rt = [_oqr.empty_colmajor(Zs[b].shape[1], Zs[b].shape[1], dev) for b in idx]
-        _, _, st, o = ctx.oqr_batched_mixed([As[b] for b in idx], [Zs[b] for b in idx], program=programs,
-                                            Qs=Qt, Rs=Rt, stream=stream, check=True)
-        return Qt, Rt, st.cpu().tolist(), o.cpu().tolist()
-
-    def run_fp64(idx):
-        Qt = [_oqr.empty_colmajor(Zs[b].shape[0], Zs[b].shape[1], dev) for b in idx]
-        Rt = [_oqr.empty_colmajor(Zs[b].shape[1], Zs[b].shape[1], dev) for b in idx]
-        _, _, st = ctx.oqr_batched([As[b] for b in idx], [Zs[b] for b in idx], Qs=Qt, Rs=Rt, stream=stream)
-        return Qt, Rt, st.cpu().tolist(), [float("nan")] * len(idx)
-
-    def take(idx, res, options):
-        """Keeps each completed result that is the instance's first or more orthogonal than its last."""
-        Qt, Rt, st, o = res
-        for k, b in enumerate(idx):
-            if st[k] != 0:
-                continue
-            if status[b] != 0 or o[k] < orth[b]:
-                Qs[b].copy_(Qt[k])
-                Rs[b].copy_(Rt[k])
-                status[b], orth[b], used[b] = 0, o[k], options[k]
-            if options[k] in (2, 3) or o[k] <= tol:
-                accepted[b] = True
-
-    tc = [b for b in range(B) if choice[b] != 3]
-    if tc:
-        take(tc, run_tc(tc, [BATCH_PROGRAMS[choice[b]] for b in tc]), [choice[b] for b in tc])
-    fp = [b for b in range(B) if choice[b] == 3]
-    if fp:
-        take(fp, run_fp64(fp), [3] * len(fp))
-    rest = [b for b in range(B) if not accepted[b]]
-    if rest:
-        take(rest, run_tc(rest, [BATCH_PROGRAMS[2]] * len(rest)), [2] * len(rest))
-    rest = [b for b in range(B) if status[b] != 0]
-    if rest:
-        take(rest, run_fp64(rest), [3] * len(rest))
-    return Qs, Rs, {"choice": choice, "used": used, "orth": orth, "status": status}
+    orth = torch.empty(len(Zs), dtype=torch.float64, device=dev)
+    choice = torch.empty(len(Zs), dtype=torch.int32, device=dev)
+    Qs, Rs, st = ctx.oqr_batched(As, Zs, mode=_oqr.OQR_BATCHED_SELECTOR, params=P, tol=tol, check_all=check_all,
+                                 orth=orth, choice=choice, stream=stream)
+    return Qs, Rs, st, orth, choice
 
 
-def save(P, path):
+def save(P, path=WEIGHTS, meta=None):
     with open(path, "w") as f:
-        json.dump({"layout": "W1[64][16] b1[64] W2[64][64] b2[64] W3[4][64] b3[4]",
+        json.dump({"layout": "W1[64][16] b1[64] W2[64][64] b2[64] W3[4][64] b3[4]", "meta": meta or {},
                    "params": [float(x) for x in P.detach().cpu().numpy()]}, f)
 
 
-def load(path, device="cuda"):
+def load(path=WEIGHTS, device="cuda"):
     import torch
     with open(path) as f:
         return torch.tensor(json.load(f)["params"], dtype=torch.float32, device=device)

@@ -317,25 +317,6 @@ def test_batched_check_estimates_orthogonality(env):
             assert ref > 10 * slack and 0.9 * ref <= orth[b] <= 1.05 * ref
 
 
-def test_selector_solve_batch_completes(env):
-    """The batched selector with an untrained network (arbitrary choices): checks and the fallback chain
-    give every instance the attainable orthogonality (kappa(A^{1/2} Z) up to ~1e12)."""
-    torch, oqr, ctx = env
-    from paper_1401_5171_gb300 import selector
-    P = torch.as_tensor(selector.init_params(3), device="cuda")
-    As, Zs, _ = inputs.batch_instances(16, seed=51, device="cuda", m_range=(64, 600), n_range=(4, 40),
-                                       log_kappa_a=(0.0, 4.0), log_kappa_z=(0.0, 8.0))
-    Qs, Rs, info = selector.solve_batch(ctx, As, Zs, P)
-    torch.cuda.synchronize()
-    for b in range(len(Zs)):
-        A, Z, Q, R = (x.cpu().numpy() for x in (As[b], Zs[b], Qs[b], Rs[b]))
-        assert info["status"][b] == 0
-        Qr, _ = oracle.oblique_qr(A, Z)
-        floor = 100 * U * np.linalg.eigvalsh(A).max() * np.linalg.norm(Qr, 2) ** 2
-        assert oracle.orth_error(A, Q) <= max(1e-12, 10 * oracle.orth_error(A, Qr), floor)
-        assert np.linalg.norm(Z - Q @ R, 2) / np.linalg.norm(Z, 2) <= 1e-13
-
-
 def test_batched_check_graph_replay_new_outputs(env):
     """A replay of the cached graph writes this call's status and orth arrays, not the first call's."""
     torch, oqr, ctx = env

@@ -2,22 +2,26 @@
 
 The network's forward and backward kernels are checked against the CPU
 restatement in oracle/mlp.py (itself pinned by finite differences); the
-feature kernel against its definition evaluated on the oracle's FP64 Gram; the
-mixed shifted A-CholQR3 option against the CHOL-EQR oracle.  The last test
-trains the network with the library's kernels on method-generated instances
-and measures what it gains over always running the safe mixed option, with
-every result meeting ||Q^T A Q - I||_2 <= 1e-12 after the FP64 fallback.
+feature kernels against their definitions evaluated on the oracle's FP64 Gram;
+the shifted A-CholQR3 option against the CHOL-EQR oracle; the selector mode of
+oqr_batched (through the C ABI) against the oracle and the attainable
+orthogonality.  The last test trains the network with the library's kernels on
+method-generated instances and measures what it gains over the fixed policies
+that meet the bar on every instance.
 """
+import os
 import time
 
 import numpy as np
 import pytest
 
 import oracle
+import selector_defs
 from oracle import mlp
 from paper_1401_5171_gb300 import inputs, selector
 
 pytestmark = pytest.mark.gpu
+U = 2.0 ** -53
 
 
 @pytest.fixture(scope="module")
@@ -112,7 +116,7 @@ def test_mixed_shifted_cholqr3_option(env):
     A, Z = inputs.paper_case(4, 600, 20, 1e4, 1e9, seed=21)
     Qr, Rr = oracle.oblique_qr(A, Z)
     Ad, Zd = (oqr.colmajor(torch.as_tensor(x).cuda()) for x in (A, Z))
-    Q, R, st, orth = selector.run_option(ctx, 2, Ad, Zd)
+    Q, R, (st, _) = ctx.oqr_cholqr2(Ad, Zd, shifted=1, prec=3, prec_mid=3, final_prec=3)
     assert st == 0
     # and the BF16X3-first shifted variant (trace-based shift) on the same instance
     Qb, Rb, (stb, infob) = ctx.oqr_cholqr2(Ad, Zd, shifted=1, prec=1, prec_mid=3, final_prec=3, check=2)
@@ -123,52 +127,114 @@ def test_mixed_shifted_cholqr3_option(env):
     assert np.linalg.norm(R - Rr) / np.linalg.norm(Rr) <= 1e-6
 
 
-def test_selector_trains_and_gains(env):
-    """Train on small and mid-size instances; evaluate on large ones, where the
-    options' costs differ: time of selected-option + check + fallback against
-    always running the plain FP64 A-CholQR2 (the method without the network)
-    and against always running the safe shifted mixed A-CholQR3."""
+def _instances_host(As, Zs, idx):
+    return [(As[b].cpu().numpy(), Zs[b].cpu().numpy()) for b in idx]
+
+
+def test_batched_features_match_definition(env):
+    """oqr_batched_features against the CPU definition (tests/selector_defs.py) evaluated on the oracle's
+    FP64 Gram and Cholesky factor: instances that complete the first pass and instances that break down."""
     torch, oqr, ctx = env
-    tr1 = selector.make_set(ctx, 700, seed=100, m_range=(64, 1024), n_range=(4, 64))
-    tr2 = selector.make_set(ctx, 160, seed=101, m_range=(2048, 6144), n_range=(8, 64))
-    X = torch.cat([tr1["X"], tr2["X"]])
-    y = torch.cat([tr1["y"], tr2["y"]])
-    P, losses = selector.train(ctx, X, y, epochs=150)
-    assert losses[-1] < 0.6 * losses[0]
-    count = 48
-    feats, labels = [], []
-    t_sel = t_safe = t_fp64 = 0.0
-    fallbacks = 0
-    for A, Z in selector.instances(count, seed=200, m_range=(8192, 12288), n_range=(16, 64)):
-        lab, orth = selector.label_instance(ctx, A, Z)
-        labels.append(lab)
+    As, Zs, tab = inputs.batch_instances(24, seed=31, device="cuda", m_range=(64, 900), n_range=(1, 64),
+                                         log_kappa_a=(0.0, 6.0), log_kappa_z=(0.0, 12.0))
+    F = ctx.oqr_batched_features(As, Zs).cpu().numpy()
+    for b, (A, Z) in enumerate(_instances_host(As, Zs, range(24))):
+        m, n = Z.shape
+        G0 = oracle.gram(A, Z)
+        G0 = 0.5 * (G0 + G0.T)
+        try:
+            R1 = oracle.chol_upper(G0)
+            col = 0
+        except oracle.OracleBreakdown as e:
+            R1, col = None, e.column
+        ref = selector_defs.features(m, n, G0, R1, col)
+        if (F[b, 10] == 1.0) != (R1 is None):
+            continue          # at the breakdown threshold the two Grams' roundings may decide differently
+        assert np.allclose(F[b, [0, 1, 2, 9, 10]], ref[[0, 1, 2, 9, 10]], atol=1e-5), b
+        assert np.allclose(F[b, [3, 4]], ref[[3, 4]], atol=1e-4), b
+        if R1 is not None:
+            assert abs(F[b, 12] - ref[12]) <= 1e-3, (b, F[b, 12], ref[12])
+            if ref[5] == 0.0:
+                assert abs(F[b, 7] - ref[7]) <= 2e-3 and abs(F[b, 8] - ref[8]) <= 2e-3, b
+        else:
+            assert abs(F[b, 11] - col / n) <= 1.5 / n, b
+
+
+def _bar(torch, As, Zs, Qs, st, tab):
+    """Per instance: ||Q^T A Q - I||_2 (torch, FP64) and the bar max(1e-12, m u ||A||_2 ||Q||_2^2) (Thm 4.1's
+    attainable level with c = 1; ||A||_2 = kappa(A), the smallest eigenvalue being 1)."""
+    orth, bar = np.full(len(Zs), np.inf), np.zeros(len(Zs))
+    for b in range(len(Zs)):
+        m, n = Zs[b].shape
+        qn = torch.linalg.matrix_norm(Qs[b], 2).item() if st[b] == 0 else 1.0
+        bar[b] = max(1e-12, m * U * float(tab["kappa_A"][b]) * qn * qn)
+        if st[b] == 0:
+            E = Qs[b].T @ (As[b] @ Qs[b]) - torch.eye(n, dtype=torch.float64, device="cuda")
+            orth[b] = torch.linalg.eigvalsh(0.5 * (E + E.T)).abs().max().item()
+    return orth, bar
+
+
+def test_selector_mode_through_the_c_abi(env):
+    """OQR_BATCHED_SELECTOR with an untrained network (its choices are arbitrary): the checks and the
+    fallback chain still give every instance a result at the bar, and R matches the oracle's."""
+    torch, oqr, ctx = env
+    As, Zs, tab = inputs.batch_instances(40, seed=41, device="cuda", m_range=(64, 700), n_range=(4, 64),
+                                         log_kappa_a=(0.0, 6.0), log_kappa_z=(0.0, 10.0))
+    P = torch.as_tensor(selector.init_params(3), device="cuda")
+    Qs, Rs, st, orth, choice = selector.solve_batch(ctx, As, Zs, P)
+    st = st.cpu().numpy()
+    ch = choice.cpu().numpy()
+    assert set(ch.tolist()) <= {0, 1, 2, 3}
+    o, bar = _bar(torch, As, Zs, Qs, st, tab)
+    for b in range(40):
+        assert st[b] == 0, (b, st[b])
+        assert o[b] <= bar[b], (b, ch[b], o[b], bar[b])
+    for b in range(0, 40, 8):       # a sample against the oracle
+        A, Z = As[b].cpu().numpy(), Zs[b].cpu().numpy()
+        Qr, Rr = oracle.oblique_qr(A, Z)
+        assert np.linalg.norm(Rs[b].cpu().numpy() - Rr) / np.linalg.norm(Rr) <= max(1e-12, 100 * U * np.linalg.cond(Rr))
+
+
+def test_selector_trains_and_beats_fixed_policies(env):
+    """Train on method-generated instances (m <= 1024) with the library's kernels; then, on the selector's
+    workload at the batched sizes (m up to 4096, kappa(A^{1/2} Z) to ~1e12), the selector through the C ABI
+    against the fixed policies that meet the bar everywhere: always shifted A-CholQR3 on the tensor cores,
+    and always A-CholQR2 on the tensor cores with the same check and fallback.  Every result of the selector
+    must meet the bar; it must be faster than both."""
+    torch, oqr, ctx = env
+    tr = selector.make_set(ctx, 8192, seed=5, batch_size=2048)
+    P, losses = selector.train(ctx, tr["X"], tr["y"], epochs=40)
+    assert losses[-1] < 0.7 * losses[0]
+    ho = selector.make_set(ctx, 512, seed=6, batch_size=512, m_range=(64, 4096))
+    acc = float(np.mean(selector.choose(ctx, ho["X"], P).cpu().numpy() == ho["y"].cpu().numpy()))
+    assert acc >= 0.7, acc
+    if os.path.exists(selector.WEIGHTS):
+        P = selector.load()                 # the committed network, trained on 1e5 instances
+    As, Zs, tab = selector.batch(1024, seed=77, m_range=(64, 4096))
+
+    def timed(fn):
+        fn()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        Q, R, info = selector.solve(ctx, A, Z, P)
+        out = fn()
         torch.cuda.synchronize()
-        t_sel += time.perf_counter() - t0
-        fallbacks += info["fallback"]
-        feats.append(info["choice"])
-        best = np.min(orth)
-        if np.isfinite(best):                     # some option completes: so must the chain
-            assert info["status"] == 0
-            if info["used"] in (0, 1) or best <= 1e-12:
-                assert info["orth"] <= max(1e-12, 10 * best)
-        for k, acc in ((2, "safe"), (3, "fp64")):
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            selector.run_option(ctx, k, A, Z, check=False)
-            torch.cuda.synchronize()
-            dt = time.perf_counter() - t0
-            if acc == "safe":
-                t_safe += dt
-            else:
-                t_fp64 += dt
-        del A, Z, Q, R
-    acc = float(np.mean(np.array(feats) == np.array(labels)))
-    print(f"\nselector: train label mix {np.bincount(y.cpu().numpy(), minlength=4)}, held-out (m 8192-12288) "
-          f"accuracy {acc:.3f}, fallbacks {fallbacks}/{count}; time features+choice+selected+check "
-          f"{t_sel:.3f}s vs always FP64 A-CholQR2 {t_fp64:.3f}s ({t_fp64 / t_sel:.2f}x) vs always shifted "
-          f"mixed A-CholQR3 {t_safe:.3f}s ({t_safe / t_sel:.2f}x); the baselines run without a check")
-    assert acc >= 0.6
-    assert t_sel < t_fp64
+        return time.perf_counter() - t0, out
+
+    t_sel, (Qs, Rs, st, orth, choice) = timed(lambda: selector.solve_batch(ctx, As, Zs, P))
+    st = st.cpu().numpy()
+    o, bar = _bar(torch, As, Zs, Qs, st, tab)
+    bad = [b for b in range(len(Zs)) if not (o[b] <= bar[b])]
+    assert not bad, [(b, o[b], bar[b], int(choice[b])) for b in bad[:5]]
+    t_shift, _ = timed(lambda: ctx.oqr_batched(As, Zs, mode=oqr.OQR_BATCHED_SHIFTED_TC))
+    # always A-CholQR2 (tensor cores): every result checked, failures to shifted A-CholQR3
+    def cholqr2_checked():
+        _, _, st2, o2 = ctx.oqr_batched_mixed(As, Zs, program=[2] * len(Zs), check=True)
+        fail = [b for b in range(len(Zs)) if st2[b].item() != 0 or not (o2[b].item() <= 1e-12)]
+        if fail:
+            ctx.oqr_batched_mixed([As[b] for b in fail], [Zs[b] for b in fail], program=[3] * len(fail), check=True)
+    t_c2, _ = timed(cholqr2_checked)
+    mix = np.bincount(choice.cpu().numpy(), minlength=4).tolist()
+    print(f"\nselector: trained loss {losses[0]:.3f} -> {losses[-1]:.3f}, held-out accuracy {acc:.3f}; on 1024 "
+          f"instances: selector {t_sel:.3f}s (options used {mix}), always shifted A-CholQR3 {t_shift:.3f}s "
+          f"({t_shift / t_sel:.2f}x), always A-CholQR2 + check + fallback {t_c2:.3f}s ({t_c2 / t_sel:.2f}x)")
+    assert t_sel < t_shift and t_sel < t_c2
