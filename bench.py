@@ -75,6 +75,8 @@ def parse():
                    help="skip the CPU A-CholQR2 timed on the full instance (tens of seconds)")
     p.add_argument("--batch-count", type=int, default=512,
                    help="side measurement: a batch of this many instances of the batched workload (0: none)")
+    p.add_argument("--selector-count", type=int, default=512,
+                   help="side measurement: the learned selector on this many instances of its workload (0: none)")
     p.add_argument("--batch-profile", type=int, default=None, choices=[0, 1, 2, 3],
                    help="only: one oqr_batched call of this mode on the batch sample, inside a profiler range "
                         "(for ncu --profile-from-start off)")
@@ -366,6 +368,138 @@ def run_batch(ctx, torch, dev, count, stream, steps=2):
     return out
 
 
+def events_ms(torch, stream, fn, reps=1):
+    """CUDA-event milliseconds of fn() on stream (after one warm call), averaged over reps."""
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def run_selector(ctx, torch, dev, count, stream):
+    """The learned selector (oqr_batched, OQR_BATCHED_SELECTOR, the committed network) on a sample of its
+    workload (m ~ U[64, 4096], n ~ U[4, 64], kappa(A) log-uniform to 1e6, kappa(Z) log-uniform to 1e12),
+    against the fixed policies that reach the bar on every instance: always shifted A-CholQR3 on the tensor
+    cores, and always A-CholQR2 on the tensor cores with the same check and fallback.  The per-instance
+    orthogonality of the selector's results is measured after the timing."""
+    import numpy as np
+
+    from paper_1401_5171_gb300 import oqr, selector
+    if not os.path.exists(selector.WEIGHTS):
+        return None
+    P = selector.load(device=dev)
+    As, Zs, tab = selector.batch(count, seed=4343, device=dev, m_range=(64, 4096))
+    out = {"instances": count, "recipe": "m ~ U[64, 4096], n ~ U[4, 64], kappa(A) log-uniform in [1, 1e6], "
+                                         "kappa(Z) log-uniform in [1, 1e12], seed 4343"}
+    res = {}
+
+    def sel():
+        res["r"] = selector.solve_batch(ctx, As, Zs, P, stream=stream)
+
+    t_sel = events_ms(torch, stream, sel)
+    Qs, Rs, st, orth, choice = res["r"]
+    stc = st.cpu().numpy()
+    worst, above = 0.0, 0
+    for b in range(count):
+        n = Zs[b].shape[1]
+        if stc[b] != 0:
+            above += 1
+            continue
+        E = Qs[b].T @ (As[b] @ Qs[b]) - torch.eye(n, dtype=torch.float64, device=dev)
+        o = torch.linalg.eigvalsh(0.5 * (E + E.T)).abs().max().item()
+        qn = torch.linalg.matrix_norm(Qs[b], 2).item()
+        bar = max(1e-12, Zs[b].shape[0] * 2.0 ** -53 * float(tab["kappa_A"][b]) * qn * qn)
+        worst = max(worst, o / bar)
+        above += o > bar
+    t_shift = events_ms(torch, stream, lambda: ctx.oqr_batched(As, Zs, mode=oqr.OQR_BATCHED_SHIFTED_TC,
+                                                                  stream=stream))
+
+    def cholqr2_checked():
+        _, _, st2, o2 = ctx.oqr_batched_mixed(As, Zs, program=[2] * count, check=True, stream=stream)
+        s2, oo = st2.cpu().numpy(), o2.cpu().numpy()
+        fail = [b for b in range(count) if s2[b] != 0 or not (oo[b] <= 1e-12)]
+        if fail:
+            ctx.oqr_batched_mixed([As[b] for b in fail], [Zs[b] for b in fail], program=[3] * len(fail),
+                                  check=True, stream=stream)
+
+    t_c2 = events_ms(torch, stream, cholqr2_checked)
+    out.update({"qr_per_s": count / (t_sel / 1e3), "ms_per_batch": t_sel,
+                "options_used": np.bincount(choice.cpu().numpy(), minlength=4).tolist(),
+                "instances_above_bar": int(above), "worst_orth_over_bar": worst,
+                "bar": "max(1e-12, m u ||A||_2 ||Q||_2^2) per instance (Thm 4.1 with c = 1)",
+                "always_shifted_tc": {"qr_per_s": count / (t_shift / 1e3), "ms_per_batch": t_shift},
+                "always_cholqr2_tc_checked": {"qr_per_s": count / (t_c2 / 1e3), "ms_per_batch": t_c2},
+                "gain_over_best_fixed": min(t_shift, t_c2) / t_sel})
+    del As, Zs, Qs, Rs
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_next_paths(ctx, torch, dev, A, Z, stream, m, n, peaks):
+    """Side measurements of the paths beyond the headline: PRE-CHOLQR (Algorithm 2) and A-CholQR2 reusing
+    W = A Z (FP64) on the benchmark's instance, the generalized least-squares solve (Sec. 1) with the HBM
+    roofline of its symmetric product, and Sec. 8's tridiagonal workload at m = 100000."""
+    from paper_1401_5171_gb300 import inputs, oqr
+    out = {}
+    Q = oqr.empty_colmajor(m, n, dev)
+    R = oqr.empty_colmajor(n, n, dev)
+    for label, name, kw in (("precholqr_fp64tc", "oqr_precholqr", {"final_prec": 3}),
+                            ("cholqr2_reuse_w_fp64", "oqr_cholqr2", {"reuse_w": 1})):
+        opts = oqr.make_opts(**kw)
+        _, _, (st, info) = ctx._qr(name, A, Z, Q=Q, R=R, opts=oqr.make_opts(check=1, **kw), stream=stream)
+        ms = events_ms(torch, stream, lambda: ctx._qr(name, A, Z, Q=Q, R=R, opts=opts, stream=stream, sync=False))
+        out[label] = {"qr_per_s": 1e3 / ms, "ms_per_qr": ms, "orth_err": info.orth_err, "status": st}
+    # GLLS x = R^{-1} Q^T A b for one right-hand side, with (Q, R) from the mixed A-CholQR2
+    ctx._qr("oqr_cholqr2", A, Z, Q=Q, R=R, opts=oqr.make_opts(prec=4, final_prec=3), stream=stream)
+    b = oqr.colmajor(torch.randn((m, 1), dtype=torch.float64, device=dev))
+    C = oqr.empty_colmajor(m, 1, dev)
+    ms_glls = events_ms(torch, stream, lambda: ctx.oqr_glls(A, Q, R, b, stream=stream), reps=5)
+    ms_symm = events_ms(torch, stream, lambda: ctx.oqr_symm(A, b, C=C, stream=stream), reps=5)
+    bytes_symm = 8.0 * m * (m + 1) / 2 + 16.0 * m      # A's lower triangle once, b in, A b out
+    peak = float(peaks.get("hbm_gbs", 6781.4))
+    out["glls_k1"] = {"ms": ms_glls, "symm_ms": ms_symm,
+                      "symm_roofline": {"bound": "hbm", "achieved": bytes_symm / (ms_symm / 1e3) / 1e9,
+                                        "peak": peak, "unit": "GB/s",
+                                        "frac": bytes_symm / (ms_symm / 1e3) / 1e9 / peak,
+                                        "peak_source": "MEASURED_PEAKS.json hbm_gbs, of measured"}}
+    # tridiagonal A (Sec. 8): m = 100000, the paper's size
+    mt = 100000
+    d, e = inputs.tridiag_spd(mt, 1e4)
+    dd = torch.as_tensor(d, device=dev)
+    ed = torch.as_tensor(e, device=dev)
+    Zt = oqr.colmajor(inputs.tall_z(mt, n, 1e2, seed=11, device=dev))
+    Qt = oqr.empty_colmajor(mt, n, dev)
+    Rt = oqr.empty_colmajor(n, n, dev)
+    tri = {"m": mt, "n": n, "kappa_T": 1e4, "kappa_Z": 1e2,
+           "recipe": "T = tridiag(-1, 2 + mu, -1) with mu giving kappa(T) = 1e4; Z = U diag(sigma) W^T, Haar U"}
+    for label, kw in (("mixed", {"prec": 4, "final_prec": 3}), ("fp64", {}), ("precholqr_fp64tc", None)):
+        if kw is None:
+            fn = lambda: ctx.oqr_precholqr_tridiag(dd, ed, Zt, Q=Qt, R=Rt, stream=stream, sync=False,
+                                                   opts=oqr.make_opts(final_prec=3))
+            _, _, (st, info) = ctx.oqr_precholqr_tridiag(dd, ed, Zt, Q=Qt, R=Rt, stream=stream,
+                                                         opts=oqr.make_opts(final_prec=3, check=1))
+            passes = 1
+        else:
+            fn = lambda kw=kw: ctx.oqr_cholqr2_tridiag(dd, ed, Zt, Q=Qt, R=Rt, stream=stream, sync=False,
+                                                       opts=oqr.make_opts(**kw))
+            _, _, (st, info) = ctx.oqr_cholqr2_tridiag(dd, ed, Zt, Q=Qt, R=Rt, stream=stream,
+                                                       opts=oqr.make_opts(check=1, **kw))
+            passes = 2
+        ms = events_ms(torch, stream, fn, reps=3)
+        tri[label] = {"qr_per_s": 1e3 / ms, "ms_per_qr": ms, "orth_err": info.orth_err, "status": st,
+                      "tflops_normalised": passes * 2.0 * mt * n * n / (ms / 1e3) / 1e12,
+                      "normalisation": "2 m n^2 per CHOLQR pass (Sec. 8)"}
+    out["tridiagonal"] = tri
+    del Zt, Qt, Rt
+    torch.cuda.empty_cache()
+    return out
+
+
 def profile_batch(ctx, torch, dev, count, mode):
     """One oqr_batched call (after a warm-up call that captures its graph) inside cudaProfilerStart/Stop."""
     from paper_1401_5171_gb300 import inputs
@@ -456,6 +590,13 @@ def main():
 
     # side measurement: the batched workload (m ~ U[64, 4096], n ~ U[4, 64], kappa(A), kappa(Z) log-uniform
     # to 1e6), a sample of args.batch_count instances; every path factors the whole batch per step
+    nxt = sel = None
+    if world == 1 and not args.no_side_paths:
+        nxt = run_next_paths(ctx, torch, dev, A, Z, stream, m, n,
+                             json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+                             if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {})
+        if args.selector_count > 0:
+            sel = run_selector(ctx, torch, dev, args.selector_count, stream)
     batch = None
     if args.batch_count > 0 and world == 1:  # a single-GPU side measurement
         batch = run_batch(ctx, torch, dev, args.batch_count, stream)
@@ -554,6 +695,7 @@ def main():
             "tflops_normalised": head["tflops_normalised"], "orth_err": head["orth_err"],
             "repres_err": head["repres_err"],
             "meets_1e-12": bool(0 <= head["orth_err"] <= 1e-12), "paths": others, "batched": batch,
+            "selector": sel, "next_paths": nxt,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": lps * args.steps if lps is not None else None, "clocks": clocks}
     if rank == 0:
