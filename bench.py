@@ -20,6 +20,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import re
 import statistics
@@ -75,6 +76,12 @@ def parse():
                    help="skip the CPU A-CholQR2 timed on the full instance (tens of seconds)")
     p.add_argument("--batch-count", type=int, default=512,
                    help="side measurement: a batch of this many instances of the batched workload (0: none)")
+    p.add_argument("--sweep", action="store_true",
+                   help="only: config 1's kappa(Z) x n sweep at --m (JSON line per cell; not a bench line)")
+    p.add_argument("--sweep-n", default="64,128,256,512")
+    p.add_argument("--sweep-kappa-z", default="1e2,1e4,1e6,1e8")
+    p.add_argument("--precision-study", action="store_true",
+                   help="only: config 2's per-kappa precision study at --m, --n (JSON line per kappa)")
     p.add_argument("--selector-count", type=int, default=512,
                    help="side measurement: the learned selector on this many instances of its workload (0: none)")
     p.add_argument("--batch-profile", type=int, default=None, choices=[0, 1, 2, 3],
@@ -500,6 +507,83 @@ def run_next_paths(ctx, torch, dev, A, Z, stream, m, n, peaks):
     return out
 
 
+def run_sweep(ctx, torch, dev, m, ns, kappas, seed=301):
+    """Config 1's sweep at m (default 32768), kappa(A) = 1e6: for every n and kappa(Z), A-CholQR2 (FP64 and
+    mixed TC2 -> FP64_TC), shifted A-CholQR3 (FP64 and all FP64-accurate on the tensor cores) and block
+    A-CGS2, with ||Q^T A Q - I||_2 and ||Z - Q R||_2 / ||Z||_2 measured by torch's FP64 GEMMs and
+    eigensolver (Sec. 7's two measures), and the time of each.  One JSON line per cell."""
+    from paper_1401_5171_gb300 import inputs, oqr
+    Af, _ = inputs.dense_spd(m, 1e6, seed=seed, device=dev)
+    A = oqr.colmajor(Af)
+    stream = torch.cuda.current_stream(dev)
+    methods = (("cholqr2_fp64", "oqr_cholqr2", {}), ("cholqr2_mixed", "oqr_cholqr2", {"prec": 4, "final_prec": 3}),
+               ("scholqr3_fp64", "oqr_cholqr2", {"shifted": 1}),
+               ("scholqr3_fp64tc", "oqr_cholqr2", {"shifted": 1, "prec": 3, "prec_mid": 3, "final_prec": 3}),
+               ("cgs2_fp64", "oqr_cgs2", {}), ("precholqr_fp64tc", "oqr_precholqr", {"final_prec": 3}))
+    for n in ns:
+        for kz in kappas:
+            Z = oqr.colmajor(inputs.tall_z(m, n, kz, seed=seed + n + int(math.log10(kz)), device=dev))
+            zn = torch.linalg.matrix_norm(Z, 2).item()
+            cell = {"m": m, "n": n, "kappa_A": 1e6, "kappa_Z": kz}
+            for label, name, kw in methods:
+                Q = oqr.empty_colmajor(m, n, dev)
+                R = oqr.empty_colmajor(n, n, dev)
+                opts = oqr.make_opts(**kw)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                _, _, (st, _) = ctx._qr(name, A, Z, Q=Q, R=R, opts=opts, stream=stream, raise_on_error=False)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if st != 0:
+                    cell[label] = {"status": st}
+                    continue
+                E = Q.T @ (Af @ Q) - torch.eye(n, dtype=torch.float64, device=dev)
+                orth = torch.linalg.eigvalsh(0.5 * (E + E.T)).abs().max().item()
+                rep = torch.linalg.matrix_norm(Z - Q @ R, 2).item() / zn
+                cell[label] = {"orth": orth, "repres": rep, "ms": e0.elapsed_time(e1), "status": 0}
+                del Q, R, E
+            print(json.dumps({"sweep": cell}), flush=True)
+            del Z
+            torch.cuda.empty_cache()
+
+
+def run_precision_study(ctx, torch, dev, m, n, seed=401):
+    """Config 2 at m (default 32768): kappa(A) = 1e6, Z = V_top diag(sigma) W^T with V_top the n largest
+    eigenvectors of A (Sec. 7's case 2, which sets kappa(A^{1/2} Z) through kappa(Z)); the BF16X3, FP8 and
+    TC2 Grams against the DFMA Gram (||G - G_64||_2 / ||G_64||_2), and the orthogonality of the mixed
+    A-CholQR2 variants, per kappa(A^{1/2} Z) in {1e1, 1e3, 1e5, 1e7}.  One JSON line per kappa."""
+    import numpy as np
+
+    from paper_1401_5171_gb300 import inputs, oqr
+    Af, p = inputs.dense_spd(m, 1e6, seed=seed, device=dev)
+    A = oqr.colmajor(Af)
+    V = inputs.eigvecs(p, np.arange(m - n, m))
+    d_top = p.d[m - n:]
+    for target in (1e1, 1e3, 1e5, 1e7):
+        # kappa(A^{1/2} Z) with Z = V diag(z) W^T is kappa(diag(sqrt(d) z)): pick z to give the target
+        kz = target / math.sqrt(d_top.max() / d_top.min())
+        Z = oqr.colmajor(inputs.tall_z(m, n, max(kz, 1.0), seed=seed + int(math.log10(target)), device=dev, U=V))
+        G64 = ctx.oqr_gram(A, Z, prec=oqr.OQR_FP64)
+        g2 = torch.linalg.matrix_norm(G64, 2).item()
+        ev = torch.linalg.eigvalsh(0.5 * (G64 + G64.T))
+        row = {"m": m, "n": n, "kappa_A": 1e6, "kappa_A_half_Z": math.sqrt((ev.max() / ev.min()).item())}
+        for label, prec in (("bf16x3", oqr.OQR_BF16X3), ("fp8", oqr.OQR_FP8), ("tc2", oqr.OQR_TC2),
+                            ("fp64tc", oqr.OQR_FP64_TC)):
+            G = ctx.oqr_gram(A, Z, prec=prec)
+            row["gram_err_" + label] = torch.linalg.matrix_norm(G - G64, 2).item() / g2
+        for label, kw in (("bf16x3_fp64tc", {"prec": 1, "final_prec": 3}), ("tc2_fp64tc", {"prec": 4, "final_prec": 3}),
+                          ("fp8_fp64tc", {"prec": 2, "final_prec": 3}),
+                          ("shifted_bf16x3_fp64tc", {"shifted": 1, "prec": 1, "prec_mid": 3, "final_prec": 3})):
+            Q, R, (st, _) = ctx.oqr_cholqr2(A, Z, raise_on_error=False, **kw)
+            if st != 0:
+                row["orth_" + label] = None
+                continue
+            E = Q.T @ (Af @ Q) - torch.eye(n, dtype=torch.float64, device=dev)
+            row["orth_" + label] = torch.linalg.eigvalsh(0.5 * (E + E.T)).abs().max().item()
+        print(json.dumps({"precision_study": row}), flush=True)
+
+
 def profile_batch(ctx, torch, dev, count, mode):
     """One oqr_batched call (after a warm-up call that captures its graph) inside cudaProfilerStart/Stop."""
     from paper_1401_5171_gb300 import inputs
@@ -540,6 +624,13 @@ def main():
     dev = torch.device("cuda", local)
     if args.batch_profile is not None:
         profile_batch(oqr.Oqr(local), torch, dev, args.batch_count, args.batch_profile)
+        return
+    if args.sweep:
+        run_sweep(oqr.Oqr(local), torch, dev, args.m, [int(x) for x in args.sweep_n.split(",")],
+                  [float(x) for x in args.sweep_kappa_z.split(",")])
+        return
+    if args.precision_study:
+        run_precision_study(oqr.Oqr(local), torch, dev, args.m, args.n)
         return
     m, n = args.m, args.n
     # inputs resident in HBM before the timed region
