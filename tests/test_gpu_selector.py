@@ -159,7 +159,10 @@ def test_batched_features_match_definition(env):
             tol = 1e-3 + min(0.1, kap * kap * 1e-15 / 8)
             assert abs(F[b, 12] - ref[12]) <= tol, (b, F[b, 12], ref[12])
             if ref[5] == 0.0:
-                assert abs(F[b, 7] - ref[7]) <= 2e-3 and abs(F[b, 8] - ref[8]) <= 2e-3, b
+                # the smallest pivot p of the scaled Gram moves by about 1e-15 / p relative (its rounding)
+                pmin = 10.0 ** (-6 * ref[7])
+                assert abs(F[b, 7] - ref[7]) <= 2e-3 + min(0.2, 1e-14 / pmin), b
+                assert abs(F[b, 8] - ref[8]) <= 2e-3, b
         else:   # both broke down; where depends on the last bits of pivots near zero, so only the range is fixed
             assert 0.0 < F[b, 11] <= 1.0, b
 
