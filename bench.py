@@ -323,8 +323,10 @@ def launches_per_step(path, n):
 def tc_u_flops(m, n):
     """Tensor-core flops of the FP64-accurate U = M Z product as executed: 28 slice
     products (levels 2..8 of 7 slices) over the 128-row tiles of the lower triangle,
-    each row tile I contracting over k < 128 (I + 1), n padded to the 64-column chunks."""
-    npad = -(-n // 64) * 64
+    each row tile I contracting over k < 128 (I + 1), n padded to the column tiles
+    (128 wide for n > 64, where two level-group kernels share the products; else 64)."""
+    tile = 128 if n > 64 else 64
+    npad = -(-n // tile) * tile
     rt = -(-m // 128)
     ksum = sum(min(128 * (i + 1), m) for i in range(rt))
     return 2.0 * 28 * 128 * npad * ksum
@@ -714,7 +716,10 @@ def main():
                     "frac": achieved / peak,
                     "traffic": ncu_traffic("emu_kernel_u_m32768_n256", ["paper_1401_5171_gb300/csrc/k_tc.cu"])
                     if (m, n) == (32768, 256) else None,
-                    "kernel": "emu_kernel (U = M Z: 28 BF16 slice products into 6 TMEM level accumulators, "
+                    "kernel": ("emu2_kernel<0> + emu2_kernel<1> (U = M Z: the 28 BF16 slice products in two "
+                               "level groups, L2..L5 in 4 TMEM accumulators and L6..L8 in 2 double-buffered ones, "
+                               "tcgen05 kind::f16, N = 128); timed together as the U phase") if n > 64 else
+                              "emu_kernel (U = M Z: 28 BF16 slice products into 6 TMEM level accumulators, "
                               "tcgen05 kind::f16, N = 64)",
                     "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst; kernel timed alone), of measured",
                     "launch_ms": t * 1e3, "phases_ms": ph}

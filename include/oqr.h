@@ -369,7 +369,10 @@ oqr_status oqr_symm(oqr_ctx* ctx, int m, int k, const double* A, long lda, const
  *     the wave's one split of A.  One-pass results (all results when
  *     opts->selector_check = 1) are checked: ||Q^T A Q - I||_2 above
  *     opts->selector_tol, or a breakdown, sends the instance down the fallback
- *     chain: shifted A-CholQR3 on the tensor cores (checked), then FP64
+ *     chain; so does a two-pass result whose second pass factored a Gram
+ *     Q_1^T A Q_1 more than 0.5 from I (read from that Gram, at no extra
+ *     cost: within 0.5 the last pass leaves the orthogonality at rounding
+ *     level).  The fallback chain: shifted A-CholQR3 on the tensor cores (checked), then FP64
  *     A-CholQR2 (accepted once it completes).  opts->batch_orth and
  *     opts->batch_choice, when given, receive the checks and the option each
  *     result comes from.  This mode synchronizes the stream (the choices are

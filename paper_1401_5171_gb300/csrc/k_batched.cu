@@ -370,6 +370,10 @@ __global__ void shift_batched_kernel(const BatchDesc* __restrict__ d, int count,
 
 // ||E||_2 estimate of E = G - I for the instances checked at this pass (one CTA each).
 constexpr int BCHECK_ITERS = 40;
+// last = false: the check of the instances whose factor passes end at pass (D.npass == pass), from one
+// more Gram of Q.  last = true: the defect of the Gram that an instance's last factor pass factors
+// (D.npass >= 2, pass == D.npass - 1): ||Q_prev^T A Q_prev - I||_2 of the previous pass's Q.
+template <bool LAST>
 __global__ void __launch_bounds__(256) check_batched_kernel(const BatchDesc* __restrict__ d, const int* status,
                                                             int pass, double* orth)
 {
@@ -378,7 +382,7 @@ __global__ void __launch_bounds__(256) check_batched_kernel(const BatchDesc* __r
     __shared__ double red[8];
     const int b = blockIdx.x;
     const BatchDesc D = d[b];
-    if (D.npass != pass) return;
+    if (LAST ? (D.npass < 2 || pass != D.npass - 1) : (D.npass != pass)) return;
     if (status[b] != 0) {
         if (threadIdx.x == 0) orth[b] = INFINITY;
         return;
@@ -521,7 +525,14 @@ cudaError_t launch_batch_status_scatter(const int* st_sorted, const int* perm, i
 cudaError_t launch_batched_check(const BatchDesc* d, int count, const int* status, int pass, double* orth,
                                  cudaStream_t s)
 {
-    check_batched_kernel<<<count, 256, 0, s>>>(d, status, pass, orth);
+    check_batched_kernel<false><<<count, 256, 0, s>>>(d, status, pass, orth);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batched_last_defect(const BatchDesc* d, int count, const int* status, int pass, double* defect,
+                                       cudaStream_t s)
+{
+    check_batched_kernel<true><<<count, 256, 0, s>>>(d, status, pass, defect);
     return cudaGetLastError();
 }
 

@@ -794,6 +794,9 @@ oqr_status batched_fp64_impl(oqr_ctx* ctx, int count, const int* m, const int* n
 // A-CholQR3 on the tensor cores (checked), then FP64 A-CholQR2.
 namespace {
 constexpr int SEL_ONE = 0, SEL_TWO = 1, SEL_SHIFTED = 2, SEL_FP64 = 3;
+// A last pass factoring a Gram within 0.5 of I leaves kappa(Q_prev)^2 <= 3 in the A inner product, so its
+// result is at rounding level (Thm 2.1 with kappa^2 <= 3); a larger defect sends the result to the fallback.
+constexpr double LAST_DEFECT_MAX = 0.5;
 
 struct SelInputs {
     int count;
@@ -834,9 +837,11 @@ oqr_status selector_waves(oqr_ctx* ctx, const SelInputs& I, const float* params,
     const TcBatchPlan plan = tc_batch_plan(sh1, budget);
     const TcBatchPlan pmax = tc_batch_plan(shmax, budget);  // bounds every per-wave plan of the later passes
     if (pmax.waves.size() != plan.waves.size()) return OQR_ERR_UNSUPPORTED;
+    double* defects = nullptr;
     auto layout = [&](Carve& c, char** tab1, char** tab2, BatchDesc** d, int** sts, int** dshifted, double** sums,
                       double** shifts, double** orths, float** feat, int** choice, double** pool, double** upool,
                       void** scratch) {
+        defects = c.take<double>((size_t)count);
         *tab1 = c.take<char>(plan.table_bytes);
         *tab2 = c.take<char>(pmax.table_bytes);
         *d = c.take<BatchDesc>((size_t)count);
@@ -953,6 +958,7 @@ oqr_status selector_waves(oqr_ctx* ctx, const SelInputs& I, const float* params,
         OQR_TRY(cudaMemcpyAsync(tab2, image2.data(), image2.size(), cudaMemcpyHostToDevice, s));
         for (int pass = 1; pass < p2.waves[0].maxpass; ++pass) {
             OQR_TRY(tc_batch_gram(p2, 0, pass, tab2, scratch, ctx->st, limit, ctx->sm_count, s));
+            OQR_TRY(launch_batched_last_defect(dw, cnt, sw, pass, defects + f, s));
             OQR_TRY(launch_batched_factor(dw, cnt, sw, pass, nullptr, s));
             OQR_TRY(launch_batched_check(dw, cnt, sw, pass, orths + f, s));
         }
@@ -968,9 +974,10 @@ oqr_status selector_waves(oqr_ctx* ctx, const SelInputs& I, const float* params,
         if (cudaStreamSynchronize(s) != cudaSuccess) return OQR_ERR_CUDA;
         return OQR_OK;
     }
-    std::vector<double> hor((size_t)count);
+    std::vector<double> hor((size_t)count), hdef((size_t)count);
     OQR_TRY(cudaMemcpyAsync(hst.data(), sts, sizeof(int) * count, cudaMemcpyDeviceToHost, s));
     OQR_TRY(cudaMemcpyAsync(hor.data(), orths, sizeof(double) * count, cudaMemcpyDeviceToHost, s));
+    OQR_TRY(cudaMemcpyAsync(hdef.data(), defects, sizeof(double) * count, cudaMemcpyDeviceToHost, s));
     DevStatus hs;
     OQR_TRY(cudaMemcpyAsync(&hs, ctx->st, sizeof(hs), cudaMemcpyDeviceToHost, s));
     if (cudaStreamSynchronize(s) != cudaSuccess) return OQR_ERR_CUDA;
@@ -982,6 +989,11 @@ oqr_status selector_waves(oqr_ctx* ctx, const SelInputs& I, const float* params,
         res->status[b] = hs.code != 0 ? -1 : hst[i];
         res->choice[b] = opt[i];
         if (chk[i]) res->orth[b] = hst[i] == 0 ? hor[i] : INFINITY;
+        // the free check of a two-pass result: the Gram its second pass factored was far from I, so that
+        // pass did not bring the orthogonality to rounding level; the fallback chain redoes it (the shifted
+        // option, the most robust, is accepted once it completes, as the network's answer for hard instances)
+        if (!chk[i] && opt[i] == SEL_TWO && hst[i] == 0 && !(hdef[i] <= LAST_DEFECT_MAX))
+            res->status[b] = -2;
     }
     return hs.code != 0 ? OQR_ERR_TIMEOUT : OQR_OK;
 }

@@ -211,6 +211,8 @@ struct TcPlan {
     int kch;        // exponent chunks of the contraction (256 long; 128 for FP8)
     int nitems_max; // work items of the larger of the two products
     int noA;        // 1: no planes of A (only C = X^T U; launch_tc_cross)
+    int u128;       // mode 1, n > 64: U = M Z by two level-group kernels with 128-column tiles
+    int nitems_u128;  // their work items
 };
 TcPlan tc_plan(int m, int n, int mode, int sa = 0, bool no_a = false);
 size_t tc_plan_bytes(const TcPlan& p);
@@ -308,6 +310,11 @@ cudaError_t launch_batch_scatter_rows_f32(const float* in, const int* perm, int 
                                           cudaStream_t s);
 // The selector's 16 features of each instance of a batch after its first FP64-accurate pass (k_features.cu).
 cudaError_t launch_features_batched(const BatchDesc* d, int count, const int* status, float* feat, cudaStream_t s);
+// defect[b] = ||Q^T A Q - I||_2 estimate of the Gram that instance b's last factor pass factors (the
+// instances with 2 or more passes whose last factor pass is pass), read from that Gram's partial before the
+// factor; a free check of the result: the last pass leaves orthogonality at rounding level when it is small.
+cudaError_t launch_batched_last_defect(const BatchDesc* d, int count, const int* status, int pass, double* defect,
+                                       cudaStream_t s);
 // out[perm[i]] = in[i] (count doubles).
 cudaError_t launch_batch_scatter_f64(const double* in, const int* perm, int count, double* out, cudaStream_t s);
 
