@@ -82,6 +82,8 @@ def parse():
     p.add_argument("--sweep-kappa-z", default="1e2,1e4,1e6,1e8")
     p.add_argument("--precision-study", action="store_true",
                    help="only: config 2's per-kappa precision study at --m, --n (JSON line per kappa)")
+    p.add_argument("--only", default=None, choices=["next", "selector"],
+                   help="only: one side measurement (the next paths at --m, --n; or the selector), for profiling")
     p.add_argument("--selector-count", type=int, default=512,
                    help="side measurement: the learned selector on this many instances of its workload (0: none)")
     p.add_argument("--batch-profile", type=int, default=None, choices=[0, 1, 2, 3],
@@ -323,10 +325,8 @@ def launches_per_step(path, n):
 def tc_u_flops(m, n):
     """Tensor-core flops of the FP64-accurate U = M Z product as executed: 28 slice
     products (levels 2..8 of 7 slices) over the 128-row tiles of the lower triangle,
-    each row tile I contracting over k < 128 (I + 1), n padded to the column tiles
-    (128 wide for n > 64, where two level-group kernels share the products; else 64)."""
-    tile = 128 if n > 64 else 64
-    npad = -(-n // tile) * tile
+    each row tile I contracting over k < 128 (I + 1), n padded to the 64-column chunks."""
+    npad = -(-n // 64) * 64
     rt = -(-m // 128)
     ksum = sum(min(128 * (i + 1), m) for i in range(rt))
     return 2.0 * 28 * 128 * npad * ksum
@@ -634,6 +634,20 @@ def main():
     if args.precision_study:
         run_precision_study(oqr.Oqr(local), torch, dev, args.m, args.n)
         return
+    if args.only:   # one side measurement alone (for profiling it); prints its JSON, not a bench line
+        ctx1 = oqr.Oqr(local)
+        if args.only == "selector":
+            print(json.dumps({"selector": run_selector(ctx1, torch, dev, args.selector_count,
+                                                       torch.cuda.current_stream(dev))}), flush=True)
+            return
+        Af1, _ = inputs.dense_spd(args.m, args.kappa_a, seed=instance_seeds(rank)[0], device=dev)
+        A1 = oqr.colmajor(Af1)
+        Z1 = oqr.colmajor(inputs.tall_z(args.m, args.n, args.kappa_z, seed=instance_seeds(rank)[1], device=dev))
+        peaks1 = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+            if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+        print(json.dumps({"next_paths": run_next_paths(ctx1, torch, dev, A1, Z1, torch.cuda.current_stream(dev),
+                                                       args.m, args.n, peaks1)}), flush=True)
+        return
     m, n = args.m, args.n
     # inputs resident in HBM before the timed region
     seed_a, seed_z = instance_seeds(rank)
@@ -716,10 +730,7 @@ def main():
                     "frac": achieved / peak,
                     "traffic": ncu_traffic("emu_kernel_u_m32768_n256", ["paper_1401_5171_gb300/csrc/k_tc.cu"])
                     if (m, n) == (32768, 256) else None,
-                    "kernel": ("emu2_kernel<0> + emu2_kernel<1> (U = M Z: the 28 BF16 slice products in two "
-                               "level groups, L2..L5 in 4 TMEM accumulators and L6..L8 in 2 double-buffered ones, "
-                               "tcgen05 kind::f16, N = 128); timed together as the U phase") if n > 64 else
-                              "emu_kernel (U = M Z: 28 BF16 slice products into 6 TMEM level accumulators, "
+                    "kernel": "emu_kernel (U = M Z: 28 BF16 slice products into 6 TMEM level accumulators, "
                               "tcgen05 kind::f16, N = 64)",
                     "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst; kernel timed alone), of measured",
                     "launch_ms": t * 1e3, "phases_ms": ph}

@@ -606,7 +606,7 @@ __device__ inline Item item_of(const TcArgs& a, int j)
 __device__ inline uint64_t smem_desc(uint32_t addr, int swizzle_bytes)
 {
     const uint64_t sbo = (uint64_t)(8 * swizzle_bytes) >> 4;  // 8 rows x swizzle width
-    const uint64_t layout = swizzle_bytes == 128 ? 2ull : swizzle_bytes == 64 ? 4ull : 6ull;  // 128B, 64B, 32B
+    const uint64_t layout = swizzle_bytes == 128 ? 2ull : 4ull;  // SWIZZLE_128B : SWIZZLE_64B
     return (uint64_t)((addr & 0x3FFFFu) >> 4) | (1ull << 16) | (sbo << 32) | (1ull << 46) | (layout << 61);
 }
 
@@ -1439,332 +1439,6 @@ __global__ void __launch_bounds__(EMU_THREADS, 1)
     }
 }
 
-// ----------------------- FP64-accurate product in two level groups, N = 128 ----
-// The same 28 slice products as emu_kernel, as two kernels over the same work
-// items with 128-column tiles (an MMA of N = 128 does twice the work of one of
-// N = 64 in about the same issue time), because the six level accumulators of
-// one kernel do not fit 512 TMEM columns at N = 128:
-//   G = 0 (levels L2..L5, slices 0..3): four accumulators of 128 columns fill
-//     TMEM; a chunk's MMAs wait until the drain has read the previous chunk.
-//     The drain adds each level, scaled, into a double-float (H, L) by TwoSum
-//     (exact level sums, as in emu_kernel) and writes (H + L) 2^(emax_row +
-//     emax_col) into the item's FP64 slot.
-//   G = 1 (levels L6..L8, all 7 slices): two accumulators (L6; L7 and L8
-//     together) of 128 columns, double-buffered by chunk parity; the drain adds
-//     (L6 + L78) times the chunk's scale into an FP64 sum (these terms are below
-//     2^-29 of the chunk's scale, so one FP32 rounding of L6 + L78 costs below
-//     2^-53 of it) and adds its value into the slot G = 0 wrote.
-// G = 1's seven planes per operand take 16-long k-steps (32-byte swizzled rows)
-// so that three stages fit in shared memory.
-template <int G>
-struct Emu2Cfg {
-    static constexpr int KS = G == 0 ? 32 : 16;       // k-step
-    static constexpr int SW = KS * 2;                 // swizzle width (bytes)
-    static constexpr int SP = G == 0 ? 4 : 7;         // planes per operand
-    static constexpr int LMIN = G == 0 ? 2 : 6, LMAX = G == 0 ? 5 : 8;
-    static constexpr int N = 128;
-    static constexpr int A_TILE = TM * KS * 2;
-    static constexpr int B_TILE = N * KS * 2;
-    static constexpr int STAGE = SP * (A_TILE + B_TILE);
-    static constexpr int STAGES = 3;
-    static constexpr int CH = KCH_EMU / KS;           // k-steps per chunk
-    static constexpr int KK = KS / 16;                // MMAs (K = 16) per product per k-step
-    static constexpr int DRAIN = 512;
-    static constexpr int THREADS = 64 + DRAIN;
-    static constexpr int CPT = N / 4;                 // columns per drain thread
-    static constexpr int MAXCH = 2048 / KCH_EMU;
-    static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE + 1024 + (size_t)MAXCH * (TM + N) * 4;
-    static_assert(STAGE % 1024 == 0, "stage alignment");
-    static_assert(SMEM <= 232448, "shared memory");
-};
-
-// Levels LMIN..LMAX of one k-step: product (s, L - 2 - s) into accumulator acc(L).
-template <int G, int L>
-__device__ __forceinline__ void emu2_issue_level(uint32_t d, uint64_t desc0A, uint64_t desc0B, uint32_t idesc,
-                                                 bool first)
-{
-    using C = Emu2Cfg<G>;
-#pragma unroll
-    for (int s = 0; s <= L - 2; ++s) {
-        const int t = L - 2 - s;
-#pragma unroll
-        for (int kk = 0; kk < C::KK; ++kk) {
-            const uint64_t ad = desc0A + (uint64_t)((s * C::A_TILE + kk * 32) >> 4);
-            const uint64_t bd = desc0B + (uint64_t)((t * C::B_TILE + kk * 32) >> 4);
-            umma_bf16(d, ad, bd, idesc, (first && s == 0 && kk == 0) ? 0u : 1u);
-        }
-    }
-}
-
-template <int G>
-__global__ void __launch_bounds__(Emu2Cfg<G>::THREADS, 1)
-    emu2_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, TcArgs a)
-{
-    using C = Emu2Cfg<G>;
-    extern __shared__ __align__(1024) unsigned char emu2_smem_raw[];
-    unsigned char* smem =
-        reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(emu2_smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE);
-    uint64_t* empty = full + C::STAGES;
-    uint64_t* accf = empty + C::STAGES;  // [2]: a chunk's MMAs complete (G = 0 uses [0] only)
-    uint64_t* acce = accf + 2;           // [2]: a chunk's accumulators read by the drain
-    uint64_t* done = acce + 2;
-    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(done + 1);
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
-    volatile int* go = abort_flag + 1;
-    float* rowsc = reinterpret_cast<float*>(smem + C::STAGES * C::STAGE + 1024);
-    float* colsc = rowsc + C::MAXCH * TM;
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (*(volatile int*)&a.st->code != 0) return;
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < C::STAGES; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1);
-        }
-        for (int b = 0; b < 2; ++b) {
-            mbar_init(&accf[b], 1);
-            mbar_init(&acce[b], 1);
-        }
-        mbar_init(done, 1);
-        *abort_flag = 0;
-        fence_barrier_init();
-        tma_prefetch_desc(&mapA);
-        tma_prefetch_desc(&mapB);
-    }
-    if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
-                     "r"(512)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = *tmem_holder;
-
-    auto fail = [&](int where_info) {
-        if (*abort_flag == 0) {
-            *abort_flag = 1;
-            raise_status(a.st, OQR_ERR_TIMEOUT, where_info, TAG_MIXED);
-        }
-    };
-
-    if (warp == 0) {
-        // ------------------------------------------------ TMA producer
-        if (lane == 0) {
-            long it = 0;
-            for (int j = blockIdx.x; j < a.nitems && !*abort_flag; j += gridDim.x) {
-                const Item item = item_of(a, j);
-                for (int ks = item.ks0; ks < item.ks1 && !*abort_flag; ++ks, ++it) {
-                    const int stg = (int)(it % C::STAGES);
-                    const uint32_t ph = (uint32_t)((it / C::STAGES) & 1);
-                    if (!mbar_wait(&empty[stg], ph ^ 1u, a.limit_ns)) {
-                        fail(21);
-                        break;
-                    }
-                    unsigned char* base = smem + stg * C::STAGE;
-                    mbar_expect_tx(&full[stg], C::STAGE);
-                    for (int s = 0; s < C::SP; ++s)
-                        tma_load_3d(base + s * C::A_TILE, &mapA, &full[stg], ks * C::KS, item.roff + item.I * TM, s);
-                    for (int t = 0; t < C::SP; ++t)
-                        tma_load_3d(base + C::SP * C::A_TILE + t * C::B_TILE, &mapB, &full[stg], ks * C::KS,
-                                    item.coff + item.c * C::N, t);
-                }
-            }
-            const long issued = it;  // copies still in flight must land before the CTA may exit
-            for (long q = issued - C::STAGES; q < issued; ++q)
-                if (q >= 0)
-                    mbar_wait(&full[q % C::STAGES], (uint32_t)((q / C::STAGES) & 1), exit_drain_ns(a.limit_ns));
-        }
-    } else if (warp == 1) {
-        // ------------------------------------------------ MMA issuer
-        if (lane == 0) {
-            constexpr uint32_t idesc = idesc_bf16(C::N);
-            long it = 0, chunk = 0;
-            bool ok = true;
-            for (int j = blockIdx.x; j < a.nitems && ok && !*abort_flag; j += gridDim.x) {
-                const Item item = item_of(a, j);
-                for (int ks = item.ks0; ks < item.ks1 && !*abort_flag; ++ks, ++it) {
-                    const int kin = ks - item.ks0;
-                    const bool cstart = kin % C::CH == 0;
-                    const bool cend = (kin + 1) % C::CH == 0 || ks + 1 == item.ks1;
-                    const int stg = (int)(it % C::STAGES);
-                    if (!mbar_wait(&full[stg], (uint32_t)((it / C::STAGES) & 1), a.limit_ns)) {
-                        fail(23);
-                        ok = false;
-                        break;
-                    }
-                    tc_fence_after();
-                    const uint32_t base = smem_u32(smem + stg * C::STAGE);
-                    const uint64_t dA = smem_desc(base, C::SW), dB = smem_desc(base + C::SP * C::A_TILE, C::SW);
-                    if (G == 0) {
-                        if (cstart && chunk >= 1) {  // the previous chunk's accumulators must have been read
-                            if (!mbar_wait(&acce[0], (uint32_t)((chunk - 1) & 1), a.limit_ns)) {
-                                fail(24);
-                                ok = false;
-                                break;
-                            }
-                            tc_fence_after();
-                        }
-                        emu2_issue_level<G, 5>(tmem + 384u, dA, dB, idesc, cstart);
-                        emu2_issue_level<G, 4>(tmem + 256u, dA, dB, idesc, cstart);
-                        emu2_issue_level<G, 3>(tmem + 128u, dA, dB, idesc, cstart);
-                        emu2_issue_level<G, 2>(tmem, dA, dB, idesc, cstart);
-                    } else {
-                        const int b = (int)(chunk & 1);
-                        if (cstart && chunk >= 2) {  // this buffer was read two chunks ago
-                            if (!mbar_wait(&acce[b], (uint32_t)(((chunk - 2) >> 1) & 1), a.limit_ns)) {
-                                fail(24);
-                                ok = false;
-                                break;
-                            }
-                            tc_fence_after();
-                        }
-                        const uint32_t hb = tmem + (uint32_t)(b * 256);
-                        emu2_issue_level<G, 6>(hb, dA, dB, idesc, cstart);
-                        emu2_issue_level<G, 7>(hb + 128u, dA, dB, idesc, cstart);
-                        emu2_issue_level<G, 8>(hb + 128u, dA, dB, idesc, false);
-                    }
-                    umma_commit(&empty[stg]);
-                    if (cend) {
-                        umma_commit(&accf[G == 0 ? 0 : (int)(chunk & 1)]);
-                        ++chunk;
-                    }
-                }
-            }
-            umma_commit(done);
-            mbar_wait(done, 0, exit_drain_ns(a.limit_ns));
-        }
-    } else {
-        // ------------------------------------------------ drain (warps 2..17)
-        const int dt = threadIdx.x - 64;
-        const int q = warp & 3;
-        const int g = (warp - 2) >> 2;
-        const int r = q * 32 + lane;
-        const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(g * C::CPT);
-        long chunk = 0;
-        bool stop = false;
-        for (int j = blockIdx.x; j < a.nitems && !stop; j += gridDim.x) {
-            const Item item = item_of(a, j);
-            const int gi = item.I * TM + r;
-            const bool row_ok = gi < item.rows;
-            float2 H[C::CPT / 2], Lw[C::CPT / 2];  // G = 0: double-float level sum
-            double S[G == 1 ? C::CPT : 1];           // G = 1: the small levels' sum
-#pragma unroll
-            for (int c = 0; c < C::CPT / 2; ++c) H[c] = Lw[c] = make_float2(0.f, 0.f);
-#pragma unroll
-            for (int c = 0; c < (G == 1 ? C::CPT : 1); ++c) S[c] = 0.0;
-            const int emax_r = row_ok ? a.emaxA[item.roff + gi] : 0;
-            const int nsteps = item.ks1 - item.ks0;
-            const int nch = (nsteps + C::CH - 1) / C::CH;
-            {
-                const int kc0 = (item.ks0 * C::KS) / KCH_EMU;
-                for (int e = dt; e < nch * TM; e += C::DRAIN) {
-                    const int ch = e / TM, rr = e % TM;
-                    const int gg = item.I * TM + rr;
-                    float v = 0.0f;
-                    if (gg < item.rows) {
-                        const long gr = item.roff + gg;
-                        const int er = a.eA[(size_t)(kc0 + ch) * a.rowsA + gr];
-                        if (er != EXP_NONE) v = pow2f(er - a.emaxA[gr] - 14);
-                    }
-                    rowsc[ch * TM + rr] = v;
-                }
-                for (int e = dt; e < nch * C::N; e += C::DRAIN) {
-                    const int ch = e / C::N, cc = e % C::N;
-                    const int col = item.c * C::N + cc;
-                    float v = 0.0f;
-                    if (col < item.cols) {
-                        const long gc = item.coff + col;
-                        const int eb = a.eB[(size_t)(kc0 + ch) * a.colsB + gc];
-                        if (eb != EXP_NONE) v = pow2f(eb - a.emaxB[gc]);
-                    }
-                    colsc[ch * C::N + cc] = v;
-                }
-            }
-            for (int ch = 0; ch < nch; ++ch, ++chunk) {
-                const int b = G == 0 ? 0 : (int)(chunk & 1);
-                if (dt == 0) {
-                    const uint32_t par = G == 0 ? (uint32_t)(chunk & 1) : (uint32_t)((chunk >> 1) & 1);
-                    const bool okw = mbar_wait(&accf[b], par, a.limit_ns);
-                    if (!okw) fail(26);
-                    *go = (okw && !*abort_flag) ? 1 : 0;
-                }
-                asm volatile("bar.sync 1, 512;" ::: "memory");  // also publishes the item's scales
-                if (*go == 0) {
-                    stop = true;
-                    break;
-                }
-                tc_fence_after();
-                const float rs = rowsc[ch * TM + r];
-                if (G == 0) {
-#pragma unroll
-                    for (int lv = 0; lv < 4; ++lv)          // L5, L4, L3, L2
-#pragma unroll
-                        for (int part = 0; part < C::CPT / 8; ++part) {
-                            uint32_t v[8];
-                            tmem_ld8(lane_addr + (uint32_t)((3 - lv) * 128 + 8 * part), v);
-#pragma unroll
-                            for (int cc = 0; cc < 4; ++cc) {
-                                const int c = part * 4 + cc;  // column pair
-                                const float2 sc = __fmul2_rn(
-                                    make_float2(rs, rs),
-                                    make_float2(colsc[ch * C::N + g * C::CPT + 2 * c],
-                                                colsc[ch * C::N + g * C::CPT + 2 * c + 1]));
-                                two_sum2(H[c], Lw[c],
-                                         __fmul2_rn(make_float2(__uint_as_float(v[2 * cc]), __uint_as_float(v[2 * cc + 1])),
-                                                    sc));
-                            }
-                        }
-                } else {
-                    const uint32_t hb = lane_addr + (uint32_t)(b * 256);
-#pragma unroll
-                    for (int part = 0; part < C::CPT / 8; ++part) {
-                        uint32_t v6[8], v78[8];
-                        tmem_ld8x2(hb + (uint32_t)(8 * part), hb + 128u + (uint32_t)(8 * part), v6, v78);
-#pragma unroll
-                        for (int cc = 0; cc < 8; ++cc) {
-                            const int c = part * 8 + cc;
-                            const float sc = rs * colsc[ch * C::N + g * C::CPT + c];  // a power of two (exact)
-                            const float h = __uint_as_float(v6[cc]) + __uint_as_float(v78[cc]);
-                            S[c] = fma((double)h, (double)sc, S[c]);
-                        }
-                    }
-                }
-                tc_fence_before();
-                asm volatile("bar.sync 1, 512;" ::: "memory");  // accumulators and scales fully read
-                if (dt == 0) mbar_arrive(&acce[b]);
-            }
-            if (stop) break;
-            double* slot = a.slots + (size_t)j * TM * C::N + (size_t)r * C::N + g * C::CPT;
-#pragma unroll
-            for (int c = 0; c < C::CPT; ++c) {
-                const int col = item.c * C::N + g * C::CPT + c;
-                const int ec = col < item.cols ? __ldg(a.emaxB + item.coff + col) : EXP_NONE;
-                double out = 0.0;
-                if (row_ok && emax_r != EXP_NONE && ec != EXP_NONE) {
-                    const int k = emax_r + ec;
-                    if (G == 0) {
-                        const float hc = (c & 1) ? H[c / 2].y : H[c / 2].x, lc = (c & 1) ? Lw[c / 2].y : Lw[c / 2].x;
-                        out = f32_scaled_to_f64(hc, k) + f32_scaled_to_f64(lc, k);
-                    } else {
-                        out = ldexp(S[c], k);
-                    }
-                }
-                if (G == 0) slot[c] = out;
-                else slot[c] += out;
-            }
-        }
-    }
-    tc_fence_before();
-    __syncthreads();
-    if (warp == 1) {
-        tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
-    }
-}
-
 // ------------------------------------------------------------ host side ----
 bool make_map_3d(CUtensorMap* map, const void* base, long kext, long rows, long ldp, size_t plane_bytes, int S,
                  int box_k, int box_rows, int elem_bytes);
@@ -1801,41 +1475,12 @@ cudaError_t launch_emu(const TcArgs& a0, const void* planesA, long ldpA, size_t 
     if (grid > 0) emu_kernel<<<grid, EMU_THREADS, EMU_SMEM, s>>>(mA, mB, a);
     return cudaGetLastError();
 }
-
-// The FP64-accurate product of a1's items (128-column tiles) by the two level-group kernels, into a1's slots.
-template <int G>
-cudaError_t launch_emu2_group(const TcArgs& a0, const void* planesA, long ldpA, size_t planeA, const void* planesB,
-                              long ldpB, size_t planeB, int sms, cudaStream_t s)
-{
-    using C = Emu2Cfg<G>;
-    TcArgs a = a0;
-    a.ks = C::KS;
-    a.piece = 2048 / C::KS;
-    CUtensorMap mA{}, mB{};
-    if (!make_map_3d(&mA, planesA, a.K, a.rowsA, ldpA, planeA * 2, EMU_S, C::KS, TM, 2)) return cudaErrorInvalidValue;
-    if (!make_map_3d(&mB, planesB, a.K, a.colsB, ldpB, planeB * 2, EMU_S, C::KS, C::N, 2))
-        return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(emu2_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
-    if (e != cudaSuccess) return e;
-    const int grid = a.nitems < sms ? a.nitems : sms;
-    if (grid > 0) emu2_kernel<G><<<grid, C::THREADS, C::SMEM, s>>>(mA, mB, a);
-    return cudaGetLastError();
-}
-cudaError_t launch_emu2(const TcArgs& a, const void* planesA, long ldpA, size_t planeA, const void* planesB, long ldpB,
-                        size_t planeB, int sms, cudaStream_t s)
-{
-    cudaError_t e = launch_emu2_group<0>(a, planesA, ldpA, planeA, planesB, ldpB, planeB, sms, s);
-    if (e != cudaSuccess) return e;
-    return launch_emu2_group<1>(a, planesA, ldpA, planeA, planesB, ldpB, planeB, sms, s);
-}
 }  // namespace
 
 // -------------------------------------------------------- public (internal) API
 size_t tc_plan_bytes(const TcPlan& p)
 {
-    const size_t a = (size_t)p.nitems_max * TM * p.N * sizeof(double);
-    const size_t b = (size_t)p.nitems_u128 * TM * 128 * sizeof(double);
-    return a > b ? a : b;
+    return (size_t)p.nitems_max * TM * p.N * sizeof(double);
 }
 
 static TcArgs make_args(const TcPlan& p, int rowsA, int colsB, int K, int tri, int N)
@@ -1876,8 +1521,6 @@ TcPlan tc_plan(int m, int n, int mode, int sa, bool no_a)
     }
     const TcArgs u = make_args(p, m, n, m, 1, p.N);
     p.nitems_max = u.nitems > c.nitems ? u.nitems : c.nitems;
-    p.u128 = (mode == 1 && n > EMU_N) ? 1 : 0;  // U = M Z by the two level-group kernels, 128-column tiles
-    p.nitems_u128 = p.u128 ? make_args(p, m, n, m, 1, 128).nitems : 0;
     return p;
 }
 
@@ -2093,28 +1736,11 @@ cudaError_t launch_tc_gram(const TcPlan& p, const double* A, long lda, const dou
     a1.emaxB = L.mZ;
     a1.st = st;
     a1.limit_ns = limit_ns;
-    if (p.u128) {  // 128-column tiles: the two level-group kernels, one slot per item
-        a1 = make_args(p, mm, nn, mm, 1, 128);
-        a1.cum = L.cum1;
-        a1.slots = L.slots;
-        a1.eA = L.eA;
-        a1.eB = L.eZ;
-        a1.emaxA = L.mA;
-        a1.emaxB = L.mZ;
-        a1.st = st;
-        a1.limit_ns = limit_ns;
-    }
     item_prefix_kernel<<<1, PREFIX_THREADS, 0, s>>>(a1, L.cum1);
     mark(1);
-    if (p.u128) {
-        if ((e = launch_emu2(a1, L.Ap, p.ldp, planeA, L.Zp, p.ldp, planeZ, sms, s)) != cudaSuccess) return e;
-        mark(2);
-        slot_reduce_kernel<128><<<(unsigned)(((long)mm * nn + 255) / 256), 256, 0, s>>>(a1, L.U, mm, st);
-    } else {
-        if ((e = launch_tc_mode(p, a1, L.Ap, planeA, L.Zp, planeZ, sms, s)) != cudaSuccess) return e;
-        mark(2);
-        launch_slot_reduce(p, a1, L.U, mm, st, s);
-    }
+    if ((e = launch_tc_mode(p, a1, L.Ap, planeA, L.Zp, planeZ, sms, s)) != cudaSuccess) return e;
+    mark(2);
+    launch_slot_reduce(p, a1, L.U, mm, st, s);
     // C = Z^T U (left operand: Z's columns as rows, K-major), then G = C + C^T
     return tc_cross_phase(p, L, L.U, mm, G, ldg, shift_ptr, st, limit_ns, sms, s, ev);
 }
@@ -2548,9 +2174,7 @@ bool make_map_3d(CUtensorMap* map, const void* base, long kext, long rows, long 
     cuuint64_t strides[2] = {(cuuint64_t)ldp * elem_bytes, (cuuint64_t)plane_bytes};
     cuuint32_t box[3] = {(cuuint32_t)box_k, (cuuint32_t)box_rows, 1};
     cuuint32_t estr[3] = {1, 1, 1};
-    const CUtensorMapSwizzle sw = box_k * elem_bytes == 128  ? CU_TENSOR_MAP_SWIZZLE_128B
-                                  : box_k * elem_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
-                                                             : CU_TENSOR_MAP_SWIZZLE_32B;
+    const CUtensorMapSwizzle sw = box_k * elem_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
     const CUtensorMapDataType dt = elem_bytes == 1 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     CUresult r = fn(map, dt, 3, const_cast<void*>(base), dims, strides, box, estr,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,

@@ -211,8 +211,6 @@ struct TcPlan {
     int kch;        // exponent chunks of the contraction (256 long; 128 for FP8)
     int nitems_max; // work items of the larger of the two products
     int noA;        // 1: no planes of A (only C = X^T U; launch_tc_cross)
-    int u128;       // mode 1, n > 64: U = M Z by two level-group kernels with 128-column tiles
-    int nitems_u128;  // their work items
 };
 TcPlan tc_plan(int m, int n, int mode, int sa = 0, bool no_a = false);
 size_t tc_plan_bytes(const TcPlan& p);
