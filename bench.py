@@ -413,6 +413,8 @@ def run_selector(ctx, torch, dev, count, stream):
     t_sel = events_ms(torch, stream, sel)
     Qs, Rs, st, orth, choice = res["r"]
     stc = st.cpu().numpy()
+    raw = selector.choose(ctx, ctx.oqr_batched_features(As, Zs), P).cpu().numpy()   # the network's own choices
+    final = choice.cpu().numpy()
     worst, above = 0.0, 0
     for b in range(count):
         n = Zs[b].shape[1]
@@ -438,7 +440,9 @@ def run_selector(ctx, torch, dev, count, stream):
 
     t_c2 = events_ms(torch, stream, cholqr2_checked)
     out.update({"qr_per_s": count / (t_sel / 1e3), "ms_per_batch": t_sel,
-                "options_used": np.bincount(choice.cpu().numpy(), minlength=4).tolist(),
+                "options_used": np.bincount(final, minlength=4).tolist(),
+                "network_choices": np.bincount(raw, minlength=4).tolist(),
+                "changed_by_probe_or_fallback": int((raw != final).sum()),
                 "instances_above_bar": int(above), "worst_orth_over_bar": worst,
                 "bar": "max(1e-12, m u ||A||_2 ||Q||_2^2) per instance (Thm 4.1 with c = 1)",
                 "always_shifted_tc": {"qr_per_s": count / (t_shift / 1e3), "ms_per_batch": t_shift},

@@ -38,6 +38,10 @@ struct oqr_ctx {
     // the selector's fallback calls: their per-instance status and orth (device)
     void* sel_buf = nullptr;
     size_t sel_bytes = 0;
+    // the selector's pinned host buffers (choices read back and tables uploaded while the GPU works on)
+    void* pin = nullptr;
+    size_t pin_bytes = 0;
+    cudaEvent_t sel_ev[2] = {nullptr, nullptr};
 };
 
 namespace {
@@ -837,13 +841,17 @@ oqr_status selector_waves(oqr_ctx* ctx, const SelInputs& I, const float* params,
     const TcBatchPlan plan = tc_batch_plan(sh1, budget);
     const TcBatchPlan pmax = tc_batch_plan(shmax, budget);  // bounds every per-wave plan of the later passes
     if (pmax.waves.size() != plan.waves.size()) return OQR_ERR_UNSUPPORTED;
+    const int nw = (int)plan.waves.size();
+    const int nbuf = (features_only || nw == 1) ? 1 : 2;  // wave w + 1's first pass runs while wave w is planned
+    const size_t scratch_bytes = std::max(plan.scratch_bytes, pmax.scratch_bytes);
     double* defects = nullptr;
-    auto layout = [&](Carve& c, char** tab1, char** tab2, BatchDesc** d, int** sts, int** dshifted, double** sums,
-                      double** shifts, double** orths, float** feat, int** choice, double** pool, double** upool,
-                      void** scratch) {
+    char* tab2[2] = {nullptr, nullptr};
+    void* scr[2] = {nullptr, nullptr};
+    auto layout = [&](Carve& c, char** tab1, BatchDesc** d, int** sts, int** dshifted, double** sums,
+                      double** shifts, double** orths, float** feat, int** choice, double** pool, double** upool) {
         defects = c.take<double>((size_t)count);
         *tab1 = c.take<char>(plan.table_bytes);
-        *tab2 = c.take<char>(pmax.table_bytes);
+        for (int k = 0; k < 2; ++k) tab2[k] = c.take<char>(k < nbuf ? pmax.table_bytes : 0);
         *d = c.take<BatchDesc>((size_t)count);
         *sts = c.take<int>((size_t)count);
         *dshifted = c.take<int>((size_t)count);
@@ -854,22 +862,55 @@ oqr_status selector_waves(oqr_ctx* ctx, const SelInputs& I, const float* params,
         *choice = c.take<int>((size_t)count);
         *pool = c.take<double>(pool_doubles);
         *upool = c.take<double>((size_t)std::max(plan.upool_doubles, pmax.upool_doubles));
-        *scratch = c.take<char>(std::max(plan.scratch_bytes, pmax.scratch_bytes));
+        for (int k = 0; k < 2; ++k) scr[k] = c.take<char>(k < nbuf ? scratch_bytes : 0);
     };
-    char *tab1, *tab2;
+    char* tab1;
     BatchDesc* ddesc;
     int *sts, *dshifted, *dchoice;
     double *sums, *shifts, *orths, *pool, *upool;
     float* feat;
-    void* scratch;
     Carve probe(nullptr);
-    layout(probe, &tab1, &tab2, &ddesc, &sts, &dshifted, &sums, &shifts, &orths, &feat, &dchoice, &pool, &upool,
-           &scratch);
+    layout(probe, &tab1, &ddesc, &sts, &dshifted, &sums, &shifts, &orths, &feat, &dchoice, &pool, &upool);
     oqr_status v = ensure_ws(ctx, probe.off);
     if (v != OQR_OK) return v;
     Carve cv(ctx->ws);
-    layout(cv, &tab1, &tab2, &ddesc, &sts, &dshifted, &sums, &shifts, &orths, &feat, &dchoice, &pool, &upool,
-           &scratch);
+    layout(cv, &tab1, &ddesc, &sts, &dshifted, &sums, &shifts, &orths, &feat, &dchoice, &pool, &upool);
+    // pinned host memory: the choices and statuses read back per wave, two copies of the descriptors
+    // (the shifted refactor's and the final ones), the statuses and shift flags uploaded, and two table images
+    auto pin_layout = [&](Carve& c, BatchDesc** hdA, BatchDesc** hdB, int** hch, int** hst, int** hup, int** hsh,
+                          char** img0, char** img1) {
+        *hdA = c.take<BatchDesc>((size_t)count);
+        *hdB = c.take<BatchDesc>((size_t)count);
+        *hch = c.take<int>((size_t)count);
+        *hst = c.take<int>((size_t)count);
+        *hup = c.take<int>((size_t)count);
+        *hsh = c.take<int>((size_t)count);
+        *img0 = c.take<char>(pmax.table_bytes);
+        *img1 = c.take<char>(pmax.table_bytes);
+    };
+    BatchDesc *hdA, *hdB;
+    int *hch, *hst, *hup, *hsh;
+    char* img[2];
+    Carve pprobe(nullptr);
+    pin_layout(pprobe, &hdA, &hdB, &hch, &hst, &hup, &hsh, &img[0], &img[1]);
+    if (ctx->pin_bytes < pprobe.off) {
+        if (ctx->pin) {
+            cudaStreamSynchronize(s);
+            cudaFreeHost(ctx->pin);
+            ctx->pin = nullptr;
+            ctx->pin_bytes = 0;
+        }
+        if (cudaHostAlloc(&ctx->pin, pprobe.off, cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            return OQR_ERR_NO_MEMORY;
+        }
+        ctx->pin_bytes = pprobe.off;
+    }
+    for (int k = 0; k < 2; ++k)
+        if (!ctx->sel_ev[k] && cudaEventCreateWithFlags(&ctx->sel_ev[k], cudaEventDisableTiming) != cudaSuccess)
+            return OQR_ERR_CUDA;
+    Carve pc(ctx->pin);
+    pin_layout(pc, &hdA, &hdB, &hch, &hst, &hup, &hsh, &img[0], &img[1]);
     std::vector<BatchDesc> desc((size_t)count);
     std::vector<TcBatchIn> in((size_t)count);
     double* q = pool;
@@ -903,27 +944,47 @@ oqr_status selector_waves(oqr_ctx* ctx, const SelInputs& I, const float* params,
     OQR_TRY(cudaMemcpyAsync(ddesc, desc.data(), sizeof(BatchDesc) * count, cudaMemcpyHostToDevice, s));
     OQR_TRY(cudaMemsetAsync(sts, 0, sizeof(int) * count, s));
     if ((v = reset_status(ctx, s)) != OQR_OK) return v;
+    // the pageable uploads above must have left their staging before the host reuses these vectors
+    if (cudaStreamSynchronize(s) != cudaSuccess) return OQR_ERR_CUDA;
     const uint64_t limit = 4000000000ull;
-    std::vector<int> hst((size_t)count, 0), hch((size_t)count, 0), opt((size_t)count, 0), chk((size_t)count, 0);
-    for (int w = 0; w < (int)plan.waves.size(); ++w) {
-        const NvtxRange range("oqr: selector wave %d", w);
+    std::vector<int> opt((size_t)count, 0), chk((size_t)count, 0);
+    // the first pass of wave w: split of A into scratch w % nbuf, the FP64-accurate Gram of Z, its
+    // Cholesky factor (and Q_1), the features, the network, and the choices read back to pinned memory
+    auto first_pass = [&](int w) -> oqr_status {
         const TcBatchWave& W = plan.waves[w];
         const int f = W.first, cnt = W.count;
         BatchDesc* dw = ddesc + f;
         int* sw = sts + f;
+        void* scratch = scr[w % nbuf];
         OQR_TRY(tc_batch_split_a(plan, w, tab1, scratch, s));
         OQR_TRY(tc_batch_gram(plan, w, 0, tab1, scratch, ctx->st, limit, ctx->sm_count, s));
         if (features_only) OQR_TRY(launch_batched_gram_chol(dw, cnt, sw, s));
         else OQR_TRY(launch_batched_factor(dw, cnt, sw, 0, nullptr, s));
         OQR_TRY(launch_features_batched(dw, cnt, sw, feat + (size_t)f * MLP_IN, s));
-        if (features_only) continue;
+        if (features_only) return OQR_OK;
         OQR_TRY(launch_mlp_forward(cnt, feat + (size_t)f * MLP_IN, params, 1, nullptr, dchoice + f, s));
-        OQR_TRY(cudaMemcpyAsync(hch.data() + f, dchoice + f, sizeof(int) * cnt, cudaMemcpyDeviceToHost, s));
-        OQR_TRY(cudaMemcpyAsync(hst.data() + f, sw, sizeof(int) * cnt, cudaMemcpyDeviceToHost, s));
-        if (cudaStreamSynchronize(s) != cudaSuccess) return OQR_ERR_CUDA;
+        OQR_TRY(cudaMemcpyAsync(hch + f, dchoice + f, sizeof(int) * cnt, cudaMemcpyDeviceToHost, s));
+        OQR_TRY(cudaMemcpyAsync(hst + f, sw, sizeof(int) * cnt, cudaMemcpyDeviceToHost, s));
+        OQR_TRY(cudaEventRecord(ctx->sel_ev[w & 1], s));
+        return OQR_OK;
+    };
+    if (nw > 0 && (v = first_pass(0)) != OQR_OK) return v;
+    for (int w = 0; w < nw; ++w) {
+        const NvtxRange range("oqr: selector wave %d", w);
+        if (features_only) {
+            if (w + 1 < nw && (v = first_pass(w + 1)) != OQR_OK) return v;
+            continue;
+        }
+        // wave w + 1's first pass is queued before the host waits for wave w's choices
+        if (nbuf == 2 && w + 1 < nw && (v = first_pass(w + 1)) != OQR_OK) return v;
+        if (cudaEventSynchronize(ctx->sel_ev[w & 1]) != cudaSuccess) return OQR_ERR_CUDA;
+        const TcBatchWave& W = plan.waves[w];
+        const int f = W.first, cnt = W.count;
+        BatchDesc* dw = ddesc + f;
+        int* sw = sts + f;
+        void* scratch = scr[w % nbuf];
         // the option each instance finishes with, and its passes
         std::vector<TcBatchShape> sh2((size_t)cnt);
-        std::vector<int> shifted((size_t)cnt, 0);
         bool any_shift = false;
         for (int k = 0; k < cnt; ++k) {
             const int i = f + k;
@@ -933,49 +994,49 @@ oqr_status selector_waves(oqr_ctx* ctx, const SelInputs& I, const float* params,
             chk[i] = o == SEL_ONE || (check_all && o != SEL_FP64);
             const int np = o == SEL_ONE ? 1 : o == SEL_TWO ? 2 : o == SEL_SHIFTED ? 3 : 1;
             sh2[k] = TcBatchShape{sh1[i].m, sh1[i].n, 1, np + chk[i]};
-            shifted[k] = o == SEL_SHIFTED;
-            any_shift = any_shift || shifted[k];
-            desc[i].npass = shifted[k] ? 3 : 0;
+            hsh[i] = o == SEL_SHIFTED;
+            any_shift = any_shift || hsh[i];
+            hdA[i] = desc[i];
+            hdA[i].npass = hsh[i] ? 3 : 0;
+            hdB[i] = desc[i];
+            hdB[i].npass = np;
+            hup[i] = hsh[i] ? 0 : hst[i];
         }
         if (any_shift) {  // the shifted first pass from the same G0
-            for (int k = 0; k < cnt; ++k)
-                if (shifted[k]) hst[f + k] = 0;
-            OQR_TRY(cudaMemcpyAsync(dw, desc.data() + f, sizeof(BatchDesc) * cnt, cudaMemcpyHostToDevice, s));
-            OQR_TRY(cudaMemcpyAsync(sw, hst.data() + f, sizeof(int) * cnt, cudaMemcpyHostToDevice, s));
-            OQR_TRY(cudaMemcpyAsync(dshifted + f, shifted.data(), sizeof(int) * cnt, cudaMemcpyHostToDevice, s));
+            OQR_TRY(cudaMemcpyAsync(dw, hdA + f, sizeof(BatchDesc) * cnt, cudaMemcpyHostToDevice, s));
+            OQR_TRY(cudaMemcpyAsync(sw, hup + f, sizeof(int) * cnt, cudaMemcpyHostToDevice, s));
+            OQR_TRY(cudaMemcpyAsync(dshifted + f, hsh + f, sizeof(int) * cnt, cudaMemcpyHostToDevice, s));
             OQR_TRY(launch_batched_shifts(dw, cnt, dshifted + f, sums + 2 * f, 11.0, U64, shifts + f, s));
             OQR_TRY(launch_batched_factor(dw, cnt, sw, 0, shifts + f, s));
         }
-        for (int k = 0; k < cnt; ++k) desc[f + k].npass = sh2[k].npass - chk[f + k];
-        OQR_TRY(cudaMemcpyAsync(dw, desc.data() + f, sizeof(BatchDesc) * cnt, cudaMemcpyHostToDevice, s));
-        // the later passes of the wave, with tables for exactly this wave (same packing as the probe's)
+        OQR_TRY(cudaMemcpyAsync(dw, hdB + f, sizeof(BatchDesc) * cnt, cudaMemcpyHostToDevice, s));
+        // the later passes of the wave, with tables for exactly this wave (same packing as the first pass's)
         const std::vector<TcBatchIn> in2(in.begin() + f, in.begin() + f + cnt);
         const TcBatchPlan p2 = tc_batch_plan(sh2, budget);
-        if (p2.waves.size() != 1 || p2.table_bytes > pmax.table_bytes || p2.scratch_bytes > pmax.scratch_bytes)
+        if (p2.waves.size() != 1 || p2.table_bytes > pmax.table_bytes || p2.scratch_bytes > scratch_bytes)
             return OQR_ERR_UNSUPPORTED;
         std::vector<char> image2;
-        tc_batch_tables(p2, sh2, in2, tab2, upool, image2);
-        OQR_TRY(cudaMemcpyAsync(tab2, image2.data(), image2.size(), cudaMemcpyHostToDevice, s));
+        char* t2 = tab2[w % nbuf];
+        tc_batch_tables(p2, sh2, in2, t2, upool, image2);
+        memcpy(img[w & 1], image2.data(), image2.size());
+        OQR_TRY(cudaMemcpyAsync(t2, img[w & 1], image2.size(), cudaMemcpyHostToDevice, s));
         for (int pass = 1; pass < p2.waves[0].maxpass; ++pass) {
-            OQR_TRY(tc_batch_gram(p2, 0, pass, tab2, scratch, ctx->st, limit, ctx->sm_count, s));
+            OQR_TRY(tc_batch_gram(p2, 0, pass, t2, scratch, ctx->st, limit, ctx->sm_count, s));
             OQR_TRY(launch_batched_last_defect(dw, cnt, sw, pass, defects + f, s));
             OQR_TRY(launch_batched_factor(dw, cnt, sw, pass, nullptr, s));
             OQR_TRY(launch_batched_check(dw, cnt, sw, pass, orths + f, s));
         }
         OQR_TRY(launch_batched_rfinal(dw, cnt, sw, s));
-        // the host images must outlive their asynchronous copies
-        if (cudaStreamSynchronize(s) != cudaSuccess) return OQR_ERR_CUDA;
     }
     if (features_only) {
-        std::vector<int> hperm(perm);
-        int* dperm = dchoice;  // free by now: the permutation for the scatter
-        OQR_TRY(cudaMemcpyAsync(dperm, hperm.data(), sizeof(int) * count, cudaMemcpyHostToDevice, s));
-        OQR_TRY(launch_batch_scatter_rows_f32(feat, dperm, count, MLP_IN, feat_out, s));
+        OQR_TRY(cudaMemcpyAsync(dchoice, perm.data(), sizeof(int) * count, cudaMemcpyHostToDevice, s));
+        OQR_TRY(launch_batch_scatter_rows_f32(feat, dchoice, count, MLP_IN, feat_out, s));
         if (cudaStreamSynchronize(s) != cudaSuccess) return OQR_ERR_CUDA;
         return OQR_OK;
     }
     std::vector<double> hor((size_t)count), hdef((size_t)count);
-    OQR_TRY(cudaMemcpyAsync(hst.data(), sts, sizeof(int) * count, cudaMemcpyDeviceToHost, s));
+    std::vector<int> hfin((size_t)count);
+    OQR_TRY(cudaMemcpyAsync(hfin.data(), sts, sizeof(int) * count, cudaMemcpyDeviceToHost, s));
     OQR_TRY(cudaMemcpyAsync(hor.data(), orths, sizeof(double) * count, cudaMemcpyDeviceToHost, s));
     OQR_TRY(cudaMemcpyAsync(hdef.data(), defects, sizeof(double) * count, cudaMemcpyDeviceToHost, s));
     DevStatus hs;
@@ -986,14 +1047,13 @@ oqr_status selector_waves(oqr_ctx* ctx, const SelInputs& I, const float* params,
     res->orth.assign((size_t)count, std::nan(""));
     for (int i = 0; i < count; ++i) {
         const int b = perm[i];
-        res->status[b] = hs.code != 0 ? -1 : hst[i];
+        res->status[b] = hs.code != 0 ? -1 : hfin[i];
         res->choice[b] = opt[i];
-        if (chk[i]) res->orth[b] = hst[i] == 0 ? hor[i] : INFINITY;
+        if (chk[i]) res->orth[b] = hfin[i] == 0 ? hor[i] : INFINITY;
         // the free check of a two-pass result: the Gram its second pass factored was far from I, so that
         // pass did not bring the orthogonality to rounding level; the fallback chain redoes it (the shifted
         // option, the most robust, is accepted once it completes, as the network's answer for hard instances)
-        if (!chk[i] && opt[i] == SEL_TWO && hst[i] == 0 && !(hdef[i] <= LAST_DEFECT_MAX))
-            res->status[b] = -2;
+        if (!chk[i] && opt[i] == SEL_TWO && hfin[i] == 0 && !(hdef[i] <= LAST_DEFECT_MAX)) res->status[b] = -2;
     }
     return hs.code != 0 ? OQR_ERR_TIMEOUT : OQR_OK;
 }
@@ -1145,6 +1205,9 @@ oqr_status oqr_destroy(oqr_ctx* ctx)
     if (ctx->mixed_exec) cudaGraphExecDestroy(ctx->mixed_exec);
     if (ctx->stage) cudaFree(ctx->stage);
     if (ctx->sel_buf) cudaFree(ctx->sel_buf);
+    if (ctx->pin) cudaFreeHost(ctx->pin);
+    for (cudaEvent_t e : ctx->sel_ev)
+        if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
     if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
     if (ctx->ws && ctx->ws_owned) cudaFree(ctx->ws);
