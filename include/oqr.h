@@ -183,10 +183,11 @@ oqr_status oqr_cholqr2(oqr_ctx* ctx, int m, int n, const double* A, long lda, co
 /*
  * A-CGS2: classical Gram-Schmidt with reorthogonalisation in the A inner
  * product (Sec. 6, Thm 6.4), in block form with column blocks of
- * opts->block columns.  For each block Z_j: S_j = A Z_j; twice
- * { r = (A Q)^T Z_j; Z_j -= Q r; S_j -= (A Q) r; R(<j, j) += r };
- * then A-CholQR2 of the block against S_j; A Q is kept so that each block
- * costs one product with A.  Needs an extra m x n of workspace for A Q.
+ * opts->block columns.  For each block Z_j: twice
+ * { r = (A Q)^T Z_j; Z_j -= Q r; R(<j, j) += r }; then S_j = A Z_j of the
+ * projected block and A-CholQR2 of the block against S_j, whose solves give
+ * the block's A Q; A Q is kept so that each block costs one product with A.
+ * Needs an extra m x n of workspace for A Q.
  */
 /*
  * oqr_cholqr2_host: oqr_cholqr2 with A, Z, Q and R in HOST memory (column-major,

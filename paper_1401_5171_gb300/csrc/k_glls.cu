@@ -1,7 +1,10 @@
 // The generalized least-squares solve of Sec. 1, x = R^{-1} Q^T A b, and its
 // product with A: C = A B for a symmetric A read from its lower triangle.
 //
-// C = A B is the HBM-bound step (A is m^2/2 doubles, B only m x k): A's lower
+// C = A B reads A's lower triangle (m^2/2 doubles) once per group of right-hand
+// sides, with two FP64 FMAs per stored element and right-hand side; on GB300
+// (about 0.19 flop per byte of HBM bandwidth at FP64) those FMAs, not HBM, bound
+// it even for one right-hand side.  A's lower
 // triangle is cut into 64 x 64 tiles (I, J), I >= J, each read from memory
 // exactly once.  With M = tril(A, -1) + diag(A)/2, A = M + M^T, and tile (I, J)
 // of M contributes M_IJ B_J to block row I of C and M_IJ^T B_I to block row J.
@@ -32,19 +35,23 @@ __device__ inline void tile_of(long t, int* I, int* J)
 
 __device__ inline long tile_index(int I, int J) { return (long)I * (I + 1) / 2 + J; }
 
-// part: per tile, a row partial (M_IJ B_J, 64 x kc) then a column partial (M_IJ^T B_I, 64 x kc),
-// each element (r, kk) at r * kc + kk.
-__global__ void __launch_bounds__(SY_THREADS) symm_tiles_kernel(int m, int kc, const double* __restrict__ A, long lda,
+// part: per tile, a row partial (M_IJ B_J, 64 x KC) then a column partial (M_IJ^T B_I, 64 x KC),
+// each element (r, kk) at r * KC + kk.  KC is the exact number of right-hand sides of the launch: on
+// GB300 the FP64 FMAs (two per stored element and right-hand side), not HBM, bound this kernel.
+template <int KC>
+__global__ void __launch_bounds__(SY_THREADS) symm_tiles_kernel(int m, const double* __restrict__ A, long lda,
                                                                  const double* __restrict__ B, long ldb,
                                                                  double* __restrict__ part, long ntiles)
 {
     __shared__ double tile[SY_T * SY_LD];
-    __shared__ double bI[SY_T * SY_KMAX], bJ[SY_T * SY_KMAX];
-    __shared__ double red[4][SY_T * SY_KMAX];
+    __shared__ double bI[SY_T * KC], bJ[SY_T * KC];
+    __shared__ double red[4][SY_T * KC];
+    __shared__ int tij[2];
     const int tid = threadIdx.x;
     for (long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        int I, J;
-        tile_of(t, &I, &J);
+        if (tid == 0) tile_of(t, &tij[0], &tij[1]);
+        __syncthreads();
+        const int I = tij[0], J = tij[1];
         const long r0 = (long)I * SY_T, c0 = (long)J * SY_T;
         // the tile of M: below the diagonal as stored, the diagonal halved, zero above it and past m
         double v[SY_T * SY_T / SY_THREADS];
@@ -59,49 +66,40 @@ __global__ void __launch_bounds__(SY_THREADS) symm_tiles_kernel(int m, int kc, c
             const int e = tid + q * SY_THREADS, r = e % SY_T, c = e / SY_T;
             tile[r + c * SY_LD] = (r0 + r == c0 + c) ? 0.5 * v[q] : v[q];
         }
-        for (int e = tid; e < SY_T * kc; e += SY_THREADS) {
+        for (int e = tid; e < SY_T * KC; e += SY_THREADS) {
             const int r = e % SY_T, kk = e / SY_T;
-            bI[r * SY_KMAX + kk] = r0 + r < m ? B[r0 + r + kk * ldb] : 0.0;
-            bJ[r * SY_KMAX + kk] = c0 + r < m ? B[c0 + r + kk * ldb] : 0.0;
+            bI[r * KC + kk] = r0 + r < m ? B[r0 + r + kk * ldb] : 0.0;
+            bJ[r * KC + kk] = c0 + r < m ? B[c0 + r + kk * ldb] : 0.0;
         }
         __syncthreads();
         const int x = tid % SY_T, q = tid / SY_T;  // a row (or column) of the tile, a quarter of the other axis
-        double acc[SY_KMAX];
-        // row partial: sum over the quarter's columns of M(x, c) B_J(c)
+        double acc[KC], acc2[KC];
 #pragma unroll
-        for (int kk = 0; kk < SY_KMAX; ++kk) acc[kk] = 0.0;
+        for (int kk = 0; kk < KC; ++kk) acc[kk] = acc2[kk] = 0.0;
+        // row partial: sum over the quarter's columns of M(x, c) B_J(c); column partial: over its rows of
+        // M(r, x) B_I(r)
+#pragma unroll 4
         for (int c = q * 16; c < q * 16 + 16; ++c) {
-            const double a = tile[x + c * SY_LD];
+            const double a = tile[x + c * SY_LD], at = tile[c + x * SY_LD];
 #pragma unroll
-            for (int kk = 0; kk < SY_KMAX; ++kk) acc[kk] = fma(a, bJ[c * SY_KMAX + kk], acc[kk]);
+            for (int kk = 0; kk < KC; ++kk) {
+                acc[kk] = fma(a, bJ[c * KC + kk], acc[kk]);
+                acc2[kk] = fma(at, bI[c * KC + kk], acc2[kk]);
+            }
         }
 #pragma unroll
-        for (int kk = 0; kk < SY_KMAX; ++kk) red[q][x * SY_KMAX + kk] = acc[kk];
+        for (int kk = 0; kk < KC; ++kk) red[q][x * KC + kk] = acc[kk];
         __syncthreads();
-        double* prow = part + (size_t)(2 * t) * SY_T * kc;
-        for (int e = tid; e < SY_T * kc; e += SY_THREADS) {
-            const int r = e / kc, kk = e % kc;
-            prow[e] = ((red[0][r * SY_KMAX + kk] + red[1][r * SY_KMAX + kk]) + red[2][r * SY_KMAX + kk]) +
-                      red[3][r * SY_KMAX + kk];
-        }
+        double* prow = part + (size_t)(2 * t) * SY_T * KC;
+        for (int e = tid; e < SY_T * KC; e += SY_THREADS)
+            prow[e] = ((red[0][e] + red[1][e]) + red[2][e]) + red[3][e];
         __syncthreads();
-        // column partial: sum over the quarter's rows of M(r, x) B_I(r)
 #pragma unroll
-        for (int kk = 0; kk < SY_KMAX; ++kk) acc[kk] = 0.0;
-        for (int r = q * 16; r < q * 16 + 16; ++r) {
-            const double a = tile[r + x * SY_LD];
-#pragma unroll
-            for (int kk = 0; kk < SY_KMAX; ++kk) acc[kk] = fma(a, bI[r * SY_KMAX + kk], acc[kk]);
-        }
-#pragma unroll
-        for (int kk = 0; kk < SY_KMAX; ++kk) red[q][x * SY_KMAX + kk] = acc[kk];
+        for (int kk = 0; kk < KC; ++kk) red[q][x * KC + kk] = acc2[kk];
         __syncthreads();
-        double* pcol = prow + SY_T * kc;
-        for (int e = tid; e < SY_T * kc; e += SY_THREADS) {
-            const int r = e / kc, kk = e % kc;
-            pcol[e] = ((red[0][r * SY_KMAX + kk] + red[1][r * SY_KMAX + kk]) + red[2][r * SY_KMAX + kk]) +
-                      red[3][r * SY_KMAX + kk];
-        }
+        double* pcol = prow + SY_T * KC;
+        for (int e = tid; e < SY_T * KC; e += SY_THREADS)
+            pcol[e] = ((red[0][e] + red[1][e]) + red[2][e]) + red[3][e];
         __syncthreads();  // the tile, bI, bJ and red are rewritten by the next tile
     }
 }
@@ -160,7 +158,17 @@ cudaError_t launch_symm(int m, int k, const double* A, long lda, const double* B
     const long grid = ntiles < 4L * sms ? ntiles : 4L * sms;
     for (int k0 = 0; k0 < k; k0 += SY_KMAX) {
         const int kc = k - k0 < SY_KMAX ? k - k0 : SY_KMAX;
-        symm_tiles_kernel<<<(unsigned)grid, SY_THREADS, 0, s>>>(m, kc, A, lda, B + (long)k0 * ldb, ldb, part, ntiles);
+        const double* Bk = B + (long)k0 * ldb;
+        switch (kc) {
+            case 1: symm_tiles_kernel<1><<<(unsigned)grid, SY_THREADS, 0, s>>>(m, A, lda, Bk, ldb, part, ntiles); break;
+            case 2: symm_tiles_kernel<2><<<(unsigned)grid, SY_THREADS, 0, s>>>(m, A, lda, Bk, ldb, part, ntiles); break;
+            case 3: symm_tiles_kernel<3><<<(unsigned)grid, SY_THREADS, 0, s>>>(m, A, lda, Bk, ldb, part, ntiles); break;
+            case 4: symm_tiles_kernel<4><<<(unsigned)grid, SY_THREADS, 0, s>>>(m, A, lda, Bk, ldb, part, ntiles); break;
+            case 5: symm_tiles_kernel<5><<<(unsigned)grid, SY_THREADS, 0, s>>>(m, A, lda, Bk, ldb, part, ntiles); break;
+            case 6: symm_tiles_kernel<6><<<(unsigned)grid, SY_THREADS, 0, s>>>(m, A, lda, Bk, ldb, part, ntiles); break;
+            case 7: symm_tiles_kernel<7><<<(unsigned)grid, SY_THREADS, 0, s>>>(m, A, lda, Bk, ldb, part, ntiles); break;
+            default: symm_tiles_kernel<8><<<(unsigned)grid, SY_THREADS, 0, s>>>(m, A, lda, Bk, ldb, part, ntiles); break;
+        }
         const long tot = (long)m * kc;
         symm_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(m, kc, nb, part, C + (long)k0 * ldc, ldc);
     }

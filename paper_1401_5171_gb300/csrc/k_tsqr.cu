@@ -45,11 +45,13 @@ __device__ inline double ts_block_sum(double v, double* red)
 // fixed enumeration k = 0, 1, ...: dense blocks all rows j+1 .. rows-1;
 // stacked triangles (kids > 1 children of n rows each) rows c n + r for
 // c = 1 .. kids-1, r = 0 .. j.
+// A stacked node has at most three children, so row k of the enumeration is
+// n + k for the second child and 2 n + (k - j - 1) for the third.
 struct Active {
     bool tri;
     int rows, n, j, kids;
-    __device__ long count() const { return tri ? (long)(kids - 1) * (j + 1) : (long)(rows - j - 1); }
-    __device__ long row(long k) const { return tri ? (long)(1 + k / (j + 1)) * n + k % (j + 1) : j + 1 + k; }
+    __device__ int count() const { return tri ? (kids - 1) * (j + 1) : rows - j - 1; }
+    __device__ int row(int k) const { return tri ? (k <= j ? n + k : 2 * n + (k - j - 1)) : j + 1 + k; }
 };
 
 // Block geometry of node t at a level: leaves (tri = false) of b0 rows (the
@@ -88,9 +90,9 @@ __global__ void __launch_bounds__(TS_THREADS) tsqr_factor_kernel(double* V, long
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     for (int j = 0; j < n; ++j) {
         const Active act{tri != 0, g.rows, n, j, g.kids};
-        const long na = act.count();
+        const int na = act.count();
         double s = 0.0;
-        for (long k = tid; k < na; k += TS_THREADS) {
+        for (int k = tid; k < na; k += TS_THREADS) {
             const double x = X[act.row(k) + (long)j * ld];
             s = fma(x, x, s);
         }
@@ -104,19 +106,19 @@ __global__ void __launch_bounds__(TS_THREADS) tsqr_factor_kernel(double* V, long
             scale = 1.0 / (alpha - beta);
         }
         if (sigma2 > 0.0)
-            for (long k = tid; k < na; k += TS_THREADS) X[act.row(k) + (long)j * ld] *= scale;  // v below row j
+            for (int k = tid; k < na; k += TS_THREADS) X[act.row(k) + (long)j * ld] *= scale;  // v below row j
         __syncthreads();
         if (sigma2 > 0.0) {
             // trailing columns: w = x_j + v^T x, then x_j -= tau w, x -= tau w v (one warp per column)
             for (int c = j + 1 + warp; c < n; c += TS_WARPS) {
                 double* xc = X + (long)c * ld;
                 double w = 0.0;
-                for (long k = lane; k < na; k += 32) w = fma(X[act.row(k) + (long)j * ld], xc[act.row(k)], w);
+                for (int k = lane; k < na; k += 32) w = fma(X[act.row(k) + (long)j * ld], xc[act.row(k)], w);
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
                 w += xc[j];
                 const double tw = tj * w;
-                for (long k = lane; k < na; k += 32) xc[act.row(k)] = fma(-tw, X[act.row(k) + (long)j * ld], xc[act.row(k)]);
+                for (int k = lane; k < na; k += 32) xc[act.row(k)] = fma(-tw, X[act.row(k) + (long)j * ld], xc[act.row(k)]);
                 if (lane == 0) xc[j] -= tw;
             }
         }
@@ -174,16 +176,16 @@ __global__ void __launch_bounds__(TS_THREADS) tsqr_apply_kernel(const double* V,
         const double tj = tau[(long)t * n + j];
         if (tj != 0.0) {
             const Active act{tri != 0, g.rows, n, j, g.kids};
-            const long na = act.count();
+            const int na = act.count();
             for (int c = warp; c < n; c += TS_WARPS) {
                 double* yc = Yt + (long)c * ldy;
                 double w = 0.0;
-                for (long k = lane; k < na; k += 32) w = fma(Vt[act.row(k) + (long)j * ld], yc[act.row(k)], w);
+                for (int k = lane; k < na; k += 32) w = fma(Vt[act.row(k) + (long)j * ld], yc[act.row(k)], w);
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
                 w += yc[j];
                 const double tw = tj * w;
-                for (long k = lane; k < na; k += 32) yc[act.row(k)] = fma(-tw, Vt[act.row(k) + (long)j * ld], yc[act.row(k)]);
+                for (int k = lane; k < na; k += 32) yc[act.row(k)] = fma(-tw, Vt[act.row(k) + (long)j * ld], yc[act.row(k)]);
                 if (lane == 0) yc[j] -= tw;
             }
         }

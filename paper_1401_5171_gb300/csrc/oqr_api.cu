@@ -605,16 +605,17 @@ oqr_status cgs2_impl(oqr_ctx* ctx, int m, int n, const double* A, long lda, cons
     for (int j0 = 0; j0 < n; j0 += b) {
         const int bj = std::min(b, n - j0);
         double* Zj = Q + (size_t)j0 * ldq;
-        // S = A Z_j (symmetric A from its lower triangle)
-        OQR_TRY(launch_gemm_f64(GEMM_SYML, m, bj, m, 1.0, A, lda, Zj, ldq, 0.0, L.S, m, nullptr, 1, s));
         for (int sweep = 0; sweep < 2 && j0 > 0; ++sweep) {
             const int sp = splits_for(j0, bj);
-            // r = (A Q)^T Z_j ; Z_j -= Q r ; S -= (A Q) r ; R(:j0, block) += r
+            // r = (A Q)^T Z_j ; Z_j -= Q r ; R(:j0, block) += r
             OQR_TRY(launch_gemm_f64(GEMM_T, j0, bj, m, 1.0, L.AQ, m, Zj, ldq, 0.0, L.r, n, L.sk, sp, s));
             OQR_TRY(launch_gemm_f64(GEMM_N, m, bj, j0, -1.0, Q, ldq, L.r, n, 1.0, Zj, ldq, nullptr, 1, s));
-            OQR_TRY(launch_gemm_f64(GEMM_N, m, bj, j0, -1.0, L.AQ, m, L.r, n, 1.0, L.S, m, nullptr, 1, s));
             OQR_TRY(launch_axpby(j0, bj, 1.0, L.r, n, 1.0, R + (size_t)j0 * ldr, ldr, s));
         }
+        // S = A Z_j of the projected block, formed afresh (symmetric A from its lower triangle): updating an
+        // earlier A Z_j by the projections would cancel, with an error growing like kappa(Z), when the
+        // projected block is much smaller than the original one
+        OQR_TRY(launch_gemm_f64(GEMM_SYML, m, bj, m, 1.0, A, lda, Zj, ldq, 0.0, L.S, m, nullptr, 1, s));
         // A-CholQR2 of the block against S = A Z_j
         const int sp = splits_for(bj, bj);
         for (int pass = 0; pass < 2; ++pass) {

@@ -312,3 +312,26 @@ def test_precholqr_in_place_and_tridiagonal(env):
     assert st == 0
     assert np.linalg.norm(R - Rr) / np.linalg.norm(Rr) <= max(1e-12, 100 * U * np.linalg.cond(Rr))
     assert oracle.orth_error_tridiag(d, e, Q) <= max(1e-12, 100 * oracle.orth_error_tridiag(d, e, Qr))
+
+
+# ---------------------------------------------------------- A-CGS2 at full size --
+def test_cgs2_full_size_stable_in_kappa_z(env):
+    """Block A-CGS2 at m = 32768, n = 256, kappa(A) = 1e6, kappa(Z) = 1e8 (config 1's hardest cell): Thm 6.4
+    bounds its loss of orthogonality by c m^{3/2} n u ||A|| ||Q||^2, independent of kappa(Z), as A-CholQR2's;
+    held to 10x A-CholQR2's orthogonality on the same instance (both measured by torch's FP64 GEMMs)."""
+    torch, oqr, ctx = env
+    m, n = 32768, 256
+    Af, _ = inputs.dense_spd(m, 1e6, seed=301, device="cuda")
+    A = oqr.colmajor(Af)
+    Z = oqr.colmajor(inputs.tall_z(m, n, 1e8, seed=311, device="cuda"))
+    orth = {}
+    for name in ("oqr_cholqr2", "oqr_cgs2"):
+        Q, R, (st, _) = getattr(ctx, name)(A, Z)
+        assert st == 0
+        E = Q.T @ (Af @ Q) - torch.eye(n, dtype=torch.float64, device="cuda")
+        orth[name] = torch.linalg.eigvalsh(0.5 * (E + E.T)).abs().max().item()
+        rep = (torch.linalg.matrix_norm(Z - Q @ R, 2) / torch.linalg.matrix_norm(Z, 2)).item()
+        assert rep <= 1e-13, (name, rep)
+    assert orth["oqr_cgs2"] <= max(1e-12, 10 * orth["oqr_cholqr2"]), orth
+    del Af, A
+    torch.cuda.empty_cache()
