@@ -518,15 +518,16 @@ def run_next_paths(ctx, torch, dev, A, Z, stream, m, n, peaks):
 
 
 def run_sweep(ctx, torch, dev, m, ns, kappas, seed=301):
-    """Config 1's sweep at m (default 32768), kappa(A) = 1e6: for every n and kappa(Z), A-CholQR2 (FP64 and
-    mixed TC2 -> FP64_TC), shifted A-CholQR3 (FP64 and all FP64-accurate on the tensor cores) and block
-    A-CGS2, with ||Q^T A Q - I||_2 and ||Z - Q R||_2 / ||Z||_2 measured by torch's FP64 GEMMs and
+    """Config 1's sweep at m (default 32768), kappa(A) = 1e6: for every n and kappa(Z), A-CholQR2 (FP64, mixed
+    TC2 -> FP64_TC, and both passes FP64-accurate on the tensor cores), shifted A-CholQR3 (FP64 and all
+    FP64-accurate on the tensor cores), PRE-CHOLQR and block A-CGS2, with ||Q^T A Q - I||_2 and ||Z - Q R||_2 / ||Z||_2 measured by torch's FP64 GEMMs and
     eigensolver (Sec. 7's two measures), and the time of each.  One JSON line per cell."""
     from paper_1401_5171_gb300 import inputs, oqr
     Af, _ = inputs.dense_spd(m, 1e6, seed=seed, device=dev)
     A = oqr.colmajor(Af)
     stream = torch.cuda.current_stream(dev)
     methods = (("cholqr2_fp64", "oqr_cholqr2", {}), ("cholqr2_mixed", "oqr_cholqr2", {"prec": 4, "final_prec": 3}),
+               ("cholqr2_fp64tc", "oqr_cholqr2", {"prec": 3, "final_prec": 3}),
                ("scholqr3_fp64", "oqr_cholqr2", {"shifted": 1}),
                ("scholqr3_fp64tc", "oqr_cholqr2", {"shifted": 1, "prec": 3, "prec_mid": 3, "final_prec": 3}),
                ("cgs2_fp64", "oqr_cgs2", {}), ("precholqr_fp64tc", "oqr_precholqr", {"final_prec": 3}))

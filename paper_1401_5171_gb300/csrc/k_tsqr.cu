@@ -78,6 +78,48 @@ __device__ inline Geo node_geo(int t, int count_below, int n)
     return g;
 }
 
+// Columns c0 .. n-1 of X (ld) -= tau (x_jc + v^T x_c) v for the reflector of
+// column j (v_j = 1 at row j, the active rows below it in v, a column of the
+// factored block).  Each warp takes its columns CG at a time, so that CG
+// columns' loads are in flight together (the block is in L2, and one column
+// at a time leaves the warp waiting on two round trips per column).
+constexpr int CG = 4;
+__device__ inline void apply_reflector(double* X, long ld, const double* v, const Active& act, double tj, int c0,
+                                       int n, int warp, int lane)
+{
+    const int na = act.count(), j = act.j;
+    for (int cb = c0 + warp * CG; cb < n; cb += TS_WARPS * CG) {
+        double w[CG];
+#pragma unroll
+        for (int u = 0; u < CG; ++u) w[u] = 0.0;
+        for (int k = lane; k < na; k += 32) {
+            const int r = act.row(k);
+            const double vr = v[r];
+#pragma unroll
+            for (int u = 0; u < CG; ++u)
+                if (cb + u < n) w[u] = fma(vr, X[r + (long)(cb + u) * ld], w[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < CG; ++u) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) w[u] += __shfl_xor_sync(0xffffffffu, w[u], o);
+            if (cb + u < n) w[u] = tj * (w[u] + X[j + (long)(cb + u) * ld]);
+        }
+        for (int k = lane; k < na; k += 32) {
+            const int r = act.row(k);
+            const double vr = v[r];
+#pragma unroll
+            for (int u = 0; u < CG; ++u)
+                if (cb + u < n) X[r + (long)(cb + u) * ld] = fma(-w[u], vr, X[r + (long)(cb + u) * ld]);
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int u = 0; u < CG; ++u)
+                if (cb + u < n) X[j + (long)(cb + u) * ld] -= w[u];
+        }
+    }
+}
+
 // Householder QR of each block of a level, in place.
 __global__ void __launch_bounds__(TS_THREADS) tsqr_factor_kernel(double* V, long ld, int n, int count, int m, int b0,
                                                                  int tri, int count_below, double* tau)
@@ -108,20 +150,8 @@ __global__ void __launch_bounds__(TS_THREADS) tsqr_factor_kernel(double* V, long
         if (sigma2 > 0.0)
             for (int k = tid; k < na; k += TS_THREADS) X[act.row(k) + (long)j * ld] *= scale;  // v below row j
         __syncthreads();
-        if (sigma2 > 0.0) {
-            // trailing columns: w = x_j + v^T x, then x_j -= tau w, x -= tau w v (one warp per column)
-            for (int c = j + 1 + warp; c < n; c += TS_WARPS) {
-                double* xc = X + (long)c * ld;
-                double w = 0.0;
-                for (int k = lane; k < na; k += 32) w = fma(X[act.row(k) + (long)j * ld], xc[act.row(k)], w);
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-                w += xc[j];
-                const double tw = tj * w;
-                for (int k = lane; k < na; k += 32) xc[act.row(k)] = fma(-tw, X[act.row(k) + (long)j * ld], xc[act.row(k)]);
-                if (lane == 0) xc[j] -= tw;
-            }
-        }
+        if (sigma2 > 0.0)  // trailing columns: x_c -= tau (x_jc + v^T x_c) v, with v_j = 1
+            apply_reflector(X, ld, X + (long)j * ld, act, tj, j + 1, n, warp, lane);
         if (tid == 0) {
             X[j + (long)j * ld] = beta;
             tau[(long)t * n + j] = tj;
@@ -176,18 +206,7 @@ __global__ void __launch_bounds__(TS_THREADS) tsqr_apply_kernel(const double* V,
         const double tj = tau[(long)t * n + j];
         if (tj != 0.0) {
             const Active act{tri != 0, g.rows, n, j, g.kids};
-            const int na = act.count();
-            for (int c = warp; c < n; c += TS_WARPS) {
-                double* yc = Yt + (long)c * ldy;
-                double w = 0.0;
-                for (int k = lane; k < na; k += 32) w = fma(Vt[act.row(k) + (long)j * ld], yc[act.row(k)], w);
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-                w += yc[j];
-                const double tw = tj * w;
-                for (int k = lane; k < na; k += 32) yc[act.row(k)] = fma(-tw, Vt[act.row(k) + (long)j * ld], yc[act.row(k)]);
-                if (lane == 0) yc[j] -= tw;
-            }
+            apply_reflector(Yt, ldy, Vt + (long)j * ld, act, tj, 0, n, warp, lane);
         }
         __syncthreads();
     }
