@@ -405,13 +405,18 @@ def run_selector(ctx, torch, dev, count, stream):
     As, Zs, tab = selector.batch(count, seed=4343, device=dev, m_range=(64, 4096))
     out = {"instances": count, "recipe": "m ~ U[64, 4096], n ~ U[4, 64], kappa(A) log-uniform in [1, 1e6], "
                                          "kappa(Z) log-uniform in [1, 1e12], seed 4343"}
-    res = {}
+    # outputs allocated once, outside the timing, for every policy
+    Qs = [oqr.empty_colmajor(z.shape[0], z.shape[1], dev) for z in Zs]
+    Rs = [oqr.empty_colmajor(z.shape[1], z.shape[1], dev) for z in Zs]
+    st = torch.empty(count, dtype=torch.int32, device=dev)
+    orth = torch.empty(count, dtype=torch.float64, device=dev)
+    choice = torch.empty(count, dtype=torch.int32, device=dev)
 
     def sel():
-        res["r"] = selector.solve_batch(ctx, As, Zs, P, stream=stream)
+        ctx.oqr_batched(As, Zs, Qs, Rs, status=st, mode=oqr.OQR_BATCHED_SELECTOR, params=P, orth=orth,
+                        choice=choice, stream=stream)
 
     t_sel = events_ms(torch, stream, sel)
-    Qs, Rs, st, orth, choice = res["r"]
     stc = st.cpu().numpy()
     raw = selector.choose(ctx, ctx.oqr_batched_features(As, Zs), P).cpu().numpy()   # the network's own choices
     final = choice.cpu().numpy()
@@ -427,16 +432,18 @@ def run_selector(ctx, torch, dev, count, stream):
         bar = max(1e-12, Zs[b].shape[0] * 2.0 ** -53 * float(tab["kappa_A"][b]) * qn * qn)
         worst = max(worst, o / bar)
         above += o > bar
-    t_shift = events_ms(torch, stream, lambda: ctx.oqr_batched(As, Zs, mode=oqr.OQR_BATCHED_SHIFTED_TC,
-                                                                  stream=stream))
+    st2 = torch.empty(count, dtype=torch.int32, device=dev)
+    t_shift = events_ms(torch, stream, lambda: ctx.oqr_batched(As, Zs, Qs, Rs, status=st2,
+                                                                  mode=oqr.OQR_BATCHED_SHIFTED_TC, stream=stream))
 
     def cholqr2_checked():
-        _, _, st2, o2 = ctx.oqr_batched_mixed(As, Zs, program=[2] * count, check=True, stream=stream)
+        _, _, st2, o2 = ctx.oqr_batched_mixed(As, Zs, program=[2] * count, Qs=Qs, Rs=Rs, check=True,
+                                              stream=stream)
         s2, oo = st2.cpu().numpy(), o2.cpu().numpy()
         fail = [b for b in range(count) if s2[b] != 0 or not (oo[b] <= 1e-12)]
         if fail:
             ctx.oqr_batched_mixed([As[b] for b in fail], [Zs[b] for b in fail], program=[3] * len(fail),
-                                  check=True, stream=stream)
+                                  Qs=[Qs[b] for b in fail], Rs=[Rs[b] for b in fail], check=True, stream=stream)
 
     t_c2 = events_ms(torch, stream, cholqr2_checked)
     out.update({"qr_per_s": count / (t_sel / 1e3), "ms_per_batch": t_sel,

@@ -17,7 +17,7 @@
 // 1 to 3 passes per instance (BatchDesc.npass; instances whose passes are done
 // sit later passes out): reduce (+ s_b I on a shifted first pass), potrf,
 // trsm, racc_batched (R1 <- R2 R1 after every later pass), rfinal_batched
-// (the caller's R = R1), norms/shift_batched (the first pass's shift) and
+// (the caller's R = R1), shift_batched (the first pass's shift, ||A||_F from the split) and
 // check_batched (||Q^T A Q - I||_2 from one more Gram of Q).
 // A Cholesky breakdown is recorded in the instance's own status word and that
 // instance's later kernels skip it; other instances are unaffected.
@@ -167,14 +167,25 @@ __global__ void reduce_batched_kernel(const BatchDesc* __restrict__ d, const int
 
 // One CTA per instance: R = chol(G), G n x n (n <= 64) in shared memory,
 // right-looking, column by column.  Writes R (upper, zeros below) into Rout.
+// mask (or NULL for all): the instances to factor.  Per column j: the row
+// R(j, j+1:n) = S(j, j+1:n) / R(j, j) into srow, then the trailing update of
+// the upper triangle over its pairs (r, c), j < r <= c, read from a table
+// built once per block.  Thread 0 owns the first pair, (j+1, j+1), so it
+// takes the next pivot (1 / sqrt by FP64 rsqrt, the diagonal as pivot times
+// that) while the other threads finish the update: two block barriers per
+// column.
+constexpr int POTRF_PAIRS = 63 * 64 / 2;
 __global__ void __launch_bounds__(256) potrf_batched_kernel(const BatchDesc* __restrict__ d, int* status, int which,
-                                                            int pass)
+                                                            int pass, const int* mask = nullptr)
 {
     __shared__ double S[64][65];
+    __shared__ double srow[64];
+    __shared__ unsigned short pair[POTRF_PAIRS];  // (r' << 8) | c', r' <= c': the trailing triangle column by column
+    __shared__ double rinv_s;
     __shared__ int broke;
     const int b = blockIdx.x;
     const BatchDesc D = d[b];
-    if (status[b] != 0 || pass >= D.npass) return;
+    if (status[b] != 0 || pass >= D.npass || (mask && !mask[b])) return;
     const int n = D.n;
     double* Rout = which == 0 ? D.R1 : D.R2;
     const int tid = threadIdx.x;
@@ -182,35 +193,43 @@ __global__ void __launch_bounds__(256) potrf_batched_kernel(const BatchDesc* __r
         const int i = e % n, j = e / n;
         S[i][j] = (i <= j) ? D.G[j + (size_t)i * n] : 0.0;  // lower triangle of G -> upper of S
     }
-    __shared__ double rinv;
-    if (tid == 0) broke = 0;
+    for (int e = tid; e < POTRF_PAIRS; e += 256) {
+        int c = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+        while (c * (c + 1) / 2 > e) --c;
+        while ((c + 1) * (c + 2) / 2 <= e) ++c;
+        pair[e] = (unsigned short)(((e - c * (c + 1) / 2) << 8) | c);
+    }
+    auto pivot = [&](int j) {  // thread 0
+        const double piv = S[j][j];
+        if (!(piv > 0.0)) {
+            broke = j + 1;
+        } else {
+            const double r = rsqrt(piv);
+            S[j][j] = piv * r;
+            rinv_s = r;
+        }
+    };
+    __syncthreads();
+    if (tid == 0) {
+        broke = 0;
+        pivot(0);
+    }
     __syncthreads();
     for (int j = 0; j < n; ++j) {
-        // one thread takes the pivot's square root and reciprocal (FP64 is scarce: not once per thread)
-        if (tid == 0) {
-            const double piv = S[j][j];
-            if (!(piv > 0.0)) {
-                broke = j + 1;
-            } else {
-                const double dj = sqrt(piv);
-                S[j][j] = dj;
-                rinv = 1.0 / dj;
-            }
+        if (broke) break;
+        const double rj = rinv_s;
+        for (int c = j + 1 + tid; c < n; c += 256) {
+            const double v = S[j][c] * rj;
+            srow[c] = v;
+            S[j][c] = v;
         }
         __syncthreads();
-        if (broke) break;
-        const double rj = rinv;
-        for (int c = j + 1 + tid; c < n; c += 256) S[j][c] *= rj;
-        __syncthreads();
-        // trailing update of the upper triangle, its w (w + 1) / 2 pairs (r <= c) enumerated densely:
-        // pair e is column c' = max{c : c (c + 1) / 2 <= e}, row r' = e - c' (c' + 1) / 2
         const int w = n - j - 1;
         for (int e = tid; e < w * (w + 1) / 2; e += 256) {
-            int cp = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
-            while (cp * (cp + 1) / 2 > e) --cp;
-            while ((cp + 1) * (cp + 2) / 2 <= e) ++cp;
-            const int r = j + 1 + (e - cp * (cp + 1) / 2), c = j + 1 + cp;
-            S[r][c] -= S[j][r] * S[j][c];
+            const int p = pair[e];
+            const int r = j + 1 + (p >> 8), c = j + 1 + (p & 255);
+            S[r][c] = fma(-srow[r], srow[c], S[r][c]);
+            if (e == 0) pivot(j + 1);  // thread 0, pair (j+1, j+1)
         }
         __syncthreads();
     }
@@ -225,14 +244,16 @@ __global__ void __launch_bounds__(256) potrf_batched_kernel(const BatchDesc* __r
 }
 
 // Q = X / R row by row, 128 rows per CTA, R (<= 64 x 64) in shared memory.
+// mask (or NULL for all): the instances to solve.
 __global__ void __launch_bounds__(128) trsm_batched_kernel(const BatchDesc* __restrict__ d, const int* status,
-                                                           int pass_in_place, int which, int pass)
+                                                           int pass_in_place, int which, int pass,
+                                                           const int* mask = nullptr)
 {
     __shared__ double Rs[64][65];
     __shared__ double dinv[64];
     const int b = blockIdx.y;
     const BatchDesc D = d[b];
-    if (status[b] != 0 || pass >= D.npass) return;
+    if (status[b] != 0 || pass >= D.npass || (mask && !mask[b])) return;
     const int m = D.m, n = D.n;
     const long row0 = (long)blockIdx.x * 128;
     if (row0 >= m) return;  // the grid covers the largest m of the batch
@@ -313,59 +334,40 @@ __global__ void rfinal_batched_kernel(const BatchDesc* __restrict__ d, const int
     D.R[i + (long)j * D.ldr] = i <= j ? D.R1[i + (size_t)j * n] : 0.0;
 }
 
-// ||A||_F^2 (from A's lower triangle) and ||Z||_F^2 of the instances with a
-// shifted first pass, summed into sums[2b], sums[2b + 1] by gridDim.x blocks
-// per instance (columns j = x, x + gridDim.x, ...).
-constexpr int NORM_BLOCKS = 64;
-__global__ void __launch_bounds__(256) norms_batched_kernel(const BatchDesc* __restrict__ d,
-                                                            const int* __restrict__ shifted, double* sums)
+// s_b = c u (m n + n (n + 1)) ||A_b||_F ||Z_b||_F^2 for a shifted instance (mask[b] != 0), else 0; ||A_b||_F^2
+// comes from the split of A (anorm2[b]), ||Z_b||_F^2 is summed here by one block per instance in a fixed order.
+__global__ void __launch_bounds__(256) shift_batched_kernel(const BatchDesc* __restrict__ d,
+                                                            const int* __restrict__ mask, const double* anorm2,
+                                                            double c, double u, double* shifts)
 {
-    __shared__ double red[2][8];
-    const int b = blockIdx.y;
-    if (!shifted[b]) return;
+    __shared__ double red[8];
+    const int b = blockIdx.x;
+    if (!mask[b]) {
+        if (threadIdx.x == 0) shifts[b] = 0.0;
+        return;
+    }
     const BatchDesc D = d[b];
-    const int m = D.m, n = D.n;
-    double sa = 0.0, sz = 0.0;
-    for (int j = blockIdx.x; j < m; j += gridDim.x) {
-        for (int i = j + threadIdx.x; i < m; i += 256) {
-            const double v = D.A[i + (long)j * D.lda];
-            sa += (i == j ? 1.0 : 2.0) * v * v;
+    double sz = 0.0, sz2 = 0.0;  // two chains: the loads of one column overlap the other's
+    int j = 0;
+    for (; j + 1 < D.n; j += 2)
+        for (int i = threadIdx.x; i < D.m; i += 256) {
+            const double v = D.Z[i + (long)j * D.ldz], v2 = D.Z[i + (long)(j + 1) * D.ldz];
+            sz = fma(v, v, sz);
+            sz2 = fma(v2, v2, sz2);
         }
-        if (j < n)
-            for (int i = threadIdx.x; i < m; i += 256) {
-                const double v = D.Z[i + (long)j * D.ldz];
-                sz += v * v;
-            }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        sa += __shfl_xor_sync(0xffffffffu, sa, o);
-        sz += __shfl_xor_sync(0xffffffffu, sz, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        red[0][threadIdx.x >> 5] = sa;
-        red[1][threadIdx.x >> 5] = sz;
-    }
+    for (; j < D.n; ++j)
+        for (int i = threadIdx.x; i < D.m; i += 256) {
+            const double v = D.Z[i + (long)j * D.ldz];
+            sz = fma(v, v, sz);
+        }
+    sz += sz2;
+    for (int o = 16; o > 0; o >>= 1) sz += __shfl_xor_sync(0xffffffffu, sz, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sz;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double ta = 0.0, tz = 0.0;
-        for (int w = 0; w < 8; ++w) {
-            ta += red[0][w];
-            tz += red[1][w];
-        }
-        atomicAdd(&sums[2 * b], ta);
-        atomicAdd(&sums[2 * b + 1], tz);
+        const double z2 = ((red[0] + red[1]) + (red[2] + red[3])) + ((red[4] + red[5]) + (red[6] + red[7]));
+        shifts[b] = c * u * ((double)D.m * D.n + (double)D.n * (D.n + 1)) * sqrt(anorm2[b]) * z2;
     }
-}
-
-// s_b = c u (m n + n (n + 1)) ||A||_F ||Z||_F^2 for a shifted instance, else 0.
-__global__ void shift_batched_kernel(const BatchDesc* __restrict__ d, int count, const int* __restrict__ shifted,
-                                     const double* sums, double c, double u, double* shifts)
-{
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= count) return;
-    const BatchDesc D = d[b];
-    shifts[b] = shifted[b] ? c * u * ((double)D.m * D.n + (double)D.n * (D.n + 1)) * sqrt(sums[2 * b]) * sums[2 * b + 1]
-                           : 0.0;
 }
 
 // ||E||_2 estimate of E = G - I for the instances checked at this pass (one CTA each).
@@ -498,6 +500,15 @@ cudaError_t launch_batched_gram_chol(const BatchDesc* d, int count, int* status,
     return cudaGetLastError();
 }
 
+cudaError_t launch_batched_chol_solve(const BatchDesc* d, int count, int* status, const int* chol_mask,
+                                      const int* solve_mask, cudaStream_t s)
+{
+    potrf_batched_kernel<<<count, 256, 0, s>>>(d, status, 0, 0, chol_mask);
+    dim3 gt(BATCH_MAX_M / 128, count);
+    trsm_batched_kernel<<<gt, 128, 0, s>>>(d, status, 0, 0, 0, solve_mask);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_batched_rfinal(const BatchDesc* d, int count, int* status, cudaStream_t s)
 {
     dim3 gp((BATCH_MAX_N * BATCH_MAX_N + 255) / 256, count);
@@ -505,13 +516,10 @@ cudaError_t launch_batched_rfinal(const BatchDesc* d, int count, int* status, cu
     return cudaGetLastError();
 }
 
-cudaError_t launch_batched_shifts(const BatchDesc* d, int count, const int* shifted, double* sums, double c,
+cudaError_t launch_batched_shifts(const BatchDesc* d, int count, const int* mask, const double* anorm2, double c,
                                   double u, double* shifts, cudaStream_t s)
 {
-    cudaError_t e = cudaMemsetAsync(sums, 0, sizeof(double) * 2 * count, s);
-    if (e != cudaSuccess) return e;
-    norms_batched_kernel<<<dim3(NORM_BLOCKS, count), 256, 0, s>>>(d, shifted, sums);
-    shift_batched_kernel<<<(count + 255) / 256, 256, 0, s>>>(d, count, shifted, sums, c, u, shifts);
+    if (count > 0) shift_batched_kernel<<<count, 256, 0, s>>>(d, mask, anorm2, c, u, shifts);
     return cudaGetLastError();
 }
 

@@ -158,11 +158,32 @@ __device__ inline double sketch_gauss(int i, int j, int n)
     return sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2);
 }
 
+// W_n (n x 2n, column-major) for every n <= 64, one after another: W_n starts at sketch_offset(n).
+__host__ __device__ inline long sketch_offset(int n) { return (long)(n - 1) * n * (2 * n - 1) / 3; }
+
+__global__ void sketch_table_kernel(double* tab, long total)
+{
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    int n = 1;
+    while (sketch_offset(n + 1) <= t) ++n;
+    const long loc = t - sketch_offset(n);
+    tab[t] = sketch_gauss((int)(loc % n), (int)(loc / n), n);
+}
+
+constexpr int FEAT_PAIRS = 63 * 64 / 2;
+// One CTA per instance.  The scaled Cholesky runs column by column with its trailing pairs from a table
+// and thread 0 taking the next pivot while the update finishes (two block barriers per column); the
+// sketch solve R1 X = W runs one column of W per thread, held in registers, column-oriented.
 __global__ void __launch_bounds__(256) features_batched_kernel(const BatchDesc* __restrict__ d, const int* status,
-                                                               float* feat)
+                                                               const double* __restrict__ wtab, float* feat)
 {
     __shared__ double C[64][65];
+    __shared__ double srow[64];
+    __shared__ double dinv[64];
+    __shared__ unsigned short pair[FEAT_PAIRS];
     __shared__ double red[8];
+    __shared__ double rinv_s;
     __shared__ int broke;
     const int b = blockIdx.x, tid = threadIdx.x;
     const BatchDesc D = d[b];
@@ -189,29 +210,50 @@ __global__ void __launch_bounds__(256) features_batched_kernel(const BatchDesc* 
         C[i][j] = v;
         if (i != j) coh = fmax(coh, fabs(v));
     }
-    coh = bmax(coh, red);
-    if (tid == 0) broke = 0;
-    __syncthreads();
-    double pmin = INFINITY, pmax = 0.0;
-    for (int j = 0; j < n; ++j) {
+    for (int e = tid; e < FEAT_PAIRS; e += 256) {
+        int c = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+        while (c * (c + 1) / 2 > e) --c;
+        while ((c + 1) * (c + 2) / 2 <= e) ++c;
+        pair[e] = (unsigned short)(((e - c * (c + 1) / 2) << 8) | c);
+    }
+    coh = bmax(coh, red);  // (its barriers also publish C and the pair table)
+    double pmin = INFINITY, pmax = 0.0;  // thread 0's
+    auto pivot = [&](int j) {
         const double piv = C[j][j];
-        if (!(piv > 0.0) && tid == 0) broke = j + 1;
-        __syncthreads();
+        if (!(piv > 0.0)) {
+            broke = j + 1;
+        } else {
+            pmin = fmin(pmin, piv);
+            pmax = fmax(pmax, piv);
+            const double r = rsqrt(piv);
+            C[j][j] = piv * r;
+            rinv_s = r;
+        }
+    };
+    if (tid == 0) {
+        broke = 0;
+        pivot(0);
+    }
+    __syncthreads();
+    for (int j = 0; j < n; ++j) {
         if (broke) break;
-        pmin = fmin(pmin, piv);
-        pmax = fmax(pmax, piv);
-        const double dj = sqrt(piv);
-        __syncthreads();
-        for (int c = j + 1 + tid; c < n; c += 256) C[j][c] /= dj;
+        const double rj = rinv_s;
+        for (int c = j + 1 + tid; c < n; c += 256) {
+            const double v = C[j][c] * rj;
+            srow[c] = v;
+            C[j][c] = v;
+        }
         __syncthreads();
         const int w = n - j - 1;
-        for (int e = tid; e < w * w; e += 256) {
-            const int r = j + 1 + e % w, c = j + 1 + e / w;
-            if (r <= c) C[r][c] -= C[j][r] * C[j][c];
+        for (int e = tid; e < w * (w + 1) / 2; e += 256) {
+            const int p = pair[e];
+            const int r = j + 1 + (p >> 8), c = j + 1 + (p & 255);
+            C[r][c] = fma(-srow[r], srow[c], C[r][c]);
+            if (e == 0) pivot(j + 1);  // thread 0, pair (j+1, j+1)
         }
         __syncthreads();
     }
-    // sketched kappa(R1): ||R1||_F ||R1^{-1} W||_F / ||W||_F, one column of W per thread
+    // sketched kappa(R1): ||R1||_F ||R1^{-1} W||_F / ||W||_F
     double ksk = 0.0;
     if (probe == 0) {
         __syncthreads();
@@ -220,17 +262,26 @@ __global__ void __launch_bounds__(256) features_batched_kernel(const BatchDesc* 
             C[i][j] = i <= j ? D.R1[i + (long)j * n] : 0.0;
         }
         __syncthreads();
+        if (tid < n) dinv[tid] = 1.0 / C[tid][tid];
         double rf = 0.0, xf = 0.0, wf = 0.0;
         for (int e = tid; e < n * n; e += 256) rf += C[e % n][e / n] * C[e % n][e / n];
+        __syncthreads();
         if (tid < 2 * n) {
-            double x[64];
-            for (int i = n - 1; i >= 0; --i) {
-                const double w = sketch_gauss(i, tid, n);
-                wf += w * w;
-                double t = w;
-                for (int l = i + 1; l < n; ++l) t -= C[i][l] * x[l];
-                x[i] = t / C[i][i];
-                xf += x[i] * x[i];
+            const double* wc = wtab + sketch_offset(n) + (long)tid * n;
+            double x[64];  // this column of W, becoming R1^{-1} W from the bottom up
+#pragma unroll
+            for (int i = 0; i < 64; ++i) {
+                x[i] = i < n ? wc[i] : 0.0;
+                wf = fma(x[i], x[i], wf);
+            }
+#pragma unroll
+            for (int i = 63; i >= 0; --i) {
+                if (i < n) {
+                    x[i] *= dinv[i];
+                    xf = fma(x[i], x[i], xf);
+#pragma unroll
+                    for (int l = 0; l < i; ++l) x[l] = fma(-C[l][i], x[i], x[l]);
+                }
             }
         }
         rf = bsum(rf, red);
@@ -260,10 +311,18 @@ __global__ void __launch_bounds__(256) features_batched_kernel(const BatchDesc* 
 
 }  // namespace
 
-cudaError_t launch_features_batched(const BatchDesc* d, int count, const int* status, float* feat, cudaStream_t s)
+cudaError_t launch_sketch_table(double* tab, cudaStream_t s)
+{
+    const long total = sketch_offset(BATCH_MAX_N + 1);
+    sketch_table_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(tab, total);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_features_batched(const BatchDesc* d, int count, const int* status, const double* wtab, float* feat,
+                                    cudaStream_t s)
 {
     if (count <= 0) return cudaSuccess;
-    features_batched_kernel<<<count, 256, 0, s>>>(d, status, feat);
+    features_batched_kernel<<<count, 256, 0, s>>>(d, status, wtab, feat);
     return cudaGetLastError();
 }
 

@@ -316,17 +316,23 @@ __device__ inline void store_run(__nv_bfloat16* planes, size_t plane, size_t off
 // and the CW-chunk kc; the output rows are offset by roff (a packed batch) and
 // the exponents are strided by erows (the packed row count).
 template <int MODE, bool TRI, int CW>
+// sq (or NULL): the tile's share of ||A||_F^2 (lower-triangle elements, off-diagonal ones twice, to a
+// relative 2^-20 or so: a scale for a shift), summed in a fixed order and written to *sq.
 __device__ __forceinline__ void split_lower_tile(int m, int K, const double* __restrict__ A, long lda, int S,
                                                  __nv_bfloat16* planes, long ldp, size_t plane, int* eA, int* emax,
-                                                 int kc, int ib, long roff, long erows)
+                                                 int kc, int ib, long roff, long erows, double* sq = nullptr)
 {
     constexpr bool SCALED = MODE != 0;  // exponents are recorded
     constexpr int VPL = CW / 32;        // values per lane
     constexpr int ROWS = 4096 / CW;     // rows per tile
     constexpr int CG = 256 / ROWS;      // column groups in the load phase
     __shared__ double T[ROWS][VPL * 33 + 1];
+    __shared__ double red[8];
     const long row0 = (long)ib * ROWS, col0 = (long)kc * CW;
-    if (row0 >= m || (TRI && col0 > row0 + ROWS - 1)) return;
+    if (row0 >= m || (TRI && col0 > row0 + ROWS - 1)) {
+        if (sq && threadIdx.x == 0) *sq = 0.0;
+        return;
+    }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int lr = threadIdx.x % ROWS, lg = threadIdx.x / ROWS;  // load phase: row, column group
     double ld[16];  // all of this thread's loads in flight before the first store
@@ -350,7 +356,39 @@ __device__ __forceinline__ void split_lower_tile(int m, int K, const double* __r
         const int k = lg + CG * t;
         T[lr][(k % VPL) * 33 + k / VPL] = ld[t];
     }
+    if (sq) {
+        // Elements outside A's lower triangle were loaded as zeros.  FP64 arithmetic is scarce, so the
+        // squares are summed in FP32: |v| = 1.f 2^(E - 1023) becomes 1.f' 2^(E - emax) with f' the top 20
+        // bits of f (relative error below 2^-20; zeros and subnormals add nothing), emax the largest
+        // exponent of the thread's values, then of its warp; one FP64 scaling per warp.
+        int ex[16], emx = 0;
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+            ex[t] = (__double2hiint(ld[t]) >> 20) & 0x7FF;
+            emx = max(emx, ex[t]);
+        }
+        float acc = 0.0f;
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+            const int d = ex[t] - emx;
+            if (ex[t] != 0 && d > -60) {
+                const float f = __int_as_float(((127 + d) << 23) | ((__double2hiint(ld[t]) & 0xFFFFF) << 3));
+                const float wf = (col0 + lg + CG * t == row0 + lr) ? f : 2.0f * f;  // off-diagonal: twice
+                acc = fmaf(wf, f, acc);
+            }
+        }
+        int ew = emx;
+        for (int o = 16; o > 0; o >>= 1) ew = max(ew, __shfl_xor_sync(0xffffffffu, ew, o));
+        const int dd = 2 * (emx - ew);
+        float a = (emx != 0 && dd > -120) ? acc * __int_as_float((127 + dd) << 23) : 0.0f;
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if ((threadIdx.x & 31) == 0) {
+            const double sc = ew == 0 ? 0.0 : __hiloint2double(ew << 20, 0);  // 2^(ew - 1023)
+            red[threadIdx.x >> 5] = ((double)a * sc) * sc;
+        }
+    }
     __syncthreads();
+    if (sq && threadIdx.x == 0) *sq = ((red[0] + red[1]) + (red[2] + red[3])) + ((red[4] + red[5]) + (red[6] + red[7]));
     if constexpr (TRI) {
         // M's diagonal is A's halved: one FP64 multiply per diagonal element, only in the tiles that
         // hold the diagonal (FP64 instructions are scarce, so none sits in the load loop)
@@ -396,21 +434,37 @@ struct SplitInst {
     int rows, K, cols;
     long off;
     int kch;
+    int tile0, ntiles;  // the A split: the instance's tiles in the wave's tile list
 };
 static_assert(BATCH_MAX_M <= 4096, "tile codes hold 4 chunk bits, 8 row-block bits; reduce codes 10 block bits");
 
 // The triangular row split of a packed batch of A's: block j takes the tile
 // tiles[j] = (instance << 12) | (chunk << 8) | 16-row block, listed for the
-// lower-triangle tiles only.
+// lower-triangle tiles only, and writes the tile's share of ||A||_F^2 to sq[j].
 __global__ void __launch_bounds__(256, 4) split_lower_batch_kernel(const SplitInst* __restrict__ inst,
                                                                 const int* __restrict__ tiles, int S,
                                                                 __nv_bfloat16* planes, long ldp, size_t plane, int* eA,
-                                                                int* emax, long erows)
+                                                                int* emax, long erows, double* sq)
 {
     const int code = tiles[blockIdx.x];
     const SplitInst I = inst[code >> 12];
     split_lower_tile<1, true, KCH_EMU>(I.rows, I.rows, I.X, I.ldx, S, planes, ldp, plane, eA, emax, (code >> 8) & 15,
-                                       code & 255, I.off, erows);
+                                       code & 255, I.off, erows, sq + blockIdx.x);
+}
+
+// ||A_i||_F^2 of the wave's instances from their tiles' shares: one block per instance, each thread a
+// strided share of the tiles, then a fixed tree.
+__global__ void __launch_bounds__(128) anorm_batch_kernel(const SplitInst* __restrict__ inst,
+                                                          const double* __restrict__ sq, double* out)
+{
+    __shared__ double red[4];
+    const SplitInst I = inst[blockIdx.x];
+    double a = 0.0;
+    for (int t = threadIdx.x; t < I.ntiles; t += 128) a += sq[I.tile0 + t];
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) out[blockIdx.x] = (red[0] + red[1]) + (red[2] + red[3]);
 }
 
 // X (K x C, column-major) -> slices written column-major (column c, k
@@ -452,14 +506,15 @@ __global__ void __launch_bounds__(256) split_tall_kernel(int K, int C, const dou
 }
 
 // The column split of a packed batch: warp w of block y takes packed column
-// 8y + w, of instance colinst[8y + w].
+// 8y + w, of instance colinst[8y + w] (skipped when live[instance] <= pass).
 __global__ void __launch_bounds__(256) split_tall_batch_kernel(const SplitInst* __restrict__ inst,
                                                                const int* __restrict__ colinst, int S,
                                                                __nv_bfloat16* planes, long ldp, size_t plane, int* eX,
-                                                               int* xmax, long ecols)
+                                                               int* xmax, long ecols, const int* live, int pass)
 {
     const long gc = (long)blockIdx.y * 8 + (threadIdx.x >> 5);
     if (gc >= ecols) return;
+    if (live && live[colinst[gc]] <= pass) return;  // the instance sits this pass out
     const SplitInst I = inst[colinst[gc]];
     const int kc = blockIdx.x;
     if (kc >= I.kch) return;
@@ -478,7 +533,7 @@ __global__ void fill_int_kernel(int* p, long n, int v)
 // [coff, coff + cols) of the packed right planes; K is its contraction length.
 // Its items are [item0, item0 + items); cum + cum0 holds its per-row-tile
 // item prefix (rt + 1 entries).  Its output (rows x cols, column-major, ldo)
-// starts at out.
+// starts at out.  wi is its index within the wave (the index of its pass count in TcArgs.live).
 struct TcInst {
     int rows, cols, K, tri;
     int roff, coff;
@@ -486,6 +541,7 @@ struct TcInst {
     int item0, cum0;
     double* out;
     long ldo;
+    int wi;
 };
 
 struct TcArgs {
@@ -508,7 +564,54 @@ struct TcArgs {
     const TcInst* inst;   // [ninst]
     const int* inst_item0;  // [ninst + 1]: first item of each instance, then the total
     const int* rblk;      // a batch: the reduction's blocks (instance << 10 | block)
+    const int* live;      // a batch, or NULL: the wave's Gram pass counts; instances with live[wi] <= pass sit
+    int pass;             // this launch out (their items are not in list, their outputs are not written)
+    const int* list;      // NULL: items 0..nitems-1; else list[0] items, list[1..]: their indices
 };
+
+__device__ inline int item_total(const TcArgs& a) { return a.list ? a.list[0] : a.nitems; }
+__device__ inline int item_index(const TcArgs& a, int jj) { return a.list ? a.list[1 + jj] : jj; }
+
+// The items of a packed launch whose instance takes part in this pass (live[wi] > pass), in item order:
+// list[0] = their count, list[1..] = their indices.  One block; instances in chunks of its threads.
+constexpr int ALIST_THREADS = 1024;
+__global__ void __launch_bounds__(ALIST_THREADS) active_items_kernel(const TcInst* __restrict__ inst,
+                                                                     const int* __restrict__ item0, int ninst,
+                                                                     const int* __restrict__ live, int pass, int* list)
+{
+    __shared__ int wsum[ALIST_THREADS / 32];
+    __shared__ int base;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    if (t == 0) base = 0;
+    __syncthreads();
+    for (int k0 = 0; k0 < ninst; k0 += ALIST_THREADS) {
+        const int k = k0 + t;
+        const int c = (k < ninst && live[inst[k].wi] > pass) ? item0[k + 1] - item0[k] : 0;
+        int incl = c;  // inclusive scan within the warp, then over the warps
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (lane == 31) wsum[w] = incl;
+        __syncthreads();
+        if (w == 0) {
+            int x = wsum[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += v;
+            }
+            wsum[lane] = x;  // inclusive over warps
+        }
+        __syncthreads();
+        const int excl = base + (w > 0 ? wsum[w - 1] : 0) + incl - c;
+        for (int q = 0; q < c; ++q) list[1 + excl + q] = item0[k] + q;
+        const int total = base + wsum[ALIST_THREADS / 32 - 1];
+        __syncthreads();  // every thread has read base and wsum
+        if (t == 0) base = total;
+        __syncthreads();
+    }
+    if (t == 0) list[0] = base;
+}
 
 __device__ __host__ inline int kend_of(int K, int tri, int I)
 {
@@ -728,6 +831,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);  // the drain's flag at +32 ints
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nit = item_total(a);  // the launch's items (a packed batch: only the active instances')
     if (*(volatile int*)&a.st->code != 0) return;
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::STAGES; ++s) {
@@ -766,7 +870,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // ------------------------------------------------ TMA producer
         if (lane == 0) {
             long it = 0;
-            for (int j = blockIdx.x; j < a.nitems && !*abort_flag; j += gridDim.x) {
+            for (int jj = blockIdx.x; jj < nit && !*abort_flag; jj += gridDim.x) {
+                const int j = item_index(a, jj);
                 const Item item = item_of(a, j);
                 for (int ks = item.ks0; ks < item.ks1 && !*abort_flag; ++ks, ++it) {
                     const int stg = (int)(it % C::STAGES);
@@ -795,7 +900,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (lane == 0) {
             constexpr uint32_t idesc = MODE == 2 ? idesc_e4m3(N) : idesc_bf16(N);
             long it = 0, chunk = 0;
-            for (int j = blockIdx.x; j < a.nitems && !*abort_flag; j += gridDim.x) {
+            for (int jj = blockIdx.x; jj < nit && !*abort_flag; jj += gridDim.x) {
+                const int j = item_index(a, jj);
                 const Item item = item_of(a, j);
                 for (int ks = item.ks0; ks < item.ks1 && !*abort_flag; ++ks, ++it) {
                     const bool chunk_start = CHUNKED ? ((ks - item.ks0) % C::CH_STEPS == 0) : (ks == item.ks0);
@@ -866,7 +972,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         float* colsc = rowsc + C::MAXCH * TM;
         long chunk = 0;
         bool stop = false;
-        for (int j = blockIdx.x; j < a.nitems && !stop; j += gridDim.x) {
+        for (int jj = blockIdx.x; jj < nit && !stop; jj += gridDim.x) {
+            const int j = item_index(a, jj);
             const Item item = item_of(a, j);
             double* slot = a.slots + (size_t)j * TM * N + (size_t)r * N + half * NH;  // MODE 0: FP64 slots
             float H[CHUNKED ? NH : 1];
@@ -1033,6 +1140,7 @@ __global__ void slot_reduce_batch_kernel(TcArgs a)
     if (*(volatile const int*)&a.st->code != 0) return;
     const int code = a.rblk[blockIdx.x];
     const TcInst I = a.inst[code >> 10];
+    if (a.live && a.live[I.wi] <= a.pass) return;
     const long el = (long)(code & 1023) * 256 + threadIdx.x;
     if (el >= (long)I.rows * I.cols) return;
     const int col = (int)(el / I.rows), row = (int)(el % I.rows);
@@ -1185,6 +1293,7 @@ __global__ void __launch_bounds__(EMU_THREADS, 1)
     float* colsc = rowsc + EMU_MAXCH * TM;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nit = item_total(a);  // the launch's items (a packed batch: only the active instances')
     if (*(volatile int*)&a.st->code != 0) return;
     if (threadIdx.x == 0) {
         for (int s = 0; s < EMU_STAGES; ++s) {
@@ -1223,7 +1332,8 @@ __global__ void __launch_bounds__(EMU_THREADS, 1)
         // ------------------------------------------------ TMA producer
         if (lane == 0) {
             long it = 0;
-            for (int j = blockIdx.x; j < a.nitems && !*abort_flag; j += gridDim.x) {
+            for (int jj = blockIdx.x; jj < nit && !*abort_flag; jj += gridDim.x) {
+                const int j = item_index(a, jj);
                 const Item item = item_of(a, j);
                 for (int ks = item.ks0; ks < item.ks1 && !*abort_flag; ++ks, ++it) {
                     const int stg = (int)(it % EMU_STAGES);
@@ -1253,7 +1363,8 @@ __global__ void __launch_bounds__(EMU_THREADS, 1)
             constexpr uint32_t idesc = idesc_bf16(EMU_N);
             long it = 0, chunk = 0;
             bool ok = true;
-            for (int j = blockIdx.x; j < a.nitems && ok && !*abort_flag; j += gridDim.x) {
+            for (int jj = blockIdx.x; jj < nit && ok && !*abort_flag; jj += gridDim.x) {
+                const int j = item_index(a, jj);
                 const Item item = item_of(a, j);
                 for (int ks = item.ks0; ks < item.ks1 && !*abort_flag; ++ks, ++it) {
                     const int kin = ks - item.ks0;
@@ -1315,15 +1426,16 @@ __global__ void __launch_bounds__(EMU_THREADS, 1)
         const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(g * EMU_CPT);
         long chunk = 0;
         bool stop = false;
-        for (int j = blockIdx.x; j < a.nitems && !stop; j += gridDim.x) {
+        for (int jj = blockIdx.x; jj < nit && !stop; jj += gridDim.x) {
+            const int j = item_index(a, jj);
             const Item item = item_of(a, j);
             const int gi = item.I * TM + r;  // row within the instance
             const bool row_ok = gi < item.rows;
             float2 H[EMU_CPT / 2], L[EMU_CPT / 2];  // column pairs
 #pragma unroll
             for (int c = 0; c < EMU_CPT / 2; ++c) H[c] = L[c] = make_float2(0.f, 0.f);
-            const int emax_r = row_ok ? a.emaxA[item.roff + gi] : 0;
             const int nsteps = item.ks1 - item.ks0;
+            const int emax_r = row_ok ? a.emaxA[item.roff + gi] : 0;
             const int nch = (nsteps + EMU_CH - 1) / EMU_CH;
             {
                 // all of the item's scales, loaded once: row scale 2^(e_row - emax_row - 14) (x y =
@@ -1846,6 +1958,8 @@ struct WaveLayout {
     __nv_bfloat16 *Ap, *Zp, *Up;
     int *eA, *mA, *eZ, *mZ, *eU, *mU;
     double* slots;
+    double* asq;  // the A split's per-tile shares of ||A||_F^2
+    int* alist;   // a launch's active items (max_items + 1)
     size_t bytes;
 };
 WaveLayout wave_layout(const TcBatchWave& w, void* ws)
@@ -1869,6 +1983,8 @@ WaveLayout wave_layout(const TcBatchWave& w, void* ws)
     L.mZ = reinterpret_cast<int*>(take((size_t)w.cols * 4));
     L.mU = reinterpret_cast<int*>(take((size_t)w.cols * 4));
     L.slots = reinterpret_cast<double*>(take((size_t)w.max_items * TM * EMU_N * 8));
+    L.asq = reinterpret_cast<double*>(take((size_t)w.tilesA * 8));
+    L.alist = reinterpret_cast<int*>(take((size_t)(w.max_items + 1) * 4));
     L.bytes = o;
     return L;
 }
@@ -2014,13 +2130,14 @@ void tc_batch_tables(const TcBatchPlan& p, const std::vector<TcBatchShape>& sh, 
         int nt = 0;
         for (int i = 0; i < w.count; ++i) {
             const int b = w.first + i, m = sh[b].m, n = sh[b].n, kch = (m + KCH_EMU - 1) / KCH_EMU;
-            sa[i] = SplitInst{in[b].A, in[b].lda, m, m, 0, roff[i], kch};
-            sz[i] = SplitInst{in[b].Z, in[b].ldz, 0, m, n, coff[i], kch};
-            sq[i] = SplitInst{in[b].Q, in[b].ldq, 0, m, n, coff[i], kch};
-            su[i] = SplitInst{upool + uoff[i], (long)m, 0, m, n, coff[i], kch};
+            sa[i] = SplitInst{in[b].A, in[b].lda, m, m, 0, roff[i], kch, nt, 0};
+            sz[i] = SplitInst{in[b].Z, in[b].ldz, 0, m, n, coff[i], kch, 0, 0};
+            sq[i] = SplitInst{in[b].Q, in[b].ldq, 0, m, n, coff[i], kch, 0, 0};
+            su[i] = SplitInst{upool + uoff[i], (long)m, 0, m, n, coff[i], kch, 0, 0};
             const int nrb = (m + 15) / 16;
             for (int kc = 0; kc < kch; ++kc)
                 for (int ib = 16 * kc; ib < nrb; ++ib) tiles[nt++] = (i << 12) | (kc << 8) | ib;
+            sa[i].ntiles = nt - sa[i].tile0;
             for (int c = 0; c < n; ++c) colinst[coff[i] + c] = i;
         }
         for (int pass = 0; pass < w.maxpass; ++pass)
@@ -2049,6 +2166,7 @@ void tc_batch_tables(const TcBatchPlan& p, const std::vector<TcBatchShape>& sh, 
                         t.cum0 = cm;
                         t.out = prod == 0 ? upool + uoff[i] : in[b].C;
                         t.ldo = t.rows;
+                        t.wi = i;
                         int s = 0;
                         for (int I = 0; I < t.rt; ++I) {
                             cum[cm + I] = s;
@@ -2075,12 +2193,23 @@ cudaError_t tc_batch_split_a(const TcBatchPlan& p, int w, const void* table_dev,
     fill_int_kernel<<<(unsigned)((W.rows + 255) / 256), 256, 0, s>>>(L.mA, W.rows, EXP_NONE);
     split_lower_batch_kernel<<<W.tilesA, 256, 0, s>>>(reinterpret_cast<const SplitInst*>(tab + W.splitA),
                                                       reinterpret_cast<const int*>(tab + W.tileTab), EMU_S, L.Ap,
-                                                      W.ldp, (size_t)W.rows * W.ldp, L.eA, L.mA, W.rows);
+                                                      W.ldp, (size_t)W.rows * W.ldp, L.eA, L.mA, W.rows, L.asq);
+    return cudaGetLastError();
+}
+
+cudaError_t tc_batch_anorm2(const TcBatchPlan& p, int w, const void* table_dev, void* scratch, double* out,
+                            cudaStream_t s)
+{
+    const TcBatchWave& W = p.waves[w];
+    const WaveLayout L = wave_layout(W, scratch);
+    const char* tab = static_cast<const char*>(table_dev);
+    if (W.count > 0)
+        anorm_batch_kernel<<<W.count, 128, 0, s>>>(reinterpret_cast<const SplitInst*>(tab + W.splitA), L.asq, out);
     return cudaGetLastError();
 }
 
 cudaError_t tc_batch_gram(const TcBatchPlan& p, int w, int pass, const void* table_dev, void* scratch,
-                          DevStatus* st, uint64_t limit_ns, int sms, cudaStream_t s)
+                          DevStatus* st, uint64_t limit_ns, int sms, cudaStream_t s, const int* live)
 {
     const TcBatchWave& W = p.waves[w];
     const WaveLayout L = wave_layout(W, scratch);
@@ -2108,10 +2237,15 @@ cudaError_t tc_batch_gram(const TcBatchPlan& p, int w, int pass, const void* tab
         a.inst = reinterpret_cast<const TcInst*>(tab + B.inst);
         a.inst_item0 = reinterpret_cast<const int*>(tab + B.item0);
         a.rblk = reinterpret_cast<const int*>(tab + B.rblk);
+        a.live = live;
+        a.pass = pass;
+        a.list = live ? L.alist : nullptr;
         return a;
     };
     auto product = [&](const TcBatchLaunch& B, const TcArgs& a, const void* PA, size_t plA, const void* PB) {
         cudaError_t e;
+        if (live)
+            active_items_kernel<<<1, ALIST_THREADS, 0, s>>>(a.inst, a.inst_item0, a.ninst, live, pass, L.alist);
         if (B.mode == 1) e = launch_emu(a, PA, W.ldp, plA, PB, W.ldp, planeZ, sms, s);
         else e = launch_tc<64, 64, 2, 3>(a, PA, W.ldp, plA, PB, W.ldp, planeZ, sms, s);
         if (e != cudaSuccess) return e;
@@ -2125,7 +2259,7 @@ cudaError_t tc_batch_gram(const TcBatchPlan& p, int w, int pass, const void* tab
     fill_int_kernel<<<(unsigned)((W.cols + 255) / 256), 256, 0, s>>>(L.mZ, W.cols, EXP_NONE);
     const int* colinst = reinterpret_cast<const int*>(tab + W.colTab);
     split_tall_batch_kernel<<<gt, 256, 0, s>>>(reinterpret_cast<const SplitInst*>(tab + (pass ? W.splitQ : W.splitZ)),
-                                               colinst, EMU_S, L.Zp, W.ldp, planeZ, L.eZ, L.mZ, W.cols);
+                                               colinst, EMU_S, L.Zp, W.ldp, planeZ, L.eZ, L.mZ, W.cols, live, pass);
     for (int li = 0; li < W.nl[pass]; ++li) {
         const TcBatchLaunch& B = W.u[pass][li];
         if ((e = product(B, args(B, W.rows, L.eA, L.eZ, L.mA, L.mZ), L.Ap, planeA, L.Zp)) != cudaSuccess) return e;
@@ -2133,7 +2267,7 @@ cudaError_t tc_batch_gram(const TcBatchPlan& p, int w, int pass, const void* tab
     // the split of U, then C = X^T U
     fill_int_kernel<<<(unsigned)((W.cols + 255) / 256), 256, 0, s>>>(L.mU, W.cols, EXP_NONE);
     split_tall_batch_kernel<<<gt, 256, 0, s>>>(reinterpret_cast<const SplitInst*>(tab + W.splitU), colinst, EMU_S,
-                                               L.Up, W.ldp, planeZ, L.eU, L.mU, W.cols);
+                                               L.Up, W.ldp, planeZ, L.eU, L.mU, W.cols, live, pass);
     for (int li = 0; li < W.nl[pass]; ++li) {
         const TcBatchLaunch& B = W.c[pass][li];
         if ((e = product(B, args(B, W.cols, L.eZ, L.eU, L.mZ, L.mU), L.Zp, planeZ, L.Up)) != cudaSuccess) return e;

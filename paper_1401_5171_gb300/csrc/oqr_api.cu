@@ -787,21 +787,14 @@ oqr_status batched_fp64_impl(oqr_ctx* ctx, int count, const int* m, const int* n
 // Every option of the selector starts with the same first pass, an
 // FP64-accurate Gram G0 = Z^T A Z on the tensor cores, so that pass runs
 // first for the whole wave (the probe); its Gram and Cholesky factor give the
-// features, the MLP picks an option per instance, and each option finishes
-// from the probe in the same wave, reading the wave's split of A again:
-//   0 one pass:   Q = Z R1^{-1} is the result (checked: ||Q^T A Q - I||_2)
-//   1 two passes: one more FP64-accurate pass on Q (A-CholQR2)
-//   2 shifted:    R1 = chol(G0 + s I) from the same G0, then two more passes
-//                 (shifted A-CholQR3); also taken when the probe's Cholesky
-//                 broke down and the network chose 0 or 1
-//   3 FP64 A-CholQR2 (DFMA), run after the waves.
-// A failed check or a breakdown goes down the fallback chain: shifted
-// A-CholQR3 on the tensor cores (checked), then FP64 A-CholQR2.
+// features and the network picks a route per instance.  The rest of the wave
+// is a fixed sequence of launches whose decisions are taken on the device
+// (k_select.cu): each instance takes part in the Gram passes of its route, the
+// tensor-core launches skipping the tiles of the others, so the host neither
+// waits for the choices nor plans per choice.  Instances that end with a
+// failed check, a breakdown or the network's FP64 choice are redone by FP64
+// A-CholQR2 after the waves.
 namespace {
-constexpr int SEL_ONE = 0, SEL_TWO = 1, SEL_SHIFTED = 2, SEL_FP64 = 3;
-// A last pass factoring a Gram within 0.5 of I leaves kappa(Q_prev)^2 <= 3 in the A inner product, so its
-// result is at rounding level (Thm 2.1 with kappa^2 <= 3); a larger defect sends the result to the fallback.
-constexpr double LAST_DEFECT_MAX = 0.5;
 
 struct SelInputs {
     int count;
@@ -822,103 +815,44 @@ struct SelResult {
     std::vector<double> orth;  // NaN where not checked
 };
 
-oqr_status selector_waves(oqr_ctx* ctx, const SelInputs& I, const float* params, bool check_all, float* feat_out,
-                          SelResult* res, cudaStream_t s)
-{
-    const int count = I.count;
-    const bool features_only = I.Q == nullptr;
-    std::vector<int> perm((size_t)count);
-    for (int b = 0; b < count; ++b) perm[b] = b;
-    std::stable_sort(perm.begin(), perm.end(), [&](int x, int y) { return I.m[x] > I.m[y]; });
-    std::vector<TcBatchShape> sh1((size_t)count), shmax((size_t)count);
+// Instances sorted by m (largest first), their descriptors and tensor-core inputs, over a pool of
+// per-instance n x n buffers (partials, G, R1, R2, G0).
+struct SelSetup {
+    std::vector<int> perm;
+    std::vector<TcBatchShape> sh;
+    std::vector<BatchDesc> desc;
+    std::vector<TcBatchIn> in;
     size_t pool_doubles = 0;
+};
+constexpr int SEL_NN_BUFS = 5;
+
+SelSetup sel_setup(const SelInputs& I, int npass)
+{
+    SelSetup S;
+    const int count = I.count;
+    S.perm.resize((size_t)count);
+    for (int b = 0; b < count; ++b) S.perm[b] = b;
+    std::stable_sort(S.perm.begin(), S.perm.end(), [&](int x, int y) { return I.m[x] > I.m[y]; });
+    S.sh.resize((size_t)count);
     for (int i = 0; i < count; ++i) {
-        const int b = perm[i];
-        sh1[i] = TcBatchShape{I.m[b], I.n[b], 1, 1};
-        shmax[i] = TcBatchShape{I.m[b], I.n[b], 1, TC_BATCH_MAX_PASS};
-        pool_doubles += align256((size_t)4 * I.n[b] * I.n[b] * sizeof(double)) / sizeof(double);
+        const int b = S.perm[i];
+        S.sh[i] = TcBatchShape{I.m[b], I.n[b], 1, npass};
+        S.pool_doubles += align256((size_t)SEL_NN_BUFS * I.n[b] * I.n[b] * sizeof(double)) / sizeof(double);
     }
-    const size_t budget = ctx->batch_budget ? ctx->batch_budget : BATCH_WAVE_BYTES;
-    const TcBatchPlan plan = tc_batch_plan(sh1, budget);
-    const TcBatchPlan pmax = tc_batch_plan(shmax, budget);  // bounds every per-wave plan of the later passes
-    if (pmax.waves.size() != plan.waves.size()) return OQR_ERR_UNSUPPORTED;
-    const int nw = (int)plan.waves.size();
-    const int nbuf = (features_only || nw == 1) ? 1 : 2;  // wave w + 1's first pass runs while wave w is planned
-    const size_t scratch_bytes = std::max(plan.scratch_bytes, pmax.scratch_bytes);
-    double* defects = nullptr;
-    char* tab2[2] = {nullptr, nullptr};
-    void* scr[2] = {nullptr, nullptr};
-    auto layout = [&](Carve& c, char** tab1, BatchDesc** d, int** sts, int** dshifted, double** sums,
-                      double** shifts, double** orths, float** feat, int** choice, double** pool, double** upool) {
-        defects = c.take<double>((size_t)count);
-        *tab1 = c.take<char>(plan.table_bytes);
-        for (int k = 0; k < 2; ++k) tab2[k] = c.take<char>(k < nbuf ? pmax.table_bytes : 0);
-        *d = c.take<BatchDesc>((size_t)count);
-        *sts = c.take<int>((size_t)count);
-        *dshifted = c.take<int>((size_t)count);
-        *sums = c.take<double>((size_t)2 * count);
-        *shifts = c.take<double>((size_t)count);
-        *orths = c.take<double>((size_t)count);
-        *feat = c.take<float>((size_t)count * MLP_IN);
-        *choice = c.take<int>((size_t)count);
-        *pool = c.take<double>(pool_doubles);
-        *upool = c.take<double>((size_t)std::max(plan.upool_doubles, pmax.upool_doubles));
-        for (int k = 0; k < 2; ++k) scr[k] = c.take<char>(k < nbuf ? scratch_bytes : 0);
-    };
-    char* tab1;
-    BatchDesc* ddesc;
-    int *sts, *dshifted, *dchoice;
-    double *sums, *shifts, *orths, *pool, *upool;
-    float* feat;
-    Carve probe(nullptr);
-    layout(probe, &tab1, &ddesc, &sts, &dshifted, &sums, &shifts, &orths, &feat, &dchoice, &pool, &upool);
-    oqr_status v = ensure_ws(ctx, probe.off);
-    if (v != OQR_OK) return v;
-    Carve cv(ctx->ws);
-    layout(cv, &tab1, &ddesc, &sts, &dshifted, &sums, &shifts, &orths, &feat, &dchoice, &pool, &upool);
-    // pinned host memory: the choices and statuses read back per wave, two copies of the descriptors
-    // (the shifted refactor's and the final ones), the statuses and shift flags uploaded, and two table images
-    auto pin_layout = [&](Carve& c, BatchDesc** hdA, BatchDesc** hdB, int** hch, int** hst, int** hup, int** hsh,
-                          char** img0, char** img1) {
-        *hdA = c.take<BatchDesc>((size_t)count);
-        *hdB = c.take<BatchDesc>((size_t)count);
-        *hch = c.take<int>((size_t)count);
-        *hst = c.take<int>((size_t)count);
-        *hup = c.take<int>((size_t)count);
-        *hsh = c.take<int>((size_t)count);
-        *img0 = c.take<char>(pmax.table_bytes);
-        *img1 = c.take<char>(pmax.table_bytes);
-    };
-    BatchDesc *hdA, *hdB;
-    int *hch, *hst, *hup, *hsh;
-    char* img[2];
-    Carve pprobe(nullptr);
-    pin_layout(pprobe, &hdA, &hdB, &hch, &hst, &hup, &hsh, &img[0], &img[1]);
-    if (ctx->pin_bytes < pprobe.off) {
-        if (ctx->pin) {
-            cudaStreamSynchronize(s);
-            cudaFreeHost(ctx->pin);
-            ctx->pin = nullptr;
-            ctx->pin_bytes = 0;
-        }
-        if (cudaHostAlloc(&ctx->pin, pprobe.off, cudaHostAllocDefault) != cudaSuccess) {
-            cudaGetLastError();
-            return OQR_ERR_NO_MEMORY;
-        }
-        ctx->pin_bytes = pprobe.off;
-    }
-    for (int k = 0; k < 2; ++k)
-        if (!ctx->sel_ev[k] && cudaEventCreateWithFlags(&ctx->sel_ev[k], cudaEventDisableTiming) != cudaSuccess)
-            return OQR_ERR_CUDA;
-    Carve pc(ctx->pin);
-    pin_layout(pc, &hdA, &hdB, &hch, &hst, &hup, &hsh, &img[0], &img[1]);
-    std::vector<BatchDesc> desc((size_t)count);
-    std::vector<TcBatchIn> in((size_t)count);
+    return S;
+}
+
+void sel_fill(const SelInputs& I, SelSetup& S, double* pool)
+{
+    const bool features_only = I.Q == nullptr;
+    const int count = I.count;
+    S.desc.assign((size_t)count, BatchDesc{});
+    S.in.resize((size_t)count);
     double* q = pool;
     for (int i = 0; i < count; ++i) {
-        const int b = perm[i];
+        const int b = S.perm[i];
         const size_t nn = (size_t)I.n[b] * I.n[b];
-        BatchDesc& d = desc[i];
+        BatchDesc& d = S.desc[i];
         d.A = I.A[b];
         d.Z = I.Z[b];
         d.Q = features_only ? nullptr : I.Q[b];
@@ -930,143 +864,237 @@ oqr_status selector_waves(oqr_ctx* ctx, const SelInputs& I, const float* params,
         d.m = I.m[b];
         d.n = I.n[b];
         d.splits = 1;
-        d.npass = 1;
+        d.npass = 2;
         d.partials = q;
         d.G = q + nn;
         d.R1 = d.G + nn;
         d.R2 = d.R1 + nn;
-        q += align256(4 * nn * sizeof(double)) / sizeof(double);
-        in[i] = TcBatchIn{I.A[b], I.lda[b], I.Z[b], I.ldz[b], features_only ? const_cast<double*>(I.Z[b]) : I.Q[b],
-                          features_only ? I.ldz[b] : I.ldq[b], d.partials};
+        d.G0 = d.R2 + nn;
+        q += align256(SEL_NN_BUFS * nn * sizeof(double)) / sizeof(double);
+        S.in[i] = TcBatchIn{I.A[b], I.lda[b], I.Z[b], I.ldz[b], features_only ? const_cast<double*>(I.Z[b]) : I.Q[b],
+                            features_only ? I.ldz[b] : I.ldq[b], d.partials};
     }
+}
+
+// Pinned host memory of the context, grown to bytes (the previous call's copies are complete: every
+// selector call ends with a synchronization).
+oqr_status sel_pinned(oqr_ctx* ctx, size_t bytes, cudaStream_t s)
+{
+    if (ctx->pin_bytes >= bytes) return OQR_OK;
+    if (ctx->pin) {
+        cudaStreamSynchronize(s);
+        cudaFreeHost(ctx->pin);
+        ctx->pin = nullptr;
+        ctx->pin_bytes = 0;
+    }
+    if (cudaHostAlloc(&ctx->pin, bytes, cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        return OQR_ERR_NO_MEMORY;
+    }
+    ctx->pin_bytes = bytes;
+    return OQR_OK;
+}
+
+// The features of every instance after its first FP64-accurate pass (oqr_batched_features).
+oqr_status features_waves(oqr_ctx* ctx, const SelInputs& I, float* feat_out, cudaStream_t s)
+{
+    const int count = I.count;
+    SelSetup S = sel_setup(I, 1);
+    const size_t budget = ctx->batch_budget ? ctx->batch_budget : BATCH_WAVE_BYTES;
+    const TcBatchPlan plan = tc_batch_plan(S.sh, budget);
+    double* wtab = nullptr;
+    auto layout = [&](Carve& c, char** tab, BatchDesc** d, int** sts, float** feat, int** perm, double** pool,
+                      double** upool, void** scr) {
+        wtab = c.take<double>((size_t)SKETCH_TABLE_DOUBLES);
+        *tab = c.take<char>(plan.table_bytes);
+        *d = c.take<BatchDesc>((size_t)count);
+        *sts = c.take<int>((size_t)count);
+        *feat = c.take<float>((size_t)count * MLP_IN);
+        *perm = c.take<int>((size_t)count);
+        *pool = c.take<double>(S.pool_doubles);
+        *upool = c.take<double>(plan.upool_doubles);
+        *scr = c.take<char>(plan.scratch_bytes);
+    };
+    char* tab;
+    BatchDesc* ddesc;
+    int *sts, *dperm;
+    float* feat;
+    double *pool, *upool;
+    void* scratch;
+    Carve probe(nullptr);
+    layout(probe, &tab, &ddesc, &sts, &feat, &dperm, &pool, &upool, &scratch);
+    oqr_status v = ensure_ws(ctx, probe.off);
+    if (v != OQR_OK) return v;
+    Carve cv(ctx->ws);
+    layout(cv, &tab, &ddesc, &sts, &feat, &dperm, &pool, &upool, &scratch);
+    sel_fill(I, S, pool);
     std::vector<char> image;
-    tc_batch_tables(plan, sh1, in, tab1, upool, image);
-    OQR_TRY(cudaMemcpyAsync(tab1, image.data(), image.size(), cudaMemcpyHostToDevice, s));
-    OQR_TRY(cudaMemcpyAsync(ddesc, desc.data(), sizeof(BatchDesc) * count, cudaMemcpyHostToDevice, s));
+    tc_batch_tables(plan, S.sh, S.in, tab, upool, image);
+    OQR_TRY(cudaMemcpyAsync(tab, image.data(), image.size(), cudaMemcpyHostToDevice, s));
+    OQR_TRY(cudaMemcpyAsync(ddesc, S.desc.data(), sizeof(BatchDesc) * count, cudaMemcpyHostToDevice, s));
+    OQR_TRY(cudaMemcpyAsync(dperm, S.perm.data(), sizeof(int) * count, cudaMemcpyHostToDevice, s));
     OQR_TRY(cudaMemsetAsync(sts, 0, sizeof(int) * count, s));
     if ((v = reset_status(ctx, s)) != OQR_OK) return v;
-    // the pageable uploads above must have left their staging before the host reuses these vectors
-    if (cudaStreamSynchronize(s) != cudaSuccess) return OQR_ERR_CUDA;
+    OQR_TRY(launch_sketch_table(wtab, s));
     const uint64_t limit = 4000000000ull;
-    std::vector<int> opt((size_t)count, 0), chk((size_t)count, 0);
-    // the first pass of wave w: split of A into scratch w % nbuf, the FP64-accurate Gram of Z, its
-    // Cholesky factor (and Q_1), the features, the network, and the choices read back to pinned memory
-    auto first_pass = [&](int w) -> oqr_status {
+    for (int w = 0; w < (int)plan.waves.size(); ++w) {
+        const NvtxRange range("oqr: features wave %d", w);
         const TcBatchWave& W = plan.waves[w];
-        const int f = W.first, cnt = W.count;
-        BatchDesc* dw = ddesc + f;
-        int* sw = sts + f;
-        void* scratch = scr[w % nbuf];
-        OQR_TRY(tc_batch_split_a(plan, w, tab1, scratch, s));
-        OQR_TRY(tc_batch_gram(plan, w, 0, tab1, scratch, ctx->st, limit, ctx->sm_count, s));
-        if (features_only) OQR_TRY(launch_batched_gram_chol(dw, cnt, sw, s));
-        else OQR_TRY(launch_batched_factor(dw, cnt, sw, 0, nullptr, s));
-        OQR_TRY(launch_features_batched(dw, cnt, sw, feat + (size_t)f * MLP_IN, s));
-        if (features_only) return OQR_OK;
-        OQR_TRY(launch_mlp_forward(cnt, feat + (size_t)f * MLP_IN, params, 1, nullptr, dchoice + f, s));
-        OQR_TRY(cudaMemcpyAsync(hch + f, dchoice + f, sizeof(int) * cnt, cudaMemcpyDeviceToHost, s));
-        OQR_TRY(cudaMemcpyAsync(hst + f, sw, sizeof(int) * cnt, cudaMemcpyDeviceToHost, s));
-        OQR_TRY(cudaEventRecord(ctx->sel_ev[w & 1], s));
-        return OQR_OK;
+        BatchDesc* dw = ddesc + W.first;
+        int* sw = sts + W.first;
+        OQR_TRY(tc_batch_split_a(plan, w, tab, scratch, s));
+        OQR_TRY(tc_batch_gram(plan, w, 0, tab, scratch, ctx->st, limit, ctx->sm_count, s));
+        OQR_TRY(launch_batched_gram_chol(dw, W.count, sw, s));
+        OQR_TRY(launch_features_batched(dw, W.count, sw, wtab, feat + (size_t)W.first * MLP_IN, s));
+    }
+    OQR_TRY(launch_batch_scatter_rows_f32(feat, dperm, count, MLP_IN, feat_out, s));
+    // the pageable uploads above have left their host vectors once the stream is done
+    if (cudaStreamSynchronize(s) != cudaSuccess) return OQR_ERR_CUDA;
+    DevStatus hs;
+    if (cudaMemcpy(&hs, ctx->st, sizeof(hs), cudaMemcpyDeviceToHost) != cudaSuccess) return OQR_ERR_CUDA;
+    return hs.code != 0 ? OQR_ERR_TIMEOUT : OQR_OK;
+}
+
+// The selector over a batch: the probe, the network and every route's passes, wave by wave, with no
+// host round trip until the end.
+oqr_status selector_run(oqr_ctx* ctx, const SelInputs& I, const float* params, double tol, bool check_all,
+                        SelResult* res, cudaStream_t s)
+{
+    const int count = I.count;
+    const int extra = check_all ? 1 : 0;
+    SelSetup S = sel_setup(I, TC_BATCH_MAX_PASS);
+    const size_t budget = ctx->batch_budget ? ctx->batch_budget : BATCH_WAVE_BYTES;
+    const TcBatchPlan plan = tc_batch_plan(S.sh, budget);
+    struct Dev {
+        char* tab;
+        BatchDesc* d;
+        int *sts, *route, *opt, *gpass, *mask, *choice;
+        double *anorm2, *shifts, *orth, *defect, *pool, *upool, *wtab;
+        float* feat;
+        void* scratch;
+    } D{};
+    auto layout = [&](Carve& c, Dev& x) {
+        x.wtab = c.take<double>((size_t)SKETCH_TABLE_DOUBLES);
+        x.tab = c.take<char>(plan.table_bytes);
+        x.d = c.take<BatchDesc>((size_t)count);
+        x.sts = c.take<int>((size_t)count);
+        x.route = c.take<int>((size_t)count);
+        x.opt = c.take<int>((size_t)count);
+        x.gpass = c.take<int>((size_t)count);
+        x.mask = c.take<int>((size_t)count);
+        x.choice = c.take<int>((size_t)count);
+        x.anorm2 = c.take<double>((size_t)count);
+        x.shifts = c.take<double>((size_t)count);
+        x.orth = c.take<double>((size_t)count);
+        x.defect = c.take<double>((size_t)count);
+        x.feat = c.take<float>((size_t)count * MLP_IN);
+        x.pool = c.take<double>(S.pool_doubles);
+        x.upool = c.take<double>(plan.upool_doubles);
+        x.scratch = c.take<char>(plan.scratch_bytes);
     };
-    if (nw > 0 && (v = first_pass(0)) != OQR_OK) return v;
-    for (int w = 0; w < nw; ++w) {
+    Carve probe(nullptr);
+    layout(probe, D);
+    oqr_status v = ensure_ws(ctx, probe.off);
+    if (v != OQR_OK) return v;
+    Carve cv(ctx->ws);
+    layout(cv, D);
+    sel_fill(I, S, D.pool);
+    // pinned: the table image and the descriptors going up, the statuses, options and checks coming back
+    struct Pin {
+        char* img;
+        BatchDesc* desc;
+        int *sts, *opt;
+        double* orth;
+        DevStatus* st;
+    } P{};
+    auto pin_layout = [&](Carve& c, Pin& x) {
+        x.img = c.take<char>(plan.table_bytes);
+        x.desc = c.take<BatchDesc>((size_t)count);
+        x.sts = c.take<int>((size_t)count);
+        x.opt = c.take<int>((size_t)count);
+        x.orth = c.take<double>((size_t)count);
+        x.st = c.take<DevStatus>(1);
+    };
+    Carve pprobe(nullptr);
+    pin_layout(pprobe, P);
+    if ((v = sel_pinned(ctx, pprobe.off, s)) != OQR_OK) return v;
+    Carve pc(ctx->pin);
+    pin_layout(pc, P);
+    std::vector<char> image;
+    tc_batch_tables(plan, S.sh, S.in, D.tab, D.upool, image);
+    memcpy(P.img, image.data(), image.size());
+    memcpy(P.desc, S.desc.data(), sizeof(BatchDesc) * count);
+    OQR_TRY(cudaMemcpyAsync(D.tab, P.img, image.size(), cudaMemcpyHostToDevice, s));
+    OQR_TRY(cudaMemcpyAsync(D.d, P.desc, sizeof(BatchDesc) * count, cudaMemcpyHostToDevice, s));
+    OQR_TRY(cudaMemsetAsync(D.sts, 0, sizeof(int) * count, s));
+    if ((v = reset_status(ctx, s)) != OQR_OK) return v;
+    OQR_TRY(launch_sketch_table(D.wtab, s));
+    const uint64_t limit = 4000000000ull;
+    for (int w = 0; w < (int)plan.waves.size(); ++w) {
         const NvtxRange range("oqr: selector wave %d", w);
-        if (features_only) {
-            if (w + 1 < nw && (v = first_pass(w + 1)) != OQR_OK) return v;
-            continue;
-        }
-        // wave w + 1's first pass is queued before the host waits for wave w's choices
-        if (nbuf == 2 && w + 1 < nw && (v = first_pass(w + 1)) != OQR_OK) return v;
-        if (cudaEventSynchronize(ctx->sel_ev[w & 1]) != cudaSuccess) return OQR_ERR_CUDA;
         const TcBatchWave& W = plan.waves[w];
         const int f = W.first, cnt = W.count;
-        BatchDesc* dw = ddesc + f;
-        int* sw = sts + f;
-        void* scratch = scr[w % nbuf];
-        // the option each instance finishes with, and its passes
-        std::vector<TcBatchShape> sh2((size_t)cnt);
-        bool any_shift = false;
-        for (int k = 0; k < cnt; ++k) {
-            const int i = f + k;
-            int o = hch[i] < 0 || hch[i] > 3 ? SEL_SHIFTED : hch[i];
-            if ((o == SEL_ONE || o == SEL_TWO) && hst[i] != 0) o = SEL_SHIFTED;  // the unshifted probe broke down
-            opt[i] = o;
-            chk[i] = o == SEL_ONE || (check_all && o != SEL_FP64);
-            const int np = o == SEL_ONE ? 1 : o == SEL_TWO ? 2 : o == SEL_SHIFTED ? 3 : 1;
-            sh2[k] = TcBatchShape{sh1[i].m, sh1[i].n, 1, np + chk[i]};
-            hsh[i] = o == SEL_SHIFTED;
-            any_shift = any_shift || hsh[i];
-            hdA[i] = desc[i];
-            hdA[i].npass = hsh[i] ? 3 : 0;
-            hdB[i] = desc[i];
-            hdB[i].npass = np;
-            hup[i] = hsh[i] ? 0 : hst[i];
-        }
-        if (any_shift) {  // the shifted first pass from the same G0
-            OQR_TRY(cudaMemcpyAsync(dw, hdA + f, sizeof(BatchDesc) * cnt, cudaMemcpyHostToDevice, s));
-            OQR_TRY(cudaMemcpyAsync(sw, hup + f, sizeof(int) * cnt, cudaMemcpyHostToDevice, s));
-            OQR_TRY(cudaMemcpyAsync(dshifted + f, hsh + f, sizeof(int) * cnt, cudaMemcpyHostToDevice, s));
-            OQR_TRY(launch_batched_shifts(dw, cnt, dshifted + f, sums + 2 * f, 11.0, U64, shifts + f, s));
-            OQR_TRY(launch_batched_factor(dw, cnt, sw, 0, shifts + f, s));
-        }
-        OQR_TRY(cudaMemcpyAsync(dw, hdB + f, sizeof(BatchDesc) * cnt, cudaMemcpyHostToDevice, s));
-        // the later passes of the wave, with tables for exactly this wave (same packing as the first pass's)
-        const std::vector<TcBatchIn> in2(in.begin() + f, in.begin() + f + cnt);
-        const TcBatchPlan p2 = tc_batch_plan(sh2, budget);
-        if (p2.waves.size() != 1 || p2.table_bytes > pmax.table_bytes || p2.scratch_bytes > scratch_bytes)
-            return OQR_ERR_UNSUPPORTED;
-        std::vector<char> image2;
-        char* t2 = tab2[w % nbuf];
-        tc_batch_tables(p2, sh2, in2, t2, upool, image2);
-        memcpy(img[w & 1], image2.data(), image2.size());
-        OQR_TRY(cudaMemcpyAsync(t2, img[w & 1], image2.size(), cudaMemcpyHostToDevice, s));
-        for (int pass = 1; pass < p2.waves[0].maxpass; ++pass) {
-            OQR_TRY(tc_batch_gram(p2, 0, pass, t2, scratch, ctx->st, limit, ctx->sm_count, s));
-            OQR_TRY(launch_batched_last_defect(dw, cnt, sw, pass, defects + f, s));
+        BatchDesc* dw = D.d + f;
+        int* sw = D.sts + f;
+        const SelWave sel{dw,           sw,         D.route + f,  D.opt + f, D.gpass + f, D.mask + f, D.anorm2 + f,
+                          D.shifts + f, D.orth + f, D.defect + f, cnt,       extra,       tol};
+        const int* live = D.gpass + f;
+        // the probe: the split of A (read by every pass of the wave), G0, its Cholesky factor, the
+        // features, the network, the routes
+        OQR_TRY(tc_batch_split_a(plan, w, D.tab, D.scratch, s));
+        OQR_TRY(tc_batch_anorm2(plan, w, D.tab, D.scratch, sel.anorm2, s));
+        OQR_TRY(tc_batch_gram(plan, w, 0, D.tab, D.scratch, ctx->st, limit, ctx->sm_count, s));
+        OQR_TRY(launch_batched_gram_chol(dw, cnt, sw, s));
+        OQR_TRY(launch_features_batched(dw, cnt, sw, D.wtab, D.feat + (size_t)f * MLP_IN, s));
+        OQR_TRY(launch_mlp_forward(cnt, D.feat + (size_t)f * MLP_IN, params, 1, nullptr, D.choice + f, s));
+        OQR_TRY(launch_sel_route(sel, D.choice + f, s));
+        // the first factor: R1 = chol(G0 + s I) on the shifted route (elsewhere the probe's R1 stands),
+        // then Q1 = Z R1^{-1}
+        OQR_TRY(launch_batched_shifts(dw, cnt, sel.mask, sel.anorm2, 11.0, U64, sel.shifts, s));
+        OQR_TRY(launch_sel_shift_g(sel, s));
+        OQR_TRY(launch_batched_chol_solve(dw, cnt, sw, sel.mask, nullptr, s));
+        OQR_TRY(launch_sel_after_factor(sel, 0, s));
+        // passes 1..3 (4: the extra check of a late instance)
+        for (int pass = 1; pass < 4 + extra; ++pass) {
+            OQR_TRY(tc_batch_gram(plan, w, pass, D.tab, D.scratch, ctx->st, limit, ctx->sm_count, s, live));
+            OQR_TRY(launch_sel_decide(sel, pass, s));
             OQR_TRY(launch_batched_factor(dw, cnt, sw, pass, nullptr, s));
-            OQR_TRY(launch_batched_check(dw, cnt, sw, pass, orths + f, s));
+            if (pass == 1) {  // the late refactor: R1 = chol(G0 + s I), Q1 = Z R1^{-1}
+                OQR_TRY(launch_sel_late_mask(sel, s));
+                OQR_TRY(launch_batched_shifts(dw, cnt, sel.mask, sel.anorm2, 11.0, U64, sel.shifts, s));
+                OQR_TRY(launch_sel_late_prep(sel, s));
+                OQR_TRY(launch_batched_chol_solve(dw, cnt, sw, sel.mask, sel.mask, s));
+            }
+            OQR_TRY(launch_sel_after_factor(sel, pass, s));
         }
         OQR_TRY(launch_batched_rfinal(dw, cnt, sw, s));
     }
-    if (features_only) {
-        OQR_TRY(cudaMemcpyAsync(dchoice, perm.data(), sizeof(int) * count, cudaMemcpyHostToDevice, s));
-        OQR_TRY(launch_batch_scatter_rows_f32(feat, dchoice, count, MLP_IN, feat_out, s));
-        if (cudaStreamSynchronize(s) != cudaSuccess) return OQR_ERR_CUDA;
-        return OQR_OK;
-    }
-    std::vector<double> hor((size_t)count), hdef((size_t)count);
-    std::vector<int> hfin((size_t)count);
-    OQR_TRY(cudaMemcpyAsync(hfin.data(), sts, sizeof(int) * count, cudaMemcpyDeviceToHost, s));
-    OQR_TRY(cudaMemcpyAsync(hor.data(), orths, sizeof(double) * count, cudaMemcpyDeviceToHost, s));
-    OQR_TRY(cudaMemcpyAsync(hdef.data(), defects, sizeof(double) * count, cudaMemcpyDeviceToHost, s));
-    DevStatus hs;
-    OQR_TRY(cudaMemcpyAsync(&hs, ctx->st, sizeof(hs), cudaMemcpyDeviceToHost, s));
+    OQR_TRY(cudaMemcpyAsync(P.sts, D.sts, sizeof(int) * count, cudaMemcpyDeviceToHost, s));
+    OQR_TRY(cudaMemcpyAsync(P.opt, D.opt, sizeof(int) * count, cudaMemcpyDeviceToHost, s));
+    OQR_TRY(cudaMemcpyAsync(P.orth, D.orth, sizeof(double) * count, cudaMemcpyDeviceToHost, s));
+    OQR_TRY(cudaMemcpyAsync(P.st, ctx->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
     if (cudaStreamSynchronize(s) != cudaSuccess) return OQR_ERR_CUDA;
+    const bool timed_out = P.st->code != 0;
     res->status.assign((size_t)count, 0);
     res->choice.assign((size_t)count, 0);
     res->orth.assign((size_t)count, std::nan(""));
     for (int i = 0; i < count; ++i) {
-        const int b = perm[i];
-        res->status[b] = hs.code != 0 ? -1 : hfin[i];
-        res->choice[b] = opt[i];
-        if (chk[i]) res->orth[b] = hfin[i] == 0 ? hor[i] : INFINITY;
-        // the free check of a two-pass result: the Gram its second pass factored was far from I, so that
-        // pass did not bring the orthogonality to rounding level; the fallback chain redoes it (the shifted
-        // option, the most robust, is accepted once it completes, as the network's answer for hard instances)
-        if (!chk[i] && opt[i] == SEL_TWO && hfin[i] == 0 && !(hdef[i] <= LAST_DEFECT_MAX)) res->status[b] = -2;
+        const int b = S.perm[i];
+        res->status[b] = timed_out ? -1 : P.sts[i];
+        res->choice[b] = P.opt[i];
+        res->orth[b] = P.orth[i];
     }
-    return hs.code != 0 ? OQR_ERR_TIMEOUT : OQR_OK;
+    return timed_out ? OQR_ERR_TIMEOUT : OQR_OK;
 }
 
-// A sub-batch call for the fallback chain: outputs into the caller's Q and R of
-// those instances; status (and orth) through the context's small selector buffer.
-oqr_status selector_subset(oqr_ctx* ctx, const SelInputs& I, const std::vector<int>& idx, int mode,
-                           SelResult* res, cudaStream_t s)
+// FP64 A-CholQR2 over a sub-batch (the fallback and the network's FP64 choices): outputs into the
+// caller's Q and R of those instances, statuses through the context's small selector buffer.
+oqr_status selector_fp64(oqr_ctx* ctx, const SelInputs& I, const std::vector<int>& idx, SelResult* res,
+                         cudaStream_t s)
 {
     const int k = (int)idx.size();
     if (k == 0) return OQR_OK;
-    std::vector<int> m(k), n(k), pr(k, OQR_BATCH_SCHOLQR3_TC);
+    std::vector<int> m(k), n(k);
     std::vector<const double*> A(k), Z(k);
     std::vector<double*> Q(k), R(k);
     std::vector<long> lda(k), ldz(k), ldq(k), ldr(k);
@@ -1083,7 +1111,7 @@ oqr_status selector_subset(oqr_ctx* ctx, const SelInputs& I, const std::vector<i
         ldq[j] = I.ldq[b];
         ldr[j] = I.ldr[b];
     }
-    const size_t need = (size_t)k * (sizeof(int) + sizeof(double)) + 256;
+    const size_t need = (size_t)k * sizeof(int) + 256;
     if (ctx->sel_bytes < need) {
         if (ctx->sel_buf) {
             cudaStreamSynchronize(s);
@@ -1097,27 +1125,18 @@ oqr_status selector_subset(oqr_ctx* ctx, const SelInputs& I, const std::vector<i
         }
         ctx->sel_bytes = need;
     }
-    double* dorth = static_cast<double*>(ctx->sel_buf);
-    int* dst = reinterpret_cast<int*>(dorth + k);
-    oqr_status v;
-    if (mode == 0) {
-        v = batched_fp64_impl(ctx, k, m.data(), n.data(), A.data(), lda.data(), Z.data(), ldz.data(), Q.data(),
-                              ldq.data(), R.data(), ldr.data(), nullptr, dst, s);
-    } else {
-        v = oqr_batched_mixed(ctx, k, m.data(), n.data(), A.data(), lda.data(), Z.data(), ldz.data(), Q.data(),
-                              ldq.data(), R.data(), ldr.data(), pr.data(), dst, dorth, s);
-    }
+    int* dst = static_cast<int*>(ctx->sel_buf);
+    oqr_status v = batched_fp64_impl(ctx, k, m.data(), n.data(), A.data(), lda.data(), Z.data(), ldz.data(),
+                                     Q.data(), ldq.data(), R.data(), ldr.data(), nullptr, dst, s);
     if (v != OQR_OK) return v;
     std::vector<int> hst(k);
-    std::vector<double> hor(k);
     OQR_TRY(cudaMemcpyAsync(hst.data(), dst, sizeof(int) * k, cudaMemcpyDeviceToHost, s));
-    if (mode != 0) OQR_TRY(cudaMemcpyAsync(hor.data(), dorth, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
     if (cudaStreamSynchronize(s) != cudaSuccess) return OQR_ERR_CUDA;
     for (int j = 0; j < k; ++j) {
         const int b = idx[j];
         res->status[b] = hst[j];
-        res->choice[b] = mode == 0 ? SEL_FP64 : SEL_SHIFTED;
-        res->orth[b] = mode == 0 ? std::nan("") : (hst[j] == 0 ? hor[j] : INFINITY);
+        res->choice[b] = SEL_FP64;
+        res->orth[b] = std::nan("");
     }
     return OQR_OK;
 }
@@ -1125,23 +1144,18 @@ oqr_status selector_subset(oqr_ctx* ctx, const SelInputs& I, const std::vector<i
 oqr_status selector_batch(oqr_ctx* ctx, const SelInputs& I, const oqr_opts& o, int* status, cudaStream_t s)
 {
     if (!o.selector_params) return OQR_ERR_INVALID_ARG;
-    SelResult res;
-    oqr_status v = selector_waves(ctx, I, o.selector_params, o.selector_check != 0, nullptr, &res, s);
-    if (v != OQR_OK && v != OQR_ERR_TIMEOUT) return v;
     const double tol = o.selector_tol > 0 ? o.selector_tol : 1e-12;
+    SelResult res;
+    oqr_status v = selector_run(ctx, I, o.selector_params, tol, o.selector_check != 0, &res, s);
+    if (v != OQR_OK && v != OQR_ERR_TIMEOUT) return v;
     if (v == OQR_OK) {
-        auto failed = [&](int b) {
-            return res.status[b] != 0 || (!std::isnan(res.orth[b]) && !(res.orth[b] <= tol));
-        };
-        // fallback 1: shifted A-CholQR3 on the tensor cores for a failed check or a breakdown of an unshifted option
-        std::vector<int> fb1, fb2;
+        // FP64 A-CholQR2 for the network's FP64 choices, a breakdown, a failed last-pass check, or a
+        // failed extra check
+        std::vector<int> fb;
         for (int b = 0; b < I.count; ++b)
-            if (res.choice[b] != SEL_SHIFTED && res.choice[b] != SEL_FP64 && failed(b)) fb1.push_back(b);
-        if ((v = selector_subset(ctx, I, fb1, 1, &res, s)) != OQR_OK) return v;
-        // fallback 2 (and the network's own FP64 choices): FP64 A-CholQR2
-        for (int b = 0; b < I.count; ++b)
-            if (res.choice[b] == SEL_FP64 || failed(b)) fb2.push_back(b);
-        if ((v = selector_subset(ctx, I, fb2, 0, &res, s)) != OQR_OK) return v;
+            if (res.choice[b] == SEL_FP64 || res.status[b] != 0 || (!std::isnan(res.orth[b]) && !(res.orth[b] <= tol)))
+                fb.push_back(b);
+        if ((v = selector_fp64(ctx, I, fb, &res, s)) != OQR_OK) return v;
     }
     OQR_TRY(cudaMemcpy(status, res.status.data(), sizeof(int) * I.count, cudaMemcpyHostToDevice));
     if (o.batch_orth)
@@ -1453,7 +1467,7 @@ oqr_status oqr_batched_features(oqr_ctx* ctx, int count, const int* m, const int
         if (bad_matrix(A[b], lda[b], mb, mb) || bad_matrix(Z[b], ldz[b], mb, nb)) return OQR_ERR_INVALID_ARG;
     }
     const SelInputs in{count, m, n, A, lda, Z, ldz, nullptr, nullptr, nullptr, nullptr};
-    return selector_waves(ctx, in, nullptr, false, feat, nullptr, static_cast<cudaStream_t>(stream));
+    return features_waves(ctx, in, feat, static_cast<cudaStream_t>(stream));
 }
 
 oqr_status oqr_batched_mixed(oqr_ctx* ctx, int count, const int* m, const int* n, const double* const* A,
@@ -1494,7 +1508,7 @@ oqr_status oqr_batched_mixed(oqr_ctx* ctx, int count, const int* m, const int* n
     const size_t budget = ctx->batch_budget ? ctx->batch_budget : BATCH_WAVE_BYTES;
     key.push_back((long)budget);
     const TcBatchPlan plan = tc_batch_plan(sh, budget);
-    auto layout = [&](Carve& c, char** tab, BatchDesc** d, int** sts, int** dperm, int** dshifted, double** sums,
+    auto layout = [&](Carve& c, char** tab, BatchDesc** d, int** sts, int** dperm, int** dshifted, double** anorm2,
                       double** shifts, double** orths, double** pool, double** upool, void** scratch) {
         *tab = c.take<char>(plan.table_bytes);
         *orths = c.take<double>((size_t)count);
@@ -1502,7 +1516,7 @@ oqr_status oqr_batched_mixed(oqr_ctx* ctx, int count, const int* m, const int* n
         *sts = c.take<int>((size_t)count);
         *dperm = c.take<int>((size_t)count);
         *dshifted = c.take<int>((size_t)count);
-        *sums = c.take<double>((size_t)2 * count);
+        *anorm2 = c.take<double>((size_t)count);
         *shifts = c.take<double>((size_t)count);
         *pool = c.take<double>(pool_doubles);
         *upool = c.take<double>((size_t)plan.upool_doubles);
@@ -1511,14 +1525,14 @@ oqr_status oqr_batched_mixed(oqr_ctx* ctx, int count, const int* m, const int* n
     char* tab;
     BatchDesc* ddesc;
     int *sts, *dperm, *dshifted;
-    double *sums, *shifts, *orths, *pool, *upool;
+    double *anorm2, *shifts, *orths, *pool, *upool;
     void* scratch;
     Carve probe(nullptr);
-    layout(probe, &tab, &ddesc, &sts, &dperm, &dshifted, &sums, &shifts, &orths, &pool, &upool, &scratch);
+    layout(probe, &tab, &ddesc, &sts, &dperm, &dshifted, &anorm2, &shifts, &orths, &pool, &upool, &scratch);
     oqr_status v = ensure_ws(ctx, probe.off);
     if (v != OQR_OK) return v;
     Carve cv(ctx->ws);
-    layout(cv, &tab, &ddesc, &sts, &dperm, &dshifted, &sums, &shifts, &orths, &pool, &upool, &scratch);
+    layout(cv, &tab, &ddesc, &sts, &dperm, &dshifted, &anorm2, &shifts, &orths, &pool, &upool, &scratch);
     key[1] = (long)reinterpret_cast<uintptr_t>(ctx->ws);
     // per instance (sorted order): its descriptor (one Gram partial = the product's half C) and tensor-core inputs
     std::vector<BatchDesc> desc((size_t)count);
@@ -1567,9 +1581,9 @@ oqr_status oqr_batched_mixed(oqr_ctx* ctx, int count, const int* m, const int* n
             bool any_shift = false;
             for (int i = W.first; i < W.first + W.count; ++i) any_shift = any_shift || shifted[i];
             if ((e = tc_batch_split_a(plan, w, tab, scratch, s)) != cudaSuccess) return e;
-            if (any_shift &&
-                (e = launch_batched_shifts(dw, W.count, dshifted + W.first, sums + 2 * W.first, 11.0, U64,
-                                           shifts + W.first, s)) != cudaSuccess)
+            if (any_shift && ((e = tc_batch_anorm2(plan, w, tab, scratch, anorm2 + W.first, s)) != cudaSuccess ||
+                              (e = launch_batched_shifts(dw, W.count, dshifted + W.first, anorm2 + W.first, 11.0, U64,
+                                                         shifts + W.first, s)) != cudaSuccess))
                 return e;
             for (int pass = 0; pass < W.maxpass; ++pass) {
                 if ((e = tc_batch_gram(plan, w, pass, tab, scratch, ctx->st, limit, ctx->sm_count, s)) != cudaSuccess)

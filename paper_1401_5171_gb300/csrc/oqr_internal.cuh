@@ -275,6 +275,7 @@ struct BatchDesc {
     double* G;         // n x n
     double* R1;        // n x n
     double* R2;        // n x n
+    double* G0;        // n x n: the first pass's Gram, kept by the selector for a later shifted refactor
 };
 cudaError_t launch_batched_cholqr2(const BatchDesc* d, int count, const int* const* cls_idx, const int* cls_count,
                                    const int* cls_max_splits, int max_n, int* status, cudaStream_t s);
@@ -286,13 +287,17 @@ cudaError_t launch_batched_cholqr2(const BatchDesc* d, int count, const int* con
 //           pass > 0 R1 <- R2 R1;
 //   rfinal: the caller's R_b = R1;
 //   shifts: shifts[b] = c u (m n + n (n + 1)) ||A_b||_F ||Z_b||_F^2 where
-//           shifted[b], else 0 (sums: 2 count doubles of scratch);
+//           mask[b], else 0, with ||A_b||_F^2 = anorm2[b] (from the split of A);
 //   scatter: status[perm[i]] = st_sorted[i], or -1 for every instance when a
 //           tensor-core wait of the context timed out.
 cudaError_t launch_batched_factor(const BatchDesc* d, int count, int* status, int pass, const double* shifts,
                                   cudaStream_t s);
 cudaError_t launch_batched_rfinal(const BatchDesc* d, int count, int* status, cudaStream_t s);
-cudaError_t launch_batched_shifts(const BatchDesc* d, int count, const int* shifted, double* sums, double c,
+// R1 = chol(G) for the instances with chol_mask[b] != 0, then Q = Z / R1 for those with solve_mask[b] != 0
+// (a first pass from a new G; NULL masks: every instance).
+cudaError_t launch_batched_chol_solve(const BatchDesc* d, int count, int* status, const int* chol_mask,
+                                      const int* solve_mask, cudaStream_t s);
+cudaError_t launch_batched_shifts(const BatchDesc* d, int count, const int* mask, const double* anorm2, double c,
                                   double u, double* shifts, cudaStream_t s);
 cudaError_t launch_batch_status_scatter(const int* st_sorted, const int* perm, int count, const DevStatus* st,
                                         int* status, cudaStream_t s);
@@ -307,7 +312,11 @@ cudaError_t launch_batched_gram_chol(const BatchDesc* d, int count, int* status,
 cudaError_t launch_batch_scatter_rows_f32(const float* in, const int* perm, int count, int width, float* out,
                                           cudaStream_t s);
 // The selector's 16 features of each instance of a batch after its first FP64-accurate pass (k_features.cu).
-cudaError_t launch_features_batched(const BatchDesc* d, int count, const int* status, float* feat, cudaStream_t s);
+// wtab: the sketches W_n of every n <= BATCH_MAX_N (launch_sketch_table, SKETCH_TABLE_DOUBLES doubles).
+cudaError_t launch_features_batched(const BatchDesc* d, int count, const int* status, const double* wtab, float* feat,
+                                    cudaStream_t s);
+constexpr long SKETCH_TABLE_DOUBLES = (long)BATCH_MAX_N * (BATCH_MAX_N + 1) * (2 * BATCH_MAX_N + 1) / 3;
+cudaError_t launch_sketch_table(double* tab, cudaStream_t s);
 // defect[b] = ||Q^T A Q - I||_2 estimate of the Gram that instance b's last factor pass factors (the
 // instances with 2 or more passes whose last factor pass is pass), read from that Gram's partial before the
 // factor; a free check of the result: the last pass leaves orthogonality at rounding level when it is small.
@@ -315,6 +324,46 @@ cudaError_t launch_batched_last_defect(const BatchDesc* d, int count, const int*
                                        cudaStream_t s);
 // out[perm[i]] = in[i] (count doubles).
 cudaError_t launch_batch_scatter_f64(const double* in, const int* perm, int count, double* out, cudaStream_t s);
+
+// The learned selector's decisions on the device (k_select.cu), over a wave of count instances.
+// Routes: SEL_R_PLAIN (unshifted passes), SEL_R_SHIFT (shifted A-CholQR3 from the probe's Gram), SEL_R_FP64
+// (FP64 A-CholQR2 after the waves), SEL_R_LATE (an unshifted result that failed: shifted A-CholQR3 redone
+// from the saved probe Gram G0).  Options reported: SEL_ONE, SEL_TWO, SEL_SHIFTED, SEL_FP64.
+// gpass[b]: the Gram passes instance b takes part in (the tensor-core launches skip the others);
+// BatchDesc.npass: its factor passes.  Status -3 (transient): the instance skips this pass's factor for
+// its late refactor.
+constexpr int SEL_R_PLAIN = 0, SEL_R_SHIFT = 1, SEL_R_FP64 = 2, SEL_R_LATE = 3;
+constexpr int SEL_ONE = 0, SEL_TWO = 1, SEL_SHIFTED = 2, SEL_FP64 = 3;
+constexpr int SEL_ST_LATE = -3;
+struct SelWave {
+    BatchDesc* d;   // count descriptors (npass updated on the device)
+    int* status;
+    int* route;
+    int* opt;       // the option used
+    int* gpass;
+    int* mask;      // scratch: shifted first pass or late refactor
+    double* anorm2; // ||A_b||_F^2 (from the split of A)
+    double* shifts;
+    double* orth;   // ||E||_F of the checked Gram, NaN where not checked
+    double* defect; // ||E||_F of the Gram that the last factor pass factored
+    int count;
+    int extra;      // 1: every result is checked with one more Gram
+    double tol;
+};
+// After the probe's Gram, its Cholesky, the features and the network: routes, pass counts, G0, the mask
+// of shifted first passes.
+cudaError_t launch_sel_route(const SelWave& w, const int* choice, cudaStream_t s);
+// After the Gram of pass p (p >= 1): ONE / TWO / LATE for plain instances at p = 1, the defect of the
+// Gram that a shifted route's last factor pass factors (reported), the extra check's value.
+cudaError_t launch_sel_decide(const SelWave& w, int pass, cudaStream_t s);
+// After the factor of pass p: an instance whose factor failed takes part in no later Gram.
+cudaError_t launch_sel_after_factor(const SelWave& w, int pass, cudaStream_t s);
+// The late refactor: mask = late instances, status 0, G = G0 + shift I (shifts from launch_batched_shifts
+// over the mask), then launch_batched_chol_solve over the mask.
+cudaError_t launch_sel_late_mask(const SelWave& w, cudaStream_t s);
+cudaError_t launch_sel_late_prep(const SelWave& w, cudaStream_t s);
+// G += shift I for the instances of the mask (the shifted route's first factor, G holding G0).
+cudaError_t launch_sel_shift_g(const SelWave& w, cudaStream_t s);
 
 // Packed tensor-core batches (k_tc.cu).  Instances (sorted by m, largest
 // first) are cut into waves whose slice planes fit a byte budget; a wave's A
@@ -326,7 +375,7 @@ struct TcBatchShape {
     int mode0;  // tensor-core mode of pass 0 (1: EMU64, 3: TC2); later passes are EMU64
     int npass;  // Gram passes: 1..3 normal-equation passes, + 1 when the result is checked (Q^T A Q)
 };
-constexpr int TC_BATCH_MAX_PASS = 4;
+constexpr int TC_BATCH_MAX_PASS = 5;
 struct TcBatchIn {
     const double* A;
     long lda;
@@ -366,9 +415,15 @@ void tc_batch_tables(const TcBatchPlan& p, const std::vector<TcBatchShape>& sh, 
                      const void* table_dev, double* upool, std::vector<char>& image);
 // Wave w: the split of A (once), then the Gram of pass p into the C of each
 // instance with npass > p (X = Z in pass 0, Q later).
+// The split also leaves each tile's share of ||A||_F^2 in the scratch; tc_batch_anorm2 sums them per
+// instance (fixed order): out[i] = ||A_i||_F^2 for the wave's instance i.
 cudaError_t tc_batch_split_a(const TcBatchPlan& p, int w, const void* table_dev, void* scratch, cudaStream_t s);
+cudaError_t tc_batch_anorm2(const TcBatchPlan& p, int w, const void* table_dev, void* scratch, double* out,
+                            cudaStream_t s);
+// live (the wave's per-instance Gram pass counts on the device, or NULL): instances with live[i] <= pass
+// sit the pass out, their tiles skipped, so that one set of tables serves passes chosen on the device.
 cudaError_t tc_batch_gram(const TcBatchPlan& p, int w, int pass, const void* table_dev, void* scratch,
-                          DevStatus* st, uint64_t limit_ns, int sms, cudaStream_t s);
+                          DevStatus* st, uint64_t limit_ns, int sms, cudaStream_t s, const int* live = nullptr);
 
 
 // Selector (k_mlp.cu, k_features.cu).
