@@ -420,11 +420,13 @@ def run_selector(ctx, torch, dev, count, stream):
     stc = st.cpu().numpy()
     raw = selector.choose(ctx, ctx.oqr_batched_features(As, Zs), P).cpu().numpy()   # the network's own choices
     final = choice.cpu().numpy()
-    worst, above = 0.0, 0
+    worst, above, failed = 0.0, 0, []
     for b in range(count):
         n = Zs[b].shape[1]
         if stc[b] != 0:
             above += 1
+            failed.append({"m": int(Zs[b].shape[0]), "n": int(n), "kappa_A": float(tab["kappa_A"][b]),
+                           "kappa_Z": float(tab["kappa_Z"][b]), "status": int(stc[b]), "option": int(final[b])})
             continue
         E = Qs[b].T @ (As[b] @ Qs[b]) - torch.eye(n, dtype=torch.float64, device=dev)
         o = torch.linalg.eigvalsh(0.5 * (E + E.T)).abs().max().item()
@@ -435,6 +437,7 @@ def run_selector(ctx, torch, dev, count, stream):
     st2 = torch.empty(count, dtype=torch.int32, device=dev)
     t_shift = events_ms(torch, stream, lambda: ctx.oqr_batched(As, Zs, Qs, Rs, status=st2,
                                                                   mode=oqr.OQR_BATCHED_SHIFTED_TC, stream=stream))
+    shift_failed = int((st2 != 0).sum().item())
 
     def cholqr2_checked():
         _, _, st2, o2 = ctx.oqr_batched_mixed(As, Zs, program=[2] * count, Qs=Qs, Rs=Rs, check=True,
@@ -450,9 +453,10 @@ def run_selector(ctx, torch, dev, count, stream):
                 "options_used": np.bincount(final, minlength=4).tolist(),
                 "network_choices": np.bincount(raw, minlength=4).tolist(),
                 "changed_by_probe_or_fallback": int((raw != final).sum()),
-                "instances_above_bar": int(above), "worst_orth_over_bar": worst,
+                "instances_above_bar": int(above), "worst_orth_over_bar": worst, "failed": failed[:5],
                 "bar": "max(1e-12, m u ||A||_2 ||Q||_2^2) per instance (Thm 4.1 with c = 1)",
-                "always_shifted_tc": {"qr_per_s": count / (t_shift / 1e3), "ms_per_batch": t_shift},
+                "always_shifted_tc": {"qr_per_s": count / (t_shift / 1e3), "ms_per_batch": t_shift,
+                                      "breakdowns": shift_failed},
                 "always_cholqr2_tc_checked": {"qr_per_s": count / (t_c2 / 1e3), "ms_per_batch": t_c2},
                 "gain_over_best_fixed": min(t_shift, t_c2) / t_sel})
     del As, Zs, Qs, Rs

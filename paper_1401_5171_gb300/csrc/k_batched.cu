@@ -243,9 +243,11 @@ __global__ void __launch_bounds__(256) potrf_batched_kernel(const BatchDesc* __r
     }
 }
 
-// Q = X / R row by row, 128 rows per CTA, R (<= 64 x 64) in shared memory.
+// Q = X / R row by row, TRSM_ROWS rows per CTA (one per thread; FP64 is scarce, so an instance's rows
+// are spread over many SMs), R (<= 64 x 64) in shared memory.
 // mask (or NULL for all): the instances to solve.
-__global__ void __launch_bounds__(128) trsm_batched_kernel(const BatchDesc* __restrict__ d, const int* status,
+constexpr int TRSM_ROWS = 64;
+__global__ void __launch_bounds__(TRSM_ROWS) trsm_batched_kernel(const BatchDesc* __restrict__ d, const int* status,
                                                            int pass_in_place, int which, int pass,
                                                            const int* mask = nullptr)
 {
@@ -255,10 +257,10 @@ __global__ void __launch_bounds__(128) trsm_batched_kernel(const BatchDesc* __re
     const BatchDesc D = d[b];
     if (status[b] != 0 || pass >= D.npass || (mask && !mask[b])) return;
     const int m = D.m, n = D.n;
-    const long row0 = (long)blockIdx.x * 128;
+    const long row0 = (long)blockIdx.x * TRSM_ROWS;
     if (row0 >= m) return;  // the grid covers the largest m of the batch
     const double* Rin = which == 0 ? D.R1 : D.R2;
-    for (int e = threadIdx.x; e < n * n; e += 128) {
+    for (int e = threadIdx.x; e < n * n; e += TRSM_ROWS) {
         const int i = e % n, j = e / n;
         Rs[i][j] = Rin[i + (size_t)j * n];
     }
@@ -334,40 +336,15 @@ __global__ void rfinal_batched_kernel(const BatchDesc* __restrict__ d, const int
     D.R[i + (long)j * D.ldr] = i <= j ? D.R1[i + (size_t)j * n] : 0.0;
 }
 
-// s_b = c u (m n + n (n + 1)) ||A_b||_F ||Z_b||_F^2 for a shifted instance (mask[b] != 0), else 0; ||A_b||_F^2
-// comes from the split of A (anorm2[b]), ||Z_b||_F^2 is summed here by one block per instance in a fixed order.
-__global__ void __launch_bounds__(256) shift_batched_kernel(const BatchDesc* __restrict__ d,
-                                                            const int* __restrict__ mask, const double* anorm2,
-                                                            double c, double u, double* shifts)
+// s_b = c u (m n + n (n + 1)) ||A_b||_F ||Z_b||_F^2 for a shifted instance (mask[b] != 0), else 0, from the
+// squared norms the splits summed (anorm2, znorm2).
+__global__ void shift_batched_kernel(const BatchDesc* __restrict__ d, int count, const int* __restrict__ mask,
+                                     const double* anorm2, const double* znorm2, double c, double u, double* shifts)
 {
-    __shared__ double red[8];
-    const int b = blockIdx.x;
-    if (!mask[b]) {
-        if (threadIdx.x == 0) shifts[b] = 0.0;
-        return;
-    }
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= count) return;
     const BatchDesc D = d[b];
-    double sz = 0.0, sz2 = 0.0;  // two chains: the loads of one column overlap the other's
-    int j = 0;
-    for (; j + 1 < D.n; j += 2)
-        for (int i = threadIdx.x; i < D.m; i += 256) {
-            const double v = D.Z[i + (long)j * D.ldz], v2 = D.Z[i + (long)(j + 1) * D.ldz];
-            sz = fma(v, v, sz);
-            sz2 = fma(v2, v2, sz2);
-        }
-    for (; j < D.n; ++j)
-        for (int i = threadIdx.x; i < D.m; i += 256) {
-            const double v = D.Z[i + (long)j * D.ldz];
-            sz = fma(v, v, sz);
-        }
-    sz += sz2;
-    for (int o = 16; o > 0; o >>= 1) sz += __shfl_xor_sync(0xffffffffu, sz, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sz;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const double z2 = ((red[0] + red[1]) + (red[2] + red[3])) + ((red[4] + red[5]) + (red[6] + red[7]));
-        shifts[b] = c * u * ((double)D.m * D.n + (double)D.n * (D.n + 1)) * sqrt(anorm2[b]) * z2;
-    }
+    shifts[b] = mask[b] ? c * u * ((double)D.m * D.n + (double)D.n * (D.n + 1)) * sqrt(anorm2[b]) * znorm2[b] : 0.0;
 }
 
 // ||E||_2 estimate of E = G - I for the instances checked at this pass (one CTA each).
@@ -471,8 +448,8 @@ cudaError_t launch_batched_cholqr2(const BatchDesc* d, int count, const int* con
         dim3 gr((max_n * max_n + 255) / 256, count);
         reduce_batched_kernel<<<gr, 256, 0, s>>>(d, status, nullptr, pass);
         potrf_batched_kernel<<<count, 256, 0, s>>>(d, status, pass, pass);
-        dim3 gt(BATCH_MAX_M / 128, count);
-        trsm_batched_kernel<<<gt, 128, 0, s>>>(d, status, pass, pass, pass);
+        dim3 gt(BATCH_MAX_M / TRSM_ROWS, count);
+        trsm_batched_kernel<<<gt, TRSM_ROWS, 0, s>>>(d, status, pass, pass, pass);
     }
     dim3 gp((64 * 64 + 255) / 256, count);
     rprod_batched_kernel<<<gp, 256, 0, s>>>(d, status);
@@ -486,8 +463,8 @@ cudaError_t launch_batched_factor(const BatchDesc* d, int count, int* status, in
     dim3 gr((BATCH_MAX_N * BATCH_MAX_N + 255) / 256, count);
     reduce_batched_kernel<<<gr, 256, 0, s>>>(d, status, pass == 0 ? shifts : nullptr, pass);
     potrf_batched_kernel<<<count, 256, 0, s>>>(d, status, which, pass);
-    dim3 gt(BATCH_MAX_M / 128, count);
-    trsm_batched_kernel<<<gt, 128, 0, s>>>(d, status, pass > 0, which, pass);
+    dim3 gt(BATCH_MAX_M / TRSM_ROWS, count);
+    trsm_batched_kernel<<<gt, TRSM_ROWS, 0, s>>>(d, status, pass > 0, which, pass);
     if (pass > 0) racc_batched_kernel<<<count, 256, 0, s>>>(d, status, pass);
     return cudaGetLastError();
 }
@@ -504,8 +481,8 @@ cudaError_t launch_batched_chol_solve(const BatchDesc* d, int count, int* status
                                       const int* solve_mask, cudaStream_t s)
 {
     potrf_batched_kernel<<<count, 256, 0, s>>>(d, status, 0, 0, chol_mask);
-    dim3 gt(BATCH_MAX_M / 128, count);
-    trsm_batched_kernel<<<gt, 128, 0, s>>>(d, status, 0, 0, 0, solve_mask);
+    dim3 gt(BATCH_MAX_M / TRSM_ROWS, count);
+    trsm_batched_kernel<<<gt, TRSM_ROWS, 0, s>>>(d, status, 0, 0, 0, solve_mask);
     return cudaGetLastError();
 }
 
@@ -516,10 +493,10 @@ cudaError_t launch_batched_rfinal(const BatchDesc* d, int count, int* status, cu
     return cudaGetLastError();
 }
 
-cudaError_t launch_batched_shifts(const BatchDesc* d, int count, const int* mask, const double* anorm2, double c,
-                                  double u, double* shifts, cudaStream_t s)
+cudaError_t launch_batched_shifts(const BatchDesc* d, int count, const int* mask, const double* anorm2,
+                                  const double* znorm2, double c, double u, double* shifts, cudaStream_t s)
 {
-    if (count > 0) shift_batched_kernel<<<count, 256, 0, s>>>(d, mask, anorm2, c, u, shifts);
+    if (count > 0) shift_batched_kernel<<<(count + 127) / 128, 128, 0, s>>>(d, count, mask, anorm2, znorm2, c, u, shifts);
     return cudaGetLastError();
 }
 

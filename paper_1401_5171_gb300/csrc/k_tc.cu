@@ -452,19 +452,33 @@ __global__ void __launch_bounds__(256, 4) split_lower_batch_kernel(const SplitIn
                                        code & 255, I.off, erows, sq + blockIdx.x);
 }
 
-// ||A_i||_F^2 of the wave's instances from their tiles' shares: one block per instance, each thread a
-// strided share of the tiles, then a fixed tree.
-__global__ void __launch_bounds__(128) anorm_batch_kernel(const SplitInst* __restrict__ inst,
-                                                          const double* __restrict__ sq, double* out)
+// ||A_i||_F^2 and ||Z_i||_F^2 of the wave's instances from the splits' shares (A: per tile, Z: per chunk
+// and column): one block per instance, each thread a strided share, then a fixed tree.
+__global__ void __launch_bounds__(128) norms_batch_kernel(const SplitInst* __restrict__ instA,
+                                                          const SplitInst* __restrict__ instZ,
+                                                          const double* __restrict__ asq,
+                                                          const double* __restrict__ zsq, long ecols, double* anorm2,
+                                                          double* znorm2)
 {
-    __shared__ double red[4];
-    const SplitInst I = inst[blockIdx.x];
-    double a = 0.0;
-    for (int t = threadIdx.x; t < I.ntiles; t += 128) a += sq[I.tile0 + t];
-    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+    __shared__ double red[2][4];
+    const SplitInst IA = instA[blockIdx.x], IZ = instZ[blockIdx.x];
+    double a = 0.0, z = 0.0;
+    for (int t = threadIdx.x; t < IA.ntiles; t += 128) a += asq[IA.tile0 + t];
+    for (int t = threadIdx.x; t < IZ.kch * IZ.cols; t += 128)
+        z += zsq[(size_t)(t / IZ.cols) * ecols + IZ.off + t % IZ.cols];
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        z += __shfl_xor_sync(0xffffffffu, z, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = a;
+        red[1][threadIdx.x >> 5] = z;
+    }
     __syncthreads();
-    if (threadIdx.x == 0) out[blockIdx.x] = (red[0] + red[1]) + (red[2] + red[3]);
+    if (threadIdx.x == 0) {
+        anorm2[blockIdx.x] = (red[0][0] + red[0][1]) + (red[0][2] + red[0][3]);
+        znorm2[blockIdx.x] = (red[1][0] + red[1][1]) + (red[1][2] + red[1][3]);
+    }
 }
 
 // X (K x C, column-major) -> slices written column-major (column c, k
@@ -473,9 +487,10 @@ __global__ void __launch_bounds__(128) anorm_batch_kernel(const SplitInst* __res
 // output column is offset by coff and the exponents are strided by ecols (a
 // packed batch).
 template <int MODE, int CW>
+// sq (or NULL): the chunk's sum of squares of the column, written to sq[kc * ecols + coff + c].
 __device__ __forceinline__ void split_tall_column(int K, const double* __restrict__ X, long ldx, long c, int S,
                                                   __nv_bfloat16* planes, long ldp, size_t plane, int* eX, int* xmax,
-                                                  int kc, long coff, long ecols)
+                                                  int kc, long coff, long ecols, double* sq = nullptr)
 {
     constexpr bool SCALED = MODE != 0;  // exponents are recorded
     constexpr int VPL = CW / 32;
@@ -491,6 +506,13 @@ __device__ __forceinline__ void split_tall_column(int K, const double* __restric
     if (SCALED && lane == 0) {
         eX[(size_t)kc * ecols + coff + c] = e;
         if (e != EXP_NONE) atomicMax(&xmax[coff + c], e);
+    }
+    if (sq) {
+        double a = 0.0;
+#pragma unroll
+        for (int j = 0; j < VPL; ++j) a = fma(v[j], v[j], a);
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (lane == 0) sq[(size_t)kc * ecols + coff + c] = a;
     }
     store_run<MODE, VPL>(planes, plane, (size_t)(coff + c) * ldp + k0, S, v, e);
 }
@@ -510,7 +532,8 @@ __global__ void __launch_bounds__(256) split_tall_kernel(int K, int C, const dou
 __global__ void __launch_bounds__(256) split_tall_batch_kernel(const SplitInst* __restrict__ inst,
                                                                const int* __restrict__ colinst, int S,
                                                                __nv_bfloat16* planes, long ldp, size_t plane, int* eX,
-                                                               int* xmax, long ecols, const int* live, int pass)
+                                                               int* xmax, long ecols, const int* live, int pass,
+                                                               double* sq)
 {
     const long gc = (long)blockIdx.y * 8 + (threadIdx.x >> 5);
     if (gc >= ecols) return;
@@ -518,7 +541,7 @@ __global__ void __launch_bounds__(256) split_tall_batch_kernel(const SplitInst* 
     const SplitInst I = inst[colinst[gc]];
     const int kc = blockIdx.x;
     if (kc >= I.kch) return;
-    split_tall_column<1, KCH_EMU>(I.K, I.X, I.ldx, gc - I.off, S, planes, ldp, plane, eX, xmax, kc, I.off, ecols);
+    split_tall_column<1, KCH_EMU>(I.K, I.X, I.ldx, gc - I.off, S, planes, ldp, plane, eX, xmax, kc, I.off, ecols, sq);
 }
 
 __global__ void fill_int_kernel(int* p, long n, int v)
@@ -564,6 +587,7 @@ struct TcArgs {
     const TcInst* inst;   // [ninst]
     const int* inst_item0;  // [ninst + 1]: first item of each instance, then the total
     const int* rblk;      // a batch: the reduction's blocks (instance << 10 | block)
+    int nrblk;            // a batch: their count
     const int* live;      // a batch, or NULL: the wave's Gram pass counts; instances with live[wi] <= pass sit
     int pass;             // this launch out (their items are not in list, their outputs are not written)
     const int* list;      // NULL: items 0..nitems-1; else list[0] items, list[1..]: their indices
@@ -573,8 +597,11 @@ __device__ inline int item_total(const TcArgs& a) { return a.list ? a.list[0] : 
 __device__ inline int item_index(const TcArgs& a, int jj) { return a.list ? a.list[1 + jj] : jj; }
 
 // The items of a packed launch whose instance takes part in this pass (live[wi] > pass), in item order:
-// list[0] = their count, list[1..] = their indices.  One block; instances in chunks of its threads.
+// list[0] = their count, list[1..] = their indices; with blocks (rlist), the same for the reduction's
+// blocks (rlist[1..]: codes (member << 10) | block).  One block; instances in chunks of its threads.
 constexpr int ALIST_THREADS = 1024;
+__device__ inline int reduce_blocks(const TcInst& I) { return (int)(((long)I.rows * I.cols + 255) / 256); }
+template <bool BLOCKS>
 __global__ void __launch_bounds__(ALIST_THREADS) active_items_kernel(const TcInst* __restrict__ inst,
                                                                      const int* __restrict__ item0, int ninst,
                                                                      const int* __restrict__ live, int pass, int* list)
@@ -586,7 +613,8 @@ __global__ void __launch_bounds__(ALIST_THREADS) active_items_kernel(const TcIns
     __syncthreads();
     for (int k0 = 0; k0 < ninst; k0 += ALIST_THREADS) {
         const int k = k0 + t;
-        const int c = (k < ninst && live[inst[k].wi] > pass) ? item0[k + 1] - item0[k] : 0;
+        const bool on = k < ninst && live[inst[k].wi] > pass;
+        const int c = !on ? 0 : BLOCKS ? reduce_blocks(inst[k]) : item0[k + 1] - item0[k];
         int incl = c;  // inclusive scan within the warp, then over the warps
         for (int o = 1; o < 32; o <<= 1) {
             const int v = __shfl_up_sync(0xffffffffu, incl, o);
@@ -604,7 +632,7 @@ __global__ void __launch_bounds__(ALIST_THREADS) active_items_kernel(const TcIns
         }
         __syncthreads();
         const int excl = base + (w > 0 ? wsum[w - 1] : 0) + incl - c;
-        for (int q = 0; q < c; ++q) list[1 + excl + q] = item0[k] + q;
+        for (int q = 0; q < c; ++q) list[1 + excl + q] = BLOCKS ? ((k << 10) | q) : item0[k] + q;
         const int total = base + wsum[ALIST_THREADS / 32 - 1];
         __syncthreads();  // every thread has read base and wsum
         if (t == 0) base = total;
@@ -1129,18 +1157,11 @@ __global__ void slot_reduce_f32_kernel(TcArgs a, double* out, long ldo, const De
     out[row + (long)col * ldo] = (er == EXP_NONE || ec == EXP_NONE) ? 0.0 : f32_scaled_to_f64(s, er + ec);
 }
 
-// A packed batch: every instance's output (rows x cols, column-major, ldo) is
-// the sum over the pieces of each tile of its slots, in piece order; F32: FP32
-// slots scaled by 2^(emax_row + emax_col) (TC2), else FP64 slots (EMU64).
-// Block j reduces elements [256 b, 256 b + 256) of instance k, where
-// rblk[j] = (k << 10) | b.
+// One reduction block: the 256 elements [256 b, 256 b + 256) of member k's output, code = (k << 10) | b.
 template <int N, bool F32>
-__global__ void slot_reduce_batch_kernel(TcArgs a)
+__device__ inline void slot_reduce_block(const TcArgs& a, int code)
 {
-    if (*(volatile const int*)&a.st->code != 0) return;
-    const int code = a.rblk[blockIdx.x];
     const TcInst I = a.inst[code >> 10];
-    if (a.live && a.live[I.wi] <= a.pass) return;
     const long el = (long)(code & 1023) * 256 + threadIdx.x;
     if (el >= (long)I.rows * I.cols) return;
     const int col = (int)(el / I.rows), row = (int)(el % I.rows);
@@ -1166,6 +1187,19 @@ __global__ void slot_reduce_batch_kernel(TcArgs a)
         r = s;
     }
     I.out[row + (long)col * I.ldo] = r;
+}
+
+// A packed batch: every instance's output (rows x cols, column-major, ldo) is
+// the sum over the pieces of each tile of its slots, in piece order; F32: FP32
+// slots scaled by 2^(emax_row + emax_col) (TC2), else FP64 slots (EMU64).
+// The blocks are the launch's rblk codes, or (rlist) those of the instances
+// taking part in the pass; grid-stride over them.
+template <int N, bool F32>
+__global__ void slot_reduce_batch_kernel(TcArgs a, const int* rlist)
+{
+    if (*(volatile const int*)&a.st->code != 0) return;
+    const int nb = rlist ? rlist[0] : a.nrblk;
+    for (int q = blockIdx.x; q < nb; q += gridDim.x) slot_reduce_block<N, F32>(a, rlist ? rlist[1 + q] : a.rblk[q]);
 }
 
 // G = C + C^T (+ shift I), exactly symmetric.
@@ -1959,7 +1993,9 @@ struct WaveLayout {
     int *eA, *mA, *eZ, *mZ, *eU, *mU;
     double* slots;
     double* asq;  // the A split's per-tile shares of ||A||_F^2
+    double* zsq;  // pass 0's Z split: per chunk and column, the sum of squares
     int* alist;   // a launch's active items (max_items + 1)
+    int* rlist;   // a launch's active reduction blocks (max_rblk + 1)
     size_t bytes;
 };
 WaveLayout wave_layout(const TcBatchWave& w, void* ws)
@@ -1984,7 +2020,9 @@ WaveLayout wave_layout(const TcBatchWave& w, void* ws)
     L.mU = reinterpret_cast<int*>(take((size_t)w.cols * 4));
     L.slots = reinterpret_cast<double*>(take((size_t)w.max_items * TM * EMU_N * 8));
     L.asq = reinterpret_cast<double*>(take((size_t)w.tilesA * 8));
+    L.zsq = reinterpret_cast<double*>(take((size_t)w.kch * w.cols * 8));
     L.alist = reinterpret_cast<int*>(take((size_t)(w.max_items + 1) * 4));
+    L.rlist = reinterpret_cast<int*>(take((size_t)(w.max_rblk + 1) * 4));
     L.bytes = o;
     return L;
 }
@@ -2053,6 +2091,7 @@ TcBatchPlan tc_batch_plan(const std::vector<TcBatchShape>& sh, size_t budget)
         w.tileTab = tk((size_t)w.tilesA * 4);
         w.colTab = tk((size_t)w.cols * 4);
         w.max_items = 1;
+        w.max_rblk = 1;
         w.maxpass = 1;
         for (int i = b; i < e; ++i)
             if (sh[i].npass > w.maxpass) w.maxpass = sh[i].npass;
@@ -2090,6 +2129,7 @@ TcBatchPlan tc_batch_plan(const std::vector<TcBatchShape>& sh, size_t budget)
                     L.item0 = tk((size_t)(L.ninst + 1) * 4);
                     L.cum = tk((size_t)ncum * 4);
                     L.rblk = tk((size_t)L.nrblk * 4);
+                    if (L.nrblk > w.max_rblk) w.max_rblk = L.nrblk;
                     if (L.nitems > w.max_items) w.max_items = L.nitems;
                 }
             }
@@ -2197,14 +2237,16 @@ cudaError_t tc_batch_split_a(const TcBatchPlan& p, int w, const void* table_dev,
     return cudaGetLastError();
 }
 
-cudaError_t tc_batch_anorm2(const TcBatchPlan& p, int w, const void* table_dev, void* scratch, double* out,
-                            cudaStream_t s)
+cudaError_t tc_batch_norms(const TcBatchPlan& p, int w, const void* table_dev, void* scratch, double* anorm2,
+                           double* znorm2, cudaStream_t s)
 {
     const TcBatchWave& W = p.waves[w];
     const WaveLayout L = wave_layout(W, scratch);
     const char* tab = static_cast<const char*>(table_dev);
     if (W.count > 0)
-        anorm_batch_kernel<<<W.count, 128, 0, s>>>(reinterpret_cast<const SplitInst*>(tab + W.splitA), L.asq, out);
+        norms_batch_kernel<<<W.count, 128, 0, s>>>(reinterpret_cast<const SplitInst*>(tab + W.splitA),
+                                                   reinterpret_cast<const SplitInst*>(tab + W.splitZ), L.asq, L.zsq,
+                                                   W.cols, anorm2, znorm2);
     return cudaGetLastError();
 }
 
@@ -2237,6 +2279,7 @@ cudaError_t tc_batch_gram(const TcBatchPlan& p, int w, int pass, const void* tab
         a.inst = reinterpret_cast<const TcInst*>(tab + B.inst);
         a.inst_item0 = reinterpret_cast<const int*>(tab + B.item0);
         a.rblk = reinterpret_cast<const int*>(tab + B.rblk);
+        a.nrblk = B.nrblk;
         a.live = live;
         a.pass = pass;
         a.list = live ? L.alist : nullptr;
@@ -2244,14 +2287,17 @@ cudaError_t tc_batch_gram(const TcBatchPlan& p, int w, int pass, const void* tab
     };
     auto product = [&](const TcBatchLaunch& B, const TcArgs& a, const void* PA, size_t plA, const void* PB) {
         cudaError_t e;
-        if (live)
-            active_items_kernel<<<1, ALIST_THREADS, 0, s>>>(a.inst, a.inst_item0, a.ninst, live, pass, L.alist);
+        if (live) {  // the items and reduction blocks of the instances taking part in this pass
+            active_items_kernel<false><<<1, ALIST_THREADS, 0, s>>>(a.inst, a.inst_item0, a.ninst, live, pass, L.alist);
+            active_items_kernel<true><<<1, ALIST_THREADS, 0, s>>>(a.inst, a.inst_item0, a.ninst, live, pass, L.rlist);
+        }
         if (B.mode == 1) e = launch_emu(a, PA, W.ldp, plA, PB, W.ldp, planeZ, sms, s);
         else e = launch_tc<64, 64, 2, 3>(a, PA, W.ldp, plA, PB, W.ldp, planeZ, sms, s);
         if (e != cudaSuccess) return e;
-        const unsigned g = (unsigned)B.nrblk;
-        if (B.mode == 1) slot_reduce_batch_kernel<EMU_N, false><<<g, 256, 0, s>>>(a);
-        else slot_reduce_batch_kernel<EMU_N, true><<<g, 256, 0, s>>>(a);
+        const unsigned g = (unsigned)(B.nrblk < 16 * sms ? B.nrblk : 16 * sms);
+        const int* rl = live ? L.rlist : nullptr;
+        if (B.mode == 1) slot_reduce_batch_kernel<EMU_N, false><<<g, 256, 0, s>>>(a, rl);
+        else slot_reduce_batch_kernel<EMU_N, true><<<g, 256, 0, s>>>(a, rl);
         return cudaGetLastError();
     };
     cudaError_t e;
@@ -2259,7 +2305,8 @@ cudaError_t tc_batch_gram(const TcBatchPlan& p, int w, int pass, const void* tab
     fill_int_kernel<<<(unsigned)((W.cols + 255) / 256), 256, 0, s>>>(L.mZ, W.cols, EXP_NONE);
     const int* colinst = reinterpret_cast<const int*>(tab + W.colTab);
     split_tall_batch_kernel<<<gt, 256, 0, s>>>(reinterpret_cast<const SplitInst*>(tab + (pass ? W.splitQ : W.splitZ)),
-                                               colinst, EMU_S, L.Zp, W.ldp, planeZ, L.eZ, L.mZ, W.cols, live, pass);
+                                               colinst, EMU_S, L.Zp, W.ldp, planeZ, L.eZ, L.mZ, W.cols, live, pass,
+                                               pass == 0 ? L.zsq : nullptr);
     for (int li = 0; li < W.nl[pass]; ++li) {
         const TcBatchLaunch& B = W.u[pass][li];
         if ((e = product(B, args(B, W.rows, L.eA, L.eZ, L.mA, L.mZ), L.Ap, planeA, L.Zp)) != cudaSuccess) return e;
@@ -2267,7 +2314,7 @@ cudaError_t tc_batch_gram(const TcBatchPlan& p, int w, int pass, const void* tab
     // the split of U, then C = X^T U
     fill_int_kernel<<<(unsigned)((W.cols + 255) / 256), 256, 0, s>>>(L.mU, W.cols, EXP_NONE);
     split_tall_batch_kernel<<<gt, 256, 0, s>>>(reinterpret_cast<const SplitInst*>(tab + W.splitU), colinst, EMU_S,
-                                               L.Up, W.ldp, planeZ, L.eU, L.mU, W.cols, live, pass);
+                                               L.Up, W.ldp, planeZ, L.eU, L.mU, W.cols, live, pass, nullptr);
     for (int li = 0; li < W.nl[pass]; ++li) {
         const TcBatchLaunch& B = W.c[pass][li];
         if ((e = product(B, args(B, W.cols, L.eZ, L.eU, L.mZ, L.mU), L.Zp, planeZ, L.Up)) != cudaSuccess) return e;

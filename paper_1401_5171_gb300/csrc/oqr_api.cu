@@ -969,7 +969,7 @@ oqr_status selector_run(oqr_ctx* ctx, const SelInputs& I, const float* params, d
         char* tab;
         BatchDesc* d;
         int *sts, *route, *opt, *gpass, *mask, *choice;
-        double *anorm2, *shifts, *orth, *defect, *pool, *upool, *wtab;
+        double *anorm2, *znorm2, *shifts, *orth, *defect, *pool, *upool, *wtab;
         float* feat;
         void* scratch;
     } D{};
@@ -984,6 +984,7 @@ oqr_status selector_run(oqr_ctx* ctx, const SelInputs& I, const float* params, d
         x.mask = c.take<int>((size_t)count);
         x.choice = c.take<int>((size_t)count);
         x.anorm2 = c.take<double>((size_t)count);
+        x.znorm2 = c.take<double>((size_t)count);
         x.shifts = c.take<double>((size_t)count);
         x.orth = c.take<double>((size_t)count);
         x.defect = c.take<double>((size_t)count);
@@ -1036,21 +1037,21 @@ oqr_status selector_run(oqr_ctx* ctx, const SelInputs& I, const float* params, d
         const int f = W.first, cnt = W.count;
         BatchDesc* dw = D.d + f;
         int* sw = D.sts + f;
-        const SelWave sel{dw,           sw,         D.route + f,  D.opt + f, D.gpass + f, D.mask + f, D.anorm2 + f,
-                          D.shifts + f, D.orth + f, D.defect + f, cnt,       extra,       tol};
+        const SelWave sel{dw,           sw,           D.route + f, D.opt + f, D.gpass + f, D.mask + f, D.anorm2 + f,
+                          D.znorm2 + f, D.shifts + f, D.orth + f,  D.defect + f, cnt,     extra,       tol};
         const int* live = D.gpass + f;
         // the probe: the split of A (read by every pass of the wave), G0, its Cholesky factor, the
         // features, the network, the routes
         OQR_TRY(tc_batch_split_a(plan, w, D.tab, D.scratch, s));
-        OQR_TRY(tc_batch_anorm2(plan, w, D.tab, D.scratch, sel.anorm2, s));
         OQR_TRY(tc_batch_gram(plan, w, 0, D.tab, D.scratch, ctx->st, limit, ctx->sm_count, s));
+        OQR_TRY(tc_batch_norms(plan, w, D.tab, D.scratch, sel.anorm2, sel.znorm2, s));
         OQR_TRY(launch_batched_gram_chol(dw, cnt, sw, s));
         OQR_TRY(launch_features_batched(dw, cnt, sw, D.wtab, D.feat + (size_t)f * MLP_IN, s));
         OQR_TRY(launch_mlp_forward(cnt, D.feat + (size_t)f * MLP_IN, params, 1, nullptr, D.choice + f, s));
         OQR_TRY(launch_sel_route(sel, D.choice + f, s));
         // the first factor: R1 = chol(G0 + s I) on the shifted route (elsewhere the probe's R1 stands),
         // then Q1 = Z R1^{-1}
-        OQR_TRY(launch_batched_shifts(dw, cnt, sel.mask, sel.anorm2, 11.0, U64, sel.shifts, s));
+        OQR_TRY(launch_batched_shifts(dw, cnt, sel.mask, sel.anorm2, sel.znorm2, 11.0, U64, sel.shifts, s));
         OQR_TRY(launch_sel_shift_g(sel, s));
         OQR_TRY(launch_batched_chol_solve(dw, cnt, sw, sel.mask, nullptr, s));
         OQR_TRY(launch_sel_after_factor(sel, 0, s));
@@ -1061,7 +1062,7 @@ oqr_status selector_run(oqr_ctx* ctx, const SelInputs& I, const float* params, d
             OQR_TRY(launch_batched_factor(dw, cnt, sw, pass, nullptr, s));
             if (pass == 1) {  // the late refactor: R1 = chol(G0 + s I), Q1 = Z R1^{-1}
                 OQR_TRY(launch_sel_late_mask(sel, s));
-                OQR_TRY(launch_batched_shifts(dw, cnt, sel.mask, sel.anorm2, 11.0, U64, sel.shifts, s));
+                OQR_TRY(launch_batched_shifts(dw, cnt, sel.mask, sel.anorm2, sel.znorm2, 11.0, U64, sel.shifts, s));
                 OQR_TRY(launch_sel_late_prep(sel, s));
                 OQR_TRY(launch_batched_chol_solve(dw, cnt, sw, sel.mask, sel.mask, s));
             }
@@ -1516,7 +1517,7 @@ oqr_status oqr_batched_mixed(oqr_ctx* ctx, int count, const int* m, const int* n
         *sts = c.take<int>((size_t)count);
         *dperm = c.take<int>((size_t)count);
         *dshifted = c.take<int>((size_t)count);
-        *anorm2 = c.take<double>((size_t)count);
+        *anorm2 = c.take<double>((size_t)2 * count);  // ||A_b||_F^2, then ||Z_b||_F^2
         *shifts = c.take<double>((size_t)count);
         *pool = c.take<double>(pool_doubles);
         *upool = c.take<double>((size_t)plan.upool_doubles);
@@ -1581,12 +1582,15 @@ oqr_status oqr_batched_mixed(oqr_ctx* ctx, int count, const int* m, const int* n
             bool any_shift = false;
             for (int i = W.first; i < W.first + W.count; ++i) any_shift = any_shift || shifted[i];
             if ((e = tc_batch_split_a(plan, w, tab, scratch, s)) != cudaSuccess) return e;
-            if (any_shift && ((e = tc_batch_anorm2(plan, w, tab, scratch, anorm2 + W.first, s)) != cudaSuccess ||
-                              (e = launch_batched_shifts(dw, W.count, dshifted + W.first, anorm2 + W.first, 11.0, U64,
-                                                         shifts + W.first, s)) != cudaSuccess))
-                return e;
             for (int pass = 0; pass < W.maxpass; ++pass) {
                 if ((e = tc_batch_gram(plan, w, pass, tab, scratch, ctx->st, limit, ctx->sm_count, s)) != cudaSuccess)
+                    return e;
+                if (pass == 0 && any_shift &&
+                    ((e = tc_batch_norms(plan, w, tab, scratch, anorm2 + W.first, anorm2 + count + W.first, s)) !=
+                         cudaSuccess ||
+                     (e = launch_batched_shifts(dw, W.count, dshifted + W.first, anorm2 + W.first,
+                                                anorm2 + count + W.first, 11.0, U64, shifts + W.first, s)) !=
+                         cudaSuccess))
                     return e;
                 if ((e = launch_batched_factor(dw, W.count, sw, pass, any_shift ? shifts + W.first : nullptr, s)) !=
                     cudaSuccess)

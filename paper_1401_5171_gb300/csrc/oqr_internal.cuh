@@ -287,7 +287,7 @@ cudaError_t launch_batched_cholqr2(const BatchDesc* d, int count, const int* con
 //           pass > 0 R1 <- R2 R1;
 //   rfinal: the caller's R_b = R1;
 //   shifts: shifts[b] = c u (m n + n (n + 1)) ||A_b||_F ||Z_b||_F^2 where
-//           mask[b], else 0, with ||A_b||_F^2 = anorm2[b] (from the split of A);
+//           mask[b], else 0, with ||A_b||_F^2 = anorm2[b], ||Z_b||_F^2 = znorm2[b] (from the splits);
 //   scatter: status[perm[i]] = st_sorted[i], or -1 for every instance when a
 //           tensor-core wait of the context timed out.
 cudaError_t launch_batched_factor(const BatchDesc* d, int count, int* status, int pass, const double* shifts,
@@ -297,8 +297,8 @@ cudaError_t launch_batched_rfinal(const BatchDesc* d, int count, int* status, cu
 // (a first pass from a new G; NULL masks: every instance).
 cudaError_t launch_batched_chol_solve(const BatchDesc* d, int count, int* status, const int* chol_mask,
                                       const int* solve_mask, cudaStream_t s);
-cudaError_t launch_batched_shifts(const BatchDesc* d, int count, const int* mask, const double* anorm2, double c,
-                                  double u, double* shifts, cudaStream_t s);
+cudaError_t launch_batched_shifts(const BatchDesc* d, int count, const int* mask, const double* anorm2,
+                                  const double* znorm2, double c, double u, double* shifts, cudaStream_t s);
 cudaError_t launch_batch_status_scatter(const int* st_sorted, const int* perm, int count, const DevStatus* st,
                                         int* status, cudaStream_t s);
 // The check of the instances whose factor passes end at pass (npass == pass):
@@ -342,7 +342,8 @@ struct SelWave {
     int* opt;       // the option used
     int* gpass;
     int* mask;      // scratch: shifted first pass or late refactor
-    double* anorm2; // ||A_b||_F^2 (from the split of A)
+    double* anorm2; // ||A_b||_F^2 (from the splits)
+    double* znorm2; // ||Z_b||_F^2
     double* shifts;
     double* orth;   // ||E||_F of the checked Gram, NaN where not checked
     double* defect; // ||E||_F of the Gram that the last factor pass factored
@@ -395,7 +396,7 @@ struct TcBatchLaunch {
 struct TcBatchWave {
     int first, count;     // instances [first, first + count) of the sorted order
     long rows, cols, ldp;  // packed rows (sum of m), packed columns (sum of n), plane row pitch
-    int K, kch, tilesA, max_items;
+    int K, kch, tilesA, max_items, max_rblk;
     size_t splitA, splitZ, splitQ, splitU;  // SplitInst tables (byte offsets)
     size_t tileTab, colTab;                 // the A split's tiles, the packed columns' instances
     TcBatchLaunch u[TC_BATCH_MAX_PASS][2], c[TC_BATCH_MAX_PASS][2];  // [pass][launch]: pass 0 one per mode present
@@ -415,11 +416,12 @@ void tc_batch_tables(const TcBatchPlan& p, const std::vector<TcBatchShape>& sh, 
                      const void* table_dev, double* upool, std::vector<char>& image);
 // Wave w: the split of A (once), then the Gram of pass p into the C of each
 // instance with npass > p (X = Z in pass 0, Q later).
-// The split also leaves each tile's share of ||A||_F^2 in the scratch; tc_batch_anorm2 sums them per
-// instance (fixed order): out[i] = ||A_i||_F^2 for the wave's instance i.
+// The split of A leaves each tile's share of ||A||_F^2 in the scratch, and pass 0's split of Z each
+// chunk's and column's sum of squares; tc_batch_norms (after pass 0's Gram) sums them per instance in a
+// fixed order: anorm2[i] = ||A_i||_F^2, znorm2[i] = ||Z_i||_F^2 for the wave's instance i.
 cudaError_t tc_batch_split_a(const TcBatchPlan& p, int w, const void* table_dev, void* scratch, cudaStream_t s);
-cudaError_t tc_batch_anorm2(const TcBatchPlan& p, int w, const void* table_dev, void* scratch, double* out,
-                            cudaStream_t s);
+cudaError_t tc_batch_norms(const TcBatchPlan& p, int w, const void* table_dev, void* scratch, double* anorm2,
+                           double* znorm2, cudaStream_t s);
 // live (the wave's per-instance Gram pass counts on the device, or NULL): instances with live[i] <= pass
 // sit the pass out, their tiles skipped, so that one set of tables serves passes chosen on the device.
 cudaError_t tc_batch_gram(const TcBatchPlan& p, int w, int pass, const void* table_dev, void* scratch,
