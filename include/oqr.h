@@ -272,18 +272,25 @@ oqr_status oqr_repres(oqr_ctx* ctx, int m, int n, const double* Z, long ldz, con
 
 /*
  * PRE-CHOLQR (Algorithm 2, Sec. 3): [Y, S] = qr(Z) (Euclidean), then
- * [Q, U] = CHOLQR(A, Y), R = U S.  The Euclidean QR is Householder QR on a
- * reduction tree (oqr_tsqr, FP64), so Y is orthonormal to working precision
- * and the loss of orthogonality of Q no longer depends on kappa(Z)
- * (Thm 3.1: ||Q^T A Q - I||_2 <= c m n^2 u ||Q||_2^2 ||A||_2).  The CHOLQR
- * pass runs in opts->final_prec (OQR_FP64 or OQR_FP64_TC; opts->check as for
+ * [Q, U] = CHOLQR(A, Y), R = U S.  The Euclidean QR is Householder QR
+ * (oqr_tsqr, FP64), so Y is orthonormal to working precision and the loss of
+ * orthogonality of Q no longer depends on kappa(Z) (Thm 3.1:
+ * ||Q^T A Q - I||_2 <= c m n^2 u ||Q||_2^2 ||A||_2).  The CHOLQR pass runs in
+ * opts->final_prec (OQR_FP64 or OQR_FP64_TC; opts->check as for
  * oqr_cholqr2); R has a positive diagonal.  Q may alias Z.  Workspace: the
- * tree's blocks (about 2 m n + 4 n^2 log2(m / 256) doubles) and the pass's.
+ * Householder QR's (about 3 m n doubles for n > 32) and the pass's.
  * oqr_precholqr_tridiag: the same for a tridiagonal A (d, e as for
  *   oqr_cholqr2_tridiag).
  * oqr_tsqr: the Euclidean step alone, Z = Y S with Y (m x n, device) having
  *   orthonormal columns and S (n x n, device) upper triangular with a
- *   positive diagonal (zeros below).  Y must not overlap Z.
+ *   positive diagonal (zeros below).  Y must not overlap Z.  For n <= 32 it is
+ *   Householder QR on a reduction tree (TSQR: leaves of max(n, 256) rows,
+ *   stacked pairs of R factors, Y formed top-down).  Above, it is blocked
+ *   Householder QR: panels of 32 columns factored by that TSQR, their
+ *   Householder vectors V and factor T recovered from the explicit panel Q by
+ *   an LU factorization with sign choice (Ballard et al., 2015), the trailing
+ *   columns updated as C - V T^T V^T C and Y formed by applying the
+ *   reflectors to [I; 0], both by FP64 GEMMs.
  */
 oqr_status oqr_precholqr(oqr_ctx* ctx, int m, int n, const double* A, long lda, const double* Z, long ldz, double* Q,
                          long ldq, double* R, long ldr, const oqr_opts* opts, oqr_info* info, void* stream);

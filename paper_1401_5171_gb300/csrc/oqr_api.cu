@@ -534,6 +534,19 @@ oqr_status cholqr2_reuse_w(oqr_ctx* ctx, int m, int n, const double* A, long lda
 
 // PRE-CHOLQR (Algorithm 2, Sec. 3): [Y, S] = qr(Z) by Householder TSQR,
 // [Q, U] = CHOLQR(A, Y) (one pass in opts->final_prec), R = U S.
+// The Euclidean Householder QR Z = Y S (Y orthonormal, S with a positive diagonal): the TSQR for one
+// panel's width or less, the blocked form (TSQR panels, trailing updates by FP64 GEMMs) above it.
+size_t euclid_qr_bytes(int m, int n, int sms)
+{
+    return align256((n <= BH_B ? tsqr_plan(m, n).doubles : bhqr_plan(m, n, sms).doubles) * sizeof(double));
+}
+cudaError_t launch_euclid_qr(int m, int n, const double* Z, long ldz, double* Y, long ldy, double* S, long lds,
+                             double* ws, int sms, cudaStream_t s)
+{
+    if (n <= BH_B) return launch_tsqr(tsqr_plan(m, n), Z, ldz, Y, ldy, S, lds, ws, s);
+    return launch_bhqr(bhqr_plan(m, n, sms), Z, ldz, Y, ldy, S, lds, ws, s);
+}
+
 oqr_status precholqr_impl(oqr_ctx* ctx, int m, int n, const AOp& op, const double* Z, long ldz, double* Q, long ldq,
                           double* R, long ldr, const oqr_opts* opts, oqr_info* info, cudaStream_t s)
 {
@@ -553,15 +566,14 @@ oqr_status precholqr_impl(oqr_ctx* ctx, int m, int n, const AOp& op, const doubl
     const GramPlan gp = gram_plan(m, n, ctx->sm_count);
     NeBuffers B;
     const size_t reserve = align256((size_t)2 * n * n * sizeof(double));  // S, U
-    const TsqrPlan tp = tsqr_plan(m, n);
-    const size_t need = reserve + std::max(align256(tp.doubles * sizeof(double)), ne_carve(nullptr, gp, P, &B));
+    const size_t need = reserve + std::max(euclid_qr_bytes(m, n, ctx->sm_count), ne_carve(nullptr, gp, P, &B));
     if ((v = ensure_ws(ctx, need)) != OQR_OK) return v;
     double* S = static_cast<double*>(ctx->ws);
     double* Uf = S + (size_t)n * n;
     double* tws = reinterpret_cast<double*>(static_cast<char*>(ctx->ws) + reserve);
     {
-        const NvtxRange range("oqr: Householder TSQR %d", n);
-        OQR_TRY(launch_tsqr(tp, Z, ldz, Q, ldq, S, n, tws, s));  // Y into Q
+        const NvtxRange range("oqr: Householder QR %d", n);
+        OQR_TRY(launch_euclid_qr(m, n, Z, ldz, Q, ldq, S, n, tws, ctx->sm_count, s));  // Y into Q
     }
     // CHOLQR on Y in place (Q aliases Y), its factor into U; no synchronization yet
     if ((v = normal_equation(ctx, m, n, op, Q, ldq, Q, ldq, Uf, n, &o, nullptr, s, 1, false, reserve)) != OQR_OK)
@@ -1914,10 +1926,10 @@ oqr_status oqr_tsqr(oqr_ctx* ctx, int m, int n, const double* Z, long ldz, doubl
         bad_matrix(S, lds, n, n))
         return OQR_ERR_INVALID_ARG;
     if (n > 1024) return OQR_ERR_UNSUPPORTED;
-    const TsqrPlan tp = tsqr_plan(m, n);
-    oqr_status v = ensure_ws(ctx, align256(tp.doubles * sizeof(double)));
+    oqr_status v = ensure_ws(ctx, euclid_qr_bytes(m, n, ctx->sm_count));
     if (v != OQR_OK) return v;
-    OQR_TRY(launch_tsqr(tp, Z, ldz, Y, ldy, S, lds, static_cast<double*>(ctx->ws), static_cast<cudaStream_t>(stream)));
+    OQR_TRY(launch_euclid_qr(m, n, Z, ldz, Y, ldy, S, lds, static_cast<double*>(ctx->ws), ctx->sm_count,
+                             static_cast<cudaStream_t>(stream)));
     return OQR_OK;
 }
 

@@ -242,6 +242,20 @@ TsqrPlan tsqr_plan(int m, int n);
 cudaError_t launch_tsqr(const TsqrPlan& p, const double* Z, long ldz, double* Y, long ldy, double* S, long lds,
                         double* ws, cudaStream_t s);
 
+// Blocked Householder QR of a tall-skinny Z (k_bhqr.cu), the same contract as launch_tsqr: Z = Y S, Y
+// orthonormal, S upper triangular with a positive diagonal.  Panels of BH_B columns are factored by the
+// TSQR, their Householder vectors recovered from its explicit Q, the trailing columns and Y updated by
+// FP64 GEMMs; the workspace holds bhqr_plan(m, n, sms).doubles doubles.
+constexpr int BH_B = 32;
+struct BhqrPlan {
+    int m, n, panels, sms, splits_max;
+    size_t oX, oV, oQp, oRp, oU, oT, oD, oW, oW2, oSK, oTS;  // workspace offsets (doubles)
+    size_t doubles;
+};
+BhqrPlan bhqr_plan(int m, int n, int sms);
+cudaError_t launch_bhqr(const BhqrPlan& p, const double* Z, long ldz, double* Y, long ldy, double* S, long lds,
+                        double* ws, cudaStream_t s);
+
 // Tridiagonal A (k_tridiag.cu): d (m), e (m - 1); U = M X with M = tril(T, -1) + diag(T) / 2.
 cudaError_t launch_tridiag_u(int m, int n, const double* d, const double* e, const double* X, long ldx, double* U,
                              long ldu, cudaStream_t s);

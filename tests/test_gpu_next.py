@@ -246,6 +246,25 @@ def test_tsqr_matches_lapack(env, m, n):
     assert np.linalg.norm(Z - Y @ S) / np.linalg.norm(Z) <= 10 * n * U
 
 
+@pytest.mark.parametrize("m,n", [(3000, 100), (1500, 64)])
+def test_blocked_householder_ill_conditioned(env, m, n):
+    """The blocked Householder QR (n > 32: TSQR panels, reconstructed Householder vectors, GEMM updates) at
+    kappa(Z) = 1e12: Y orthonormal and Z = Y S to working precision, as Householder QR is backward stable
+    whatever kappa(Z); at kappa(Z) = 1e3 (the same sizes) S is LAPACK's R within 1e-13."""
+    torch, oqr, ctx = env
+    _, Z = inputs.paper_case(4, m, n, 1.0, 1e12, seed=m + n)
+    Y, S = ctx.oqr_tsqr(dev(torch, Z, oqr))
+    Y, S = host(Y), host(S)
+    assert np.all(np.tril(S, -1) == 0) and np.all(np.diag(S) > 0)
+    assert np.linalg.norm(Y.T @ Y - np.eye(n), 2) <= 20 * np.sqrt(m) * n * U
+    assert np.linalg.norm(Z - Y @ S, 2) / np.linalg.norm(Z, 2) <= 10 * n * U
+    _, Z = inputs.paper_case(4, m, n, 1.0, 1e3, seed=m + n)
+    _, S = ctx.oqr_tsqr(dev(torch, Z, oqr))
+    _, Rl = np.linalg.qr(Z)
+    Rl = (Rl.T * np.where(np.diag(Rl) < 0, -1.0, 1.0)).T
+    assert np.linalg.norm(host(S) - Rl) / np.linalg.norm(Rl) <= 1e-13
+
+
 def _pre_orth_bound(A, Q, m, n):
     """Thm 3.1's bound c m n^2 u ||Q||_2^2 ||A||_2 with c = 1."""
     return m * n * n * U * np.linalg.norm(Q, 2) ** 2 * np.linalg.eigvalsh(A).max()
@@ -268,13 +287,14 @@ def test_precholqr_config0_parity(env, final_prec):
     assert oracle.repres_error(Z, Q, R) <= 1e-13
 
 
-def test_precholqr_orthogonality_independent_of_kappa_z(env):
+@pytest.mark.parametrize("n", [20, 80])
+def test_precholqr_orthogonality_independent_of_kappa_z(env, n):
     """Thm 3.1: PRE-CHOLQR's loss of orthogonality does not grow with kappa(Z).  The same A (m = 2000,
     kappa(A) = 1e4), kappa(Z) = 1e2 and 1e8: the orthogonality stays within 10x, inside the theorem's
     bound, while one-pass CHOLQR at kappa(Z) = 1e8 breaks down or loses at least 1000x more; R is the
-    oracle's within 100 u kappa(R)."""
+    oracle's within 100 u kappa(R).  n = 20: the TSQR; n = 80: the blocked Householder QR."""
     torch, oqr, ctx = env
-    m, n = 2000, 20
+    m = 2000
     orths = []
     for kz in (1e2, 1e8):
         A, Z = inputs.paper_case(4, m, n, 1e4, kz, seed=8)
