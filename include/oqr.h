@@ -286,11 +286,13 @@ oqr_status oqr_repres(oqr_ctx* ctx, int m, int n, const double* Z, long ldz, con
  *   positive diagonal (zeros below).  Y must not overlap Z.  For n <= 32 it is
  *   Householder QR on a reduction tree (TSQR: leaves of max(n, 256) rows,
  *   stacked pairs of R factors, Y formed top-down).  Above, it is blocked
- *   Householder QR: panels of 32 columns factored by that TSQR, their
- *   Householder vectors V and factor T recovered from the explicit panel Q by
- *   an LU factorization with sign choice (Ballard et al., 2015), the trailing
+ *   Householder QR: panels of 32 columns, each factored column by column
+ *   (LAPACK's reflectors) in one cooperative launch over all SMs with
+ *   time-limited grid-wide waits, blocked as I - V T V^T, the trailing
  *   columns updated as C - V T^T V^T C and Y formed by applying the
- *   reflectors to [I; 0], both by FP64 GEMMs.
+ *   reflectors to [I; 0], both by FP64 GEMMs.  oqr_tsqr synchronizes the
+ *   stream and returns the context status (OQR_ERR_TIMEOUT if a grid-wide
+ *   wait of the panel factorization ran out).
  */
 oqr_status oqr_precholqr(oqr_ctx* ctx, int m, int n, const double* A, long lda, const double* Z, long ldz, double* Q,
                          long ldq, double* R, long ldr, const oqr_opts* opts, oqr_info* info, void* stream);

@@ -3,115 +3,349 @@
 // triangular with a positive diagonal.
 //
 // Panels of BH_B columns.  Panel p (columns k..k+w-1 of the working copy X,
-// rows k..m-1) is factored by the Householder TSQR (k_tsqr.cu) into an
-// explicit Qp (orthonormal, m-k x w) and Rp.  Its Householder vectors V and
-// triangular factor T, with (I - V T V^T)[I; 0] = Qp D, are recovered from Qp
-// by an LU factorization without pivoting of Qp - [D; 0] (Ballard, Demmel,
-// Grigori, Jacquelin, Nguyen and Solomonik, "Reconstructing Householder
-// vectors from tall-skinny QR", 2015): V = L, T = -U D L1^{-T}, the signs D
-// chosen as the elimination goes (d_j = -sign of the current pivot, so every
-// pivot has magnitude at least 1).  The panel's Householder R is D Rp; the
-// trailing columns C = X(k:m, k+w:n) become (I - V T V^T)^T C =
-// C - V (T^T (V^T C)), and their top w rows are R's next rows.  Y is formed
-// from the right: [I_n; 0], then (I - V T V^T) applied to it for the panels
-// in reverse order.  Y D and D R_h give S's positive diagonal.
+// rows k..m-1) is factored column by column by Householder reflections
+// H_j = I - tau_j v_j v_j^T (LAPACK's construction: beta = -sign(x0) ||x||,
+// v = x / (x0 - beta) below its leading 1, tau = (beta - x0) / beta), every
+// step spread over all SMs: one kernel forms the reflector from the column's
+// norm and the partial dot products with the panel's later columns, the next
+// applies it and sums the next column's norm; the block partials are reduced
+// in a fixed order.  The panel's reflectors are then blocked as
+// I - V T V^T with T upper triangular (T_jj = tau_j, T(0:j, j) =
+// -tau_j T(0:j, 0:j) V(:, 0:j)^T v_j), and the trailing columns
+// C = X(k:m, k+w:n) become C - V (T^T (V^T C)) by FP64 GEMMs.  Y is formed
+// from the right: [I_n; 0], then I - V T V^T applied for the panels in
+// reverse order.  With D = sign(diag(R)), Y D and D R give S's positive
+// diagonal.
 #include "oqr_internal.cuh"
 
 namespace oqr {
 namespace {
 
-constexpr int HR_THREADS = 256;
+constexpr int HH_THREADS = 256;
 
-// The top w x w block of Qp (w <= BH_B): LU without pivoting of Qp1 - D with the
-// signs chosen on the fly; writes V's top block (L1: unit diagonal, zeros above), U,
-// T = -U D L1^{-T} (upper) and d.
-__global__ void __launch_bounds__(HR_THREADS) hr_top_kernel(int w, const double* __restrict__ Qp, long ldq,
-                                                            double* V, long ldv, double* U, double* T, long ldt,
-                                                            double* dsign)
+// The rows [r0, r1) of the panel (mk rows) that block b takes.
+__device__ inline void hh_rows(int mk, int* r0, int* r1)
 {
-    __shared__ double Y[BH_B][BH_B + 1];
-    __shared__ double Mi[BH_B][BH_B + 1];  // L1^{-1}
-    __shared__ double d[BH_B];
-    const int tid = threadIdx.x;
-    for (int e = tid; e < w * w; e += HR_THREADS) Y[e % w][e / w] = Qp[e % w + (long)(e / w) * ldq];
+    const int per = (mk + gridDim.x - 1) / gridDim.x;
+    *r0 = blockIdx.x * per;
+    *r1 = min(mk, *r0 + per);
+}
+
+// Fixed-order sum of v[0..len) by one warp (every block computes the same value); the values come from
+// other blocks, so they are read past L1.
+__device__ inline double warp_sum_fixed(const double* v, int len, int lane)
+{
+    double s = 0.0;
+    for (int i = lane; i < len; i += 32) s += __ldcg(v + i);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
+// Block sum in a fixed tree; red holds HH_THREADS / 32 doubles.
+__device__ inline double block_sum(double v, double* red)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int w = 0; w < HH_THREADS / 32; ++w) t += red[w];
+    return t;
+}
+
+// A grid-wide barrier for a cooperative launch (every block resident): count and gen in global memory,
+// zero before the launch.  The wait is time-limited: past limit_ns the status is raised and every block
+// returns false at this or its next barrier, so the kernel ends.
+__device__ inline bool grid_barrier(unsigned* count, unsigned* gen, uint64_t limit_ns, DevStatus* st, int* ok_s)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* vg = gen;
+        const unsigned g = *vg;
+        __threadfence();
+        bool ok = *(volatile int*)&st->code == 0;
+        if (atomicAdd(count, 1u) == gridDim.x - 1) {
+            *(volatile unsigned*)count = 0;
+            __threadfence();
+            atomicAdd(gen, 1u);
+        } else {
+            const uint64_t t0 = global_ns();
+            while (ok && *vg == g) {
+                if (*(volatile int*)&st->code != 0) ok = false;
+                else if (global_ns() - t0 > limit_ns) {
+                    raise_status(st, OQR_ERR_TIMEOUT, 0, TAG_DIAG);
+                    ok = false;
+                }
+            }
+        }
+        __threadfence();
+        *ok_s = ok ? 1 : 0;
+    }
+    __syncthreads();
+    return *ok_s != 0;
+}
+
+// The panel (mk x w, leading dimension ldp) factored by w Householder reflections, one cooperative launch:
+// per column, the reflector from the column's norm (partials summed in a fixed order by every block), the
+// partial dot products with the later columns; a grid barrier; their sums, the update of the later columns
+// and the next column's norm partials; a grid barrier.  v below the diagonal goes into P; beta, tau out.
+__global__ void __launch_bounds__(HH_THREADS) hh_panel_kernel(int mk, int w, double* P, long ldp, double* part,
+                                                              double* dpart, double* beta, double* tau,
+                                                              unsigned* bar, DevStatus* st, uint64_t limit_ns)
+{
+    __shared__ double red[HH_THREADS / 32];
+    __shared__ double wred[HH_THREADS / 32][BH_B];
+    __shared__ double wv[BH_B];
+    __shared__ double sc_s, tau_s;
+    __shared__ int ok_s;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int r0, r1;
+    hh_rows(mk, &r0, &r1);
+    // column 0's norm below its first row
+    {
+        double a = 0.0;
+        for (int i = max(r0, 1) + threadIdx.x; i < r1; i += HH_THREADS) {
+            const double x = P[i];
+            a = fma(x, x, a);
+        }
+        a = block_sum(a, red);
+        if (threadIdx.x == 0) part[blockIdx.x] = a;
+    }
+    if (!grid_barrier(bar, bar + 1, limit_ns, st, &ok_s)) return;
+    for (int j = 0; j < w; ++j) {
+        // the reflector
+        if (threadIdx.x < 32) {
+            const double s2 = warp_sum_fixed(part, gridDim.x, lane);
+            if (lane == 0) {
+                const double x0 = __ldcg(P + j + (long)j * ldp);  // updated by the block holding row j
+                double b = x0, t = 0.0, sc = 0.0;
+                if (s2 > 0.0) {
+                    b = -copysign(sqrt(fma(x0, x0, s2)), x0);
+                    t = (b - x0) / b;
+                    sc = 1.0 / (x0 - b);
+                }
+                sc_s = sc;
+                tau_s = t;
+                if (blockIdx.x == 0) {
+                    beta[j] = b;
+                    tau[j] = t;
+                }
+            }
+        }
+        __syncthreads();
+        const double sc = sc_s, t = tau_s;
+        double d[BH_B];
+#pragma unroll
+        for (int c = 0; c < BH_B; ++c) d[c] = 0.0;
+        for (int i = max(r0, j) + threadIdx.x; i < r1; i += HH_THREADS) {
+            double v = 1.0;
+            if (i > j) {
+                v = P[i + (long)j * ldp] * sc;
+                P[i + (long)j * ldp] = v;
+            }
+#pragma unroll
+            for (int c = 0; c < BH_B; ++c)
+                if (c > j && c < w) d[c] = fma(v, P[i + (long)c * ldp], d[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < BH_B; ++c) {
+            if (c > j && c < w) {
+                double x = d[c];
+                for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+                if (lane == 0) wred[warp][c] = x;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x > j && threadIdx.x < w) {
+            double x = 0.0;
+            for (int q = 0; q < HH_THREADS / 32; ++q) x += wred[q][threadIdx.x];
+            dpart[(long)threadIdx.x * gridDim.x + blockIdx.x] = x;
+        }
+        if (j + 1 == w) break;  // nothing after the last column (the same for every block)
+        if (!grid_barrier(bar, bar + 1, limit_ns, st, &ok_s)) return;
+        // the update of the later columns, and the next column's norm
+        for (int c = j + 1 + warp; c < w; c += HH_THREADS / 32) {
+            const double x = warp_sum_fixed(dpart + (long)c * gridDim.x, gridDim.x, lane);
+            if (lane == 0) wv[c] = t * x;
+        }
+        __syncthreads();
+        double a = 0.0;
+        for (int i = max(r0, j) + threadIdx.x; i < r1; i += HH_THREADS) {
+            const double v = i > j ? P[i + (long)j * ldp] : 1.0;
+            for (int c = j + 1; c < w; ++c) {
+                const double x = fma(-wv[c], v, P[i + (long)c * ldp]);
+                P[i + (long)c * ldp] = x;
+                if (c == j + 1 && i > j + 1) a = fma(x, x, a);
+            }
+        }
+        a = block_sum(a, red);
+        if (threadIdx.x == 0) part[blockIdx.x] = a;
+        if (!grid_barrier(bar, bar + 1, limit_ns, st, &ok_s)) return;
+    }
+}
+
+// The same factorization with each block's rows of the panel held in shared memory for the whole panel
+// (rows r0..r1-1 at tile[(i - r0) * TS_LD + c]): only the partial sums, and each pivot P(j, j) (published
+// by the block holding row j into xj[j]), go through global memory.  Dynamic shared memory:
+// rows per block x TS_LD doubles.
+constexpr int TS_LD = BH_B + 1;
+__global__ void __launch_bounds__(HH_THREADS) hh_panel_smem_kernel(int mk, int w, double* P, long ldp, double* part,
+                                                                   double* dpart, double* beta, double* tau,
+                                                                   double* xj, int rpb, unsigned* bar,
+                                                                   DevStatus* st, uint64_t limit_ns)
+{
+    extern __shared__ double tile[];
+    __shared__ double red[HH_THREADS / 32];
+    __shared__ double wred[HH_THREADS / 32][BH_B];
+    __shared__ double wv[BH_B];
+    __shared__ double sc_s, tau_s;
+    __shared__ int ok_s;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int r0 = blockIdx.x * rpb, r1 = min(mk, r0 + rpb), nr = max(0, r1 - r0);
+    for (int e = threadIdx.x; e < nr * w; e += HH_THREADS) {
+        const int i = e % nr, c = e / nr;
+        tile[i * TS_LD + c] = P[r0 + i + (long)c * ldp];
+    }
+    __syncthreads();
+    {
+        double a = 0.0;
+        for (int i = max(r0, 1) + threadIdx.x; i < r1; i += HH_THREADS) {
+            const double x = tile[(i - r0) * TS_LD];
+            a = fma(x, x, a);
+        }
+        a = block_sum(a, red);
+        if (threadIdx.x == 0) {
+            part[blockIdx.x] = a;
+            if (r0 == 0 && nr > 0) xj[0] = tile[0];
+        }
+    }
+    if (!grid_barrier(bar, bar + 1, limit_ns, st, &ok_s)) return;
+    for (int j = 0; j < w; ++j) {
+        if (threadIdx.x < 32) {
+            const double s2 = warp_sum_fixed(part, gridDim.x, lane);
+            if (lane == 0) {
+                const double x0 = __ldcg(xj + j);
+                double b = x0, t = 0.0, sc = 0.0;
+                if (s2 > 0.0) {
+                    b = -copysign(sqrt(fma(x0, x0, s2)), x0);
+                    t = (b - x0) / b;
+                    sc = 1.0 / (x0 - b);
+                }
+                sc_s = sc;
+                tau_s = t;
+                if (blockIdx.x == 0) {
+                    beta[j] = b;
+                    tau[j] = t;
+                }
+            }
+        }
+        __syncthreads();
+        const double sc = sc_s, t = tau_s;
+        double d[BH_B];
+#pragma unroll
+        for (int c = 0; c < BH_B; ++c) d[c] = 0.0;
+        for (int i = max(r0, j) + threadIdx.x; i < r1; i += HH_THREADS) {
+            double* row = tile + (i - r0) * TS_LD;
+            double v = 1.0;
+            if (i > j) {
+                v = row[j] * sc;
+                row[j] = v;
+            }
+#pragma unroll
+            for (int c = 0; c < BH_B; ++c)
+                if (c > j && c < w) d[c] = fma(v, row[c], d[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < BH_B; ++c) {
+            if (c > j && c < w) {
+                double x = d[c];
+                for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+                if (lane == 0) wred[warp][c] = x;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x > j && threadIdx.x < w) {
+            double x = 0.0;
+            for (int q = 0; q < HH_THREADS / 32; ++q) x += wred[q][threadIdx.x];
+            dpart[(long)threadIdx.x * gridDim.x + blockIdx.x] = x;
+        }
+        if (j + 1 == w) break;  // the same for every block
+        if (!grid_barrier(bar, bar + 1, limit_ns, st, &ok_s)) return;
+        for (int c = j + 1 + warp; c < w; c += HH_THREADS / 32) {
+            const double x = warp_sum_fixed(dpart + (long)c * gridDim.x, gridDim.x, lane);
+            if (lane == 0) wv[c] = t * x;
+        }
+        __syncthreads();
+        double a = 0.0;
+        for (int i = max(r0, j) + threadIdx.x; i < r1; i += HH_THREADS) {
+            double* row = tile + (i - r0) * TS_LD;
+            const double v = i > j ? row[j] : 1.0;
+            for (int c = j + 1; c < w; ++c) {
+                const double x = fma(-wv[c], v, row[c]);
+                row[c] = x;
+                if (c == j + 1 && i > j + 1) a = fma(x, x, a);
+            }
+            if (i == j + 1) xj[j + 1] = row[j + 1];  // the next pivot, for every block
+        }
+        a = block_sum(a, red);
+        if (threadIdx.x == 0) part[blockIdx.x] = a;
+        if (!grid_barrier(bar, bar + 1, limit_ns, st, &ok_s)) return;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nr * w; e += HH_THREADS) {
+        const int i = e % nr, c = e / nr;
+        P[r0 + i + (long)c * ldp] = tile[i * TS_LD + c];
+    }
+}
+
+// The panel's V (unit lower trapezoidal, explicit) from P's strict lower part.
+__global__ void hh_copy_v_kernel(int mk, int w, const double* __restrict__ P, long ldp, double* V, long ldv)
+{
+    const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long)mk * w) return;
+    const long i = e % mk;
+    const int j = (int)(e / mk);
+    V[i + j * ldv] = i > j ? P[i + j * ldp] : (i == j ? 1.0 : 0.0);
+}
+
+// T (w x w, upper) from tau and G = V^T V: T_jj = tau_j, T(0:j, j) = -tau_j T(0:j, 0:j) G(0:j, j).  One block.
+__global__ void hh_t_kernel(int w, const double* __restrict__ G, const double* __restrict__ tau, double* T, long ldt)
+{
+    __shared__ double Ts[BH_B][BH_B + 1];
+    __shared__ double g[BH_B];
+    const int t = threadIdx.x;
+    for (int e = t; e < BH_B * BH_B; e += blockDim.x) Ts[e % BH_B][e / BH_B] = 0.0;
     __syncthreads();
     for (int j = 0; j < w; ++j) {
-        if (tid == 0) {
-            const double sj = Y[j][j] >= 0.0 ? -1.0 : 1.0;
-            d[j] = sj;
-            Y[j][j] -= sj;  // |pivot| >= 1
-        }
+        if (t < j) g[t] = G[t + j * BH_B];
         __syncthreads();
-        const double piv = Y[j][j];
-        for (int i = j + 1 + tid; i < w; i += HR_THREADS) Y[i][j] /= piv;
-        __syncthreads();
-        for (int e = tid; e < (w - j - 1) * (w - j - 1); e += HR_THREADS) {
-            const int i = j + 1 + e % (w - j - 1), c = j + 1 + e / (w - j - 1);
-            Y[i][c] = fma(-Y[i][j], Y[j][c], Y[i][c]);
+        if (t < j) {
+            double s = 0.0;
+            for (int l = t; l < j; ++l) s = fma(Ts[t][l], g[l], s);
+            Ts[t][j] = -tau[j] * s;
         }
+        if (t == 0) Ts[j][j] = tau[j];
         __syncthreads();
     }
-    // Mi = L1^{-1} (unit lower), column by column
-    for (int c = tid; c < w; c += HR_THREADS) {
-        for (int i = 0; i < w; ++i) Mi[i][c] = i == c ? 1.0 : 0.0;
-        for (int i = c + 1; i < w; ++i) {
-            double t = 0.0;
-            for (int l = c; l < i; ++l) t = fma(Y[i][l], Mi[l][c], t);
-            Mi[i][c] = -t;
-        }
-    }
-    __syncthreads();
-    for (int e = tid; e < w * w; e += HR_THREADS) {
-        const int i = e % w, j = e / w;
-        V[i + (long)j * ldv] = i > j ? Y[i][j] : (i == j ? 1.0 : 0.0);
-        U[i + j * BH_B] = i <= j ? Y[i][j] : 0.0;
-        // T(i, j) = -sum_k U(i, k) d_k L1^{-T}(k, j) = -sum_{k = i..j} U(i, k) d_k Mi(j, k)
-        double t = 0.0;
-        for (int k = i; k <= j; ++k) t = fma(Y[i][k] * d[k], Mi[j][k], t);
-        T[i + (long)j * ldt] = i <= j ? -t : 0.0;
-    }
-    if (tid < w) dsign[tid] = d[tid];
+    for (int e = t; e < w * w; e += blockDim.x) T[e % w + (long)(e / w) * ldt] = Ts[e % w][e / w];
 }
 
-// Rows w..rows-1 of V: V(i, :) = Qp(i, :) U^{-1}, one row per thread.
-__global__ void __launch_bounds__(128) hr_rows_kernel(int rows, int w, const double* __restrict__ Qp, long ldq,
-                                                      const double* __restrict__ U, double* V, long ldv)
-{
-    __shared__ double Us[BH_B][BH_B + 1];
-    __shared__ double dinv[BH_B];
-    for (int e = threadIdx.x; e < w * w; e += 128) Us[e % w][e / w] = U[e % w + (e / w) * BH_B];
-    if (threadIdx.x < w) dinv[threadIdx.x] = 1.0 / U[threadIdx.x * (BH_B + 1)];
-    __syncthreads();
-    const long i = (long)w + (long)blockIdx.x * 128 + threadIdx.x;
-    if (i >= rows) return;
-    double x[BH_B];
-#pragma unroll
-    for (int j = 0; j < BH_B; ++j) {
-        if (j < w) {
-            double t = Qp[i + (long)j * ldq];
-            for (int l = 0; l < j; ++l) t = fma(-x[l], Us[l][j], t);
-            x[j] = t * dinv[j];
-        }
-    }
-#pragma unroll
-    for (int j = 0; j < BH_B; ++j)
-        if (j < w) V[i + (long)j * ldv] = x[j];
-}
-
-// S(k:k+w, k:k+w) = D (D Rp) = Rp (the panel's Householder R, rows scaled by D), and
-// S(k:k+w, k+w:n) = D C(0:w, :) (the panel rows of the updated trailing columns).
-__global__ void panel_r_kernel(int w, int nrest, const double* __restrict__ Rp, const double* __restrict__ C, long ldc,
-                               const double* __restrict__ dsign, double* S, long lds)
+// S(k:k+w, k:n) = D R: the panel's R (beta on the diagonal, P's upper part above it) and the updated
+// trailing rows C(0:w, :), rows scaled by d = sign(beta); dsign = d.
+__global__ void panel_r_kernel(int w, int nrest, const double* __restrict__ P, long ldp, const double* __restrict__ C,
+                               long ldc, const double* __restrict__ beta, double* dsign, double* S, long lds)
 {
     const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
     const long ncol = (long)w + nrest;
     if (e >= (long)w * ncol) return;
     const int i = (int)(e % w);
     const long j = e / w;
+    const double d = beta[i] < 0.0 ? -1.0 : 1.0;
     double v;
-    if (j < w) v = i <= j ? Rp[i + j * (long)w] : 0.0;  // D (D Rp): Rp itself
-    else v = dsign[i] * C[i + (j - w) * ldc];
-    S[i + j * lds] = v;
+    if (j < w) v = j < i ? 0.0 : (j == i ? beta[i] : P[i + j * ldp]);
+    else v = C[i + (j - w) * ldc];
+    S[i + j * lds] = d * v;
+    if (j == 0) dsign[i] = d;
 }
 
 // Y = [I_n; 0]
@@ -141,13 +375,29 @@ BhqrPlan bhqr_plan(int m, int n, int sms)
     p.n = n;
     p.panels = (n + BH_B - 1) / BH_B;
     p.sms = sms;
-    size_t ts = 0;  // the panels' TSQR workspace, the largest over the panels
-    for (int pi = 0; pi < p.panels; ++pi) {
-        const int k = pi * BH_B, w = n - k < BH_B ? n - k : BH_B;
-        const size_t d = tsqr_plan(m - k, w).doubles;
-        if (d > ts) ts = d;
-    }
     p.splits_max = 2 * sms;
+    // the panel kernel's blocks must all be resident (cooperative launch)
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hh_panel_kernel, HH_THREADS, 0) != cudaSuccess ||
+        per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    p.blocks_max = per_sm >= 2 ? 2 * sms : sms;
+    // the shared-memory panel kernel: its tile and static arrays in one SM's shared memory
+    int optin = 0;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, 0) != cudaSuccess) {
+        cudaGetLastError();
+        optin = 0;
+    }
+    const int static_bytes = 8 * 1024;  // red, wred, wv and scalars, rounded up
+    p.smem_rows = optin > static_bytes ? (optin - static_bytes) / (TS_LD * (int)sizeof(double)) : 0;
+    if (p.smem_rows > 0 &&
+        cudaFuncSetAttribute(hh_panel_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             p.smem_rows * TS_LD * (int)sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        p.smem_rows = 0;
+    }
     size_t o = 0;
     auto take = [&](size_t doubles) {
         const size_t r = o;
@@ -156,50 +406,84 @@ BhqrPlan bhqr_plan(int m, int n, int sms)
     };
     p.oX = take((size_t)m * n);
     p.oV = take((size_t)m * n);
-    p.oQp = take((size_t)m * BH_B);
-    p.oRp = take((size_t)BH_B * BH_B);
-    p.oU = take((size_t)BH_B * BH_B);
     p.oT = take((size_t)p.panels * BH_B * BH_B);
     p.oD = take((size_t)p.panels * BH_B);
     p.oW = take((size_t)BH_B * n);
     p.oW2 = take((size_t)BH_B * n);
+    p.oG = take((size_t)BH_B * BH_B);
+    p.oBeta = take(BH_B);
+    p.oTau = take(BH_B);
+    p.oPart = take((size_t)p.blocks_max);
+    p.oDpart = take((size_t)BH_B * p.blocks_max);
     p.oSK = take(gemm_splitk_bytes(BH_B, n, p.splits_max) / sizeof(double) + 1);
-    p.oTS = take(ts);
+    p.oBar = take(1);
+    p.oXj = take(BH_B);
     p.doubles = o;
     return p;
 }
 
 cudaError_t launch_bhqr(const BhqrPlan& p, const double* Z, long ldz, double* Y, long ldy, double* S, long lds,
-                        double* ws, cudaStream_t s)
+                        double* ws, DevStatus* st, uint64_t limit_ns, cudaStream_t s)
 {
     const int m = p.m, n = p.n;
-    double *X = ws + p.oX, *V = ws + p.oV, *Qp = ws + p.oQp, *Rp = ws + p.oRp, *U = ws + p.oU;
-    double *W = ws + p.oW, *W2 = ws + p.oW2, *SK = ws + p.oSK, *TS = ws + p.oTS;
+    double *X = ws + p.oX, *V = ws + p.oV, *W = ws + p.oW, *W2 = ws + p.oW2, *G = ws + p.oG, *SK = ws + p.oSK;
+    double *beta = ws + p.oBeta, *tau = ws + p.oTau, *part = ws + p.oPart, *dpart = ws + p.oDpart;
+    unsigned* bar = reinterpret_cast<unsigned*>(ws + p.oBar);
+    double* xj = ws + p.oXj;
     cudaError_t e;
     if ((e = cudaMemcpy2DAsync(X, (size_t)m * sizeof(double), Z, ldz * sizeof(double), (size_t)m * sizeof(double), n,
                                cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
         return e;
     if ((e = cudaMemsetAsync(V, 0, (size_t)m * n * sizeof(double), s)) != cudaSuccess) return e;
     if ((e = cudaMemset2DAsync(S, lds * sizeof(double), 0, (size_t)n * sizeof(double), n, s)) != cudaSuccess) return e;
-    auto splits_for = [&](int M, int N) {
-        const int tiles = ((M + 63) / 64) * ((N + 63) / 64);
-        const int sp = 2 * p.sms / tiles;
+    // split-K for a product with an M <= 32 row result (32 x 128 tiles) and a long contraction: about two
+    // blocks per SM (FP64 throughput needs them; a warp per element sums the partials)
+    auto splits_for = [&](int N, int K) {
+        const int tiles = (N + 127) / 128;
+        int sp = 2 * p.sms / tiles;
+        const int by_k = K / 64;  // at least four 16-deep k-steps per split
+        if (sp > by_k) sp = by_k;
         return sp < 1 ? 1 : sp > p.splits_max ? p.splits_max : sp;
     };
     for (int pi = 0; pi < p.panels; ++pi) {
         const int k = pi * BH_B, w = n - k < BH_B ? n - k : BH_B, mk = m - k, nrest = n - k - w;
         double* T = ws + p.oT + (size_t)pi * BH_B * BH_B;
         double* D = ws + p.oD + (size_t)pi * BH_B;
-        double* Vp = V + k + (size_t)k * m;  // rows k.., columns k..k+w-1 of V
+        double* P = X + k + (size_t)k * m;   // the panel, rows k.., leading dimension m
+        double* Vp = V + k + (size_t)k * m;
         double* C = X + k + (size_t)(k + w) * m;
-        const TsqrPlan tp = tsqr_plan(mk, w);
-        if ((e = launch_tsqr(tp, X + k + (size_t)k * m, m, Qp, mk, Rp, w, TS, s)) != cudaSuccess) return e;
-        hr_top_kernel<<<1, HR_THREADS, 0, s>>>(w, Qp, mk, Vp, m, U, T, BH_B, D);
-        if (mk > w) hr_rows_kernel<<<(unsigned)((mk - w + 127) / 128), 128, 0, s>>>(mk, w, Qp, mk, U, Vp, m);
+        // the panel's reflectors, column by column (one cooperative launch); each block's rows in shared
+        // memory when the panel fits (one block per SM), else in global memory
+        if ((e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s)) != cudaSuccess) return e;
+        int mk_ = mk, w_ = w;
+        long ldp_ = m;
+        uint64_t lim = limit_ns;
+        int rpb = (mk + p.sms - 1) / p.sms;
+        if (rpb < 512) rpb = 512;
+        if (rpb <= p.smem_rows) {
+            int nb = (mk + rpb - 1) / rpb;
+            void* args[] = {&mk_, &w_, &P, &ldp_, &part, &dpart, &beta, &tau, &xj, &rpb, &bar, &st, &lim};
+            if ((e = cudaLaunchCooperativeKernel((const void*)hh_panel_smem_kernel, dim3(nb), dim3(HH_THREADS), args,
+                                                 (size_t)rpb * TS_LD * sizeof(double), s)) != cudaSuccess)
+                return e;
+        } else {
+            int nb = (mk + 511) / 512;
+            nb = nb < 1 ? 1 : nb > p.blocks_max ? p.blocks_max : nb;
+            void* args[] = {&mk_, &w_, &P, &ldp_, &part, &dpart, &beta, &tau, &bar, &st, &lim};
+            if ((e = cudaLaunchCooperativeKernel((const void*)hh_panel_kernel, dim3(nb), dim3(HH_THREADS), args, 0,
+                                                 s)) != cudaSuccess)
+                return e;
+        }
+        // V explicit, then T from V^T V
+        hh_copy_v_kernel<<<(unsigned)(((long)mk * w + 255) / 256), 256, 0, s>>>(mk, w, P, m, Vp, m);
+        if ((e = launch_gemm_f64(GEMM_T, w, w, mk, 1.0, Vp, m, Vp, m, 0.0, G, BH_B, SK, splits_for(w, mk), s)) !=
+            cudaSuccess)
+            return e;
+        hh_t_kernel<<<1, 64, 0, s>>>(w, G, tau, T, BH_B);
         if (nrest > 0) {
             // C = C - V (T^T (V^T C))
-            const int sp = splits_for(w, nrest);
-            if ((e = launch_gemm_f64(GEMM_T, w, nrest, mk, 1.0, Vp, m, C, m, 0.0, W, BH_B, SK, sp, s)) != cudaSuccess)
+            if ((e = launch_gemm_f64(GEMM_T, w, nrest, mk, 1.0, Vp, m, C, m, 0.0, W, BH_B, SK, splits_for(nrest, mk),
+                                     s)) != cudaSuccess)
                 return e;
             if ((e = launch_gemm_f64(GEMM_T, w, nrest, w, 1.0, T, BH_B, W, BH_B, 0.0, W2, BH_B, nullptr, 1, s)) !=
                 cudaSuccess)
@@ -209,8 +493,8 @@ cudaError_t launch_bhqr(const BhqrPlan& p, const double* Z, long ldz, double* Y,
                 return e;
         }
         const long tot = (long)w * (w + nrest);
-        panel_r_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(w, nrest, Rp, C, m, D, S + k + (size_t)k * lds,
-                                                                     lds);
+        panel_r_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(w, nrest, P, m, C, m, beta, D,
+                                                                     S + k + (size_t)k * lds, lds);
     }
     // Y = H_0 ... H_{P-1} [I_n; 0], then Y D
     identity_kernel<<<(unsigned)(((long)m * n + 255) / 256), 256, 0, s>>>(m, n, Y, ldy);
@@ -219,8 +503,8 @@ cudaError_t launch_bhqr(const BhqrPlan& p, const double* Z, long ldz, double* Y,
         const double* T = ws + p.oT + (size_t)pi * BH_B * BH_B;
         const double* Vp = V + k + (size_t)k * m;
         double* B = Y + k + (size_t)k * ldy;
-        const int sp = splits_for(w, nc);
-        if ((e = launch_gemm_f64(GEMM_T, w, nc, mk, 1.0, Vp, m, B, ldy, 0.0, W, BH_B, SK, sp, s)) != cudaSuccess)
+        if ((e = launch_gemm_f64(GEMM_T, w, nc, mk, 1.0, Vp, m, B, ldy, 0.0, W, BH_B, SK, splits_for(nc, mk), s)) !=
+            cudaSuccess)
             return e;
         if ((e = launch_gemm_f64(GEMM_N, w, nc, w, 1.0, T, BH_B, W, BH_B, 0.0, W2, BH_B, nullptr, 1, s)) != cudaSuccess)
             return e;

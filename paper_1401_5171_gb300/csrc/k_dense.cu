@@ -569,14 +569,75 @@ __global__ void __launch_bounds__(GTHREADS) gemm_f64_kernel(GemmOp op, int M, in
         }
 }
 
+// C = beta C + alpha A^T B for M <= 32 (A stored K x M): 32 x 128 tiles, so a narrow A^T fills the tile;
+// the same 16-deep k-steps, 4 x 4 per thread, and split-K partials as gemm_f64_kernel.
+constexpr int GTN_M = 32, GTN_N = 128;
+__global__ void __launch_bounds__(GTHREADS) gemm_f64_tn32_kernel(int M, int N, int K, double alpha,
+                                                                 const double* __restrict__ A, long lda,
+                                                                 const double* __restrict__ B, long ldb, double beta,
+                                                                 double* C, long ldc, double* ws)
+{
+    __shared__ double As[GK][GTN_M + 1];
+    __shared__ double Bs[GK][GTN_N + 1];
+    const int tid = threadIdx.x, ty = tid & 7, tx = tid >> 3;
+    const long j0 = (long)blockIdx.y * GTN_N;
+    const int splits = gridDim.z;
+    const long kper = ((K + splits - 1) / splits + GK - 1) / GK * GK;
+    const long k0 = (long)blockIdx.z * kper, k1 = min((long)K, k0 + kper);
+    double acc[4][4] = {};
+    for (long kk = k0; kk < k1; kk += GK) {
+        for (int e = tid; e < GTN_M * GK; e += GTHREADS) {
+            const int k = e % GK, r = e / GK;
+            const long gk = kk + k;
+            As[k][r] = (r < M && gk < k1) ? A[gk + r * lda] : 0.0;
+        }
+        for (int e = tid; e < GK * GTN_N; e += GTHREADS) {
+            const int k = e % GK, c = e / GK;
+            const long gk = kk + k, gj = j0 + c;
+            Bs[k][c] = (gk < k1 && gj < N) ? B[gk + gj * ldb] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < GK; ++k) {
+            double av[4], bv[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) av[i] = As[k][ty + 8 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) bv[j] = Bs[k][tx + 32 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const long gi = ty + 8 * i, gj = j0 + tx + 32 * j;
+            if (gi >= M || gj >= N) continue;
+            if (splits == 1) {
+                const double c0 = beta == 0.0 ? 0.0 : beta * C[gi + gj * ldc];
+                C[gi + gj * ldc] = c0 + alpha * acc[i][j];
+            } else {
+                ws[(size_t)blockIdx.z * M * N + gi + gj * (size_t)M] = acc[i][j];
+            }
+        }
+}
+
+// One warp per output element: lane l sums partials l, l + 32, ..., then a fixed shuffle tree.
 __global__ void gemm_splitk_reduce_kernel(int M, int N, int splits, double alpha, const double* ws, double beta,
                                           double* C, long ldc)
 {
-    const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long e = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (e >= (long)M * N) return;
     const long i = e % M, j = e / M;
     double s = 0.0;
-    for (int z = 0; z < splits; ++z) s += ws[(size_t)z * M * N + e];
+    for (int z = lane; z < splits; z += 32) s += ws[(size_t)z * M * N + e];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane != 0) return;
     const double c0 = beta == 0.0 ? 0.0 : beta * C[i + j * ldc];
     C[i + j * ldc] = c0 + alpha * s;
 }
@@ -684,10 +745,15 @@ cudaError_t launch_gemm_f64(GemmOp op, int M, int N, int K, double alpha, const 
 {
     if (M <= 0 || N <= 0) return cudaSuccess;
     if (splits < 1) splits = 1;
-    dim3 grid((M + GT - 1) / GT, (N + GT - 1) / GT, splits);
-    gemm_f64_kernel<<<grid, GTHREADS, 0, s>>>(op, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, splitk_ws);
+    if (op == GEMM_T && M <= GTN_M) {
+        dim3 grid(1, (N + GTN_N - 1) / GTN_N, splits);
+        gemm_f64_tn32_kernel<<<grid, GTHREADS, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, splitk_ws);
+    } else {
+        dim3 grid((M + GT - 1) / GT, (N + GT - 1) / GT, splits);
+        gemm_f64_kernel<<<grid, GTHREADS, 0, s>>>(op, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, splitk_ws);
+    }
     if (splits > 1) {
-        const long total = (long)M * N;
+        const long total = (long)M * N * 32;  // a warp per element
         gemm_splitk_reduce_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(M, N, splits, alpha, splitk_ws,
                                                                                  beta, C, ldc);
     }

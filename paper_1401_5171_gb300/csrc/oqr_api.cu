@@ -541,10 +541,10 @@ size_t euclid_qr_bytes(int m, int n, int sms)
     return align256((n <= BH_B ? tsqr_plan(m, n).doubles : bhqr_plan(m, n, sms).doubles) * sizeof(double));
 }
 cudaError_t launch_euclid_qr(int m, int n, const double* Z, long ldz, double* Y, long ldy, double* S, long lds,
-                             double* ws, int sms, cudaStream_t s)
+                             double* ws, int sms, DevStatus* st, uint64_t limit_ns, cudaStream_t s)
 {
     if (n <= BH_B) return launch_tsqr(tsqr_plan(m, n), Z, ldz, Y, ldy, S, lds, ws, s);
-    return launch_bhqr(bhqr_plan(m, n, sms), Z, ldz, Y, ldy, S, lds, ws, s);
+    return launch_bhqr(bhqr_plan(m, n, sms), Z, ldz, Y, ldy, S, lds, ws, st, limit_ns, s);
 }
 
 oqr_status precholqr_impl(oqr_ctx* ctx, int m, int n, const AOp& op, const double* Z, long ldz, double* Q, long ldq,
@@ -573,7 +573,16 @@ oqr_status precholqr_impl(oqr_ctx* ctx, int m, int n, const AOp& op, const doubl
     double* tws = reinterpret_cast<double*>(static_cast<char*>(ctx->ws) + reserve);
     {
         const NvtxRange range("oqr: Householder QR %d", n);
-        OQR_TRY(launch_euclid_qr(m, n, Z, ldz, Q, ldq, S, n, tws, ctx->sm_count, s));  // Y into Q
+        if ((v = reset_status(ctx, s)) != OQR_OK) return v;
+        OQR_TRY(launch_euclid_qr(m, n, Z, ldz, Q, ldq, S, n, tws, ctx->sm_count, ctx->st, (uint64_t)o.spin_limit,
+                                 s));  // Y into Q
+        if (n > BH_B) {  // the blocked QR's waits report through the status, which the pass below resets
+            DevStatus h;
+            if (cudaMemcpyAsync(&h, ctx->st, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                cudaStreamSynchronize(s) != cudaSuccess)
+                return OQR_ERR_CUDA;
+            if (h.code != 0) return static_cast<oqr_status>(h.code);
+        }
     }
     // CHOLQR on Y in place (Q aliases Y), its factor into U; no synchronization yet
     if ((v = normal_equation(ctx, m, n, op, Q, ldq, Q, ldq, Uf, n, &o, nullptr, s, 1, false, reserve)) != OQR_OK)
@@ -1928,9 +1937,13 @@ oqr_status oqr_tsqr(oqr_ctx* ctx, int m, int n, const double* Z, long ldz, doubl
     if (n > 1024) return OQR_ERR_UNSUPPORTED;
     oqr_status v = ensure_ws(ctx, euclid_qr_bytes(m, n, ctx->sm_count));
     if (v != OQR_OK) return v;
-    OQR_TRY(launch_euclid_qr(m, n, Z, ldz, Y, ldy, S, lds, static_cast<double*>(ctx->ws), ctx->sm_count,
-                             static_cast<cudaStream_t>(stream)));
-    return OQR_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if ((v = reset_status(ctx, s)) != OQR_OK) return v;
+    const oqr_opts o = resolve(nullptr);
+    OQR_TRY(launch_euclid_qr(m, n, Z, ldz, Y, ldy, S, lds, static_cast<double*>(ctx->ws), ctx->sm_count, ctx->st,
+                             (uint64_t)o.spin_limit, s));
+    oqr_info info;
+    return finish(ctx, s, &info, 0, false);
 }
 
 oqr_status oqr_symm(oqr_ctx* ctx, int m, int k, const double* A, long lda, const double* B, long ldb, double* C,

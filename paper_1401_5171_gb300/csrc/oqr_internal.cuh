@@ -243,18 +243,21 @@ cudaError_t launch_tsqr(const TsqrPlan& p, const double* Z, long ldz, double* Y,
                         double* ws, cudaStream_t s);
 
 // Blocked Householder QR of a tall-skinny Z (k_bhqr.cu), the same contract as launch_tsqr: Z = Y S, Y
-// orthonormal, S upper triangular with a positive diagonal.  Panels of BH_B columns are factored by the
-// TSQR, their Householder vectors recovered from its explicit Q, the trailing columns and Y updated by
-// FP64 GEMMs; the workspace holds bhqr_plan(m, n, sms).doubles doubles.
+// orthonormal, S upper triangular with a positive diagonal.  Panels of BH_B columns are factored column
+// by column over all SMs, blocked as I - V T V^T, the trailing columns and Y updated by FP64 GEMMs; the
+// workspace holds bhqr_plan(m, n, sms).doubles doubles.
 constexpr int BH_B = 32;
 struct BhqrPlan {
-    int m, n, panels, sms, splits_max;
-    size_t oX, oV, oQp, oRp, oU, oT, oD, oW, oW2, oSK, oTS;  // workspace offsets (doubles)
+    int m, n, panels, sms, splits_max, blocks_max;
+    int smem_rows;  // rows per block that the shared-memory panel kernel can hold
+    size_t oX, oV, oT, oD, oW, oW2, oG, oBeta, oTau, oPart, oDpart, oSK, oBar, oXj;  // workspace offsets (doubles)
     size_t doubles;
 };
 BhqrPlan bhqr_plan(int m, int n, int sms);
+// The panel kernel's grid barriers wait at most limit_ns; past it the status st is raised (OQR_ERR_TIMEOUT)
+// and the factorization's results are not to be used.
 cudaError_t launch_bhqr(const BhqrPlan& p, const double* Z, long ldz, double* Y, long ldy, double* S, long lds,
-                        double* ws, cudaStream_t s);
+                        double* ws, DevStatus* st, uint64_t limit_ns, cudaStream_t s);
 
 // Tridiagonal A (k_tridiag.cu): d (m), e (m - 1); U = M X with M = tril(T, -1) + diag(T) / 2.
 cudaError_t launch_tridiag_u(int m, int n, const double* d, const double* e, const double* X, long ldx, double* U,
