@@ -202,6 +202,38 @@ def test_selector_mode_through_the_c_abi(env):
         assert np.linalg.norm(Rs[b].cpu().numpy() - Rr) / np.linalg.norm(Rr) <= max(1e-12, 100 * U * np.linalg.cond(Rr))
 
 
+def _forced(torch, k):
+    """Network parameters whose choice is always option k (last layer: zero weights, bias one-hot)."""
+    p = np.zeros(mlp.COUNT, dtype=np.float32)
+    p[-4 + k] = 10.0
+    return torch.as_tensor(p, device="cuda")
+
+
+def test_selector_routes_on_the_device(env):
+    """The routes decided on the device, each forced by the network on a batch whose kappa(A^{1/2} Z) reaches
+    ~1e11: 'plain' (options 1 and 2) must settle one-pass against two-pass from the pass-1 Gram and send
+    the instances a plain route cannot reach to the late shifted refactor (reported as the shifted
+    option); 'shift' runs shifted A-CholQR3 from the probe's Gram; every result meets the bar, with the
+    extra check's values (check_all) at most that bar."""
+    torch, oqr, ctx = env
+    As, Zs, tab = inputs.batch_instances(48, seed=43, device="cuda", m_range=(64, 1500), n_range=(4, 64),
+                                         log_kappa_a=(0.0, 5.0), log_kappa_z=(0.0, 9.0))
+    for k in (0, 1, 2):
+        Qs, Rs, st, orth, choice = selector.solve_batch(ctx, As, Zs, _forced(torch, k), check_all=True)
+        st, ch, orth = st.cpu().numpy(), choice.cpu().numpy(), orth.cpu().numpy()
+        o, bar = _bar(torch, As, Zs, Qs, st, tab)
+        for b in range(len(Zs)):
+            assert st[b] == 0, (k, b, st[b])
+            assert o[b] <= bar[b], (k, b, ch[b], o[b], bar[b])
+            assert np.isnan(orth[b]) or orth[b] <= 10 * bar[b] + 1e-12, (k, b, orth[b])
+        if k < 2:
+            assert set(ch.tolist()) <= {0, 1, 2}
+            assert (ch == 2).any(), "no instance of this batch needed the late shifted refactor"
+            assert (ch < 2).any()
+        else:
+            assert set(ch.tolist()) == {2}
+
+
 def test_selector_trains_and_beats_fixed_policies(env):
     """Train on method-generated instances (m <= 1024) with the library's kernels; then, on the selector's
     workload at the batched sizes (m up to 4096, kappa(A^{1/2} Z) to ~1e12), the selector through the C ABI
