@@ -12,9 +12,12 @@
 // in a fixed order.  The panel's reflectors are then blocked as
 // I - V T V^T with T upper triangular (T_jj = tau_j, T(0:j, j) =
 // -tau_j T(0:j, 0:j) V(:, 0:j)^T v_j), and the trailing columns
-// C = X(k:m, k+w:n) become C - V (T^T (V^T C)) by FP64 GEMMs.  Y is formed
-// from the right: [I_n; 0], then I - V T V^T applied for the panels in
-// reverse order.  With D = sign(diag(R)), Y D and D R give S's positive
+// C = X(k:m, k+w:n) become C - V (T^T (V^T C)): V^T C (contraction over the
+// m - k rows) and V W (contraction over the w columns, formed transposed as
+// W^T V^T and subtracted transposed) FP64-accurate on the tensor cores
+// (launch_tc_xty), T^T (V^T C) in FP64.  Y is formed from the right:
+// [I_n; 0], then I - V T V^T applied for the panels in reverse order, the
+// same way.  With D = sign(diag(R)), Y D and D R give S's positive
 // diagonal.
 #include "oqr_internal.cuh"
 
@@ -348,6 +351,34 @@ __global__ void panel_r_kernel(int w, int nrest, const double* __restrict__ P, l
     if (j == 0) dsign[i] = d;
 }
 
+// Vt (w x rows, leading dimension ldt) = V^T for V (rows x w, leading dimension ldv).
+__global__ void transpose_kernel(int rows, int w, const double* __restrict__ V, long ldv, double* Vt, long ldt)
+{
+    __shared__ double t[32][33];
+    const int r0 = blockIdx.x * 32, c = threadIdx.y;
+    {
+        const int r = r0 + threadIdx.x;  // coalesced read of V along its rows
+        t[threadIdx.x][c] = (r < rows && c < w) ? V[r + (long)c * ldv] : 0.0;
+    }
+    __syncthreads();
+    const int r = r0 + threadIdx.y;
+    if (threadIdx.x < w && r < rows) Vt[threadIdx.x + (long)r * ldt] = t[threadIdx.y][threadIdx.x];
+}
+
+// B(i, j) -= P(j, i) for B rows x cols (leading dimension ldb) and P cols x rows (leading dimension ldp).
+__global__ void sub_transposed_kernel(int rows, int cols, const double* __restrict__ P, long ldp, double* B, long ldb)
+{
+    __shared__ double t[32][33];
+    const int j0 = blockIdx.y * 32, i0 = blockIdx.x * 32;
+    {
+        const int j = j0 + threadIdx.x, i = i0 + threadIdx.y;  // coalesced read of P along j
+        t[threadIdx.y][threadIdx.x] = (j < cols && i < rows) ? P[j + (long)i * ldp] : 0.0;
+    }
+    __syncthreads();
+    const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;  // coalesced update of B along i
+    if (i < rows && j < cols) B[i + (long)j * ldb] -= t[threadIdx.x][threadIdx.y];
+}
+
 // Y = [I_n; 0]
 __global__ void identity_kernel(int m, int n, double* Y, long ldy)
 {
@@ -375,7 +406,6 @@ BhqrPlan bhqr_plan(int m, int n, int sms)
     p.n = n;
     p.panels = (n + BH_B - 1) / BH_B;
     p.sms = sms;
-    p.splits_max = 2 * sms;
     // the panel kernel's blocks must all be resident (cooperative launch)
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hh_panel_kernel, HH_THREADS, 0) != cudaSuccess ||
@@ -415,9 +445,12 @@ BhqrPlan bhqr_plan(int m, int n, int sms)
     p.oTau = take(BH_B);
     p.oPart = take((size_t)p.blocks_max);
     p.oDpart = take((size_t)BH_B * p.blocks_max);
-    p.oSK = take(gemm_splitk_bytes(BH_B, n, p.splits_max) / sizeof(double) + 1);
     p.oBar = take(1);
     p.oXj = take(BH_B);
+    const size_t xt1 = tc_xty_bytes(m, BH_B, n), xt2 = tc_xty_bytes(BH_B, n, m);
+    p.oXT = take((xt1 > xt2 ? xt1 : xt2) / sizeof(double) + 1);
+    p.oVt = take((size_t)BH_B * m);
+    p.oPt = take((size_t)n * m);
     p.doubles = o;
     return p;
 }
@@ -426,9 +459,10 @@ cudaError_t launch_bhqr(const BhqrPlan& p, const double* Z, long ldz, double* Y,
                         double* ws, DevStatus* st, uint64_t limit_ns, cudaStream_t s)
 {
     const int m = p.m, n = p.n;
-    double *X = ws + p.oX, *V = ws + p.oV, *W = ws + p.oW, *W2 = ws + p.oW2, *G = ws + p.oG, *SK = ws + p.oSK;
+    double *X = ws + p.oX, *V = ws + p.oV, *W = ws + p.oW, *W2 = ws + p.oW2, *G = ws + p.oG;
     double *beta = ws + p.oBeta, *tau = ws + p.oTau, *part = ws + p.oPart, *dpart = ws + p.oDpart;
     unsigned* bar = reinterpret_cast<unsigned*>(ws + p.oBar);
+    double *Vt = ws + p.oVt, *Pt = ws + p.oPt;
     double* xj = ws + p.oXj;
     cudaError_t e;
     if ((e = cudaMemcpy2DAsync(X, (size_t)m * sizeof(double), Z, ldz * sizeof(double), (size_t)m * sizeof(double), n,
@@ -436,15 +470,6 @@ cudaError_t launch_bhqr(const BhqrPlan& p, const double* Z, long ldz, double* Y,
         return e;
     if ((e = cudaMemsetAsync(V, 0, (size_t)m * n * sizeof(double), s)) != cudaSuccess) return e;
     if ((e = cudaMemset2DAsync(S, lds * sizeof(double), 0, (size_t)n * sizeof(double), n, s)) != cudaSuccess) return e;
-    // split-K for a product with an M <= 32 row result (32 x 128 tiles) and a long contraction: about two
-    // blocks per SM (FP64 throughput needs them; a warp per element sums the partials)
-    auto splits_for = [&](int N, int K) {
-        const int tiles = (N + 127) / 128;
-        int sp = 2 * p.sms / tiles;
-        const int by_k = K / 64;  // at least four 16-deep k-steps per split
-        if (sp > by_k) sp = by_k;
-        return sp < 1 ? 1 : sp > p.splits_max ? p.splits_max : sp;
-    };
     for (int pi = 0; pi < p.panels; ++pi) {
         const int k = pi * BH_B, w = n - k < BH_B ? n - k : BH_B, mk = m - k, nrest = n - k - w;
         double* T = ws + p.oT + (size_t)pi * BH_B * BH_B;
@@ -476,21 +501,24 @@ cudaError_t launch_bhqr(const BhqrPlan& p, const double* Z, long ldz, double* Y,
         }
         // V explicit, then T from V^T V
         hh_copy_v_kernel<<<(unsigned)(((long)mk * w + 255) / 256), 256, 0, s>>>(mk, w, P, m, Vp, m);
-        if ((e = launch_gemm_f64(GEMM_T, w, w, mk, 1.0, Vp, m, Vp, m, 0.0, G, BH_B, SK, splits_for(w, mk), s)) !=
-            cudaSuccess)
+        if ((e = launch_tc_xty(mk, w, w, Vp, m, Vp, m, G, BH_B, ws + p.oXT, st, limit_ns, p.sms, s)) != cudaSuccess)
             return e;
+        transpose_kernel<<<dim3((mk + 31) / 32), dim3(32, 32), 0, s>>>(mk, w, Vp, m, Vt, BH_B);
         hh_t_kernel<<<1, 64, 0, s>>>(w, G, tau, T, BH_B);
         if (nrest > 0) {
             // C = C - V (T^T (V^T C))
-            if ((e = launch_gemm_f64(GEMM_T, w, nrest, mk, 1.0, Vp, m, C, m, 0.0, W, BH_B, SK, splits_for(nrest, mk),
-                                     s)) != cudaSuccess)
+            if ((e = launch_tc_xty(mk, w, nrest, Vp, m, C, m, W, BH_B, ws + p.oXT, st, limit_ns, p.sms, s)) !=
+                cudaSuccess)
                 return e;
             if ((e = launch_gemm_f64(GEMM_T, w, nrest, w, 1.0, T, BH_B, W, BH_B, 0.0, W2, BH_B, nullptr, 1, s)) !=
                 cudaSuccess)
                 return e;
-            if ((e = launch_gemm_f64(GEMM_N, mk, nrest, w, -1.0, Vp, m, W2, BH_B, 1.0, C, m, nullptr, 1, s)) !=
-                cudaSuccess)
+            // C -= V W2, formed transposed on the tensor cores: Pt = W2^T V^T (nrest x mk), contraction w
+            if ((e = launch_tc_xty(w, nrest, mk, W2, BH_B, Vt, BH_B, Pt, nrest, ws + p.oXT, st, limit_ns, p.sms,
+                                   s)) != cudaSuccess)
                 return e;
+            sub_transposed_kernel<<<dim3((mk + 31) / 32, (nrest + 31) / 32), dim3(32, 32), 0, s>>>(mk, nrest, Pt,
+                                                                                                  nrest, C, m);
         }
         const long tot = (long)w * (w + nrest);
         panel_r_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(w, nrest, P, m, C, m, beta, D,
@@ -503,13 +531,15 @@ cudaError_t launch_bhqr(const BhqrPlan& p, const double* Z, long ldz, double* Y,
         const double* T = ws + p.oT + (size_t)pi * BH_B * BH_B;
         const double* Vp = V + k + (size_t)k * m;
         double* B = Y + k + (size_t)k * ldy;
-        if ((e = launch_gemm_f64(GEMM_T, w, nc, mk, 1.0, Vp, m, B, ldy, 0.0, W, BH_B, SK, splits_for(nc, mk), s)) !=
-            cudaSuccess)
+        if ((e = launch_tc_xty(mk, w, nc, Vp, m, B, ldy, W, BH_B, ws + p.oXT, st, limit_ns, p.sms, s)) != cudaSuccess)
             return e;
         if ((e = launch_gemm_f64(GEMM_N, w, nc, w, 1.0, T, BH_B, W, BH_B, 0.0, W2, BH_B, nullptr, 1, s)) != cudaSuccess)
             return e;
-        if ((e = launch_gemm_f64(GEMM_N, mk, nc, w, -1.0, Vp, m, W2, BH_B, 1.0, B, ldy, nullptr, 1, s)) != cudaSuccess)
+        transpose_kernel<<<dim3((mk + 31) / 32), dim3(32, 32), 0, s>>>(mk, w, Vp, m, Vt, BH_B);
+        if ((e = launch_tc_xty(w, nc, mk, W2, BH_B, Vt, BH_B, Pt, nc, ws + p.oXT, st, limit_ns, p.sms, s)) !=
+            cudaSuccess)
             return e;
+        sub_transposed_kernel<<<dim3((mk + 31) / 32, (nc + 31) / 32), dim3(32, 32), 0, s>>>(mk, nc, Pt, nc, B, ldy);
     }
     scale_columns_kernel<<<(unsigned)(((long)m * n + 255) / 256), 256, 0, s>>>(m, n, Y, ldy, ws + p.oD);
     return cudaGetLastError();

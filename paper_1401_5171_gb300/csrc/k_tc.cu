@@ -1848,6 +1848,90 @@ cudaError_t launch_tc_cross(const TcPlan& p, const double* X, long ldx, const do
     return tc_cross_phase(p, L, U, ldu, G, ldg, shift_ptr, st, limit_ns, sms, s, nullptr);
 }
 
+// C = X^T Y, FP64-accurate on the tensor cores, for X (K x n1) and Y (K x n2) of any widths (each up to
+// the plane capacity given to tc_xty_bytes): the two column splits, the EMU64 product with items of
+// XTY_PIECE k-steps (short, so that a narrow output still spreads over the SMs), the reduction of each
+// element's pieces in order.  C is n1 x n2 with leading dimension ldc.
+namespace {
+constexpr int XTY_PIECE = 2 * EMU_CH;  // k-steps per item: two exponent chunks
+struct XtyLayout {
+    __nv_bfloat16 *Xp, *Yp;
+    int *eX, *eY, *mX, *mY, *cum;
+    double* slots;
+    size_t bytes;
+};
+XtyLayout xty_layout(int K, int n1, int n2, void* ws)
+{
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    char* base = static_cast<char*>(ws);
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        char* q = base ? base + o : nullptr;
+        o += al(bytes);
+        return q;
+    };
+    const long ldp = ((long)K + KCH_EMU - 1) / KCH_EMU * KCH_EMU;
+    const int kch = (int)(ldp / KCH_EMU);
+    const long items = (long)((n1 + TM - 1) / TM) * ((n2 + EMU_N - 1) / EMU_N) *
+                       ((ldp / EMU_KS + XTY_PIECE - 1) / XTY_PIECE);
+    XtyLayout L;
+    L.Xp = reinterpret_cast<__nv_bfloat16*>(take((size_t)EMU_S * n1 * ldp * 2));
+    L.Yp = reinterpret_cast<__nv_bfloat16*>(take((size_t)EMU_S * n2 * ldp * 2));
+    L.eX = reinterpret_cast<int*>(take((size_t)kch * n1 * 4));
+    L.eY = reinterpret_cast<int*>(take((size_t)kch * n2 * 4));
+    L.mX = reinterpret_cast<int*>(take((size_t)n1 * 4));
+    L.mY = reinterpret_cast<int*>(take((size_t)n2 * 4));
+    L.cum = reinterpret_cast<int*>(take((size_t)((n1 + TM - 1) / TM + 2) * 4));
+    L.slots = reinterpret_cast<double*>(take((size_t)items * TM * EMU_N * 8));
+    L.bytes = o;
+    return L;
+}
+}  // namespace
+
+size_t tc_xty_bytes(int K, int n1, int n2) { return xty_layout(K, n1, n2, nullptr).bytes; }
+
+cudaError_t launch_tc_xty(int K, int n1, int n2, const double* X, long ldx, const double* Y, long ldy, double* C,
+                          long ldc, void* ws, DevStatus* st, uint64_t limit_ns, int sms, cudaStream_t s)
+{
+    if (K <= 0 || n1 <= 0 || n2 <= 0) return cudaSuccess;
+    const XtyLayout L = xty_layout(K, n1, n2, ws);
+    const long ldp = ((long)K + KCH_EMU - 1) / KCH_EMU * KCH_EMU;
+    const int kch = (int)(ldp / KCH_EMU);
+    const size_t planeX = (size_t)n1 * ldp, planeY = (size_t)n2 * ldp;
+    fill_int_kernel<<<(n1 + 255) / 256, 256, 0, s>>>(L.mX, n1, EXP_NONE);
+    fill_int_kernel<<<(n2 + 255) / 256, 256, 0, s>>>(L.mY, n2, EXP_NONE);
+    split_tall_kernel<1, KCH_EMU><<<dim3(kch, (n1 + 7) / 8), 256, 0, s>>>(K, n1, X, ldx, EMU_S, L.Xp, ldp, planeX,
+                                                                          L.eX, L.mX);
+    split_tall_kernel<1, KCH_EMU><<<dim3(kch, (n2 + 7) / 8), 256, 0, s>>>(K, n2, Y, ldy, EMU_S, L.Yp, ldp, planeY,
+                                                                          L.eY, L.mY);
+    TcArgs a{};
+    a.rowsA = n1;
+    a.colsB = n2;
+    a.K = K;
+    a.tri = 0;
+    a.ks = EMU_KS;
+    a.piece = XTY_PIECE;
+    a.cc = (n2 + EMU_N - 1) / EMU_N;
+    a.rt = (n1 + TM - 1) / TM;
+    int items = 0;
+    for (int I = 0; I < a.rt; ++I) items += pieces_of(a, I) * a.cc;
+    a.nitems = items;
+    a.cum = L.cum;
+    a.slots = L.slots;
+    a.eA = L.eX;
+    a.eB = L.eY;
+    a.emaxA = L.mX;
+    a.emaxB = L.mY;
+    a.st = st;
+    a.limit_ns = limit_ns;
+    item_prefix_kernel<<<1, PREFIX_THREADS, 0, s>>>(a, L.cum);
+    cudaError_t e = launch_emu(a, L.Xp, ldp, planeX, L.Yp, ldp, planeY, sms, s);
+    if (e != cudaSuccess) return e;
+    const long tot = (long)n1 * n2;
+    slot_reduce_kernel<EMU_N><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(a, C, ldc, st);
+    return cudaGetLastError();
+}
+
 // G = Z^T A Z (+ shift) from A's lower triangle on the tensor cores; see the
 // file comment.  ws holds tc_workspace_bytes(p).  a_ready: the workspace
 // already holds the split of this A (planes, exponents, row maxima) made by a

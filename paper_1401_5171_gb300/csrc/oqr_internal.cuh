@@ -228,6 +228,12 @@ cudaError_t launch_tc_cross(const TcPlan& p, const double* X, long ldx, const do
                             const double* shift_ptr, void* ws, DevStatus* st, uint64_t limit_ns, int sms,
                             cudaStream_t s);
 
+// C = X^T Y (n1 x n2, leading dimension ldc) for X (K x n1) and Y (K x n2), FP64-accurate on the tensor
+// cores (the EMU64 slices); ws holds tc_xty_bytes(K, n1, n2) bytes.
+size_t tc_xty_bytes(int K, int n1, int n2);
+cudaError_t launch_tc_xty(int K, int n1, int n2, const double* X, long ldx, const double* Y, long ldy, double* C,
+                          long ldc, void* ws, DevStatus* st, uint64_t limit_ns, int sms, cudaStream_t s);
+
 // Euclidean Householder QR of a tall-skinny Z on a reduction tree (k_tsqr.cu):
 // Z = Y S with Y (m x n) orthonormal and S upper triangular with a positive
 // diagonal; the workspace holds tsqr_plan(m, n).doubles doubles.
@@ -244,13 +250,14 @@ cudaError_t launch_tsqr(const TsqrPlan& p, const double* Z, long ldz, double* Y,
 
 // Blocked Householder QR of a tall-skinny Z (k_bhqr.cu), the same contract as launch_tsqr: Z = Y S, Y
 // orthonormal, S upper triangular with a positive diagonal.  Panels of BH_B columns are factored column
-// by column over all SMs, blocked as I - V T V^T, the trailing columns and Y updated by FP64 GEMMs; the
-// workspace holds bhqr_plan(m, n, sms).doubles doubles.
+// by column over all SMs, blocked as I - V T V^T, the trailing columns and Y updated with the
+// products V^T X and V (T^T W) FP64-accurate on the tensor cores; the workspace holds
+// bhqr_plan(m, n, sms).doubles doubles.
 constexpr int BH_B = 32;
 struct BhqrPlan {
-    int m, n, panels, sms, splits_max, blocks_max;
+    int m, n, panels, sms, blocks_max;
     int smem_rows;  // rows per block that the shared-memory panel kernel can hold
-    size_t oX, oV, oT, oD, oW, oW2, oG, oBeta, oTau, oPart, oDpart, oSK, oBar, oXj;  // workspace offsets (doubles)
+    size_t oX, oV, oT, oD, oW, oW2, oG, oBeta, oTau, oPart, oDpart, oBar, oXj, oXT, oVt, oPt;  // offsets (doubles)
     size_t doubles;
 };
 BhqrPlan bhqr_plan(int m, int n, int sms);
