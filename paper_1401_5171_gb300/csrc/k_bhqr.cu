@@ -225,9 +225,9 @@ __global__ void __launch_bounds__(HH_THREADS) hh_panel_smem_kernel(int mk, int w
     if (!grid_barrier(bar, bar + 1, limit_ns, st, &ok_s)) return;
     for (int j = 0; j < w; ++j) {
         if (threadIdx.x < 32) {
+            const double x0 = __ldcg(xj + j);  // in flight with the partials below
             const double s2 = warp_sum_fixed(part, gridDim.x, lane);
             if (lane == 0) {
-                const double x0 = __ldcg(xj + j);
                 double b = x0, t = 0.0, sc = 0.0;
                 if (s2 > 0.0) {
                     b = -copysign(sqrt(fma(x0, x0, s2)), x0);
@@ -274,9 +274,25 @@ __global__ void __launch_bounds__(HH_THREADS) hh_panel_smem_kernel(int mk, int w
         }
         if (j + 1 == w) break;  // the same for every block
         if (!grid_barrier(bar, bar + 1, limit_ns, st, &ok_s)) return;
-        for (int c = j + 1 + warp; c < w; c += HH_THREADS / 32) {
-            const double x = warp_sum_fixed(dpart + (long)c * gridDim.x, gridDim.x, lane);
-            if (lane == 0) wv[c] = t * x;
+        {
+            // this warp's columns c = j+1+warp, +8, ... (at most BH_B / 8): every partial load in flight
+            // before the fixed-order sums
+            constexpr int CPW = BH_B / (HH_THREADS / 32);
+            double x[CPW];
+#pragma unroll
+            for (int q = 0; q < CPW; ++q) {
+                const int c = j + 1 + warp + q * (HH_THREADS / 32);
+                double a = 0.0;
+                if (c < w)
+                    for (int b = lane; b < (int)gridDim.x; b += 32) a += __ldcg(dpart + (long)c * gridDim.x + b);
+                x[q] = a;
+            }
+#pragma unroll
+            for (int q = 0; q < CPW; ++q) {
+                for (int o = 16; o > 0; o >>= 1) x[q] += __shfl_xor_sync(0xffffffffu, x[q], o);
+                const int c = j + 1 + warp + q * (HH_THREADS / 32);
+                if (lane == 0 && c < w) wv[c] = t * x[q];
+            }
         }
         __syncthreads();
         double a = 0.0;

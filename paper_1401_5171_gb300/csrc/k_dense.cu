@@ -264,21 +264,22 @@ __global__ void __launch_bounds__(TRSM_THREADS) trsm_kernel(int m, int n, int ro
 // R(0:jb, jb:jb+bw), formed elsewhere (NULL for the first block).  In place
 // when Q aliases Z.
 constexpr int TBW = 64;
-constexpr int TB_THREADS = 128;
+constexpr int TB_THREADS = 32;  // one warp of rows per CTA: ~1000 CTAs spread the FP64 work evenly over the SMs
+constexpr int TB_PACKED = TBW * (TBW + 1) / 2;
+// The upper triangle of the diagonal block, packed row by row: (c, k), k >= c, at c TBW - c (c - 1) / 2 + k - c.
+__host__ __device__ constexpr int tb_idx(int c, int k) { return c * TBW - c * (c - 1) / 2 + (k - c); }
 __global__ void __launch_bounds__(TB_THREADS) trsm_block_kernel(int m, int jb, int bw, const double* Z, long ldz,
                                                                 const double* __restrict__ U, long ldu,
                                                                 const double* __restrict__ R, long ldr, double* Q,
                                                                 long ldq, const DevStatus* st)
 {
-    __shared__ double D[TBW][TBW + 1];
+    __shared__ double D[TB_PACKED];
     __shared__ double dinv[TBW];
     if (*(volatile const int*)&st->code != 0) return;
-    for (int e = threadIdx.x; e < TBW * TBW; e += TB_THREADS) {
-        const int i = e % TBW, j = e / TBW;
-        D[i][j] = (i <= j && j < bw) ? R[(jb + i) + (long)(jb + j) * ldr] : 0.0;
-    }
-    __syncthreads();
-    if (threadIdx.x < bw) dinv[threadIdx.x] = 1.0 / D[threadIdx.x][threadIdx.x];
+    for (int c = 0; c < TBW; ++c)
+        for (int k = c + threadIdx.x; k < TBW; k += TB_THREADS)
+            D[tb_idx(c, k)] = k < bw ? R[(jb + c) + (long)(jb + k) * ldr] : 0.0;
+    for (int c = threadIdx.x; c < TBW; c += TB_THREADS) dinv[c] = c < bw ? 1.0 / R[(jb + c) + (long)(jb + c) * ldr] : 0.0;
     __syncthreads();
     const long i = (long)blockIdx.x * TB_THREADS + threadIdx.x;
     if (i >= m) return;
@@ -294,7 +295,7 @@ __global__ void __launch_bounds__(TB_THREADS) trsm_block_kernel(int m, int jb, i
             asm volatile("" ::: "memory");  // keeps only row c of D live: no hoisted loads, no spills
             b[c] *= dinv[c];
 #pragma unroll
-            for (int k = c + 1; k < TBW; ++k) b[k] -= D[c][k] * b[c];
+            for (int k = c + 1; k < TBW; ++k) b[k] -= D[tb_idx(c, k)] * b[c];
         }
     }
 #pragma unroll
