@@ -737,7 +737,7 @@ __device__ inline Item item_of(const TcArgs& a, int j)
 __device__ inline uint64_t smem_desc(uint32_t addr, int swizzle_bytes)
 {
     const uint64_t sbo = (uint64_t)(8 * swizzle_bytes) >> 4;  // 8 rows x swizzle width
-    const uint64_t layout = swizzle_bytes == 128 ? 2ull : 4ull;  // SWIZZLE_128B : SWIZZLE_64B
+    const uint64_t layout = swizzle_bytes == 128 ? 2ull : swizzle_bytes == 64 ? 4ull : 6ull;  // 128B, 64B, 32B
     return (uint64_t)((addr & 0x3FFFFu) >> 4) | (1ull << 16) | (sbo << 32) | (1ull << 46) | (layout << 61);
 }
 
@@ -1233,6 +1233,12 @@ __global__ void symmetrize_kernel(int n, const double* __restrict__ Cm, long ldc
 //
 // Warps: 0 TMA producer, 1 TMEM allocation + MMA issuer, 2..17 drain (four
 // warps per TMEM lane quarter, 16 columns each).
+//
+// Staging: k-steps of 32 (one 64-byte swizzled row of BF16 per tile row, two
+// MMAs per product), two stages.  The MMA issue bounds the kernel (measured:
+// the drain's work removed leaves the U product's time unchanged; the MMAs
+// removed halve it), and part of it is a cost per k-step: 16-long k-steps in
+// four stages of the same bytes took 8.32 ms against 7.22.
 constexpr int EMU_KS = 32;                          // k-step: one 64-byte swizzled row of BF16
 constexpr int EMU_N = 64;                           // UMMA N
 constexpr int EMU_S = 7;                            // slices per operand
@@ -1299,7 +1305,7 @@ __device__ __forceinline__ void emu_issue_level(uint32_t d, uint64_t desc0A, uin
     for (int s = 0; s <= L - 2; ++s) {
         const int t = L - 2 - s;
 #pragma unroll
-        for (int kk = 0; kk < 2; ++kk) {
+        for (int kk = 0; kk < EMU_KS / 16; ++kk) {  // one MMA (K = 16) per 32 bytes of the row
             const uint64_t ad = desc0A + (uint64_t)((s * EMU_A_TILE + kk * 32) >> 4);
             const uint64_t bd = desc0B + (uint64_t)((t * EMU_B_TILE + kk * 32) >> 4);
             umma_bf16(d, ad, bd, idesc, (first && s == 0 && kk == 0) ? 0u : 1u);
@@ -1412,7 +1418,7 @@ __global__ void __launch_bounds__(EMU_THREADS, 1)
                     }
                     tc_fence_after();
                     const uint32_t base = smem_u32(smem + stg * EMU_STAGE);
-                    const uint64_t dA = smem_desc(base, 64), dB = smem_desc(base + EMU_S * EMU_A_TILE, 64);
+                    const uint64_t dA = smem_desc(base, EMU_KS * 2), dB = smem_desc(base + EMU_S * EMU_A_TILE, EMU_KS * 2);
                     const uint32_t hi = tmem + 256u + (uint32_t)((chunk & 1) * 128);
                     if (cstart && chunk >= 2) {  // this parity's L6, L7+8 slots: read two chunks ago
                         if (!mbar_wait(&hi_empty[chunk & 1], (uint32_t)(((chunk - 2) >> 1) & 1), a.limit_ns)) {
@@ -2006,7 +2012,7 @@ TrsmLayout trsm_layout(int m, int n, void* ws)
     L.ldp = ((long)kmax + KCH_EMU - 1) / KCH_EMU * KCH_EMU;
     L.kch = (kmax + KCH_EMU - 1) / KCH_EMU;
     const int rt = (m + TM - 1) / TM;
-    const int pieces = (int)((L.ldp / EMU_KS + 63) / 64);
+    const int pieces = (int)((L.ldp + 2047) / 2048);  // 2048-long items
     L.Xp = reinterpret_cast<__nv_bfloat16*>(take((size_t)EMU_S * m * L.ldp * 2));
     L.Yp = reinterpret_cast<__nv_bfloat16*>(take((size_t)EMU_S * TRSM_BW * L.ldp * 2));
     L.eX = reinterpret_cast<int*>(take((size_t)L.kch * m * 4));
@@ -2429,7 +2435,7 @@ EncodeTiledFn3 encode3()
 }
 
 // Slice planes: dims {K (contiguous), rows, S}; box {box_k, box_rows, 1};
-// swizzle = box_k * 2 bytes (64 or 128), matching the UMMA K-major layout.
+// swizzle = box_k * 2 bytes (32, 64 or 128), matching the UMMA K-major layout.
 bool make_map_3d(CUtensorMap* map, const void* base, long kext, long rows, long ldp, size_t plane_bytes, int S,
                  int box_k, int box_rows, int elem_bytes)
 {
@@ -2439,7 +2445,9 @@ bool make_map_3d(CUtensorMap* map, const void* base, long kext, long rows, long 
     cuuint64_t strides[2] = {(cuuint64_t)ldp * elem_bytes, (cuuint64_t)plane_bytes};
     cuuint32_t box[3] = {(cuuint32_t)box_k, (cuuint32_t)box_rows, 1};
     cuuint32_t estr[3] = {1, 1, 1};
-    const CUtensorMapSwizzle sw = box_k * elem_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
+    const CUtensorMapSwizzle sw = box_k * elem_bytes == 128  ? CU_TENSOR_MAP_SWIZZLE_128B
+                                  : box_k * elem_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                                             : CU_TENSOR_MAP_SWIZZLE_32B;
     const CUtensorMapDataType dt = elem_bytes == 1 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     CUresult r = fn(map, dt, 3, const_cast<void*>(base), dims, strides, box, estr,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
