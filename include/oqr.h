@@ -86,13 +86,16 @@ typedef struct {
                                      the built-in heuristic [NULL] */
     const float* selector_params; /* OQR_BATCHED_SELECTOR: the trained network (device, oqr_mlp_param_count()
                                      FP32 values, the layout of oqr_mlp_forward) [NULL] */
-    double selector_tol;          /* OQR_BATCHED_SELECTOR: the largest ||Q^T A Q - I||_2 a checked result may
-                                     keep [1e-12] */
-    int selector_check;           /* OQR_BATCHED_SELECTOR: 0 = check the one-pass choices only, 1 = check every
-                                     tensor-core result [0] */
-    double* batch_orth;           /* optional device output (count doubles): ||Q_b^T A_b Q_b - I||_2 estimates
-                                     (power iteration on one more FP64-accurate Gram of Q_b; NaN where the mode
-                                     did not check the instance, +inf after a breakdown) [NULL] */
+    double selector_tol;          /* OQR_BATCHED_SELECTOR: the largest ||Q^T A Q - I||_F a one-pass (or
+                                     checked) result may keep [1e-12] */
+    int selector_check;           /* OQR_BATCHED_SELECTOR: 0 = check the one-pass results only (their check is
+                                     the Gram the second pass would factor), 1 = also every other tensor-core
+                                     result, with one more Gram [0] */
+    double* batch_orth;           /* optional device output (count doubles): the checks.  OQR_BATCHED_TC*:
+                                     ||Q_b^T A_b Q_b - I||_2 estimates (power iteration on one more FP64-accurate
+                                     Gram of Q_b; +inf after a breakdown); OQR_BATCHED_SELECTOR: ||Q_b^T A_b Q_b -
+                                     I||_F of the checked Gram (an upper bound of the 2-norm); NaN where the mode
+                                     did not check the instance [NULL] */
     int* batch_choice;            /* OQR_BATCHED_SELECTOR: optional device output (count ints), the option whose
                                      result each instance holds: 0 one pass, 1 two passes, 2 shifted three passes
                                      (all FP64-accurate on the tensor cores), 3 FP64 A-CholQR2 [NULL] */
@@ -372,21 +375,22 @@ oqr_status oqr_symm(oqr_ctx* ctx, int m, int k, const double* A, long lda, const
  *     G_0, breakdown, a sketched estimate of kappa(R_1) from an n x 2n Gaussian
  *     sketch, sizes) go through the MLP 16 -> 64 -> 64 -> 4 (opts->
  *     selector_params, BF16 inference), whose argmax says how the instance
- *     finishes: 0 with Q = Z R_1^{-1} (one pass), 1 with one more pass
- *     (A-CholQR2), 2 with a shifted first pass refactored from the same G_0
- *     and two more passes (shifted A-CholQR3), 3 with FP64 A-CholQR2.  The
- *     passes of options 0-2 run in the same packed waves as the first, reading
- *     the wave's one split of A.  One-pass results (all results when
- *     opts->selector_check = 1) are checked: ||Q^T A Q - I||_2 above
- *     opts->selector_tol, or a breakdown, sends the instance down the fallback
- *     chain; so does a two-pass result whose second pass factored a Gram
- *     Q_1^T A Q_1 more than 0.5 from I (read from that Gram, at no extra
- *     cost: within 0.5 the last pass leaves the orthogonality at rounding
- *     level).  The fallback chain: shifted A-CholQR3 on the tensor cores (checked), then FP64
- *     A-CholQR2 (accepted once it completes).  opts->batch_orth and
+ *     finishes: unshifted (options 0 and 1), 2 with a shifted first pass
+ *     refactored from the same G_0 and two more passes (shifted A-CholQR3),
+ *     3 with FP64 A-CholQR2.  Options 0 and 1 share the Gram of pass 1,
+ *     G_1 = Q_1^T A Q_1 with Q_1 = Z R_1^{-1}, which decides on the device:
+ *     ||G_1 - I||_F <= opts->selector_tol keeps Q_1 (one pass, checked);
+ *     <= 0.5 factors G_1 once more (A-CholQR2: within 0.5 of I the last pass
+ *     leaves the orthogonality at rounding level); larger, or a breakdown,
+ *     redoes the instance as shifted A-CholQR3 from the saved G_0 in the same
+ *     wave.  Every wave is one fixed sequence of launches over its packed
+ *     instances (each takes part in the Gram passes its route needs), reading
+ *     the wave's one split of A; no host round trip sits between the passes.
+ *     A breakdown, or the network's choice 3, ends with FP64 A-CholQR2 after
+ *     the waves (accepted once it completes).  opts->batch_orth and
  *     opts->batch_choice, when given, receive the checks and the option each
- *     result comes from.  This mode synchronizes the stream (the choices are
- *     read between the passes) and is not captured into a graph.
+ *     result comes from (2 for a shifted refactor).  This mode synchronizes
+ *     the stream once, after the waves.
  * Argument errors are returned; otherwise every mode but the selector returns
  * after enqueueing.
  */
