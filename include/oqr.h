@@ -230,7 +230,18 @@ oqr_status oqr_cgs2(oqr_ctx* ctx, int m, int n, const double* A, long lda, const
  *   product of the already solved columns with R's block column is formed
  *   FP64-accurately on the tensor cores (the OQR_FP64_TC slices), and the
  *   64 x 64 diagonal block is solved by FP64 row-wise substitution.  The
- *   factorizations use it in every pass whose Gram runs on the tensor cores.
+ *   factorizations use it in every pass whose Gram runs on the tensor cores,
+ *   except the last pass of a multi-pass one (oqr_trsm_last).
+ *   Uses the context's workspace; Q may alias Z.
+ * oqr_trsm_last: the solve of a multi-pass factorization's last tensor-core
+ *   pass, Q = Z / R, given the symmetric G = R^T R the factor came from (read
+ *   from its lower triangle).  When ||G - I||_F <= 0.5 (every eigenvalue of G
+ *   in [0.5, 1.5], so cond(R)^2 <= 3), R^{-1} is formed by FP64 back
+ *   substitution and Q = Z R^{-1} is one FP64-accurate tensor-core product;
+ *   otherwise it is oqr_trsm (FP64 row-wise substitution).  The choice is
+ *   taken on the device (no synchronization).  n <= 8192 (else
+ *   OQR_ERR_UNSUPPORTED; the factorizations then solve their last pass with
+ *   oqr_trsm_tc's method).
  *   Uses the context's workspace; Q may alias Z.
  * oqr_rprod: R = U S for upper triangular U, S (R must not alias U or S).
  * oqr_check: E = Q^T A Q - I (n x n, written in full when E != NULL), and
@@ -245,6 +256,8 @@ oqr_status oqr_trsm_tc(oqr_ctx* ctx, int m, int n, const double* Z, long ldz, co
                        double* Q, long ldq, void* stream);
 oqr_status oqr_trsm(oqr_ctx* ctx, int m, int n, const double* Z, long ldz, const double* R, long ldr,
                     double* Q, long ldq, void* stream);
+oqr_status oqr_trsm_last(oqr_ctx* ctx, int m, int n, const double* G, long ldg, const double* Z, long ldz,
+                         const double* R, long ldr, double* Q, long ldq, void* stream);
 oqr_status oqr_rprod(oqr_ctx* ctx, int n, const double* U, long ldu, const double* S, long lds, double* R,
                      long ldr, void* stream);
 oqr_status oqr_check(oqr_ctx* ctx, int m, int n, const double* A, long lda, const double* Q, long ldq,

@@ -185,10 +185,11 @@ constexpr int TNB = 32;
 
 __global__ void __launch_bounds__(TRSM_THREADS) trsm_kernel(int m, int n, int rows, const double* Z, long ldz,
                                                             const double* __restrict__ R, long ldr, double* Q,
-                                                            long ldq, const DevStatus* st)
+                                                            long ldq, const DevStatus* st, const int* gate,
+                                                            int want)
 {
     extern __shared__ double ts[];
-    if (*(volatile const int*)&st->code != 0) return;
+    if (*(volatile const int*)&st->code != 0 || gated_off(gate, want)) return;
     const int ldsm = n + 1;                         // padded row stride
     double* Zs = ts;                                // [rows][n+1]
     double* Rd = ts + (size_t)rows * ldsm;          // [TNB][TNB+1] diagonal block
@@ -271,11 +272,12 @@ __host__ __device__ constexpr int tb_idx(int c, int k) { return c * TBW - c * (c
 __global__ void __launch_bounds__(TB_THREADS) trsm_block_kernel(int m, int jb, int bw, const double* Z, long ldz,
                                                                 const double* __restrict__ U, long ldu,
                                                                 const double* __restrict__ R, long ldr, double* Q,
-                                                                long ldq, const DevStatus* st)
+                                                                long ldq, const DevStatus* st, const int* gate,
+                                                                int want)
 {
     __shared__ double D[TB_PACKED];
     __shared__ double dinv[TBW];
-    if (*(volatile const int*)&st->code != 0) return;
+    if (*(volatile const int*)&st->code != 0 || gated_off(gate, want)) return;
     for (int c = 0; c < TBW; ++c)
         for (int k = c + threadIdx.x; k < TBW; k += TB_THREADS)
             D[tb_idx(c, k)] = k < bw ? R[(jb + c) + (long)(jb + k) * ldr] : 0.0;
@@ -314,6 +316,107 @@ __global__ void rprod_kernel(int n, const double* __restrict__ U, long ldu, cons
     if (i <= j)
         for (int k = i; k <= j; ++k) s += U[i + (long)k * ldu] * S[k + (long)j * lds];
     R[i + (long)j * ldr] = s;
+}
+
+// D (cols x rows, leading dimension ldd) = S^T for S (rows x cols, leading dimension lds): 32 x 32 tiles.
+__global__ void transpose_kernel(int rows, int cols, const double* __restrict__ S, long lds, double* D, long ldd)
+{
+    __shared__ double t[32][33];
+    const long r0 = (long)blockIdx.x * 32, c0 = (long)blockIdx.y * 32;
+    {
+        const long r = r0 + threadIdx.x, c = c0 + threadIdx.y;  // coalesced along S's rows
+        t[threadIdx.y][threadIdx.x] = (r < rows && c < cols) ? S[r + c * lds] : 0.0;
+    }
+    __syncthreads();
+    const long c = c0 + threadIdx.x, r = r0 + threadIdx.y;  // coalesced along D's rows (S's columns)
+    if (r < rows && c < cols) D[c + r * ldd] = t[threadIdx.x][threadIdx.y];
+}
+
+// out[0] = ||G - I||_F for a symmetric G (n x n) read from its lower triangle (an off-diagonal element counts
+// twice), one block, a fixed-order sum; gate[0] = (out[0] <= tol).  Thread t takes rows i = t mod 128 (+ 128
+// k) and, of each row, the columns j <= i with j = t / 128 (mod 8): warps read along columns (coalesced).
+constexpr int GD_THREADS = 1024, GD_ROWS = 128, GD_PHASES = GD_THREADS / GD_ROWS;
+__global__ void __launch_bounds__(GD_THREADS) gram_defect_kernel(int n, const double* __restrict__ G, long ldg,
+                                                                 double* out, int* gate, double tol)
+{
+    __shared__ double red[GD_THREADS / 32];
+    const int t = threadIdx.x;
+    double a = 0.0;
+    for (int i = t % GD_ROWS; i < n; i += GD_ROWS) {
+#pragma unroll 4
+        for (int j = t / GD_ROWS; j <= i; j += GD_PHASES) {
+            const double v = G[i + (long)j * ldg] - (i == j ? 1.0 : 0.0);
+            a = fma(i == j ? v : 2.0 * v, v, a);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if ((t & 31) == 0) red[t >> 5] = a;
+    __syncthreads();
+    if (t < 32) {
+        double v = red[t];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (t == 0) {
+            const double f = sqrt(v);
+            out[0] = f;
+            gate[0] = f <= tol ? 1 : 0;
+        }
+    }
+}
+
+// X = R^{-1} for upper triangular R (n x n), one block per column j: x = R^{-1} e_j by column-oriented back
+// substitution, x_i = x_i / r_ii (as a product with the reciprocal), then x_t -= x_i r_ti for t < i; column
+// j costs j^2 / 2 FMAs and j block barriers, and the n columns run side by side.  Each thread keeps rows
+// t + TI_THREADS k (k < RPT) and loads their elements of R's columns TI_AHEAD steps before use, so a step
+// waits on a barrier, not on a load.  X's strict lower triangle is written with zeros.
+constexpr int TI_THREADS = 256, TI_AHEAD = 8;
+template <int RPT>
+__global__ void __launch_bounds__(TI_THREADS) trinv_upper_kernel(int n, const double* __restrict__ R, long ldr,
+                                                                 double* X, long ldx, const DevStatus* st)
+{
+    extern __shared__ double ti_sh[];  // x (n), then the diagonal's reciprocals (n)
+    if (*(volatile const int*)&st->code != 0) return;
+    const int j = blockIdx.x;
+    double* x = ti_sh;
+    double* dinv = ti_sh + n;
+    for (int t = threadIdx.x; t <= j; t += TI_THREADS) {
+        x[t] = t == j ? 1.0 : 0.0;
+        dinv[t] = 1.0 / R[t + (long)t * ldr];
+    }
+    // ring[u][k]: R(row_k, i0 - u) for the TI_AHEAD steps from i0 down
+    double ring[TI_AHEAD][RPT], next[TI_AHEAD][RPT];
+    auto load = [&](double (&b)[TI_AHEAD][RPT], int i0) {
+#pragma unroll
+        for (int u = 0; u < TI_AHEAD; ++u)
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) {
+                const int row = threadIdx.x + k * TI_THREADS, col = i0 - u;
+                b[u][k] = (col >= 0 && row < col) ? R[row + (long)col * ldr] : 0.0;
+            }
+    };
+    load(ring, j);
+    __syncthreads();
+    for (int i0 = j; i0 >= 0; i0 -= TI_AHEAD) {
+        load(next, i0 - TI_AHEAD);
+#pragma unroll
+        for (int u = 0; u < TI_AHEAD; ++u) {
+            const int i = i0 - u;
+            if (i < 0) break;  // uniform over the block
+            const double q = x[i] * dinv[i];
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) {
+                const int row = threadIdx.x + k * TI_THREADS;
+                if (row < i) x[row] = fma(-q, ring[u][k], x[row]);
+            }
+            __syncthreads();                 // every read of x[i] is done; x[0..i-1] are updated
+            if (threadIdx.x == 0) x[i] = q;  // x[i] is read by no later step
+        }
+#pragma unroll
+        for (int u = 0; u < TI_AHEAD; ++u)
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) ring[u][k] = next[u][k];
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < n; t += TI_THREADS) X[t + (long)j * ldx] = t <= j ? x[t] : 0.0;
 }
 
 __global__ void copy_upper_kernel(int n, const double* __restrict__ S, long lds, double* D, long ldd)
@@ -680,17 +783,18 @@ cudaError_t launch_potrf(int n, const double* G, long ldg, double* R, long ldr, 
 }
 
 cudaError_t launch_trsm_block(int m, int jb, int bw, const double* Z, long ldz, const double* U, long ldu,
-                              const double* R, long ldr, double* Q, long ldq, DevStatus* st, cudaStream_t s)
+                              const double* R, long ldr, double* Q, long ldq, DevStatus* st, cudaStream_t s,
+                              const int* gate, int want)
 {
     if (m <= 0 || bw <= 0) return cudaSuccess;
     if (bw > TBW) return cudaErrorInvalidValue;
     trsm_block_kernel<<<(unsigned)((m + TB_THREADS - 1) / TB_THREADS), TB_THREADS, 0, s>>>(m, jb, bw, Z, ldz, U, ldu, R,
-                                                                                          ldr, Q, ldq, st);
+                                                                                          ldr, Q, ldq, st, gate, want);
     return cudaGetLastError();
 }
 
 cudaError_t launch_trsm(int m, int n, const double* Z, long ldz, const double* R, long ldr, double* Q, long ldq,
-                        DevStatus* st, cudaStream_t s)
+                        DevStatus* st, cudaStream_t s, const int* gate, int want)
 {
     int rows = 64;
     while (rows > 8 && (size_t)rows * (n + 1) * sizeof(double) > 160 * 1024) rows /= 2;
@@ -698,7 +802,7 @@ cudaError_t launch_trsm(int m, int n, const double* Z, long ldz, const double* R
     if (smem > 220 * 1024) return cudaErrorInvalidValue;
     cudaFuncSetAttribute(trsm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const unsigned blocks = (unsigned)((m + rows - 1) / rows);
-    trsm_kernel<<<blocks, TRSM_THREADS, smem, s>>>(m, n, rows, Z, ldz, R, ldr, Q, ldq, st);
+    trsm_kernel<<<blocks, TRSM_THREADS, smem, s>>>(m, n, rows, Z, ldz, R, ldr, Q, ldq, st, gate, want);
     return cudaGetLastError();
 }
 
@@ -708,6 +812,43 @@ cudaError_t launch_rprod(int n, const double* U, long ldu, const double* S, long
     const long total = (long)n * n;
     rprod_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(n, U, ldu, S, lds, R, ldr);
     return cudaGetLastError();
+}
+
+cudaError_t launch_transpose(int rows, int cols, const double* S, long lds, double* D, long ldd, cudaStream_t s)
+{
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    transpose_kernel<<<dim3((unsigned)((rows + 31) / 32), (unsigned)((cols + 31) / 32)), dim3(32, 32), 0, s>>>(
+        rows, cols, S, lds, D, ldd);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gram_defect(int n, const double* G, long ldg, double* out, int* gate, double gate_tol,
+                               cudaStream_t s)
+{
+    gram_defect_kernel<<<1, GD_THREADS, 0, s>>>(n, G, ldg, out, gate, gate_tol);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_trinv(int n, const double* R, long ldr, double* X, long ldx, const DevStatus* st, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    const size_t smem = (size_t)2 * n * sizeof(double);
+    if (n > TRINV_MAX_N) return cudaErrorInvalidValue;
+    auto run = [&](auto kernel) {
+        if (smem > 48 * 1024) {
+            const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        kernel<<<(unsigned)n, TI_THREADS, smem, s>>>(n, R, ldr, X, ldx, st);
+        return cudaGetLastError();
+    };
+    const int rpt = (n + TI_THREADS - 1) / TI_THREADS;
+    if (rpt <= 1) return run(trinv_upper_kernel<1>);
+    if (rpt <= 2) return run(trinv_upper_kernel<2>);
+    if (rpt <= 4) return run(trinv_upper_kernel<4>);
+    if (rpt <= 8) return run(trinv_upper_kernel<8>);
+    if (rpt <= 16) return run(trinv_upper_kernel<16>);
+    return run(trinv_upper_kernel<32>);
 }
 
 cudaError_t launch_copy_upper(int n, const double* S, long lds, double* D, long ldd, cudaStream_t s)

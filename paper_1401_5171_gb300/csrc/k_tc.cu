@@ -420,8 +420,10 @@ __device__ __forceinline__ void split_lower_tile(int m, int K, const double* __r
 template <int MODE, bool TRI, int CW>
 __global__ void __launch_bounds__(256, 4) split_lower_kernel(int m, int K, const double* __restrict__ A, long lda, int S,
                                                           __nv_bfloat16* planes, long ldp, size_t plane,
-                                                          int* eA, int* emax, int kc0 = 0)
+                                                          int* eA, int* emax, int kc0 = 0,
+                                                          const int* gate = nullptr, int want = 0)
 {
+    if (gated_off(gate, want)) return;
     split_lower_tile<MODE, TRI, CW>(m, K, A, lda, S, planes, ldp, plane, eA, emax, kc0 + blockIdx.x, blockIdx.y, 0,
                                     m);
 }
@@ -520,8 +522,9 @@ __device__ __forceinline__ void split_tall_column(int K, const double* __restric
 template <int MODE, int CW>
 __global__ void __launch_bounds__(256) split_tall_kernel(int K, int C, const double* __restrict__ X, long ldx, int S,
                                                          __nv_bfloat16* planes, long ldp, size_t plane, int* eX,
-                                                         int* xmax)
+                                                         int* xmax, const int* gate = nullptr, int want = 0)
 {
+    if (gated_off(gate, want)) return;
     const long c = (long)blockIdx.y * 8 + (threadIdx.x >> 5);
     if (c >= C) return;
     split_tall_column<MODE, CW>(K, X, ldx, c, S, planes, ldp, plane, eX, xmax, blockIdx.x, 0, C);
@@ -576,7 +579,8 @@ struct TcArgs {
     int rt;               // row tiles (one instance)
     int nitems;
     const int* cum;       // one instance: rt + 1 item offsets; a batch: the instances' prefixes
-    double* slots;        // nitems x 128 x N, row-major per slot (FP32 slots use the first half)
+    double* slots;        // nitems x 128 x N, column-major per slot: (r, c) at c * 128 + r (FP32 slots use the
+                          // first half); a warp's 32 rows of one column are one coalesced store or load
     const int* eA;        // [chunks][rowsA]
     const int* eB;        // [chunks][colsB]
     const int* emaxA;     // [rowsA]
@@ -591,6 +595,8 @@ struct TcArgs {
     const int* live;      // a batch, or NULL: the wave's Gram pass counts; instances with live[wi] <= pass sit
     int pass;             // this launch out (their items are not in list, their outputs are not written)
     const int* list;      // NULL: items 0..nitems-1; else list[0] items, list[1..]: their indices
+    const int* gate;      // NULL, or the launch does nothing unless *gate == gate_want
+    int gate_want;
 };
 
 __device__ inline int item_total(const TcArgs& a) { return a.list ? a.list[0] : a.nitems; }
@@ -660,6 +666,7 @@ __device__ __host__ inline int pieces_of(const TcArgs& a, int I) { return pieces
 constexpr int PREFIX_THREADS = 256;
 __global__ void __launch_bounds__(PREFIX_THREADS) item_prefix_kernel(TcArgs a, int* cum)
 {
+    if (gated_off(a.gate, a.gate_want)) return;
     __shared__ int wsum[PREFIX_THREADS / 32];
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     const int run = (a.rt + PREFIX_THREADS - 1) / PREFIX_THREADS;
@@ -1003,7 +1010,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         for (int jj = blockIdx.x; jj < nit && !stop; jj += gridDim.x) {
             const int j = item_index(a, jj);
             const Item item = item_of(a, j);
-            double* slot = a.slots + (size_t)j * TM * N + (size_t)r * N + half * NH;  // MODE 0: FP64 slots
+            double* slot = a.slots + (size_t)j * TM * N + (size_t)(half * NH) * TM + r;  // MODE 0: FP64 slots
             float H[CHUNKED ? NH : 1];
 #pragma unroll
             for (int c = 0; c < (CHUNKED ? NH : 1); ++c) H[c] = 0.f;
@@ -1075,7 +1082,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         float v[32];
                         tmem_ld32(buf + (uint32_t)(h * 32), v);
 #pragma unroll
-                        for (int c = 0; c < 32; ++c) slot[h * 32 + c] = (double)v[c];
+                        for (int c = 0; c < 32; ++c) slot[(size_t)(h * 32 + c) * TM] = (double)v[c];
                     }
                 }
                 tc_fence_before();
@@ -1086,10 +1093,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             if constexpr (CHUNKED) {
                 // FP32 slots relative to 2^(emax_row + emax_col): the reduce sums the pieces and scales
                 // once per output element (no FP64 work here)
-                float* fslot = reinterpret_cast<float*>(a.slots) + (size_t)j * TM * N + (size_t)r * N + half * NH;
+                float* fslot = reinterpret_cast<float*>(a.slots) + (size_t)j * TM * N + (size_t)(half * NH) * TM + r;
 #pragma unroll
-                for (int c = 0; c < NH; c += 4)
-                    *reinterpret_cast<float4*>(fslot + c) = make_float4(H[c], H[c + 1], H[c + 2], H[c + 3]);
+                for (int c = 0; c < NH; ++c) fslot[(size_t)c * TM] = H[c];
             }
         }
     }
@@ -1122,7 +1128,7 @@ __device__ inline double f32_scaled_to_f64(float x, int k)
 template <int N>
 __global__ void slot_reduce_kernel(TcArgs a, double* out, long ldo, const DevStatus* st)
 {
-    if (*(volatile const int*)&st->code != 0) return;
+    if (*(volatile const int*)&st->code != 0 || gated_off(a.gate, a.gate_want)) return;
     const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (long)a.rowsA * a.colsB) return;
     const int col = (int)(e / a.rowsA), row = (int)(e % a.rowsA);
@@ -1131,7 +1137,7 @@ __global__ void slot_reduce_kernel(TcArgs a, double* out, long ldo, const DevSta
     double s = 0.0;
     for (int p = 0; p < np; ++p) {
         const int j = a.cum[I] + p * a.cc + c;
-        s += a.slots[(size_t)j * TM * N + (size_t)(row % TM) * N + (col % N)];
+        s += a.slots[(size_t)j * TM * N + (size_t)(col % N) * TM + (row % TM)];
     }
     out[row + (long)col * ldo] = s;
 }
@@ -1151,7 +1157,7 @@ __global__ void slot_reduce_f32_kernel(TcArgs a, double* out, long ldo, const De
     float s = 0.0f;
     for (int p = 0; p < np; ++p) {
         const int j = a.cum[I] + p * a.cc + c;
-        s += slots[(size_t)j * TM * N + (size_t)(row % TM) * N + (col % N)];
+        s += slots[(size_t)j * TM * N + (size_t)(col % N) * TM + (row % TM)];
     }
     const int er = a.emaxA[row], ec = a.emaxB[col];
     out[row + (long)col * ldo] = (er == EXP_NONE || ec == EXP_NONE) ? 0.0 : f32_scaled_to_f64(s, er + ec);
@@ -1174,7 +1180,7 @@ __device__ inline void slot_reduce_block(const TcArgs& a, int code)
         float s = 0.0f;
         for (int p = 0; p < np; ++p) {
             const int j = I.item0 + cum[T] + p * I.cc + c;
-            s += slots[(size_t)j * TM * N + (size_t)(row % TM) * N + (col % N)];
+            s += slots[(size_t)j * TM * N + (size_t)(col % N) * TM + (row % TM)];
         }
         const int er = a.emaxA[I.roff + row], ec = a.emaxB[I.coff + col];
         r = (er == EXP_NONE || ec == EXP_NONE) ? 0.0 : f32_scaled_to_f64(s, er + ec);
@@ -1182,7 +1188,7 @@ __device__ inline void slot_reduce_block(const TcArgs& a, int code)
         double s = 0.0;
         for (int p = 0; p < np; ++p) {
             const int j = I.item0 + cum[T] + p * I.cc + c;
-            s += a.slots[(size_t)j * TM * N + (size_t)(row % TM) * N + (col % N)];
+            s += a.slots[(size_t)j * TM * N + (size_t)(col % N) * TM + (row % TM)];
         }
         r = s;
     }
@@ -1316,6 +1322,7 @@ __device__ __forceinline__ void emu_issue_level(uint32_t d, uint64_t desc0A, uin
 __global__ void __launch_bounds__(EMU_THREADS, 1)
     emu_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, TcArgs a)
 {
+    if (gated_off(a.gate, a.gate_want)) return;  // uniform over the grid, before any barrier or TMEM
     extern __shared__ __align__(1024) unsigned char emu_smem_raw[];
     unsigned char* smem =
         reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(emu_smem_raw) + 1023) & ~uintptr_t(1023));
@@ -1568,7 +1575,7 @@ __global__ void __launch_bounds__(EMU_THREADS, 1)
             if (stop) break;
             // (H + L) 2^(emax_row + emax_col) into this item's FP64 slot: H and L become scaled doubles
             // by integer operations, and one FP64 add (exact: H and L do not overlap) joins them
-            double* slot = a.slots + (size_t)j * TM * EMU_N + (size_t)r * EMU_N + g * EMU_CPT;
+            double* slot = a.slots + (size_t)j * TM * EMU_N + (size_t)(g * EMU_CPT) * TM + r;
 #pragma unroll
             for (int c = 0; c < EMU_CPT; ++c) {
                 const int col = item.c * EMU_N + g * EMU_CPT + c;  // column within the instance
@@ -1579,7 +1586,7 @@ __global__ void __launch_bounds__(EMU_THREADS, 1)
                     const float hc = (c & 1) ? H[c / 2].y : H[c / 2].x, lc = (c & 1) ? L[c / 2].y : L[c / 2].x;
                     out = f32_scaled_to_f64(hc, k) + f32_scaled_to_f64(lc, k);
                 }
-                slot[c] = out;
+                slot[(size_t)c * TM] = out;
             }
         }
     }
@@ -1897,7 +1904,8 @@ XtyLayout xty_layout(int K, int n1, int n2, void* ws)
 size_t tc_xty_bytes(int K, int n1, int n2) { return xty_layout(K, n1, n2, nullptr).bytes; }
 
 cudaError_t launch_tc_xty(int K, int n1, int n2, const double* X, long ldx, const double* Y, long ldy, double* C,
-                          long ldc, void* ws, DevStatus* st, uint64_t limit_ns, int sms, cudaStream_t s)
+                          long ldc, void* ws, DevStatus* st, uint64_t limit_ns, int sms, cudaStream_t s,
+                          const int* gate, int want)
 {
     if (K <= 0 || n1 <= 0 || n2 <= 0) return cudaSuccess;
     const XtyLayout L = xty_layout(K, n1, n2, ws);
@@ -1907,10 +1915,12 @@ cudaError_t launch_tc_xty(int K, int n1, int n2, const double* X, long ldx, cons
     fill_int_kernel<<<(n1 + 255) / 256, 256, 0, s>>>(L.mX, n1, EXP_NONE);
     fill_int_kernel<<<(n2 + 255) / 256, 256, 0, s>>>(L.mY, n2, EXP_NONE);
     split_tall_kernel<1, KCH_EMU><<<dim3(kch, (n1 + 7) / 8), 256, 0, s>>>(K, n1, X, ldx, EMU_S, L.Xp, ldp, planeX,
-                                                                          L.eX, L.mX);
+                                                                          L.eX, L.mX, gate, want);
     split_tall_kernel<1, KCH_EMU><<<dim3(kch, (n2 + 7) / 8), 256, 0, s>>>(K, n2, Y, ldy, EMU_S, L.Yp, ldp, planeY,
-                                                                          L.eY, L.mY);
+                                                                          L.eY, L.mY, gate, want);
     TcArgs a{};
+    a.gate = gate;
+    a.gate_want = want;
     a.rowsA = n1;
     a.colsB = n2;
     a.K = K;
@@ -2030,7 +2040,8 @@ TrsmLayout trsm_layout(int m, int n, void* ws)
 size_t trsm_tc_workspace_bytes(int m, int n) { return trsm_layout(m, n, nullptr).bytes; }
 
 cudaError_t launch_trsm_tc(int m, int n, const double* Z, long ldz, const double* R, long ldr, double* Q, long ldq,
-                           void* ws, DevStatus* st, uint64_t limit_ns, int sms, cudaStream_t s)
+                           void* ws, DevStatus* st, uint64_t limit_ns, int sms, cudaStream_t s, const int* gate,
+                           int want)
 {
     if (m <= 0 || n <= 0) return cudaSuccess;
     const TrsmLayout L = trsm_layout(m, n, ws);
@@ -2047,10 +2058,13 @@ cudaError_t launch_trsm_tc(int m, int n, const double* Z, long ldz, const double
             fill_int_kernel<<<1, TRSM_BW, 0, s>>>(L.mY, bw, EXP_NONE);
             const size_t planeX = (size_t)m * L.ldp, planeY = (size_t)TRSM_BW * L.ldp;
             split_lower_kernel<1, false, KCH_EMU><<<dim3(kch, (m + 15) / 16), 256, 0, s>>>(
-                m, K, Q, ldq, EMU_S, L.Xp, L.ldp, planeX, L.eX, L.mX);
+                m, K, Q, ldq, EMU_S, L.Xp, L.ldp, planeX, L.eX, L.mX, 0, gate, want);
             split_tall_kernel<1, KCH_EMU><<<dim3(kch, (bw + 7) / 8), 256, 0, s>>>(K, bw, R + (long)jb * ldr, ldr, EMU_S,
-                                                                                  L.Yp, L.ldp, planeY, L.eY, L.mY);
+                                                                                  L.Yp, L.ldp, planeY, L.eY, L.mY,
+                                                                                  gate, want);
             TcArgs a = make_args(p, m, bw, K, 0, EMU_N);
+            a.gate = gate;
+            a.gate_want = want;
             a.cum = L.cum;
             a.slots = L.slots;
             a.eA = L.eX;
@@ -2064,7 +2078,8 @@ cudaError_t launch_trsm_tc(int m, int n, const double* Z, long ldz, const double
             slot_reduce_kernel<EMU_N><<<(unsigned)(((long)m * bw + 255) / 256), 256, 0, s>>>(a, L.U, m, st);
             U = L.U;
         }
-        if ((e = launch_trsm_block(m, jb, bw, Z, ldz, U, m, R, ldr, Q, ldq, st, s)) != cudaSuccess) return e;
+        if ((e = launch_trsm_block(m, jb, bw, Z, ldz, U, m, R, ldr, Q, ldq, st, s, gate, want)) != cudaSuccess)
+            return e;
     }
     return cudaGetLastError();
 }

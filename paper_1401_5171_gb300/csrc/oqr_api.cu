@@ -113,6 +113,46 @@ struct Carve {
     }
 };
 
+// The last pass's solve (see launch_last_solve): R^{-1} (n x n), ||G - I||_F, the gate, X^T (n x m) and
+// the tensor-core product's workspace.
+struct LastSolve {
+    double *Rinv = nullptr, *defect = nullptr, *Xt = nullptr;
+    int* gate = nullptr;
+    void* xtyws = nullptr;
+};
+template <class C>
+void carve_last(C& c, int m, int n, bool on, LastSolve* L)
+{
+    const size_t nn = (size_t)n * n, nm = (size_t)n * m;
+    L->Rinv = c.template take<double>(on ? nn : 0);
+    L->defect = c.template take<double>(on ? 1 : 0);
+    L->Xt = c.template take<double>(on ? nm : 0);
+    L->gate = c.template take<int>(on ? 1 : 0);
+    L->xtyws = c.template take<char>(on ? tc_xty_bytes(n, m, n) : 0);
+}
+
+// The solve Q = X R^{-1} of a pass whose Gram G (= R^T R) is close to I, as the last pass of a multi-pass
+// factorization is.  When ||G - I||_F <= 0.5 every eigenvalue of G lies in [0.5, 1.5], so kappa(R)^2 <= 3:
+// then X times R^{-1} (FP64 back substitution) is one FP64-accurate tensor-core product, as accurate as
+// the substitution (the explicit inverse's error grows with kappa(R)^2) and with the residual X - Q R
+// within a few units of rounding.  Otherwise (a pass that starts far from orthogonality) FP64 row-wise
+// substitution runs: one launch, so that the gated-off alternative costs one empty launch.  Both are
+// enqueued; the gate written by the defect kernel makes the other's launches return at once, so the host
+// never waits.  Q may alias X.
+cudaError_t launch_last_solve(oqr_ctx* ctx, int m, int n, const double* G, long ldg, const double* X, long ldx,
+                              const double* R, long ldr, double* Q, long ldq, const LastSolve& L, uint64_t limit,
+                              cudaStream_t s)
+{
+    cudaError_t e;
+    if ((e = launch_gram_defect(n, G, ldg, L.defect, L.gate, 0.5, s)) != cudaSuccess) return e;
+    if ((e = launch_trinv(n, R, ldr, L.Rinv, n, ctx->st, s)) != cudaSuccess) return e;
+    if ((e = launch_transpose(m, n, X, ldx, L.Xt, n, s)) != cudaSuccess) return e;  // X^T, n x m
+    if ((e = launch_tc_xty(n, m, n, L.Xt, n, L.Rinv, n, Q, ldq, L.xtyws, ctx->st, limit, ctx->sm_count, s, L.gate,
+                           1)) != cudaSuccess)
+        return e;
+    return launch_trsm(m, n, X, ldx, R, ldr, Q, ldq, ctx->st, s, L.gate, 0);
+}
+
 // Workspace of the normal-equation family: Gram partials, G (+ check work),
 // three n x n triangles, shift scratch.
 template <class C>
@@ -336,6 +376,7 @@ struct NePlan {
     int sa = 0;        // planes of A kept for the EMU64-family passes (7 with any FP64_TC, else 0)
     size_t tcb = 0;    // tensor-core Gram region
     size_t trb = 0;    // blocked-TRSM region
+    bool last = false;  // the last pass solves with launch_last_solve (a tensor-core pass after another pass)
     int prec_of(int p) const { return p == passes - 1 ? prec_final : (p == 0 ? prec_first : prec_mid); }
 };
 
@@ -361,6 +402,7 @@ oqr_status ne_plan(const oqr_opts& o, int forced_passes, int m, int n, NePlan* P
     // passes whose Gram runs on the tensor cores also solve Q = X / R with tensor-core products
     const bool any_tc = P->prec_first != OQR_FP64 || P->prec_mid != OQR_FP64 || P->prec_final != OQR_FP64;
     P->trb = any_tc ? trsm_tc_workspace_bytes(m, n) : 0;
+    P->last = P->passes > 1 && P->prec_final != OQR_FP64 && n <= TRINV_MAX_N;
     return OQR_OK;
 }
 
@@ -368,6 +410,7 @@ struct NeBuffers {
     double *partials, *G, *work, *R1, *R2, *R3, *scratch;
     void *tcws, *trws;
     double *U, *C;  // tridiagonal A: U = M X (m x n) and C = X^T U (n x n)
+    LastSolve last;  // the last pass's solve (a tensor-core last pass after another pass)
 };
 // base == nullptr: offsets only; returns the bytes.
 size_t ne_carve(void* base, const GramPlan& gp, const NePlan& P, NeBuffers* B)
@@ -378,6 +421,7 @@ size_t ne_carve(void* base, const GramPlan& gp, const NePlan& P, NeBuffers* B)
     B->trws = c.take<char>(P.trb);
     B->U = c.take<double>(P.tri ? (size_t)gp.m * gp.n : 0);
     B->C = c.take<double>(P.tri ? (size_t)gp.n * gp.n : 0);
+    carve_last(c, gp.m, gp.n, P.last, &B->last);
     return c.off;
 }
 
@@ -452,10 +496,13 @@ oqr_status normal_equation(oqr_ctx* ctx, int m, int n, const AOp& op, const doub
         if (p == 0 && trace_shift)  // u of the first pass's products: 2^-16 (BF16X3, TC2) or 2^-4 (E4M3)
             OQR_TRY(launch_trace_shift(n, G, n, o.shift_c, prec == OQR_FP8 ? 0.0625 : 1.52587890625e-05, ctx->st, s));
         OQR_TRY(launch_potrf(n, G, n, Rp, ldrp, nullptr, ctx->st, s));
-        if (prec != OQR_FP64)
+        if (P.last && p == passes - 1) {
+            OQR_TRY(launch_last_solve(ctx, m, n, G, n, X, ldx, Rp, ldrp, Q, ldq, B.last, limit, s));
+        } else if (prec != OQR_FP64) {
             OQR_TRY(launch_trsm_tc(m, n, X, ldx, Rp, ldrp, Q, ldq, trws, ctx->st, limit, ctx->sm_count, s));
-        else
+        } else {
             OQR_TRY(launch_trsm(m, n, X, ldx, Rp, ldrp, Q, ldq, ctx->st, s));
+        }
         if (passes > 1) {
             if (p == 0) {
                 OQR_TRY(launch_copy_upper(n, R1, n, R2, n, s));
@@ -1766,6 +1813,26 @@ oqr_status oqr_trsm_tc(oqr_ctx* ctx, int m, int n, const double* Z, long ldz, co
     if (v != OQR_OK) return v;
     if ((v = reset_status(ctx, s)) != OQR_OK) return v;
     OQR_TRY(launch_trsm_tc(m, n, Z, ldz, R, ldr, Q, ldq, ctx->ws, ctx->st, 4000000000ull, ctx->sm_count, s));
+    return OQR_OK;
+}
+
+oqr_status oqr_trsm_last(oqr_ctx* ctx, int m, int n, const double* G, long ldg, const double* Z, long ldz,
+                         const double* R, long ldr, double* Q, long ldq, void* stream)
+{
+    if (!ctx || m < 1 || n < 1 || bad_matrix(G, ldg, n, n) || bad_matrix(Z, ldz, m, n) || bad_matrix(R, ldr, n, n) ||
+        bad_matrix(Q, ldq, m, n))
+        return OQR_ERR_INVALID_ARG;
+    if (n > TRINV_MAX_N) return OQR_ERR_UNSUPPORTED;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    LastSolve L;
+    Carve sz(nullptr);
+    carve_last(sz, m, n, true, &L);
+    oqr_status v = ensure_ws(ctx, sz.off);
+    if (v != OQR_OK) return v;
+    Carve c(ctx->ws);
+    carve_last(c, m, n, true, &L);
+    if ((v = reset_status(ctx, s)) != OQR_OK) return v;
+    OQR_TRY(launch_last_solve(ctx, m, n, G, ldg, Z, ldz, R, ldr, Q, ldq, L, 4000000000ull, s));
     return OQR_OK;
 }
 

@@ -34,6 +34,13 @@ static_assert(sizeof(DevStatus) == 96, "status layout");
 enum KernelTag { TAG_GRAM = 1, TAG_POTRF = 2, TAG_TRSM = 3, TAG_GEMM = 4, TAG_CHECK = 5, TAG_MIXED = 6,
                  TAG_BATCH = 7, TAG_DIAG = 8 };
 
+// A device-side branch between two enqueued alternatives: a gated launch does nothing (every block returns
+// at once) unless *gate == want; a NULL gate always runs.
+__device__ __forceinline__ bool gated_off(const int* gate, int want)
+{
+    return gate != nullptr && *(volatile const int*)gate != want;
+}
+
 __device__ inline void raise_status(DevStatus* st, int code, int info, int where)
 {
     if (atomicCAS(&st->code, 0, code) == 0) {
@@ -166,13 +173,22 @@ cudaError_t launch_gram_reduce(const GramPlan& p, const double* partials, double
 cudaError_t launch_potrf(int n, const double* G, long ldg, double* R, long ldr, const double* shift_ptr,
                          DevStatus* st, cudaStream_t s);
 cudaError_t launch_trsm(int m, int n, const double* Z, long ldz, const double* R, long ldr, double* Q, long ldq,
-                        DevStatus* st, cudaStream_t s);
+                        DevStatus* st, cudaStream_t s, const int* gate = nullptr, int want = 0);
 // One 64-column block of the blocked TRSM: Q(:, jb:jb+bw) = (Z(:, jb:jb+bw) - U) R_bb^{-1}.
 cudaError_t launch_trsm_block(int m, int jb, int bw, const double* Z, long ldz, const double* U, long ldu,
-                              const double* R, long ldr, double* Q, long ldq, DevStatus* st, cudaStream_t s);
+                              const double* R, long ldr, double* Q, long ldq, DevStatus* st, cudaStream_t s,
+                              const int* gate = nullptr, int want = 0);
 cudaError_t launch_rprod(int n, const double* U, long ldu, const double* S, long lds, double* R, long ldr,
                          cudaStream_t s);
 cudaError_t launch_copy_upper(int n, const double* S, long lds, double* D, long ldd, cudaStream_t s);
+// D (cols x rows) = S^T (S rows x cols).
+cudaError_t launch_transpose(int rows, int cols, const double* S, long lds, double* D, long ldd, cudaStream_t s);
+// X = R^{-1} (upper triangular, n x n, n <= TRINV_MAX_N), FP64 column-oriented back substitution.
+constexpr int TRINV_MAX_N = 8192;
+cudaError_t launch_trinv(int n, const double* R, long ldr, double* X, long ldx, const DevStatus* st, cudaStream_t s);
+// gate[0] = 1 if ||G - I||_F <= gate_tol, else 0 (also for a NaN).
+cudaError_t launch_gram_defect(int n, const double* G, long ldg, double* out, int* gate, double gate_tol,
+                               cudaStream_t s);
 // Shift for the shifted pass: s = c * u * (m n + n (n+1)) * ||A||_F * ||Z||_F^2.
 cudaError_t launch_norms_and_shift(int m, int n, const double* A, long lda, const double* Z, long ldz,
                                    double c, double u, double* scratch, int scratch_len, DevStatus* st,
@@ -231,8 +247,10 @@ cudaError_t launch_tc_cross(const TcPlan& p, const double* X, long ldx, const do
 // C = X^T Y (n1 x n2, leading dimension ldc) for X (K x n1) and Y (K x n2), FP64-accurate on the tensor
 // cores (the EMU64 slices); ws holds tc_xty_bytes(K, n1, n2) bytes.
 size_t tc_xty_bytes(int K, int n1, int n2);
+// gate/want: see gated_off (every launch of the product is gated).
 cudaError_t launch_tc_xty(int K, int n1, int n2, const double* X, long ldx, const double* Y, long ldy, double* C,
-                          long ldc, void* ws, DevStatus* st, uint64_t limit_ns, int sms, cudaStream_t s);
+                          long ldc, void* ws, DevStatus* st, uint64_t limit_ns, int sms, cudaStream_t s,
+                          const int* gate = nullptr, int want = 0);
 
 // Euclidean Householder QR of a tall-skinny Z on a reduction tree (k_tsqr.cu):
 // Z = Y S with Y (m x n) orthonormal and S upper triangular with a positive
@@ -281,7 +299,8 @@ cudaError_t launch_sym_plus_transpose(int n, const double* C, long ldc, double* 
 // (k_tc.cu).  ws holds trsm_tc_workspace_bytes(m, n).
 size_t trsm_tc_workspace_bytes(int m, int n);
 cudaError_t launch_trsm_tc(int m, int n, const double* Z, long ldz, const double* R, long ldr, double* Q, long ldq,
-                           void* ws, DevStatus* st, uint64_t limit_ns, int sms, cudaStream_t s);
+                           void* ws, DevStatus* st, uint64_t limit_ns, int sms, cudaStream_t s,
+                           const int* gate = nullptr, int want = 0);
 
 // Batched A-CholQR2 (k_batched.cu): one descriptor per instance, n <= 64, m <= 4096.
 constexpr int BATCH_MAX_N = 64;

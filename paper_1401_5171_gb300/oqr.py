@@ -108,6 +108,7 @@ def load(path: str | None = None):
     lib.oqr_potrf.argtypes = [vp, i, vp, l, d, vp, l, ctypes.POINTER(i), vp]
     lib.oqr_trsm.argtypes = [vp, i, i, vp, l, vp, l, vp, l, vp]
     lib.oqr_trsm_tc.argtypes = [vp, i, i, vp, l, vp, l, vp, l, vp]
+    lib.oqr_trsm_last.argtypes = [vp, i, i, vp, l, vp, l, vp, l, vp, l, vp]
     lib.oqr_cholqr2_host.argtypes = [vp, i, i, vp, l, vp, l, vp, l, vp, l, po, pi, vp]
     lib.oqr_rprod.argtypes = [vp, i, vp, l, vp, l, vp, l, vp]
     lib.oqr_check.argtypes = [vp, i, i, vp, l, vp, l, vp, l, ctypes.POINTER(d), ctypes.POINTER(d), vp]
@@ -143,7 +144,7 @@ def _raw(name):
 
 
 for _n in ("oqr_default_opts", "oqr_create", "oqr_destroy", "oqr_workspace_size", "oqr_set_workspace",
-           "oqr_get_status", "oqr_cholqr", "oqr_cholqr2", "oqr_cholqr2_host", "oqr_cgs2", "oqr_gram", "oqr_gram_noalloc", "oqr_gram_phases", "oqr_potrf", "oqr_trsm", "oqr_trsm_tc",
+           "oqr_get_status", "oqr_cholqr", "oqr_cholqr2", "oqr_cholqr2_host", "oqr_cgs2", "oqr_gram", "oqr_gram_noalloc", "oqr_gram_phases", "oqr_potrf", "oqr_trsm", "oqr_trsm_tc", "oqr_trsm_last",
            "oqr_rprod", "oqr_check", "oqr_repres", "oqr_diag_timeout", "oqr_set_batch_budget", "oqr_batched", "oqr_batched_mixed", "oqr_batched_default_splits", "oqr_features",
            "oqr_mlp_param_count", "oqr_mlp_forward", "oqr_mlp_grad", "oqr_mlp_adam", "oqr_glls", "oqr_symm", "oqr_cholqr2_tridiag", "oqr_gram_tridiag",
            "oqr_precholqr", "oqr_precholqr_tridiag", "oqr_tsqr", "oqr_batched_features"):
@@ -450,6 +451,18 @@ class Oqr:
 
     def oqr_trsm_tc(self, Z, R, Q=None, stream=None):
         return self.oqr_trsm(Z, R, Q=Q, stream=stream, name="oqr_trsm_tc")
+
+    def oqr_trsm_last(self, G, Z, R, Q=None, stream=None):
+        m, n = Z.shape
+        Q = Q if Q is not None else empty_colmajor(m, n, Z.device)
+        g, ldg = _m(G)
+        z, ldz = _m(Z)
+        r, ldr = _m(R)
+        q, ldq = _m(Q)
+        st = self.lib.oqr_trsm_last(self.ctx, m, n, g, ldg, z, ldz, r, ldr, q, ldq, self._stream(stream))
+        if st != OQR_OK:
+            raise OqrError(st, "oqr_trsm_last")
+        return Q
 
     def oqr_rprod(self, U, S, R=None, stream=None):
         n = U.shape[0]

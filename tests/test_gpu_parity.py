@@ -154,6 +154,53 @@ def test_trsm_tc_rowwise_backward_error(env):
     assert res.max() <= 4 * 150 * 2.0 ** -53, (res.max(), res_f.max())
 
 
+def _near_identity_gram(rng, n, frob):
+    """G = I + E, E symmetric with ||E||_F = frob, and R = chol(G) (upper, from the oracle)."""
+    E = rng.standard_normal((n, n))
+    E = E + E.T
+    G = np.eye(n) + frob * E / np.linalg.norm(E)
+    return G, oracle.chol_upper(G)
+
+
+@pytest.mark.parametrize("m,n", [(1, 1), (63, 20), (1000, 33), (3000, 65), (2000, 130), (4097, 256)])
+def test_trsm_last_near_identity(env, m, n):
+    # ||G - I||_F <= 0.5: Q = Z R^{-1} as one FP64-accurate product with the explicit inverse.  R's
+    # condition is at most sqrt(3), so the result matches the substitution at rounding level and every
+    # row's backward error |z - q R| stays within a small multiple of n u |q| |R|
+    torch, oqr, ctx = env
+    rng = np.random.default_rng(3 * m + n)
+    G, R = _near_identity_gram(rng, n, 0.45)
+    Z = rng.standard_normal((m, n))
+    Qr = oracle.trsm_right_upper(Z, R)
+    Gd, Rd = dev(torch, G, oqr), dev(torch, R, oqr)
+    Q = host(ctx.oqr_trsm_last(Gd, dev(torch, Z, oqr), Rd))
+    assert rel(Q, Qr) < 1e-14
+    res = np.abs(Z - Q @ R).max(axis=1) / (np.abs(Q) @ np.abs(R)).max(axis=1)
+    assert res.max() <= 4 * n * U
+    Zd = dev(torch, Z, oqr)
+    ctx.oqr_trsm_last(Gd, Zd, Rd, Q=Zd)  # in place
+    assert np.array_equal(host(Zd), Q)
+    if m * n >= 1000:  # the product route ran, not the substitution (their roundings differ somewhere)
+        assert not np.array_equal(Q, host(ctx.oqr_trsm(dev(torch, Z, oqr), Rd)))
+
+
+@pytest.mark.parametrize("m,n", [(63, 20), (3000, 65), (2000, 130)])
+def test_trsm_last_far_from_identity_is_the_rowwise_solve(env, m, n):
+    # ||G - I||_F > 0.5 (here 0.6, and a Gram of condition ~1e6): FP64 row-wise substitution runs, bit for bit
+    torch, oqr, ctx = env
+    rng = np.random.default_rng(5 * m + n)
+    cases = [_near_identity_gram(rng, n, 0.6)]
+    A, Zc = inputs.paper_case(4, 2 * n + 10, n, 1e4, 1e3, seed=n)
+    Gc = oracle.gram(A, Zc)
+    cases.append((Gc, oracle.chol_upper(Gc)))
+    for G, R in cases:
+        Z = rng.standard_normal((m, n))
+        Gd, Rd = dev(torch, G, oqr), dev(torch, R, oqr)
+        Q = host(ctx.oqr_trsm_last(Gd, dev(torch, Z, oqr), Rd))
+        assert np.array_equal(Q, host(ctx.oqr_trsm(dev(torch, Z, oqr), Rd)))
+        assert rel(Q, oracle.trsm_right_upper(Z, R)) < 1e-9
+
+
 @pytest.mark.parametrize("m,n", [(1, 1), (63, 20), (1000, 33), (2000, 20), (4097, 300), (640, 512)])
 def test_trsm_matches_oracle(env, m, n):
     torch, oqr, ctx = env

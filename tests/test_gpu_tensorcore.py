@@ -131,8 +131,8 @@ def test_tc_gram_tc2_definition(env, m, n):
 
 def test_shared_split_matches_separate_steps(env):
     # A-CholQR2 with a TC2 then an FP64_TC pass splits A once for both passes; composing the same
-    # steps from separate calls (each splitting A itself; tensor-core passes solve with oqr_trsm_tc)
-    # must give bit-identical Q and R
+    # steps from separate calls (each splitting A itself; the first pass solves with oqr_trsm_tc, the
+    # last with oqr_trsm_last) must give bit-identical Q and R
     torch, oqr, ctx = env
     A, Z = inputs.paper_case(4, 1100, 70, 1e5, 1e2, seed=21)
     Ad, Zd = dev(torch, oqr, A), dev(torch, oqr, Z)
@@ -142,7 +142,7 @@ def test_shared_split_matches_separate_steps(env):
     Q1 = ctx.oqr_trsm_tc(Zd, R1)
     G2 = ctx.oqr_gram(Ad, Q1, prec=oqr.OQR_FP64_TC)
     R2, st2, _ = ctx.oqr_potrf(G2)
-    Q2 = ctx.oqr_trsm_tc(Q1, R2)
+    Q2 = ctx.oqr_trsm_last(G2, Q1, R2)
     Rm = ctx.oqr_rprod(R2, R1)
     assert st == st1 == st2 == oqr.OQR_OK
     assert torch.equal(Q, Q2) and torch.equal(R, Rm)
