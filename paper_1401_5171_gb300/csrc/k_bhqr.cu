@@ -56,38 +56,9 @@ __device__ inline double block_sum(double v, double* red)
     return t;
 }
 
-// A grid-wide barrier for a cooperative launch (every block resident): count and gen in global memory,
-// zero before the launch.  The wait is time-limited: past limit_ns the status is raised and every block
-// returns false at this or its next barrier, so the kernel ends.
-__device__ inline bool grid_barrier(unsigned* count, unsigned* gen, uint64_t limit_ns, DevStatus* st, int* ok_s)
-{
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        volatile unsigned* vg = gen;
-        const unsigned g = *vg;
-        __threadfence();
-        bool ok = *(volatile int*)&st->code == 0;
-        if (atomicAdd(count, 1u) == gridDim.x - 1) {
-            *(volatile unsigned*)count = 0;
-            __threadfence();
-            atomicAdd(gen, 1u);
-        } else {
-            const uint64_t t0 = global_ns();
-            while (ok && *vg == g) {
-                if (*(volatile int*)&st->code != 0) ok = false;
-                else if (global_ns() - t0 > limit_ns) {
-                    raise_status(st, OQR_ERR_TIMEOUT, 0, TAG_DIAG);
-                    ok = false;
-                }
-            }
-        }
-        __threadfence();
-        *ok_s = ok ? 1 : 0;
-    }
-    __syncthreads();
-    return *ok_s != 0;
-}
-
+// The grid-wide barrier of the cooperative launches below is grid_barrier (oqr_internal.cuh): count and gen
+// in global memory, zero before the launch; past limit_ns the status is raised and every block returns
+// false at this or its next barrier, so the kernel ends.
 // The panel (mk x w, leading dimension ldp) factored by w Householder reflections, one cooperative launch:
 // per column, the reflector from the column's norm (partials summed in a fixed order by every block), the
 // partial dot products with the later columns; a grid barrier; their sums, the update of the later columns
@@ -114,7 +85,7 @@ __global__ void __launch_bounds__(HH_THREADS) hh_panel_kernel(int mk, int w, dou
         a = block_sum(a, red);
         if (threadIdx.x == 0) part[blockIdx.x] = a;
     }
-    if (!grid_barrier(bar, bar + 1, limit_ns, st, &ok_s)) return;
+    if (!grid_barrier(bar, bar + 1, limit_ns, st, &ok_s, TAG_DIAG)) return;
     for (int j = 0; j < w; ++j) {
         // the reflector
         if (threadIdx.x < 32) {
@@ -165,7 +136,7 @@ __global__ void __launch_bounds__(HH_THREADS) hh_panel_kernel(int mk, int w, dou
             dpart[(long)threadIdx.x * gridDim.x + blockIdx.x] = x;
         }
         if (j + 1 == w) break;  // nothing after the last column (the same for every block)
-        if (!grid_barrier(bar, bar + 1, limit_ns, st, &ok_s)) return;
+        if (!grid_barrier(bar, bar + 1, limit_ns, st, &ok_s, TAG_DIAG)) return;
         // the update of the later columns, and the next column's norm
         for (int c = j + 1 + warp; c < w; c += HH_THREADS / 32) {
             const double x = warp_sum_fixed(dpart + (long)c * gridDim.x, gridDim.x, lane);
@@ -183,7 +154,7 @@ __global__ void __launch_bounds__(HH_THREADS) hh_panel_kernel(int mk, int w, dou
         }
         a = block_sum(a, red);
         if (threadIdx.x == 0) part[blockIdx.x] = a;
-        if (!grid_barrier(bar, bar + 1, limit_ns, st, &ok_s)) return;
+        if (!grid_barrier(bar, bar + 1, limit_ns, st, &ok_s, TAG_DIAG)) return;
     }
 }
 
@@ -222,7 +193,7 @@ __global__ void __launch_bounds__(HH_THREADS) hh_panel_smem_kernel(int mk, int w
             if (r0 == 0 && nr > 0) xj[0] = tile[0];
         }
     }
-    if (!grid_barrier(bar, bar + 1, limit_ns, st, &ok_s)) return;
+    if (!grid_barrier(bar, bar + 1, limit_ns, st, &ok_s, TAG_DIAG)) return;
     for (int j = 0; j < w; ++j) {
         if (threadIdx.x < 32) {
             const double x0 = __ldcg(xj + j);  // in flight with the partials below
@@ -273,7 +244,7 @@ __global__ void __launch_bounds__(HH_THREADS) hh_panel_smem_kernel(int mk, int w
             dpart[(long)threadIdx.x * gridDim.x + blockIdx.x] = x;
         }
         if (j + 1 == w) break;  // the same for every block
-        if (!grid_barrier(bar, bar + 1, limit_ns, st, &ok_s)) return;
+        if (!grid_barrier(bar, bar + 1, limit_ns, st, &ok_s, TAG_DIAG)) return;
         {
             // this warp's columns c = j+1+warp, +8, ... (at most BH_B / 8): every partial load in flight
             // before the fixed-order sums
@@ -308,7 +279,7 @@ __global__ void __launch_bounds__(HH_THREADS) hh_panel_smem_kernel(int mk, int w
         }
         a = block_sum(a, red);
         if (threadIdx.x == 0) part[blockIdx.x] = a;
-        if (!grid_barrier(bar, bar + 1, limit_ns, st, &ok_s)) return;
+        if (!grid_barrier(bar, bar + 1, limit_ns, st, &ok_s, TAG_DIAG)) return;
     }
     __syncthreads();
     for (int e = threadIdx.x; e < nr * w; e += HH_THREADS) {

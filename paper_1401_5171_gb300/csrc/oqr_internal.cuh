@@ -56,6 +56,40 @@ __device__ inline uint64_t global_ns()
     return t;
 }
 
+// Barrier over the whole (cooperative) grid: count arrivals, the last one resets the count and advances the
+// generation; the others wait for the generation to change, giving up when the status word is set (every
+// block then returns) or after limit_ns (OQR_ERR_TIMEOUT with the given tag).  Returns false if the grid
+// must stop.  Data written before the barrier by other blocks is read after it through L2 (__ldcg).
+__device__ inline bool grid_barrier(unsigned* count, unsigned* gen, uint64_t limit_ns, DevStatus* st, int* ok_s,
+                                    int tag)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* vg = gen;
+        const unsigned g = *vg;
+        __threadfence();
+        bool ok = *(volatile int*)&st->code == 0;
+        if (atomicAdd(count, 1u) == gridDim.x - 1) {
+            *(volatile unsigned*)count = 0;
+            __threadfence();
+            atomicAdd(gen, 1u);
+        } else {
+            const uint64_t t0 = global_ns();
+            while (ok && *vg == g) {
+                if (*(volatile int*)&st->code != 0) ok = false;
+                else if (global_ns() - t0 > limit_ns) {
+                    raise_status(st, OQR_ERR_TIMEOUT, 0, tag);
+                    ok = false;
+                }
+            }
+        }
+        __threadfence();
+        *ok_s = ok ? 1 : 0;
+    }
+    __syncthreads();
+    return *ok_s != 0;
+}
+
 __device__ inline uint32_t smem_u32(const void* p)
 {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
