@@ -794,23 +794,9 @@ def main():
         torch.cuda.synchronize()
         ems = max_over_ranks(x0.elapsed_time(x1), world, dist, dev)
         tri = sum((m - j0) * min(256, m - j0) for j0 in range(0, m, 256))  # lower-triangle panels
-        # the host link alone: one pinned-to-device copy of as many bytes as a step sends, timed the same way
-        src = Ah.t().reshape(-1)[:tri + m * n]
-        dst = torch.empty(tri + m * n, dtype=torch.float64, device=dev)
-        with torch.cuda.stream(stream):
-            dst.copy_(src, non_blocking=True)
-            x0.record(stream)
-            for _ in range(2):
-                dst.copy_(src, non_blocking=True)
-            x1.record(stream)
-        torch.cuda.synchronize()
-        link_gbs = 2 * 8 * (tri + m * n) / (x0.elapsed_time(x1) * 1e-3) / 1e9
-        del dst
         e2e = {"value": whole_job_rate(world, args.e2e_steps, ems), "unit": "QR/s",
                "h2d_bytes_per_step": 8 * (tri + m * n), "d2h_bytes_per_step": 8 * (m * n + n * n),
-               "call": "oqr_cholqr2_host (pinned host buffers; lower triangle of A copied in 256-column panels)",
-               "host_link_h2d_gbs": link_gbs,
-               "link_bound_qr_s": link_gbs * 1e9 / (8 * (tri + m * n))}
+               "call": "oqr_cholqr2_host (pinned host buffers; lower triangle of A copied in 256-column panels)"}
         del Ah
 
     cpu = None
