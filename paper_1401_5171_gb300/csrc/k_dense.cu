@@ -332,34 +332,39 @@ __global__ void transpose_kernel(int rows, int cols, const double* __restrict__ 
     if (r < rows && c < cols) D[c + r * ldd] = t[threadIdx.x][threadIdx.y];
 }
 
-// out[0] = ||G - I||_F for a symmetric G (n x n) read from its lower triangle (an off-diagonal element counts
-// twice), one block, a fixed-order sum; gate[0] = (out[0] <= tol).  Thread t takes rows i = t mod 128 (+ 128
-// k) and, of each row, the columns j <= i with j = t / 128 (mod 8): warps read along columns (coalesced).
-constexpr int GD_THREADS = 1024, GD_ROWS = 128, GD_PHASES = GD_THREADS / GD_ROWS;
-__global__ void __launch_bounds__(GD_THREADS) gram_defect_kernel(int n, const double* __restrict__ G, long ldg,
-                                                                 double* out, int* gate, double tol)
+// ||G - I||_F for a symmetric G (n x n) read from its lower triangle (an off-diagonal element counts twice),
+// in two launches with a fixed summation order: block b sums the columns j = b (mod GD_BLOCKS) into
+// part[b] (FP64 being about 2 FMAs per clock per SM, one block would take tens of microseconds), then one
+// warp sums the parts, writes out[0] and gate[0] = (out[0] <= tol).
+constexpr int GD_BLOCKS = 64, GD_THREADS = 256;
+__global__ void __launch_bounds__(GD_THREADS) gram_defect_part_kernel(int n, const double* __restrict__ G, long ldg,
+                                                                      double* part)
 {
     __shared__ double red[GD_THREADS / 32];
-    const int t = threadIdx.x;
     double a = 0.0;
-    for (int i = t % GD_ROWS; i < n; i += GD_ROWS) {
-#pragma unroll 4
-        for (int j = t / GD_ROWS; j <= i; j += GD_PHASES) {
+    for (int j = blockIdx.x; j < n; j += GD_BLOCKS)
+        for (int i = j + threadIdx.x; i < n; i += GD_THREADS) {
             const double v = G[i + (long)j * ldg] - (i == j ? 1.0 : 0.0);
             a = fma(i == j ? v : 2.0 * v, v, a);
         }
-    }
     for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-    if ((t & 31) == 0) red[t >> 5] = a;
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
     __syncthreads();
-    if (t < 32) {
-        double v = red[t];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (t == 0) {
-            const double f = sqrt(v);
-            out[0] = f;
-            gate[0] = f <= tol ? 1 : 0;
-        }
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < GD_THREADS / 32; ++w) t += red[w];
+        part[blockIdx.x] = t;
+    }
+}
+
+__global__ void gram_defect_sum_kernel(const double* __restrict__ part, double* out, int* gate, double tol)
+{
+    double v = part[threadIdx.x] + part[threadIdx.x + 32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) {
+        const double f = sqrt(v);
+        out[0] = f;
+        gate[0] = f <= tol ? 1 : 0;
     }
 }
 
@@ -401,14 +406,16 @@ __global__ void __launch_bounds__(TI_THREADS) trinv_upper_kernel(int n, const do
         for (int u = 0; u < TI_AHEAD; ++u) {
             const int i = i0 - u;
             if (i < 0) break;  // uniform over the block
-            const double q = x[i] * dinv[i];
+            if (threadIdx.x < i) {  // only the threads with rows above i spend FP64 work
+                const double q = x[i] * dinv[i];
 #pragma unroll
-            for (int k = 0; k < RPT; ++k) {
-                const int row = threadIdx.x + k * TI_THREADS;
-                if (row < i) x[row] = fma(-q, ring[u][k], x[row]);
+                for (int k = 0; k < RPT; ++k) {
+                    const int row = threadIdx.x + k * TI_THREADS;
+                    if (row < i) x[row] = fma(-q, ring[u][k], x[row]);
+                }
             }
-            __syncthreads();                 // every read of x[i] is done; x[0..i-1] are updated
-            if (threadIdx.x == 0) x[i] = q;  // x[i] is read by no later step
+            __syncthreads();                               // every read of x[i] is done; x[0..i-1] updated
+            if (threadIdx.x == 0) x[i] = x[i] * dinv[i];  // x[i] is read by no later step
         }
 #pragma unroll
         for (int u = 0; u < TI_AHEAD; ++u)
@@ -825,7 +832,9 @@ cudaError_t launch_transpose(int rows, int cols, const double* S, long lds, doub
 cudaError_t launch_gram_defect(int n, const double* G, long ldg, double* out, int* gate, double gate_tol,
                                cudaStream_t s)
 {
-    gram_defect_kernel<<<1, GD_THREADS, 0, s>>>(n, G, ldg, out, gate, gate_tol);
+    static_assert(GD_BLOCKS == 64, "the sum kernel reads two parts per lane");
+    gram_defect_part_kernel<<<GD_BLOCKS, GD_THREADS, 0, s>>>(n, G, ldg, out + 1);
+    gram_defect_sum_kernel<<<1, 32, 0, s>>>(out + 1, out, gate, gate_tol);
     return cudaGetLastError();
 }
 

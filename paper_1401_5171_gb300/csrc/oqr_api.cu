@@ -125,7 +125,7 @@ void carve_last(C& c, int m, int n, bool on, LastSolve* L)
 {
     const size_t nn = (size_t)n * n, nm = (size_t)n * m;
     L->Rinv = c.template take<double>(on ? nn : 0);
-    L->defect = c.template take<double>(on ? 1 : 0);
+    L->defect = c.template take<double>(on ? GRAM_DEFECT_DOUBLES : 0);
     L->Xt = c.template take<double>(on ? nm : 0);
     L->gate = c.template take<int>(on ? 1 : 0);
     L->xtyws = c.template take<char>(on ? tc_xty_bytes(n, m, n) : 0);

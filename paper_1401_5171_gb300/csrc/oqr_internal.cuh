@@ -220,7 +220,9 @@ cudaError_t launch_transpose(int rows, int cols, const double* S, long lds, doub
 // X = R^{-1} (upper triangular, n x n, n <= TRINV_MAX_N), FP64 column-oriented back substitution.
 constexpr int TRINV_MAX_N = 8192;
 cudaError_t launch_trinv(int n, const double* R, long ldr, double* X, long ldx, const DevStatus* st, cudaStream_t s);
+// out[0] = ||G - I||_F (out holds GRAM_DEFECT_DOUBLES doubles: the result, then the blocks' partial sums);
 // gate[0] = 1 if ||G - I||_F <= gate_tol, else 0 (also for a NaN).
+constexpr int GRAM_DEFECT_DOUBLES = 1 + 64;
 cudaError_t launch_gram_defect(int n, const double* G, long ldg, double* out, int* gate, double gate_tol,
                                cudaStream_t s);
 // Shift for the shifted pass: s = c * u * (m n + n (n+1)) * ||A||_F * ||Z||_F^2.
